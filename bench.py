@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark of the one-obstacle MFS solution operator on one GB300.
+
+A step is one pass of the whole hot path on the smooth-body workload
+(r = 1 + 0.2 sum_j a_j cos js, k = 10, N = 180, M = 216, P = 120, q = 400,
+16 seeded plane waves): ring-kernel fill of the 61 distinct modal matrices,
+blocked Householder QR of each, then for the 16 waves the incident data,
+transform to modes, Q^H, triangular solve and inverse transform to point
+strengths.
+
+value = FP64-equivalent algorithmic TFLOP/s of the step: per distinct mode
+8 M N^2 - 8 N^3 / 3 (complex QR) plus per wave and mode 16 M N - 4 N^2
+(Q^H and back substitution), divided by the device time of the step. The
+L2 is flushed (a 256 MB write) before every timed step.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+Multi-GPU (torchrun): each rank runs its own copy of the workload (the
+operator's (obstacle, mode) tasks are independent); value sums the ranks'
+work over the slowest rank's time ("weak" scaling), no collective on the
+data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "operator build time (FP64-equiv TFLOP/s), per-wave apply us at 1e-10 rel err"
+FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_probe_gb300.md)
+
+
+def workload():
+    wl = synth.config_smooth()
+    return wl, wl.obstacles[0]
+
+
+def algorithmic_flops(M, N, P, W):
+    D = P // 2 + 1
+    qr = D * (8.0 * M * N * N - 8.0 * N ** 3 / 3.0)
+    apply = W * P * (16.0 * M * N - 4.0 * N * N)
+    return qr, apply
+
+
+def fill_flops(M, N, P, q):
+    """Algorithmic FP64 flops of the folded cosine transform of the fill:
+    4 flops (two FMAs on a complex sample) per (pair, node, mode);
+    the sample evaluations (sqrt, sincos, division) are not counted."""
+    D = P // 2 + 1
+    return 4.0 * M * N * (q // 2 + 1) * D
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_step(ob, dirs):
+    import oracle as O
+    coll, src, srcx = O.geometry(ob)
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    c = O.solve_modes(ob, fac, O.rhs_modes(O.incident_samples(ob, coll, dirs)))
+    O.point_strengths(c, ob.P)
+    return c
+
+
+def cpu_baseline_line(ob, dirs, steps=1):
+    """Oracle on the host cores: the whole smooth-body workload (all 61 modes, 16 waves)."""
+    qr, ap = algorithmic_flops(ob.M, ob.N, ob.P, dirs.shape[0])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run_oracle_step(ob, dirs)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": (qr + ap) / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds_per_step": dt,
+            "sample": f"full workload: fill+QR of {ob.P // 2 + 1} modes, apply of "
+                      f"{dirs.shape[0]} waves (numpy FP64, BLAS threads = host cores)"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    wl, ob = workload()
+    W = wl.n_waves
+    dirs_np = synth.plane_wave_directions(W, wl.wave_seed)
+    qr_fl, ap_fl = algorithmic_flops(ob.M, ob.N, ob.P, W)
+    config = {"workload": wl.name, "obstacle": "smooth r=1+0.2*sum a_j cos(js), seed 2",
+              "k": ob.k, "M": ob.M, "N": ob.N, "P": ob.P, "q": ob.q, "waves": W,
+              "distinct_modes": ob.P // 2 + 1, "l2": "flushed (256 MB write) before each timed step"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            run_oracle_step(ob, dirs_np)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run_oracle_step(ob, dirs_np)
+        dt = (time.perf_counter() - t0) / args.steps
+        v = (qr_fl + ap_fl) / dt / 1e12
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": "full workload per step"},
+                "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1506_05083_gb300 import axi
+
+    spec = axi.spec_from_obstacle(ob)
+    stream = torch.cuda.current_stream()
+    op = axi.Operator([spec])
+    dirs = torch.tensor(dirs_np, device=dev)
+    coef = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128, device=dev)
+    sigma = torch.empty((W, spec.cols, ob.P), dtype=torch.complex128, device=dev)
+    scratch = torch.empty(op.apply_scratch_bytes(W), dtype=torch.uint8, device=dev)
+    fill_out = torch.empty((ob.P // 2 + 1, spec.cols, spec.rows), dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        op.refactor()
+        f = op.incident(dirs)
+        op.apply(f, want_sigma=True, scratch=scratch, coef=coef, sigma=sigma)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1, e2 = evs[i]
+            e0.record(stream)
+            op.refactor()
+            e1.record(stream)
+            f = op.incident(dirs)
+            op.apply(f, want_sigma=True, scratch=scratch, coef=coef, sigma=sigma)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        # dominant-kernel timing: the fill kernel alone, same stream, L2 flushed
+        fev = []
+        for i in range(5):
+            flush.fill_(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            op.fill_modes(out=fill_out)
+            b.record(stream)
+            fev.append((a, b))
+        torch.cuda.synchronize()
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
+    build_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    apply_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
+    fill_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+    ms = float(np.mean(step_ms))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * (qr_fl + ap_fl) / (ms * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers: H2D of the wave
+    # directions from pinned memory, build + apply, D2H of the coefficients
+    dirs_host = torch.tensor(dirs_np).pin_memory()
+    coef_host = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128).pin_memory()
+    e2e = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dirs.copy_(dirs_host, non_blocking=True)
+        step()
+        coef_host.copy_(coef, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(e2e[1:]))
+    h2d = dirs_host.numel() * 8
+    d2h = coef_host.numel() * 16
+
+    fl_fill = fill_flops(ob.M, ob.N, ob.P, spec.q)
+    ach = fl_fill / (fill_ms * 1e-3) / 1e12
+    npanels = (spec.cols + 15) // 16
+    # fill + (panel, update) per panel step (no update after the last) + incident + 5 apply kernels
+    launches_per_step = 1 + npanels + (npanels - 1) + 1 + 5
+    torch.cuda.synchronize()
+    status = op.status()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "build_ms": float(np.mean(build_ms)),
+            "build_tflops": qr_fl / (np.mean(build_ms) * 1e-3) / 1e12,
+            "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
+            "e2e": {"value": ws * (qr_fl + ap_fl) / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"kernel": "fill_kernel", "bound": "alu", "achieved": ach,
+                         "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 DFMA probe (MEASURED_PEAKS.json has no FP64 entry)",
+                         "kernel_ms": fill_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "device_status": status,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline_line(ob, dirs_np)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

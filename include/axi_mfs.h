@@ -1,0 +1,262 @@
+/*
+ * axi_mfs.h -- C ABI of the GB300 one-obstacle MFS solution operator.
+ *
+ * The library builds and applies the solution operator A_0^+ of the
+ * axisymmetric method of fundamental solutions (Liu & Barnett, "Efficient
+ * numerical solution of acoustic scattering from doubly-periodic arrays of
+ * axisymmetric objects", arXiv:1506.05083):
+ *
+ *   build_operator : for every distinct azimuthal mode n = 0..P/2, fill the
+ *                    modal MFS matrix by the q-node trapezoid rule over
+ *                    azimuth (Sec. 3.1, eq. ptr) and factor it by blocked
+ *                    Householder QR (Sec. 3, eq. linsys: a backward-stable
+ *                    dense least-squares solve per mode);
+ *   apply_operator : FFT of boundary data to modes (eq. fhatquad), Q^H and
+ *                    triangular solve per mode (Sec. 4.4, never an explicit
+ *                    inverse), optional inverse FFT to point strengths
+ *                    (Sec. 4.2);
+ *   eval_field     : scattered potential, normal derivative or far field of
+ *                    the coefficients, optionally summed over the eight
+ *                    phased nearest lattice images (Sec. 4.2, A_else).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an axi_status; nothing aborts, throws or prints.
+ *   - Device pointers ("d_") are borrowed: the caller allocates and frees
+ *     them. Host pointers ("h_") are read during the call only.
+ *   - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) are asynchronous on that stream. Device-side
+ *     errors are latched into a status word of the operator and reported by
+ *     axi_operator_status() after the caller synchronises the stream.
+ *   - Handles are not thread-safe; one handle must not be used from two
+ *     host threads at once.
+ *   - Complex numbers are interleaved (re, im) doubles, 16 bytes each.
+ *   - Modes: coefficient and modal arrays store mode n, -P/2 < n <= P/2,
+ *     at index n mod P (FFT order). The scattered field is
+ *       u(rho, phi, z) = sum_n e^{+i n phi} sum_j A_n(rho, z; j) c_nj,
+ *     which pairs mode n of the data with mode n of the coefficients; the
+ *     ring kernel is even in n (A_n = A_{-n}), so modes +n and -n share
+ *     one factorisation.
+ */
+#ifndef AXI_MFS_H
+#define AXI_MFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } axi_c128;
+
+typedef enum {
+  AXI_OK = 0,
+  AXI_ERR_ARG = -1,          /* NULL pointer or invalid enum                  */
+  AXI_ERR_SHAPE = -2,        /* sizes violate P even, q even, q >= P, M >= N, */
+                             /* or exceed the compiled limits                 */
+  AXI_ERR_GEOMETRY = -3,     /* rho' <= 0, non-finite or coincident points    */
+  AXI_ERR_WORKSPACE = -4,    /* workspace too small or misaligned             */
+  AXI_ERR_CUDA = -5,         /* a CUDA runtime call failed                    */
+  AXI_ERR_TIMEOUT = -6,      /* a bounded device-side wait expired            */
+  AXI_ERR_NUMERIC = -7,      /* non-finite value met on the device            */
+  AXI_ERR_UNSUPPORTED = -8   /* option not built into this library            */
+} axi_status;
+
+typedef enum { AXI_BC_NEUMANN = 0, AXI_BC_TRANSMISSION = 1 } axi_bc;
+
+/* Arithmetic of the trailing-matrix updates of the QR and of the apply
+ * GEMMs. Fill, Householder panels and triangular solves are native FP64 in
+ * every mode. */
+typedef enum {
+  AXI_PREC_FP64 = 0,         /* native FP64 (DFMA)                              */
+  AXI_PREC_SPLIT_BF16 = 1    /* FP64 operands split into BF16 integer slices,   */
+                             /* products on tensor cores with exact FP32 sums,  */
+                             /* recombined in FP64 (Ozaki scheme)               */
+} axi_precision;
+
+typedef enum { AXI_SHAPE_POLAR = 0, AXI_SHAPE_CUP = 1 } axi_shape;
+
+/*
+ * axi_geometry -- discretise a generating curve (Sec. 3; Sec. 3.2 scheme (c);
+ * Sec. 3.4 for the exterior proxies).
+ *
+ *   shape, h_params, n_params : AXI_SHAPE_POLAR with params {r0, a_1..a_J}:
+ *       r(t) = r0 + sum_j a_j cos(j t), (rho, z) = r(t) (sin t, cos t);
+ *     AXI_SHAPE_CUP with params {a, b} (Fig. 2(c)): r(t) = 1 - a erf((t-pi/2)/a),
+ *       theta(t) = b - a + 2(1-(b-a)/pi) s_a(t-pi/2),
+ *       s_a(x) = (a/sqrt(pi)) e^{-x^2/a^2} + x erf(x/a), (rho, z) = r (sin, cos)(theta).
+ *   M, N       : collocation points t_m = pi(m-1/2)/M and proxies t_j = pi(j-1/2)/N.
+ *   tau        : complexification distance; proxies are zeta(t_j + i s tau) with
+ *                zeta = z + i rho and s = +-1 chosen so they fall inside the body.
+ *   h_coll     : out, host [M][4] doubles (rho, z, n_rho, n_z), unit outward normal.
+ *   h_src      : out, host [N][2] doubles (rho', z'), interior proxies.
+ *   h_src_ext  : out, host [N][2] doubles, exterior proxies (-tau), or NULL.
+ * Errors: AXI_ERR_ARG (NULL output, unknown shape), AXI_ERR_SHAPE (M<1, N<1),
+ *         AXI_ERR_GEOMETRY (a proxy with rho' <= 0 or non-finite values).
+ */
+axi_status axi_geometry(int32_t shape, const double *h_params, int32_t n_params,
+                        int32_t M, int32_t N, double tau,
+                        double *h_coll, double *h_src, double *h_src_ext);
+
+/*
+ * axi_choose_q -- quadrature count of the ring-kernel fill from Theorem 1:
+ * alpha_min = min over (m, j) of acosh(1 + d^2/(2 rho rho')); q is the
+ * smallest even 2^a 3^b 5^c >= max(2P, 37/alpha_min + P/2) (e^{-alpha q}
+ * ~ 1e-16 plus ~|n| extra nodes, as remarked after the theorem).
+ *   h_coll [M][4], h_src [N][2] as produced by axi_geometry; h_src_ext may be
+ *   NULL (Neumann). Writes *q. Errors: AXI_ERR_ARG, AXI_ERR_GEOMETRY.
+ */
+axi_status axi_choose_q(int32_t M, int32_t N, int32_t P, const double *h_coll,
+                        const double *h_src, const double *h_src_ext, int32_t *q);
+
+/* One obstacle of a batch. All pointers are host pointers read by
+ * axi_plan_create only. */
+typedef struct {
+  int32_t bc;            /* axi_bc                                                */
+  int32_t M, N, P, q;    /* P even >= 2, q even >= P, M >= N >= 1                 */
+  double k;              /* exterior wavenumber > 0                               */
+  double k_minus;        /* interior wavenumber (transmission), else ignored      */
+  const double *h_coll;    /* [M][4] rho, z, n_rho, n_z                           */
+  const double *h_src;     /* [N][2] interior proxies (rho' > 0)                  */
+  const double *h_src_ext; /* [N][2] exterior proxies (transmission) or NULL      */
+} axi_obstacle;
+
+typedef struct axi_plan_s axi_plan;
+typedef struct axi_operator_s axi_operator;
+
+/*
+ * axi_plan_create -- validate a batch of obstacles and lay out the device
+ * workspace of its operator. Copies the geometry; the caller's arrays may be
+ * freed afterwards. Per obstacle the operator holds, for D = P/2+1 distinct
+ * modes, the packed QR factors of the rows x cols modal matrix (rows = M,
+ * cols = N for Neumann; 2M x 2N for transmission, eq. trans), column-major
+ * with leading dimension rows, plus reflector scalars and compact-WY T blocks.
+ *   obs[n_obs] : obstacles; prec : axi_precision; *plan : out.
+ * Errors: AXI_ERR_ARG, AXI_ERR_SHAPE, AXI_ERR_GEOMETRY, AXI_ERR_UNSUPPORTED.
+ */
+axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
+                           axi_plan **plan);
+
+/* Bytes of device workspace the plan needs (256-byte aligned base required). */
+axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes);
+
+/*
+ * axi_build_operator -- fill and factor all distinct modes of all obstacles
+ * (Sec. 3.1 eq. ptr; Sec. 3 eq. linsys, linsysb; Sec. 3.4 eq. trans).
+ *   d_workspace, bytes : caller-owned device buffer of at least
+ *                        axi_plan_workspace_bytes(); it holds the operator and
+ *                        must outlive it.
+ *   stream             : cudaStream_t (void*). The build is asynchronous.
+ *   *op                : out, operator handle (owns no device memory). The
+ *                        plan must outlive the operator, and a plan backs
+ *                        one operator at a time.
+ * Errors: AXI_ERR_ARG, AXI_ERR_WORKSPACE, AXI_ERR_CUDA.
+ */
+axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes,
+                              void *stream, axi_operator **op);
+
+/*
+ * axi_refactor_operator -- re-run the fill and the factorisation of an
+ * existing operator in place (same plan, same workspace). Issues kernel
+ * launches only (no host copies, no allocation), so a caller may capture it
+ * in a CUDA graph. Errors: AXI_ERR_ARG, AXI_ERR_CUDA.
+ */
+axi_status axi_refactor_operator(axi_operator *op, void *stream);
+
+/*
+ * axi_fill_modes -- the fill step alone (Sec. 3.1, eq. ptr): write the D
+ * distinct modal matrices of obstacle `obs` to d_out [D][cols][rows]
+ * (column-major per mode; Neumann: A'_n; transmission: the 2x2 block of
+ * eq. trans), leaving the operator's factors untouched.
+ */
+axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, void *stream);
+
+/* Device view of the packed factors of one obstacle (read-only). For mode d,
+ * A + d*cols*rows is the rows x cols column-major array with R on and above
+ * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols
+ * holds the reflector scalars; T + (d*npanels + p)*nb*nb the nb x nb upper
+ * triangular compact-WY factor of panel p (column-major), so that the panel's
+ * reflectors multiply to I - V T V^H. */
+typedef struct {
+  int32_t rows, cols, D, nb, npanels;
+  const axi_c128 *d_A, *d_tau, *d_T;
+} axi_factor_view;
+
+axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *view);
+
+/*
+ * axi_incident_planewaves -- boundary data of W incident plane waves
+ * u_i = e^{i k d.x} (eq. ui) on the rows x P ring nodes (rho_m, 2 pi l/P, z_m)
+ * of obstacle `obs`: Neumann f = -du_i/dn (eq. neu); transmission
+ * [-u_i; -du_i/dn] (eq. trans).
+ *   d_dirs : device [W][3] unit directions d.
+ *   d_f    : out, device [W][rows][P] complex.
+ */
+axi_status axi_incident_planewaves(const axi_operator *op, int32_t obs, int32_t W,
+                                   const double *d_dirs, axi_c128 *d_f, void *stream);
+
+/*
+ * axi_apply_workspace_bytes -- scratch bytes axi_apply_operator needs for W
+ * right-hand sides of obstacle `obs` (modal data and RHS blocks).
+ */
+axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W,
+                                     size_t *bytes);
+
+/*
+ * axi_apply_operator -- apply A_0^+ of obstacle `obs` to W data sets
+ * (eq. fhatquad with q = P; Sec. 4.4 application of the factors):
+ *   fhat_n = (1/P) sum_l f_l e^{-2 pi i n l/P};  c_n = R^{-1} (Q^H fhat_n)_{1:cols}.
+ *   d_f      : device [W][rows][P] samples on the ring nodes.
+ *   d_coef   : out, device [W][P][cols], mode n at index n mod P.
+ *   d_sigma  : out or NULL, device [W][cols][P] point strengths
+ *              sigma_jl = (1/P) sum_n c_nj e^{2 pi i n l/P} (Sec. 4.2).
+ *   d_scratch, scratch_bytes : >= axi_apply_workspace_bytes(op, obs, W).
+ * Errors: AXI_ERR_ARG, AXI_ERR_WORKSPACE, AXI_ERR_CUDA.
+ */
+axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W,
+                              const axi_c128 *d_f, axi_c128 *d_coef, axi_c128 *d_sigma,
+                              void *d_scratch, size_t scratch_bytes, void *stream);
+
+typedef enum {
+  AXI_EVAL_POTENTIAL = 0,   /* u(x)                                    */
+  AXI_EVAL_NORMAL_DERIV = 1,/* du/dn_x, normals required              */
+  AXI_EVAL_FAR_FIELD = 2    /* F(xhat), targets are unit directions   */
+} axi_eval_kind;
+
+/*
+ * axi_eval_field -- evaluate the exterior scattered field of coefficients
+ * d_coef [W][P][cols] of obstacle `obs` from its point strengths
+ * (sigma over qe = P azimuthal nodes, Sec. 4.2):
+ *   POTENTIAL     u(x)  = sum_{j,l} G_k(x, y_jl) sigma_jl
+ *   NORMAL_DERIV  du/dn = sum_{j,l} dG_k/dn_x(x, y_jl) sigma_jl
+ *   FAR_FIELD     F(xh) = (1/4pi) sum_{j,l} e^{-i k xh.y_jl} sigma_jl.
+ * With lattice != NULL the sum runs over the eight phased nearest images
+ * y_jl + a e_x + b e_y, (a, b) in {-1,0,1}^2 \ {(0,0)}, weighted by
+ * alpha^a beta^b, alpha = e^{i k d_x e_x}, beta = e^{i k d_y e_y} (eq. bloch,
+ * Sec. 4.2 A_else) with d read per wave from d_dirs [W][3].
+ *   d_targets [T][3], d_normals [T][3] (NORMAL_DERIV), d_out [W][T].
+ *   d_scratch : >= W * cols * P * 16 bytes (point strengths).
+ */
+typedef struct { double ex, ey; } axi_lattice;
+
+axi_status axi_eval_field(const axi_operator *op, int32_t obs, int32_t W,
+                          const axi_c128 *d_coef, int32_t T, const double *d_targets,
+                          const double *d_normals, int32_t kind,
+                          const axi_lattice *lattice, const double *d_dirs,
+                          axi_c128 *d_out, void *d_scratch, size_t scratch_bytes,
+                          void *stream);
+
+/* Device status word of the operator (read after synchronising the stream). */
+axi_status axi_operator_status(const axi_operator *op);
+
+/* Release handles. Does not free the caller's workspace. NULL is accepted. */
+axi_status axi_operator_destroy(axi_operator *op);
+axi_status axi_plan_destroy(axi_plan *plan);
+
+/* Static description of a status code. */
+const char *axi_status_string(int32_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AXI_MFS_H */

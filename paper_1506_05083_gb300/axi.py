@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libaxi_mfs.so (include/axi_mfs.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. PyTorch supplies device memory and the current stream. If the
+library has not been built this module raises at first use; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaxi_mfs.so")
+
+BC_NEUMANN, BC_TRANSMISSION = 0, 1
+PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+SHAPE_POLAR, SHAPE_CUP = 0, 1
+EVAL_POTENTIAL, EVAL_NORMAL_DERIV, EVAL_FAR_FIELD = 0, 1, 2
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+class _Obstacle(C.Structure):
+    _fields_ = [("bc", C.c_int32), ("M", C.c_int32), ("N", C.c_int32), ("P", C.c_int32),
+                ("q", C.c_int32), ("k", C.c_double), ("k_minus", C.c_double),
+                ("h_coll", _dp), ("h_src", _dp), ("h_src_ext", _dp)]
+
+
+class _FactorView(C.Structure):
+    _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("D", C.c_int32), ("nb", C.c_int32),
+                ("npanels", C.c_int32), ("d_A", _vp), ("d_tau", _vp), ("d_T", _vp)]
+
+
+class _Lattice(C.Structure):
+    _fields_ = [("ex", C.c_double), ("ey", C.c_double)]
+
+
+# (name, restype, argtypes); every entry point declared in include/axi_mfs.h
+SIGNATURES = [
+    ("axi_geometry", C.c_int, [C.c_int32, _dp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
+    ("axi_choose_q", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, C.POINTER(C.c_int32)]),
+    ("axi_plan_create", C.c_int, [C.POINTER(_Obstacle), C.c_int32, C.c_int32, C.POINTER(_vp)]),
+    ("axi_plan_workspace_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    ("axi_build_operator", C.c_int, [_vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
+    ("axi_refactor_operator", C.c_int, [_vp, _vp]),
+    ("axi_fill_modes", C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
+    ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
+    ("axi_apply_workspace_bytes", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_apply_operator", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    ("axi_eval_field", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_int32,
+                                 C.POINTER(_Lattice), _vp, _vp, _vp, C.c_size_t, _vp]),
+    ("axi_operator_status", C.c_int, [_vp]),
+    ("axi_operator_destroy", C.c_int, [_vp]),
+    ("axi_plan_destroy", C.c_int, [_vp]),
+    ("axi_status_string", C.c_char_p, [C.c_int32]),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libaxi_mfs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class AxiError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {lib().axi_status_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code != 0:
+        raise AxiError(code, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def geometry(shape: int, params: Sequence[float], M: int, N: int, tau: float):
+    """axi_geometry: (coll [M][4], src [N][2], src_ext [N][2]) as numpy arrays."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    coll = np.zeros((M, 4))
+    src = np.zeros((N, 2))
+    srcx = np.zeros((N, 2))
+    _check(lib().axi_geometry(shape, _ptr(p), len(p), M, N, tau, _ptr(coll), _ptr(src), _ptr(srcx)),
+           "axi_geometry")
+    return coll, src, srcx
+
+
+def choose_q(M, N, P, coll, src, src_ext=None) -> int:
+    q = C.c_int32(0)
+    coll = np.ascontiguousarray(coll, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    sx = None if src_ext is None else np.ascontiguousarray(src_ext, dtype=np.float64)
+    _check(lib().axi_choose_q(M, N, P, _ptr(coll), _ptr(src), None if sx is None else _ptr(sx),
+                              C.byref(q)), "axi_choose_q")
+    return q.value
+
+
+class ObstacleSpec:
+    """Host description of one obstacle (arguments of axi_obstacle)."""
+
+    def __init__(self, bc, M, N, P, q, k, k_minus, coll, src, src_ext=None):
+        self.bc, self.M, self.N, self.P, self.q = int(bc), int(M), int(N), int(P), int(q)
+        self.k, self.k_minus = float(k), float(k_minus)
+        self.coll = np.ascontiguousarray(coll, dtype=np.float64)
+        self.src = np.ascontiguousarray(src, dtype=np.float64)
+        self.src_ext = None if src_ext is None else np.ascontiguousarray(src_ext, dtype=np.float64)
+
+    @property
+    def rows(self):
+        return self.M * (2 if self.bc == BC_TRANSMISSION else 1)
+
+    @property
+    def cols(self):
+        return self.N * (2 if self.bc == BC_TRANSMISSION else 1)
+
+
+class Operator:
+    """Plan + workspace + built operator (axi_plan_create / axi_build_operator)."""
+
+    def __init__(self, specs: List[ObstacleSpec], prec: int = PREC_FP64, device="cuda",
+                 stream=None):
+        self.specs = specs
+        arr = (_Obstacle * len(specs))()
+        for i, s in enumerate(specs):
+            arr[i] = _Obstacle(s.bc, s.M, s.N, s.P, s.q, s.k, s.k_minus, _ptr(s.coll), _ptr(s.src),
+                               _ptr(s.src_ext) if s.src_ext is not None else None)
+        plan = C.c_void_p()
+        _check(lib().axi_plan_create(arr, len(specs), prec, C.byref(plan)), "axi_plan_create")
+        self._plan = plan
+        nb = C.c_size_t(0)
+        _check(lib().axi_plan_workspace_bytes(plan, C.byref(nb)), "axi_plan_workspace_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        op = C.c_void_p()
+        _check(lib().axi_build_operator(plan, _dev(self.workspace), nb.value, _stream(stream),
+                                        C.byref(op)), "axi_build_operator")
+        self._op = op
+
+    def __del__(self):
+        try:
+            if getattr(self, "_op", None):
+                lib().axi_operator_destroy(self._op)
+            if getattr(self, "_plan", None):
+                lib().axi_plan_destroy(self._plan)
+        except Exception:
+            pass
+
+    def refactor(self, stream=None):
+        _check(lib().axi_refactor_operator(self._op, _stream(stream)), "axi_refactor_operator")
+
+    def status(self) -> int:
+        return lib().axi_operator_status(self._op)
+
+    def fill_modes(self, obs=0, out=None, stream=None) -> torch.Tensor:
+        s = self.specs[obs]
+        if out is None:
+            out = torch.empty((s.P // 2 + 1, s.cols, s.rows), dtype=torch.complex128,
+                              device=self.workspace.device)
+        _check(lib().axi_fill_modes(self._op, obs, _dev(out), _stream(stream)), "axi_fill_modes")
+        return out
+
+    def factors(self, obs=0):
+        """(A [D][cols][rows], tau [D][cols], T [D][npanels][nb][nb] col-major) views."""
+        v = _FactorView()
+        _check(lib().axi_operator_factors(self._op, obs, C.byref(v)), "axi_operator_factors")
+        base = self.workspace.data_ptr()
+
+        def view(ptr, shape):
+            off = ptr - base
+            n = int(np.prod(shape))
+            return self.workspace[off:off + 16 * n].view(torch.complex128).view(*shape)
+
+        A = view(v.d_A, (v.D, v.cols, v.rows))
+        tau = view(v.d_tau, (v.D, v.cols))
+        T = view(v.d_T, (v.D, v.npanels, v.nb, v.nb))
+        return A, tau, T, v.nb
+
+    def incident(self, dirs: torch.Tensor, obs=0, stream=None) -> torch.Tensor:
+        s = self.specs[obs]
+        W = dirs.shape[0]
+        f = torch.empty((W, s.rows, s.P), dtype=torch.complex128, device=dirs.device)
+        _check(lib().axi_incident_planewaves(self._op, obs, W, _dev(dirs), _dev(f), _stream(stream)),
+               "axi_incident_planewaves")
+        return f
+
+    def apply_scratch_bytes(self, W, obs=0) -> int:
+        nb = C.c_size_t(0)
+        _check(lib().axi_apply_workspace_bytes(self._op, obs, W, C.byref(nb)),
+               "axi_apply_workspace_bytes")
+        return nb.value
+
+    def apply(self, f: torch.Tensor, obs=0, want_sigma=False, scratch=None, coef=None,
+              sigma=None, stream=None):
+        s = self.specs[obs]
+        W = f.shape[0]
+        dev = f.device
+        if coef is None:
+            coef = torch.empty((W, s.P, s.cols), dtype=torch.complex128, device=dev)
+        if want_sigma and sigma is None:
+            sigma = torch.empty((W, s.cols, s.P), dtype=torch.complex128, device=dev)
+        need = self.apply_scratch_bytes(W, obs)
+        if scratch is None:
+            scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+        _check(lib().axi_apply_operator(self._op, obs, W, _dev(f), _dev(coef),
+                                        _dev(sigma) if want_sigma else None, _dev(scratch),
+                                        scratch.numel() * scratch.element_size(), _stream(stream)),
+               "axi_apply_operator")
+        return (coef, sigma) if want_sigma else coef
+
+    def eval_field(self, coef: torch.Tensor, targets: torch.Tensor, kind=EVAL_FAR_FIELD, obs=0,
+                   normals=None, lattice=None, dirs=None, scratch=None, stream=None):
+        s = self.specs[obs]
+        W = coef.shape[0]
+        T = targets.shape[0]
+        out = torch.empty((W, T), dtype=torch.complex128, device=coef.device)
+        need = 16 * W * s.cols * s.P
+        if scratch is None:
+            scratch = torch.empty(need, dtype=torch.uint8, device=coef.device)
+        lat = C.byref(_Lattice(*lattice)) if lattice is not None else None
+        _check(lib().axi_eval_field(self._op, obs, W, _dev(coef), T, _dev(targets), _dev(normals),
+                                    kind, lat, _dev(dirs), _dev(out), _dev(scratch),
+                                    scratch.numel() * scratch.element_size(), _stream(stream)),
+               "axi_eval_field")
+        return out
+
+
+def spec_from_obstacle(ob, q: Optional[int] = None) -> ObstacleSpec:
+    """ObstacleSpec from a synth.Obstacle, discretised by axi_geometry."""
+    coll, src, srcx = geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+    if q is None:
+        q = ob.q if ob.q else choose_q(ob.M, ob.N, ob.P, coll, src,
+                                       srcx if ob.bc == BC_TRANSMISSION else None)
+    return ObstacleSpec(ob.bc, ob.M, ob.N, ob.P, q, ob.k, ob.k_minus, coll, src,
+                        srcx if ob.bc == BC_TRANSMISSION else None)

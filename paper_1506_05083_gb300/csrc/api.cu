@@ -1,0 +1,354 @@
+// C-ABI entry points: validation, workspace layout, launch sequencing.
+// The device work is in fill.cu (A2), qr.cu (A3, A4-A6) and field.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "axi_internal.h"
+
+using axi::ObsDev;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct ObsHost {
+  ObsDev dev;  // device pointers are filled at build time from the offsets below
+  std::vector<double> coll, src, srcx, tab_cos, tab_s2;
+  std::vector<double2> tw_P;
+  size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
+};
+
+}  // namespace
+
+struct axi_plan_s {
+  std::vector<ObsHost> obs;
+  int prec = 0;
+  std::vector<int> task_obs, task_mode;   // sorted by obstacle panel count, descending
+  std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
+  std::vector<int> step_cols;             // widest trailing matrix at step p
+  size_t off_obsdev = 0, off_task_obs = 0, off_task_mode = 0, off_status = 0;
+  size_t bytes = 0;
+};
+
+struct axi_operator_s {
+  axi_plan_s *plan;
+  char *ws;
+  ObsDev *d_obs;
+  int *d_task_obs, *d_task_mode, *d_status;
+};
+
+namespace {
+
+axi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AXI_OK : AXI_ERR_CUDA; }
+
+axi_status validate(const axi_obstacle &o) {
+  if (!o.h_coll || !o.h_src) return AXI_ERR_ARG;
+  if (o.bc != AXI_BC_NEUMANN && o.bc != AXI_BC_TRANSMISSION) return AXI_ERR_ARG;
+  if (o.bc == AXI_BC_TRANSMISSION && !o.h_src_ext) return AXI_ERR_ARG;
+  if (o.M < 1 || o.N < 1 || o.M < o.N) return AXI_ERR_SHAPE;
+  if (o.P < 2 || (o.P & 1) || o.P > axi::kMaxP) return AXI_ERR_SHAPE;
+  if (o.q < o.P || (o.q & 1)) return AXI_ERR_SHAPE;
+  if (!(o.k > 0) || !std::isfinite(o.k)) return AXI_ERR_ARG;
+  if (o.bc == AXI_BC_TRANSMISSION && (!(o.k_minus > 0) || !std::isfinite(o.k_minus)))
+    return AXI_ERR_ARG;
+  for (int m = 0; m < o.M; ++m)
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(o.h_coll[4 * m + i])) return AXI_ERR_GEOMETRY;
+  for (int s = 0; s < (o.bc == AXI_BC_TRANSMISSION ? 2 : 1); ++s) {
+    const double *S = s ? o.h_src_ext : o.h_src;
+    for (int j = 0; j < o.N; ++j) {
+      if (!(S[2 * j] > 0) || !std::isfinite(S[2 * j + 1])) return AXI_ERR_GEOMETRY;
+      for (int m = 0; m < o.M; ++m) {
+        const double dr = o.h_coll[4 * m] - S[2 * j], dz = o.h_coll[4 * m + 1] - S[2 * j + 1];
+        if (dr * dr + dz * dz == 0.0) return AXI_ERR_GEOMETRY;  // target on a source ring
+      }
+    }
+  }
+  return AXI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *axi_status_string(int32_t s) {
+  switch (s) {
+    case AXI_OK: return "ok";
+    case AXI_ERR_ARG: return "invalid argument";
+    case AXI_ERR_SHAPE: return "invalid sizes";
+    case AXI_ERR_GEOMETRY: return "invalid geometry";
+    case AXI_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case AXI_ERR_CUDA: return "CUDA runtime error";
+    case AXI_ERR_TIMEOUT: return "device wait timed out";
+    case AXI_ERR_NUMERIC: return "non-finite value on the device";
+    case AXI_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec, axi_plan **out) {
+  if (!obs || !out || n_obs < 1) return AXI_ERR_ARG;
+  if (prec != AXI_PREC_FP64) return prec == AXI_PREC_SPLIT_BF16 ? AXI_ERR_UNSUPPORTED : AXI_ERR_ARG;
+  for (int i = 0; i < n_obs; ++i) {
+    axi_status s = validate(obs[i]);
+    if (s != AXI_OK) return s;
+  }
+  axi_plan_s *p = new (std::nothrow) axi_plan_s;
+  if (!p) return AXI_ERR_ARG;
+  p->prec = prec;
+  p->obs.resize(n_obs);
+  size_t off = 0;
+  p->off_obsdev = off; off = align_up(off + sizeof(ObsDev) * n_obs);
+  int ntask = 0;
+  for (int i = 0; i < n_obs; ++i) ntask += obs[i].P / 2 + 1;
+  p->off_task_obs = off; off = align_up(off + sizeof(int) * ntask);
+  p->off_task_mode = off; off = align_up(off + sizeof(int) * ntask);
+  p->off_status = off; off = align_up(off + sizeof(int));
+  for (int i = 0; i < n_obs; ++i) {
+    const axi_obstacle &o = obs[i];
+    ObsHost &h = p->obs[i];
+    ObsDev &d = h.dev;
+    std::memset(&d, 0, sizeof(d));
+    d.M = o.M; d.N = o.N; d.P = o.P; d.q = o.q; d.bc = o.bc;
+    d.rows = o.bc == AXI_BC_TRANSMISSION ? 2 * o.M : o.M;
+    d.cols = o.bc == AXI_BC_TRANSMISSION ? 2 * o.N : o.N;
+    d.D = o.P / 2 + 1;
+    d.npanels = (d.cols + axi::kNB - 1) / axi::kNB;
+    d.k = o.k; d.km = o.bc == AXI_BC_TRANSMISSION ? o.k_minus : 0.0;
+    h.coll.assign(o.h_coll, o.h_coll + 4 * o.M);
+    h.src.assign(o.h_src, o.h_src + 2 * o.N);
+    if (o.bc == AXI_BC_TRANSMISSION) h.srcx.assign(o.h_src_ext, o.h_src_ext + 2 * o.N);
+    h.tab_cos.resize(o.q);
+    for (int r = 0; r < o.q; ++r) h.tab_cos[r] = std::cos(2.0 * kPi * r / o.q);
+    h.tab_s2.resize(o.q / 2 + 1);
+    for (int l = 0; l <= o.q / 2; ++l) {
+      const double s = std::sin(kPi * l / o.q);
+      h.tab_s2[l] = s * s;
+    }
+    h.tw_P.resize(o.P);
+    for (int r = 0; r < o.P; ++r)
+      h.tw_P[r] = make_double2(std::cos(2.0 * kPi * r / o.P), -std::sin(2.0 * kPi * r / o.P));
+    h.off_coll = off; off = align_up(off + sizeof(double) * h.coll.size());
+    h.off_src = off; off = align_up(off + sizeof(double) * h.src.size());
+    h.off_srcx = off; off = align_up(off + sizeof(double) * h.srcx.size());
+    h.off_cos = off; off = align_up(off + sizeof(double) * h.tab_cos.size());
+    h.off_s2 = off; off = align_up(off + sizeof(double) * h.tab_s2.size());
+    h.off_tw = off; off = align_up(off + sizeof(double2) * h.tw_P.size());
+    h.off_A = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.rows);
+    h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
+    h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
+  }
+  p->bytes = off;
+  // QR task list: (obstacle, mode), obstacles with more panels first so the
+  // tasks still active at panel step s form a prefix of the list.
+  std::vector<int> order(n_obs);
+  for (int i = 0; i < n_obs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return p->obs[a].dev.npanels > p->obs[b].dev.npanels;
+  });
+  int maxpan = 0;
+  for (int i : order) {
+    for (int m = 0; m < p->obs[i].dev.D; ++m) { p->task_obs.push_back(i); p->task_mode.push_back(m); }
+    maxpan = std::max(maxpan, p->obs[i].dev.npanels);
+  }
+  p->step_tasks.assign(maxpan, 0);
+  p->step_cols.assign(maxpan, 0);
+  for (int s = 0; s < maxpan; ++s) {
+    for (int t = 0; t < (int)p->task_obs.size(); ++t) {
+      const ObsDev &d = p->obs[p->task_obs[t]].dev;
+      if (d.npanels > s) {
+        p->step_tasks[s] = t + 1;
+        const int k0 = s * axi::kNB, nbp = std::min(axi::kNB, d.cols - k0);
+        p->step_cols[s] = std::max(p->step_cols[s], d.cols - k0 - nbp);
+      }
+    }
+  }
+  *out = p;
+  return AXI_OK;
+}
+
+axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes) {
+  if (!plan || !bytes) return AXI_ERR_ARG;
+  *bytes = plan->bytes;
+  return AXI_OK;
+}
+
+axi_status axi_plan_destroy(axi_plan *plan) {
+  delete plan;
+  return AXI_OK;
+}
+
+static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
+  axi_plan_s *p = op->plan;
+  cudaError_t e = cudaMemsetAsync(op->d_status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return AXI_ERR_CUDA;
+  for (size_t i = 0; i < p->obs.size(); ++i) {
+    const ObsDev &d = p->obs[i].dev;
+    e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st);
+    if (e != cudaSuccess) return AXI_ERR_CUDA;
+  }
+  for (size_t s = 0; s < p->step_tasks.size(); ++s) {
+    e = axi::launch_qr_step(op->d_obs, op->d_task_obs, op->d_task_mode, p->step_tasks[s], (int)s,
+                            p->step_cols[s], st);
+    if (e != cudaSuccess) return AXI_ERR_CUDA;
+  }
+  return AXI_OK;
+}
+
+axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, void *stream,
+                              axi_operator **out) {
+  if (!plan || !d_workspace || !out) return AXI_ERR_ARG;
+  if (bytes < plan->bytes || (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1)))
+    return AXI_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *ws = static_cast<char *>(d_workspace);
+  std::vector<ObsDev> devs(plan->obs.size());
+  for (size_t i = 0; i < plan->obs.size(); ++i) {
+    ObsHost &h = plan->obs[i];
+    ObsDev &d = h.dev;
+    d.coll = reinterpret_cast<const double *>(ws + h.off_coll);
+    d.src = reinterpret_cast<const double *>(ws + h.off_src);
+    d.srcx = h.srcx.empty() ? nullptr : reinterpret_cast<const double *>(ws + h.off_srcx);
+    d.tab_cos = reinterpret_cast<const double *>(ws + h.off_cos);
+    d.tab_s2 = reinterpret_cast<const double *>(ws + h.off_s2);
+    d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
+    d.A = reinterpret_cast<double2 *>(ws + h.off_A);
+    d.tau = reinterpret_cast<double2 *>(ws + h.off_tau);
+    d.T = reinterpret_cast<double2 *>(ws + h.off_T);
+    d.status = reinterpret_cast<int *>(ws + plan->off_status);
+    devs[i] = d;
+    struct { size_t off; const void *src; size_t n; } cp[] = {
+        {h.off_coll, h.coll.data(), sizeof(double) * h.coll.size()},
+        {h.off_src, h.src.data(), sizeof(double) * h.src.size()},
+        {h.off_srcx, h.srcx.data(), sizeof(double) * h.srcx.size()},
+        {h.off_cos, h.tab_cos.data(), sizeof(double) * h.tab_cos.size()},
+        {h.off_s2, h.tab_s2.data(), sizeof(double) * h.tab_s2.size()},
+        {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
+    };
+    for (auto &c : cp) {
+      if (!c.n) continue;
+      if (cudaMemcpyAsync(ws + c.off, c.src, c.n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return AXI_ERR_CUDA;
+    }
+  }
+  if (cudaMemcpyAsync(ws + plan->off_obsdev, devs.data(), sizeof(ObsDev) * devs.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ws + plan->off_task_obs, plan->task_obs.data(),
+                      sizeof(int) * plan->task_obs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ws + plan->off_task_mode, plan->task_mode.data(),
+                      sizeof(int) * plan->task_mode.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return AXI_ERR_CUDA;
+  // the host staging vectors above must not be released before the copies finish
+  if (cudaStreamSynchronize(st) != cudaSuccess) return AXI_ERR_CUDA;
+  axi_operator_s *op = new (std::nothrow) axi_operator_s;
+  if (!op) return AXI_ERR_ARG;
+  op->plan = plan;
+  op->ws = ws;
+  op->d_obs = reinterpret_cast<ObsDev *>(ws + plan->off_obsdev);
+  op->d_task_obs = reinterpret_cast<int *>(ws + plan->off_task_obs);
+  op->d_task_mode = reinterpret_cast<int *>(ws + plan->off_task_mode);
+  op->d_status = reinterpret_cast<int *>(ws + plan->off_status);
+  axi_status s = run_build(op, st);
+  if (s != AXI_OK) { delete op; return s; }
+  *out = op;
+  return AXI_OK;
+}
+
+axi_status axi_refactor_operator(axi_operator *op, void *stream) {
+  if (!op) return AXI_ERR_ARG;
+  return run_build(op, static_cast<cudaStream_t>(stream));
+}
+
+axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, void *stream) {
+  if (!op || !d_out || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  return cuda_status(axi::launch_fill(op->d_obs, d, obs, reinterpret_cast<double2 *>(d_out), d.rows,
+                                      d.cols, static_cast<cudaStream_t>(stream)));
+}
+
+axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
+  if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  v->rows = d.rows; v->cols = d.cols; v->D = d.D; v->nb = axi::kNB; v->npanels = d.npanels;
+  v->d_A = reinterpret_cast<const axi_c128 *>(d.A);
+  v->d_tau = reinterpret_cast<const axi_c128 *>(d.tau);
+  v->d_T = reinterpret_cast<const axi_c128 *>(d.T);
+  return AXI_OK;
+}
+
+axi_status axi_incident_planewaves(const axi_operator *op, int32_t obs, int32_t W,
+                                   const double *d_dirs, axi_c128 *d_f, void *stream) {
+  if (!op || !d_dirs || !d_f || obs < 0 || obs >= (int)op->plan->obs.size() || W < 1)
+    return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  return cuda_status(axi::launch_incident(op->d_obs + obs, d, W, d_dirs,
+                                          reinterpret_cast<double2 *>(d_f),
+                                          static_cast<cudaStream_t>(stream)));
+}
+
+axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W, size_t *bytes) {
+  if (!op || !bytes || obs < 0 || obs >= (int)op->plan->obs.size() || W < 1) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  *bytes = align_up(sizeof(double2) * (size_t)d.D * 2 * W * d.rows);
+  return AXI_OK;
+}
+
+axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W, const axi_c128 *d_f,
+                              axi_c128 *d_coef, axi_c128 *d_sigma, void *d_scratch,
+                              size_t scratch_bytes, void *stream) {
+  if (!op || !d_f || !d_coef || !d_scratch || obs < 0 || obs >= (int)op->plan->obs.size() || W < 1)
+    return AXI_ERR_ARG;
+  size_t need = 0;
+  axi_apply_workspace_bytes(op, obs, W, &need);
+  if (scratch_bytes < need) return AXI_ERR_WORKSPACE;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  return cuda_status(axi::launch_apply(op->d_obs + obs, d, W, reinterpret_cast<const double2 *>(d_f),
+                                       reinterpret_cast<double2 *>(d_coef),
+                                       reinterpret_cast<double2 *>(d_sigma),
+                                       static_cast<double2 *>(d_scratch),
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+axi_status axi_eval_field(const axi_operator *op, int32_t obs, int32_t W, const axi_c128 *d_coef,
+                          int32_t T, const double *d_targets, const double *d_normals, int32_t kind,
+                          const axi_lattice *lattice, const double *d_dirs, axi_c128 *d_out,
+                          void *d_scratch, size_t scratch_bytes, void *stream) {
+  if (!op || !d_coef || !d_targets || !d_out || !d_scratch || obs < 0 ||
+      obs >= (int)op->plan->obs.size() || W < 1 || T < 1)
+    return AXI_ERR_ARG;
+  if (kind < AXI_EVAL_POTENTIAL || kind > AXI_EVAL_FAR_FIELD) return AXI_ERR_ARG;
+  if (kind == AXI_EVAL_NORMAL_DERIV && !d_normals) return AXI_ERR_ARG;
+  if (lattice && !d_dirs) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (scratch_bytes < sizeof(double2) * (size_t)W * d.cols * d.P) return AXI_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double2 *sigma = static_cast<double2 *>(d_scratch);
+  cudaError_t e = axi::launch_point_strengths(op->d_obs + obs, d, W,
+                                              reinterpret_cast<const double2 *>(d_coef), sigma, st);
+  if (e != cudaSuccess) return AXI_ERR_CUDA;
+  return cuda_status(axi::launch_eval(op->d_obs + obs, d, W, sigma, T, d_targets, d_normals, kind,
+                                      lattice, d_dirs, reinterpret_cast<double2 *>(d_out), st));
+}
+
+axi_status axi_operator_status(const axi_operator *op) {
+  if (!op) return AXI_ERR_ARG;
+  int s = 0;
+  if (cudaMemcpy(&s, op->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return AXI_ERR_CUDA;
+  if (s & axi::kStatTimeout) return AXI_ERR_TIMEOUT;
+  if (s & axi::kStatNonFinite) return AXI_ERR_NUMERIC;
+  return AXI_OK;
+}
+
+axi_status axi_operator_destroy(axi_operator *op) {
+  delete op;
+  return AXI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// Internal types shared by the host API and the kernels. Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/axi_mfs.h"
+
+namespace axi {
+
+constexpr int kNB = 16;        // Householder panel width (columns per block reflector)
+constexpr int kMaxModes = 128; // D = P/2 + 1 <= 128, i.e. P <= 254
+constexpr int kMaxP = 254;
+
+// Device status bits latched by kernels (OR-ed into ObsDev::status).
+enum : int { kStatNonFinite = 1, kStatTimeout = 2 };
+
+// Per-obstacle view of the operator in the caller's workspace (device side).
+struct ObsDev {
+  int M, N, P, q;         // discretisation
+  int rows, cols;         // modal matrix size: M x N (Neumann), 2M x 2N (transmission)
+  int D;                  // distinct modes n = 0..P/2
+  int bc;                 // axi_bc
+  int npanels;            // ceil(cols / kNB)
+  int pad_;
+  double k, km;           // exterior / interior wavenumber
+  const double *coll;     // [M][4] rho, z, n_rho, n_z
+  const double *src;      // [N][2] interior proxies
+  const double *srcx;     // [N][2] exterior proxies (transmission) or null
+  const double *tab_cos;  // [q]   cos(2 pi r / q)
+  const double *tab_s2;   // [q/2+1] sin^2(pi l / q)
+  const double2 *tw_P;    // [P]   e^{-2 pi i r / P}
+  double2 *A;             // [D][cols][rows] packed QR factors (column-major)
+  double2 *tau;           // [D][cols] reflector scalars
+  double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
+  int *status;            // device status word
+};
+
+// Launch wrappers (each returns the cudaError_t of its launch).
+cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
+                        double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
+cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                           int ntasks, int panel, int max_trailing_cols, cudaStream_t st);
+cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
+                            double2 *f, cudaStream_t st);
+cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,
+                         double2 *coef, double2 *sigma, double2 *X, cudaStream_t st);
+cudaError_t launch_eval(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *sigma,
+                        int T, const double *targets, const double *normals, int kind,
+                        const axi_lattice *lat, const double *dirs, double2 *out,
+                        cudaStream_t st);
+cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h_o, int W,
+                                   const double2 *coef, double2 *sigma, cudaStream_t st);
+
+}  // namespace axi

@@ -1,0 +1,149 @@
+// Step A2: ring-kernel modal fill (Sec. 3.1, eqs. ringkernel, ringkernelderiv, ptr).
+//
+// For a collocation point x_m = (rho_m, 0, z_m) with outward normal n_m and a
+// proxy ring (rho'_j, z'_j), the q-node periodic trapezoid rule gives
+//   A_n(m, j) = (1/q) sum_{l=0}^{q-1} g_l e^{-2 pi i n l / q},
+// g_l = G_k(x_m, y_j(phi_l)) or dG_k/dn_m, phi_l = 2 pi l / q. The samples are
+// even in l (g_l = g_{q-l}: the distance depends on cos phi only), so only
+// l = 0..q/2 are evaluated and the transform folds to a real cosine sum
+//   A_n = (1/q) [g_0 + (-1)^n g_{q/2} + 2 sum_{l=1}^{q/2-1} g_l cos(2 pi n l / q)],
+// which also shows A_n = A_{-n}: only n = 0..P/2 are produced.
+//
+// Mapping: one CTA = 32 consecutive collocation points (one per lane) x one
+// proxy ring x one kernel kind; 8 warps. Samples for a chunk of 32 nodes are
+// evaluated by all warps into shared memory, then warp w accumulates modes
+// n = w, w+8, ... in registers from the shared samples and a shared cosine
+// table indexed by (n l) mod q. Stores are 512-byte coalesced columns.
+// Arithmetic is native FP64 throughout (the ill-conditioned MFS matrices need
+// the full precision); the kernel is bound by the FP64 pipe.
+#include "axi_internal.h"
+
+namespace axi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kLanes = 32;
+constexpr int kChunk = 32;                 // trapezoid nodes per shared-memory chunk
+constexpr int kAcc = kMaxModes / 8;        // modes per thread
+constexpr double kInv4Pi = 0.07957747154594766788;
+
+__global__ void __launch_bounds__(kThreads)
+fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ out,
+            int ld_rows, int ld_cols) {
+  const ObsDev &o = obs_arr[oi];
+  extern __shared__ double smem[];
+  double *tcos = smem;                                             // [q]
+  double2 *samp = reinterpret_cast<double2 *>(smem + ((o.q + 1) & ~1));  // [kChunk][kLanes]
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int m = blockIdx.x * kLanes + lane;
+  const int j = blockIdx.y;
+  const int kind = blockIdx.z;
+  // Neumann: one kind (dG/dn, k, interior proxies). Transmission (eq. trans):
+  // 0: A (value, k, interior), 1: A' (derivative, k, interior),
+  // 2: A^- (value, k_-, exterior), 3: A'^- (derivative, k_-, exterior);
+  // the minus blocks enter the system with a negative sign.
+  const bool deriv = (o.bc == AXI_BC_NEUMANN) ? true : (kind & 1);
+  const bool ext = (o.bc == AXI_BC_TRANSMISSION) && kind >= 2;
+  const double k = ext ? o.km : o.k;
+  const double *S = ext ? o.srcx : o.src;
+  const double rs = S[2 * j], zs = S[2 * j + 1];
+  const int mm = m < o.M ? m : o.M - 1;
+  const double rho = o.coll[4 * mm], z = o.coll[4 * mm + 1];
+  const double nr = o.coll[4 * mm + 2], nz = o.coll[4 * mm + 3];
+  const int q = o.q, half = q / 2, D = o.D;
+
+  for (int i = threadIdx.x; i < q; i += kThreads) tcos[i] = o.tab_cos[i];
+
+  double2 acc[kAcc];
+#pragma unroll
+  for (int a = 0; a < kAcc; ++a) acc[a] = make_double2(0.0, 0.0);
+
+  const double dr = rho - rs, dz = z - zs;
+  const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
+  const double wq = kInv4Pi / q;
+
+  for (int l0 = 0; l0 <= half; l0 += kChunk) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kChunk / 8; ++i) {
+      const int ll = warp + 8 * i;
+      const int l = l0 + ll;
+      double2 s = make_double2(0.0, 0.0);
+      if (l <= half) {
+        // R^2 = (rho - rho')^2 + 4 rho rho' sin^2(phi/2) + (z - z')^2 (no cancellation)
+        const double R = sqrt(base + fourrr * o.tab_s2[l]);
+        const double inv = 1.0 / R;
+        double sn, cs;
+        sincos(k * R, &sn, &cs);
+        const double w = ((l == 0 || l == half) ? 1.0 : 2.0) * wq;
+        if (!deriv) {
+          s = make_double2(cs * inv * w, sn * inv * w);
+        } else {
+          // dG/dn_x = (n . (x - y)) (i k R - 1) e^{ikR} / (4 pi R^3)
+          const double ndot = nr * (rho - rs * tcos[l]) + nz * dz;
+          const double f = ndot * inv * inv * inv * w, kR = k * R;
+          s = make_double2(f * (-cs - kR * sn), f * (-sn + kR * cs));
+        }
+      }
+      samp[ll * kLanes + lane] = s;
+    }
+    __syncthreads();
+    const int lmax = min(kChunk, half + 1 - l0);
+    for (int ll = 0; ll < lmax; ++ll) {
+      const double2 s = samp[ll * kLanes + lane];
+      const int l = l0 + ll;
+      const int step = (8 * l) % q;
+      int idx = (warp * l) % q;
+#pragma unroll
+      for (int a = 0; a < kAcc; ++a) {
+        if (warp + 8 * a < D) {
+          const double c = tcos[idx];
+          acc[a].x = fma(c, s.x, acc[a].x);
+          acc[a].y = fma(c, s.y, acc[a].y);
+        }
+        idx += step;
+        if (idx >= q) idx -= q;
+      }
+    }
+  }
+
+  if (m >= o.M) return;
+  int row = m, col = j;
+  double sign = 1.0;
+  if (o.bc == AXI_BC_TRANSMISSION) {
+    row += (kind & 1) ? o.M : 0;
+    col += ext ? o.N : 0;
+    sign = ext ? -1.0 : 1.0;
+  }
+  const size_t mode_stride = (size_t)ld_cols * ld_rows;
+  double2 *dst = out + (size_t)col * ld_rows + row;
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < kAcc; ++a) {
+    const int n = warp + 8 * a;
+    if (n < D) {
+      const double2 v = make_double2(sign * acc[a].x, sign * acc[a].y);
+      bad |= !isfinite(v.x) || !isfinite(v.y);
+      dst[n * mode_stride] = v;
+    }
+  }
+  if (bad) atomicOr(o.status, kStatNonFinite);
+}
+
+}  // namespace
+
+cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out, int ld_rows,
+                        int ld_cols, cudaStream_t st) {
+  dim3 grid((h.M + kLanes - 1) / kLanes, h.N, h.bc == AXI_BC_TRANSMISSION ? 4 : 1);
+  size_t smem = sizeof(double) * ((h.q + 1) & ~1) + sizeof(double2) * kChunk * kLanes;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fill_kernel<<<grid, kThreads, smem, st>>>(d_obs, oi, out, ld_rows, ld_cols);
+  return cudaGetLastError();
+}
+
+}  // namespace axi

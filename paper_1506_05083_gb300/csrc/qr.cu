@@ -1,0 +1,498 @@
+// Steps A3 and A5: blocked complex Householder QR of every distinct modal
+// matrix, and application of the factors to right-hand sides.
+//
+// Sec. 3 (eq. linsys) solves each mode's rectangular system by a dense
+// backward-stable least-squares method; Sec. 4.4 applies the factors, never
+// an explicit inverse. We use unpivoted Householder QR with the LAPACK
+// reflector convention: H = I - tau v v^H, v[0] = 1, and H^H maps the column
+// (alpha; x) to (beta; 0) with real beta = -sign(Re alpha) ||(alpha; x)||,
+// tau = (beta - alpha)/beta, v = x/(alpha - beta).
+//
+// Blocking (compact WY): a panel of kNB columns is factored by one CTA per
+// (obstacle, mode); its reflectors combine into H_1 ... H_nb = I - V T V^H
+// with T upper triangular, and the trailing matrix is updated by
+//   A22 <- (I - V T^H V^H) A22 = A22 - V (T^H (V^H A22)),
+// in a second launch whose CTAs each own a tile of trailing columns. The
+// apply runs the same block-reflector product over the stored panels for a
+// tile of right-hand-side columns, then a blocked back substitution with R.
+#include "axi_internal.h"
+
+namespace axi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTN = 16;   // columns of the target per CTA in block-reflector kernels
+constexpr int kRC = 32;   // rows per shared-memory chunk
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cjmul(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum `n` complex partials over the CTA; result in out[0..n). Contains syncs.
+__device__ void block_sum_c(double2 *part, int n, double (*red)[2 * kNB], double2 *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < n; ++r) {
+    double x = warp_sum(part[r].x), y = warp_sum(part[r].y);
+    if (lane == 0) { red[warp][2 * r] = x; red[warp][2 * r + 1] = y; }
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    double x = 0, y = 0;
+    for (int w = 0; w < kThreads / 32; ++w) { x += red[w][2 * threadIdx.x]; y += red[w][2 * threadIdx.x + 1]; }
+    out[threadIdx.x] = make_double2(x, y);
+  }
+  __syncthreads();
+}
+
+// Element (i, a) of the panel's reflector matrix V (rows i >= k0; unit
+// diagonal, zeros above it, stored entries below it).
+__device__ __forceinline__ double2 vget(const double2 *A, int lda, int rows, int k0, int nbp,
+                                        int i, int a) {
+  if (a >= nbp || i >= rows) return make_double2(0.0, 0.0);
+  const int c = k0 + a;
+  if (i < c) return make_double2(0.0, 0.0);
+  if (i == c) return make_double2(1.0, 0.0);
+  return A[(size_t)c * lda + i];
+}
+
+// ---------------------------------------------------------------------------
+// Panel: unblocked Householder on columns [k0, k0+nbp) of one modal matrix,
+// then the T factor of the compact WY form (forward, column-wise):
+//   T(j, j) = tau_j,  T(0:j, j) = -tau_j T(0:j, 0:j) (V(:, 0:j)^H v_j).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int lda = o.rows, rows = o.rows;
+  const int k0 = p * kNB;
+  const int nbp = min(kNB, o.cols - k0);
+  double2 *A = o.A + (size_t)d * o.cols * lda;
+  const int tid = threadIdx.x;
+
+  __shared__ double red[kThreads / 32][2 * kNB];
+  __shared__ double2 wsh[kNB];
+  __shared__ double2 G[kNB][kNB];
+  __shared__ double2 Tsh[kNB][kNB];
+  __shared__ double2 taush[kNB];
+
+  for (int jj = 0; jj < nbp; ++jj) {
+    const int c = k0 + jj;
+    double2 *col = A + (size_t)c * lda;
+    // ||x||^2 of the part below the diagonal
+    double s = 0.0;
+    for (int i = c + 1 + tid; i < rows; i += kThreads) {
+      const double2 v = col[i];
+      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    double2 part[kNB];
+    part[0] = make_double2(s, 0.0);
+    block_sum_c(part, 1, red, wsh);
+    const double xn2 = wsh[0].x;
+    const double2 alpha = col[c];
+    double beta;
+    double2 tau, scale;
+    if (xn2 == 0.0 && alpha.y == 0.0) {
+      beta = alpha.x; tau = make_double2(0.0, 0.0); scale = make_double2(0.0, 0.0);
+    } else {
+      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+      beta = -copysign(nrm, alpha.x);
+      tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+      const double2 den = make_double2(alpha.x - beta, alpha.y);
+      const double dd = den.x * den.x + den.y * den.y;
+      scale = make_double2(den.x / dd, -den.y / dd);       // 1 / (alpha - beta)
+    }
+    const int nrem = nbp - jj - 1;
+#pragma unroll
+    for (int r = 0; r < kNB; ++r) part[r] = make_double2(0.0, 0.0);
+    for (int i = c + 1 + tid; i < rows; i += kThreads) {
+      const double2 v = cmul(col[i], scale);
+      col[i] = v;
+#pragma unroll
+      for (int r = 0; r < kNB - 1; ++r)
+        if (r < nrem) part[r] = cadd(part[r], cjmul(v, A[(size_t)(c + 1 + r) * lda + i]));
+    }
+    if (tid == 0) {
+#pragma unroll
+      for (int r = 0; r < kNB - 1; ++r)
+        if (r < nrem) part[r] = cadd(part[r], A[(size_t)(c + 1 + r) * lda + c]);
+    }
+    if (nrem > 0) block_sum_c(part, nrem, red, wsh);
+    // A(c:, c2) -= v conj(tau) w_c2   (H^H applied to the rest of the panel)
+    const double2 ctau = make_double2(tau.x, -tau.y);
+    for (int i = c + tid; i < rows; i += kThreads) {
+      const double2 v = (i == c) ? make_double2(1.0, 0.0) : col[i];
+      for (int r = 0; r < nrem; ++r) {
+        const double2 w = cmul(ctau, wsh[r]);
+        double2 *x = &A[(size_t)(c + 1 + r) * lda + i];
+        const double2 vw = cmul(v, w);
+        *x = make_double2(x->x - vw.x, x->y - vw.y);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      col[c] = make_double2(beta, 0.0);
+      o.tau[(size_t)d * o.cols + c] = tau;
+      taush[jj] = tau;
+      if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
+    }
+    __syncthreads();
+  }
+
+  // Gram matrix G(a, b) = v_a^H v_b, a < b (v_b vanishes above row k0 + b).
+  const int lane = tid & 31, warp = tid >> 5;
+  const int npair = nbp * (nbp - 1) / 2;
+  for (int pi = warp; pi < npair; pi += kThreads / 32) {
+    int b = 1, acc = 0;
+    while (acc + b <= pi) { acc += b; ++b; }
+    const int a = pi - acc;
+    const double2 *va = A + (size_t)(k0 + a) * lda;
+    const double2 *vb = A + (size_t)(k0 + b) * lda;
+    double2 g = make_double2(0.0, 0.0);
+    for (int i = k0 + b + 1 + lane; i < rows; i += 32) g = cadd(g, cjmul(va[i], vb[i]));
+    g.x = warp_sum(g.x);
+    g.y = warp_sum(g.y);
+    if (lane == 0) {
+      const double2 vab = va[k0 + b];  // v_a at row k0+b, times v_b = 1 there
+      G[a][b] = make_double2(g.x + vab.x, g.y - vab.y);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < kNB; ++j)
+      for (int i = 0; i < kNB; ++i) Tsh[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < nbp; ++j) {
+      const double2 tj = taush[j];
+      Tsh[j][j] = tj;
+      for (int i = 0; i < j; ++i) {
+        double2 zz = make_double2(0.0, 0.0);
+        for (int l = i; l < j; ++l) zz = cadd(zz, cmul(Tsh[i][l], G[l][j]));
+        const double2 t = cmul(tj, zz);
+        Tsh[i][j] = make_double2(-t.x, -t.y);
+      }
+    }
+  }
+  __syncthreads();
+  double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  for (int e = tid; e < kNB * kNB; e += kThreads) Tg[e] = Tsh[e % kNB][e / kNB];
+}
+
+// ---------------------------------------------------------------------------
+// X(k0:rows, 0:ncols) <- (I - V T^H V^H) X(k0:rows, 0:ncols) for one panel.
+// One CTA, kTN target columns; FP64. Thread (a, c) = (tid / kTN, tid % kTN).
+// ---------------------------------------------------------------------------
+struct BrSmem {
+  double2 V[kRC][kNB + 1];
+  double2 X[kRC][kTN + 1];
+  double2 W[kNB][kTN + 1];
+  double2 T[kNB][kNB + 1];
+};
+
+__device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, int rows, int k0,
+                                        int nbp, const double2 *__restrict__ Tg,
+                                        double2 *__restrict__ X, int ldx, int ncols, BrSmem &sm) {
+  const int tid = threadIdx.x;
+  const int ta = tid / kTN, tc = tid % kTN;
+  for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
+  double2 w = make_double2(0.0, 0.0);
+  for (int r0 = k0; r0 < rows; r0 += kRC) {
+    __syncthreads();
+    for (int e = tid; e < kRC * kNB; e += kThreads) {
+      const int r = e % kRC, a = e / kRC;
+      sm.V[r][a] = vget(A, lda, rows, k0, nbp, r0 + r, a);
+    }
+    for (int e = tid; e < kRC * kTN; e += kThreads) {
+      const int r = e % kRC, c = e / kRC;
+      const int i = r0 + r;
+      sm.X[r][c] = (i < rows && c < ncols) ? X[(size_t)c * ldx + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < kRC; ++r) w = cadd(w, cjmul(sm.V[r][ta], sm.X[r][tc]));
+  }
+  sm.W[ta][tc] = w;
+  __syncthreads();
+  // W' = T^H W  (T upper triangular, so T^H is lower)
+  double2 wp = make_double2(0.0, 0.0);
+  for (int b = 0; b <= ta; ++b) wp = cadd(wp, cjmul(sm.T[b][ta], sm.W[b][tc]));
+  __syncthreads();
+  sm.W[ta][tc] = wp;
+  __syncthreads();
+  // X -= V W'
+  const int r = tid % kRC, cg = tid / kRC;  // 8 column groups
+  for (int r0 = k0; r0 < rows; r0 += kRC) {
+    const int i = r0 + r;
+    double2 vrow[kNB];
+#pragma unroll
+    for (int a = 0; a < kNB; ++a) vrow[a] = vget(A, lda, rows, k0, nbp, i, a);
+    if (i < rows) {
+      for (int c = cg; c < ncols; c += kThreads / kRC) {
+        double2 x = X[(size_t)c * ldx + i];
+#pragma unroll
+        for (int a = 0; a < kNB; ++a) {
+          const double2 t = cmul(vrow[a], sm.W[a][c]);
+          x.x -= t.x;
+          x.y -= t.y;
+        }
+        X[(size_t)c * ldx + i] = x;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+qr_update_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                 const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int k0 = p * kNB;
+  const int nbp = min(kNB, o.cols - k0);
+  const int c0 = k0 + nbp + blockIdx.y * kTN;
+  if (c0 >= o.cols) return;
+  const int ncols = min(kTN, o.cols - c0);
+  __shared__ BrSmem sm;
+  double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  apply_block_reflector_h(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows, ncols,
+                          sm);
+}
+
+// Q^H applied to the RHS block of mode d: X_d is [2W][rows] column-major.
+__global__ void __launch_bounds__(kThreads)
+apply_qh_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
+  const ObsDev &o = *od;
+  const int d = blockIdx.x;
+  const int c0 = blockIdx.y * kTN;
+  if (c0 >= ncols_total) return;
+  const int ncols = min(kTN, ncols_total - c0);
+  __shared__ BrSmem sm;
+  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
+  for (int p = 0; p < o.npanels; ++p) {
+    const int k0 = p * kNB;
+    const int nbp = min(kNB, o.cols - k0);
+    const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+    apply_block_reflector_h(A, o.rows, o.rows, k0, nbp, Tg, Xd, o.rows, ncols, sm);
+  }
+}
+
+// Blocked back substitution R X = Y on the first `cols` rows of each RHS
+// column (R real-diagonal upper triangle of the packed factors). One warp
+// per RHS column inside 32x32 diagonal blocks; rows above are updated with
+// the solved block before moving up.
+constexpr int kTB = 32;
+__global__ void __launch_bounds__(kThreads)
+trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
+  const ObsDev &o = *od;
+  const int d = blockIdx.x;
+  const int c0 = blockIdx.y * kTN;
+  if (c0 >= ncols_total) return;
+  const int ncols = min(kTN, ncols_total - c0);
+  const double2 *R = o.A + (size_t)d * o.cols * o.rows;
+  const int ld = o.rows, n = o.cols;
+  double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
+  __shared__ double2 Rb[kTB][kTB + 1];
+  __shared__ double2 Yb[kTB][kTN + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (n + kTB - 1) / kTB;
+  for (int ib = nblk - 1; ib >= 0; --ib) {
+    const int r0 = ib * kTB, nb = min(kTB, n - r0);
+    __syncthreads();
+    for (int e = tid; e < kTB * kTB; e += kThreads) {
+      const int r = e % kTB, c = e / kTB;
+      Rb[r][c] = (r < nb && c < nb) ? R[(size_t)(r0 + c) * ld + r0 + r] : make_double2(0.0, 0.0);
+    }
+    for (int e = tid; e < kTB * kTN; e += kThreads) {
+      const int r = e % kTB, c = e / kTB;
+      Yb[r][c] = (r < nb && c < ncols) ? Xd[(size_t)c * ld + r0 + r] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int c = warp; c < ncols; c += kThreads / 32) {
+      double2 y = Yb[lane][c];
+      for (int rr = nb - 1; rr >= 0; --rr) {
+        double2 x = make_double2(0.0, 0.0);
+        if (lane == rr) {
+          const double piv = Rb[rr][rr].x;  // real diagonal (beta of the reflector)
+          y = make_double2(y.x / piv, y.y / piv);
+          x = y;
+        }
+        x.x = __shfl_sync(0xffffffffu, x.x, rr);
+        x.y = __shfl_sync(0xffffffffu, x.y, rr);
+        if (lane < rr) {
+          const double2 t = cmul(Rb[lane][rr], x);
+          y.x -= t.x;
+          y.y -= t.y;
+        }
+      }
+      Yb[lane][c] = y;
+    }
+    __syncthreads();
+    for (int e = tid; e < kTB * kTN; e += kThreads) {
+      const int r = e % kTB, c = e / kTB;
+      if (r < nb && c < ncols) Xd[(size_t)c * ld + r0 + r] = Yb[r][c];
+    }
+    // rows above: Y(0:r0, c) -= R(0:r0, r0:r0+nb) X_b(:, c)
+    for (int e = tid; e < r0 * kTN; e += kThreads) {
+      const int r = e % r0, c = e / r0;
+      if (c >= ncols) continue;
+      double2 acc = Xd[(size_t)c * ld + r];
+      for (int b = 0; b < nb; ++b) {
+        const double2 t = cmul(R[(size_t)(r0 + b) * ld + r], Yb[b][c]);
+        acc.x -= t.x;
+        acc.y -= t.y;
+      }
+      Xd[(size_t)c * ld + r] = acc;
+    }
+  }
+}
+
+// fhat_n = (1/P) sum_l f_l e^{-2 pi i n l / P} (eq. fhatquad with q = P),
+// written as RHS blocks X[d][2w + s][row]: s = 0 holds mode +d, s = 1 mode -d.
+constexpr int kDR = 16;  // rows per CTA
+__global__ void __launch_bounds__(kThreads)
+rhs_dft_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__ f,
+               double2 *__restrict__ X) {
+  const ObsDev &o = *od;
+  const int P = o.P, rows = o.rows;
+  const int w = blockIdx.y;
+  const int r0 = blockIdx.x * kDR;
+  extern __shared__ double2 sh[];
+  double2 *tw = sh;            // [P]
+  double2 *F = sh + P;         // [kDR][P + 1] (padded rows: conflict-free reads)
+  const int ldF = P + 1;
+  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = o.tw_P[i];
+  for (int e = threadIdx.x; e < kDR * P; e += kThreads) {
+    const int r = e / P, l = e % P;
+    F[r * ldF + l] = (r0 + r < rows) ? f[((size_t)w * rows + r0 + r) * P + l] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int r = threadIdx.x % kDR, tn = threadIdx.x / kDR;  // 16 mode lanes
+  const int row = r0 + r;
+  const double invP = 1.0 / P;
+  const int ncol = 2 * W;
+  for (int ni = tn; ni < P; ni += kThreads / kDR) {
+    double2 acc = make_double2(0.0, 0.0);
+    int idx = 0;
+    for (int l = 0; l < P; ++l) {
+      acc = cadd(acc, cmul(F[r * ldF + l], tw[idx]));
+      idx += ni;
+      if (idx >= P) idx -= P;
+    }
+    acc.x *= invP;
+    acc.y *= invP;
+    if (row < rows) {
+      const int dmode = ni <= P / 2 ? ni : P - ni;
+      const int s = ni <= P / 2 ? 0 : 1;
+      X[((size_t)dmode * ncol + 2 * w + s) * rows + row] = acc;
+      if (dmode == 0 || 2 * dmode == P)  // +-n coincide: duplicate to keep X defined
+        X[((size_t)dmode * ncol + 2 * w + 1) * rows + row] = acc;
+    }
+  }
+}
+
+// coef[w][n mod P][j] from the solved blocks.
+__global__ void scatter_coef_kernel(const ObsDev *__restrict__ od, int W,
+                                    const double2 *__restrict__ X, double2 *__restrict__ coef) {
+  const ObsDev &o = *od;
+  const int P = o.P, cols = o.cols, rows = o.rows;
+  const int ni = blockIdx.x, w = blockIdx.y;
+  const int dmode = ni <= P / 2 ? ni : P - ni;
+  const int s = ni <= P / 2 ? 0 : 1;
+  const double2 *src = X + ((size_t)dmode * 2 * W + 2 * w + s) * rows;
+  double2 *dst = coef + ((size_t)w * P + ni) * cols;
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) dst[j] = src[j];
+}
+
+// sigma[w][j][l] = (1/P) sum_n c[w][n][j] e^{+2 pi i n l / P}  (Sec. 4.2)
+__global__ void __launch_bounds__(kThreads)
+point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__ coef,
+                      double2 *__restrict__ sigma) {
+  const ObsDev &o = *od;
+  const int P = o.P, cols = o.cols;
+  const int w = blockIdx.y;
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  extern __shared__ double2 sh[];
+  double2 *tw = sh;  // e^{-2 pi i r / P}
+  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = o.tw_P[i];
+  __syncthreads();
+  if (j >= cols) return;
+  const double invP = 1.0 / P;
+  for (int l = threadIdx.x >> 5; l < P; l += kThreads / 32) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int ni = 0; ni < P; ++ni) {
+      const int nn = ni <= P / 2 ? ni : ni - P;      // signed mode
+      int idx = (int)(((long long)nn * l) % P);
+      if (idx < 0) idx += P;
+      const double2 e = tw[idx];                      // e^{-2 pi i n l / P}
+      const double2 ep = make_double2(e.x, -e.y);     // e^{+2 pi i n l / P}
+      acc = cadd(acc, cmul(coef[((size_t)w * P + ni) * cols + j], ep));
+    }
+    sigma[((size_t)w * cols + j) * P + l] = make_double2(acc.x * invP, acc.y * invP);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                           int ntasks, int p, int max_trailing_cols, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (max_trailing_cols > 0) {
+    dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
+    qr_update_kernel<<<grid, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double2 *f,
+                         double2 *coef, double2 *sigma, double2 *X, cudaStream_t st) {
+  const int ncol = 2 * W;
+  {
+    dim3 grid((h.rows + kDR - 1) / kDR, W);
+    size_t smem = sizeof(double2) * (h.P + (size_t)kDR * (h.P + 1));
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(rhs_dft_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    rhs_dft_kernel<<<grid, kThreads, smem, st>>>(d_o, W, f, X);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g2(h.D, (ncol + kTN - 1) / kTN);
+  apply_qh_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  trsm_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scatter_coef_kernel<<<dim3(h.P, W), 128, 0, st>>>(d_o, W, X, coef);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !sigma) return e;
+  return launch_point_strengths(d_o, h, W, coef, sigma, st);
+}
+
+cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h, int W, const double2 *coef,
+                                   double2 *sigma, cudaStream_t st) {
+  dim3 grid((h.cols + 31) / 32, W);
+  point_strength_kernel<<<grid, kThreads, sizeof(double2) * h.P, st>>>(d_o, W, coef, sigma);
+  return cudaGetLastError();
+}
+
+}  // namespace axi

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+declared entry point, and its host logic (geometry, quadrature rule,
+validation) agrees with the oracle and rejects bad input."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def axi():
+    from paper_1506_05083_gb300 import axi as A, build
+    if not os.path.exists(A.LIB_PATH):
+        build.build()
+    A.lib()
+    return A
+
+
+def test_exports_every_declared_symbol(axi):
+    hdr = open(os.path.join(ROOT, "include", "axi_mfs.h")).read()
+    declared = set(re.findall(r"^(?:axi_status|const char \*)\s*(axi_\w+)\(", hdr, re.M))
+    assert len(declared) >= 15
+    L = axi.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    bound = {s[0] for s in axi.SIGNATURES}
+    assert declared == bound
+
+
+@pytest.mark.parametrize("make", [synth.config_sphere, synth.config_smooth, synth.config_cup,
+                                  synth.small_case])
+def test_geometry_matches_oracle(axi, make):
+    ob = make().obstacles[0]
+    c1, s1, x1 = axi.geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+    c2, s2, x2 = O.geometry(ob)
+    assert np.abs(c1 - c2).max() < 1e-14
+    assert np.abs(s1 - s2).max() < 1e-14
+    assert np.abs(x1 - x2).max() < 1e-14
+    assert axi.choose_q(ob.M, ob.N, ob.P, c1, s1) == O.choose_q(ob, c2, s2)
+
+
+def test_batched_geometry_and_q(axi):
+    for ob in synth.config_batched().obstacles:
+        c1, s1, x1 = axi.geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+        c2, s2, x2 = O.geometry(ob)
+        assert np.abs(c1 - c2).max() < 1e-14 and np.abs(x1 - x2).max() < 1e-14
+        q1 = axi.choose_q(ob.M, ob.N, ob.P, c1, s1, x1 if ob.bc else None)
+        assert q1 == O.choose_q(ob, c2, s2, x2)
+
+
+def _plan(axi, **kw):
+    import ctypes as C
+    ob = synth.small_case().obstacles[0]
+    coll, src, srcx = axi.geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+    args = dict(bc=0, M=ob.M, N=ob.N, P=ob.P, q=64, k=ob.k, k_minus=0.0, coll=coll, src=src,
+                src_ext=None, prec=0)
+    args.update(kw)
+    prec = args.pop("prec")
+    s = axi.ObstacleSpec(**args)
+    arr = (axi._Obstacle * 1)()
+    arr[0] = axi._Obstacle(s.bc, s.M, s.N, s.P, s.q, s.k, s.k_minus, axi._ptr(s.coll),
+                           axi._ptr(s.src), axi._ptr(s.src_ext) if s.src_ext is not None else None)
+    plan = C.c_void_p()
+    code = axi.lib().axi_plan_create(arr, 1, prec, C.byref(plan))
+    if code == 0:
+        nb = C.c_size_t()
+        assert axi.lib().axi_plan_workspace_bytes(plan, C.byref(nb)) == 0 and nb.value > 0
+        axi.lib().axi_plan_destroy(plan)
+    return code
+
+
+def test_plan_validation(axi):
+    assert _plan(axi) == 0
+    assert _plan(axi, P=15) == -2                  # P odd
+    assert _plan(axi, q=10) == -2                  # q < P
+    assert _plan(axi, M=10) == -2                  # M < N
+    assert _plan(axi, bc=1) == -1                  # transmission without exterior proxies
+    assert _plan(axi, k=-1.0) == -1
+    ob = synth.small_case().obstacles[0]
+    coll, src, _ = axi.geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+    bad = src.copy(); bad[3, 0] = -0.1
+    assert _plan(axi, src=bad) == -3               # proxy across the axis
+    nan = coll.copy(); nan[2, 1] = float("nan")
+    assert _plan(axi, coll=nan) == -3
+    assert _plan(axi, prec=7) == -1
+
+
+def test_status_strings(axi):
+    for c in range(-8, 1):
+        assert axi.lib().axi_status_string(c)
