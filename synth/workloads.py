@@ -137,8 +137,11 @@ def config_batched(n_obs=64, seed=4, max_N=360) -> Workload:
     return Workload("batched64_N60-360_P32-240_k1-30", obs, 4, 6)
 
 
-def small_case(seed=7, k=3.0, M=40, N=32, P=16, q=64, bc=BC_NEUMANN) -> Workload:
-    """A small perturbed body for quick parity tests (several tiles, ragged tail)."""
+def small_case(seed=7, k=3.0, M=40, N=32, P=16, q=0, bc=BC_NEUMANN) -> Workload:
+    """A small perturbed body for quick parity tests (several tiles, ragged tail).
+
+    q = 0: each side picks q from its geometry by the Theorem 1 rule.
+    """
     o = perturbed_polar(seed, k, M, N, P, q)
     if bc == BC_TRANSMISSION:
         o.bc = BC_TRANSMISSION
