@@ -25,7 +25,7 @@ def axi():
 
 def test_exports_every_declared_symbol(axi):
     hdr = open(os.path.join(ROOT, "include", "axi_mfs.h")).read()
-    declared = set(re.findall(r"^(?:axi_status|const char \*)\s*(axi_\w+)\(", hdr, re.M))
+    declared = set(re.findall(r"^(?:axi_status|const char \*|size_t)\s*(axi_\w+)\(", hdr, re.M))
     assert len(declared) >= 15
     L = axi.lib()
     for name in declared:
