@@ -217,6 +217,35 @@ axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W,
                               const axi_c128 *d_f, axi_c128 *d_coef, axi_c128 *d_sigma,
                               void *d_scratch, size_t scratch_bytes, void *stream);
 
+/*
+ * axi_apply_operator_noalloc -- axi_apply_operator for callers that cannot
+ * allocate device memory at the time they apply the operator (for example a
+ * host application that owns the GPU's memory budget and passes a plug-in
+ * only its input and output buffers, or a latency-critical loop where a
+ * cudaMalloc, which can synchronise the device, is not allowed).
+ * The paper has no counterpart: this is a deployment variant of the apply.
+ *
+ * Same arguments and results as axi_apply_operator, without the scratch
+ * buffer: the RHS blocks live in a static device array of
+ * axi_noalloc_scratch_bytes() bytes (32 MiB) that every GPU loading this
+ * library holds until the process exits. The call allocates nothing.
+ *   - Sizes: returns AXI_ERR_SHAPE when axi_apply_workspace_bytes(op, obs, W)
+ *     exceeds the static array (e.g. W > 79 for N=180, M=216, P=120).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (different streams, no ordering) race.
+ *     Every element the apply reads is written first, so nothing needs
+ *     clearing between calls.
+ */
+axi_status axi_apply_operator_noalloc(const axi_operator *op, int32_t obs, int32_t W,
+                                      const axi_c128 *d_f, axi_c128 *d_coef,
+                                      axi_c128 *d_sigma, void *stream);
+
+/* Size in bytes of the static scratch used by axi_apply_operator_noalloc. */
+size_t axi_noalloc_scratch_bytes(void);
+
 typedef enum {
   AXI_EVAL_POTENTIAL = 0,   /* u(x)                                    */
   AXI_EVAL_NORMAL_DERIV = 1,/* du/dn_x, normals required              */

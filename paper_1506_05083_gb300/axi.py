@@ -54,6 +54,8 @@ SIGNATURES = [
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     ("axi_apply_workspace_bytes", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     ("axi_apply_operator", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    ("axi_apply_operator_noalloc", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
+    ("axi_noalloc_scratch_bytes", C.c_size_t, []),
     ("axi_eval_field", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_int32,
                                  C.POINTER(_Lattice), _vp, _vp, _vp, C.c_size_t, _vp]),
     ("axi_operator_status", C.c_int, [_vp]),
@@ -235,6 +237,12 @@ class Operator:
                                         scratch.numel() * scratch.element_size(), _stream(stream)),
                "axi_apply_operator")
         return (coef, sigma) if want_sigma else coef
+
+    def apply_noalloc(self, f: torch.Tensor, coef: torch.Tensor, sigma=None, obs=0, stream=None):
+        """axi_apply_operator_noalloc into caller-provided coef (and sigma)."""
+        code = lib().axi_apply_operator_noalloc(self._op, obs, f.shape[0], _dev(f), _dev(coef),
+                                                _dev(sigma), _stream(stream))
+        _check(code, "axi_apply_operator_noalloc")
 
     def eval_field(self, coef: torch.Tensor, targets: torch.Tensor, kind=EVAL_FAR_FIELD, obs=0,
                    normals=None, lattice=None, dirs=None, scratch=None, stream=None):
