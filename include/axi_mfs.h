@@ -64,15 +64,19 @@ typedef enum {
 
 typedef enum { AXI_BC_NEUMANN = 0, AXI_BC_TRANSMISSION = 1 } axi_bc;
 
-/* Arithmetic of the trailing-matrix updates of the QR and of the apply
- * GEMMs. Fill, Householder panels and triangular solves are native FP64 in
- * every mode. */
+/* Arithmetic of the trailing-matrix updates of the QR and of the apply's
+ * Q^H. Fill, Householder panels, T factors and triangular solves are native
+ * FP64 in every mode. The `prec` argument of axi_plan_create is
+ * AXI_PREC_FP64, or AXI_PREC_SPLIT_BF16 optionally or-ed with
+ * AXI_PREC_SLICES(s), s in 4..8 (default 7): each FP64 value is scaled by a
+ * power of two per row or column and cut into s signed 7-bit digits, exact in
+ * BF16; digit products run on tensor cores with exact FP32 integer sums and
+ * are recombined in FP64 (Ozaki scheme). s = 7 keeps 49 bits per value. */
 typedef enum {
-  AXI_PREC_FP64 = 0,         /* native FP64 (DFMA)                              */
-  AXI_PREC_SPLIT_BF16 = 1    /* FP64 operands split into BF16 integer slices,   */
-                             /* products on tensor cores with exact FP32 sums,  */
-                             /* recombined in FP64 (Ozaki scheme)               */
+  AXI_PREC_FP64 = 0,
+  AXI_PREC_SPLIT_BF16 = 1
 } axi_precision;
+#define AXI_PREC_SLICES(s) ((int32_t)(s) << 8)
 
 typedef enum { AXI_SHAPE_POLAR = 0, AXI_SHAPE_CUP = 1 } axi_shape;
 

@@ -32,6 +32,7 @@ struct axi_plan_s {
   std::vector<int> task_obs, task_mode;   // sorted by obstacle panel count, descending
   std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
   std::vector<int> step_cols;             // widest trailing matrix at step p
+  std::vector<int> step_rows;             // tallest panel at step p
   size_t off_obsdev = 0, off_task_obs = 0, off_task_mode = 0, off_status = 0;
   size_t bytes = 0;
 };
@@ -94,7 +95,15 @@ const char *axi_status_string(int32_t s) {
 
 axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec, axi_plan **out) {
   if (!obs || !out || n_obs < 1) return AXI_ERR_ARG;
-  if (prec != AXI_PREC_FP64) return prec == AXI_PREC_SPLIT_BF16 ? AXI_ERR_UNSUPPORTED : AXI_ERR_ARG;
+  const int mode = prec & 0xff;
+  int slices = 0;
+  if (mode == AXI_PREC_SPLIT_BF16) {
+    slices = (prec >> 8) & 0xff;
+    if (slices == 0) slices = 7;
+    if (!axi::split_slices_supported(slices)) return AXI_ERR_UNSUPPORTED;
+  } else if (prec != AXI_PREC_FP64) {
+    return AXI_ERR_ARG;
+  }
   for (int i = 0; i < n_obs; ++i) {
     axi_status s = validate(obs[i]);
     if (s != AXI_OK) return s;
@@ -120,6 +129,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     d.cols = o.bc == AXI_BC_TRANSMISSION ? 2 * o.N : o.N;
     d.D = o.P / 2 + 1;
     d.npanels = (d.cols + axi::kNB - 1) / axi::kNB;
+    d.slices = slices;
     d.k = o.k; d.km = o.bc == AXI_BC_TRANSMISSION ? o.k_minus : 0.0;
     h.coll.assign(o.h_coll, o.h_coll + 4 * o.M);
     h.src.assign(o.h_src, o.h_src + 2 * o.N);
@@ -159,6 +169,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
   }
   p->step_tasks.assign(maxpan, 0);
   p->step_cols.assign(maxpan, 0);
+  p->step_rows.assign(maxpan, 0);
   for (int s = 0; s < maxpan; ++s) {
     for (int t = 0; t < (int)p->task_obs.size(); ++t) {
       const ObsDev &d = p->obs[p->task_obs[t]].dev;
@@ -166,6 +177,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
         p->step_tasks[s] = t + 1;
         const int k0 = s * axi::kNB, nbp = std::min(axi::kNB, d.cols - k0);
         p->step_cols[s] = std::max(p->step_cols[s], d.cols - k0 - nbp);
+        p->step_rows[s] = std::max(p->step_rows[s], d.rows - k0);
       }
     }
   }
@@ -195,7 +207,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   }
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     e = axi::launch_qr_step(op->d_obs, op->d_task_obs, op->d_task_mode, p->step_tasks[s], (int)s,
-                            p->step_cols[s], st);
+                            p->step_cols[s], p->step_rows[s], p->obs[0].dev.slices, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   return AXI_OK;

@@ -11,6 +11,7 @@ namespace axi {
 constexpr int kNB = 16;        // Householder panel width (columns per block reflector)
 constexpr int kMaxModes = 128; // D = P/2 + 1 <= 128, i.e. P <= 254
 constexpr int kMaxP = 254;
+constexpr int kPanelSmemRows = 864;  // panels up to this many rows are factored in shared memory
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
 enum : int { kStatNonFinite = 1, kStatTimeout = 2 };
@@ -22,7 +23,7 @@ struct ObsDev {
   int D;                  // distinct modes n = 0..P/2
   int bc;                 // axi_bc
   int npanels;            // ceil(cols / kNB)
-  int pad_;
+  int slices;             // 0: native FP64 updates; 4..8: BF16 digits per FP64 value
   double k, km;           // exterior / interior wavenumber
   const double *coll;     // [M][4] rho, z, n_rho, n_z
   const double *src;      // [N][2] interior proxies
@@ -40,7 +41,14 @@ struct ObsDev {
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
 cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int panel, int max_trailing_cols, cudaStream_t st);
+                           int ntasks, int panel, int max_trailing_cols, int max_panel_rows,
+                           int slices, cudaStream_t st);
+cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
+                                   const int *d_task_mode, int ntasks, int panel,
+                                   int max_trailing_cols, int slices, cudaStream_t st);
+cudaError_t launch_apply_qh_split(const ObsDev *d_o, int D, double2 *X, int ncol, int slices,
+                                  cudaStream_t st);
+bool split_slices_supported(int slices);
 cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
                             double2 *f, cudaStream_t st);
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,

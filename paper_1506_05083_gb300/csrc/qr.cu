@@ -190,6 +190,132 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 }
 
 // ---------------------------------------------------------------------------
+// Panel with the K x nbp panel held in shared memory (K = rows - k0 <= kPanelSmemRows):
+// same arithmetic as qr_panel_kernel, but every column operation reads shared
+// memory, and the dot products against the remaining panel columns are one
+// warp per column (warp-shuffle reductions), so each column costs three block
+// barriers instead of several L2 round trips.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                     const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int lda = o.rows;
+  const int k0 = p * kNB;
+  const int nbp = min(kNB, o.cols - k0);
+  const int K = o.rows - k0;
+  double2 *A = o.A + (size_t)d * o.cols * lda;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ double2 Ps[];            // [nbp][K], column a at Ps + a*K
+  __shared__ double red[kThreads / 32];
+  __shared__ double2 wsh[kNB];
+  __shared__ double2 G[kNB][kNB];
+  __shared__ double2 Tsh[kNB][kNB];
+  __shared__ double2 taush[kNB];
+
+  for (int e = tid; e < nbp * K; e += kThreads) {
+    const int a = e / K, i = e % K;
+    Ps[e] = A[(size_t)(k0 + a) * lda + k0 + i];
+  }
+  __syncthreads();
+
+  for (int jj = 0; jj < nbp; ++jj) {
+    double2 *col = Ps + jj * K;
+    double s = 0.0;
+    for (int i = jj + 1 + tid; i < K; i += kThreads) {
+      const double2 v = col[i];
+      s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    double xn2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) xn2 += red[w];
+    const double2 alpha = col[jj];
+    double beta;
+    double2 tau, scale;
+    if (xn2 == 0.0 && alpha.y == 0.0) {
+      beta = alpha.x; tau = make_double2(0.0, 0.0); scale = make_double2(0.0, 0.0);
+    } else {
+      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+      beta = -copysign(nrm, alpha.x);
+      tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+      const double2 den = make_double2(alpha.x - beta, alpha.y);
+      const double dd = den.x * den.x + den.y * den.y;
+      scale = make_double2(den.x / dd, -den.y / dd);       // 1 / (alpha - beta)
+    }
+    for (int i = jj + 1 + tid; i < K; i += kThreads) col[i] = cmul(col[i], scale);
+    __syncthreads();
+    const int nrem = nbp - jj - 1;
+    if (tid == 0) {
+      col[jj] = make_double2(beta, 0.0);
+      taush[jj] = tau;
+      if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
+    }
+    // w_r = conj(tau) * (v^H A(:, jj+1+r)), v = (1; col[jj+1:])
+    const double2 ctau = make_double2(tau.x, -tau.y);
+    for (int r = warp; r < nrem; r += kThreads / 32) {
+      const double2 *x = Ps + (jj + 1 + r) * K;
+      double2 acc = make_double2(0.0, 0.0);
+      if (lane == 0) acc = x[jj];
+      for (int i = jj + 1 + lane; i < K; i += 32) acc = cadd(acc, cjmul(col[i], x[i]));
+      acc.x = warp_sum(acc.x);
+      acc.y = warp_sum(acc.y);
+      if (lane == 0) wsh[r] = cmul(ctau, acc);
+    }
+    __syncthreads();
+    const int len = K - jj;
+    for (int e = tid; e < nrem * len; e += kThreads) {
+      const int r = e / len, i = jj + e % len;
+      const double2 v = (i == jj) ? make_double2(1.0, 0.0) : col[i];
+      double2 *x = Ps + (jj + 1 + r) * K + i;
+      const double2 vw = cmul(v, wsh[r]);
+      *x = make_double2(x->x - vw.x, x->y - vw.y);
+    }
+    __syncthreads();
+  }
+
+  // Gram G(a, b) = v_a^H v_b (a < b) and the compact-WY T factor
+  const int npair = nbp * (nbp - 1) / 2;
+  for (int pi = warp; pi < npair; pi += kThreads / 32) {
+    int b = 1, acc = 0;
+    while (acc + b <= pi) { acc += b; ++b; }
+    const int a = pi - acc;
+    const double2 *va = Ps + a * K, *vb = Ps + b * K;
+    double2 g = make_double2(0.0, 0.0);
+    for (int i = b + 1 + lane; i < K; i += 32) g = cadd(g, cjmul(va[i], vb[i]));
+    g.x = warp_sum(g.x);
+    g.y = warp_sum(g.y);
+    if (lane == 0) G[a][b] = make_double2(g.x + va[b].x, g.y - va[b].y);
+  }
+  for (int e = tid; e < nbp * K; e += kThreads) {
+    const int a = e / K, i = e % K;
+    A[(size_t)(k0 + a) * lda + k0 + i] = Ps[e];
+  }
+  if (tid < nbp) o.tau[(size_t)d * o.cols + k0 + tid] = taush[tid];
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < kNB; ++j)
+      for (int i = 0; i < kNB; ++i) Tsh[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < nbp; ++j) {
+      const double2 tj = taush[j];
+      Tsh[j][j] = tj;
+      for (int i = 0; i < j; ++i) {
+        double2 zz = make_double2(0.0, 0.0);
+        for (int l = i; l < j; ++l) zz = cadd(zz, cmul(Tsh[i][l], G[l][j]));
+        const double2 t = cmul(tj, zz);
+        Tsh[i][j] = make_double2(-t.x, -t.y);
+      }
+    }
+  }
+  __syncthreads();
+  double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  for (int e = tid; e < kNB * kNB; e += kThreads) Tg[e] = Tsh[e % kNB][e / kNB];
+}
+
+// ---------------------------------------------------------------------------
 // X(k0:rows, 0:ncols) <- (I - V T^H V^H) X(k0:rows, 0:ncols) for one panel.
 // One CTA, kTN target columns; FP64. Thread (a, c) = (tid / kTN, tid % kTN).
 // ---------------------------------------------------------------------------
@@ -447,11 +573,27 @@ point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__res
 }  // namespace
 
 cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int p, int max_trailing_cols, cudaStream_t st) {
+                           int ntasks, int p, int max_trailing_cols, int max_panel_rows,
+                           int slices, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
-  qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (max_panel_rows <= kPanelSmemRows) {
+    const size_t smem = sizeof(double2) * (size_t)kNB * max_panel_rows;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(qr_panel_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(double2) * (size_t)kNB * kPanelSmemRows));
+      if (e != cudaSuccess) return e;
+    }
+    qr_panel_smem_kernel<<<ntasks, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  } else {
+    qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
+  if (slices > 0)
+    return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols,
+                                  slices, st);
   if (max_trailing_cols > 0) {
     dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
     qr_update_kernel<<<grid, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
@@ -476,8 +618,13 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
     if (e != cudaSuccess) return e;
   }
   dim3 g2(h.D, (ncol + kTN - 1) / kTN);
-  apply_qh_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (h.slices > 0) {
+    e = launch_apply_qh_split(d_o, h.D, X, ncol, h.slices, st);
+  } else {
+    apply_qh_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   trsm_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
   e = cudaGetLastError();

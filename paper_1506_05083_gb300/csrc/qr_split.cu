@@ -1,0 +1,340 @@
+// Split-precision (AXI_PREC_SPLIT_BF16) block-reflector update on tensor cores.
+//
+// The trailing update of the blocked Householder QR and the Q^H of the apply
+// both compute, for one panel's reflectors V (K x nb, unit lower trapezoidal)
+// and compact-WY factor T,
+//     X <- X - V (T^H (V^H X))         (Sec. 3 eq. linsys; Sec. 4.4),
+// on a tile of kTN target columns. Here the two GEMMs run as Ozaki slice
+// products on BF16 mma.sync (ozaki.cuh) and T^H in FP64:
+//   pass 0  exponents: per column of V (for V^H) and per column of X;
+//   pass 1  W = V^H X, contraction over the K rows in chunks of 32;
+//   pass 2  W' = T^H W (FP64), per-column exponents and digits of W';
+//   pass 3  X -= V W', V digits per row (exponent over the nb columns),
+//           contraction nb = 16 (one k16 step), FP64 read-modify-write of X.
+// Native FP64 work per X element and panel step: its digit split and the
+// group recombination, about 20 operations against 256 for the FP64 kernel.
+#include "axi_internal.h"
+#include "ozaki.cuh"
+
+namespace axi {
+namespace {
+
+constexpr int kThreads = 128;          // 4 warps
+constexpr int kTN = 32;                // target columns per CTA
+constexpr int kKC = 32;                // contraction rows per chunk (pass 1)
+constexpr int kRC = 64;                // output rows per chunk (pass 3): 4 warps x 16
+constexpr int kLD1 = kKC + 8;          // padded k stride (conflict-free fragment loads)
+constexpr int kLD2 = kNB + 8;
+
+template <int S>
+struct Pass1 {
+  __nv_bfloat16 A[S][2][kNB][kLD1];    // digits of V^H chunk (rows = panel columns)
+  __nv_bfloat16 B[S][2][kTN][kLD1];    // digits of X chunk ([column][row])
+};
+template <int S>
+struct Pass3 {
+  __nv_bfloat16 A[S][2][kRC][kLD2];    // digits of V rows chunk ([row][panel column])
+  __nv_bfloat16 B[S][2][kTN][kLD2];    // digits of W' ([column][panel column])
+};
+template <int S>
+struct OzSmem {
+  union {
+    Pass1<S> p1;
+    Pass3<S> p3;
+  } u;
+  double2 W[kNB][kTN + 1];
+  double2 T[kNB][kNB + 1];
+  int eVH[kNB], eX[kTN], eW[kTN], eV[kRC];
+};
+
+__device__ __forceinline__ double2 vget(const double2 *A, int lda, int rows, int k0, int nbp, int i,
+                                        int a) {
+  if (a >= nbp || i >= rows) return make_double2(0.0, 0.0);
+  const int c = k0 + a;
+  if (i < c) return make_double2(0.0, 0.0);
+  if (i == c) return make_double2(1.0, 0.0);
+  return A[(size_t)c * lda + i];
+}
+
+__device__ __forceinline__ double amax2(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <int S>
+__device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda, int rows, int k0,
+                                          int nbp, const double2 *__restrict__ Tg,
+                                          double2 *__restrict__ X, int ldx, int ncols,
+                                          OzSmem<S> &sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = lane >> 2, tig = lane & 3;
+
+  // ---- pass 0: exponents of V's columns and X's columns over rows k0..rows-1
+  for (int a = warp; a < kNB; a += kThreads / 32) {
+    double m = 0.0;
+    for (int i = k0 + lane; i < rows; i += 32) m = fmax(m, amax2(vget(A, lda, rows, k0, nbp, i, a)));
+    m = warp_max(m);
+    if (lane == 0) sm.eVH[a] = oz::scale_exponent(m);
+  }
+  for (int j = warp; j < kTN; j += kThreads / 32) {
+    double m = 0.0;
+    if (j < ncols)
+      for (int i = k0 + lane; i < rows; i += 32) m = fmax(m, amax2(X[(size_t)j * ldx + i]));
+    m = warp_max(m);
+    if (lane == 0) sm.eX[j] = oz::scale_exponent(m);
+  }
+  for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
+  __syncthreads();
+
+  // ---- pass 1: W = V^H X (16 x kTN); warp w owns columns 8w..8w+7
+  double wre[4] = {0, 0, 0, 0}, wim[4] = {0, 0, 0, 0};
+  for (int r0 = k0; r0 < rows; r0 += kKC) {
+    __syncthreads();
+    for (int e = tid; e < kNB * kKC; e += kThreads) {
+      const int a = e / kKC, r = e % kKC;
+      const double2 v = vget(A, lda, rows, k0, nbp, r0 + r, a);
+      const int ev = sm.eVH[a];
+      oz::split_store<S>(v.x, ev, &sm.u.p1.A[0][0][a][r], 2 * kNB * kLD1);
+      oz::split_store<S>(-v.y, ev, &sm.u.p1.A[0][1][a][r], 2 * kNB * kLD1);   // conj
+    }
+    for (int e = tid; e < kTN * kKC; e += kThreads) {
+      const int j = e / kKC, r = e % kKC, i = r0 + r;
+      const double2 x = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
+      const int ex = sm.eX[j];
+      oz::split_store<S>(x.x, ex, &sm.u.p1.B[0][0][j][r], 2 * kTN * kLD1);
+      oz::split_store<S>(x.y, ex, &sm.u.p1.B[0][1][j][r], 2 * kTN * kLD1);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int g = 2; g <= S + 1; ++g) {
+      float are[4] = {0, 0, 0, 0}, aim[4] = {0, 0, 0, 0};
+#pragma unroll 1
+      for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
+        const int t = g - s;
+#pragma unroll
+        for (int kk = 0; kk < kKC; kk += 16) {
+          uint32_t ar[4], ai[4], br[2], bi[2];
+          oz::load_a(&sm.u.p1.A[s - 1][0][0][kk], kLD1, lane, ar);
+          oz::load_a(&sm.u.p1.A[s - 1][1][0][kk], kLD1, lane, ai);
+          oz::load_b(&sm.u.p1.B[t - 1][0][8 * warp][kk], kLD1, lane, br);
+          oz::load_b(&sm.u.p1.B[t - 1][1][8 * warp][kk], kLD1, lane, bi);
+          oz::cmma(are, aim, ar, ai, br, bi);
+        }
+      }
+      const double sc = ldexp(1.0, -7 * g);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        wre[q] = fma((double)are[q], sc, wre[q]);
+        wim[q] = fma((double)aim[q], sc, wim[q]);
+      }
+    }
+  }
+  // c-fragment element q: row grp (+8 for q >= 2), column 8w + 2 tig + (q & 1)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = grp + (q >= 2 ? 8 : 0), j = 8 * warp + 2 * tig + (q & 1);
+    const int e = sm.eVH[a] + sm.eX[j];
+    sm.W[a][j] = make_double2(ldexp(wre[q], e), ldexp(wim[q], e));
+  }
+  __syncthreads();
+
+  // ---- pass 2: W' = T^H W (T upper triangular) in FP64, then digits of W'
+  double2 wp[kNB * kTN / kThreads];
+#pragma unroll
+  for (int u = 0; u < kNB * kTN / kThreads; ++u) {
+    const int e = tid + u * kThreads, a = e / kTN, j = e % kTN;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = 0; b <= a; ++b) {
+      const double2 t = sm.T[b][a], w = sm.W[b][j];
+      acc.x += t.x * w.x + t.y * w.y;          // conj(t) * w
+      acc.y += t.x * w.y - t.y * w.x;
+    }
+    wp[u] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kNB * kTN / kThreads; ++u) {
+    const int e = tid + u * kThreads, a = e / kTN, j = e % kTN;
+    sm.W[a][j] = wp[u];
+  }
+  __syncthreads();
+  if (tid < kTN) {
+    double m = 0.0;
+    for (int a = 0; a < kNB; ++a) m = fmax(m, amax2(sm.W[a][tid]));
+    sm.eW[tid] = oz::scale_exponent(m);
+  }
+  __syncthreads();
+  for (int e = tid; e < kNB * kTN; e += kThreads) {
+    const int j = e / kNB, a = e % kNB;
+    const double2 w = sm.W[a][j];
+    oz::split_store<S>(w.x, sm.eW[j], &sm.u.p3.B[0][0][j][a], 2 * kTN * kLD2);
+    oz::split_store<S>(w.y, sm.eW[j], &sm.u.p3.B[0][1][j][a], 2 * kTN * kLD2);
+  }
+
+  // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk
+  for (int r0 = k0; r0 < rows; r0 += kRC) {
+    __syncthreads();
+    if (tid < kRC) {
+      double m = 0.0;
+      for (int a = 0; a < kNB; ++a) m = fmax(m, amax2(vget(A, lda, rows, k0, nbp, r0 + tid, a)));
+      sm.eV[tid] = oz::scale_exponent(m);
+    }
+    __syncthreads();
+    for (int e = tid; e < kRC * kNB; e += kThreads) {
+      const int r = e / kNB, a = e % kNB;
+      const double2 v = vget(A, lda, rows, k0, nbp, r0 + r, a);
+      oz::split_store<S>(v.x, sm.eV[r], &sm.u.p3.A[0][0][r][a], 2 * kRC * kLD2);
+      oz::split_store<S>(v.y, sm.eV[r], &sm.u.p3.A[0][1][r][a], 2 * kRC * kLD2);
+    }
+    __syncthreads();
+    if (r0 + 16 * warp >= rows) continue;
+    double yre[4][4], yim[4][4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) yre[f][q] = yim[f][q] = 0.0;
+#pragma unroll 1
+    for (int g = 2; g <= S + 1; ++g) {
+      float are[4][4], aim[4][4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) are[f][q] = aim[f][q] = 0.f;
+#pragma unroll 1
+      for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
+        const int t = g - s;
+        uint32_t ar[4], ai[4];
+        oz::load_a(&sm.u.p3.A[s - 1][0][16 * warp][0], kLD2, lane, ar);
+        oz::load_a(&sm.u.p3.A[s - 1][1][16 * warp][0], kLD2, lane, ai);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          uint32_t br[2], bi[2];
+          oz::load_b(&sm.u.p3.B[t - 1][0][8 * f][0], kLD2, lane, br);
+          oz::load_b(&sm.u.p3.B[t - 1][1][8 * f][0], kLD2, lane, bi);
+          oz::cmma(are[f], aim[f], ar, ai, br, bi);
+        }
+      }
+      const double sc = ldexp(1.0, -7 * g);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          yre[f][q] = fma((double)are[f][q], sc, yre[f][q]);
+          yim[f][q] = fma((double)aim[f][q], sc, yim[f][q]);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
+        const int i = r0 + r, j = 8 * f + 2 * tig + (q & 1);
+        if (i < rows && j < ncols) {
+          const int e = sm.eV[r] + sm.eW[j];
+          double2 *x = &X[(size_t)j * ldx + i];
+          double2 v = *x;
+          v.x -= ldexp(yre[f][q], e);
+          v.y -= ldexp(yim[f][q], e);
+          *x = v;
+        }
+      }
+  }
+  __syncthreads();
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                       const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int k0 = p * kNB;
+  const int nbp = min(kNB, o.cols - k0);
+  const int c0 = k0 + nbp + blockIdx.y * kTN;
+  if (c0 >= o.cols) return;
+  const int ncols = min(kTN, o.cols - c0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
+  double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  oz_block_reflector_update<S>(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows,
+                               ncols, sm);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads)
+apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
+  const ObsDev &o = *od;
+  const int d = blockIdx.x;
+  const int c0 = blockIdx.y * kTN;
+  if (c0 >= ncols_total) return;
+  const int ncols = min(kTN, ncols_total - c0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
+  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
+  for (int p = 0; p < o.npanels; ++p) {
+    const int k0 = p * kNB;
+    const int nbp = min(kNB, o.cols - k0);
+    const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+    oz_block_reflector_update<S>(A, o.rows, o.rows, k0, nbp, Tg, Xd, o.rows, ncols, sm);
+  }
+}
+
+template <int S>
+cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int max_trailing_cols, cudaStream_t st) {
+  const size_t smem = sizeof(OzSmem<S>);
+  cudaError_t e = cudaFuncSetAttribute(qr_update_split_kernel<S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
+  qr_update_split_kernel<S><<<grid, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_apply_qh_s(const ObsDev *d_o, int D, double2 *X, int ncol, cudaStream_t st) {
+  const size_t smem = sizeof(OzSmem<S>);
+  cudaError_t e = cudaFuncSetAttribute(apply_qh_split_kernel<S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(D, (ncol + kTN - 1) / kTN);
+  apply_qh_split_kernel<S><<<grid, kThreads, smem, st>>>(d_o, X, ncol);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool split_slices_supported(int s) { return s >= 4 && s <= 8; }
+
+cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
+                                   const int *d_task_mode, int ntasks, int p,
+                                   int max_trailing_cols, int slices, cudaStream_t st) {
+  if (ntasks <= 0 || max_trailing_cols <= 0) return cudaSuccess;
+  switch (slices) {
+    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply_qh_split(const ObsDev *d_o, int D, double2 *X, int ncol, int slices,
+                                  cudaStream_t st) {
+  switch (slices) {
+    case 4: return launch_apply_qh_s<4>(d_o, D, X, ncol, st);
+    case 5: return launch_apply_qh_s<5>(d_o, D, X, ncol, st);
+    case 6: return launch_apply_qh_s<6>(d_o, D, X, ncol, st);
+    case 7: return launch_apply_qh_s<7>(d_o, D, X, ncol, st);
+    case 8: return launch_apply_qh_s<8>(d_o, D, X, ncol, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace axi

@@ -1,0 +1,71 @@
+"""Split-precision (Ozaki, BF16 digits on tensor cores) QR updates and apply,
+against the FP64 oracle. Parity bar as for the native path: e_bd, e_ff <= 1e-10
+at the default 7 digits; fewer digits must degrade gracefully and monotonically.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from test_gpu_parity import _case, _e_bd, _householder_q
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _op(name, slices):
+    from paper_1506_05083_gb300 import axi
+    wl, ob, geo, A, fac = _case(name)
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    assert spec.q == ob.q
+    prec = axi.PREC_SPLIT_BF16 | (slices << 8)
+    return axi, axi.Operator([spec], prec=prec), (wl, ob, geo, A, fac)
+
+
+@pytest.mark.parametrize("name", ["small", "small_trans"])
+def test_split_qr_invariants(name):
+    axi, op, (wl, ob, geo, A, fac) = _op(name, 7)
+    Af = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
+    Ap, tau, T, nb = op.factors()
+    Ap = Ap.cpu().numpy().transpose(0, 2, 1)
+    tau = tau.cpu().numpy()
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    rows, cols = Ap.shape[1], Ap.shape[2]
+    for d in (0, 1, ob.P // 2):
+        Q = _householder_q(Ap[d], tau[d], rows, cols)
+        R = np.triu(Ap[d][:cols])
+        assert np.linalg.norm(Q[:, :cols] @ R - Af[d]) < 1e-12 * np.linalg.norm(Af[d])
+
+
+@pytest.mark.parametrize("name", ["small", "small_trans", "sphere", "smooth"])
+def test_split_apply_parity(name):
+    axi, op, (wl, ob, (coll, src, srcx), A, fac) = _op(name, 7)
+    dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+    coef = op.apply(op.incident(torch.tensor(dirs_np, device="cuda")))
+    xh = synth.plane_wave_directions(64, 99)
+    F = op.eval_field(coef, torch.tensor(xh, device="cuda"), axi.EVAL_FAR_FIELD).cpu().numpy()
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+    c_ora = O.solve_modes(ob, fac, fh)
+    assert _e_bd(A, ob, coef.cpu().numpy(), c_ora, fh) < 1e-10
+    F_ora = O.far_field(ob, src, c_ora, xh)
+    assert np.abs(F - F_ora).max() / np.abs(F_ora).max() < 1e-10
+
+
+def test_split_digits_sweep():
+    """Error against the oracle shrinks as digits are added (4 -> 8)."""
+    errs = []
+    for s in (4, 5, 6, 7, 8):
+        axi, op, (wl, ob, (coll, src, srcx), A, fac) = _op("small", s)
+        dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+        coef = op.apply(op.incident(torch.tensor(dirs_np, device="cuda")))
+        fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+        c_ora = O.solve_modes(ob, fac, fh)
+        errs.append(_e_bd(A, ob, coef.cpu().numpy(), c_ora, fh))
+    assert errs[-1] < 1e-11
+    assert errs[0] > errs[-1]
+    assert all(e < 1e-3 for e in errs)
