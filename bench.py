@@ -147,13 +147,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"],
+                    help="trailing-update / Q^H arithmetic: Ozaki BF16 digits or native FP64")
+    ap.add_argument("--slices", type=int, default=7)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     wl, ob = workload()
     W = wl.n_waves
     dirs_np = synth.plane_wave_directions(W, wl.wave_seed)
     qr_fl, ap_fl = algorithmic_flops(ob.M, ob.N, ob.P, W)
-    config = {"workload": wl.name, "obstacle": "smooth r=1+0.2*sum a_j cos(js), seed 2",
+    config = {"workload": wl.name, "precision": args.prec, "obstacle": "smooth r=1+0.2*sum a_j cos(js), seed 2",
               "k": ob.k, "M": ob.M, "N": ob.N, "P": ob.P, "q": ob.q, "waves": W,
               "distinct_modes": ob.P // 2 + 1, "l2": "flushed (256 MB write) before each timed step"}
 
@@ -189,7 +192,8 @@ def main():
 
     spec = axi.spec_from_obstacle(ob)
     stream = torch.cuda.current_stream()
-    op = axi.Operator([spec])
+    prec = axi.PREC_SPLIT_BF16 | (args.slices << 8) if args.prec == "split" else axi.PREC_FP64
+    op = axi.Operator([spec], prec=prec)
     dirs = torch.tensor(dirs_np, device=dev)
     coef = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128, device=dev)
     sigma = torch.empty((W, spec.cols, ob.P), dtype=torch.complex128, device=dev)
@@ -278,6 +282,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "precision": (f"split-bf16 {args.slices} digits (QR trailing updates, Q^H); "
+                          "fill, panels, T, TRSM, transforms FP64") if args.prec == "split"
+                         else "native fp64",
             "build_ms": float(np.mean(build_ms)),
             "build_tflops": qr_fl / (np.mean(build_ms) * 1e-3) / 1e12,
             "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,

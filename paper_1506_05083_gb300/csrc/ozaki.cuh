@@ -10,9 +10,10 @@
 // sum_k d_{s,ik} d_{t,kj} exactly as long as every partial sum stays below
 // 2^24 in magnitude (all terms are integers, so the tensor core's alignment
 // and rounding lose nothing). Pairs with s + t = g share one FP32
-// accumulator ("group" g); groups are flushed into FP64 after at most 32
-// products of the contraction, far inside the 2^24 bound
-// (32 * 7 pairs * 2^14 * 2 real products < 2^24). Only pairs with
+// accumulator ("group" g); groups are flushed after at most 32 products of
+// the contraction: with |d_1| <= 128 and |d_s| <= 64 otherwise, a group sum
+// of one complex component stays below 32 * 2 * 2^12 (g + 1) <= 2^22, so the
+// FP32 sums are exact and convert to integers by a magic-number add. Only pairs with
 // s + t <= S + 1 are formed: the dropped terms are below 2^{-7S} S relative to
 // the row/column maxima, the same order as the truncation of the digits.
 #pragma once
@@ -31,35 +32,89 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// Exponent e with max|x| < 2^e (0 for an all-zero set).
-__device__ __forceinline__ int scale_exponent(double maxabs) {
-  if (!(maxabs > 0.0)) return 0;
-  int e;
-  frexp(maxabs, &e);
-  return e;
+// On this part the FP64 pipe is ~1/1600 of the BF16 tensor rate, so the
+// split and the recombination below use integer and FP32 instructions only:
+// exponents and digits come from the IEEE-754 bit patterns, and FP32 group
+// sums are turned into integers and accumulated in 64-bit integers.
+
+// |x| as an ordered 64-bit key (IEEE bit patterns of non-negative doubles
+// sort like the values).
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// Balanced digits of x * 2^{-e} (|x| < 2^e): x * 2^{56-e} is rounded to the
-// nearest integer, rounded again to its top 7S bits, and written in base 128
-// with digits d_2..d_S in [-64, 63] and a leading digit |d_1| <= 128, so that
-//   x = 2^e sum_s d_s 2^{-7s} + err,  |err| <= 2^{e - 7S - 1} (1 + 2^-7).
+// Exponent e with |x| < 2^e for the largest key (0 for an all-zero set).
+__device__ __forceinline__ int key_exponent(unsigned long long key) {
+  if (key == 0) return 0;
+  const int E = (int)(key >> 52);
+  return E == 0 ? -1022 : E - 1022;
+}
+
+// BF16 bit pattern of a small integer (|d| <= 255), built with integer ops.
+__device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
+  if (d == 0) return 0;
+  const unsigned short sign = d < 0 ? 0x8000 : 0;
+  const unsigned a = d < 0 ? -d : d;
+  const int p = 31 - __clz(a);                      // a = 2^p * 1.f, p <= 7
+  return sign | (unsigned short)((127 + p) << 7) | (unsigned short)((a << (7 - p)) & 0x7f);
+}
+
+// Balanced digits of x * 2^{-e} (|x| < 2^e): m = round(x * 2^{7S - e}) is
+// formed exactly from the mantissa and exponent bits, then written in base 128
+// with digits d_2..d_S in [-64, 63] and a leading digit |d_1| <= 128:
+//   x = 2^e sum_s d_s 2^{-7s} + err,  |err| <= 2^{e - 7S - 1}.
 // Rounding (not truncation) keeps the digit errors unbiased, so they do not
-// add up coherently along a contraction. All steps after the rounding are
-// exact integer operations.
+// add up coherently along a contraction.
 template <int S>
 __device__ __forceinline__ void split_store(double x, int e, __nv_bfloat16 *dst, int stride) {
   static_assert(S >= 1 && S <= 8, "1..8 digits");
-  const long long n = __double2ll_rn(ldexp(x, 56 - e));   // |n| <= 2^56
-  constexpr int drop = 56 - 7 * S;
-  long long m = drop > 0 ? ((n + (1ll << (drop > 0 ? drop - 1 : 0))) >> drop) : n;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  int Ee = E;
+  if (E == 0) Ee = 1; else M |= 1ull << 52;
+  const int sh = Ee - 1075 + 7 * S - e;             // x * 2^{7S-e} = M * 2^sh, sh <= 3
+  long long m;
+  if (sh >= 0) m = (long long)(M << sh);
+  else if (sh > -60) m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else m = 0;
+  if (b >> 63) m = -m;
+  unsigned short *out = reinterpret_cast<unsigned short *>(dst);
 #pragma unroll
   for (int s = S; s >= 2; --s) {
     int d = (int)(m & 127);
     if (d >= 64) d -= 128;
-    dst[(s - 1) * stride] = __float2bfloat16_rn((float)d);
+    out[(s - 1) * stride] = int_to_bf16_bits(d);
     m = (m - d) >> 7;
   }
-  dst[0] = __float2bfloat16_rn((float)m);
+  out[0] = int_to_bf16_bits((int)m);
+}
+
+// Exact FP32 integer (|v| < 2^22) -> int32 without a conversion instruction.
+__device__ __forceinline__ int f32_int(float v) {
+  return __float_as_int(v + 12582912.0f) - 0x4B400000;
+}
+
+// Group accumulators folded into two 64-bit integers: groups g = 2..4 into
+// hi (weight 2^{7(4-g)}), groups g = 5..S+1 into lo (weight 2^{7(S+1-g)}).
+// The represented value is hi 2^-28 + lo 2^{-7(S+1)}.
+template <int S>
+__device__ __forceinline__ void fold_group(long long &hi, long long &lo, int g, float acc) {
+  const long long v = (long long)f32_int(acc);
+  if (g <= 4) hi += v << (7 * (4 - g));
+  else lo += v << (7 * (S + 1 - g));
+}
+
+// hi 2^{-28} + lo 2^{-7(S+1)}, times 2^E.
+template <int S>
+__device__ __forceinline__ double unfold(long long hi, long long lo, int E) {
+  const int e1 = E - 28, e2 = E - 7 * (S + 1);
+  if (e1 < 1000 && e2 > -1000) {
+    const double p1 = __longlong_as_double((long long)(1023 + e1) << 52);
+    const double p2 = __longlong_as_double((long long)(1023 + e2) << 52);
+    return fma((double)hi, p1, (double)lo * p2);
+  }
+  return ldexp((double)hi, e1) + ldexp((double)lo, e2);
 }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {

@@ -190,11 +190,14 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 }
 
 // ---------------------------------------------------------------------------
-// Panel with the K x nbp panel held in shared memory (K = rows - k0 <= kPanelSmemRows):
-// same arithmetic as qr_panel_kernel, but every column operation reads shared
-// memory, and the dot products against the remaining panel columns are one
-// warp per column (warp-shuffle reductions), so each column costs three block
-// barriers instead of several L2 round trips.
+// Panel with the K x nbp panel held in shared memory (K = rows - k0 <= kPanelSmemRows).
+// Thread t owns local rows t, t + kThreads, ...; for column jj it forms, for its
+// rows, the partial sums of the 15 quantities the column needs (the dot
+// products v^H A(:, c) with the remaining panel columns c > jj, and the Gram
+// entries v_a^H v for the earlier reflectors a < jj that build T), reduces them
+// in one block reduction, and applies the rank-1 update to its own rows. Three
+// barriers per column; the per-row work is 15 independent complex FMAs.
+//   T(jj, jj) = tau_jj,  T(0:jj, jj) = -tau_jj T(0:jj, 0:jj) (V(:, 0:jj)^H v_jj).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
 qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
@@ -207,32 +210,39 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   const int K = o.rows - k0;
   double2 *A = o.A + (size_t)d * o.cols * lda;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  extern __shared__ double2 Ps[];            // [nbp][K], column a at Ps + a*K
-  __shared__ double red[kThreads / 32];
-  __shared__ double2 wsh[kNB];
-  __shared__ double2 G[kNB][kNB];
-  __shared__ double2 Tsh[kNB][kNB];
+  constexpr int kW = kThreads / 32;
+  constexpr int kX = kNB - 1;                  // reduced quantities per column
+  extern __shared__ double2 Ps[];              // [nbp][K], column a at Ps + a*K
+  __shared__ double red1[kW];
+  __shared__ double2 red2[kW][kX];
+  __shared__ double2 wsh[kX];                  // conj(tau) v^H A(:, c), index c - 1
+  __shared__ double2 gsh[kX];                  // v_a^H v_jj, index a
+  __shared__ double2 Tsh[kNB][kNB + 1];
   __shared__ double2 taush[kNB];
 
   for (int e = tid; e < nbp * K; e += kThreads) {
     const int a = e / K, i = e % K;
     Ps[e] = A[(size_t)(k0 + a) * lda + k0 + i];
   }
+  for (int e = tid; e < kNB * (kNB + 1); e += kThreads) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
   __syncthreads();
 
   for (int jj = 0; jj < nbp; ++jj) {
     double2 *col = Ps + jj * K;
     double s = 0.0;
-    for (int i = jj + 1 + tid; i < K; i += kThreads) {
+    // Row i is always handled by thread i mod kThreads, so every row's
+    // updates are made and read by one thread; only reductions cross threads.
+    for (int i = tid; i < K; i += kThreads) {
+      if (i <= jj) continue;
       const double2 v = col[i];
       s = fma(v.x, v.x, fma(v.y, v.y, s));
     }
     s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
+    if (lane == 0) red1[warp] = s;
+    __syncthreads();                                           // S1
     double xn2 = 0.0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) xn2 += red[w];
+    for (int w = 0; w < kW; ++w) xn2 += red1[w];
     const double2 alpha = col[jj];
     double beta;
     double2 tau, scale;
@@ -244,73 +254,77 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
       const double2 den = make_double2(alpha.x - beta, alpha.y);
       const double dd = den.x * den.x + den.y * den.y;
-      scale = make_double2(den.x / dd, -den.y / dd);       // 1 / (alpha - beta)
+      scale = make_double2(den.x / dd, -den.y / dd);          // 1 / (alpha - beta)
     }
-    for (int i = jj + 1 + tid; i < K; i += kThreads) col[i] = cmul(col[i], scale);
-    __syncthreads();
-    const int nrem = nbp - jj - 1;
+    // partial sums over own rows i >= jj
+    double2 part[kX];
+#pragma unroll
+    for (int x = 0; x < kX; ++x) part[x] = make_double2(0.0, 0.0);
+    for (int i = tid; i < K; i += kThreads) {
+      if (i < jj) continue;
+      double2 v;
+      if (i == jj) {
+        v = make_double2(1.0, 0.0);
+      } else {
+        v = cmul(col[i], scale);
+        col[i] = v;
+      }
+#pragma unroll
+      for (int x = 0; x < kX; ++x) {
+        if (x < jj) {
+          part[x] = cadd(part[x], cjmul(Ps[x * K + i], v));        // Gram: v_x^H v_jj
+        } else if (x + 1 < nbp) {
+          part[x] = cadd(part[x], cjmul(v, Ps[(x + 1) * K + i]));  // v^H A(:, x+1)
+        }
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < kX; ++x) {
+      const double rx = warp_sum(part[x].x), ry = warp_sum(part[x].y);
+      if (lane == 0) red2[warp][x] = make_double2(rx, ry);
+    }
+    __syncthreads();                                           // S2
+    if (tid < kX) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int w = 0; w < kW; ++w) acc = cadd(acc, red2[w][tid]);
+      if (tid < jj) gsh[tid] = acc;
+      else wsh[tid] = cmul(make_double2(tau.x, -tau.y), acc);
+    }
     if (tid == 0) {
       col[jj] = make_double2(beta, 0.0);
       taush[jj] = tau;
       if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
     }
-    // w_r = conj(tau) * (v^H A(:, jj+1+r)), v = (1; col[jj+1:])
-    const double2 ctau = make_double2(tau.x, -tau.y);
-    for (int r = warp; r < nrem; r += kThreads / 32) {
-      const double2 *x = Ps + (jj + 1 + r) * K;
-      double2 acc = make_double2(0.0, 0.0);
-      if (lane == 0) acc = x[jj];
-      for (int i = jj + 1 + lane; i < K; i += 32) acc = cadd(acc, cjmul(col[i], x[i]));
-      acc.x = warp_sum(acc.x);
-      acc.y = warp_sum(acc.y);
-      if (lane == 0) wsh[r] = cmul(ctau, acc);
+    __syncthreads();                                           // S3
+    // T column jj (rows < jj in parallel), then the rank-1 update of own rows
+    if (tid < jj) {
+      double2 z = make_double2(0.0, 0.0);
+      for (int l = tid; l < jj; ++l) z = cadd(z, cmul(Tsh[tid][l], gsh[l]));
+      const double2 t = cmul(tau, z);
+      Tsh[tid][jj] = make_double2(-t.x, -t.y);
     }
-    __syncthreads();
-    const int len = K - jj;
-    for (int e = tid; e < nrem * len; e += kThreads) {
-      const int r = e / len, i = jj + e % len;
+    if (tid == 0) Tsh[jj][jj] = tau;
+    for (int i = tid; i < K; i += kThreads) {
+      if (i < jj) continue;
       const double2 v = (i == jj) ? make_double2(1.0, 0.0) : col[i];
-      double2 *x = Ps + (jj + 1 + r) * K + i;
-      const double2 vw = cmul(v, wsh[r]);
-      *x = make_double2(x->x - vw.x, x->y - vw.y);
+#pragma unroll
+      for (int x = 0; x < kX; ++x) {
+        if (x >= jj && x + 1 < nbp) {
+          double2 *y = Ps + (x + 1) * K + i;
+          const double2 vw = cmul(v, wsh[x]);
+          *y = make_double2(y->x - vw.x, y->y - vw.y);
+        }
+      }
     }
-    __syncthreads();
+    // col[jj + 1] (alpha of the next column) is read by all threads only after the next S1
   }
-
-  // Gram G(a, b) = v_a^H v_b (a < b) and the compact-WY T factor
-  const int npair = nbp * (nbp - 1) / 2;
-  for (int pi = warp; pi < npair; pi += kThreads / 32) {
-    int b = 1, acc = 0;
-    while (acc + b <= pi) { acc += b; ++b; }
-    const int a = pi - acc;
-    const double2 *va = Ps + a * K, *vb = Ps + b * K;
-    double2 g = make_double2(0.0, 0.0);
-    for (int i = b + 1 + lane; i < K; i += 32) g = cadd(g, cjmul(va[i], vb[i]));
-    g.x = warp_sum(g.x);
-    g.y = warp_sum(g.y);
-    if (lane == 0) G[a][b] = make_double2(g.x + va[b].x, g.y - va[b].y);
-  }
+  __syncthreads();
   for (int e = tid; e < nbp * K; e += kThreads) {
     const int a = e / K, i = e % K;
     A[(size_t)(k0 + a) * lda + k0 + i] = Ps[e];
   }
   if (tid < nbp) o.tau[(size_t)d * o.cols + k0 + tid] = taush[tid];
-  __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < kNB; ++j)
-      for (int i = 0; i < kNB; ++i) Tsh[i][j] = make_double2(0.0, 0.0);
-    for (int j = 0; j < nbp; ++j) {
-      const double2 tj = taush[j];
-      Tsh[j][j] = tj;
-      for (int i = 0; i < j; ++i) {
-        double2 zz = make_double2(0.0, 0.0);
-        for (int l = i; l < j; ++l) zz = cadd(zz, cmul(Tsh[i][l], G[l][j]));
-        const double2 t = cmul(tj, zz);
-        Tsh[i][j] = make_double2(-t.x, -t.y);
-      }
-    }
-  }
-  __syncthreads();
   double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
   for (int e = tid; e < kNB * kNB; e += kThreads) Tg[e] = Tsh[e % kNB][e / kNB];
 }

@@ -56,11 +56,17 @@ __device__ __forceinline__ double2 vget(const double2 *A, int lda, int rows, int
   return A[(size_t)c * lda + i];
 }
 
-__device__ __forceinline__ double amax2(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
+__device__ __forceinline__ unsigned long long key2(double2 v) {
+  const unsigned long long a = oz::abs_key(v.x), b = oz::abs_key(v.y);
+  return a > b ? a : b;
+}
 
-__device__ __forceinline__ double warp_max(double v) {
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   return v;
 }
 
@@ -74,23 +80,29 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
 
   // ---- pass 0: exponents of V's columns and X's columns over rows k0..rows-1
   for (int a = warp; a < kNB; a += kThreads / 32) {
-    double m = 0.0;
-    for (int i = k0 + lane; i < rows; i += 32) m = fmax(m, amax2(vget(A, lda, rows, k0, nbp, i, a)));
-    m = warp_max(m);
-    if (lane == 0) sm.eVH[a] = oz::scale_exponent(m);
+    unsigned long long m = 0;
+    for (int i = k0 + lane; i < rows; i += 32) {
+      const unsigned long long k = key2(vget(A, lda, rows, k0, nbp, i, a));
+      m = k > m ? k : m;
+    }
+    m = warp_max_u64(m);
+    if (lane == 0) sm.eVH[a] = oz::key_exponent(m);
   }
   for (int j = warp; j < kTN; j += kThreads / 32) {
-    double m = 0.0;
+    unsigned long long m = 0;
     if (j < ncols)
-      for (int i = k0 + lane; i < rows; i += 32) m = fmax(m, amax2(X[(size_t)j * ldx + i]));
-    m = warp_max(m);
-    if (lane == 0) sm.eX[j] = oz::scale_exponent(m);
+      for (int i = k0 + lane; i < rows; i += 32) {
+        const unsigned long long k = key2(X[(size_t)j * ldx + i]);
+        m = k > m ? k : m;
+      }
+    m = warp_max_u64(m);
+    if (lane == 0) sm.eX[j] = oz::key_exponent(m);
   }
   for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
   __syncthreads();
 
   // ---- pass 1: W = V^H X (16 x kTN); warp w owns columns 8w..8w+7
-  double wre[4] = {0, 0, 0, 0}, wim[4] = {0, 0, 0, 0};
+  long long whi[2][4] = {}, wlo[2][4] = {};
   for (int r0 = k0; r0 < rows; r0 += kKC) {
     __syncthreads();
     for (int e = tid; e < kNB * kKC; e += kThreads) {
@@ -124,11 +136,10 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
           oz::cmma(are, aim, ar, ai, br, bi);
         }
       }
-      const double sc = ldexp(1.0, -7 * g);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        wre[q] = fma((double)are[q], sc, wre[q]);
-        wim[q] = fma((double)aim[q], sc, wim[q]);
+        oz::fold_group<S>(whi[0][q], wlo[0][q], g, are[q]);
+        oz::fold_group<S>(whi[1][q], wlo[1][q], g, aim[q]);
       }
     }
   }
@@ -137,7 +148,8 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
   for (int q = 0; q < 4; ++q) {
     const int a = grp + (q >= 2 ? 8 : 0), j = 8 * warp + 2 * tig + (q & 1);
     const int e = sm.eVH[a] + sm.eX[j];
-    sm.W[a][j] = make_double2(ldexp(wre[q], e), ldexp(wim[q], e));
+    sm.W[a][j] = make_double2(oz::unfold<S>(whi[0][q], wlo[0][q], e),
+                              oz::unfold<S>(whi[1][q], wlo[1][q], e));
   }
   __syncthreads();
 
@@ -162,9 +174,12 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
   }
   __syncthreads();
   if (tid < kTN) {
-    double m = 0.0;
-    for (int a = 0; a < kNB; ++a) m = fmax(m, amax2(sm.W[a][tid]));
-    sm.eW[tid] = oz::scale_exponent(m);
+    unsigned long long m = 0;
+    for (int a = 0; a < kNB; ++a) {
+      const unsigned long long k = key2(sm.W[a][tid]);
+      m = k > m ? k : m;
+    }
+    sm.eW[tid] = oz::key_exponent(m);
   }
   __syncthreads();
   for (int e = tid; e < kNB * kTN; e += kThreads) {
@@ -174,13 +189,17 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
     oz::split_store<S>(w.y, sm.eW[j], &sm.u.p3.B[0][1][j][a], 2 * kTN * kLD2);
   }
 
-  // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk
+  // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk,
+  // the 32 target columns in two halves of 16 (two n8 fragments each)
   for (int r0 = k0; r0 < rows; r0 += kRC) {
     __syncthreads();
     if (tid < kRC) {
-      double m = 0.0;
-      for (int a = 0; a < kNB; ++a) m = fmax(m, amax2(vget(A, lda, rows, k0, nbp, r0 + tid, a)));
-      sm.eV[tid] = oz::scale_exponent(m);
+      unsigned long long m = 0;
+      for (int a = 0; a < kNB; ++a) {
+        const unsigned long long k = key2(vget(A, lda, rows, k0, nbp, r0 + tid, a));
+        m = k > m ? k : m;
+      }
+      sm.eV[tid] = oz::key_exponent(m);
     }
     __syncthreads();
     for (int e = tid; e < kRC * kNB; e += kThreads) {
@@ -191,56 +210,50 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
     }
     __syncthreads();
     if (r0 + 16 * warp >= rows) continue;
-    double yre[4][4], yim[4][4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) yre[f][q] = yim[f][q] = 0.0;
 #pragma unroll 1
-    for (int g = 2; g <= S + 1; ++g) {
-      float are[4][4], aim[4][4];
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) are[f][q] = aim[f][q] = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      long long yhi[2][2][4] = {}, ylo[2][2][4] = {};     // [part][fragment][element]
 #pragma unroll 1
-      for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
-        const int t = g - s;
-        uint32_t ar[4], ai[4];
-        oz::load_a(&sm.u.p3.A[s - 1][0][16 * warp][0], kLD2, lane, ar);
-        oz::load_a(&sm.u.p3.A[s - 1][1][16 * warp][0], kLD2, lane, ai);
+      for (int g = 2; g <= S + 1; ++g) {
+        float are[2][4] = {}, aim[2][4] = {};
+#pragma unroll 1
+        for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
+          const int t = g - s;
+          uint32_t ar[4], ai[4];
+          oz::load_a(&sm.u.p3.A[s - 1][0][16 * warp][0], kLD2, lane, ar);
+          oz::load_a(&sm.u.p3.A[s - 1][1][16 * warp][0], kLD2, lane, ai);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          uint32_t br[2], bi[2];
-          oz::load_b(&sm.u.p3.B[t - 1][0][8 * f][0], kLD2, lane, br);
-          oz::load_b(&sm.u.p3.B[t - 1][1][8 * f][0], kLD2, lane, bi);
-          oz::cmma(are[f], aim[f], ar, ai, br, bi);
+          for (int f = 0; f < 2; ++f) {
+            uint32_t br[2], bi[2];
+            oz::load_b(&sm.u.p3.B[t - 1][0][16 * h + 8 * f][0], kLD2, lane, br);
+            oz::load_b(&sm.u.p3.B[t - 1][1][16 * h + 8 * f][0], kLD2, lane, bi);
+            oz::cmma(are[f], aim[f], ar, ai, br, bi);
+          }
         }
-      }
-      const double sc = ldexp(1.0, -7 * g);
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            oz::fold_group<S>(yhi[0][f][q], ylo[0][f][q], g, are[f][q]);
+            oz::fold_group<S>(yhi[1][f][q], ylo[1][f][q], g, aim[f][q]);
+          }
+      }
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          yre[f][q] = fma((double)are[f][q], sc, yre[f][q]);
-          yim[f][q] = fma((double)aim[f][q], sc, yim[f][q]);
+          const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
+          const int i = r0 + r, j = 16 * h + 8 * f + 2 * tig + (q & 1);
+          if (i < rows && j < ncols) {
+            const int e = sm.eV[r] + sm.eW[j];
+            double2 *x = &X[(size_t)j * ldx + i];
+            double2 v = *x;
+            v.x -= oz::unfold<S>(yhi[0][f][q], ylo[0][f][q], e);
+            v.y -= oz::unfold<S>(yhi[1][f][q], ylo[1][f][q], e);
+            *x = v;
+          }
         }
     }
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
-        const int i = r0 + r, j = 8 * f + 2 * tig + (q & 1);
-        if (i < rows && j < ncols) {
-          const int e = sm.eV[r] + sm.eW[j];
-          double2 *x = &X[(size_t)j * ldx + i];
-          double2 v = *x;
-          v.x -= ldexp(yre[f][q], e);
-          v.y -= ldexp(yim[f][q], e);
-          *x = v;
-        }
-      }
   }
   __syncthreads();
 }
