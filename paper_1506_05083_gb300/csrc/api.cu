@@ -21,7 +21,9 @@ struct ObsHost {
   ObsDev dev;  // device pointers are filled at build time from the offsets below
   std::vector<double> coll, src, srcx, tab_cos, tab_s2;
   std::vector<double2> tw_P;
+  std::vector<int> fft_perm;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
+  size_t off_vdig = 0, off_vexp = 0, off_perm = 0;
 };
 
 }  // namespace
@@ -144,7 +146,33 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.tw_P.resize(o.P);
     for (int r = 0; r < o.P; ++r)
       h.tw_P[r] = make_double2(std::cos(2.0 * kPi * r / o.P), -std::sin(2.0 * kPi * r / o.P));
+    // radices 4, 2, 3, 5 of P for the apply's FFTs and the output permutation
+    {
+      std::vector<int> rad;
+      int n = o.P;
+      while (n % 4 == 0) { rad.push_back(4); n /= 4; }
+      while (n % 2 == 0) { rad.push_back(2); n /= 2; }
+      while (n % 3 == 0) { rad.push_back(3); n /= 3; }
+      while (n % 5 == 0) { rad.push_back(5); n /= 5; }
+      d.fft_nst = (n == 1 && rad.size() <= 8) ? (int)rad.size() : 0;
+      for (int s = 0; s < d.fft_nst; ++s) d.fft_rad[s] = rad[s];
+      h.fft_perm.assign(o.P, 0);
+      if (d.fft_nst > 0) {
+        // pos(n) = (n mod r1) (P / r1) + pos'(n div r1), built from the last radix up
+        std::vector<int> cur(1, 0);
+        int len = 1;
+        for (int s = d.fft_nst - 1; s >= 0; --s) {
+          const int r = rad[s];
+          std::vector<int> nxt(len * r);
+          for (int m = 0; m < len * r; ++m) nxt[m] = (m % r) * len + cur[m / r];
+          cur.swap(nxt);
+          len *= r;
+        }
+        h.fft_perm = cur;
+      }
+    }
     h.off_coll = off; off = align_up(off + sizeof(double) * h.coll.size());
+    h.off_perm = off; off = align_up(off + sizeof(int) * h.fft_perm.size());
     h.off_src = off; off = align_up(off + sizeof(double) * h.src.size());
     h.off_srcx = off; off = align_up(off + sizeof(double) * h.srcx.size());
     h.off_cos = off; off = align_up(off + sizeof(double) * h.tab_cos.size());
@@ -153,6 +181,12 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.off_A = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.rows);
     h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
     h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
+    if (slices > 0) {
+      d.kp = (d.rows + 63) / 64 * 64;
+      const size_t blocks = (size_t)d.D * d.npanels;
+      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * blocks * 4 * slices * axi::kNB * d.kp);
+      h.off_vexp = off; off = align_up(off + sizeof(int) * blocks * (axi::kNB + d.kp));
+    }
   }
   p->bytes = off;
   // QR task list: (obstacle, mode), obstacles with more panels first so the
@@ -230,9 +264,12 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.tab_cos = reinterpret_cast<const double *>(ws + h.off_cos);
     d.tab_s2 = reinterpret_cast<const double *>(ws + h.off_s2);
     d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
+    d.fft_perm = reinterpret_cast<const int *>(ws + h.off_perm);
     d.A = reinterpret_cast<double2 *>(ws + h.off_A);
     d.tau = reinterpret_cast<double2 *>(ws + h.off_tau);
     d.T = reinterpret_cast<double2 *>(ws + h.off_T);
+    d.vdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_vdig) : nullptr;
+    d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
     d.status = reinterpret_cast<int *>(ws + plan->off_status);
     devs[i] = d;
     struct { size_t off; const void *src; size_t n; } cp[] = {
@@ -242,6 +279,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_cos, h.tab_cos.data(), sizeof(double) * h.tab_cos.size()},
         {h.off_s2, h.tab_s2.data(), sizeof(double) * h.tab_s2.size()},
         {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
+        {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
     };
     for (auto &c : cp) {
       if (!c.n) continue;

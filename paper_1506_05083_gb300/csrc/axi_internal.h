@@ -35,6 +35,17 @@ struct ObsDev {
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
   int *status;            // device status word
+  // split precision only: BF16 digits of every panel's reflectors, written once
+  // per factorisation and read by the trailing updates and by every apply.
+  // Per (mode d, panel p) block of 4*slices*kNB*kp entries: first V^H digits
+  // [slices][re/im][kNB][kp] (conjugated), then V row digits [slices][re/im][kp][kNB];
+  // exponents [kNB + kp] (per reflector column, then per row).
+  unsigned short *vdig;
+  int *vexp;
+  int kp;                 // digit row stride: rows rounded up to a multiple of 64
+  int fft_nst;            // radices of P for the apply's FFTs (0: P has other prime factors)
+  int fft_rad[8];
+  const int *fft_perm;    // [P] position of output n after the in-place FFT
 };
 
 // Launch wrappers (each returns the cudaError_t of its launch).
@@ -49,6 +60,8 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, int D, double2 *X, int ncol, int slices,
                                   cudaStream_t st);
 bool split_slices_supported(int slices);
+cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int panel, int slices, cudaStream_t st);
 cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
                             double2 *f, cudaStream_t st);
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,
@@ -57,6 +70,10 @@ cudaError_t launch_eval(const ObsDev *d_o, const ObsDev &h_o, int W, const doubl
                         int T, const double *targets, const double *normals, int kind,
                         const axi_lattice *lat, const double *dirs, double2 *out,
                         cudaStream_t st);
+cudaError_t launch_rhs_fft(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,
+                           double2 *X, cudaStream_t st);
+cudaError_t launch_point_fft(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *coef,
+                             double2 *sigma, cudaStream_t st);
 cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h_o, int W,
                                    const double2 *coef, double2 *sigma, cudaStream_t st);
 

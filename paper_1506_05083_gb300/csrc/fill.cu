@@ -52,6 +52,7 @@ fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ ou
   const double rho = o.coll[4 * mm], z = o.coll[4 * mm + 1];
   const double nr = o.coll[4 * mm + 2], nz = o.coll[4 * mm + 3];
   const int q = o.q, half = q / 2, D = o.D;
+  const int na = (D - warp + 7) / 8;          // modes n = warp + 8a < D handled by this warp
 
   for (int i = threadIdx.x; i < q; i += kThreads) tcos[i] = o.tab_cos[i];
 
@@ -72,8 +73,10 @@ fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ ou
       double2 s = make_double2(0.0, 0.0);
       if (l <= half) {
         // R^2 = (rho - rho')^2 + 4 rho rho' sin^2(phi/2) + (z - z')^2 (no cancellation)
-        const double R = sqrt(base + fourrr * o.tab_s2[l]);
-        const double inv = 1.0 / R;
+        // one reciprocal square root gives both 1/R and R (FP64 rsqrt, <= 1 ulp)
+        const double R2 = base + fourrr * o.tab_s2[l];
+        const double inv = rsqrt(R2);
+        const double R = R2 * inv;
         double sn, cs;
         sincos(k * R, &sn, &cs);
         const double w = ((l == 0 || l == half) ? 1.0 : 2.0) * wq;
@@ -95,13 +98,13 @@ fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ ou
       const int l = l0 + ll;
       const int step = (8 * l) % q;
       int idx = (warp * l) % q;
+      // uniform early exit: predicated-off FP64 FMAs would still occupy the pipe
 #pragma unroll
       for (int a = 0; a < kAcc; ++a) {
-        if (warp + 8 * a < D) {
-          const double c = tcos[idx];
-          acc[a].x = fma(c, s.x, acc[a].x);
-          acc[a].y = fma(c, s.y, acc[a].y);
-        }
+        if (a >= na) break;
+        const double c = tcos[idx];
+        acc[a].x = fma(c, s.x, acc[a].x);
+        acc[a].y = fma(c, s.y, acc[a].y);
         idx += step;
         if (idx >= q) idx -= q;
       }

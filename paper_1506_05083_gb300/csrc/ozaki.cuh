@@ -90,6 +90,29 @@ __device__ __forceinline__ void split_store(double x, int e, __nv_bfloat16 *dst,
   out[0] = int_to_bf16_bits((int)m);
 }
 
+// split_store with a run-time digit count S (1..8) into raw BF16 bit patterns.
+__device__ __forceinline__ void split_store_n(double x, int e, int S, unsigned short *dst,
+                                              size_t stride) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  int Ee = E;
+  if (E == 0) Ee = 1; else M |= 1ull << 52;
+  const int sh = Ee - 1075 + 7 * S - e;
+  long long m;
+  if (sh >= 0) m = (long long)(M << sh);
+  else if (sh > -60) m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else m = 0;
+  if (b >> 63) m = -m;
+  for (int s = S; s >= 2; --s) {
+    int d = (int)(m & 127);
+    if (d >= 64) d -= 128;
+    dst[(s - 1) * stride] = int_to_bf16_bits(d);
+    m = (m - d) >> 7;
+  }
+  dst[0] = int_to_bf16_bits((int)m);
+}
+
 // Exact FP32 integer (|v| < 2^22) -> int32 without a conversion instruction.
 __device__ __forceinline__ int f32_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;

@@ -39,6 +39,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Reduce-scatter of 32 values per lane over the warp: afterwards lane l holds
+// the warp-wide sum of value l. Each level sends half of the remaining values
+// to the partner lane and adds the other half: 31 shuffles and 31 additions
+// per lane, against 160 for 32 separate butterfly sums.
+__device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const double send = upper ? v[i] : v[i + n];
+      const double keep = upper ? v[i + n] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // Sum `n` complex partials over the CTA; result in out[0..n). Contains syncs.
 __device__ void block_sum_c(double2 *part, int n, double (*red)[2 * kNB], double2 *out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -278,10 +297,15 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
         }
       }
     }
+    {
+      // lane l ends with the warp sum of component l (value l/2, re/im l%2)
+      double v[32];
 #pragma unroll
-    for (int x = 0; x < kX; ++x) {
-      const double rx = warp_sum(part[x].x), ry = warp_sum(part[x].y);
-      if (lane == 0) red2[warp][x] = make_double2(rx, ry);
+      for (int x = 0; x < kX; ++x) { v[2 * x] = part[x].x; v[2 * x + 1] = part[x].y; }
+      v[30] = 0.0;
+      v[31] = 0.0;
+      const double r = warp_reduce_scatter32(v);
+      if (lane < 2 * kX) reinterpret_cast<double *>(&red2[warp][0])[lane] = r;
     }
     __syncthreads();                                           // S2
     if (tid < kX) {
@@ -434,18 +458,19 @@ apply_qh_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncol
 // per RHS column inside 32x32 diagonal blocks; rows above are updated with
 // the solved block before moving up.
 constexpr int kTB = 32;
+constexpr int kTS = 8;    // RHS columns per CTA in the triangular solve (one warp each)
 __global__ void __launch_bounds__(kThreads)
 trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
   const ObsDev &o = *od;
   const int d = blockIdx.x;
-  const int c0 = blockIdx.y * kTN;
+  const int c0 = blockIdx.y * kTS;
   if (c0 >= ncols_total) return;
-  const int ncols = min(kTN, ncols_total - c0);
+  const int ncols = min(kTS, ncols_total - c0);
   const double2 *R = o.A + (size_t)d * o.cols * o.rows;
   const int ld = o.rows, n = o.cols;
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   __shared__ double2 Rb[kTB][kTB + 1];
-  __shared__ double2 Yb[kTB][kTN + 1];
+  __shared__ double2 Yb[kTB][kTS + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + kTB - 1) / kTB;
   for (int ib = nblk - 1; ib >= 0; --ib) {
@@ -455,7 +480,7 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
       const int r = e % kTB, c = e / kTB;
       Rb[r][c] = (r < nb && c < nb) ? R[(size_t)(r0 + c) * ld + r0 + r] : make_double2(0.0, 0.0);
     }
-    for (int e = tid; e < kTB * kTN; e += kThreads) {
+    for (int e = tid; e < kTB * kTS; e += kThreads) {
       const int r = e % kTB, c = e / kTB;
       Yb[r][c] = (r < nb && c < ncols) ? Xd[(size_t)c * ld + r0 + r] : make_double2(0.0, 0.0);
     }
@@ -480,12 +505,12 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
       Yb[lane][c] = y;
     }
     __syncthreads();
-    for (int e = tid; e < kTB * kTN; e += kThreads) {
+    for (int e = tid; e < kTB * kTS; e += kThreads) {
       const int r = e % kTB, c = e / kTB;
       if (r < nb && c < ncols) Xd[(size_t)c * ld + r0 + r] = Yb[r][c];
     }
     // rows above: Y(0:r0, c) -= R(0:r0, r0:r0+nb) X_b(:, c)
-    for (int e = tid; e < r0 * kTN; e += kThreads) {
+    for (int e = tid; e < r0 * kTS; e += kThreads) {
       const int r = e % r0, c = e / r0;
       if (c >= ncols) continue;
       double2 acc = Xd[(size_t)c * ld + r];
@@ -605,9 +630,12 @@ cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (e != cudaSuccess) return e;
-  if (slices > 0)
+  if (slices > 0) {
+    e = launch_panel_digits(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, st);
+    if (e != cudaSuccess) return e;
     return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols,
                                   slices, st);
+  }
   if (max_trailing_cols > 0) {
     dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
     qr_update_kernel<<<grid, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
@@ -619,7 +647,10 @@ cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double2 *f,
                          double2 *coef, double2 *sigma, double2 *X, cudaStream_t st) {
   const int ncol = 2 * W;
-  {
+  if (h.fft_nst > 0) {
+    cudaError_t e = launch_rhs_fft(d_o, h, W, f, X, st);
+    if (e != cudaSuccess) return e;
+  } else {
     dim3 grid((h.rows + kDR - 1) / kDR, W);
     size_t smem = sizeof(double2) * (h.P + (size_t)kDR * (h.P + 1));
     if (smem > 48 * 1024) {
@@ -640,7 +671,7 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
-  trsm_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
+  trsm_kernel<<<dim3(h.D, (ncol + kTS - 1) / kTS), kThreads, 0, st>>>(d_o, X, ncol);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scatter_coef_kernel<<<dim3(h.P, W), 128, 0, st>>>(d_o, W, X, coef);
@@ -651,6 +682,7 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
 
 cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h, int W, const double2 *coef,
                                    double2 *sigma, cudaStream_t st) {
+  if (h.fft_nst > 0) return launch_point_fft(d_o, h, W, coef, sigma, st);
   dim3 grid((h.cols + 31) / 32, W);
   point_strength_kernel<<<grid, kThreads, sizeof(double2) * h.P, st>>>(d_o, W, coef, sigma);
   return cudaGetLastError();

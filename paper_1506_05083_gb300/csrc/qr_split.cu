@@ -6,13 +6,16 @@
 //     X <- X - V (T^H (V^H X))         (Sec. 3 eq. linsys; Sec. 4.4),
 // on a tile of kTN target columns. Here the two GEMMs run as Ozaki slice
 // products on BF16 mma.sync (ozaki.cuh) and T^H in FP64:
-//   pass 0  exponents: per column of V (for V^H) and per column of X;
+//   digits  the panel's reflectors are split once per factorisation
+//           (panel_digits_kernel) into V^H digits (exponent per reflector)
+//           and V row digits (exponent per row), kept for every apply;
+//   pass 0  exponents of X's columns;
 //   pass 1  W = V^H X, contraction over the K rows in chunks of 32;
 //   pass 2  W' = T^H W (FP64), per-column exponents and digits of W';
-//   pass 3  X -= V W', V digits per row (exponent over the nb columns),
-//           contraction nb = 16 (one k16 step), FP64 read-modify-write of X.
-// Native FP64 work per X element and panel step: its digit split and the
-// group recombination, about 20 operations against 256 for the FP64 kernel.
+//   pass 3  X -= V W', contraction nb = 16 (one k16 step), FP64
+//           read-modify-write of X.
+// Native FP64 work per X element and panel step: the final recombination
+// and subtraction, a handful of operations against 256 for the FP64 kernel.
 #include "axi_internal.h"
 #include "ozaki.cuh"
 
@@ -70,24 +73,35 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+// Digits and exponents of one (mode, panel) block (layout in ObsDev::vdig).
+struct PanelDigits {
+  const unsigned short *vh;   // [S][2][kNB][kp]
+  const unsigned short *v;    // [S][2][kp][kNB]
+  const int *ex;              // [kNB + kp]
+  int kp;
+};
+
 template <int S>
-__device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda, int rows, int k0,
-                                          int nbp, const double2 *__restrict__ Tg,
+__device__ __forceinline__ PanelDigits panel_digits(const ObsDev &o, int d, int p) {
+  const size_t blk = (size_t)4 * S * kNB * o.kp;
+  PanelDigits pd;
+  pd.vh = o.vdig + ((size_t)d * o.npanels + p) * blk;
+  pd.v = pd.vh + blk / 2;
+  pd.ex = o.vexp + ((size_t)d * o.npanels + p) * (kNB + o.kp);
+  pd.kp = o.kp;
+  return pd;
+}
+
+template <int S>
+__device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0,
+                                          const double2 *__restrict__ Tg,
                                           double2 *__restrict__ X, int ldx, int ncols,
                                           OzSmem<S> &sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane >> 2, tig = lane & 3;
 
-  // ---- pass 0: exponents of V's columns and X's columns over rows k0..rows-1
-  for (int a = warp; a < kNB; a += kThreads / 32) {
-    unsigned long long m = 0;
-    for (int i = k0 + lane; i < rows; i += 32) {
-      const unsigned long long k = key2(vget(A, lda, rows, k0, nbp, i, a));
-      m = k > m ? k : m;
-    }
-    m = warp_max_u64(m);
-    if (lane == 0) sm.eVH[a] = oz::key_exponent(m);
-  }
+  // ---- pass 0: exponents of X's columns over rows k0..rows-1 (V's are stored)
+  if (tid < kNB) sm.eVH[tid] = pd.ex[tid];
   for (int j = warp; j < kTN; j += kThreads / 32) {
     unsigned long long m = 0;
     if (j < ncols)
@@ -105,12 +119,14 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
   long long whi[2][4] = {}, wlo[2][4] = {};
   for (int r0 = k0; r0 < rows; r0 += kKC) {
     __syncthreads();
-    for (int e = tid; e < kNB * kKC; e += kThreads) {
-      const int a = e / kKC, r = e % kKC;
-      const double2 v = vget(A, lda, rows, k0, nbp, r0 + r, a);
-      const int ev = sm.eVH[a];
-      oz::split_store<S>(v.x, ev, &sm.u.p1.A[0][0][a][r], 2 * kNB * kLD1);
-      oz::split_store<S>(-v.y, ev, &sm.u.p1.A[0][1][a][r], 2 * kNB * kLD1);   // conj
+    {
+      // V^H digits of local rows r0-k0 .. +31: 16 words per (digit, part, reflector)
+      const int rr0 = r0 - k0;
+      for (int e = tid; e < S * 2 * kNB * (kKC / 2); e += kThreads) {
+        const int w = e % (kKC / 2), row = e / (kKC / 2);     // row = (s*2 + part)*kNB + a
+        const uint32_t val = reinterpret_cast<const uint32_t *>(pd.vh + (size_t)row * pd.kp + rr0)[w];
+        reinterpret_cast<uint32_t *>(&sm.u.p1.A[0][0][0][0] + row * kLD1)[w] = val;
+      }
     }
     for (int e = tid; e < kTN * kKC; e += kThreads) {
       const int j = e / kKC, r = e % kKC, i = r0 + r;
@@ -193,20 +209,15 @@ __device__ void oz_block_reflector_update(const double2 *__restrict__ A, int lda
   // the 32 target columns in two halves of 16 (two n8 fragments each)
   for (int r0 = k0; r0 < rows; r0 += kRC) {
     __syncthreads();
-    if (tid < kRC) {
-      unsigned long long m = 0;
-      for (int a = 0; a < kNB; ++a) {
-        const unsigned long long k = key2(vget(A, lda, rows, k0, nbp, r0 + tid, a));
-        m = k > m ? k : m;
-      }
-      sm.eV[tid] = oz::key_exponent(m);
-    }
-    __syncthreads();
-    for (int e = tid; e < kRC * kNB; e += kThreads) {
-      const int r = e / kNB, a = e % kNB;
-      const double2 v = vget(A, lda, rows, k0, nbp, r0 + r, a);
-      oz::split_store<S>(v.x, sm.eV[r], &sm.u.p3.A[0][0][r][a], 2 * kRC * kLD2);
-      oz::split_store<S>(v.y, sm.eV[r], &sm.u.p3.A[0][1][r][a], 2 * kRC * kLD2);
+    const int rr0 = r0 - k0;
+    if (tid < kRC) sm.eV[tid] = pd.ex[kNB + rr0 + tid];
+    // V row digits of local rows rr0 .. rr0+63: 8 words per (digit, part, row)
+    for (int e = tid; e < S * 2 * kRC * (kNB / 2); e += kThreads) {
+      const int w = e % (kNB / 2), rowi = e / (kNB / 2);       // rowi = (s*2 + part)*kRC + r
+      const int sp = rowi / kRC, r = rowi % kRC;
+      const uint32_t val =
+          reinterpret_cast<const uint32_t *>(pd.v + ((size_t)sp * pd.kp + rr0 + r) * kNB)[w];
+      reinterpret_cast<uint32_t *>(&sm.u.p3.A[0][0][0][0] + rowi * kLD2)[w] = val;
     }
     __syncthreads();
     if (r0 + 16 * warp >= rows) continue;
@@ -273,8 +284,8 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  oz_block_reflector_update<S>(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows,
-                               ncols, sm);
+  oz_block_reflector_update<S>(panel_digits<S>(o, d, p), o.rows, k0, Tg, A + (size_t)c0 * o.rows,
+                               o.rows, ncols, sm);
 }
 
 template <int S>
@@ -287,14 +298,72 @@ apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, in
   const int ncols = min(kTN, ncols_total - c0);
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
-  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   for (int p = 0; p < o.npanels; ++p) {
-    const int k0 = p * kNB;
-    const int nbp = min(kNB, o.cols - k0);
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-    oz_block_reflector_update<S>(A, o.rows, o.rows, k0, nbp, Tg, Xd, o.rows, ncols, sm);
+    oz_block_reflector_update<S>(panel_digits<S>(o, d, p), o.rows, p * kNB, Tg, Xd, o.rows, ncols,
+                                 sm);
   }
+}
+
+// Digits of one panel's reflectors for every active task (one CTA each).
+template <int S>
+__global__ void __launch_bounds__(256)
+panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                    const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows, kp = o.kp;
+  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  const size_t blk = (size_t)4 * S * kNB * kp;
+  unsigned short *vh = o.vdig + ((size_t)d * o.npanels + p) * blk;
+  unsigned short *v = vh + blk / 2;
+  int *ex = o.vexp + ((size_t)d * o.npanels + p) * (kNB + kp);
+  extern __shared__ int sexp[];                 // [kNB + kp]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int a = warp; a < kNB; a += 8) {
+    unsigned long long m = 0;
+    for (int i = k0 + lane; i < rows; i += 32) {
+      const unsigned long long k = key2(vget(A, rows, rows, k0, nbp, i, a));
+      m = k > m ? k : m;
+    }
+    m = warp_max_u64(m);
+    if (lane == 0) sexp[a] = oz::key_exponent(m);
+  }
+  for (int r = tid; r < kp; r += 256) {
+    unsigned long long m = 0;
+    for (int a = 0; a < kNB; ++a) {
+      const unsigned long long k = key2(vget(A, rows, rows, k0, nbp, k0 + r, a));
+      m = k > m ? k : m;
+    }
+    sexp[kNB + r] = oz::key_exponent(m);
+  }
+  __syncthreads();
+  for (int e = tid; e < kNB + kp; e += 256) ex[e] = sexp[e];
+  // V^H digits: [s][part][a][r]
+  for (int e = tid; e < kNB * kp; e += 256) {
+    const int a = e / kp, r = e % kp;
+    const double2 x = vget(A, rows, rows, k0, nbp, k0 + r, a);
+    const int ev = sexp[a];
+    oz::split_store_n(x.x, ev, S, vh + (size_t)a * kp + r, (size_t)2 * kNB * kp);
+    oz::split_store_n(-x.y, ev, S, vh + (size_t)(kNB + a) * kp + r, (size_t)2 * kNB * kp);
+  }
+  // V row digits: [s][part][r][a]
+  for (int e = tid; e < kp * kNB; e += 256) {
+    const int r = e / kNB, a = e % kNB;
+    const double2 x = vget(A, rows, rows, k0, nbp, k0 + r, a);
+    const int ev = sexp[kNB + r];
+    oz::split_store_n(x.x, ev, S, v + (size_t)r * kNB + a, (size_t)2 * kp * kNB);
+    oz::split_store_n(x.y, ev, S, v + (size_t)(kp + r) * kNB + a, (size_t)2 * kp * kNB);
+  }
+}
+
+template <int S>
+cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int kp_max, cudaStream_t st) {
+  const size_t smem = sizeof(int) * (kNB + kp_max);
+  panel_digits_kernel<S><<<ntasks, 256, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  return cudaGetLastError();
 }
 
 template <int S>
@@ -323,6 +392,20 @@ cudaError_t launch_apply_qh_s(const ObsDev *d_o, int D, double2 *X, int ncol, cu
 }  // namespace
 
 bool split_slices_supported(int s) { return s >= 4 && s <= 8; }
+
+cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int p, int slices, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  const int kp_max = kPanelSmemRows + 64;   // >= any kp (rows <= 2 * M, rounded up)
+  switch (slices) {
+    case 4: return launch_digits_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
+    case 5: return launch_digits_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
+    case 6: return launch_digits_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
+    case 7: return launch_digits_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
+    case 8: return launch_digits_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int p,
