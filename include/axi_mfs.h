@@ -201,7 +201,9 @@ axi_status axi_incident_planewaves(const axi_operator *op, int32_t obs, int32_t 
 
 /*
  * axi_apply_workspace_bytes -- scratch bytes axi_apply_operator needs for W
- * right-hand sides of obstacle `obs` (modal data and RHS blocks).
+ * right-hand sides of obstacle `obs`: the RHS blocks ([D][2W][rows] complex)
+ * and, for split-precision operators with W >= 33 (where the apply's Q^H
+ * runs on tensor cores), the BF16 digits of every panel's reflectors.
  */
 axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W,
                                      size_t *bytes);

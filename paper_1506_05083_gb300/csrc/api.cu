@@ -184,8 +184,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     if (slices > 0) {
       d.kp = (d.rows + 63) / 64 * 64;
       const size_t blocks = (size_t)d.D * d.npanels;
-      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * blocks * 4 * slices * axi::kNB * d.kp);
-      h.off_vexp = off; off = align_up(off + sizeof(int) * blocks * (axi::kNB + d.kp));
+      (void)blocks;
+      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 4 * slices * axi::kNB * d.kp);
+      h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * (axi::kNB + d.kp));
     }
   }
   p->bytes = off;
@@ -346,6 +347,7 @@ axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_
   if (!op || !bytes || obs < 0 || obs >= (int)op->plan->obs.size() || W < 1) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;
   *bytes = align_up(sizeof(double2) * (size_t)d.D * 2 * W * d.rows);
+  if (d.slices > 0 && W >= axi::kSplitApplyMinWaves) *bytes += align_up(axi::apply_digit_bytes(d));
   return AXI_OK;
 }
 
@@ -358,10 +360,11 @@ axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W, co
   axi_apply_workspace_bytes(op, obs, W, &need);
   if (scratch_bytes < need) return AXI_ERR_WORKSPACE;
   const ObsDev &d = op->plan->obs[obs].dev;
+  char *digit_scratch = static_cast<char *>(d_scratch) + align_up(sizeof(double2) * (size_t)d.D * 2 * W * d.rows);
   return cuda_status(axi::launch_apply(op->d_obs + obs, d, W, reinterpret_cast<const double2 *>(d_f),
                                        reinterpret_cast<double2 *>(d_coef),
                                        reinterpret_cast<double2 *>(d_sigma),
-                                       static_cast<double2 *>(d_scratch),
+                                       static_cast<double2 *>(d_scratch), digit_scratch,
                                        static_cast<cudaStream_t>(stream)));
 }
 

@@ -35,11 +35,11 @@ struct ObsDev {
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
   int *status;            // device status word
-  // split precision only: BF16 digits of every panel's reflectors, written once
-  // per factorisation and read by the trailing updates and by every apply.
-  // Per (mode d, panel p) block of 4*slices*kNB*kp entries: first V^H digits
-  // [slices][re/im][kNB][kp] (conjugated), then V row digits [slices][re/im][kp][kNB];
-  // exponents [kNB + kp] (per reflector column, then per row).
+  // split precision only: BF16 digits of the current panel's reflectors (one
+  // block per mode, rewritten at every panel step) for the trailing updates.
+  // Block of 4*slices*kNB*kp entries: V^H digits [slices][re/im][kNB][kp]
+  // (conjugated), then V row digits [slices][re/im][kp][kNB]; exponents
+  // [kNB + kp] (per reflector column, then per row).
   unsigned short *vdig;
   int *vexp;
   int kp;                 // digit row stride: rows rounded up to a multiple of 64
@@ -57,15 +57,21 @@ cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel,
                                    int max_trailing_cols, int slices, cudaStream_t st);
-cudaError_t launch_apply_qh_split(const ObsDev *d_o, int D, double2 *X, int ncol, int slices,
-                                  cudaStream_t st);
+cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                                  void *digit_scratch, cudaStream_t st);
+size_t apply_digit_bytes(const ObsDev &h);
+// Batches of more than this many waves use the split-precision Q^H in split
+// mode; smaller ones use the native FP64 kernel (the digit split of every
+// panel would cost more than it saves).
+constexpr int kSplitApplyMinWaves = 33;
 bool split_slices_supported(int slices);
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                                 int ntasks, int panel, int slices, cudaStream_t st);
 cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
                             double2 *f, cudaStream_t st);
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,
-                         double2 *coef, double2 *sigma, double2 *X, cudaStream_t st);
+                         double2 *coef, double2 *sigma, double2 *X, void *digit_scratch,
+                         cudaStream_t st);
 cudaError_t launch_eval(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *sigma,
                         int T, const double *targets, const double *normals, int kind,
                         const axi_lattice *lat, const double *dirs, double2 *out,

@@ -288,13 +288,18 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
         v = cmul(col[i], scale);
         col[i] = v;
       }
+      // Uniform early exits (jj and nbp are the same for the whole CTA): a
+      // predicated-off FP64 FMA would still occupy the FP64 pipe.
 #pragma unroll
-      for (int x = 0; x < kX; ++x) {
-        if (x < jj) {
-          part[x] = cadd(part[x], cjmul(Ps[x * K + i], v));        // Gram: v_x^H v_jj
-        } else if (x + 1 < nbp) {
-          part[x] = cadd(part[x], cjmul(v, Ps[(x + 1) * K + i]));  // v^H A(:, x+1)
-        }
+      for (int x = 0; x < kX; ++x) {                                  // Gram: v_x^H v_jj, x < jj
+        if (x >= jj) break;
+        part[x] = cadd(part[x], cjmul(Ps[x * K + i], v));
+      }
+#pragma unroll
+      for (int x = kX - 1; x >= 0; --x) {                             // v^H A(:, x+1), x >= jj
+        if (x < jj) break;
+        if (x + 1 >= nbp) continue;
+        part[x] = cadd(part[x], cjmul(v, Ps[(x + 1) * K + i]));
       }
     }
     {
@@ -333,12 +338,12 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       if (i < jj) continue;
       const double2 v = (i == jj) ? make_double2(1.0, 0.0) : col[i];
 #pragma unroll
-      for (int x = 0; x < kX; ++x) {
-        if (x >= jj && x + 1 < nbp) {
-          double2 *y = Ps + (x + 1) * K + i;
-          const double2 vw = cmul(v, wsh[x]);
-          *y = make_double2(y->x - vw.x, y->y - vw.y);
-        }
+      for (int x = kX - 1; x >= 0; --x) {
+        if (x < jj) break;
+        if (x + 1 >= nbp) continue;
+        double2 *y = Ps + (x + 1) * K + i;
+        const double2 vw = cmul(v, wsh[x]);
+        *y = make_double2(y->x - vw.x, y->y - vw.y);
       }
     }
     // col[jj + 1] (alpha of the next column) is read by all threads only after the next S1
@@ -645,7 +650,8 @@ cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int
 }
 
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double2 *f,
-                         double2 *coef, double2 *sigma, double2 *X, cudaStream_t st) {
+                         double2 *coef, double2 *sigma, double2 *X, void *digit_scratch,
+                         cudaStream_t st) {
   const int ncol = 2 * W;
   if (h.fft_nst > 0) {
     cudaError_t e = launch_rhs_fft(d_o, h, W, f, X, st);
@@ -664,8 +670,8 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
   }
   dim3 g2(h.D, (ncol + kTN - 1) / kTN);
   cudaError_t e;
-  if (h.slices > 0) {
-    e = launch_apply_qh_split(d_o, h.D, X, ncol, h.slices, st);
+  if (h.slices > 0 && W >= kSplitApplyMinWaves) {
+    e = launch_apply_qh_split(d_o, h, X, ncol, digit_scratch, st);
   } else {
     apply_qh_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
     e = cudaGetLastError();

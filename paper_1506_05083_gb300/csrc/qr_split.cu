@@ -73,22 +73,29 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
-// Digits and exponents of one (mode, panel) block (layout in ObsDev::vdig).
+// Digits and exponents of one panel's reflectors. Blocks are stored per mode
+// in `nslot` slots: the QR keeps one slot (the current panel), the apply's
+// scratch one slot per panel. Block of 4*S*kNB*kp entries: V^H digits
+// [S][2][kNB][kp], then V row digits [S][2][kp][kNB]; exponents [kNB + kp].
 struct PanelDigits {
-  const unsigned short *vh;   // [S][2][kNB][kp]
-  const unsigned short *v;    // [S][2][kp][kNB]
-  const int *ex;              // [kNB + kp]
+  const unsigned short *vh;
+  const unsigned short *v;
+  const int *ex;
   int kp;
 };
 
 template <int S>
-__device__ __forceinline__ PanelDigits panel_digits(const ObsDev &o, int d, int p) {
-  const size_t blk = (size_t)4 * S * kNB * o.kp;
+__device__ __forceinline__ size_t digit_block(int kp) { return (size_t)4 * S * kNB * kp; }
+
+template <int S>
+__device__ __forceinline__ PanelDigits panel_digits(const unsigned short *dig, const int *ex, int kp,
+                                                    int d, int nslot, int slot) {
+  const size_t blk = digit_block<S>(kp);
   PanelDigits pd;
-  pd.vh = o.vdig + ((size_t)d * o.npanels + p) * blk;
+  pd.vh = dig + ((size_t)d * nslot + slot) * blk;
   pd.v = pd.vh + blk / 2;
-  pd.ex = o.vexp + ((size_t)d * o.npanels + p) * (kNB + o.kp);
-  pd.kp = o.kp;
+  pd.ex = ex + ((size_t)d * nslot + slot) * (kNB + kp);
+  pd.kp = kp;
   return pd;
 }
 
@@ -284,13 +291,14 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  oz_block_reflector_update<S>(panel_digits<S>(o, d, p), o.rows, k0, Tg, A + (size_t)c0 * o.rows,
-                               o.rows, ncols, sm);
+  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, 1, 0), o.rows, k0, Tg,
+                               A + (size_t)c0 * o.rows, o.rows, ncols, sm);
 }
 
 template <int S>
 __global__ void __launch_bounds__(kThreads)
-apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
+apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total,
+                      const unsigned short *__restrict__ dig, const int *__restrict__ dex) {
   const ObsDev &o = *od;
   const int d = blockIdx.x;
   const int c0 = blockIdx.y * kTN;
@@ -301,24 +309,33 @@ apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, in
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   for (int p = 0; p < o.npanels; ++p) {
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-    oz_block_reflector_update<S>(panel_digits<S>(o, d, p), o.rows, p * kNB, Tg, Xd, o.rows, ncols,
-                                 sm);
+    oz_block_reflector_update<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows, p * kNB,
+                                 Tg, Xd, o.rows, ncols, sm);
   }
 }
 
 // Digits of one panel's reflectors for every active task (one CTA each).
+// One CTA per (task, panel): tasks from the QR task list at panel step p
+// (QR: one slot per mode), or every (mode, panel) of one obstacle (apply:
+// task_obs == nullptr, blockIdx.x = mode, blockIdx.y = panel).
 template <int S>
 __global__ void __launch_bounds__(256)
 panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                    const int *__restrict__ task_mode, int p) {
-  const ObsDev &o = obs[task_obs[blockIdx.x]];
-  const int d = task_mode[blockIdx.x];
+                    const int *__restrict__ task_mode, int p_qr, unsigned short *__restrict__ dig,
+                    int *__restrict__ dex) {
+  const bool qr = task_obs != nullptr;
+  const ObsDev &o = qr ? obs[task_obs[blockIdx.x]] : obs[0];
+  const int d = qr ? task_mode[blockIdx.x] : blockIdx.x;
+  const int p = qr ? p_qr : blockIdx.y;
+  const int nslot = qr ? 1 : o.npanels, slot = qr ? 0 : p;
   const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows, kp = o.kp;
   const double2 *A = o.A + (size_t)d * o.cols * o.rows;
-  const size_t blk = (size_t)4 * S * kNB * kp;
-  unsigned short *vh = o.vdig + ((size_t)d * o.npanels + p) * blk;
+  const size_t blk = digit_block<S>(kp);
+  unsigned short *base = qr ? o.vdig : dig;
+  int *ebase = qr ? o.vexp : dex;
+  unsigned short *vh = base + ((size_t)d * nslot + slot) * blk;
   unsigned short *v = vh + blk / 2;
-  int *ex = o.vexp + ((size_t)d * o.npanels + p) * (kNB + kp);
+  int *ex = ebase + ((size_t)d * nslot + slot) * (kNB + kp);
   extern __shared__ int sexp[];                 // [kNB + kp]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int a = warp; a < kNB; a += 8) {
@@ -362,7 +379,8 @@ template <int S>
 cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st) {
   const size_t smem = sizeof(int) * (kNB + kp_max);
-  panel_digits_kernel<S><<<ntasks, 256, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  panel_digits_kernel<S><<<ntasks, 256, smem, st>>>(d_obs, d_task_obs, d_task_mode, p, nullptr,
+                                                    nullptr);
   return cudaGetLastError();
 }
 
@@ -379,13 +397,18 @@ cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const in
 }
 
 template <int S>
-cudaError_t launch_apply_qh_s(const ObsDev *d_o, int D, double2 *X, int ncol, cudaStream_t st) {
-  const size_t smem = sizeof(OzSmem<S>);
-  cudaError_t e = cudaFuncSetAttribute(apply_qh_split_kernel<S>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                              unsigned short *dig, int *dex, cudaStream_t st) {
+  panel_digits_kernel<S><<<dim3(h.D, h.npanels), 256, sizeof(int) * (kNB + h.kp), st>>>(
+      d_o, nullptr, nullptr, 0, dig, dex);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 grid(D, (ncol + kTN - 1) / kTN);
-  apply_qh_split_kernel<S><<<grid, kThreads, smem, st>>>(d_o, X, ncol);
+  const size_t smem = sizeof(OzSmem<S>);
+  e = cudaFuncSetAttribute(apply_qh_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(h.D, (ncol + kTN - 1) / kTN);
+  apply_qh_split_kernel<S><<<grid, kThreads, smem, st>>>(d_o, X, ncol, dig, dex);
   return cudaGetLastError();
 }
 
@@ -421,14 +444,25 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
   }
 }
 
-cudaError_t launch_apply_qh_split(const ObsDev *d_o, int D, double2 *X, int ncol, int slices,
-                                  cudaStream_t st) {
-  switch (slices) {
-    case 4: return launch_apply_qh_s<4>(d_o, D, X, ncol, st);
-    case 5: return launch_apply_qh_s<5>(d_o, D, X, ncol, st);
-    case 6: return launch_apply_qh_s<6>(d_o, D, X, ncol, st);
-    case 7: return launch_apply_qh_s<7>(d_o, D, X, ncol, st);
-    case 8: return launch_apply_qh_s<8>(d_o, D, X, ncol, st);
+size_t apply_digit_bytes(const ObsDev &h) {
+  if (h.slices <= 0) return 0;
+  const size_t blocks = (size_t)h.D * h.npanels;
+  const size_t dig = blocks * 4 * (size_t)h.slices * kNB * h.kp * sizeof(unsigned short);
+  return ((dig + 255) & ~(size_t)255) + blocks * (kNB + h.kp) * sizeof(int);
+}
+
+cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                                  void *digit_scratch, cudaStream_t st) {
+  const size_t blocks = (size_t)h.D * h.npanels;
+  const size_t dig = blocks * 4 * (size_t)h.slices * kNB * h.kp * sizeof(unsigned short);
+  unsigned short *dg = static_cast<unsigned short *>(digit_scratch);
+  int *dx = reinterpret_cast<int *>(static_cast<char *>(digit_scratch) + ((dig + 255) & ~(size_t)255));
+  switch (h.slices) {
+    case 4: return launch_apply_qh_s<4>(d_o, h, X, ncol, dg, dx, st);
+    case 5: return launch_apply_qh_s<5>(d_o, h, X, ncol, dg, dx, st);
+    case 6: return launch_apply_qh_s<6>(d_o, h, X, ncol, dg, dx, st);
+    case 7: return launch_apply_qh_s<7>(d_o, h, X, ncol, dg, dx, st);
+    case 8: return launch_apply_qh_s<8>(d_o, h, X, ncol, dg, dx, st);
     default: return cudaErrorInvalidValue;
   }
 }
