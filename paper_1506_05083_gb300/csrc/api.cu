@@ -44,6 +44,10 @@ struct axi_operator_s {
   char *ws;
   ObsDev *d_obs;
   int *d_task_obs, *d_task_mode, *d_status;
+  // look-ahead: the bulk of each trailing update runs on `side` while the
+  // next panel runs on the caller's stream (fork/join through the events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
 };
 
 namespace {
@@ -185,8 +189,8 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       d.kp = (d.rows + 63) / 64 * 64;
       const size_t blocks = (size_t)d.D * d.npanels;
       (void)blocks;
-      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 4 * slices * axi::kNB * d.kp);
-      h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * (axi::kNB + d.kp));
+      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 4 * slices * axi::kNB * d.kp);
+      h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * 2 * (axi::kNB + d.kp));
     }
   }
   p->bytes = off;
@@ -231,6 +235,12 @@ axi_status axi_plan_destroy(axi_plan *plan) {
   return AXI_OK;
 }
 
+// Fill, then the panel steps with look-ahead. For step p:
+//   caller's stream: panel(p) [+ reflector digits] -> record ev_panel
+//                    -> wait ev_rest(p-1) -> update tile 0 (the next panel's columns)
+//   side stream:     wait ev_panel -> update tiles 1.. -> record ev_rest
+// so panel(p+1) on the caller's stream overlaps the bulk of update(p). Tiles
+// 1.. of step p-1 cover the columns of tile 0 of step p, hence the wait.
 static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   axi_plan_s *p = op->plan;
   cudaError_t e = cudaMemsetAsync(op->d_status, 0, sizeof(int), st);
@@ -240,11 +250,34 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
+  const int slices = p->obs[0].dev.slices;
+  const int tw = axi::update_tile_cols(slices);
+  bool rest_pending = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
-    e = axi::launch_qr_step(op->d_obs, op->d_task_obs, op->d_task_mode, p->step_tasks[s], (int)s,
-                            p->step_cols[s], p->step_rows[s], p->obs[0].dev.slices, st);
+    const int nt = p->step_tasks[s];
+    e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
+                             p->step_rows[s], slices, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
+    const int ntiles = (p->step_cols[s] + tw - 1) / tw;
+    if (ntiles > 1) {
+      if (cudaEventRecord(op->ev_panel, st) != cudaSuccess ||
+          cudaStreamWaitEvent(op->side, op->ev_panel, 0) != cudaSuccess)
+        return AXI_ERR_CUDA;
+    }
+    if (rest_pending && cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess) return AXI_ERR_CUDA;
+    rest_pending = false;
+    e = axi::launch_qr_update(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices, 0,
+                              ntiles > 0 ? 1 : 0, st);
+    if (e != cudaSuccess) return AXI_ERR_CUDA;
+    if (ntiles > 1) {
+      e = axi::launch_qr_update(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices, 1,
+                                ntiles - 1, op->side);
+      if (e != cudaSuccess || cudaEventRecord(op->ev_rest, op->side) != cudaSuccess)
+        return AXI_ERR_CUDA;
+      rest_pending = true;
+    }
   }
+  if (rest_pending && cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess) return AXI_ERR_CUDA;
   return AXI_OK;
 }
 
@@ -305,8 +338,14 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
   op->d_task_obs = reinterpret_cast<int *>(ws + plan->off_task_obs);
   op->d_task_mode = reinterpret_cast<int *>(ws + plan->off_task_mode);
   op->d_status = reinterpret_cast<int *>(ws + plan->off_status);
+  if (cudaStreamCreateWithFlags(&op->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&op->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&op->ev_rest, cudaEventDisableTiming) != cudaSuccess) {
+    axi_operator_destroy(op);
+    return AXI_ERR_CUDA;
+  }
   axi_status s = run_build(op, st);
-  if (s != AXI_OK) { delete op; return s; }
+  if (s != AXI_OK) { axi_operator_destroy(op); return s; }
   *out = op;
   return AXI_OK;
 }
@@ -400,6 +439,13 @@ axi_status axi_operator_status(const axi_operator *op) {
 }
 
 axi_status axi_operator_destroy(axi_operator *op) {
+  if (!op) return AXI_OK;
+  if (op->side) {
+    cudaStreamSynchronize(op->side);
+    cudaStreamDestroy(op->side);
+  }
+  if (op->ev_panel) cudaEventDestroy(op->ev_panel);
+  if (op->ev_rest) cudaEventDestroy(op->ev_rest);
   delete op;
   return AXI_OK;
 }

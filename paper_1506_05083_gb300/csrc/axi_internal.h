@@ -35,8 +35,8 @@ struct ObsDev {
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
   int *status;            // device status word
-  // split precision only: BF16 digits of the current panel's reflectors (one
-  // block per mode, rewritten at every panel step) for the trailing updates.
+  // split precision only: BF16 digits of the current panel's reflectors for
+  // the trailing updates: two blocks per mode, used by alternate panel steps.
   // Block of 4*slices*kNB*kp entries: V^H digits [slices][re/im][kNB][kp]
   // (conjugated), then V row digits [slices][re/im][kp][kNB]; exponents
   // [kNB + kp] (per reflector column, then per row).
@@ -51,12 +51,19 @@ struct ObsDev {
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
-cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int panel, int max_trailing_cols, int max_panel_rows,
-                           int slices, cudaStream_t st);
+cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int panel, int max_panel_rows, int slices, cudaStream_t st);
+// Trailing update of panel step `panel` on column tiles [tile0, tile0 + ntiles)
+// of every active task (tile width update_tile_cols(slices), starting at the
+// first column after the panel).
+cudaError_t launch_qr_update(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                             int ntasks, int panel, int slices, int tile0, int ntiles,
+                             cudaStream_t st);
+int update_tile_cols(int slices);
+int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
-                                   const int *d_task_mode, int ntasks, int panel,
-                                   int max_trailing_cols, int slices, cudaStream_t st);
+                                   const int *d_task_mode, int ntasks, int panel, int slices,
+                                   int tile0, int ntiles, cudaStream_t st);
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);

@@ -21,6 +21,9 @@ namespace axi {
 namespace {
 
 constexpr int kThreads = 256;
+// The shared-memory panel is bound by the FP64 pipe of one SM: fewer threads
+// (about two rows each) halve the per-warp reductions and scalar work.
+constexpr int kPanelThreads = 128;
 constexpr int kTN = 16;   // columns of the target per CTA in block-reflector kernels
 constexpr int kRC = 32;   // rows per shared-memory chunk
 
@@ -218,7 +221,7 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 // barriers per column; the per-row work is 15 independent complex FMAs.
 //   T(jj, jj) = tau_jj,  T(0:jj, jj) = -tau_jj T(0:jj, 0:jj) (V(:, 0:jj)^H v_jj).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPanelThreads)
 qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                      const int *__restrict__ task_mode, int p) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
@@ -229,7 +232,7 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   const int K = o.rows - k0;
   double2 *A = o.A + (size_t)d * o.cols * lda;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kThreads / 32;
+  constexpr int kW = kPanelThreads / 32;
   constexpr int kX = kNB - 1;                  // reduced quantities per column
   extern __shared__ double2 Ps[];              // [nbp][K], column a at Ps + a*K
   __shared__ double red1[kW];
@@ -239,19 +242,19 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   __shared__ double2 Tsh[kNB][kNB + 1];
   __shared__ double2 taush[kNB];
 
-  for (int e = tid; e < nbp * K; e += kThreads) {
+  for (int e = tid; e < nbp * K; e += kPanelThreads) {
     const int a = e / K, i = e % K;
     Ps[e] = A[(size_t)(k0 + a) * lda + k0 + i];
   }
-  for (int e = tid; e < kNB * (kNB + 1); e += kThreads) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
+  for (int e = tid; e < kNB * (kNB + 1); e += kPanelThreads) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
   __syncthreads();
 
   for (int jj = 0; jj < nbp; ++jj) {
     double2 *col = Ps + jj * K;
     double s = 0.0;
-    // Row i is always handled by thread i mod kThreads, so every row's
+    // Row i is always handled by thread i mod kPanelThreads, so every row's
     // updates are made and read by one thread; only reductions cross threads.
-    for (int i = tid; i < K; i += kThreads) {
+    for (int i = tid; i < K; i += kPanelThreads) {
       if (i <= jj) continue;
       const double2 v = col[i];
       s = fma(v.x, v.x, fma(v.y, v.y, s));
@@ -279,7 +282,7 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
     double2 part[kX];
 #pragma unroll
     for (int x = 0; x < kX; ++x) part[x] = make_double2(0.0, 0.0);
-    for (int i = tid; i < K; i += kThreads) {
+    for (int i = tid; i < K; i += kPanelThreads) {
       if (i < jj) continue;
       double2 v;
       if (i == jj) {
@@ -334,7 +337,7 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       Tsh[tid][jj] = make_double2(-t.x, -t.y);
     }
     if (tid == 0) Tsh[jj][jj] = tau;
-    for (int i = tid; i < K; i += kThreads) {
+    for (int i = tid; i < K; i += kPanelThreads) {
       if (i < jj) continue;
       const double2 v = (i == jj) ? make_double2(1.0, 0.0) : col[i];
 #pragma unroll
@@ -342,20 +345,25 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
         if (x < jj) break;
         if (x + 1 >= nbp) continue;
         double2 *y = Ps + (x + 1) * K + i;
-        const double2 vw = cmul(v, wsh[x]);
-        *y = make_double2(y->x - vw.x, y->y - vw.y);
+        const double2 w = wsh[x];
+        double2 t = *y;                       // t -= v w as four FMAs
+        t.x = fma(-v.x, w.x, t.x);
+        t.x = fma(v.y, w.y, t.x);
+        t.y = fma(-v.x, w.y, t.y);
+        t.y = fma(-v.y, w.x, t.y);
+        *y = t;
       }
     }
     // col[jj + 1] (alpha of the next column) is read by all threads only after the next S1
   }
   __syncthreads();
-  for (int e = tid; e < nbp * K; e += kThreads) {
+  for (int e = tid; e < nbp * K; e += kPanelThreads) {
     const int a = e / K, i = e % K;
     A[(size_t)(k0 + a) * lda + k0 + i] = Ps[e];
   }
   if (tid < nbp) o.tau[(size_t)d * o.cols + k0 + tid] = taush[tid];
   double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  for (int e = tid; e < kNB * kNB; e += kThreads) Tg[e] = Tsh[e % kNB][e / kNB];
+  for (int e = tid; e < kNB * kNB; e += kPanelThreads) Tg[e] = Tsh[e % kNB][e / kNB];
 }
 
 // ---------------------------------------------------------------------------
@@ -424,12 +432,12 @@ __device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, 
 
 __global__ void __launch_bounds__(kThreads)
 qr_update_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                 const int *__restrict__ task_mode, int p) {
+                 const int *__restrict__ task_mode, int p, int tile0) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
   const int d = task_mode[blockIdx.x];
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
-  const int c0 = k0 + nbp + blockIdx.y * kTN;
+  const int c0 = k0 + nbp + (tile0 + blockIdx.y) * kTN;
   if (c0 >= o.cols) return;
   const int ncols = min(kTN, o.cols - c0);
   __shared__ BrSmem sm;
@@ -616,9 +624,8 @@ point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__res
 
 }  // namespace
 
-cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int p, int max_trailing_cols, int max_panel_rows,
-                           int slices, cudaStream_t st) {
+cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int max_panel_rows, int slices, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   cudaError_t e;
   if (max_panel_rows <= kPanelSmemRows) {
@@ -628,25 +635,27 @@ cudaError_t launch_qr_step(const ObsDev *d_obs, const int *d_task_obs, const int
                                (int)(sizeof(double2) * (size_t)kNB * kPanelSmemRows));
       if (e != cudaSuccess) return e;
     }
-    qr_panel_smem_kernel<<<ntasks, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+    qr_panel_smem_kernel<<<ntasks, kPanelThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
   } else {
     qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   }
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (e != cudaSuccess) return e;
-  if (slices > 0) {
-    e = launch_panel_digits(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, st);
-    if (e != cudaSuccess) return e;
-    return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols,
-                                  slices, st);
-  }
-  if (max_trailing_cols > 0) {
-    dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
-    qr_update_kernel<<<grid, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
-    e = cudaGetLastError();
-  }
-  return e;
+  if (e != cudaSuccess || slices <= 0) return e;
+  return launch_panel_digits(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, st);
+}
+
+int update_tile_cols(int slices) { return slices > 0 ? split_update_tile_cols() : kTN; }
+
+cudaError_t launch_qr_update(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                             int ntasks, int p, int slices, int tile0, int ntiles,
+                             cudaStream_t st) {
+  if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
+  if (slices > 0)
+    return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, tile0, ntiles,
+                                  st);
+  qr_update_kernel<<<dim3(ntasks, ntiles), kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p,
+                                                              tile0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double2 *f,

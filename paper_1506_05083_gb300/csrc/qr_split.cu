@@ -279,20 +279,20 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                       const int *__restrict__ task_mode, int p) {
+                       const int *__restrict__ task_mode, int p, int tile0) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
   const int d = task_mode[blockIdx.x];
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
-  const int c0 = k0 + nbp + blockIdx.y * kTN;
+  const int c0 = k0 + nbp + (tile0 + blockIdx.y) * kTN;
   if (c0 >= o.cols) return;
   const int ncols = min(kTN, o.cols - c0);
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, 1, 0), o.rows, k0, Tg,
-                               A + (size_t)c0 * o.rows, o.rows, ncols, sm);
+  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, 2, p & 1), o.rows, k0,
+                               Tg, A + (size_t)c0 * o.rows, o.rows, ncols, sm);
 }
 
 template <int S>
@@ -316,7 +316,7 @@ apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, in
 
 // Digits of one panel's reflectors for every active task (one CTA each).
 // One CTA per (task, panel): tasks from the QR task list at panel step p
-// (QR: one slot per mode), or every (mode, panel) of one obstacle (apply:
+// (QR: slot p mod 2 of the mode), or every (mode, panel) of one obstacle (apply:
 // task_obs == nullptr, blockIdx.x = mode, blockIdx.y = panel).
 template <int S>
 __global__ void __launch_bounds__(256)
@@ -327,7 +327,10 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   const ObsDev &o = qr ? obs[task_obs[blockIdx.x]] : obs[0];
   const int d = qr ? task_mode[blockIdx.x] : blockIdx.x;
   const int p = qr ? p_qr : blockIdx.y;
-  const int nslot = qr ? 1 : o.npanels, slot = qr ? 0 : p;
+  // QR: two slots per mode alternating with the step, because the look-ahead
+  // lets step p's trailing update still read its digits while step p+1's are
+  // written; apply: one slot per panel.
+  const int nslot = qr ? 2 : o.npanels, slot = qr ? (p & 1) : p;
   const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows, kp = o.kp;
   const double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const size_t blk = digit_block<S>(kp);
@@ -386,13 +389,13 @@ cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const in
 
 template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int max_trailing_cols, cudaStream_t st) {
+                            int ntasks, int p, int tile0, int ntiles, cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
   cudaError_t e = cudaFuncSetAttribute(qr_update_split_kernel<S>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(ntasks, (max_trailing_cols + kTN - 1) / kTN);
-  qr_update_split_kernel<S><<<grid, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(d_obs, d_task_obs,
+                                                                           d_task_mode, p, tile0);
   return cudaGetLastError();
 }
 
@@ -430,16 +433,17 @@ cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, cons
   }
 }
 
+int split_update_tile_cols() { return kTN; }
+
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
-                                   const int *d_task_mode, int ntasks, int p,
-                                   int max_trailing_cols, int slices, cudaStream_t st) {
-  if (ntasks <= 0 || max_trailing_cols <= 0) return cudaSuccess;
+                                   const int *d_task_mode, int ntasks, int p, int slices,
+                                   int tile0, int ntiles, cudaStream_t st) {
   switch (slices) {
-    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
-    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
-    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
-    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
-    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_trailing_cols, st);
+    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
+    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
+    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
+    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
+    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
     default: return cudaErrorInvalidValue;
   }
 }
