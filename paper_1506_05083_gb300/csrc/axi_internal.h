@@ -48,6 +48,18 @@ struct ObsDev {
   const int *fft_perm;    // [P] position of output n after the in-place FFT
 };
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than any earlier launch did. The first (largest) request happens when an
+// operator is built, so later launches made under stream capture issue no
+// attribute calls.
+template <typename Kernel>
+inline cudaError_t ensure_dynamic_smem(Kernel *kernel, size_t bytes, size_t &granted) {
+  if (bytes <= 48 * 1024 || bytes <= granted) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted = bytes;
+  return e;
+}
+
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);

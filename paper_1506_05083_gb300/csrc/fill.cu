@@ -140,11 +140,9 @@ cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *o
                         int ld_cols, cudaStream_t st) {
   dim3 grid((h.M + kLanes - 1) / kLanes, h.N, h.bc == AXI_BC_TRANSMISSION ? 4 : 1);
   size_t smem = sizeof(double) * ((h.q + 1) & ~1) + sizeof(double2) * kChunk * kLanes;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(fill_kernel, smem, granted);
+  if (e != cudaSuccess) return e;
   fill_kernel<<<grid, kThreads, smem, st>>>(d_obs, oi, out, ld_rows, ld_cols);
   return cudaGetLastError();
 }

@@ -630,11 +630,10 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
   cudaError_t e;
   if (max_panel_rows <= kPanelSmemRows) {
     const size_t smem = sizeof(double2) * (size_t)kNB * max_panel_rows;
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(qr_panel_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(double2) * (size_t)kNB * kPanelSmemRows));
-      if (e != cudaSuccess) return e;
-    }
+    static size_t granted = 0;
+    e = ensure_dynamic_smem(qr_panel_smem_kernel, sizeof(double2) * (size_t)kNB * kPanelSmemRows,
+                            granted);
+    if (e != cudaSuccess) return e;
     qr_panel_smem_kernel<<<ntasks, kPanelThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
   } else {
     qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
@@ -668,11 +667,9 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
   } else {
     dim3 grid((h.rows + kDR - 1) / kDR, W);
     size_t smem = sizeof(double2) * (h.P + (size_t)kDR * (h.P + 1));
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(rhs_dft_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
+    static size_t granted = 0;
+    cudaError_t ea = ensure_dynamic_smem(rhs_dft_kernel, smem, granted);
+    if (ea != cudaSuccess) return ea;
     rhs_dft_kernel<<<grid, kThreads, smem, st>>>(d_o, W, f, X);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -391,8 +391,8 @@ template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int tile0, int ntiles, cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
-  cudaError_t e = cudaFuncSetAttribute(qr_update_split_kernel<S>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
   qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(d_obs, d_task_obs,
                                                                            d_task_mode, p, tile0);
@@ -407,8 +407,8 @@ cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, in
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(OzSmem<S>);
-  e = cudaFuncSetAttribute(apply_qh_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  static size_t granted = 0;
+  e = ensure_dynamic_smem(apply_qh_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
   dim3 grid(h.D, (ncol + kTN - 1) / kTN);
   apply_qh_split_kernel<S><<<grid, kThreads, smem, st>>>(d_o, X, ncol, dig, dex);
