@@ -125,16 +125,16 @@ eval_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__ si
 #pragma unroll
       for (int w = 0; w < kWG; ++w) {
         const double2 ph = phase[w][imi];
-        ksum[w].x += ph.x * kv.x - ph.y * kv.y;
-        ksum[w].y += ph.x * kv.y + ph.y * kv.x;
+        ksum[w].x = fma(ph.x, kv.x, fma(-ph.y, kv.y, ksum[w].x));
+        ksum[w].y = fma(ph.x, kv.y, fma(ph.y, kv.x, ksum[w].y));
       }
     }
 #pragma unroll
     for (int w = 0; w < kWG; ++w) {
       if (w < nw) {
         const double2 sg = sigma[((size_t)(w0 + w) * cols + j) * P + l];
-        acc[w].x += ksum[w].x * sg.x - ksum[w].y * sg.y;
-        acc[w].y += ksum[w].x * sg.y + ksum[w].y * sg.x;
+        acc[w].x = fma(ksum[w].x, sg.x, fma(-ksum[w].y, sg.y, acc[w].x));
+        acc[w].y = fma(ksum[w].x, sg.y, fma(ksum[w].y, sg.x, acc[w].y));
       }
     }
   }

@@ -36,6 +36,19 @@ __device__ __forceinline__ double2 cjmul(double2 a, double2 b) {  // conj(a) * b
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
 }
+// Complex multiply-accumulate as four explicit FMAs (acc + a b, acc + conj(a) b,
+// acc - a b). Written as a product plus an addition, the compiler cannot
+// reassociate and issues six FP64 instructions; these kernels are bound by
+// the FP64 pipe.
+__device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 cfma_conj(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -144,7 +157,7 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
       col[i] = v;
 #pragma unroll
       for (int r = 0; r < kNB - 1; ++r)
-        if (r < nrem) part[r] = cadd(part[r], cjmul(v, A[(size_t)(c + 1 + r) * lda + i]));
+        if (r < nrem) part[r] = cfma_conj(part[r], v, A[(size_t)(c + 1 + r) * lda + i]);
     }
     if (tid == 0) {
 #pragma unroll
@@ -183,7 +196,7 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
     const double2 *va = A + (size_t)(k0 + a) * lda;
     const double2 *vb = A + (size_t)(k0 + b) * lda;
     double2 g = make_double2(0.0, 0.0);
-    for (int i = k0 + b + 1 + lane; i < rows; i += 32) g = cadd(g, cjmul(va[i], vb[i]));
+    for (int i = k0 + b + 1 + lane; i < rows; i += 32) g = cfma_conj(g, va[i], vb[i]);
     g.x = warp_sum(g.x);
     g.y = warp_sum(g.y);
     if (lane == 0) {
@@ -296,13 +309,13 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
 #pragma unroll
       for (int x = 0; x < kX; ++x) {                                  // Gram: v_x^H v_jj, x < jj
         if (x >= jj) break;
-        part[x] = cadd(part[x], cjmul(Ps[x * K + i], v));
+        part[x] = cfma_conj(part[x], Ps[x * K + i], v);
       }
 #pragma unroll
       for (int x = kX - 1; x >= 0; --x) {                             // v^H A(:, x+1), x >= jj
         if (x < jj) break;
         if (x + 1 >= nbp) continue;
-        part[x] = cadd(part[x], cjmul(v, Ps[(x + 1) * K + i]));
+        part[x] = cfma_conj(part[x], v, Ps[(x + 1) * K + i]);
       }
     }
     {
@@ -370,40 +383,44 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
 // X(k0:rows, 0:ncols) <- (I - V T^H V^H) X(k0:rows, 0:ncols) for one panel.
 // One CTA, kTN target columns; FP64. Thread (a, c) = (tid / kTN, tid % kTN).
 // ---------------------------------------------------------------------------
+template <int TN>
 struct BrSmem {
   double2 V[kRC][kNB + 1];
-  double2 X[kRC][kTN + 1];
-  double2 W[kNB][kTN + 1];
+  double2 X[kRC][TN + 1];
+  double2 W[kNB][TN + 1];
   double2 T[kNB][kNB + 1];
 };
 
+template <int TN>
 __device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, int rows, int k0,
                                         int nbp, const double2 *__restrict__ Tg,
-                                        double2 *__restrict__ X, int ldx, int ncols, BrSmem &sm) {
+                                        double2 *__restrict__ X, int ldx, int ncols,
+                                        BrSmem<TN> &sm) {
+  constexpr int NT = kNB * TN;             // threads: one per (reflector, column) of W
   const int tid = threadIdx.x;
-  const int ta = tid / kTN, tc = tid % kTN;
-  for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
+  const int ta = tid / TN, tc = tid % TN;
+  for (int e = tid; e < kNB * kNB; e += NT) sm.T[e % kNB][e / kNB] = Tg[e];
   double2 w = make_double2(0.0, 0.0);
   for (int r0 = k0; r0 < rows; r0 += kRC) {
     __syncthreads();
-    for (int e = tid; e < kRC * kNB; e += kThreads) {
+    for (int e = tid; e < kRC * kNB; e += NT) {
       const int r = e % kRC, a = e / kRC;
       sm.V[r][a] = vget(A, lda, rows, k0, nbp, r0 + r, a);
     }
-    for (int e = tid; e < kRC * kTN; e += kThreads) {
+    for (int e = tid; e < kRC * TN; e += NT) {
       const int r = e % kRC, c = e / kRC;
       const int i = r0 + r;
       sm.X[r][c] = (i < rows && c < ncols) ? X[(size_t)c * ldx + i] : make_double2(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll 8
-    for (int r = 0; r < kRC; ++r) w = cadd(w, cjmul(sm.V[r][ta], sm.X[r][tc]));
+    for (int r = 0; r < kRC; ++r) w = cfma_conj(w, sm.V[r][ta], sm.X[r][tc]);
   }
   sm.W[ta][tc] = w;
   __syncthreads();
   // W' = T^H W  (T upper triangular, so T^H is lower)
   double2 wp = make_double2(0.0, 0.0);
-  for (int b = 0; b <= ta; ++b) wp = cadd(wp, cjmul(sm.T[b][ta], sm.W[b][tc]));
+  for (int b = 0; b <= ta; ++b) wp = cfma_conj(wp, sm.T[b][ta], sm.W[b][tc]);
   __syncthreads();
   sm.W[ta][tc] = wp;
   __syncthreads();
@@ -415,14 +432,10 @@ __device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, 
 #pragma unroll
     for (int a = 0; a < kNB; ++a) vrow[a] = vget(A, lda, rows, k0, nbp, i, a);
     if (i < rows) {
-      for (int c = cg; c < ncols; c += kThreads / kRC) {
+      for (int c = cg; c < ncols; c += NT / kRC) {
         double2 x = X[(size_t)c * ldx + i];
 #pragma unroll
-        for (int a = 0; a < kNB; ++a) {
-          const double2 t = cmul(vrow[a], sm.W[a][c]);
-          x.x -= t.x;
-          x.y -= t.y;
-        }
+        for (int a = 0; a < kNB; ++a) x = cfms(x, vrow[a], sm.W[a][c]);
         X[(size_t)c * ldx + i] = x;
       }
     }
@@ -440,29 +453,33 @@ qr_update_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_ob
   const int c0 = k0 + nbp + (tile0 + blockIdx.y) * kTN;
   if (c0 >= o.cols) return;
   const int ncols = min(kTN, o.cols - c0);
-  __shared__ BrSmem sm;
+  __shared__ BrSmem<kTN> sm;
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  apply_block_reflector_h(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows, ncols,
-                          sm);
+  apply_block_reflector_h<kTN>(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows,
+                               ncols, sm);
 }
 
 // Q^H applied to the RHS block of mode d: X_d is [2W][rows] column-major.
-__global__ void __launch_bounds__(kThreads)
+// Narrow tiles (kTA columns, 128 threads) give several CTAs per mode: the 12+
+// panel applications of one tile are sequential, so parallelism comes from
+// modes x tiles.
+constexpr int kTA = 8;
+__global__ void __launch_bounds__(kNB * kTA)
 apply_qh_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
   const ObsDev &o = *od;
   const int d = blockIdx.x;
-  const int c0 = blockIdx.y * kTN;
+  const int c0 = blockIdx.y * kTA;
   if (c0 >= ncols_total) return;
-  const int ncols = min(kTN, ncols_total - c0);
-  __shared__ BrSmem sm;
+  const int ncols = min(kTA, ncols_total - c0);
+  __shared__ BrSmem<kTA> sm;
   const double2 *A = o.A + (size_t)d * o.cols * o.rows;
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   for (int p = 0; p < o.npanels; ++p) {
     const int k0 = p * kNB;
     const int nbp = min(kNB, o.cols - k0);
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-    apply_block_reflector_h(A, o.rows, o.rows, k0, nbp, Tg, Xd, o.rows, ncols, sm);
+    apply_block_reflector_h<kTA>(A, o.rows, o.rows, k0, nbp, Tg, Xd, o.rows, ncols, sm);
   }
 }
 
@@ -503,17 +520,13 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
       for (int rr = nb - 1; rr >= 0; --rr) {
         double2 x = make_double2(0.0, 0.0);
         if (lane == rr) {
-          const double piv = Rb[rr][rr].x;  // real diagonal (beta of the reflector)
-          y = make_double2(y.x / piv, y.y / piv);
+          const double inv = 1.0 / Rb[rr][rr].x;  // real diagonal (beta of the reflector)
+          y = make_double2(y.x * inv, y.y * inv);
           x = y;
         }
         x.x = __shfl_sync(0xffffffffu, x.x, rr);
         x.y = __shfl_sync(0xffffffffu, x.y, rr);
-        if (lane < rr) {
-          const double2 t = cmul(Rb[lane][rr], x);
-          y.x -= t.x;
-          y.y -= t.y;
-        }
+        if (lane < rr) y = cfms(y, Rb[lane][rr], x);
       }
       Yb[lane][c] = y;
     }
@@ -527,11 +540,7 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
       const int r = e % r0, c = e / r0;
       if (c >= ncols) continue;
       double2 acc = Xd[(size_t)c * ld + r];
-      for (int b = 0; b < nb; ++b) {
-        const double2 t = cmul(R[(size_t)(r0 + b) * ld + r], Yb[b][c]);
-        acc.x -= t.x;
-        acc.y -= t.y;
-      }
+      for (int b = 0; b < nb; ++b) acc = cfms(acc, R[(size_t)(r0 + b) * ld + r], Yb[b][c]);
       Xd[(size_t)c * ld + r] = acc;
     }
   }
@@ -565,7 +574,7 @@ rhs_dft_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__
     double2 acc = make_double2(0.0, 0.0);
     int idx = 0;
     for (int l = 0; l < P; ++l) {
-      acc = cadd(acc, cmul(F[r * ldF + l], tw[idx]));
+      acc = cfma(acc, F[r * ldF + l], tw[idx]);
       idx += ni;
       if (idx >= P) idx -= P;
     }
@@ -616,7 +625,7 @@ point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__res
       if (idx < 0) idx += P;
       const double2 e = tw[idx];                      // e^{-2 pi i n l / P}
       const double2 ep = make_double2(e.x, -e.y);     // e^{+2 pi i n l / P}
-      acc = cadd(acc, cmul(coef[((size_t)w * P + ni) * cols + j], ep));
+      acc = cfma(acc, coef[((size_t)w * P + ni) * cols + j], ep);
     }
     sigma[((size_t)w * cols + j) * P + l] = make_double2(acc.x * invP, acc.y * invP);
   }
@@ -674,12 +683,11 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  dim3 g2(h.D, (ncol + kTN - 1) / kTN);
   cudaError_t e;
   if (h.slices > 0 && W >= kSplitApplyMinWaves) {
     e = launch_apply_qh_split(d_o, h, X, ncol, digit_scratch, st);
   } else {
-    apply_qh_kernel<<<g2, kThreads, 0, st>>>(d_o, X, ncol);
+    apply_qh_kernel<<<dim3(h.D, (ncol + kTA - 1) / kTA), kNB * kTA, 0, st>>>(d_o, X, ncol);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
