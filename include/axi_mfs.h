@@ -281,6 +281,30 @@ axi_status axi_eval_field(const axi_operator *op, int32_t obs, int32_t W,
                           axi_c128 *d_out, void *d_scratch, size_t scratch_bytes,
                           void *stream);
 
+/*
+ * axi_near_image_sum -- A_else of Sec. 4.2 for one obstacle: the normal
+ * derivative, at every ring node x_t = (rho_m, 2 pi l / P, z_m) with its
+ * normal, of the eight phased nearest lattice images of the point sources
+ * (P per proxy ring, strengths from d_coef as in axi_eval_field):
+ *   U_w(x_t) = sum_{(a,b) != 0} alpha_w^a beta_w^b sum_s dG/dn_t(x_t, y_s + (a e_x, b e_y, 0)) sigma_w(s),
+ *   alpha_w = e^{i k d_x e_x}, beta_w = e^{i k d_y e_y} (eq. bloch), d from d_dirs [W][3].
+ *   d_coef  : device [W][P][cols] coefficients (exterior field = first N columns).
+ *   slices  : 0 = native FP64 direct sum; 4..7 = kernel values and strengths
+ *             split into that many BF16 digits, contracted on tensor cores
+ *             (the lattice's 90-degree symmetry is used when e_x = e_y and 4 | P).
+ *   d_out   : device [W][M*P], target index t = m*P + l.
+ *   d_scratch, scratch_bytes : >= axi_near_image_workspace_bytes(); the split
+ *             path stages kernel digits for blocks of whole target rings (~3 GB).
+ * Errors: AXI_ERR_ARG, AXI_ERR_UNSUPPORTED (slices), AXI_ERR_WORKSPACE, AXI_ERR_CUDA.
+ */
+axi_status axi_near_image_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W,
+                                          const axi_lattice *lattice, int32_t slices,
+                                          size_t *bytes);
+axi_status axi_near_image_sum(const axi_operator *op, int32_t obs, int32_t W,
+                              const axi_c128 *d_coef, const axi_lattice *lattice,
+                              const double *d_dirs, int32_t slices, axi_c128 *d_out,
+                              void *d_scratch, size_t scratch_bytes, void *stream);
+
 /* Device status word of the operator (read after synchronising the stream). */
 axi_status axi_operator_status(const axi_operator *op);
 

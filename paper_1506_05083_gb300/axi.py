@@ -58,6 +58,10 @@ SIGNATURES = [
     ("axi_noalloc_scratch_bytes", C.c_size_t, []),
     ("axi_eval_field", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_int32,
                                  C.POINTER(_Lattice), _vp, _vp, _vp, C.c_size_t, _vp]),
+    ("axi_near_image_workspace_bytes", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(_Lattice),
+                                                 C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_near_image_sum", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_Lattice), _vp,
+                                     C.c_int32, _vp, _vp, C.c_size_t, _vp]),
     ("axi_operator_status", C.c_int, [_vp]),
     ("axi_operator_destroy", C.c_int, [_vp]),
     ("axi_plan_destroy", C.c_int, [_vp]),
@@ -259,6 +263,30 @@ class Operator:
                                     scratch.numel() * scratch.element_size(), _stream(stream)),
                "axi_eval_field")
         return out
+
+
+def _near_bytes(op, obs, W, lattice, slices):
+    nb = C.c_size_t(0)
+    _check(lib().axi_near_image_workspace_bytes(op._op, obs, W, C.byref(_Lattice(*lattice)), slices,
+                                                C.byref(nb)), "axi_near_image_workspace_bytes")
+    return nb.value
+
+
+def near_image_sum(op, coef: torch.Tensor, lattice, dirs: torch.Tensor, slices=6, obs=0,
+                   out=None, scratch=None, stream=None):
+    """axi_near_image_sum: [W][M*P] normal derivative of the eight phased images at the ring nodes."""
+    s = op.specs[obs]
+    W = coef.shape[0]
+    if out is None:
+        out = torch.empty((W, s.M * s.P), dtype=torch.complex128, device=coef.device)
+    need = _near_bytes(op, obs, W, lattice, slices)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=coef.device)
+    _check(lib().axi_near_image_sum(op._op, obs, W, _dev(coef), C.byref(_Lattice(*lattice)),
+                                    _dev(dirs), slices, _dev(out), _dev(scratch),
+                                    scratch.numel() * scratch.element_size(), _stream(stream)),
+           "axi_near_image_sum")
+    return out
 
 
 def spec_from_obstacle(ob, q: Optional[int] = None) -> ObstacleSpec:

@@ -428,6 +428,35 @@ axi_status axi_eval_field(const axi_operator *op, int32_t obs, int32_t W, const 
                                       lattice, d_dirs, reinterpret_cast<double2 *>(d_out), st));
 }
 
+axi_status axi_near_image_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W,
+                                          const axi_lattice *lattice, int32_t slices,
+                                          size_t *bytes) {
+  if (!op || !lattice || !bytes || obs < 0 || obs >= (int)op->plan->obs.size() || W < 1)
+    return AXI_ERR_ARG;
+  if (slices != 0 && (slices < 4 || slices > 7)) return AXI_ERR_UNSUPPORTED;
+  *bytes = axi::near_image_scratch_bytes(op->plan->obs[obs].dev, W, lattice->ex, lattice->ey, slices);
+  return AXI_OK;
+}
+
+axi_status axi_near_image_sum(const axi_operator *op, int32_t obs, int32_t W, const axi_c128 *d_coef,
+                              const axi_lattice *lattice, const double *d_dirs, int32_t slices,
+                              axi_c128 *d_out, void *d_scratch, size_t scratch_bytes,
+                              void *stream) {
+  if (!op || !d_coef || !lattice || !d_dirs || !d_out || !d_scratch || obs < 0 ||
+      obs >= (int)op->plan->obs.size() || W < 1)
+    return AXI_ERR_ARG;
+  if (slices != 0 && (slices < 4 || slices > 7)) return AXI_ERR_UNSUPPORTED;
+  if (!(lattice->ex > 0) || !(lattice->ey > 0)) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (scratch_bytes < axi::near_image_scratch_bytes(d, W, lattice->ex, lattice->ey, slices))
+    return AXI_ERR_WORKSPACE;
+  return cuda_status(axi::launch_near_image(op->d_obs + obs, d, W,
+                                            reinterpret_cast<const double2 *>(d_coef),
+                                            lattice->ex, lattice->ey, d_dirs, slices,
+                                            reinterpret_cast<double2 *>(d_out), d_scratch,
+                                            static_cast<cudaStream_t>(stream)));
+}
+
 axi_status axi_operator_status(const axi_operator *op) {
   if (!op) return AXI_ERR_ARG;
   int s = 0;

@@ -99,6 +99,10 @@ cudaError_t launch_rhs_fft(const ObsDev *d_o, const ObsDev &h_o, int W, const do
                            double2 *X, cudaStream_t st);
 cudaError_t launch_point_fft(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *coef,
                              double2 *sigma, cudaStream_t st);
+size_t near_image_scratch_bytes(const ObsDev &h, int W, double ex, double ey, int slices);
+cudaError_t launch_near_image(const ObsDev *d_o, const ObsDev &h, int W, const double2 *coef,
+                              double ex, double ey, const double *dirs, int slices, double2 *U,
+                              void *scratch, cudaStream_t st);
 cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h_o, int W,
                                    const double2 *coef, double2 *sigma, cudaStream_t st);
 
