@@ -21,9 +21,10 @@ struct ObsHost {
   ObsDev dev;  // device pointers are filled at build time from the offsets below
   std::vector<double> coll, src, srcx, tab_cos, tab_s2;
   std::vector<double2> tw_P;
-  std::vector<int> fft_perm;
+  std::vector<int> fft_perm, fft_perm_q;
+  std::vector<double2> tw_q;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
-  size_t off_vdig = 0, off_vexp = 0, off_perm = 0;
+  size_t off_vdig = 0, off_vexp = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
 };
 
 }  // namespace
@@ -53,6 +54,33 @@ struct axi_operator_s {
 namespace {
 
 axi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AXI_OK : AXI_ERR_CUDA; }
+
+// Mixed-radix plan of length n: radices (4s first, then 2, 3, 5) and the
+// position of output k after the in-place decimation-in-frequency FFT,
+//   pos(k) = (k mod r1) (n / r1) + pos'(k div r1).
+// Returns the number of stages, 0 if n has other prime factors.
+int fft_plan(int n, int *rad_out, std::vector<int> &perm) {
+  std::vector<int> rad;
+  int m = n;
+  while (m % 4 == 0) { rad.push_back(4); m /= 4; }
+  while (m % 2 == 0) { rad.push_back(2); m /= 2; }
+  while (m % 3 == 0) { rad.push_back(3); m /= 3; }
+  while (m % 5 == 0) { rad.push_back(5); m /= 5; }
+  perm.assign(n, 0);
+  if (m != 1 || rad.size() > 8) return 0;
+  for (size_t s = 0; s < rad.size(); ++s) rad_out[s] = rad[s];
+  std::vector<int> cur(1, 0);
+  int len = 1;
+  for (int s = (int)rad.size() - 1; s >= 0; --s) {
+    const int r = rad[s];
+    std::vector<int> nxt(len * r);
+    for (int k = 0; k < len * r; ++k) nxt[k] = (k % r) * len + cur[k / r];
+    cur.swap(nxt);
+    len *= r;
+  }
+  perm = cur;
+  return (int)rad.size();
+}
 
 axi_status validate(const axi_obstacle &o) {
   if (!o.h_coll || !o.h_src) return AXI_ERR_ARG;
@@ -150,31 +178,15 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.tw_P.resize(o.P);
     for (int r = 0; r < o.P; ++r)
       h.tw_P[r] = make_double2(std::cos(2.0 * kPi * r / o.P), -std::sin(2.0 * kPi * r / o.P));
-    // radices 4, 2, 3, 5 of P for the apply's FFTs and the output permutation
-    {
-      std::vector<int> rad;
-      int n = o.P;
-      while (n % 4 == 0) { rad.push_back(4); n /= 4; }
-      while (n % 2 == 0) { rad.push_back(2); n /= 2; }
-      while (n % 3 == 0) { rad.push_back(3); n /= 3; }
-      while (n % 5 == 0) { rad.push_back(5); n /= 5; }
-      d.fft_nst = (n == 1 && rad.size() <= 8) ? (int)rad.size() : 0;
-      for (int s = 0; s < d.fft_nst; ++s) d.fft_rad[s] = rad[s];
-      h.fft_perm.assign(o.P, 0);
-      if (d.fft_nst > 0) {
-        // pos(n) = (n mod r1) (P / r1) + pos'(n div r1), built from the last radix up
-        std::vector<int> cur(1, 0);
-        int len = 1;
-        for (int s = d.fft_nst - 1; s >= 0; --s) {
-          const int r = rad[s];
-          std::vector<int> nxt(len * r);
-          for (int m = 0; m < len * r; ++m) nxt[m] = (m % r) * len + cur[m / r];
-          cur.swap(nxt);
-          len *= r;
-        }
-        h.fft_perm = cur;
-      }
-    }
+    // radices 4, 2, 3, 5 and output permutations for the FFTs of length P
+    // (apply) and q (fill)
+    d.fft_nst = fft_plan(o.P, d.fft_rad, h.fft_perm);
+    d.fft_nst_q = fft_plan(o.q, d.fft_rad_q, h.fft_perm_q);
+    h.tw_q.resize(o.q);
+    for (int r = 0; r < o.q; ++r)
+      h.tw_q[r] = make_double2(std::cos(2.0 * kPi * r / o.q), -std::sin(2.0 * kPi * r / o.q));
+    h.off_perm_q = off; off = align_up(off + sizeof(int) * h.fft_perm_q.size());
+    h.off_tw_q = off; off = align_up(off + sizeof(double2) * h.tw_q.size());
     h.off_coll = off; off = align_up(off + sizeof(double) * h.coll.size());
     h.off_perm = off; off = align_up(off + sizeof(int) * h.fft_perm.size());
     h.off_src = off; off = align_up(off + sizeof(double) * h.src.size());
@@ -236,11 +248,13 @@ axi_status axi_plan_destroy(axi_plan *plan) {
 }
 
 // Fill, then the panel steps with look-ahead. For step p:
-//   caller's stream: panel(p) [+ reflector digits] -> record ev_panel
-//                    -> wait ev_rest(p-1) -> update tile 0 (the next panel's columns)
-//   side stream:     wait ev_panel -> update tiles 1.. -> record ev_rest
-// so panel(p+1) on the caller's stream overlaps the bulk of update(p). Tiles
-// 1.. of step p-1 cover the columns of tile 0 of step p, hence the wait.
+//   caller's stream: panel(p) -> record ev_panel -> wait ev_rest(p-1)
+//                    -> FP64 update of the next panel's columns
+//   side stream:     wait ev_panel -> [reflector digits (split)] -> update of the
+//                    columns beyond (split or FP64) -> record ev_rest
+// so panel(p+1) and the small next-panel update form the critical path while
+// the bulk of each trailing update runs beside them. The columns beyond of
+// step p-1 include the next panel's columns of step p, hence the wait.
 static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   axi_plan_s *p = op->plan;
   cudaError_t e = cudaMemsetAsync(op->d_status, 0, sizeof(int), st);
@@ -251,27 +265,32 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   const int slices = p->obs[0].dev.slices;
-  const int tw = axi::update_tile_cols(slices);
   bool rest_pending = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
                              p->step_rows[s], slices, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
-    const int ntiles = (p->step_cols[s] + tw - 1) / tw;
-    if (ntiles > 1) {
+    const int rest_cols = p->step_cols[s] - axi::kNB;
+    if (rest_cols > 0) {
       if (cudaEventRecord(op->ev_panel, st) != cudaSuccess ||
           cudaStreamWaitEvent(op->side, op->ev_panel, 0) != cudaSuccess)
         return AXI_ERR_CUDA;
     }
     if (rest_pending && cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess) return AXI_ERR_CUDA;
     rest_pending = false;
-    e = axi::launch_qr_update(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices, 0,
-                              ntiles > 0 ? 1 : 0, st);
-    if (e != cudaSuccess) return AXI_ERR_CUDA;
-    if (ntiles > 1) {
-      e = axi::launch_qr_update(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices, 1,
-                                ntiles - 1, op->side);
+    if (p->step_cols[s] > 0) {
+      e = axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
+      if (e != cudaSuccess) return AXI_ERR_CUDA;
+    }
+    if (rest_cols > 0) {
+      if (slices > 0) {
+        e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
+                                     op->side);
+        if (e != cudaSuccess) return AXI_ERR_CUDA;
+      }
+      e = axi::launch_qr_update_rest(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
+                                     rest_cols, op->side);
       if (e != cudaSuccess || cudaEventRecord(op->ev_rest, op->side) != cudaSuccess)
         return AXI_ERR_CUDA;
       rest_pending = true;
@@ -299,6 +318,8 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.tab_s2 = reinterpret_cast<const double *>(ws + h.off_s2);
     d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
     d.fft_perm = reinterpret_cast<const int *>(ws + h.off_perm);
+    d.fft_perm_q = reinterpret_cast<const int *>(ws + h.off_perm_q);
+    d.tw_q = reinterpret_cast<const double2 *>(ws + h.off_tw_q);
     d.A = reinterpret_cast<double2 *>(ws + h.off_A);
     d.tau = reinterpret_cast<double2 *>(ws + h.off_tau);
     d.T = reinterpret_cast<double2 *>(ws + h.off_T);
@@ -314,6 +335,8 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_s2, h.tab_s2.data(), sizeof(double) * h.tab_s2.size()},
         {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
         {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
+        {h.off_perm_q, h.fft_perm_q.data(), sizeof(int) * h.fft_perm_q.size()},
+        {h.off_tw_q, h.tw_q.data(), sizeof(double2) * h.tw_q.size()},
     };
     for (auto &c : cp) {
       if (!c.n) continue;

@@ -46,6 +46,10 @@ struct ObsDev {
   int fft_nst;            // radices of P for the apply's FFTs (0: P has other prime factors)
   int fft_rad[8];
   const int *fft_perm;    // [P] position of output n after the in-place FFT
+  int fft_nst_q;          // radices of q for the fill's FFT (0: direct cosine sums)
+  int fft_rad_q[8];
+  const int *fft_perm_q;  // [q]
+  const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
@@ -65,17 +69,17 @@ cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int panel, int max_panel_rows, int slices, cudaStream_t st);
-// Trailing update of panel step `panel` on column tiles [tile0, tile0 + ntiles)
-// of every active task (tile width update_tile_cols(slices), starting at the
-// first column after the panel).
-cudaError_t launch_qr_update(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                             int ntasks, int panel, int slices, int tile0, int ntiles,
-                             cudaStream_t st);
-int update_tile_cols(int slices);
+// Trailing update of panel step `panel`: the next panel's kNB columns (native
+// FP64, critical path), and the columns beyond (split or FP64; col_off = kNB).
+cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
+                                  const int *d_task_mode, int ntasks, int panel, cudaStream_t st);
+cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
+                                  const int *d_task_mode, int ntasks, int panel, int slices,
+                                  int max_rest_cols, cudaStream_t st);
 int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel, int slices,
-                                   int tile0, int ntiles, cudaStream_t st);
+                                   int col_off, int ntiles, cudaStream_t st);
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);

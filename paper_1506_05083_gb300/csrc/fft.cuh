@@ -25,7 +25,7 @@ __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
 __device__ __forceinline__ double2 c_mul_mi(double2 a) { return make_double2(a.y, -a.x); }  // -i a
 
 // In-place forward DFT X[n] = sum_l a[l] e^{-2 pi i n l / P}; output in digit-reversed order.
-__device__ void warp_fft(double2 *a, int P, const double2 *__restrict__ tw, const int *rad, int nst,
+__device__ __forceinline__ void warp_fft(double2 *a, int P, const double2 *__restrict__ tw, const int *rad, int nst,
                          int lane) {
   int L = P;
   for (int s = 0; s < nst; ++s) {

@@ -17,6 +17,7 @@
 // Arithmetic is native FP64 throughout (the ill-conditioned MFS matrices need
 // the full precision); the kernel is bound by the FP64 pipe.
 #include "axi_internal.h"
+#include "fft.cuh"
 
 namespace axi {
 namespace {
@@ -134,10 +135,90 @@ fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ ou
   if (bad) atomicOr(o.status, kStatNonFinite);
 }
 
+// FFT variant (q = 2^a 3^b 5^c): one warp per (m, j) pair evaluates the
+// q/2 + 1 samples, mirrors them into the full even sequence of length q and
+// transforms it in shared memory with the mixed-radix warp FFT (fft.cuh):
+//   A_n = (1/q) sum_{l=0}^{q-1} g_l e^{-2 pi i n l / q},  n = 0 .. D-1.
+// Per sample this costs ~5 log2(q) FP64 operations instead of 2 D FMAs.
+__global__ void __launch_bounds__(256)
+fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ out,
+                int ld_rows, int ld_cols) {
+  const ObsDev &o = obs_arr[oi];
+  const int q = o.q, half = q / 2, D = o.D;
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ double2 fsm[];
+  double2 *tw = fsm;                                        // [q]
+  int *perm = reinterpret_cast<int *>(fsm + q);             // [q]
+  double2 *seq = fsm + q + (q + 1) / 2 + warp * q;          // [nw][q]
+  for (int i = threadIdx.x; i < q; i += blockDim.x) { tw[i] = o.tw_q[i]; perm[i] = o.fft_perm_q[i]; }
+  const int m = blockIdx.x * nw + warp;
+  const int j = blockIdx.y;
+  const int kind = blockIdx.z;
+  const bool deriv = (o.bc == AXI_BC_NEUMANN) ? true : (kind & 1);
+  const bool ext = (o.bc == AXI_BC_TRANSMISSION) && kind >= 2;
+  const double k = ext ? o.km : o.k;
+  const double *S = ext ? o.srcx : o.src;
+  const double rs = S[2 * j], zs = S[2 * j + 1];
+  const int mm = m < o.M ? m : o.M - 1;
+  const double rho = o.coll[4 * mm], z = o.coll[4 * mm + 1];
+  const double nr = o.coll[4 * mm + 2], nz = o.coll[4 * mm + 3];
+  const double dr = rho - rs, dz = z - zs;
+  const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
+  const double wq = kInv4Pi / q;
+  for (int l = lane; l <= half; l += 32) {
+    const double R2 = base + fourrr * o.tab_s2[l];
+    const double inv = rsqrt(R2);
+    const double R = R2 * inv;
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    double2 s;
+    if (!deriv) {
+      s = make_double2(cs * inv * wq, sn * inv * wq);
+    } else {
+      const double ndot = nr * (rho - rs * o.tab_cos[l]) + nz * dz;
+      const double f = ndot * inv * inv * inv * wq, kR = k * R;
+      s = make_double2(f * (-cs - kR * sn), f * (-sn + kR * cs));
+    }
+    seq[l] = s;
+    if (l > 0 && l < half) seq[q - l] = s;
+  }
+  __syncthreads();                                          // tables and sequences ready
+  fft::warp_fft(seq, q, tw, o.fft_rad_q, o.fft_nst_q, lane);
+  if (m >= o.M) return;
+  int row = m, col = j;
+  double sign = 1.0;
+  if (o.bc == AXI_BC_TRANSMISSION) {
+    row += (kind & 1) ? o.M : 0;
+    col += ext ? o.N : 0;
+    sign = ext ? -1.0 : 1.0;
+  }
+  const size_t mode_stride = (size_t)ld_cols * ld_rows;
+  double2 *dst = out + (size_t)col * ld_rows + row;
+  bool bad = false;
+  for (int n = lane; n < D; n += 32) {
+    const double2 v0 = seq[perm[n]];
+    const double2 v = make_double2(sign * v0.x, sign * v0.y);
+    bad |= !isfinite(v.x) || !isfinite(v.y);
+    dst[n * mode_stride] = v;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(o.status, kStatNonFinite);
+}
+
 }  // namespace
 
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out, int ld_rows,
                         int ld_cols, cudaStream_t st) {
+  if (h.fft_nst_q > 0) {
+    const int nw = h.q <= 512 ? 8 : 4;                      // pairs (warps) per CTA
+    const size_t smem = sizeof(double2) * (h.q + (h.q + 1) / 2 + (size_t)nw * h.q);
+    static size_t granted = 0;
+    cudaError_t e = ensure_dynamic_smem(fill_fft_kernel, smem, granted);
+    if (e != cudaSuccess) return e;
+    dim3 grid((h.M + nw - 1) / nw, h.N, h.bc == AXI_BC_TRANSMISSION ? 4 : 1);
+    fill_fft_kernel<<<grid, 32 * nw, smem, st>>>(d_obs, oi, out, ld_rows, ld_cols);
+    return cudaGetLastError();
+  }
   dim3 grid((h.M + kLanes - 1) / kLanes, h.N, h.bc == AXI_BC_TRANSMISSION ? 4 : 1);
   size_t smem = sizeof(double) * ((h.q + 1) & ~1) + sizeof(double2) * kChunk * kLanes;
   static size_t granted = 0;

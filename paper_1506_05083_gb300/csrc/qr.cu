@@ -16,6 +16,7 @@
 // apply runs the same block-reflector product over the stored panels for a
 // tile of right-hand-side columns, then a blocked back substitution with R.
 #include "axi_internal.h"
+#include "ozaki.cuh"
 
 namespace axi {
 namespace {
@@ -254,6 +255,8 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   __shared__ double2 gsh[kX];                  // v_a^H v_jj, index a
   __shared__ double2 Tsh[kNB][kNB + 1];
   __shared__ double2 taush[kNB];
+  __shared__ double2 sc_tau, sc_scale;
+  __shared__ double sc_beta;
 
   for (int e = tid; e < nbp * K; e += kPanelThreads) {
     const int a = e / K, i = e % K;
@@ -275,22 +278,31 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
     s = warp_sum(s);
     if (lane == 0) red1[warp] = s;
     __syncthreads();                                           // S1
-    double xn2 = 0.0;
+    // The reflector's scalars (sqrt, divisions) are computed by one warp and
+    // published: computed by every warp they cost the FP64 pipe kW times.
+    if (warp == 0) {
+      double xn2 = 0.0;
 #pragma unroll
-    for (int w = 0; w < kW; ++w) xn2 += red1[w];
-    const double2 alpha = col[jj];
-    double beta;
-    double2 tau, scale;
-    if (xn2 == 0.0 && alpha.y == 0.0) {
-      beta = alpha.x; tau = make_double2(0.0, 0.0); scale = make_double2(0.0, 0.0);
-    } else {
-      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-      beta = -copysign(nrm, alpha.x);
-      tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-      const double2 den = make_double2(alpha.x - beta, alpha.y);
-      const double dd = den.x * den.x + den.y * den.y;
-      scale = make_double2(den.x / dd, -den.y / dd);          // 1 / (alpha - beta)
+      for (int w = 0; w < kW; ++w) xn2 += red1[w];
+      const double2 alpha = col[jj];
+      double beta;
+      double2 tau, scale;
+      if (xn2 == 0.0 && alpha.y == 0.0) {
+        beta = alpha.x; tau = make_double2(0.0, 0.0); scale = make_double2(0.0, 0.0);
+      } else {
+        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+        beta = -copysign(nrm, alpha.x);
+        const double ib = 1.0 / beta;
+        tau = make_double2((beta - alpha.x) * ib, -alpha.y * ib);
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double idd = 1.0 / (den.x * den.x + den.y * den.y);
+        scale = make_double2(den.x * idd, -den.y * idd);        // 1 / (alpha - beta)
+      }
+      if (lane == 0) { sc_beta = beta; sc_tau = tau; sc_scale = scale; }
     }
+    __syncthreads();                                           // S1b
+    const double beta = sc_beta;
+    const double2 tau = sc_tau, scale = sc_scale;
     // partial sums over own rows i >= jj
     double2 part[kX];
 #pragma unroll
@@ -443,21 +455,22 @@ __device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads)
+template <int TN>
+__global__ void __launch_bounds__(kNB * TN)
 qr_update_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                 const int *__restrict__ task_mode, int p, int tile0) {
+                 const int *__restrict__ task_mode, int p, int col_off) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
   const int d = task_mode[blockIdx.x];
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
-  const int c0 = k0 + nbp + (tile0 + blockIdx.y) * kTN;
+  const int c0 = k0 + nbp + col_off + blockIdx.y * TN;
   if (c0 >= o.cols) return;
-  const int ncols = min(kTN, o.cols - c0);
-  __shared__ BrSmem<kTN> sm;
+  const int ncols = min(TN, o.cols - c0);
+  __shared__ BrSmem<TN> sm;
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  apply_block_reflector_h<kTN>(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows,
-                               ncols, sm);
+  apply_block_reflector_h<TN>(A, o.rows, o.rows, k0, nbp, Tg, A + (size_t)c0 * o.rows, o.rows,
+                              ncols, sm);
 }
 
 // Q^H applied to the RHS block of mode d: X_d is [2W][rows] column-major.
@@ -647,22 +660,32 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
   } else {
     qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess || slices <= 0) return e;
-  return launch_panel_digits(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, st);
+  (void)slices;
+  return cudaGetLastError();
 }
 
-int update_tile_cols(int slices) { return slices > 0 ? split_update_tile_cols() : kTN; }
+// The next panel's kNB columns, in native FP64 with narrow tiles (two CTAs
+// per mode): this update is on the critical path of the factorisation.
+cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
+                                  const int *d_task_mode, int ntasks, int p, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  qr_update_kernel<kTA><<<dim3(ntasks, kNB / kTA), kNB * kTA, 0, st>>>(d_obs, d_task_obs,
+                                                                      d_task_mode, p, 0);
+  return cudaGetLastError();
+}
 
-cudaError_t launch_qr_update(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                             int ntasks, int p, int slices, int tile0, int ntiles,
-                             cudaStream_t st) {
-  if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
+// Columns from kNB past the panel onward, native FP64 or split digits.
+cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
+                                  const int *d_task_mode, int ntasks, int p, int slices,
+                                  int max_rest_cols, cudaStream_t st) {
+  if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
   if (slices > 0)
-    return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, tile0, ntiles,
+    return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, kNB,
+                                  (max_rest_cols + split_update_tile_cols() - 1) /
+                                      split_update_tile_cols(),
                                   st);
-  qr_update_kernel<<<dim3(ntasks, ntiles), kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p,
-                                                              tile0);
+  qr_update_kernel<kTN><<<dim3(ntasks, (max_rest_cols + kTN - 1) / kTN), kThreads, 0, st>>>(
+      d_obs, d_task_obs, d_task_mode, p, kNB);
   return cudaGetLastError();
 }
 

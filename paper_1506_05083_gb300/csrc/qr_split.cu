@@ -279,12 +279,12 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
 template <int S>
 __global__ void __launch_bounds__(kThreads)
 qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                       const int *__restrict__ task_mode, int p, int tile0) {
+                       const int *__restrict__ task_mode, int p, int col_off) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
   const int d = task_mode[blockIdx.x];
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
-  const int c0 = k0 + nbp + (tile0 + blockIdx.y) * kTN;
+  const int c0 = k0 + nbp + col_off + blockIdx.y * kTN;
   if (c0 >= o.cols) return;
   const int ncols = min(kTN, o.cols - c0);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -389,13 +389,13 @@ cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const in
 
 template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int tile0, int ntiles, cudaStream_t st) {
+                            int ntasks, int p, int col_off, int ntiles, cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
   qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(d_obs, d_task_obs,
-                                                                           d_task_mode, p, tile0);
+                                                                           d_task_mode, p, col_off);
   return cudaGetLastError();
 }
 
@@ -437,13 +437,13 @@ int split_update_tile_cols() { return kTN; }
 
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int p, int slices,
-                                   int tile0, int ntiles, cudaStream_t st) {
+                                   int col_off, int ntiles, cudaStream_t st) {
   switch (slices) {
-    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
-    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
-    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
-    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
-    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, tile0, ntiles, st);
+    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
+    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
+    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
+    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
+    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
     default: return cudaErrorInvalidValue;
   }
 }

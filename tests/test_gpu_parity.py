@@ -34,6 +34,9 @@ def _case(name):
         wl = synth.small_case()
     elif name == "small_trans":
         wl = synth.small_case(seed=11, k=2.0, M=44, N=36, P=20, bc=synth.BC_TRANSMISSION)
+    elif name == "medium":
+        # enough columns (80) that trailing updates reach beyond the next panel
+        wl = synth.small_case(seed=13, k=4.0, M=96, N=80, P=16)
     elif name == "smooth":
         wl = synth.config_smooth()
     else:

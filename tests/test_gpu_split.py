@@ -24,7 +24,7 @@ def _op(name, slices):
     return axi, axi.Operator([spec], prec=prec), (wl, ob, geo, A, fac)
 
 
-@pytest.mark.parametrize("name", ["small", "small_trans"])
+@pytest.mark.parametrize("name", ["medium", "small_trans"])
 def test_split_qr_invariants(name):
     axi, op, (wl, ob, geo, A, fac) = _op(name, 7)
     Af = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
@@ -40,7 +40,7 @@ def test_split_qr_invariants(name):
         assert np.linalg.norm(Q[:, :cols] @ R - Af[d]) < 1e-12 * np.linalg.norm(Af[d])
 
 
-@pytest.mark.parametrize("name", ["small", "small_trans", "sphere", "smooth"])
+@pytest.mark.parametrize("name", ["medium", "small_trans", "sphere", "smooth"])
 def test_split_apply_parity(name):
     axi, op, (wl, ob, (coll, src, srcx), A, fac) = _op(name, 7)
     dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
@@ -60,7 +60,7 @@ def test_split_digits_sweep():
     """Error against the oracle shrinks as digits are added (4 -> 8)."""
     errs = []
     for s in (4, 5, 6, 7, 8):
-        axi, op, (wl, ob, (coll, src, srcx), A, fac) = _op("small", s)
+        axi, op, (wl, ob, (coll, src, srcx), A, fac) = _op("medium", s)
         dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
         coef = op.apply(op.incident(torch.tensor(dirs_np, device="cuda")))
         fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
