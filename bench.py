@@ -152,7 +152,12 @@ def main():
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
+    ap.add_argument("--workload", default="smooth", choices=["smooth", "cup", "batched", "cup_near"],
+                    help="smooth (default, the headline line); others print their own line")
     args = ap.parse_args()
+    if args.workload != "smooth":
+        run_extra_workload(args)
+        return
     ws, rank, local = dist_env()
     wl, ob = workload()
     W = wl.n_waves
@@ -332,6 +337,97 @@ def main():
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_extra_workload(args):
+    """Device-timed lines for the other workloads (one GPU, CUDA events, L2 flushed):
+    cup      cup k=25, N=360, M=432, P=180: build + 16-wave apply per step
+    batched  64 seeded obstacles in one plan: build of all + 4 waves applied to each
+    cup_near cup factors built once; per step a 256-wave apply + the 3x3 near-image sum
+    """
+    import torch
+    from paper_1506_05083_gb300 import axi
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = axi.PREC_SPLIT_BF16 | (args.slices << 8) if args.prec == "split" else axi.PREC_FP64
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    near_slices = 6
+    if args.workload == "batched":
+        wl = synth.config_batched()
+        specs = [axi.spec_from_obstacle(o) for o in wl.obstacles]
+        W = wl.n_waves
+    else:
+        wl = synth.config_cup() if args.workload == "cup" else synth.config_cup_apply()
+        specs = [axi.spec_from_obstacle(wl.obstacles[0])]
+        W = wl.n_waves
+    op = axi.Operator(specs, prec=prec)
+    qr_fl = sum((s.P // 2 + 1) * (8.0 * s.rows * s.cols ** 2 - 8.0 * s.cols ** 3 / 3) for s in specs)
+    ap_fl = sum(W * s.P * (16.0 * s.rows * s.cols - 4.0 * s.cols ** 2) for s in specs)
+    dirs = torch.tensor(synth.plane_wave_directions(W, wl.wave_seed), device=dev)
+    bufs = []
+    for i, s in enumerate(specs):
+        bufs.append((torch.empty((W, s.P, s.cols), dtype=torch.complex128, device=dev),
+                     torch.empty((W, s.cols, s.P), dtype=torch.complex128, device=dev),
+                     torch.empty(op.apply_scratch_bytes(W, i), dtype=torch.uint8, device=dev)))
+    near = args.workload == "cup_near"
+    if near:
+        s0 = specs[0]
+        near_out = torch.empty((W, s0.M * s0.P), dtype=torch.complex128, device=dev)
+        near_scr = torch.empty(axi._near_bytes(op, 0, W, wl.lattice, near_slices), dtype=torch.uint8,
+                               device=dev)
+        near_fl = 8.0 * 8 * s0.M * s0.P * s0.N * s0.P * W
+
+    def build():
+        op.refactor()
+
+    def apply():
+        for i in range(len(specs)):
+            coef, sigma, scr = bufs[i]
+            op.apply(op.incident(dirs, obs=i), obs=i, want_sigma=True, scratch=scr, coef=coef,
+                     sigma=sigma)
+        if near:
+            axi.near_image_sum(op, bufs[0][0], wl.lattice, dirs, slices=near_slices, out=near_out,
+                               scratch=near_scr)
+
+    for _ in range(args.warmup):
+        if not near:
+            build()
+        apply()
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    stream = torch.cuda.current_stream()
+    tb, ta = [], []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            if not near:
+                build()
+            e1.record(stream)
+            apply()
+            e2.record(stream)
+            torch.cuda.synchronize()
+            tb.append(e0.elapsed_time(e1))
+            ta.append(e1.elapsed_time(e2))
+    build_ms = float(np.mean(tb))
+    apply_ms = float(np.mean(ta))
+    ms = build_ms + apply_ms
+    flops = (0.0 if near else qr_fl) + ap_fl + (near_fl if near else 0.0)
+    line = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "precision": args.prec, "obstacles": len(specs),
+                       "waves": W, "l2": "flushed (256 MB write) before each timed step",
+                       "near_image_digits": near_slices if near else None},
+            "build_ms": None if near else build_ms,
+            "build_tflops": None if near else qr_fl / (build_ms * 1e-3) / 1e12,
+            "apply_ms": apply_ms, "apply_us_per_wave": apply_ms * 1e3 / W,
+            "clocks": clk.summary(), "device_status": op.status()}
+    if near:
+        line["near_image_pairs_per_s"] = 8.0 * s0.M * s0.P * s0.N * s0.P * W / (apply_ms * 1e-3)
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

@@ -113,6 +113,43 @@ __device__ __forceinline__ void split_store_n(double x, int e, int S, unsigned s
   dst[0] = int_to_bf16_bits((int)m);
 }
 
+// Faster digits for an operand that is split on every use (the trailing
+// matrix in the QR update): sign-magnitude digits u_s = (m >> 7(S-s)) & 127 of
+// m = round(|x| 2^{7S - e}), with one bit of headroom in e (|x| < 2^{e-1}) so
+// m < 2^{7S-1} and u_1 <= 64. Rounding happens once, at the last digit, so the
+// digit errors stay unbiased. BF16 bits of u come from a magic-number add
+// (2^23 + u is exact in FP32). Two values (consecutive rows) are packed per
+// 32-bit word: low half x0, high half x1.
+__device__ __forceinline__ unsigned long long mag_fixed(double x, int e, int S7, unsigned &sign) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  sign = (unsigned)(b >> 63);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  int Ee = E;
+  if (E == 0) Ee = 1; else M |= 1ull << 52;
+  const int sh = Ee - 1075 + S7 - e;
+  if (sh >= 0) return M << sh;
+  if (sh > -60) return (M + (1ull << (-sh - 1))) >> (-sh);
+  return 0;
+}
+__device__ __forceinline__ unsigned bf16_bits_u7(unsigned u) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388608.0f) >> 16;
+}
+template <int S>
+__device__ __forceinline__ void split2_fast(double x0, double x1, int e, uint32_t *dst,
+                                            int stride_words) {
+  unsigned s0, s1;
+  const unsigned long long m0 = mag_fixed(x0, e, 7 * S, s0), m1 = mag_fixed(x1, e, 7 * S, s1);
+#pragma unroll
+  for (int s = 1; s <= S; ++s) {
+    const unsigned u0 = (unsigned)(m0 >> (7 * (S - s))) & 127u;
+    const unsigned u1 = (unsigned)(m1 >> (7 * (S - s))) & 127u;
+    const unsigned b0 = bf16_bits_u7(u0) | (u0 ? s0 << 15 : 0u);
+    const unsigned b1 = bf16_bits_u7(u1) | (u1 ? s1 << 15 : 0u);
+    dst[(s - 1) * stride_words] = b0 | (b1 << 16);
+  }
+}
+
 // Exact FP32 integer (|v| < 2^22) -> int32 without a conversion instruction.
 __device__ __forceinline__ int f32_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;

@@ -117,7 +117,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         m = k > m ? k : m;
       }
     m = warp_max_u64(m);
-    if (lane == 0) sm.eX[j] = oz::key_exponent(m);
+    if (lane == 0) sm.eX[j] = oz::key_exponent(m) + 1;   // headroom for split2_fast
   }
   for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
   __syncthreads();
@@ -135,12 +135,19 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         reinterpret_cast<uint32_t *>(&sm.u.p1.A[0][0][0][0] + row * kLD1)[w] = val;
       }
     }
-    for (int e = tid; e < kTN * kKC; e += kThreads) {
-      const int j = e / kKC, r = e % kKC, i = r0 + r;
-      const double2 x = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
+    // X digits, two consecutive rows per thread and 32-bit word
+    for (int e = tid; e < kTN * (kKC / 2); e += kThreads) {
+      const int j = e / (kKC / 2), rp = e % (kKC / 2), i = r0 + 2 * rp;
+      double2 x0 = make_double2(0.0, 0.0), x1 = make_double2(0.0, 0.0);
+      if (j < ncols) {
+        if (i < rows) x0 = X[(size_t)j * ldx + i];
+        if (i + 1 < rows) x1 = X[(size_t)j * ldx + i + 1];
+      }
       const int ex = sm.eX[j];
-      oz::split_store<S>(x.x, ex, &sm.u.p1.B[0][0][j][r], 2 * kTN * kLD1);
-      oz::split_store<S>(x.y, ex, &sm.u.p1.B[0][1][j][r], 2 * kTN * kLD1);
+      uint32_t *wr = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][0][j][0]) + rp;
+      uint32_t *wi = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][1][j][0]) + rp;
+      oz::split2_fast<S>(x0.x, x1.x, ex, wr, kTN * kLD1);
+      oz::split2_fast<S>(x0.y, x1.y, ex, wi, kTN * kLD1);
     }
     __syncthreads();
 #pragma unroll 1
@@ -159,10 +166,19 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           oz::cmma(are, aim, ar, ai, br, bi);
         }
       }
+      // group sums here reach ~4.5e6 (sign-magnitude X digits up to 127):
+      // exact in FP32 but beyond the magic-number range, so convert directly
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        oz::fold_group<S>(whi[0][q], wlo[0][q], g, are[q]);
-        oz::fold_group<S>(whi[1][q], wlo[1][q], g, aim[q]);
+        const long long vr = (long long)__float2int_rn(are[q]);
+        const long long vi = (long long)__float2int_rn(aim[q]);
+        if (g <= 4) {
+          whi[0][q] += vr << (7 * (4 - g));
+          whi[1][q] += vi << (7 * (4 - g));
+        } else {
+          wlo[0][q] += vr << (7 * (S + 1 - g));
+          wlo[1][q] += vi << (7 * (S + 1 - g));
+        }
       }
     }
   }
