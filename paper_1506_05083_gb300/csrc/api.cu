@@ -24,7 +24,7 @@ struct ObsHost {
   std::vector<int> fft_perm, fft_perm_q;
   std::vector<double2> tw_q;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
-  size_t off_vdig = 0, off_vexp = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
+  size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
 };
 
 }  // namespace
@@ -203,6 +203,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       (void)blocks;
       h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 4 * slices * axi::kNB * d.kp);
       h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * 2 * (axi::kNB + d.kp));
+      h.off_ckey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * d.cols);
     }
   }
   p->bytes = off;
@@ -325,6 +326,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.T = reinterpret_cast<double2 *>(ws + h.off_T);
     d.vdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_vdig) : nullptr;
     d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
+    d.ckey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ckey) : nullptr;
     d.status = reinterpret_cast<int *>(ws + plan->off_status);
     devs[i] = d;
     struct { size_t off; const void *src; size_t n; } cp[] = {

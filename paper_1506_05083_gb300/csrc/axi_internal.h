@@ -43,6 +43,11 @@ struct ObsDev {
   unsigned short *vdig;
   int *vexp;
   int kp;                 // digit row stride: rows rounded up to a multiple of 64
+  // split precision only: [D][2][cols] largest |entry| key (IEEE bits) of each
+  // trailing column over the next panel step's rows, written by one split
+  // update and read by the next (alternating slots), so the trailing matrix
+  // is not scanned for its exponents at every step.
+  unsigned long long *ckey;
   int fft_nst;            // radices of P for the apply's FFTs (0: P has other prime factors)
   int fft_rad[8];
   const int *fft_perm;    // [P] position of output n after the in-place FFT

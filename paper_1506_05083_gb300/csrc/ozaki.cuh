@@ -177,6 +177,29 @@ __device__ __forceinline__ double unfold(long long hi, long long lo, int E) {
   return ldexp((double)hi, e1) + ldexp((double)lo, e2);
 }
 
+// hi 2^{-28} + lo 2^{-7(S+1)} as one 64-bit integer t, the value being
+// t 2^{unfold1_shift<S>()} (times 2^E). Valid when |hi| < 2^34, which holds
+// for a single k16 step of a complex contraction (group g = 2 sums at most
+// 32 products of two digits <= 128, weight 2^14): one integer-to-FP64
+// conversion instead of two.
+template <int S>
+__device__ __forceinline__ long long unfold1_int(long long hi, long long lo) {
+  constexpr int sh = 7 * (S + 1) - 28;
+  constexpr int shh = sh < 28 ? sh : 28;
+  constexpr int drop = sh - shh;
+  if constexpr (drop > 0) return (hi << shh) + ((lo + (1ll << (drop - 1))) >> drop);
+  else return (hi << shh) + lo;
+}
+template <int S>
+__host__ __device__ constexpr int unfold1_shift() {
+  return -7 * (S + 1) + ((7 * (S + 1) - 28) - ((7 * (S + 1) - 28) < 28 ? (7 * (S + 1) - 28) : 28));
+}
+// 2^e as a double (normal range), else via ldexp.
+__device__ __forceinline__ double pow2(int e) {
+  if (e > -1000 && e < 1000) return __longlong_as_double((long long)(1023 + e) << 52);
+  return ldexp(1.0, e);
+}
+
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {
   return *reinterpret_cast<const uint32_t *>(p);
 }

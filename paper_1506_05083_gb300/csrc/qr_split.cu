@@ -48,6 +48,7 @@ struct OzSmem {
   double2 W[kNB][kTN + 1];
   double2 T[kNB][kNB + 1];
   int eVH[kNB], eX[kTN], eW[kTN], eV[kRC];
+  unsigned long long kNext[kTN];
 };
 
 __device__ __forceinline__ double2 vget(const double2 *A, int lda, int rows, int k0, int nbp, int i,
@@ -99,57 +100,89 @@ __device__ __forceinline__ PanelDigits panel_digits(const unsigned short *dig, c
   return pd;
 }
 
+// Column-max keys of X: `kin` (global, per column) when the previous update
+// left them, else `carry` (the previous panel's pass 3 of this CTA left them
+// in sm.kNext), else a scan of rows k0..rows-1. Pass 3 always leaves the keys
+// of the updated X over rows k0+kNB.. (the next panel step's rows) in
+// sm.kNext, and in `kout` when that is given.
 template <int S>
 __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0,
                                           const double2 *__restrict__ Tg,
                                           double2 *__restrict__ X, int ldx, int ncols,
-                                          OzSmem<S> &sm) {
+                                          const unsigned long long *__restrict__ kin, bool carry,
+                                          unsigned long long *__restrict__ kout, OzSmem<S> &sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane >> 2, tig = lane & 3;
 
   // ---- pass 0: exponents of X's columns over rows k0..rows-1 (V's are stored)
   if (tid < kNB) sm.eVH[tid] = pd.ex[tid];
-  for (int j = warp; j < kTN; j += kThreads / 32) {
-    unsigned long long m = 0;
-    if (j < ncols)
-      for (int i = k0 + lane; i < rows; i += 32) {
-        const unsigned long long k = key2(X[(size_t)j * ldx + i]);
-        m = k > m ? k : m;
-      }
-    m = warp_max_u64(m);
-    if (lane == 0) sm.eX[j] = oz::key_exponent(m) + 1;   // headroom for split2_fast
+  if (kin != nullptr || carry) {
+    if (tid < kTN) {
+      const unsigned long long m = tid < ncols ? (carry ? sm.kNext[tid] : kin[tid]) : 0ull;
+      sm.eX[tid] = oz::key_exponent(m) + 1;                   // headroom for split2_fast
+    }
+  } else {
+    for (int j = warp; j < kTN; j += kThreads / 32) {
+      unsigned long long m = 0;
+      if (j < ncols)
+        for (int i = k0 + lane; i < rows; i += 32) {
+          const unsigned long long k = key2(X[(size_t)j * ldx + i]);
+          m = k > m ? k : m;
+        }
+      m = warp_max_u64(m);
+      if (lane == 0) sm.eX[j] = oz::key_exponent(m) + 1;
+    }
   }
   for (int e = tid; e < kNB * kNB; e += kThreads) sm.T[e % kNB][e / kNB] = Tg[e];
   __syncthreads();
+  if (tid < kTN) sm.kNext[tid] = 0ull;
 
-  // ---- pass 1: W = V^H X (16 x kTN); warp w owns columns 8w..8w+7
-  long long whi[2][4] = {}, wlo[2][4] = {};
-  for (int r0 = k0; r0 < rows; r0 += kKC) {
-    __syncthreads();
-    {
-      // V^H digits of local rows r0-k0 .. +31: 16 words per (digit, part, reflector)
-      const int rr0 = r0 - k0;
-      for (int e = tid; e < S * 2 * kNB * (kKC / 2); e += kThreads) {
-        const int w = e % (kKC / 2), row = e / (kKC / 2);     // row = (s*2 + part)*kNB + a
-        const uint32_t val = reinterpret_cast<const uint32_t *>(pd.vh + (size_t)row * pd.kp + rr0)[w];
-        reinterpret_cast<uint32_t *>(&sm.u.p1.A[0][0][0][0] + row * kLD1)[w] = val;
+  // ---- pass 1: W = V^H X (16 x kTN); warp w owns columns 8w..8w+7. The next
+  // chunk's V^H digits and X values are loaded into registers while the
+  // current chunk's slice products run.
+  constexpr int kVU = S * 2 * kNB * (kKC / 8) / kThreads;      // uint4 of V^H digits per thread
+  constexpr int kXU = kTN * (kKC / 2) / kThreads;              // row pairs of X per thread
+  static_assert(S * 2 * kNB * (kKC / 8) % kThreads == 0 && kTN * (kKC / 2) % kThreads == 0, "");
+  uint4 vst[kVU];
+  double2 xst[kXU][2];
+  auto stage = [&](int r0) {
+    const int rr0 = r0 - k0;
+#pragma unroll
+    for (int u = 0; u < kVU; ++u) {
+      const int e = tid + u * kThreads, row = e >> 2, w4 = e & 3;  // row = (s*2 + part)*kNB + a
+      vst[u] = *reinterpret_cast<const uint4 *>(pd.vh + (size_t)row * pd.kp + rr0 + 8 * w4);
+    }
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int e = tid + u * kThreads, j = e / (kKC / 2), rp = e % (kKC / 2), i = r0 + 2 * rp;
+      xst[u][0] = xst[u][1] = make_double2(0.0, 0.0);
+      if (j < ncols) {
+        if (i < rows) xst[u][0] = X[(size_t)j * ldx + i];
+        if (i + 1 < rows) xst[u][1] = X[(size_t)j * ldx + i + 1];
       }
     }
+  };
+  long long whi[2][4] = {}, wlo[2][4] = {};
+  stage(k0);
+  for (int r0 = k0; r0 < rows; r0 += kKC) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kVU; ++u) {
+      const int e = tid + u * kThreads, row = e >> 2, w4 = e & 3;
+      *reinterpret_cast<uint4 *>(&sm.u.p1.A[0][0][0][0] + row * kLD1 + 8 * w4) = vst[u];
+    }
     // X digits, two consecutive rows per thread and 32-bit word
-    for (int e = tid; e < kTN * (kKC / 2); e += kThreads) {
-      const int j = e / (kKC / 2), rp = e % (kKC / 2), i = r0 + 2 * rp;
-      double2 x0 = make_double2(0.0, 0.0), x1 = make_double2(0.0, 0.0);
-      if (j < ncols) {
-        if (i < rows) x0 = X[(size_t)j * ldx + i];
-        if (i + 1 < rows) x1 = X[(size_t)j * ldx + i + 1];
-      }
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int e = tid + u * kThreads, j = e / (kKC / 2), rp = e % (kKC / 2);
       const int ex = sm.eX[j];
       uint32_t *wr = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][0][j][0]) + rp;
       uint32_t *wi = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][1][j][0]) + rp;
-      oz::split2_fast<S>(x0.x, x1.x, ex, wr, kTN * kLD1);
-      oz::split2_fast<S>(x0.y, x1.y, ex, wi, kTN * kLD1);
+      oz::split2_fast<S>(xst[u][0].x, xst[u][1].x, ex, wr, kTN * kLD1);
+      oz::split2_fast<S>(xst[u][0].y, xst[u][1].y, ex, wi, kTN * kLD1);
     }
     __syncthreads();
+    if (r0 + kKC < rows) stage(r0 + kKC);
 #pragma unroll 1
     for (int g = 2; g <= S + 1; ++g) {
       float are[4] = {0, 0, 0, 0}, aim[4] = {0, 0, 0, 0};
@@ -229,23 +262,35 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   }
 
   // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk,
-  // the 32 target columns in two halves of 16 (two n8 fragments each)
+  // the 32 target columns in two halves of 16 (two n8 fragments each). The
+  // X values of a half are loaded before its slice products run.
+  const int knext = k0 + kNB;
+  unsigned long long cmax0[2][2] = {}, cmax1[2][2] = {};     // halves 0/1: [fragment][q & 1]
   for (int r0 = k0; r0 < rows; r0 += kRC) {
     __syncthreads();
     const int rr0 = r0 - k0;
     if (tid < kRC) sm.eV[tid] = pd.ex[kNB + rr0 + tid];
     // V row digits of local rows rr0 .. rr0+63: 8 words per (digit, part, row)
-    for (int e = tid; e < S * 2 * kRC * (kNB / 2); e += kThreads) {
-      const int w = e % (kNB / 2), rowi = e / (kNB / 2);       // rowi = (s*2 + part)*kRC + r
+    for (int e = tid; e < S * 2 * kRC * (kNB / 8); e += kThreads) {
+      const int w4 = e % (kNB / 8), rowi = e / (kNB / 8);     // rowi = (s*2 + part)*kRC + r
       const int sp = rowi / kRC, r = rowi % kRC;
-      const uint32_t val =
-          reinterpret_cast<const uint32_t *>(pd.v + ((size_t)sp * pd.kp + rr0 + r) * kNB)[w];
-      reinterpret_cast<uint32_t *>(&sm.u.p3.A[0][0][0][0] + rowi * kLD2)[w] = val;
+      const uint4 val =
+          reinterpret_cast<const uint4 *>(pd.v + ((size_t)sp * pd.kp + rr0 + r) * kNB)[w4];
+      reinterpret_cast<uint4 *>(&sm.u.p3.A[0][0][0][0] + rowi * kLD2)[w4] = val;
     }
     __syncthreads();
     if (r0 + 16 * warp >= rows) continue;
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
+      double2 xv[2][4];
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = r0 + 16 * warp + grp + (q >= 2 ? 8 : 0);
+          const int j = 16 * h + 8 * f + 2 * tig + (q & 1);
+          xv[f][q] = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
+        }
       long long yhi[2][2][4] = {}, ylo[2][2][4] = {};     // [part][fragment][element]
 #pragma unroll 1
       for (int g = 2; g <= S + 1; ++g) {
@@ -279,17 +324,45 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
           const int i = r0 + r, j = 16 * h + 8 * f + 2 * tig + (q & 1);
           if (i < rows && j < ncols) {
-            const int e = sm.eV[r] + sm.eW[j];
-            double2 *x = &X[(size_t)j * ldx + i];
-            double2 v = *x;
-            v.x -= oz::unfold<S>(yhi[0][f][q], ylo[0][f][q], e);
-            v.y -= oz::unfold<S>(yhi[1][f][q], ylo[1][f][q], e);
-            *x = v;
+            const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
+            const double tr = (double)oz::unfold1_int<S>(yhi[0][f][q], ylo[0][f][q]);
+            const double ti = (double)oz::unfold1_int<S>(yhi[1][f][q], ylo[1][f][q]);
+            double2 v = xv[f][q];
+            if (e > -1000 && e < 1000) {
+              const double pw = oz::pow2(e);
+              v.x = fma(-tr, pw, v.x);
+              v.y = fma(-ti, pw, v.y);
+            } else {
+              v.x -= ldexp(tr, e);
+              v.y -= ldexp(ti, e);
+            }
+            X[(size_t)j * ldx + i] = v;
+            if (i >= knext) {
+              const unsigned long long k = key2(v);
+              if (h == 0) cmax0[f][q & 1] = k > cmax0[f][q & 1] ? k : cmax0[f][q & 1];
+              else cmax1[f][q & 1] = k > cmax1[f][q & 1] ? k : cmax1[f][q & 1];
+            }
           }
         }
     }
   }
+  // column keys over rows >= k0 + kNB: lanes with the same tig share columns
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        unsigned long long m = h == 0 ? cmax0[f][c] : cmax1[f][c];
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+          const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
+          m = w > m ? w : m;
+        }
+        if (grp == 0 && m != 0ull) atomicMax(&sm.kNext[16 * h + 8 * f + 2 * tig + c], m);
+      }
   __syncthreads();
+  if (kout != nullptr && tid < ncols) kout[tid] = sm.kNext[tid];
 }
 
 template <int S>
@@ -307,8 +380,12 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  // carried column keys: slot p mod 2 written by step p-1, slot (p+1) mod 2 for step p+1
+  const unsigned long long *kin =
+      p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
+  unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
   oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, 2, p & 1), o.rows, k0,
-                               Tg, A + (size_t)c0 * o.rows, o.rows, ncols, sm);
+                               Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin, false, kout, sm);
 }
 
 template <int S>
@@ -326,7 +403,7 @@ apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, in
   for (int p = 0; p < o.npanels; ++p) {
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
     oz_block_reflector_update<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows, p * kNB,
-                                 Tg, Xd, o.rows, ncols, sm);
+                                 Tg, Xd, o.rows, ncols, nullptr, p > 0, nullptr, sm);
   }
 }
 
