@@ -57,6 +57,17 @@ struct ObsDev {
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
 
+// Kernels of one factorisation step run side by side (panel and next-panel
+// update on the critical path, digits and trailing update beside them). With
+// the default carveout an SM sized for one kernel's shared memory can refuse
+// the CTAs of another; asking for the largest shared-memory carveout lets
+// them co-reside. Called once per kernel, outside stream capture.
+template <typename Kernel>
+inline void prefer_max_shared(Kernel *kernel) {
+  (void)cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
 // than any earlier launch did. The first (largest) request happens when an
 // operator is built, so later launches made under stream capture issue no

@@ -165,16 +165,29 @@ __device__ __forceinline__ void fold_group(long long &hi, long long &lo, int g, 
   else lo += v << (7 * (S + 1 - g));
 }
 
+// t 2^e rounded to the nearest double (ties to even), built from the bits
+// with integer instructions only: on this part an integer-to-FP64
+// conversion occupies the FP64 pipe like an FMA. Falls back to ldexp when
+// the result is not a normal number.
+__device__ __forceinline__ double scaled_to_double(long long t, int e) {
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = t < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                              // leading one at bit 63
+  unsigned long long m = a >> 11;                        // 53 significant bits
+  const unsigned rem = (unsigned)(a & 0x7ffu);
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  const int E = 63 - lz + e;                             // value in [2^E, 2^{E+1}]
+  if (E < -1021 || E > 1022) return ldexp((double)t, e);
+  // the hidden bit of m (or its carry) adds to the biased exponent field
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(E + 1022) << 52) + m)));
+}
+
 // hi 2^{-28} + lo 2^{-7(S+1)}, times 2^E.
 template <int S>
 __device__ __forceinline__ double unfold(long long hi, long long lo, int E) {
-  const int e1 = E - 28, e2 = E - 7 * (S + 1);
-  if (e1 < 1000 && e2 > -1000) {
-    const double p1 = __longlong_as_double((long long)(1023 + e1) << 52);
-    const double p2 = __longlong_as_double((long long)(1023 + e2) << 52);
-    return fma((double)hi, p1, (double)lo * p2);
-  }
-  return ldexp((double)hi, e1) + ldexp((double)lo, e2);
+  return scaled_to_double(hi, E - 28) + scaled_to_double(lo, E - 7 * (S + 1));
 }
 
 // hi 2^{-28} + lo 2^{-7(S+1)} as one 64-bit integer t, the value being
@@ -193,11 +206,6 @@ __device__ __forceinline__ long long unfold1_int(long long hi, long long lo) {
 template <int S>
 __host__ __device__ constexpr int unfold1_shift() {
   return -7 * (S + 1) + ((7 * (S + 1) - 28) - ((7 * (S + 1) - 28) < 28 ? (7 * (S + 1) - 28) : 28));
-}
-// 2^e as a double (normal range), else via ldexp.
-__device__ __forceinline__ double pow2(int e) {
-  if (e > -1000 && e < 1000) return __longlong_as_double((long long)(1023 + e) << 52);
-  return ldexp(1.0, e);
 }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {

@@ -227,12 +227,16 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 
 // ---------------------------------------------------------------------------
 // Panel with the K x nbp panel held in shared memory (K = rows - k0 <= kPanelSmemRows).
-// Thread t owns local rows t, t + kThreads, ...; for column jj it forms, for its
-// rows, the partial sums of the 15 quantities the column needs (the dot
-// products v^H A(:, c) with the remaining panel columns c > jj, and the Gram
-// entries v_a^H v for the earlier reflectors a < jj that build T), reduces them
-// in one block reduction, and applies the rank-1 update to its own rows. Three
-// barriers per column; the per-row work is 15 independent complex FMAs.
+// Thread t owns local rows t, t + kPanelThreads, ... for the whole panel, so
+// only reductions cross threads. Column jj needs, from the rows i > jj of its
+// unscaled column x,
+//   xn2 = sum |x_i|^2,  P_c = sum conj(x_i) a_c[i] (c > jj),  Q_a = sum conj(v_a[i]) x_i (a < jj);
+// with scale = 1 / (alpha - beta) and v = (1; x scale),
+//   v^H a_c = a_c[jj] + conj(scale) P_c,   v_a^H v = conj(v_a[jj]) + scale Q_a,
+// so one reduction per column suffices. The partial sums for column jj + 1
+// are formed in the same sweep that applies reflector jj to the owner's rows:
+// two barriers per column (partials reduced; scalars published), the
+// scalars computed by warp 0. T follows at the end from the Gram entries:
 //   T(jj, jj) = tau_jj,  T(0:jj, jj) = -tau_jj T(0:jj, 0:jj) (V(:, 0:jj)^H v_jj).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPanelThreads)
@@ -247,16 +251,15 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   double2 *A = o.A + (size_t)d * o.cols * lda;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kW = kPanelThreads / 32;
-  constexpr int kX = kNB - 1;                  // reduced quantities per column
+  constexpr int kX = kNB - 1;                  // complex partials per column
   extern __shared__ double2 Ps[];              // [nbp][K], column a at Ps + a*K
-  __shared__ double red1[kW];
-  __shared__ double2 red2[kW][kX];
-  __shared__ double2 wsh[kX];                  // conj(tau) v^H A(:, c), index c - 1
-  __shared__ double2 gsh[kX];                  // v_a^H v_jj, index a
+  __shared__ double red[kW][32];               // per-warp sums: complex x at 2x, 2x+1; xn2 at 30
+  __shared__ double tot[32];
+  __shared__ double2 wsh[kX];                  // conj(tau) v^H a_c, index c - 1
+  __shared__ double2 Gsh[kNB][kNB];            // Gsh[a][j] = v_a^H v_j, a < j
   __shared__ double2 Tsh[kNB][kNB + 1];
   __shared__ double2 taush[kNB];
-  __shared__ double2 sc_tau, sc_scale;
-  __shared__ double sc_beta;
+  __shared__ double2 sc_scale;
 
   for (int e = tid; e < nbp * K; e += kPanelThreads) {
     const int a = e / K, i = e % K;
@@ -265,121 +268,150 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   for (int e = tid; e < kNB * (kNB + 1); e += kPanelThreads) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
   __syncthreads();
 
-  for (int jj = 0; jj < nbp; ++jj) {
-    double2 *col = Ps + jj * K;
-    double s = 0.0;
-    // Row i is always handled by thread i mod kPanelThreads, so every row's
-    // updates are made and read by one thread; only reductions cross threads.
-    for (int i = tid; i < K; i += kPanelThreads) {
-      if (i <= jj) continue;
-      const double2 v = col[i];
-      s = fma(v.x, v.x, fma(v.y, v.y, s));
-    }
-    s = warp_sum(s);
-    if (lane == 0) red1[warp] = s;
-    __syncthreads();                                           // S1
-    // The reflector's scalars (sqrt, divisions) are computed by one warp and
-    // published: computed by every warp they cost the FP64 pipe kW times.
-    if (warp == 0) {
-      double xn2 = 0.0;
+  // partial sums for column 0: slot x holds P_{x+1}
+  double2 part[kX];
+  double2 qjj = make_double2(0.0, 0.0);        // Q of the latest reflector, for slot qslot
+  int qslot = -1;
+  double xn2p = 0.0;
 #pragma unroll
-      for (int w = 0; w < kW; ++w) xn2 += red1[w];
-      const double2 alpha = col[jj];
+  for (int x = 0; x < kX; ++x) part[x] = make_double2(0.0, 0.0);
+  for (int i = tid; i < K; i += kPanelThreads) {
+    if (i == 0) continue;
+    const double2 xi = Ps[i];
+    xn2p = fma(xi.x, xi.x, fma(xi.y, xi.y, xn2p));
+#pragma unroll
+    for (int x = 0; x < kX; ++x) {
+      if (x + 1 >= nbp) break;
+      part[x] = cfma_conj(part[x], xi, Ps[(x + 1) * K + i]);
+    }
+  }
+
+  for (int jj = 0; jj < nbp; ++jj) {
+    {
+      // lane l ends with the warp sum of component l
+      double v[32];
+#pragma unroll
+      for (int x = 0; x < kX; ++x) {
+        // slot qslot holds no other partial: select, not add (an FP64 add each)
+        v[2 * x] = x == qslot ? qjj.x : part[x].x;
+        v[2 * x + 1] = x == qslot ? qjj.y : part[x].y;
+      }
+      v[30] = xn2p;
+      v[31] = 0.0;
+      red[warp][lane] = warp_reduce_scatter32(v);
+    }
+    __syncthreads();                                           // B1: partials of column jj
+    if (warp == 0) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kW; ++w) s += red[w][lane];
+      tot[lane] = s;
+      __syncwarp();
+      const double xn2 = tot[30];
+      const double2 alpha = Ps[jj * K + jj];
       double beta;
       double2 tau, scale;
       if (xn2 == 0.0 && alpha.y == 0.0) {
         beta = alpha.x; tau = make_double2(0.0, 0.0); scale = make_double2(0.0, 0.0);
       } else {
-        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-        beta = -copysign(nrm, alpha.x);
-        const double ib = 1.0 / beta;
+        // one reciprocal square root gives both |beta| and 1 / beta
+        const double s2 = fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xn2));
+        const double r = rsqrt(s2);
+        beta = -copysign(s2 * r, alpha.x);
+        const double ib = -copysign(r, alpha.x);
         tau = make_double2((beta - alpha.x) * ib, -alpha.y * ib);
         const double2 den = make_double2(alpha.x - beta, alpha.y);
         const double idd = 1.0 / (den.x * den.x + den.y * den.y);
         scale = make_double2(den.x * idd, -den.y * idd);        // 1 / (alpha - beta)
       }
-      if (lane == 0) { sc_beta = beta; sc_tau = tau; sc_scale = scale; }
+      if (lane < kX) {
+        const double2 val = make_double2(tot[2 * lane], tot[2 * lane + 1]);
+        if (lane < jj) {
+          const double2 va = Ps[lane * K + jj];
+          Gsh[lane][jj] = cfma(make_double2(va.x, -va.y), scale, val);      // conj(v_a[jj]) + scale Q_a
+        } else if (lane + 1 < nbp) {
+          const double2 vh = cfma_conj(Ps[(lane + 1) * K + jj], scale, val);  // a_c[jj] + conj(scale) P_c
+          wsh[lane] = cjmul(tau, vh);
+        }
+      }
+      if (lane == 0) {
+        Ps[jj * K + jj] = make_double2(beta, 0.0);
+        taush[jj] = tau;
+        sc_scale = scale;
+        if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
+      }
     }
-    __syncthreads();                                           // S1b
-    const double beta = sc_beta;
-    const double2 tau = sc_tau, scale = sc_scale;
-    // partial sums over own rows i >= jj
-    double2 part[kX];
+    __syncthreads();                                           // B2: scalars of column jj
+    // Apply reflector jj to the owner's rows, scale v, and form the partial
+    // sums of column jn = jj + 1 (slot x < jn: Q_x; x >= jn: P_{x+1}).
+    const double2 scale = sc_scale;
+    const int jn = jj + 1;
+    double2 w[kX];
+#pragma unroll
+    for (int x = kX - 1; x >= 0; --x) {
+      if (x < jj) break;
+      w[x] = wsh[x];
+    }
 #pragma unroll
     for (int x = 0; x < kX; ++x) part[x] = make_double2(0.0, 0.0);
+    qjj = make_double2(0.0, 0.0);
+    qslot = jj;
+    xn2p = 0.0;
+    const double2 wj = jn < nbp ? wsh[jj] : make_double2(0.0, 0.0);   // column jn's coefficient
     for (int i = tid; i < K; i += kPanelThreads) {
       if (i < jj) continue;
-      double2 v;
-      if (i == jj) {
-        v = make_double2(1.0, 0.0);
-      } else {
-        v = cmul(col[i], scale);
-        col[i] = v;
+      if (i == jj) {                                           // v_jj = 1 on row jj
+#pragma unroll
+        for (int x = kX - 1; x >= 0; --x) {
+          if (x < jj) break;
+          if (x + 1 >= nbp) continue;
+          double2 *y = Ps + (x + 1) * K + jj;
+          *y = make_double2(y->x - w[x].x, y->y - w[x].y);
+        }
+        continue;
       }
-      // Uniform early exits (jj and nbp are the same for the whole CTA): a
-      // predicated-off FP64 FMA would still occupy the FP64 pipe.
-#pragma unroll
-      for (int x = 0; x < kX; ++x) {                                  // Gram: v_x^H v_jj, x < jj
-        if (x >= jj) break;
-        part[x] = cfma_conj(part[x], Ps[x * K + i], v);
+      const double2 v = cmul(Ps[jj * K + i], scale);
+      Ps[jj * K + i] = v;
+      if (jn >= nbp) continue;
+      const bool acc = i > jn;
+      const double2 xn = cfms(Ps[jn * K + i], v, wj);
+      Ps[jn * K + i] = xn;
+      if (acc) {
+        xn2p = fma(xn.x, xn.x, fma(xn.y, xn.y, xn2p));
+        qjj = cfma_conj(qjj, v, xn);
       }
 #pragma unroll
-      for (int x = kX - 1; x >= 0; --x) {                             // v^H A(:, x+1), x >= jj
-        if (x < jj) break;
-        if (x + 1 >= nbp) continue;
-        part[x] = cfma_conj(part[x], v, Ps[(x + 1) * K + i]);
-      }
-    }
-    {
-      // lane l ends with the warp sum of component l (value l/2, re/im l%2)
-      double v[32];
-#pragma unroll
-      for (int x = 0; x < kX; ++x) { v[2 * x] = part[x].x; v[2 * x + 1] = part[x].y; }
-      v[30] = 0.0;
-      v[31] = 0.0;
-      const double r = warp_reduce_scatter32(v);
-      if (lane < 2 * kX) reinterpret_cast<double *>(&red2[warp][0])[lane] = r;
-    }
-    __syncthreads();                                           // S2
-    if (tid < kX) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int w = 0; w < kW; ++w) acc = cadd(acc, red2[w][tid]);
-      if (tid < jj) gsh[tid] = acc;
-      else wsh[tid] = cmul(make_double2(tau.x, -tau.y), acc);
-    }
-    if (tid == 0) {
-      col[jj] = make_double2(beta, 0.0);
-      taush[jj] = tau;
-      if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
-    }
-    __syncthreads();                                           // S3
-    // T column jj (rows < jj in parallel), then the rank-1 update of own rows
-    if (tid < jj) {
-      double2 z = make_double2(0.0, 0.0);
-      for (int l = tid; l < jj; ++l) z = cadd(z, cmul(Tsh[tid][l], gsh[l]));
-      const double2 t = cmul(tau, z);
-      Tsh[tid][jj] = make_double2(-t.x, -t.y);
-    }
-    if (tid == 0) Tsh[jj][jj] = tau;
-    for (int i = tid; i < K; i += kPanelThreads) {
-      if (i < jj) continue;
-      const double2 v = (i == jj) ? make_double2(1.0, 0.0) : col[i];
-#pragma unroll
-      for (int x = kX - 1; x >= 0; --x) {
-        if (x < jj) break;
+      for (int x = kX - 1; x >= 0; --x) {                      // columns c = x + 1 > jn
+        if (x < jn) break;
         if (x + 1 >= nbp) continue;
         double2 *y = Ps + (x + 1) * K + i;
-        const double2 w = wsh[x];
-        double2 t = *y;                       // t -= v w as four FMAs
-        t.x = fma(-v.x, w.x, t.x);
-        t.x = fma(v.y, w.y, t.x);
-        t.y = fma(-v.x, w.y, t.y);
-        t.y = fma(-v.y, w.x, t.y);
-        *y = t;
+        const double2 yn = cfms(*y, v, w[x]);
+        *y = yn;
+        if (acc) part[x] = cfma_conj(part[x], xn, yn);
+      }
+      if (acc) {
+#pragma unroll
+        for (int x = 0; x < kX; ++x) {                         // Gram with earlier reflectors a < jj
+          if (x >= jj) break;
+          part[x] = cfma_conj(part[x], Ps[x * K + i], xn);
+        }
       }
     }
-    // col[jj + 1] (alpha of the next column) is read by all threads only after the next S1
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < nbp; ++j) {
+      const double2 tj = taush[j];
+      if (lane < j) {
+        double2 z = make_double2(0.0, 0.0);
+        for (int l = lane; l < j; ++l) z = cfma(z, Tsh[lane][l], Gsh[l][j]);
+        const double2 t = cmul(tj, z);
+        Tsh[lane][j] = make_double2(-t.x, -t.y);
+      } else if (lane == j) {
+        Tsh[j][j] = tj;
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   for (int e = tid; e < nbp * K; e += kPanelThreads) {
@@ -656,6 +688,8 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
     e = ensure_dynamic_smem(qr_panel_smem_kernel, sizeof(double2) * (size_t)kNB * kPanelSmemRows,
                             granted);
     if (e != cudaSuccess) return e;
+    static const bool carve = (prefer_max_shared(qr_panel_smem_kernel), true);
+    (void)carve;
     qr_panel_smem_kernel<<<ntasks, kPanelThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
   } else {
     qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
@@ -669,6 +703,8 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
 cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int p, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
+  static const bool carve = (prefer_max_shared(qr_update_kernel<kTA>), true);
+  (void)carve;
   qr_update_kernel<kTA><<<dim3(ntasks, kNB / kTA), kNB * kTA, 0, st>>>(d_obs, d_task_obs,
                                                                       d_task_mode, p, 0);
   return cudaGetLastError();
@@ -684,6 +720,8 @@ cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   (max_rest_cols + split_update_tile_cols() - 1) /
                                       split_update_tile_cols(),
                                   st);
+  static const bool carve = (prefer_max_shared(qr_update_kernel<kTN>), true);
+  (void)carve;
   qr_update_kernel<kTN><<<dim3(ntasks, (max_rest_cols + kTN - 1) / kTN), kThreads, 0, st>>>(
       d_obs, d_task_obs, d_task_mode, p, kNB);
   return cudaGetLastError();

@@ -325,17 +325,9 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           const int i = r0 + r, j = 16 * h + 8 * f + 2 * tig + (q & 1);
           if (i < rows && j < ncols) {
             const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
-            const double tr = (double)oz::unfold1_int<S>(yhi[0][f][q], ylo[0][f][q]);
-            const double ti = (double)oz::unfold1_int<S>(yhi[1][f][q], ylo[1][f][q]);
             double2 v = xv[f][q];
-            if (e > -1000 && e < 1000) {
-              const double pw = oz::pow2(e);
-              v.x = fma(-tr, pw, v.x);
-              v.y = fma(-ti, pw, v.y);
-            } else {
-              v.x -= ldexp(tr, e);
-              v.y -= ldexp(ti, e);
-            }
+            v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][f][q], ylo[0][f][q]), e);
+            v.y -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[1][f][q], ylo[1][f][q]), e);
             X[(size_t)j * ldx + i] = v;
             if (i >= knext) {
               const unsigned long long k = key2(v);
@@ -475,6 +467,8 @@ template <int S>
 cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st) {
   const size_t smem = sizeof(int) * (kNB + kp_max);
+  static const bool carve = (prefer_max_shared(panel_digits_kernel<S>), true);
+  (void)carve;
   panel_digits_kernel<S><<<ntasks, 256, smem, st>>>(d_obs, d_task_obs, d_task_mode, p, nullptr,
                                                     nullptr);
   return cudaGetLastError();
@@ -487,6 +481,8 @@ cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const in
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
+  static const bool carve = (prefer_max_shared(qr_update_split_kernel<S>), true);
+  (void)carve;
   qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(d_obs, d_task_obs,
                                                                            d_task_mode, p, col_off);
   return cudaGetLastError();
