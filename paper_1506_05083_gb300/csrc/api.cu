@@ -251,8 +251,8 @@ axi_status axi_plan_destroy(axi_plan *plan) {
 // Fill, then the panel steps with look-ahead. For step p:
 //   caller's stream: panel(p) -> record ev_panel -> wait ev_rest(p-1)
 //                    -> FP64 update of the next panel's columns
-//   side stream:     wait ev_panel -> [reflector digits (split)] -> update of the
-//                    columns beyond (split or FP64) -> record ev_rest
+//   side stream:     wait ev_panel -> [reflector digits (split)] -> update of
+//                    the columns beyond (split or FP64) -> record ev_rest
 // so panel(p+1) and the small next-panel update form the critical path while
 // the bulk of each trailing update runs beside them. The columns beyond of
 // step p-1 include the next panel's columns of step p, hence the wait.

@@ -95,7 +95,7 @@ cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
 int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel, int slices,
-                                   int col_off, int ntiles, cudaStream_t st);
+                                   int col_off, int ntiles, int max_cols, cudaStream_t st);
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);

@@ -228,6 +228,16 @@ __device__ __forceinline__ void load_b(const __nv_bfloat16 *base, int ld, int la
   b[1] = ld32(base + g * ld + 8 + 2 * t);
 }
 
+// ldmatrix: four 8x8 b16 matrices from shared memory; lane l gives the row
+// address of row (l mod 8) of matrix (l / 8), and receives in r[m] the pair
+// (row l / 4, columns 2 (l mod 4), +1) of matrix m, i.e. mma fragment order.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 // Complex slice product for one k16 step: acc_re += Ar Br - Ai Bi, acc_im += Ar Bi + Ai Br.
 __device__ __forceinline__ void cmma(float (&re)[4], float (&im)[4], const uint32_t (&ar)[4],
                                      const uint32_t (&ai)[4], const uint32_t (&br)[2],

@@ -17,6 +17,9 @@
 // tile of right-hand-side columns, then a blocked back substitution with R.
 #include "axi_internal.h"
 #include "ozaki.cuh"
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace axi {
 namespace {
@@ -226,47 +229,81 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 }
 
 // ---------------------------------------------------------------------------
-// Panel with the K x nbp panel held in shared memory (K = rows - k0 <= kPanelSmemRows).
-// Thread t owns local rows t, t + kPanelThreads, ... for the whole panel, so
-// only reductions cross threads. Column jj needs, from the rows i > jj of its
+// Panel held in shared memory, factored by a cluster of C CTAs (C = 1: one
+// CTA, K = rows - k0 <= kPanelSmemRows). Thread t of CTA r owns the rows
+// i = r NT + t + u C NT (NT = kPanelThreads) for the whole panel, so only
+// reductions cross threads. Column jj needs, from the rows i > jj of its
 // unscaled column x,
 //   xn2 = sum |x_i|^2,  P_c = sum conj(x_i) a_c[i] (c > jj),  Q_a = sum conj(v_a[i]) x_i (a < jj);
 // with scale = 1 / (alpha - beta) and v = (1; x scale),
 //   v^H a_c = a_c[jj] + conj(scale) P_c,   v_a^H v = conj(v_a[jj]) + scale Q_a,
 // so one reduction per column suffices. The partial sums for column jj + 1
-// are formed in the same sweep that applies reflector jj to the owner's rows:
-// two barriers per column (partials reduced; scalars published), the
-// scalars computed by warp 0. T follows at the end from the Gram entries:
+// are formed in the same sweep that applies reflector jj to the owner's rows.
+// Per column: partials reduced per warp and, with C > 1, exchanged through
+// distributed shared memory (one cluster barrier; double-buffered with the
+// row jj the owner publishes), then every CTA's warp 0 forms the same
+// scalars, and a CTA barrier publishes them. T follows at the end from the
+// Gram entries:
 //   T(jj, jj) = tau_jj,  T(0:jj, jj) = -tau_jj T(0:jj, 0:jj) (V(:, 0:jj)^H v_jj).
 // ---------------------------------------------------------------------------
+template <int C>
 __global__ void __launch_bounds__(kPanelThreads)
 qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                      const int *__restrict__ task_mode, int p) {
-  const ObsDev &o = obs[task_obs[blockIdx.x]];
-  const int d = task_mode[blockIdx.x];
+  constexpr int NT = kPanelThreads;
+  constexpr int kStride = C * NT;
+  constexpr int kBuf = C > 1 ? 2 : 1;
+  const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int task = blockIdx.x / C;
+  const ObsDev &o = obs[task_obs[task]];
+  const int d = task_mode[task];
   const int lda = o.rows;
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
   const int K = o.rows - k0;
+  const int Kl = C > 1 ? NT * ((K + kStride - 1) / kStride) : K;   // local rows per column
   double2 *A = o.A + (size_t)d * o.cols * lda;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kPanelThreads / 32;
+  constexpr int kW = NT / 32;
   constexpr int kX = kNB - 1;                  // complex partials per column
-  extern __shared__ double2 Ps[];              // [nbp][K], column a at Ps + a*K
-  __shared__ double red[kW][32];               // per-warp sums: complex x at 2x, 2x+1; xn2 at 30
+  extern __shared__ double2 Ps[];              // [nbp][Kl]; slot u NT + t holds row r NT + t + u C NT
+  __shared__ double red[kBuf][kW][32];         // per-warp sums: complex x at 2x, 2x+1; xn2 at 30
+  __shared__ double2 rowbuf[kBuf][kNB];        // row jj as published by its owner (C > 1)
   __shared__ double tot[32];
   __shared__ double2 wsh[kX];                  // conj(tau) v^H a_c, index c - 1
   __shared__ double2 Gsh[kNB][kNB];            // Gsh[a][j] = v_a^H v_j, a < j
   __shared__ double2 Tsh[kNB][kNB + 1];
   __shared__ double2 taush[kNB];
   __shared__ double2 sc_scale;
+  auto row_of = [&](int slot) { return (slot / NT) * kStride + rank * NT + slot % NT; };
+  auto owner_of = [&](int i) { return (i % kStride) / NT; };
+  auto slot_of = [&](int i) { return (i / kStride) * NT + i % NT; };
+  // Column j of T (one warp; columns < j, tau_j and the Gram column j are
+  // complete). Done while warp 0 forms the next column's scalars, on another
+  // SM sub-partition's FP64 unit.
+  auto t_column = [&](int j) {
+    const double2 tj = taush[j];
+    if (lane < j) {
+      double2 z = make_double2(0.0, 0.0);
+      for (int l = lane; l < j; ++l) z = cfma(z, Tsh[lane][l], Gsh[l][j]);
+      const double2 t = cmul(tj, z);
+      Tsh[lane][j] = make_double2(-t.x, -t.y);
+    } else if (lane == j) {
+      Tsh[j][j] = tj;
+    }
+  };
+  auto csync = [&]() {
+    if constexpr (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
 
-  for (int e = tid; e < nbp * K; e += kPanelThreads) {
-    const int a = e / K, i = e % K;
-    Ps[e] = A[(size_t)(k0 + a) * lda + k0 + i];
+  for (int e = tid; e < nbp * Kl; e += NT) {
+    const int a = e / Kl, i = row_of(e % Kl);
+    Ps[e] = i < K ? A[(size_t)(k0 + a) * lda + k0 + i] : make_double2(0.0, 0.0);
   }
-  for (int e = tid; e < kNB * (kNB + 1); e += kPanelThreads) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
+  for (int e = tid; e < kNB * (kNB + 1); e += NT) (&Tsh[0][0])[e] = make_double2(0.0, 0.0);
   __syncthreads();
+  if (C > 1 && rank == 0 && tid < nbp) rowbuf[0][tid] = Ps[tid * Kl];   // row 0 (slot 0)
 
   // partial sums for column 0: slot x holds P_{x+1}
   double2 part[kX];
@@ -275,18 +312,21 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   double xn2p = 0.0;
 #pragma unroll
   for (int x = 0; x < kX; ++x) part[x] = make_double2(0.0, 0.0);
-  for (int i = tid; i < K; i += kPanelThreads) {
+  for (int slot = tid; slot < Kl; slot += NT) {
+    const int i = row_of(slot);
+    if (i >= K) break;
     if (i == 0) continue;
-    const double2 xi = Ps[i];
+    const double2 xi = Ps[slot];
     xn2p = fma(xi.x, xi.x, fma(xi.y, xi.y, xn2p));
 #pragma unroll
     for (int x = 0; x < kX; ++x) {
       if (x + 1 >= nbp) break;
-      part[x] = cfma_conj(part[x], xi, Ps[(x + 1) * K + i]);
+      part[x] = cfma_conj(part[x], xi, Ps[(x + 1) * Kl + slot]);
     }
   }
 
   for (int jj = 0; jj < nbp; ++jj) {
+    const int buf = kBuf > 1 ? (jj & 1) : 0;
     {
       // lane l ends with the warp sum of component l
       double v[32];
@@ -298,17 +338,34 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       }
       v[30] = xn2p;
       v[31] = 0.0;
-      red[warp][lane] = warp_reduce_scatter32(v);
+      red[buf][warp][lane] = warp_reduce_scatter32(v);
     }
-    __syncthreads();                                           // B1: partials of column jj
+    csync();                                                   // partials (and row jj) of column jj
+    if (warp == 1 && jj > 0) t_column(jj - 1);                 // beside warp 0's scalars
     if (warp == 0) {
       double s = 0.0;
 #pragma unroll
-      for (int w = 0; w < kW; ++w) s += red[w][lane];
+      for (int r = 0; r < C; ++r) {
+        const double *rr = &red[buf][0][0];
+        if constexpr (C > 1) rr = cg::this_cluster().map_shared_rank(rr, r);
+#pragma unroll
+        for (int w = 0; w < kW; ++w) s += rr[w * 32 + lane];
+      }
       tot[lane] = s;
+      // row jj: local shared memory (C = 1) or the owner's published copy
+      const int own = owner_of(jj);
+      const double2 *rowj;
+      int rstride;
+      if constexpr (C > 1) {
+        rowj = cg::this_cluster().map_shared_rank(&rowbuf[buf][0], own);
+        rstride = 1;
+      } else {
+        rowj = Ps + jj;
+        rstride = Kl;
+      }
       __syncwarp();
       const double xn2 = tot[30];
-      const double2 alpha = Ps[jj * K + jj];
+      const double2 alpha = rowj[jj * rstride];
       double beta;
       double2 tau, scale;
       if (xn2 == 0.0 && alpha.y == 0.0) {
@@ -316,9 +373,9 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       } else {
         // one reciprocal square root gives both |beta| and 1 / beta
         const double s2 = fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xn2));
-        const double r = rsqrt(s2);
-        beta = -copysign(s2 * r, alpha.x);
-        const double ib = -copysign(r, alpha.x);
+        const double rs = rsqrt(s2);
+        beta = -copysign(s2 * rs, alpha.x);
+        const double ib = -copysign(rs, alpha.x);
         tau = make_double2((beta - alpha.x) * ib, -alpha.y * ib);
         const double2 den = make_double2(alpha.x - beta, alpha.y);
         const double idd = 1.0 / (den.x * den.x + den.y * den.y);
@@ -327,21 +384,21 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       if (lane < kX) {
         const double2 val = make_double2(tot[2 * lane], tot[2 * lane + 1]);
         if (lane < jj) {
-          const double2 va = Ps[lane * K + jj];
+          const double2 va = rowj[lane * rstride];
           Gsh[lane][jj] = cfma(make_double2(va.x, -va.y), scale, val);      // conj(v_a[jj]) + scale Q_a
         } else if (lane + 1 < nbp) {
-          const double2 vh = cfma_conj(Ps[(lane + 1) * K + jj], scale, val);  // a_c[jj] + conj(scale) P_c
+          const double2 vh = cfma_conj(rowj[(lane + 1) * rstride], scale, val);  // a_c[jj] + conj(scale) P_c
           wsh[lane] = cjmul(tau, vh);
         }
       }
       if (lane == 0) {
-        Ps[jj * K + jj] = make_double2(beta, 0.0);
+        if (rank == own) Ps[jj * Kl + slot_of(jj)] = make_double2(beta, 0.0);
         taush[jj] = tau;
         sc_scale = scale;
-        if (!isfinite(beta)) atomicOr(o.status, kStatNonFinite);
+        if (rank == 0 && !isfinite(beta)) atomicOr(o.status, kStatNonFinite);
       }
     }
-    __syncthreads();                                           // B2: scalars of column jj
+    __syncthreads();                                           // scalars of column jj
     // Apply reflector jj to the owner's rows, scale v, and form the partial
     // sums of column jn = jj + 1 (slot x < jn: Q_x; x >= jn: P_{x+1}).
     const double2 scale = sc_scale;
@@ -358,24 +415,20 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
     qslot = jj;
     xn2p = 0.0;
     const double2 wj = jn < nbp ? wsh[jj] : make_double2(0.0, 0.0);   // column jn's coefficient
-    for (int i = tid; i < K; i += kPanelThreads) {
+    for (int slot = tid; slot < Kl; slot += NT) {
+      const int i = row_of(slot);
+      if (i >= K) break;
       if (i < jj) continue;
-      if (i == jj) {                                           // v_jj = 1 on row jj
-#pragma unroll
-        for (int x = kX - 1; x >= 0; --x) {
-          if (x < jj) break;
-          if (x + 1 >= nbp) continue;
-          double2 *y = Ps + (x + 1) * K + jj;
-          *y = make_double2(y->x - w[x].x, y->y - w[x].y);
-        }
-        continue;
-      }
-      const double2 v = cmul(Ps[jj * K + i], scale);
-      Ps[jj * K + i] = v;
+      // Row jj (v = 1) takes the same instruction path as the rows below it:
+      // a separate branch would add its FP64 instructions to the warp's count.
+      const bool diag = i == jj;
+      double2 v = cmul(Ps[jj * Kl + slot], scale);
+      if (diag) v = make_double2(1.0, 0.0);
+      else Ps[jj * Kl + slot] = v;
       if (jn >= nbp) continue;
       const bool acc = i > jn;
-      const double2 xn = cfms(Ps[jn * K + i], v, wj);
-      Ps[jn * K + i] = xn;
+      const double2 xn = cfms(Ps[jn * Kl + slot], v, wj);
+      Ps[jn * Kl + slot] = xn;
       if (acc) {
         xn2p = fma(xn.x, xn.x, fma(xn.y, xn.y, xn2p));
         qjj = cfma_conj(qjj, v, xn);
@@ -384,7 +437,7 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
       for (int x = kX - 1; x >= 0; --x) {                      // columns c = x + 1 > jn
         if (x < jn) break;
         if (x + 1 >= nbp) continue;
-        double2 *y = Ps + (x + 1) * K + i;
+        double2 *y = Ps + (x + 1) * Kl + slot;
         const double2 yn = cfms(*y, v, w[x]);
         *y = yn;
         if (acc) part[x] = cfma_conj(part[x], xn, yn);
@@ -393,34 +446,26 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
 #pragma unroll
         for (int x = 0; x < kX; ++x) {                         // Gram with earlier reflectors a < jj
           if (x >= jj) break;
-          part[x] = cfma_conj(part[x], Ps[x * K + i], xn);
+          part[x] = cfma_conj(part[x], Ps[x * Kl + slot], xn);
         }
       }
-    }
-  }
-  __syncthreads();
-  if (warp == 0) {
-    for (int j = 0; j < nbp; ++j) {
-      const double2 tj = taush[j];
-      if (lane < j) {
-        double2 z = make_double2(0.0, 0.0);
-        for (int l = lane; l < j; ++l) z = cfma(z, Tsh[lane][l], Gsh[l][j]);
-        const double2 t = cmul(tj, z);
-        Tsh[lane][j] = make_double2(-t.x, -t.y);
-      } else if (lane == j) {
-        Tsh[j][j] = tj;
+      if (C > 1 && i == jn) {                                  // publish row jn for its scalars
+        for (int c = 0; c < nbp; ++c) rowbuf[jn & 1][c] = Ps[c * Kl + slot];
       }
-      __syncwarp();
     }
   }
+  csync();        // no CTA leaves while another may still read its shared memory
+  if (warp == 1) t_column(nbp - 1);
   __syncthreads();
-  for (int e = tid; e < nbp * K; e += kPanelThreads) {
-    const int a = e / K, i = e % K;
-    A[(size_t)(k0 + a) * lda + k0 + i] = Ps[e];
+  for (int e = tid; e < nbp * Kl; e += NT) {
+    const int a = e / Kl, i = row_of(e % Kl);
+    if (i < K) A[(size_t)(k0 + a) * lda + k0 + i] = Ps[e];
   }
-  if (tid < nbp) o.tau[(size_t)d * o.cols + k0 + tid] = taush[tid];
-  double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  for (int e = tid; e < kNB * kNB; e += kPanelThreads) Tg[e] = Tsh[e % kNB][e / kNB];
+  if (rank == 0) {
+    if (tid < nbp) o.tau[(size_t)d * o.cols + k0 + tid] = taush[tid];
+    double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+    for (int e = tid; e < kNB * kNB; e += NT) Tg[e] = Tsh[e % kNB][e / kNB];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -678,28 +723,71 @@ point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__res
 
 }  // namespace
 
+namespace {
+
+template <int C>
+cudaError_t launch_panel_cluster(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                 int ntasks, int p, int max_panel_rows, cudaStream_t st) {
+  auto local_rows = [](int K) {
+    return C > 1 ? kPanelThreads * ((K + C * kPanelThreads - 1) / (C * kPanelThreads)) : K;
+  };
+  const size_t smem = sizeof(double2) * (size_t)kNB * local_rows(max_panel_rows);
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(qr_panel_smem_kernel<C>,
+                                      sizeof(double2) * (size_t)kNB * local_rows(kPanelSmemRows),
+                                      granted);
+  if (e != cudaSuccess) return e;
+  static const bool carve = (prefer_max_shared(qr_panel_smem_kernel<C>), true);
+  (void)carve;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntasks * C);
+  cfg.blockDim = dim3(kPanelThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = C > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, qr_panel_smem_kernel<C>, d_obs, d_task_obs, d_task_mode, p);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+// The panel is bound by the FP64 pipe of the SMs that factor it: when the
+// step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int max_panel_rows, int slices, cudaStream_t st) {
-  if (ntasks <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (max_panel_rows <= kPanelSmemRows) {
-    const size_t smem = sizeof(double2) * (size_t)kNB * max_panel_rows;
-    static size_t granted = 0;
-    e = ensure_dynamic_smem(qr_panel_smem_kernel, sizeof(double2) * (size_t)kNB * kPanelSmemRows,
-                            granted);
-    if (e != cudaSuccess) return e;
-    static const bool carve = (prefer_max_shared(qr_panel_smem_kernel), true);
-    (void)carve;
-    qr_panel_smem_kernel<<<ntasks, kPanelThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p);
-  } else {
-    qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
-  }
   (void)slices;
+  if (ntasks <= 0) return cudaSuccess;
+  if (max_panel_rows <= kPanelSmemRows) {
+    const int sms = sm_count();
+    if (4 * ntasks <= sms)
+      return launch_panel_cluster<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+    if (2 * ntasks <= sms)
+      return launch_panel_cluster<2>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+    return launch_panel_cluster<1>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+  }
+  qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   return cudaGetLastError();
 }
 
 // The next panel's kNB columns, in native FP64 with narrow tiles (two CTAs
-// per mode): this update is on the critical path of the factorisation.
+// per mode): this update is on the critical path of the factorisation, where
+// the split path would first need the panel's digits.
 cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int p, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
@@ -719,7 +807,7 @@ cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
     return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, kNB,
                                   (max_rest_cols + split_update_tile_cols() - 1) /
                                       split_update_tile_cols(),
-                                  st);
+                                  split_update_tile_cols(), st);
   static const bool carve = (prefer_max_shared(qr_update_kernel<kTN>), true);
   (void)carve;
   qr_update_kernel<kTN><<<dim3(ntasks, (max_rest_cols + kTN - 1) / kTN), kThreads, 0, st>>>(

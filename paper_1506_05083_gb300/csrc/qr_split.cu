@@ -8,8 +8,8 @@
 // products on BF16 mma.sync (ozaki.cuh) and T^H in FP64:
 //   digits  the panel's reflectors are split once per factorisation
 //           (panel_digits_kernel) into V^H digits (exponent per reflector)
-//           and V row digits (exponent per row), kept for every apply;
-//   pass 0  exponents of X's columns;
+//           and V row digits (exponent per row);
+//   pass 0  exponents of X's columns (carried from the previous step);
 //   pass 1  W = V^H X, contraction over the K rows in chunks of 32;
 //   pass 2  W' = T^H W (FP64), per-column exponents and digits of W';
 //   pass 3  X -= V W', contraction nb = 16 (one k16 step), FP64
@@ -162,6 +162,9 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       }
     }
   };
+  // ldmatrix lane roles: row (l mod 8) of matrix l / 8
+  const int lrow = lane & 7, lmat = lane >> 3;
+  const int a_row = lrow + 8 * (lmat & 1), a_k = 8 * (lmat >> 1);
   long long whi[2][4] = {}, wlo[2][4] = {};
   stage(k0);
   for (int r0 = k0; r0 < rows; r0 += kKC) {
@@ -183,28 +186,39 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     }
     __syncthreads();
     if (r0 + kKC < rows) stage(r0 + kKC);
-#pragma unroll 1
-    for (int g = 2; g <= S + 1; ++g) {
-      float are[4] = {0, 0, 0, 0}, aim[4] = {0, 0, 0, 0};
-#pragma unroll 1
-      for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
-        const int t = g - s;
+    // All S groups accumulate at once (independent accumulators): digit s of
+    // V^H is loaded once, then every digit t of X with s + t <= S + 1.
+    float acc[S][2][4];
 #pragma unroll
-        for (int kk = 0; kk < kKC; kk += 16) {
-          uint32_t ar[4], ai[4], br[2], bi[2];
-          oz::load_a(&sm.u.p1.A[s - 1][0][0][kk], kLD1, lane, ar);
-          oz::load_a(&sm.u.p1.A[s - 1][1][0][kk], kLD1, lane, ai);
-          oz::load_b(&sm.u.p1.B[t - 1][0][8 * warp][kk], kLD1, lane, br);
-          oz::load_b(&sm.u.p1.B[t - 1][1][8 * warp][kk], kLD1, lane, bi);
-          oz::cmma(are, aim, ar, ai, br, bi);
-        }
+    for (int g = 0; g < S; ++g)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[g][0][q] = acc[g][1][q] = 0.0f;
+#pragma unroll
+    for (int s = 1; s <= S; ++s) {
+      uint32_t ar0[4], ar1[4], ai0[4], ai1[4];
+      oz::ldsm_x4(ar0, &sm.u.p1.A[s - 1][0][a_row][a_k]);
+      oz::ldsm_x4(ar1, &sm.u.p1.A[s - 1][0][a_row][16 + a_k]);
+      oz::ldsm_x4(ai0, &sm.u.p1.A[s - 1][1][a_row][a_k]);
+      oz::ldsm_x4(ai1, &sm.u.p1.A[s - 1][1][a_row][16 + a_k]);
+#pragma unroll
+      for (int t = 1; t <= S + 1 - s; ++t) {
+        uint32_t br[4], bi[4];
+        oz::ldsm_x4(br, &sm.u.p1.B[t - 1][0][8 * warp + lrow][8 * lmat]);
+        oz::ldsm_x4(bi, &sm.u.p1.B[t - 1][1][8 * warp + lrow][8 * lmat]);
+        const uint32_t br0[2] = {br[0], br[1]}, bi0[2] = {bi[0], bi[1]};
+        const uint32_t br1[2] = {br[2], br[3]}, bi1[2] = {bi[2], bi[3]};
+        oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar0, ai0, br0, bi0);
+        oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar1, ai1, br1, bi1);
       }
-      // group sums here reach ~4.5e6 (sign-magnitude X digits up to 127):
-      // exact in FP32 but beyond the magic-number range, so convert directly
+    }
+    // group sums here reach ~4.5e6 (sign-magnitude X digits up to 127):
+    // exact in FP32 but beyond the magic-number range, so convert directly
+#pragma unroll
+    for (int g = 2; g <= S + 1; ++g)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const long long vr = (long long)__float2int_rn(are[q]);
-        const long long vi = (long long)__float2int_rn(aim[q]);
+        const long long vr = (long long)__float2int_rn(acc[g - 2][0][q]);
+        const long long vi = (long long)__float2int_rn(acc[g - 2][1][q]);
         if (g <= 4) {
           whi[0][q] += vr << (7 * (4 - g));
           whi[1][q] += vi << (7 * (4 - g));
@@ -213,7 +227,6 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           wlo[1][q] += vi << (7 * (S + 1 - g));
         }
       }
-    }
   }
   // c-fragment element q: row grp (+8 for q >= 2), column 8w + 2 tig + (q & 1)
 #pragma unroll
@@ -261,11 +274,10 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     oz::split_store<S>(w.y, sm.eW[j], &sm.u.p3.B[0][1][j][a], 2 * kTN * kLD2);
   }
 
-  // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk,
-  // the 32 target columns in two halves of 16 (two n8 fragments each). The
-  // X values of a half are loaded before its slice products run.
+  // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk
+  // and the 32 target columns as four n8 tiles. For each tile all S groups
+  // accumulate at once; the tile's X values are loaded before its products.
   const int knext = k0 + kNB;
-  unsigned long long cmax0[2][2] = {}, cmax1[2][2] = {};     // halves 0/1: [fragment][q & 1]
   for (int r0 = k0; r0 < rows; r0 += kRC) {
     __syncthreads();
     const int rr0 = r0 - k0;
@@ -281,93 +293,87 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     __syncthreads();
     if (r0 + 16 * warp >= rows) continue;
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      double2 xv[2][4];
+    for (int nt = 0; nt < kTN / 8; ++nt) {
+      double2 xv[4];
 #pragma unroll
-      for (int f = 0; f < 2; ++f)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = r0 + 16 * warp + grp + (q >= 2 ? 8 : 0);
-          const int j = 16 * h + 8 * f + 2 * tig + (q & 1);
-          xv[f][q] = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
-        }
-      long long yhi[2][2][4] = {}, ylo[2][2][4] = {};     // [part][fragment][element]
-#pragma unroll 1
-      for (int g = 2; g <= S + 1; ++g) {
-        float are[2][4] = {}, aim[2][4] = {};
-#pragma unroll 1
-        for (int s = (g - S > 1 ? g - S : 1); s <= (g - 1 < S ? g - 1 : S); ++s) {
-          const int t = g - s;
-          uint32_t ar[4], ai[4];
-          oz::load_a(&sm.u.p3.A[s - 1][0][16 * warp][0], kLD2, lane, ar);
-          oz::load_a(&sm.u.p3.A[s - 1][1][16 * warp][0], kLD2, lane, ai);
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            uint32_t br[2], bi[2];
-            oz::load_b(&sm.u.p3.B[t - 1][0][16 * h + 8 * f][0], kLD2, lane, br);
-            oz::load_b(&sm.u.p3.B[t - 1][1][16 * h + 8 * f][0], kLD2, lane, bi);
-            oz::cmma(are[f], aim[f], ar, ai, br, bi);
-          }
-        }
-#pragma unroll
-        for (int f = 0; f < 2; ++f)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            oz::fold_group<S>(yhi[0][f][q], ylo[0][f][q], g, are[f][q]);
-            oz::fold_group<S>(yhi[1][f][q], ylo[1][f][q], g, aim[f][q]);
-          }
+      for (int q = 0; q < 4; ++q) {
+        const int i = r0 + 16 * warp + grp + (q >= 2 ? 8 : 0);
+        const int j = 8 * nt + 2 * tig + (q & 1);
+        xv[q] = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
       }
+      float acc[S][2][4];
 #pragma unroll
-      for (int f = 0; f < 2; ++f)
+      for (int g = 0; g < S; ++g)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[g][0][q] = acc[g][1][q] = 0.0f;
+#pragma unroll
+      for (int s = 1; s <= S; ++s) {
+        uint32_t ar[4], ai[4];
+        oz::ldsm_x4(ar, &sm.u.p3.A[s - 1][0][16 * warp + a_row][a_k]);
+        oz::ldsm_x4(ai, &sm.u.p3.A[s - 1][1][16 * warp + a_row][a_k]);
+#pragma unroll
+        for (int t = 1; t <= S + 1 - s; ++t) {
+          uint32_t b[4];                    // re k0-7, re k8-15, im k0-7, im k8-15
+          oz::ldsm_x4(b, &sm.u.p3.B[t - 1][lmat >> 1][8 * nt + lrow][8 * (lmat & 1)]);
+          const uint32_t br[2] = {b[0], b[1]}, bi[2] = {b[2], b[3]};
+          oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar, ai, br, bi);
+        }
+      }
+      long long yhi[2][4] = {}, ylo[2][4] = {};
+#pragma unroll
+      for (int g = 2; g <= S + 1; ++g)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
-          const int i = r0 + r, j = 16 * h + 8 * f + 2 * tig + (q & 1);
-          if (i < rows && j < ncols) {
-            const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
-            double2 v = xv[f][q];
-            v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][f][q], ylo[0][f][q]), e);
-            v.y -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[1][f][q], ylo[1][f][q]), e);
-            X[(size_t)j * ldx + i] = v;
-            if (i >= knext) {
-              const unsigned long long k = key2(v);
-              if (h == 0) cmax0[f][q & 1] = k > cmax0[f][q & 1] ? k : cmax0[f][q & 1];
-              else cmax1[f][q & 1] = k > cmax1[f][q & 1] ? k : cmax1[f][q & 1];
-            }
+          oz::fold_group<S>(yhi[0][q], ylo[0][q], g, acc[g - 2][0][q]);
+          oz::fold_group<S>(yhi[1][q], ylo[1][q], g, acc[g - 2][1][q]);
+        }
+      unsigned long long cm[2] = {0ull, 0ull};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
+        const int i = r0 + r, j = 8 * nt + 2 * tig + (q & 1);
+        if (i < rows && j < ncols) {
+          const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
+          double2 v = xv[q];
+          v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][q], ylo[0][q]), e);
+          v.y -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[1][q], ylo[1][q]), e);
+          X[(size_t)j * ldx + i] = v;
+          if (i >= knext) {
+            const unsigned long long k = key2(v);
+            cm[q & 1] = k > cm[q & 1] ? k : cm[q & 1];
           }
         }
-    }
-  }
-  // column keys over rows >= k0 + kNB: lanes with the same tig share columns
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int f = 0; f < 2; ++f)
+      }
+      // column keys over rows >= k0 + kNB: lanes with the same tig share columns
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        unsigned long long m = h == 0 ? cmax0[f][c] : cmax1[f][c];
+        unsigned long long m = cm[c];
 #pragma unroll
         for (int o = 4; o < 32; o <<= 1) {
           const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
           m = w > m ? w : m;
         }
-        if (grp == 0 && m != 0ull) atomicMax(&sm.kNext[16 * h + 8 * f + 2 * tig + c], m);
+        if (grp == 0 && m != 0ull) atomicMax(&sm.kNext[8 * nt + 2 * tig + c], m);
       }
+    }
+  }
   __syncthreads();
   if (kout != nullptr && tid < ncols) kout[tid] = sm.kNext[tid];
 }
 
+// Three CTAs' worth of registers per SM (at most 170 each): two trailing-
+// update CTAs then leave room for a panel CTA on the same SM.
 template <int S>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                       const int *__restrict__ task_mode, int p, int col_off) {
+                       const int *__restrict__ task_mode, int p, int col_off, int max_cols) {
   const ObsDev &o = obs[task_obs[blockIdx.x]];
   const int d = task_mode[blockIdx.x];
   const int k0 = p * kNB;
   const int nbp = min(kNB, o.cols - k0);
   const int c0 = k0 + nbp + col_off + blockIdx.y * kTN;
   if (c0 >= o.cols) return;
-  const int ncols = min(kTN, o.cols - c0);
+  const int ncols = min(min(kTN, max_cols), o.cols - c0);
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
@@ -476,15 +482,16 @@ cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const in
 
 template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int col_off, int ntiles, cudaStream_t st) {
+                            int ntasks, int p, int col_off, int ntiles, int max_cols,
+                            cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
   static const bool carve = (prefer_max_shared(qr_update_split_kernel<S>), true);
   (void)carve;
-  qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(d_obs, d_task_obs,
-                                                                           d_task_mode, p, col_off);
+  qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(
+      d_obs, d_task_obs, d_task_mode, p, col_off, max_cols);
   return cudaGetLastError();
 }
 
@@ -508,6 +515,27 @@ cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, in
 
 bool split_slices_supported(int s) { return s >= 4 && s <= 8; }
 
+
+int split_update_tile_cols() { return kTN; }
+
+cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
+                                   const int *d_task_mode, int ntasks, int p, int slices,
+                                   int col_off, int ntiles, int max_cols, cudaStream_t st) {
+  switch (slices) {
+    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
+                                          max_cols, st);
+    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
+                                          max_cols, st);
+    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
+                                          max_cols, st);
+    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
+                                          max_cols, st);
+    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
+                                          max_cols, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                                 int ntasks, int p, int slices, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
@@ -518,21 +546,6 @@ cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, cons
     case 6: return launch_digits_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
     case 7: return launch_digits_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
     case 8: return launch_digits_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-int split_update_tile_cols() { return kTN; }
-
-cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
-                                   const int *d_task_mode, int ntasks, int p, int slices,
-                                   int col_off, int ntiles, cudaStream_t st) {
-  switch (slices) {
-    case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
-    case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
-    case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
-    case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
-    case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles, st);
     default: return cudaErrorInvalidValue;
   }
 }
