@@ -59,7 +59,13 @@ axi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AXI_OK : AXI_E
 // position of output k after the in-place decimation-in-frequency FFT,
 //   pos(k) = (k mod r1) (n / r1) + pos'(k div r1).
 // Returns the number of stages, 0 if n has other prime factors.
-int fft_plan(int n, int *rad_out, std::vector<int> &perm) {
+// Radices of n (4s, then 2, 3, 5) and the output positions of the in-place
+// DIF FFT. With `needed` > 0 (only outputs n < needed are read), the largest
+// radix r with n / r >= needed is moved to the last stage and *sum_last is
+// set: every needed output is then output 0 of a last-stage block, i.e. the
+// plain sum of the block's r entries, and that stage need not run.
+int fft_plan(int n, int *rad_out, std::vector<int> &perm, int needed = 0,
+             int *sum_last = nullptr) {
   std::vector<int> rad;
   int m = n;
   while (m % 4 == 0) { rad.push_back(4); m /= 4; }
@@ -67,7 +73,19 @@ int fft_plan(int n, int *rad_out, std::vector<int> &perm) {
   while (m % 3 == 0) { rad.push_back(3); m /= 3; }
   while (m % 5 == 0) { rad.push_back(5); m /= 5; }
   perm.assign(n, 0);
+  if (sum_last) *sum_last = 0;
   if (m != 1 || rad.size() > 8) return 0;
+  if (sum_last && needed > 0 && rad.size() > 1) {
+    int best = -1;
+    for (size_t s = 0; s < rad.size(); ++s)
+      if (n / rad[s] >= needed && (best < 0 || rad[s] > rad[best])) best = (int)s;
+    if (best >= 0) {
+      const int r = rad[best];
+      rad.erase(rad.begin() + best);
+      rad.push_back(r);
+      *sum_last = 1;
+    }
+  }
   for (size_t s = 0; s < rad.size(); ++s) rad_out[s] = rad[s];
   std::vector<int> cur(1, 0);
   int len = 1;
@@ -181,7 +199,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     // radices 4, 2, 3, 5 and output permutations for the FFTs of length P
     // (apply) and q (fill)
     d.fft_nst = fft_plan(o.P, d.fft_rad, h.fft_perm);
-    d.fft_nst_q = fft_plan(o.q, d.fft_rad_q, h.fft_perm_q);
+    d.fft_nst_q = fft_plan(o.q, d.fft_rad_q, h.fft_perm_q, d.D, &d.fft_sum_last_q);
     h.tw_q.resize(o.q);
     for (int r = 0; r < o.q; ++r)
       h.tw_q[r] = make_double2(std::cos(2.0 * kPi * r / o.q), -std::sin(2.0 * kPi * r / o.q));

@@ -52,6 +52,7 @@ struct ObsDev {
   int fft_rad[8];
   const int *fft_perm;    // [P] position of output n after the in-place FFT
   int fft_nst_q;          // radices of q for the fill's FFT (0: direct cosine sums)
+  int fft_sum_last_q;     // 1: the needed modes are sums over the last stage's blocks
   int fft_rad_q[8];
   const int *fft_perm_q;  // [q]
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}

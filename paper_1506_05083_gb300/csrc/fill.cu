@@ -184,7 +184,10 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
     if (l > 0 && l < half) seq[q - l] = s;
   }
   __syncthreads();                                          // tables and sequences ready
-  fft::warp_fft(seq, q, tw, o.fft_rad_q, o.fft_nst_q, lane);
+  // With fft_sum_last_q the last stage is not run: each needed mode is the
+  // sum of its last-stage block (twiddle 1, output 0).
+  const int rl = o.fft_sum_last_q ? o.fft_rad_q[o.fft_nst_q - 1] : 1;
+  fft::warp_fft(seq, q, tw, o.fft_rad_q, o.fft_nst_q - (rl > 1 ? 1 : 0), lane);
   if (m >= o.M) return;
   int row = m, col = j;
   double sign = 1.0;
@@ -197,7 +200,9 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
   double2 *dst = out + (size_t)col * ld_rows + row;
   bool bad = false;
   for (int n = lane; n < D; n += 32) {
-    const double2 v0 = seq[perm[n]];
+    const double2 *blk = seq + perm[n];
+    double2 v0 = blk[0];
+    for (int k = 1; k < rl; ++k) v0 = make_double2(v0.x + blk[k].x, v0.y + blk[k].y);
     const double2 v = make_double2(sign * v0.x, sign * v0.y);
     bad |= !isfinite(v.x) || !isfinite(v.y);
     dst[n * mode_stride] = v;
