@@ -38,6 +38,10 @@ import synth  # noqa: E402
 
 METRIC = "operator build time (FP64-equiv TFLOP/s), per-wave apply us at 1e-10 rel err"
 FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_probe_gb300.md)
+# DRAM bytes (read + write) of one fill_fft_kernel launch on the smooth-body
+# workload, from the ncu capture in profiles/fill_fft_smooth_k10_N180_M216_P120.md;
+# None until that capture is taken of the current kernel.
+FILL_TRAFFIC_BYTES = 100608
 
 
 def workload():
@@ -52,12 +56,42 @@ def algorithmic_flops(M, N, P, W):
     return qr, apply
 
 
-def fill_flops(M, N, P, q):
-    """Algorithmic FP64 flops of the folded cosine transform of the fill:
-    4 flops (two FMAs on a complex sample) per (pair, node, mode);
-    the sample evaluations (sqrt, sincos, division) are not counted."""
+# FP64 issue slots (one slot = one DFMA) of the fill kernel's arithmetic, from
+# its source: per ring sample rsqrt (8.2 slots, measured) + sincos (30.6,
+# measured) + the products around them (14 for the normal derivative, 6 for
+# the value kernel); per FFT butterfly the adds, multiplies and twiddle
+# products of fft.cuh (radix 2: 8, 3: 22, 4: 28, 5: 52); the pruned last
+# stage costs 2 (r - 1) per needed mode.
+SLOTS_SAMPLE = {"deriv": 8.2 + 30.6 + 14.0, "value": 8.2 + 30.6 + 6.0}
+SLOTS_BUTTERFLY = {2: 8, 3: 22, 4: 28, 5: 52}
+
+
+def fill_fft_plan(q, D):
+    """Radices of the fill's FFT (same rule as the library's plan): 4s, 2, 3,
+    5, with the largest radix r with q / r >= D moved last and replaced by
+    block sums."""
+    rad, m = [], q
+    for r in (4, 2, 3, 5):
+        while m % r == 0:
+            rad.append(r)
+            m //= r
+    last = None
+    cands = [i for i, r in enumerate(rad) if q // r >= D]
+    if cands and len(rad) > 1:
+        i = max(cands, key=lambda i: rad[i])
+        last = rad.pop(i)
+    return rad, last
+
+
+def fill_slots(M, N, P, q, bc_kinds):
+    """FP64 slots per fill launch: pairs x ((q/2+1) samples + one pruned FFT).
+    bc_kinds lists the sample kinds per pair ("deriv" or "value")."""
     D = P // 2 + 1
-    return 4.0 * M * N * (q // 2 + 1) * D
+    rad, last = fill_fft_plan(q, D)
+    fft = sum(SLOTS_BUTTERFLY[r] * (q // r) for r in rad)
+    fft += 2 * (last - 1) * D if last else 0
+    per_pair = sum((q // 2 + 1) * SLOTS_SAMPLE[k] + fft for k in bc_kinds)
+    return M * N * per_pair
 
 
 class ClockSampler:
@@ -303,11 +337,16 @@ def main():
     h2d = dirs_host.numel() * 8
     d2h = coef_host.numel() * 16
 
-    fl_fill = fill_flops(ob.M, ob.N, ob.P, spec.q)
-    ach = fl_fill / (fill_ms * 1e-3) / 1e12
+    kinds = ["deriv"] if ob.bc == synth.BC_NEUMANN else ["value", "deriv", "value", "deriv"]
+    slots = fill_slots(ob.M, ob.N, ob.P, spec.q, kinds)
+    ach = 2.0 * slots / (fill_ms * 1e-3) / 1e12          # one slot = one FMA = 2 flops
     npanels = (spec.cols + 15) // 16
-    # fill + (panel, update) per panel step (no update after the last) + incident + 5 apply kernels
-    launches_per_step = 1 + npanels + (npanels - 1) + 1 + 5
+    n_next = sum(1 for p in range(npanels) if spec.cols - 16 * (p + 1) > 0)
+    n_rest = sum(1 for p in range(npanels) if spec.cols - 16 * (p + 2) > 0)
+    # fill + panels + next-panel updates + trailing updates (+ their digit
+    # kernels in split precision) + incident + 5 apply kernels
+    launches_per_step = (1 + npanels + n_next + n_rest * (2 if args.prec == "split" else 1)
+                         + 1 + 5)
     torch.cuda.synchronize()
     status = op.status()
     if rank == 0:
@@ -323,10 +362,13 @@ def main():
             "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
             "e2e": {"value": ws * (qr_fl + ap_fl) / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"kernel": "fill_kernel", "bound": "alu", "achieved": ach,
+            "roofline": {"kernel": "fill_fft_kernel", "bound": "alu", "achieved": ach,
                          "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "FP64 DFMA probe (MEASURED_PEAKS.json has no FP64 entry)",
+                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": FILL_TRAFFIC_BYTES,
+                         "work": "FP64 issue slots of the kernel's arithmetic x 2 flops "
+                                 f"({slots:.4g} slots per launch)",
+                         "peak_source": "FP64 DFMA probe of measured (MEASURED_PEAKS.json has "
+                                        "no FP64 entry)",
                          "kernel_ms": fill_ms},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
