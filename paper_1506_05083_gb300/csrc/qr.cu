@@ -591,6 +591,7 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   __shared__ double2 Rb[kTB][kTB + 1];
   __shared__ double2 Yb[kTB][kTS + 1];
+  __shared__ double rinv[kTB];              // 1 / R_ii of the block (real diagonal)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + kTB - 1) / kTB;
   for (int ib = nblk - 1; ib >= 0; --ib) {
@@ -604,13 +605,16 @@ trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_to
       const int r = e % kTB, c = e / kTB;
       Yb[r][c] = (r < nb && c < ncols) ? Xd[(size_t)c * ld + r0 + r] : make_double2(0.0, 0.0);
     }
+    // the block's reciprocals in one parallel division (a division per
+    // elimination step would sit on every warp's sequential chain)
+    if (tid < kTB) rinv[tid] = tid < nb ? 1.0 / R[(size_t)(r0 + tid) * ld + r0 + tid].x : 0.0;
     __syncthreads();
     for (int c = warp; c < ncols; c += kThreads / 32) {
       double2 y = Yb[lane][c];
       for (int rr = nb - 1; rr >= 0; --rr) {
         double2 x = make_double2(0.0, 0.0);
         if (lane == rr) {
-          const double inv = 1.0 / Rb[rr][rr].x;  // real diagonal (beta of the reflector)
+          const double inv = rinv[rr];            // real diagonal (beta of the reflector)
           y = make_double2(y.x * inv, y.y * inv);
           x = y;
         }
