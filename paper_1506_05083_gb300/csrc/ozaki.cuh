@@ -114,12 +114,15 @@ __device__ __forceinline__ void split_store_n(double x, int e, int S, unsigned s
 }
 
 // Faster digits for an operand that is split on every use (the trailing
-// matrix in the QR update): sign-magnitude digits u_s = (m >> 7(S-s)) & 127 of
-// m = round(|x| 2^{7S - e}), with one bit of headroom in e (|x| < 2^{e-1}) so
-// m < 2^{7S-1} and u_1 <= 64. Rounding happens once, at the last digit, so the
-// digit errors stay unbiased. BF16 bits of u come from a magic-number add
-// (2^23 + u is exact in FP32). Two values (consecutive rows) are packed per
-// 32-bit word: low half x0, high half x1.
+// matrix in the QR update). m = round(|x| 2^{7S - e}) with one bit of
+// headroom in e (|x| < 2^{e-1}, so m <= 2^{7S-1}); the signed value is
+// offset by K = 64 (1 + 2^7 + ... + 2^{7(S-1)}) so that a = K +- m >= 0 and
+// its base-128 fields f_s give balanced digits d_s = f_s - 64 without a
+// carry chain: d_s in [-64, 63], the top field left unmasked so d_1 <= 65.
+// Rounding happens once, at the last digit, so digit errors stay unbiased.
+// BF16 bits of d come from one FP32 add: (2^23 + f) - (2^23 + 64) is exact.
+// Two values (consecutive rows) are packed per 32-bit word: low half x0,
+// high half x1.
 __device__ __forceinline__ unsigned long long mag_fixed(double x, int e, int S7, unsigned &sign) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   sign = (unsigned)(b >> 63);
@@ -132,21 +135,24 @@ __device__ __forceinline__ unsigned long long mag_fixed(double x, int e, int S7,
   if (sh > -60) return (M + (1ull << (-sh - 1))) >> (-sh);
   return 0;
 }
-__device__ __forceinline__ unsigned bf16_bits_u7(unsigned u) {
-  return __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388608.0f) >> 16;
+__device__ __forceinline__ unsigned bf16_bits_bal(unsigned f) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | f) - 8388672.0f) >> 16;
 }
 template <int S>
 __device__ __forceinline__ void split2_fast(double x0, double x1, int e, uint32_t *dst,
                                             int stride_words) {
+  unsigned long long K = 0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) K = (K << 7) | 64ull;
   unsigned s0, s1;
   const unsigned long long m0 = mag_fixed(x0, e, 7 * S, s0), m1 = mag_fixed(x1, e, 7 * S, s1);
+  const unsigned long long a0 = s0 ? K - m0 : K + m0, a1 = s1 ? K - m1 : K + m1;
 #pragma unroll
   for (int s = 1; s <= S; ++s) {
-    const unsigned u0 = (unsigned)(m0 >> (7 * (S - s))) & 127u;
-    const unsigned u1 = (unsigned)(m1 >> (7 * (S - s))) & 127u;
-    const unsigned b0 = bf16_bits_u7(u0) | (u0 ? s0 << 15 : 0u);
-    const unsigned b1 = bf16_bits_u7(u1) | (u1 ? s1 << 15 : 0u);
-    dst[(s - 1) * stride_words] = b0 | (b1 << 16);
+    const unsigned mask = s == 1 ? 0xffffu : 127u;
+    const unsigned f0 = (unsigned)(a0 >> (7 * (S - s))) & mask;
+    const unsigned f1 = (unsigned)(a1 >> (7 * (S - s))) & mask;
+    dst[(s - 1) * stride_words] = bf16_bits_bal(f0) | (bf16_bits_bal(f1) << 16);
   }
 }
 

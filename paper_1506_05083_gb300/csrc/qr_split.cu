@@ -211,8 +211,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar1, ai1, br1, bi1);
       }
     }
-    // group sums here reach ~4.5e6 (sign-magnitude X digits up to 127):
-    // exact in FP32 but beyond the magic-number range, so convert directly
+    // group sums: at most 7 pairs x 2 products x 32 rows x 128 x 65 < 2^22,
+    // exact integers in FP32
 #pragma unroll
     for (int g = 2; g <= S + 1; ++g)
 #pragma unroll
