@@ -21,6 +21,7 @@ BC_NEUMANN, BC_TRANSMISSION = 0, 1
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
 SHAPE_POLAR, SHAPE_CUP = 0, 1
 EVAL_POTENTIAL, EVAL_NORMAL_DERIV, EVAL_FAR_FIELD = 0, 1, 2
+OK, ERR_ARG, ERR_SHAPE = 0, -1, -2              # axi_status values (include/axi_mfs.h)
 
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p

@@ -284,6 +284,8 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   const int slices = p->obs[0].dev.slices;
+  int kp_max = 0;
+  for (const auto &ob : p->obs) kp_max = ob.dev.kp > kp_max ? ob.dev.kp : kp_max;
   bool rest_pending = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
@@ -305,7 +307,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     if (rest_cols > 0) {
       if (slices > 0) {
         e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
-                                     op->side);
+                                     kp_max, op->side);
         if (e != cudaSuccess) return AXI_ERR_CUDA;
       }
       e = axi::launch_qr_update_rest(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,

@@ -105,8 +105,9 @@ size_t apply_digit_bytes(const ObsDev &h);
 // panel would cost more than it saves).
 constexpr int kSplitApplyMinWaves = 33;
 bool split_slices_supported(int slices);
+// kp_max: the largest digit row stride (kp) over the tasks of the launch
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                                int ntasks, int panel, int slices, cudaStream_t st);
+                                int ntasks, int panel, int slices, int kp_max, cudaStream_t st);
 cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
                             double2 *f, cudaStream_t st);
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,

@@ -472,7 +472,10 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
 template <int S>
 cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st) {
-  const size_t smem = sizeof(int) * (kNB + kp_max);
+  const size_t smem = sizeof(int) * (kNB + kp_max);     // exponents of the tallest task
+  static size_t granted = 0;
+  const cudaError_t e = ensure_dynamic_smem(panel_digits_kernel<S>, smem, granted);
+  if (e != cudaSuccess) return e;
   static const bool carve = (prefer_max_shared(panel_digits_kernel<S>), true);
   (void)carve;
   panel_digits_kernel<S><<<ntasks, 256, smem, st>>>(d_obs, d_task_obs, d_task_mode, p, nullptr,
@@ -498,9 +501,12 @@ cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const in
 template <int S>
 cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                               unsigned short *dig, int *dex, cudaStream_t st) {
+  static size_t granted_d = 0;
+  cudaError_t e = ensure_dynamic_smem(panel_digits_kernel<S>, sizeof(int) * (kNB + h.kp), granted_d);
+  if (e != cudaSuccess) return e;
   panel_digits_kernel<S><<<dim3(h.D, h.npanels), 256, sizeof(int) * (kNB + h.kp), st>>>(
       d_o, nullptr, nullptr, 0, dig, dex);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(OzSmem<S>);
   static size_t granted = 0;
@@ -537,9 +543,8 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
 }
 
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                                int ntasks, int p, int slices, cudaStream_t st) {
+                                int ntasks, int p, int slices, int kp_max, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
-  const int kp_max = kPanelSmemRows + 64;   // >= any kp (rows <= 2 * M, rounded up)
   switch (slices) {
     case 4: return launch_digits_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
     case 5: return launch_digits_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, kp_max, st);
