@@ -474,8 +474,6 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
 // ---------------------------------------------------------------------------
 template <int TN>
 struct BrSmem {
-  double2 V[kRC][kNB + 1];
-  double2 X[kRC][TN + 1];
   double2 W[kNB][TN + 1];
   double2 T[kNB][kNB + 1];
 };
@@ -489,21 +487,16 @@ __device__ void apply_block_reflector_h(const double2 *__restrict__ A, int lda, 
   const int tid = threadIdx.x;
   const int ta = tid / TN, tc = tid % TN;
   for (int e = tid; e < kNB * kNB; e += NT) sm.T[e % kNB][e / kNB] = Tg[e];
+  // W(ta, tc) = v_ta^H x_tc straight from global memory (L1-cached; no
+  // block barriers in the loop): v is 1 at row k0 + ta and zero above it.
   double2 w = make_double2(0.0, 0.0);
-  for (int r0 = k0; r0 < rows; r0 += kRC) {
-    __syncthreads();
-    for (int e = tid; e < kRC * kNB; e += NT) {
-      const int r = e % kRC, a = e / kRC;
-      sm.V[r][a] = vget(A, lda, rows, k0, nbp, r0 + r, a);
-    }
-    for (int e = tid; e < kRC * TN; e += NT) {
-      const int r = e % kRC, c = e / kRC;
-      const int i = r0 + r;
-      sm.X[r][c] = (i < rows && c < ncols) ? X[(size_t)c * ldx + i] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int r = 0; r < kRC; ++r) w = cfma_conj(w, sm.V[r][ta], sm.X[r][tc]);
+  if (ta < nbp && tc < ncols) {
+    const int c = k0 + ta;
+    const double2 *va = A + (size_t)c * lda;
+    const double2 *xc = X + (size_t)tc * ldx;
+    w = xc[c];
+#pragma unroll 4
+    for (int r = c + 1; r < rows; ++r) w = cfma_conj(w, va[r], xc[r]);
   }
   sm.W[ta][tc] = w;
   __syncthreads();
