@@ -41,7 +41,7 @@ FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_
 # DRAM bytes (read + write) of one fill_fft_kernel launch on the smooth-body
 # workload, from the ncu capture in profiles/fill_fft_smooth_k10_N180_M216_P120.md;
 # None until that capture is taken of the current kernel.
-FILL_TRAFFIC_BYTES = 100608
+FILL_TRAFFIC_BYTES = None
 
 
 def workload():
@@ -57,12 +57,12 @@ def algorithmic_flops(M, N, P, W):
 
 
 # FP64 issue slots (one slot = one DFMA) of the fill kernel's arithmetic, from
-# its source: per ring sample rsqrt (8.2 slots, measured) + sincos (30.6,
-# measured) + the products around them (14 for the normal derivative, 6 for
-# the value kernel); per FFT butterfly the adds, multiplies and twiddle
-# products of fft.cuh (radix 2: 8, 3: 22, 4: 28, 5: 52); the pruned last
-# stage costs 2 (r - 1) per needed mode.
-SLOTS_SAMPLE = {"deriv": 8.2 + 30.6 + 14.0, "value": 8.2 + 30.6 + 6.0}
+# its source: per ring sample rsqrt (8.2 slots, measured) + the ring sin/cos
+# of trig.cuh (23 operations) + the products around them (14 for the normal
+# derivative, 6 for the value kernel); per FFT butterfly the adds, multiplies
+# and twiddle products of fft.cuh (radix 2: 8, 3: 22, 4: 28, 5: 52); the
+# pruned last stage costs 2 (r - 1) per needed mode.
+SLOTS_SAMPLE = {"deriv": 8.2 + 23.0 + 14.0, "value": 8.2 + 23.0 + 6.0}
 SLOTS_BUTTERFLY = {2: 8, 3: 22, 4: 28, 5: 52}
 
 

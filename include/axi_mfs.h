@@ -315,6 +315,14 @@ axi_status axi_plan_destroy(axi_plan *plan);
 /* Static description of a status code. */
 const char *axi_status_string(int32_t s);
 
+/* axi_diag_sincos -- diagnostics, not a step of the method (the paper has no
+ * counterpart): evaluates at n device doubles d_x the sin/cos routine the
+ * ring-kernel samples use (Cody-Waite reduction and Taylor series, valid for
+ * |x| < 2^20), writing d_sin[i], d_cos[i]. Lets a caller or a test compare it
+ * with CUDA's sincos. Asynchronous on `stream`; AXI_ERR_ARG for n < 0 or
+ * missing pointers; n = 0 does nothing. */
+axi_status axi_diag_sincos(const double *d_x, int32_t n, double *d_sin, double *d_cos, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

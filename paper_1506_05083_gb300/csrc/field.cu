@@ -10,6 +10,7 @@
 // over the eight phased nearest images, the action A_else of Sec. 4.2 done by
 // direct summation instead of an FMM.
 #include "axi_internal.h"
+#include "trig.cuh"
 
 namespace axi {
 namespace {
@@ -112,7 +113,7 @@ eval_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__ si
         const double R = sqrt(dx * dx + dy * dy + dz * dz);
         const double inv = 1.0 / R;
         double sn, cs;
-        sincos(k * R, &sn, &cs);
+        trig::sincos_ring(k * R, &sn, &cs);
         if (kind == AXI_EVAL_POTENTIAL) {
           kv = make_double2(cs * inv * kInv4Pi, sn * inv * kInv4Pi);
         } else {

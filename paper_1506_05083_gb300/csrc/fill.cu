@@ -17,6 +17,7 @@
 // Arithmetic is native FP64 throughout (the ill-conditioned MFS matrices need
 // the full precision); the kernel is bound by the FP64 pipe.
 #include "axi_internal.h"
+#include "trig.cuh"
 #include "fft.cuh"
 
 namespace axi {
@@ -79,7 +80,7 @@ fill_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict__ ou
         const double inv = rsqrt(R2);
         const double R = R2 * inv;
         double sn, cs;
-        sincos(k * R, &sn, &cs);
+        trig::sincos_ring(k * R, &sn, &cs);
         const double w = ((l == 0 || l == half) ? 1.0 : 2.0) * wq;
         if (!deriv) {
           s = make_double2(cs * inv * w, sn * inv * w);
@@ -171,7 +172,7 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
     const double inv = rsqrt(R2);
     const double R = R2 * inv;
     double sn, cs;
-    sincos(k * R, &sn, &cs);
+    trig::sincos_ring(k * R, &sn, &cs);
     double2 s;
     if (!deriv) {
       s = make_double2(cs * inv * wq, sn * inv * wq);

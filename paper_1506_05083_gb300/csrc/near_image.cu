@@ -25,6 +25,7 @@
 // complex component then stays below 256 * 2 * 7 * 2^12 < 2^24, an exact FP32
 // integer converted with __float2int_rn.
 #include "axi_internal.h"
+#include "trig.cuh"
 #include "ozaki.cuh"
 
 namespace axi {
@@ -110,7 +111,7 @@ near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, 
     const double inv = rsqrt(R2);
     const double R = R2 * inv;
     double sn, cs;
-    sincos(g.k * R, &sn, &cs);
+    trig::sincos_ring(g.k * R, &sn, &cs);
     const double f = (nx * dx + ny * dy + nz * dz) * inv * inv * inv * kInv4Pi, kR = g.k * R;
     kv = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));   // (ikR - 1) e^{ikR}
   }
