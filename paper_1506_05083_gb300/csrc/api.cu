@@ -25,13 +25,59 @@ struct ObsHost {
   std::vector<double2> tw_q;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
   size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
+  std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
+  std::vector<int> fill_cex;               // and row exponents [2 MR]
+  size_t off_fcdig = 0, off_fcex = 0;
 };
+
+// Digits of the folded cosine table of the split fill (fill_mma.cu): row
+// r < 2 MR holds mode n = 2 (r mod MR) + r / MR, entries w_l cos(2 pi n l / q)
+// for l < L (w_0 = 1, else 2), zero elsewhere; balanced base-128 digits of
+// round(x 2^{7S - e}) with e the row's exponent (|x| < 2^e).
+void fill_cos_digits(ObsHost &h, int S) {
+  const ObsDev &d = h.dev;
+  const int q = d.q, rows = 2 * d.fill_MR, Lp = d.fill_Lp, L = d.fill_L;
+  h.fill_cdig.assign((size_t)S * rows * Lp, 0);
+  h.fill_cex.assign(rows, 0);
+  std::vector<double> v(L);
+  for (int r = 0; r < rows; ++r) {
+    const int n = 2 * (r % d.fill_MR) + r / d.fill_MR;
+    if (n >= d.D) continue;
+    double mx = 0.0;
+    for (int l = 0; l < L; ++l) {
+      v[l] = (l == 0 ? 1.0 : 2.0) * h.tab_cos[(size_t)n * l % q];
+      if ((n & 1) && 2 * l == q / 2) v[l] = 0.0;          // cos(pi n / 2) = 0 for odd n
+      mx = std::max(mx, std::fabs(v[l]));
+    }
+    if (mx == 0.0) continue;
+    const int e = std::ilogb(mx) + 1;
+    h.fill_cex[r] = e;
+    for (int l = 0; l < L; ++l) {
+      long long m = std::llround(std::ldexp(v[l], 7 * S - e));
+      for (int s = S; s >= 1; --s) {
+        int dg;
+        if (s > 1) {
+          dg = (int)(m & 127);
+          if (dg >= 64) dg -= 128;
+          m = (m - dg) / 128;
+        } else {
+          dg = (int)m;
+        }
+        const float f = (float)dg;
+        uint32_t b;
+        std::memcpy(&b, &f, sizeof(b));
+        h.fill_cdig[((size_t)(s - 1) * rows + r) * Lp + l] = (unsigned short)(b >> 16);
+      }
+    }
+  }
+}
 
 }  // namespace
 
 struct axi_plan_s {
   std::vector<ObsHost> obs;
   int prec = 0;
+  size_t off_fgdig = 0, off_fgex = 0;     // split fill: sample-digit scratch (shared)
   std::vector<int> task_obs, task_mode;   // sorted by obstacle panel count, descending
   std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
   std::vector<int> step_cols;             // widest trailing matrix at step p
@@ -171,6 +217,7 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
   p->off_task_obs = off; off = align_up(off + sizeof(int) * ntask);
   p->off_task_mode = off; off = align_up(off + sizeof(int) * ntask);
   p->off_status = off; off = align_up(off + sizeof(int));
+  size_t fill_gdig_bytes = 0, fill_gex_bytes = 0;
   for (int i = 0; i < n_obs; ++i) {
     const axi_obstacle &o = obs[i];
     ObsHost &h = p->obs[i];
@@ -222,7 +269,25 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 4 * slices * axi::kNB * d.kp);
       h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * 2 * (axi::kNB + d.kp));
       h.off_ckey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * d.cols);
+      // split fill: folded length, padding, cos-table digits, pair chunk
+      const int hh = d.q / 2;
+      d.fill_L = (hh % 2 == 0) ? hh / 2 + 1 : (hh + 1) / 2;
+      d.fill_Lp = (d.fill_L + 31) / 32 * 32;
+      d.fill_MR = ((d.D + 1) / 2 + 15) / 16 * 16;
+      const int kinds = o.bc == AXI_BC_TRANSMISSION ? 4 : 1;
+      const size_t per_pair = (size_t)2 * 2 * kinds * axi::kFillDigits * d.fill_Lp * sizeof(unsigned short);
+      const size_t cap = (size_t)512 << 20;
+      d.fill_chunk_pairs = (int)std::max<size_t>(8, std::min<size_t>((size_t)o.M * o.N, cap / per_pair));
+      fill_gdig_bytes = std::max(fill_gdig_bytes, per_pair * d.fill_chunk_pairs);
+      fill_gex_bytes = std::max(fill_gex_bytes, sizeof(int) * 2 * 2 * kinds * (size_t)d.fill_chunk_pairs);
+      fill_cos_digits(h, axi::kFillDigits);
+      h.off_fcdig = off; off = align_up(off + sizeof(unsigned short) * h.fill_cdig.size());
+      h.off_fcex = off; off = align_up(off + sizeof(int) * h.fill_cex.size());
     }
+  }
+  if (fill_gdig_bytes > 0) {
+    p->off_fgdig = off; off = align_up(off + fill_gdig_bytes);
+    p->off_fgex = off; off = align_up(off + fill_gex_bytes);
   }
   p->bytes = off;
   // QR task list: (obstacle, mode), obstacles with more panels first so the
@@ -347,6 +412,12 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.vdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_vdig) : nullptr;
     d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
     d.ckey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ckey) : nullptr;
+    if (d.slices > 0) {
+      d.fill_cdig = reinterpret_cast<const unsigned short *>(ws + h.off_fcdig);
+      d.fill_cex = reinterpret_cast<const int *>(ws + h.off_fcex);
+      d.fill_gdig = reinterpret_cast<uint32_t *>(ws + plan->off_fgdig);
+      d.fill_gex = reinterpret_cast<int *>(ws + plan->off_fgex);
+    }
     d.status = reinterpret_cast<int *>(ws + plan->off_status);
     devs[i] = d;
     struct { size_t off; const void *src; size_t n; } cp[] = {
@@ -359,6 +430,8 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
         {h.off_perm_q, h.fft_perm_q.data(), sizeof(int) * h.fft_perm_q.size()},
         {h.off_tw_q, h.tw_q.data(), sizeof(double2) * h.tw_q.size()},
+        {h.off_fcdig, h.fill_cdig.data(), sizeof(unsigned short) * h.fill_cdig.size()},
+        {h.off_fcex, h.fill_cex.data(), sizeof(int) * h.fill_cex.size()},
     };
     for (auto &c : cp) {
       if (!c.n) continue;

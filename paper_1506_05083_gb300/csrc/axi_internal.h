@@ -11,6 +11,7 @@ namespace axi {
 constexpr int kNB = 16;        // Householder panel width (columns per block reflector)
 constexpr int kMaxModes = 128; // D = P/2 + 1 <= 128, i.e. P <= 254
 constexpr int kMaxP = 254;
+constexpr int kFillDigits = 8;        // digits of the split fill transform (both operands)
 constexpr int kPanelSmemRows = 864;  // panels up to this many rows are factored in shared memory
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
@@ -48,6 +49,15 @@ struct ObsDev {
   // update and read by the next (alternating slots), so the trailing matrix
   // is not scanned for its exponents at every step.
   unsigned long long *ckey;
+  // split precision only: the fill's transform as a digit GEMM (fill_mma.cu).
+  // Folded length L, padded Lp (multiple of 32), MR rows per parity part;
+  // cos-table digits [kFillDigits][2 MR][Lp] and row exponents [2 MR];
+  // sample-digit scratch for fill_chunk_pairs ring pairs at a time.
+  int fill_L, fill_Lp, fill_MR, fill_chunk_pairs;
+  const unsigned short *fill_cdig;
+  const int *fill_cex;
+  uint32_t *fill_gdig;
+  int *fill_gex;
   int fft_nst;            // radices of P for the apply's FFTs (0: P has other prime factors)
   int fft_rad[8];
   const int *fft_perm;    // [P] position of output n after the in-place FFT
@@ -82,6 +92,10 @@ inline cudaError_t ensure_dynamic_smem(Kernel *kernel, size_t bytes, size_t &gra
 }
 
 // Launch wrappers (each returns the cudaError_t of its launch).
+// fill_mma.cu: the split-precision transform of the fill
+cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out,
+                            int ld_rows, int ld_cols, cudaStream_t st);
+size_t fill_gemm_smem(int MR);
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,

@@ -1,0 +1,308 @@
+// Step A2 in split precision: the modal transform of the fill as a digit GEMM
+// on BF16 tensor cores (plans with AXI_PREC_SPLIT_BF16).
+//
+// The q/2 + 1 ring samples g_l of each (m, j) pair are even in l (Sec. 3.1,
+// eq. ptr), so with h = q/2
+//   A_n = g_0 + (-1)^n g_h + 2 sum_{0<l<h} g_l cos(pi n l / h)     (1/q, 1/4pi in g).
+// Pairing l with h - l (cos(pi n (h - l)/h) = (-1)^n cos(pi n l/h)) folds it to
+//   A_n = sum_{l<L} w_l cos(pi n l / h) u_l,   u = e (n even), o (n odd),
+//   e_l = g_l + g_{h-l},  o_l = g_l - g_{h-l}  (l < h/2),  e_{h/2} = g_{h/2},
+// w_0 = 1, w_l = 2 otherwise; L = h/2 + 1 (h even) or (h + 1)/2 (h odd).
+// That is two real GEMMs per plan: [cos table of the even modes] x [e of every
+// pair, real and imaginary part as separate columns], likewise odd/o.
+//
+//   fill_samples_kernel  one warp per (pair, kind): FP64 samples, the fold,
+//                        per-column exponents and S = 8 balanced digits of
+//                        e and o (split2_fast), written to a scratch buffer;
+//   fill_gemm_kernel     CTA tile = all modes x NT real columns; the cos
+//                        table's digits (computed once per plan on the host)
+//                        and the sample digits are staged per 32-row chunk of
+//                        the contraction; every digit pair s + t <= 9 on BF16
+//                        mma.sync, FP32 group sums folded into int64 every
+//                        128 products (a group sums at most 8 pairs x 128 x
+//                        65 x 128 < 2^24: exact), doubles rebuilt with integer
+//                        instructions, written into the modal matrices.
+// The samples keep the FP64 pipe busy; the transform (the FFT's half of the
+// FP64 work) moves to the tensor pipe.
+#include "axi_internal.h"
+#include "ozaki.cuh"
+#include "trig.cuh"
+
+namespace axi {
+namespace {
+
+constexpr double kInv4Pi = 0.07957747154594766788;
+constexpr int kFS = kFillDigits;          // digits of both operands (8)
+constexpr int kFKC = 32;                  // contraction rows per staged chunk
+constexpr int kFLD = kFKC + 8;            // padded k stride in shared memory (bf16)
+constexpr int kFWarpsA = 8;               // pairs per CTA in the sample kernel
+constexpr int kFThreadsB = 512;           // 16 warps in the GEMM kernel
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Sample kernel. gdig: [2 parts][cols2][kFS][Lp] BF16 bit patterns, read as
+// 32-bit words (two k per word); gex: [2 parts][cols2] exponents (one bit of
+// headroom, as split2_fast wants). Column c2 = 2 (pair_local * kinds + kind)
+// + (0 re, 1 im).
+__global__ void __launch_bounds__(256)
+fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
+                    uint32_t *__restrict__ gdig, int *__restrict__ gex) {
+  const ObsDev &o = obs_arr[oi];
+  const int q = o.q, h = q / 2, L = o.fill_L, Lp = o.fill_Lp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ double2 fseq[];
+  double2 *seq = fseq + (size_t)warp * (h + 1);
+  const int pl = blockIdx.x * kFWarpsA + warp;
+  if (pl >= npairs) return;                       // whole warp; no block barriers below
+  const int kind = blockIdx.y;
+  const int p = pair0 + pl;
+  const int m = p / o.N, j = p % o.N;
+  const bool deriv = (o.bc == AXI_BC_NEUMANN) ? true : (kind & 1);
+  const bool ext = (o.bc == AXI_BC_TRANSMISSION) && kind >= 2;
+  const double k = ext ? o.km : o.k;
+  const double *Sp = ext ? o.srcx : o.src;
+  const double rs = Sp[2 * j], zs = Sp[2 * j + 1];
+  const double rho = o.coll[4 * m], z = o.coll[4 * m + 1];
+  const double nr = o.coll[4 * m + 2], nz = o.coll[4 * m + 3];
+  const double dr = rho - rs, dz = z - zs;
+  const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
+  const double wq = kInv4Pi / q;
+  for (int l = lane; l <= h; l += 32) {
+    const double R2 = base + fourrr * o.tab_s2[l];
+    const double inv = rsqrt(R2);
+    const double R = R2 * inv;
+    double sn, cs;
+    trig::sincos_ring(k * R, &sn, &cs);
+    double2 s;
+    if (!deriv) {
+      s = make_double2(cs * inv * wq, sn * inv * wq);
+    } else {
+      const double ndot = nr * (rho - rs * o.tab_cos[l]) + nz * dz;
+      const double f = ndot * inv * inv * inv * wq, kR = k * R;
+      s = make_double2(f * (-cs - kR * sn), f * (-sn + kR * cs));
+    }
+    seq[l] = s;
+  }
+  __syncwarp();
+  // fold in place: e_l at l, o_l at h - l (l < h/2); the middle e_{h/2} stays
+  const bool mid = (h & 1) == 0;
+  for (int l = lane; l < L; l += 32) {
+    if (mid && l == h / 2) continue;
+    const double2 a = seq[l], b = seq[h - l];
+    seq[l] = make_double2(a.x + b.x, a.y + b.y);
+    seq[h - l] = make_double2(a.x - b.x, a.y - b.y);
+  }
+  __syncwarp();
+  auto eval = [&](int l) { return l < L ? seq[l] : make_double2(0.0, 0.0); };
+  auto oval = [&](int l) {
+    return (l < L && !(mid && l == h / 2)) ? seq[h - l] : make_double2(0.0, 0.0);
+  };
+  unsigned long long ke_r = 0, ke_i = 0, ko_r = 0, ko_i = 0;
+  for (int l = lane; l < L; l += 32) {
+    const double2 e = eval(l), od = oval(l);
+    ke_r = max(ke_r, oz::abs_key(e.x));
+    ke_i = max(ke_i, oz::abs_key(e.y));
+    ko_r = max(ko_r, oz::abs_key(od.x));
+    ko_i = max(ko_i, oz::abs_key(od.y));
+  }
+  ke_r = warp_max_u64(ke_r);
+  ke_i = warp_max_u64(ke_i);
+  ko_r = warp_max_u64(ko_r);
+  ko_i = warp_max_u64(ko_i);
+  const int xe_r = oz::key_exponent(ke_r) + 1, xe_i = oz::key_exponent(ke_i) + 1;
+  const int xo_r = oz::key_exponent(ko_r) + 1, xo_i = oz::key_exponent(ko_i) + 1;
+  const size_t cols2 = (size_t)npairs * kinds * 2;
+  const size_t c2 = 2 * ((size_t)pl * kinds + kind);
+  if (lane == 0) {
+    gex[c2] = xe_r;
+    gex[c2 + 1] = xe_i;
+    gex[cols2 + c2] = xo_r;
+    gex[cols2 + c2 + 1] = xo_i;
+  }
+  const int wpr = Lp / 2;                                  // words per digit row
+  uint32_t *de_r = gdig + (c2 * kFS) * wpr;
+  uint32_t *de_i = gdig + ((c2 + 1) * kFS) * wpr;
+  uint32_t *do_r = gdig + ((cols2 + c2) * kFS) * wpr;
+  uint32_t *do_i = gdig + ((cols2 + c2 + 1) * kFS) * wpr;
+  for (int w = lane; w < wpr; w += 32) {
+    const double2 e0 = eval(2 * w), e1 = eval(2 * w + 1);
+    const double2 o0 = oval(2 * w), o1 = oval(2 * w + 1);
+    oz::split2_fast<kFS>(e0.x, e1.x, xe_r, de_r + w, wpr);
+    oz::split2_fast<kFS>(e0.y, e1.y, xe_i, de_i + w, wpr);
+    oz::split2_fast<kFS>(o0.x, o1.x, xo_r, do_r + w, wpr);
+    oz::split2_fast<kFS>(o0.y, o1.y, xo_i, do_i + w, wpr);
+  }
+}
+
+// GEMM kernel. Rows: 2 MR (MR even-mode rows, then MR odd-mode rows; mode
+// n = 2 r' + part, rows with n >= D are zero). Columns: NT real columns per
+// CTA. Warp w < MT * NT / 8 computes the 16 x 8 tile (w / (NT/8), w % (NT/8)).
+__global__ void __launch_bounds__(kFThreadsB)
+fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
+                 int NT, const uint32_t *__restrict__ gdig, const int *__restrict__ gex,
+                 double2 *__restrict__ out, int ld_rows, int ld_cols) {
+  const ObsDev &o = obs_arr[oi];
+  const int Lp = o.fill_Lp, MR = o.fill_MR, D = o.D;
+  const int rows = 2 * MR, MT = rows / 16, nt8 = NT / 8;
+  const int cols2 = npairs * kinds * 2;
+  const int c0 = blockIdx.x * NT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = lane >> 2, tig = lane & 3;
+  const int lrow = lane & 7, lmat = lane >> 3;
+  const int a_row = lrow + 8 * (lmat & 1), a_k = 8 * (lmat >> 1);
+  extern __shared__ __align__(16) unsigned char fgs[];
+  // digit-major layouts: consecutive rows (columns) 80 bytes apart, so the
+  // eight rows of every ldmatrix 8x8 matrix fall in distinct bank groups
+  __nv_bfloat16 *Cs = reinterpret_cast<__nv_bfloat16 *>(fgs);            // [kFS][rows][kFLD]
+  __nv_bfloat16 *Gs = Cs + (size_t)rows * kFS * kFLD;                     // [2][kFS][NT][kFLD]
+  const bool active = warp < MT * nt8;
+  const int mt = active ? warp / nt8 : 0, nt = active ? warp % nt8 : 0;
+  const int part = (mt * 16) / MR;
+  float acc[kFS][4];
+  long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int g = 0; g < kFS; ++g)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[g][e] = 0.0f;
+  const int nchunks = Lp / kFKC;
+  const int wpr = Lp / 2;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    __syncthreads();
+    // cos-table digits of 8 digits x rows x 32 k: four 16-byte pieces per (digit, row)
+    for (int e = tid; e < rows * kFS * 4; e += kFThreadsB) {
+      const int u = e & 3, sr = e >> 2;                     // sr = s * rows + row
+      const uint4 v = *reinterpret_cast<const uint4 *>(o.fill_cdig + (size_t)sr * Lp + ch * kFKC + 8 * u);
+      *reinterpret_cast<uint4 *>(Cs + (size_t)sr * kFLD + 8 * u) = v;
+    }
+    // sample digits of 2 parts x NT columns x 8 digits x 32 k
+    for (int e = tid; e < 2 * NT * kFS * 4; e += kFThreadsB) {
+      const int u = e & 3, r = e >> 2;                      // r = (pt * kFS + s) * NT + c
+      const int c = r % NT, s = (r / NT) % kFS, pt = r / (kFS * NT);
+      const int col = c0 + c;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (col < cols2)
+        v = *reinterpret_cast<const uint4 *>(gdig + (((size_t)pt * cols2 + col) * kFS + s) * wpr +
+                                             ch * (kFKC / 2) + 4 * u);
+      *reinterpret_cast<uint4 *>(Gs + (size_t)r * kFLD + 8 * u) = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int kk = 0; kk < kFKC; kk += 16) {
+        // digits t = 1..8 of the warp's 8 columns: two digits per ldmatrix.x4
+        uint32_t b[kFS][2];
+#pragma unroll
+        for (int t = 0; t < kFS; t += 2) {
+          uint32_t r4[4];
+          const int col = nt * 8 + lrow, dg = t + (lmat >> 1), kq = kk + 8 * (lmat & 1);
+          oz::ldsm_x4(r4, Gs + (((size_t)part * kFS + dg) * NT + col) * kFLD + kq);
+          b[t][0] = r4[0];
+          b[t][1] = r4[1];
+          b[t + 1][0] = r4[2];
+          b[t + 1][1] = r4[3];
+        }
+#pragma unroll
+        for (int s = 1; s <= kFS; ++s) {
+          uint32_t a[4];
+          oz::ldsm_x4(a, Cs + ((size_t)(s - 1) * rows + mt * 16 + a_row) * kFLD + kk + a_k);
+#pragma unroll
+          for (int t = 1; t <= kFS + 1 - s; ++t)
+            oz::mma16816(acc[s + t - 2], a[0], a[1], a[2], a[3], b[t - 1][0], b[t - 1][1]);
+        }
+      }
+    }
+    // fold every 4 chunks (128 products per group pair) and at the end
+    if (active && (((ch + 1) & 3) == 0 || ch == nchunks - 1)) {
+#pragma unroll
+      for (int g = 2; g <= kFS + 1; ++g)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long v = (long long)__float2int_rn(acc[g - 2][e]);
+          if (g <= 4) hi[e] += v << (7 * (4 - g));
+          else lo[e] += v << (7 * (kFS + 1 - g));
+          acc[g - 2][e] = 0.0f;
+        }
+    }
+  }
+  if (!active) return;
+  // c-fragment element e: row grp (+8 for e >= 2), column 2 tig + (e & 1):
+  // the (re, im) pair of one complex column
+  bool bad = false;
+  const size_t mode_stride = (size_t)ld_cols * ld_rows;
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    const int row = mt * 16 + grp + 8 * hf;
+    const int n = 2 * (row % MR) + row / MR;
+    const int colc = c0 + nt * 8 + 2 * tig;                 // real column of the real part
+    if (n >= D || colc >= cols2) continue;
+    const int ce = o.fill_cex[row];
+    double vv[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int e = 2 * hf + c;
+      const int E = ce + gex[(size_t)part * cols2 + colc + c];
+      vv[c] = oz::scaled_to_double(hi[e], E - 28) + oz::scaled_to_double(lo[e], E - 7 * (kFS + 1));
+    }
+    const int cp = colc / 2, kind = cp % kinds, pl = cp / kinds;
+    const int p = pair0 + pl, m = p / o.N, j = p % o.N;
+    int orow = m, ocol = j;
+    double sign = 1.0;
+    if (o.bc == AXI_BC_TRANSMISSION) {
+      const bool ext = kind >= 2;
+      orow += (kind & 1) ? o.M : 0;
+      ocol += ext ? o.N : 0;
+      sign = ext ? -1.0 : 1.0;
+    }
+    const double2 v = make_double2(sign * vv[0], sign * vv[1]);
+    bad |= !isfinite(v.x) || !isfinite(v.y);
+    out[(size_t)n * mode_stride + (size_t)ocol * ld_rows + orow] = v;
+  }
+  if (bad) atomicOr(o.status, kStatNonFinite);
+}
+
+}  // namespace
+
+int fill_gemm_cols(int MR) {
+  const int mt = 2 * MR / 16;
+  return 8 * (16 / mt);
+}
+
+size_t fill_gemm_smem(int MR) {
+  return sizeof(__nv_bfloat16) * kFS * kFLD * ((size_t)2 * MR + 2 * (size_t)fill_gemm_cols(MR));
+}
+
+cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out,
+                            int ld_rows, int ld_cols, cudaStream_t st) {
+  const int kinds = h.bc == AXI_BC_TRANSMISSION ? 4 : 1;
+  const int npairs_total = h.M * h.N;
+  const int NT = fill_gemm_cols(h.fill_MR);
+  const size_t smemA = sizeof(double2) * (size_t)kFWarpsA * (h.q / 2 + 1);
+  const size_t smemB = fill_gemm_smem(h.fill_MR);
+  static size_t grantedA = 0, grantedB = 0;
+  cudaError_t e = ensure_dynamic_smem(fill_samples_kernel, smemA, grantedA);
+  if (e != cudaSuccess) return e;
+  e = ensure_dynamic_smem(fill_gemm_kernel, smemB, grantedB);
+  if (e != cudaSuccess) return e;
+  for (int pair0 = 0; pair0 < npairs_total; pair0 += h.fill_chunk_pairs) {
+    const int np = min(h.fill_chunk_pairs, npairs_total - pair0);
+    fill_samples_kernel<<<dim3((np + kFWarpsA - 1) / kFWarpsA, kinds), 32 * kFWarpsA, smemA, st>>>(
+        d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int cols2 = np * kinds * 2;
+    fill_gemm_kernel<<<(cols2 + NT - 1) / NT, kFThreadsB, smemB, st>>>(
+        d_obs, oi, pair0, np, kinds, NT, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace axi

@@ -24,6 +24,18 @@ def _op(name, slices):
     return axi, axi.Operator([spec], prec=prec), (wl, ob, geo, A, fac)
 
 
+@pytest.mark.parametrize("name", ["small", "small_trans", "sphere", "medium", "smooth"])
+def test_split_fill_parity(name):
+    """Split plans fill with the tensor-core transform (8 digits, fill_mma.cu):
+    same bar as the FP64 fill, e_A <= 1e-13 against the oracle's direct sums."""
+    axi, op, (wl, ob, geo, A, fac) = _op(name, 7)
+    Ag = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    err = np.abs(Ag - A).max() / np.abs(A).max()
+    assert err < 1e-13, err
+
+
 @pytest.mark.parametrize("name", ["medium", "small_trans"])
 def test_split_qr_invariants(name):
     axi, op, (wl, ob, geo, A, fac) = _op(name, 7)
