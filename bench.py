@@ -58,11 +58,11 @@ def algorithmic_flops(M, N, P, W):
 
 # FP64 issue slots (one slot = one DFMA) of the fill kernel's arithmetic, from
 # its source: per ring sample rsqrt (8.2 slots, measured) + the ring sin/cos
-# of trig.cuh (23 operations) + the products around them (14 for the normal
+# of trig.cuh (23 operations) + the products around them (11 for the normal
 # derivative, 6 for the value kernel); per FFT butterfly the adds, multiplies
 # and twiddle products of fft.cuh (radix 2: 8, 3: 22, 4: 28, 5: 52); the
 # pruned last stage costs 2 (r - 1) per needed mode.
-SLOTS_SAMPLE = {"deriv": 8.2 + 23.0 + 14.0, "value": 8.2 + 23.0 + 6.0}
+SLOTS_SAMPLE = {"deriv": 8.2 + 23.0 + 11.0, "value": 8.2 + 23.0 + 6.0}
 SLOTS_BUTTERFLY = {2: 8, 3: 22, 4: 28, 5: 52}
 
 
@@ -83,14 +83,21 @@ def fill_fft_plan(q, D):
     return rad, last
 
 
-def fill_slots(M, N, P, q, bc_kinds):
-    """FP64 slots per fill launch: pairs x ((q/2+1) samples + one pruned FFT).
-    bc_kinds lists the sample kinds per pair ("deriv" or "value")."""
+def fill_slots(M, N, P, q, bc_kinds, split):
+    """FP64 slots per fill: pairs x ((q/2+1) samples + the transform).
+    bc_kinds lists the sample kinds per pair ("deriv" or "value"). Native FP64
+    plans transform with the pruned FFT; split plans fold the samples (4 adds
+    per folded node) and run the transform on tensor cores (no FP64 slots)."""
     D = P // 2 + 1
-    rad, last = fill_fft_plan(q, D)
-    fft = sum(SLOTS_BUTTERFLY[r] * (q // r) for r in rad)
-    fft += 2 * (last - 1) * D if last else 0
-    per_pair = sum((q // 2 + 1) * SLOTS_SAMPLE[k] + fft for k in bc_kinds)
+    h = q // 2
+    if split:
+        L = h // 2 + 1 if h % 2 == 0 else (h + 1) // 2
+        per_kind = 4.0 * L
+    else:
+        rad, last = fill_fft_plan(q, D)
+        per_kind = sum(SLOTS_BUTTERFLY[r] * (q // r) for r in rad)
+        per_kind += 2 * (last - 1) * D if last else 0
+    per_pair = sum((h + 1) * SLOTS_SAMPLE[k] + per_kind for k in bc_kinds)
     return M * N * per_pair
 
 
@@ -338,7 +345,7 @@ def main():
     d2h = coef_host.numel() * 16
 
     kinds = ["deriv"] if ob.bc == synth.BC_NEUMANN else ["value", "deriv", "value", "deriv"]
-    slots = fill_slots(ob.M, ob.N, ob.P, spec.q, kinds)
+    slots = fill_slots(ob.M, ob.N, ob.P, spec.q, kinds, args.prec == "split")
     ach = 2.0 * slots / (fill_ms * 1e-3) / 1e12          # one slot = one FMA = 2 flops
     npanels = (spec.cols + 15) // 16
     n_next = sum(1 for p in range(npanels) if spec.cols - 16 * (p + 1) > 0)
@@ -362,7 +369,10 @@ def main():
             "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
             "e2e": {"value": ws * (qr_fl + ap_fl) / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"kernel": "fill_fft_kernel", "bound": "alu", "achieved": ach,
+            "roofline": {"kernel": ("fill_samples_kernel + fill_gemm_kernel (FP64 samples, "
+                                    "tensor-core transform)") if args.prec == "split"
+                                   else "fill_fft_kernel",
+                         "bound": "alu", "achieved": ach,
                          "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": FILL_TRAFFIC_BYTES,
                          "work": "FP64 issue slots of the kernel's arithmetic x 2 flops "

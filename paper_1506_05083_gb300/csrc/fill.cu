@@ -167,19 +167,21 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
   const double dr = rho - rs, dz = z - zs;
   const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
   const double wq = kInv4Pi / q;
+  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with 1/(4 pi q) folded in
+  const double an = (nr * rho + nz * dz) * wq, bn = nr * rs * wq;
   for (int l = lane; l <= half; l += 32) {
-    const double R2 = base + fourrr * o.tab_s2[l];
+    const double R2 = fma(fourrr, o.tab_s2[l], base);
     const double inv = rsqrt(R2);
-    const double R = R2 * inv;
+    const double R = R2 * inv, kR = k * R;
     double sn, cs;
-    trig::sincos_ring(k * R, &sn, &cs);
+    trig::sincos_ring(kR, &sn, &cs);
     double2 s;
     if (!deriv) {
-      s = make_double2(cs * inv * wq, sn * inv * wq);
+      const double iw = inv * wq;
+      s = make_double2(cs * iw, sn * iw);
     } else {
-      const double ndot = nr * (rho - rs * o.tab_cos[l]) + nz * dz;
-      const double f = ndot * inv * inv * inv * wq, kR = k * R;
-      s = make_double2(f * (-cs - kR * sn), f * (-sn + kR * cs));
+      const double f = fma(-bn, o.tab_cos[l], an) * (inv * inv * inv);
+      s = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));
     }
     seq[l] = s;
     if (l > 0 && l < half) seq[q - l] = s;

@@ -74,19 +74,21 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   const double dr = rho - rs, dz = z - zs;
   const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
   const double wq = kInv4Pi / q;
+  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with 1/(4 pi q) folded in
+  const double an = (nr * rho + nz * dz) * wq, bn = nr * rs * wq;
   for (int l = lane; l <= h; l += 32) {
-    const double R2 = base + fourrr * o.tab_s2[l];
+    const double R2 = fma(fourrr, o.tab_s2[l], base);
     const double inv = rsqrt(R2);
-    const double R = R2 * inv;
+    const double R = R2 * inv, kR = k * R;
     double sn, cs;
-    trig::sincos_ring(k * R, &sn, &cs);
+    trig::sincos_ring(kR, &sn, &cs);
     double2 s;
     if (!deriv) {
-      s = make_double2(cs * inv * wq, sn * inv * wq);
+      const double iw = inv * wq;
+      s = make_double2(cs * iw, sn * iw);
     } else {
-      const double ndot = nr * (rho - rs * o.tab_cos[l]) + nz * dz;
-      const double f = ndot * inv * inv * inv * wq, kR = k * R;
-      s = make_double2(f * (-cs - kR * sn), f * (-sn + kR * cs));
+      const double f = fma(-bn, o.tab_cos[l], an) * (inv * inv * inv);
+      s = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));
     }
     seq[l] = s;
   }
@@ -160,8 +162,8 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
   extern __shared__ __align__(16) unsigned char fgs[];
   // digit-major layouts: consecutive rows (columns) 80 bytes apart, so the
   // eight rows of every ldmatrix 8x8 matrix fall in distinct bank groups
-  __nv_bfloat16 *Cs = reinterpret_cast<__nv_bfloat16 *>(fgs);            // [kFS][rows][kFLD]
-  __nv_bfloat16 *Gs = Cs + (size_t)rows * kFS * kFLD;                     // [2][kFS][NT][kFLD]
+  // two stages, each [kFS][rows][kFLD] cos-table digits then [2][kFS][NT][kFLD]
+  __nv_bfloat16 *Cs = reinterpret_cast<__nv_bfloat16 *>(fgs);
   const bool active = warp < MT * nt8;
   const int mt = active ? warp / nt8 : 0, nt = active ? warp % nt8 : 0;
   const int part = (mt * 16) / MR;
@@ -173,26 +175,39 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
     for (int e = 0; e < 4; ++e) acc[g][e] = 0.0f;
   const int nchunks = Lp / kFKC;
   const int wpr = Lp / 2;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    __syncthreads();
-    // cos-table digits of 8 digits x rows x 32 k: four 16-byte pieces per (digit, row)
+  const size_t stage_elems = (size_t)kFS * kFLD * (rows + 2 * NT);
+  // chunk ch of the cos-table digits ([kFS][rows][32 k]) and the sample digits
+  // ([2][kFS][NT][32 k]) into stage buffer b, as asynchronous 16-byte copies
+  auto stage = [&](int ch, int b) {
+    __nv_bfloat16 *cs = Cs + b * stage_elems;
+    __nv_bfloat16 *gs = cs + (size_t)rows * kFS * kFLD;
     for (int e = tid; e < rows * kFS * 4; e += kFThreadsB) {
       const int u = e & 3, sr = e >> 2;                     // sr = s * rows + row
-      const uint4 v = *reinterpret_cast<const uint4 *>(o.fill_cdig + (size_t)sr * Lp + ch * kFKC + 8 * u);
-      *reinterpret_cast<uint4 *>(Cs + (size_t)sr * kFLD + 8 * u) = v;
+      oz::cp_async16(cs + (size_t)sr * kFLD + 8 * u,
+                     o.fill_cdig + (size_t)sr * Lp + ch * kFKC + 8 * u, true);
     }
-    // sample digits of 2 parts x NT columns x 8 digits x 32 k
     for (int e = tid; e < 2 * NT * kFS * 4; e += kFThreadsB) {
       const int u = e & 3, r = e >> 2;                      // r = (pt * kFS + s) * NT + c
       const int c = r % NT, s = (r / NT) % kFS, pt = r / (kFS * NT);
       const int col = c0 + c;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (col < cols2)
-        v = *reinterpret_cast<const uint4 *>(gdig + (((size_t)pt * cols2 + col) * kFS + s) * wpr +
-                                             ch * (kFKC / 2) + 4 * u);
-      *reinterpret_cast<uint4 *>(Gs + (size_t)r * kFLD + 8 * u) = v;
+      const bool ok = col < cols2;
+      const uint32_t *src =
+          gdig + (((size_t)pt * cols2 + (ok ? col : 0)) * kFS + s) * wpr + ch * (kFKC / 2) + 4 * u;
+      oz::cp_async16(gs + (size_t)r * kFLD + 8 * u, src, ok);
     }
-    __syncthreads();
+    oz::cp_async_commit();
+  };
+  stage(0, 0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    if (ch + 1 < nchunks) {
+      stage(ch + 1, (ch + 1) & 1);
+      oz::cp_async_wait<1>();
+    } else {
+      oz::cp_async_wait<0>();
+    }
+    __syncthreads();                                        // chunk ch visible to all warps
+    const __nv_bfloat16 *Cc = Cs + (ch & 1) * stage_elems;
+    const __nv_bfloat16 *Gc = Cc + (size_t)rows * kFS * kFLD;
     if (active) {
 #pragma unroll
       for (int kk = 0; kk < kFKC; kk += 16) {
@@ -202,7 +217,7 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
         for (int t = 0; t < kFS; t += 2) {
           uint32_t r4[4];
           const int col = nt * 8 + lrow, dg = t + (lmat >> 1), kq = kk + 8 * (lmat & 1);
-          oz::ldsm_x4(r4, Gs + (((size_t)part * kFS + dg) * NT + col) * kFLD + kq);
+          oz::ldsm_x4(r4, Gc + (((size_t)part * kFS + dg) * NT + col) * kFLD + kq);
           b[t][0] = r4[0];
           b[t][1] = r4[1];
           b[t + 1][0] = r4[2];
@@ -211,13 +226,14 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
 #pragma unroll
         for (int s = 1; s <= kFS; ++s) {
           uint32_t a[4];
-          oz::ldsm_x4(a, Cs + ((size_t)(s - 1) * rows + mt * 16 + a_row) * kFLD + kk + a_k);
+          oz::ldsm_x4(a, Cc + ((size_t)(s - 1) * rows + mt * 16 + a_row) * kFLD + kk + a_k);
 #pragma unroll
           for (int t = 1; t <= kFS + 1 - s; ++t)
             oz::mma16816(acc[s + t - 2], a[0], a[1], a[2], a[3], b[t - 1][0], b[t - 1][1]);
         }
       }
     }
+    __syncthreads();                                        // buffer ch & 1 free for chunk ch + 2
     // fold every 4 chunks (128 products per group pair) and at the end
     if (active && (((ch + 1) & 3) == 0 || ch == nchunks - 1)) {
 #pragma unroll
@@ -275,7 +291,7 @@ int fill_gemm_cols(int MR) {
 }
 
 size_t fill_gemm_smem(int MR) {
-  return sizeof(__nv_bfloat16) * kFS * kFLD * ((size_t)2 * MR + 2 * (size_t)fill_gemm_cols(MR));
+  return 2 * sizeof(__nv_bfloat16) * kFS * kFLD * ((size_t)2 * MR + 2 * (size_t)fill_gemm_cols(MR));
 }
 
 cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out,

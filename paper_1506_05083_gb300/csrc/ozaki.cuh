@@ -244,6 +244,17 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
                : "r"(a));
 }
 
+// Asynchronous 16-byte global -> shared copy (L2 only); with valid == false
+// nothing is read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
 // Complex slice product for one k16 step: acc_re += Ar Br - Ai Bi, acc_im += Ar Bi + Ai Br.
 __device__ __forceinline__ void cmma(float (&re)[4], float (&im)[4], const uint32_t (&ar)[4],
                                      const uint32_t (&ai)[4], const uint32_t (&br)[2],
