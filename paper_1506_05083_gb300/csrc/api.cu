@@ -263,7 +263,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
     h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
     if (slices > 0) {
-      d.kp = (d.rows + 63) / 64 * 64;
+      // digit rows: rounded up to 64, plus 64 zero rows so that a 64-row chunk
+      // starting at any row of X stays inside the block
+      d.kp = (d.rows + 63) / 64 * 64 + 64;
       const size_t blocks = (size_t)d.D * d.npanels;
       (void)blocks;
       h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 4 * slices * axi::kNB * d.kp);

@@ -114,10 +114,9 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);
-// Batches of more than this many waves use the split-precision Q^H in split
-// mode; smaller ones use the native FP64 kernel (the digit split of every
-// panel would cost more than it saves).
-constexpr int kSplitApplyMinWaves = 33;
+// Split plans apply Q^H with split digits from this many waves up (the
+// cluster kernel is faster than the FP64 one at every batch size measured).
+constexpr int kSplitApplyMinWaves = 1;
 bool split_slices_supported(int slices);
 // kp_max: the largest digit row stride (kp) over the tasks of the launch
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,

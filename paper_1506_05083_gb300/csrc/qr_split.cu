@@ -18,6 +18,9 @@
 // and subtraction, a handful of operations against 256 for the FP64 kernel.
 #include "axi_internal.h"
 #include "ozaki.cuh"
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace axi {
 namespace {
@@ -49,6 +52,12 @@ struct OzSmem {
   double2 T[kNB][kNB + 1];
   int eVH[kNB], eX[kTN], eW[kTN], eV[kRC];
   unsigned long long kNext[kTN];
+};
+// Cluster form (rows split over C CTAs): W' slices and the cluster-summed W
+// of this CTA's column slice.
+struct ClExtra {
+  double2 Wq[kNB][kTN + 1];
+  double2 Wsum[kNB][kTN / 2 + 1];
 };
 
 __device__ __forceinline__ double2 vget(const double2 *A, int lda, int rows, int k0, int nbp, int i,
@@ -105,14 +114,21 @@ __device__ __forceinline__ PanelDigits panel_digits(const unsigned short *dig, c
 // in sm.kNext), else a scan of rows k0..rows-1. Pass 3 always leaves the keys
 // of the updated X over rows k0+kNB.. (the next panel step's rows) in
 // sm.kNext, and in `kout` when that is given.
-template <int S>
+// This CTA handles rows [rlo, rhi) of X (rlo a multiple of 32); with C > 1 the
+// CTA is one of a cluster of C that splits the rows: their partial V^H X are
+// summed through distributed shared memory, CTA r forms W' = T^H W for
+// columns [r kTN/C, (r+1) kTN/C), and every CTA gathers the whole W'.
+template <int S, int C = 1>
 __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0,
                                           const double2 *__restrict__ Tg,
                                           double2 *__restrict__ X, int ldx, int ncols,
                                           const unsigned long long *__restrict__ kin, bool carry,
-                                          unsigned long long *__restrict__ kout, OzSmem<S> &sm) {
+                                          unsigned long long *__restrict__ kout, OzSmem<S> &sm,
+                                          ClExtra *cx = nullptr, int rlo = 0, int rhi = -1) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane >> 2, tig = lane & 3;
+  if (rhi < 0) rhi = rows;
+  const int r1st = max(k0, rlo);
 
   // ---- pass 0: exponents of X's columns over rows k0..rows-1 (V's are stored)
   if (tid < kNB) sm.eVH[tid] = pd.ex[tid];
@@ -125,7 +141,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     for (int j = warp; j < kTN; j += kThreads / 32) {
       unsigned long long m = 0;
       if (j < ncols)
-        for (int i = k0 + lane; i < rows; i += 32) {
+        for (int i = r1st + lane; i < rhi; i += 32) {
           const unsigned long long k = key2(X[(size_t)j * ldx + i]);
           m = k > m ? k : m;
         }
@@ -157,8 +173,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       const int e = tid + u * kThreads, j = e / (kKC / 2), rp = e % (kKC / 2), i = r0 + 2 * rp;
       xst[u][0] = xst[u][1] = make_double2(0.0, 0.0);
       if (j < ncols) {
-        if (i < rows) xst[u][0] = X[(size_t)j * ldx + i];
-        if (i + 1 < rows) xst[u][1] = X[(size_t)j * ldx + i + 1];
+        if (i < rhi) xst[u][0] = X[(size_t)j * ldx + i];
+        if (i + 1 < rhi) xst[u][1] = X[(size_t)j * ldx + i + 1];
       }
     }
   };
@@ -166,8 +182,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   const int lrow = lane & 7, lmat = lane >> 3;
   const int a_row = lrow + 8 * (lmat & 1), a_k = 8 * (lmat >> 1);
   long long whi[2][4] = {}, wlo[2][4] = {};
-  stage(k0);
-  for (int r0 = k0; r0 < rows; r0 += kKC) {
+  if (r1st < rhi) stage(r1st);
+  for (int r0 = r1st; r0 < rhi; r0 += kKC) {
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kVU; ++u) {
@@ -185,7 +201,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       oz::split2_fast<S>(xst[u][0].y, xst[u][1].y, ex, wi, kTN * kLD1);
     }
     __syncthreads();
-    if (r0 + kKC < rows) stage(r0 + kKC);
+    if (r0 + kKC < rhi) stage(r0 + kKC);
     // All S groups accumulate at once (independent accumulators): digit s of
     // V^H is loaded once, then every digit t of X with s + t <= S + 1.
     float acc[S][2][4];
@@ -239,6 +255,42 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   __syncthreads();
 
   // ---- pass 2: W' = T^H W (T upper triangular) in FP64, then digits of W'
+  if constexpr (C > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    constexpr int CW = kTN / C;                             // columns of W' formed here
+    cl.sync();                                              // every CTA's partial W ready
+    for (int e = tid; e < kNB * CW; e += kThreads) {
+      const int a = e / CW, jl = e % CW, j = rank * CW + jl;
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const double2 *wr = cl.map_shared_rank(&sm.W[0][0], r);
+        const double2 w = wr[a * (kTN + 1) + j];
+        acc.x += w.x;
+        acc.y += w.y;
+      }
+      cx->Wsum[a][jl] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < kNB * CW; e += kThreads) {
+      const int a = e / CW, jl = e % CW;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int b = 0; b <= a; ++b) {
+        const double2 t = sm.T[b][a], w = cx->Wsum[b][jl];
+        acc.x += t.x * w.x + t.y * w.y;                     // conj(t) * w
+        acc.y += t.x * w.y - t.y * w.x;
+      }
+      cx->Wq[a][rank * CW + jl] = acc;
+    }
+    cl.sync();                                              // W' slices ready
+    for (int e = tid; e < kNB * kTN; e += kThreads) {
+      const int a = e / kTN, j = e % kTN;
+      const double2 *q = cl.map_shared_rank(&cx->Wq[0][0], j / CW);
+      sm.W[a][j] = q[a * (kTN + 1) + j];
+    }
+    __syncthreads();
+  } else {
   double2 wp[kNB * kTN / kThreads];
 #pragma unroll
   for (int u = 0; u < kNB * kTN / kThreads; ++u) {
@@ -258,6 +310,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     sm.W[a][j] = wp[u];
   }
   __syncthreads();
+  }
   if (tid < kTN) {
     unsigned long long m = 0;
     for (int a = 0; a < kNB; ++a) {
@@ -278,7 +331,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   // and the 32 target columns as four n8 tiles. For each tile all S groups
   // accumulate at once; the tile's X values are loaded before its products.
   const int knext = k0 + kNB;
-  for (int r0 = k0; r0 < rows; r0 += kRC) {
+  for (int r0 = r1st; r0 < rhi; r0 += kRC) {
     __syncthreads();
     const int rr0 = r0 - k0;
     if (tid < kRC) sm.eV[tid] = pd.ex[kNB + rr0 + tid];
@@ -291,7 +344,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       reinterpret_cast<uint4 *>(&sm.u.p3.A[0][0][0][0] + rowi * kLD2)[w4] = val;
     }
     __syncthreads();
-    if (r0 + 16 * warp >= rows) continue;
+    if (r0 + 16 * warp >= rhi) continue;
 #pragma unroll 1
     for (int nt = 0; nt < kTN / 8; ++nt) {
       double2 xv[4];
@@ -299,7 +352,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       for (int q = 0; q < 4; ++q) {
         const int i = r0 + 16 * warp + grp + (q >= 2 ? 8 : 0);
         const int j = 8 * nt + 2 * tig + (q & 1);
-        xv[q] = (i < rows && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
+        xv[q] = (i < rhi && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
       }
       float acc[S][2][4];
 #pragma unroll
@@ -332,7 +385,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       for (int q = 0; q < 4; ++q) {
         const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
         const int i = r0 + r, j = 8 * nt + 2 * tig + (q & 1);
-        if (i < rows && j < ncols) {
+        if (i < rhi && j < ncols) {
           const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
           double2 v = xv[q];
           v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][q], ylo[0][q]), e);
@@ -386,23 +439,33 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
                                Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin, false, kout, sm);
 }
 
-template <int S>
+// Q^H on RHS blocks with the rows of each (mode, 32-column tile) split over a
+// cluster of C CTAs (grid.x = D * C): the panels stay sequential, but each
+// CTA multiplies only its share of the rows, so a handful of waves' columns
+// still keep C x the SMs busy.
+template <int S, int C>
 __global__ void __launch_bounds__(kThreads)
-apply_qh_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total,
-                      const unsigned short *__restrict__ dig, const int *__restrict__ dex) {
+apply_qh_cluster_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total,
+                        const unsigned short *__restrict__ dig, const int *__restrict__ dex) {
   const ObsDev &o = *od;
-  const int d = blockIdx.x;
+  const int rank = (int)cg::this_cluster().block_rank();
+  const int d = blockIdx.x / C;
   const int c0 = blockIdx.y * kTN;
-  if (c0 >= ncols_total) return;
+  if (c0 >= ncols_total) return;                        // uniform over the cluster
   const int ncols = min(kTN, ncols_total - c0);
+  const int RB = ((o.rows + C - 1) / C + 31) / 32 * 32;
+  const int rlo = rank * RB, rhi = min(o.rows, rlo + RB);
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
+  ClExtra *cx = reinterpret_cast<ClExtra *>(smraw + (sizeof(OzSmem<S>) + 15) / 16 * 16);
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
   for (int p = 0; p < o.npanels; ++p) {
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-    oz_block_reflector_update<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows, p * kNB,
-                                 Tg, Xd, o.rows, ncols, nullptr, p > 0, nullptr, sm);
+    oz_block_reflector_update<S, C>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows,
+                                    p * kNB, Tg, Xd, o.rows, ncols, nullptr, false, nullptr, sm, cx,
+                                    rlo, rhi);
   }
+  cg::this_cluster().sync();                            // no CTA leaves while W' is being read
 }
 
 // Digits of one panel's reflectors for every active task (one CTA each).
@@ -498,6 +561,29 @@ cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const in
   return cudaGetLastError();
 }
 
+template <int S, int C>
+cudaError_t launch_apply_cluster_s(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                                   unsigned short *dig, int *dex, cudaStream_t st) {
+  const size_t smem = (sizeof(OzSmem<S>) + 15) / 16 * 16 + sizeof(ClExtra);
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(apply_qh_cluster_kernel<S, C>, smem, granted);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h.D * C, (ncol + kTN - 1) / kTN);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, apply_qh_cluster_kernel<S, C>, d_o, X, ncol,
+                            (const unsigned short *)dig, (const int *)dex);
+}
+
 template <int S>
 cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                               unsigned short *dig, int *dex, cudaStream_t st) {
@@ -508,13 +594,9 @@ cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, in
       d_o, nullptr, nullptr, 0, dig, dex);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(OzSmem<S>);
-  static size_t granted = 0;
-  e = ensure_dynamic_smem(apply_qh_split_kernel<S>, smem, granted);
-  if (e != cudaSuccess) return e;
-  dim3 grid(h.D, (ncol + kTN - 1) / kTN);
-  apply_qh_split_kernel<S><<<grid, kThreads, smem, st>>>(d_o, X, ncol, dig, dex);
-  return cudaGetLastError();
+  // rows split over a cluster of 4 CTAs (2 for short panels)
+  if (h.rows >= 192) return launch_apply_cluster_s<S, 4>(d_o, h, X, ncol, dig, dex, st);
+  return launch_apply_cluster_s<S, 2>(d_o, h, X, ncol, dig, dex, st);
 }
 
 }  // namespace
