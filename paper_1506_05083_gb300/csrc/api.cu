@@ -218,6 +218,21 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
   p->off_task_mode = off; off = align_up(off + sizeof(int) * ntask);
   p->off_status = off; off = align_up(off + sizeof(int));
   size_t fill_gdig_bytes = 0, fill_gex_bytes = 0;
+  // Split plans keep every panel's reflector digits (written by the QR, read
+  // by every apply) when they fit in 4 GB over the plan; otherwise the QR
+  // alternates two blocks per mode and each apply recomputes the digits.
+  bool keep_digits = false;
+  if (slices > 0) {
+    size_t total = 0;
+    for (int i = 0; i < n_obs; ++i) {
+      const int rows = obs[i].bc == AXI_BC_TRANSMISSION ? 2 * obs[i].M : obs[i].M;
+      const int cols = obs[i].bc == AXI_BC_TRANSMISSION ? 2 * obs[i].N : obs[i].N;
+      const size_t kp = (size_t)(rows + 63) / 64 * 64 + 64;
+      const size_t np = (size_t)(cols + axi::kNB - 1) / axi::kNB;
+      total += (size_t)(obs[i].P / 2 + 1) * np * (4 * slices * axi::kNB * kp * 2 + (axi::kNB + kp) * 4);
+    }
+    keep_digits = total <= ((size_t)4 << 30);
+  }
   for (int i = 0; i < n_obs; ++i) {
     const axi_obstacle &o = obs[i];
     ObsHost &h = p->obs[i];
@@ -268,8 +283,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       d.kp = (d.rows + 63) / 64 * 64 + 64;
       const size_t blocks = (size_t)d.D * d.npanels;
       (void)blocks;
-      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 4 * slices * axi::kNB * d.kp);
-      h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * 2 * (axi::kNB + d.kp));
+      d.dig_kept = keep_digits ? 1 : 0;
+      d.dig_nslot = keep_digits ? d.npanels : 2;
+      h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * d.dig_nslot * 4 * slices * axi::kNB * d.kp);
+      h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * d.dig_nslot * (axi::kNB + d.kp));
       h.off_ckey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * d.cols);
       // split fill: folded length, padding, cos-table digits, pair chunk
       const int hh = d.q / 2;
@@ -353,14 +370,17 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   const int slices = p->obs[0].dev.slices;
   int kp_max = 0;
   for (const auto &ob : p->obs) kp_max = ob.dev.kp > kp_max ? ob.dev.kp : kp_max;
-  bool rest_pending = false;
+  bool rest_pending = false, side_used = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
                              p->step_rows[s], slices, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
     const int rest_cols = p->step_cols[s] - axi::kNB;
-    if (rest_cols > 0) {
+    // kept digits: every panel's digits are written (the apply reads them),
+    // also at the last steps that have no trailing update
+    const bool digits_here = slices > 0 && (rest_cols > 0 || p->obs[0].dev.dig_kept);
+    if (rest_cols > 0 || digits_here) {
       if (cudaEventRecord(op->ev_panel, st) != cudaSuccess ||
           cudaStreamWaitEvent(op->side, op->ev_panel, 0) != cudaSuccess)
         return AXI_ERR_CUDA;
@@ -371,6 +391,12 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
       e = axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
     }
+    if (digits_here && rest_cols <= 0) {                  // nothing in the QR waits for these
+      e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
+                                   kp_max, op->side);
+      if (e != cudaSuccess) return AXI_ERR_CUDA;
+    }
+    if (rest_cols > 0 || digits_here) side_used = true;
     if (rest_cols > 0) {
       if (slices > 0) {
         e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
@@ -384,7 +410,10 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
       rest_pending = true;
     }
   }
-  if (rest_pending && cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess) return AXI_ERR_CUDA;
+  // join the side stream (its last kernels may be digit blocks only the apply reads)
+  if (side_used && (cudaEventRecord(op->ev_rest, op->side) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess))
+    return AXI_ERR_CUDA;
   return AXI_OK;
 }
 

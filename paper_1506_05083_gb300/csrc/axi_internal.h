@@ -43,7 +43,9 @@ struct ObsDev {
   // [kNB + kp] (per reflector column, then per row).
   unsigned short *vdig;
   int *vexp;
-  int kp;                 // digit row stride: rows rounded up to a multiple of 64
+  int kp;                 // digit row stride: rows rounded up to a multiple of 64, + 64
+  int dig_kept;           // 1: every panel's digits are kept for the apply (slot = panel)
+  int dig_nslot;          // digit blocks per mode: npanels (kept) or 2 (QR steps alternate)
   // split precision only: [D][2][cols] largest |entry| key (IEEE bits) of each
   // trailing column over the next panel step's rows, written by one split
   // update and read by the next (alternating slots), so the trailing matrix

@@ -435,7 +435,8 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
   const unsigned long long *kin =
       p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
   unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
-  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, 2, p & 1), o.rows, k0,
+  const int dslot = o.dig_kept ? p : (p & 1);
+  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot), o.rows, k0,
                                Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin, false, kout, sm);
 }
 
@@ -484,7 +485,8 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   // QR: two slots per mode alternating with the step, because the look-ahead
   // lets step p's trailing update still read its digits while step p+1's are
   // written; apply: one slot per panel.
-  const int nslot = qr ? 2 : o.npanels, slot = qr ? (p & 1) : p;
+  const int nslot = qr ? o.dig_nslot : o.npanels;
+  const int slot = (qr && !o.dig_kept) ? (p & 1) : p;
   const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows, kp = o.kp;
   const double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const size_t blk = digit_block<S>(kp);
@@ -586,14 +588,16 @@ cudaError_t launch_apply_cluster_s(const ObsDev *d_o, const ObsDev &h, double2 *
 
 template <int S>
 cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
-                              unsigned short *dig, int *dex, cudaStream_t st) {
-  static size_t granted_d = 0;
-  cudaError_t e = ensure_dynamic_smem(panel_digits_kernel<S>, sizeof(int) * (kNB + h.kp), granted_d);
-  if (e != cudaSuccess) return e;
-  panel_digits_kernel<S><<<dim3(h.D, h.npanels), 256, sizeof(int) * (kNB + h.kp), st>>>(
-      d_o, nullptr, nullptr, 0, dig, dex);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+                              unsigned short *dig, int *dex, bool kept, cudaStream_t st) {
+  if (!kept) {
+    static size_t granted_d = 0;
+    cudaError_t e = ensure_dynamic_smem(panel_digits_kernel<S>, sizeof(int) * (kNB + h.kp), granted_d);
+    if (e != cudaSuccess) return e;
+    panel_digits_kernel<S><<<dim3(h.D, h.npanels), 256, sizeof(int) * (kNB + h.kp), st>>>(
+        d_o, nullptr, nullptr, 0, dig, dex);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // rows split over a cluster of 4 CTAs (2 for short panels)
   if (h.rows >= 192) return launch_apply_cluster_s<S, 4>(d_o, h, X, ncol, dig, dex, st);
   return launch_apply_cluster_s<S, 2>(d_o, h, X, ncol, dig, dex, st);
@@ -638,7 +642,7 @@ cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, cons
 }
 
 size_t apply_digit_bytes(const ObsDev &h) {
-  if (h.slices <= 0) return 0;
+  if (h.slices <= 0 || h.dig_kept) return 0;                 // kept from the build
   const size_t blocks = (size_t)h.D * h.npanels;
   const size_t dig = blocks * 4 * (size_t)h.slices * kNB * h.kp * sizeof(unsigned short);
   return ((dig + 255) & ~(size_t)255) + blocks * (kNB + h.kp) * sizeof(int);
@@ -648,14 +652,17 @@ cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X
                                   void *digit_scratch, cudaStream_t st) {
   const size_t blocks = (size_t)h.D * h.npanels;
   const size_t dig = blocks * 4 * (size_t)h.slices * kNB * h.kp * sizeof(unsigned short);
-  unsigned short *dg = static_cast<unsigned short *>(digit_scratch);
-  int *dx = reinterpret_cast<int *>(static_cast<char *>(digit_scratch) + ((dig + 255) & ~(size_t)255));
+  const bool kept = h.dig_kept != 0;                    // the build left every panel's digits
+  unsigned short *dg = kept ? h.vdig : static_cast<unsigned short *>(digit_scratch);
+  int *dx = kept ? h.vexp
+                 : reinterpret_cast<int *>(static_cast<char *>(digit_scratch) +
+                                           ((dig + 255) & ~(size_t)255));
   switch (h.slices) {
-    case 4: return launch_apply_qh_s<4>(d_o, h, X, ncol, dg, dx, st);
-    case 5: return launch_apply_qh_s<5>(d_o, h, X, ncol, dg, dx, st);
-    case 6: return launch_apply_qh_s<6>(d_o, h, X, ncol, dg, dx, st);
-    case 7: return launch_apply_qh_s<7>(d_o, h, X, ncol, dg, dx, st);
-    case 8: return launch_apply_qh_s<8>(d_o, h, X, ncol, dg, dx, st);
+    case 4: return launch_apply_qh_s<4>(d_o, h, X, ncol, dg, dx, kept, st);
+    case 5: return launch_apply_qh_s<5>(d_o, h, X, ncol, dg, dx, kept, st);
+    case 6: return launch_apply_qh_s<6>(d_o, h, X, ncol, dg, dx, kept, st);
+    case 7: return launch_apply_qh_s<7>(d_o, h, X, ncol, dg, dx, kept, st);
+    case 8: return launch_apply_qh_s<8>(d_o, h, X, ncol, dg, dx, kept, st);
     default: return cudaErrorInvalidValue;
   }
 }
