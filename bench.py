@@ -38,15 +38,44 @@ import synth  # noqa: E402
 
 METRIC = "operator build time (FP64-equiv TFLOP/s), per-wave apply us at 1e-10 rel err"
 FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_probe_gb300.md)
-# DRAM bytes (read + write) of one fill_fft_kernel launch on the smooth-body
-# workload, from the ncu capture in profiles/fill_fft_smooth_k10_N180_M216_P120.md;
-# None until that capture is taken of the current kernel.
-FILL_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one split-plan fill on the smooth-body workload
+# (fill_samples_kernel 0.46 MB + 256.5 MB, fill_gemm_kernel 319.4 MB + 27.1 MB),
+# from the ncu capture in profiles/fill_split_smooth_k10_N180_M216_P120.md. The
+# FP64 plans' fill_fft_kernel has no capture of its current form (None).
+FILL_TRAFFIC_BYTES = {"split": 463360 + 256481536 + 319419136 + 27128832, "fp64": None}
 
 
 def workload():
     wl = synth.config_smooth()
     return wl, wl.obstacles[0]
+
+
+def step_launches(ob, spec, split, slices):
+    """Kernels one step launches, as the library schedules them: fill (split
+    plans: sample + digit-GEMM kernel per chunk of ring pairs), per panel step
+    the panel, next-panel update and trailing update (split: plus the panel's
+    reflector digits, at every step when the plan keeps them for the apply),
+    R's digits at the end of a split build, incident, and the apply's RHS
+    transform, Q^H, back substitution, scatter and point-strength transform."""
+    rows, cols = spec.rows, spec.cols
+    D = ob.P // 2 + 1
+    npanels = (cols + 15) // 16
+    n_next = sum(1 for p in range(npanels) if cols - 16 * (p + 1) > 0)
+    n_rest = sum(1 for p in range(npanels) if cols - 16 * (p + 2) > 0)
+    n = 1 + npanels + n_next + n_rest + 1 + 5
+    if split:
+        kinds = 4 if ob.bc != synth.BC_NEUMANN else 1
+        L = spec.q // 4 + 1 if (spec.q // 2) % 2 == 0 else (spec.q // 2 + 1) // 2
+        Lp = (L + 31) // 32 * 32
+        per_pair = 2 * 2 * kinds * 8 * Lp * 2
+        chunk = max(8, min(ob.M * ob.N, (512 << 20) // per_pair))
+        n += 2 * -(-ob.M * ob.N // chunk) - 1
+        kp = (rows + 63) // 64 * 64 + 64
+        kept = D * npanels * (4 * slices * 16 * kp * 2 + (16 + kp) * 4) <= (4 << 30)
+        n += npanels if kept else n_rest
+        n += 1 if (cols + 31) // 32 >= 2 else 0
+        n += 0 if kept else 1
+    return n
 
 
 def algorithmic_flops(M, N, P, W):
@@ -347,13 +376,7 @@ def main():
     kinds = ["deriv"] if ob.bc == synth.BC_NEUMANN else ["value", "deriv", "value", "deriv"]
     slots = fill_slots(ob.M, ob.N, ob.P, spec.q, kinds, args.prec == "split")
     ach = 2.0 * slots / (fill_ms * 1e-3) / 1e12          # one slot = one FMA = 2 flops
-    npanels = (spec.cols + 15) // 16
-    n_next = sum(1 for p in range(npanels) if spec.cols - 16 * (p + 1) > 0)
-    n_rest = sum(1 for p in range(npanels) if spec.cols - 16 * (p + 2) > 0)
-    # fill + panels + next-panel updates + trailing updates (+ their digit
-    # kernels in split precision) + incident + 5 apply kernels
-    launches_per_step = (1 + npanels + n_next + n_rest * (2 if args.prec == "split" else 1)
-                         + 1 + 5)
+    launches_per_step = step_launches(ob, spec, args.prec == "split", args.slices)
     torch.cuda.synchronize()
     status = op.status()
     if rank == 0:
@@ -374,7 +397,7 @@ def main():
                                    else "fill_fft_kernel",
                          "bound": "alu", "achieved": ach,
                          "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": FILL_TRAFFIC_BYTES,
+                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": FILL_TRAFFIC_BYTES[args.prec],
                          "work": "FP64 issue slots of the kernel's arithmetic x 2 flops "
                                  f"({slots:.4g} slots per launch)",
                          "peak_source": "FP64 DFMA probe of measured (MEASURED_PEAKS.json has "

@@ -24,7 +24,7 @@ struct ObsHost {
   std::vector<int> fft_perm, fft_perm_q;
   std::vector<double2> tw_q;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
-  size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
+  size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_rdig = 0, off_rex = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
   std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
   std::vector<int> fill_cex;               // and row exponents [2 MR]
   size_t off_fcdig = 0, off_fcex = 0;
@@ -288,6 +288,8 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * d.dig_nslot * 4 * slices * axi::kNB * d.kp);
       h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * d.dig_nslot * (axi::kNB + d.kp));
       h.off_ckey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * d.cols);
+      h.off_rdig = off; off = align_up(off + axi::r_digit_bytes(d));
+      h.off_rex = off; off = align_up(off + axi::r_exponent_bytes(d));
       // split fill: folded length, padding, cos-table digits, pair chunk
       const int hh = d.q / 2;
       d.fill_L = (hh % 2 == 0) ? hh / 2 + 1 : (hh + 1) / 2;
@@ -414,6 +416,11 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   if (side_used && (cudaEventRecord(op->ev_rest, op->side) != cudaSuccess ||
                     cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess))
     return AXI_ERR_CUDA;
+  // digits of R's off-diagonal blocks for every apply's back substitution
+  for (size_t i = 0; i < p->obs.size(); ++i) {
+    e = axi::launch_r_digits(op->d_obs + i, p->obs[i].dev, st);
+    if (e != cudaSuccess) return AXI_ERR_CUDA;
+  }
   return AXI_OK;
 }
 
@@ -443,6 +450,8 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.vdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_vdig) : nullptr;
     d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
     d.ckey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ckey) : nullptr;
+    d.rdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_rdig) : nullptr;
+    d.rex = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_rex) : nullptr;
     if (d.slices > 0) {
       d.fill_cdig = reinterpret_cast<const unsigned short *>(ws + h.off_fcdig);
       d.fill_cex = reinterpret_cast<const int *>(ws + h.off_fcex);

@@ -51,6 +51,13 @@ struct ObsDev {
   // update and read by the next (alternating slots), so the trailing matrix
   // is not scanned for its exponents at every step.
   unsigned long long *ckey;
+  // split precision only: digits of R's off-diagonal blocks for the back
+  // substitution, written at the end of the build. Per mode, 32-column block
+  // b (b >= 1) holds rb = r_digit_block_rows(b) rows starting at row offset
+  // r_digit_rows_before(b): digits [slices][re/im][rb][32] (row i, column
+  // 32 b + k), exponents [rb] (one per row of the block).
+  unsigned short *rdig;
+  int *rex;
   // split precision only: the fill's transform as a digit GEMM (fill_mma.cu).
   // Folded length L, padded Lp (multiple of 32), MR rows per parity part;
   // cos-table digits [kFillDigits][2 MR][Lp] and row exponents [2 MR];
@@ -69,6 +76,11 @@ struct ObsDev {
   const int *fft_perm_q;  // [q]
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
+
+// Rows of R above 32-column block b, rounded up to 64, and their running
+// total over blocks 0..b-1 (sum of 64 ceil(j/2) for j < b = 64 floor(b^2/4)).
+__host__ __device__ inline int r_digit_block_rows(int b) { return 64 * ((b + 1) / 2); }
+__host__ __device__ inline size_t r_digit_rows_before(int b) { return (size_t)64 * ((size_t)b * b / 4); }
 
 // Kernels of one factorisation step run side by side (panel and next-panel
 // update on the critical path, digits and trailing update beside them). With
@@ -116,6 +128,13 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);
+// trsm_split.cu: back substitution with its off-diagonal updates on tensor
+// cores; R's digits are written once per build (launch_r_digits)
+size_t r_digit_bytes(const ObsDev &h);
+size_t r_exponent_bytes(const ObsDev &h);
+cudaError_t launch_r_digits(const ObsDev *d_o, const ObsDev &h, cudaStream_t st);
+cudaError_t launch_trsm_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                              cudaStream_t st);
 // Split plans apply Q^H with split digits from this many waves up (the
 // cluster kernel is faster than the FP64 one at every batch size measured).
 constexpr int kSplitApplyMinWaves = 1;

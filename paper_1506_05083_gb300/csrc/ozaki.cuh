@@ -190,6 +190,15 @@ __device__ __forceinline__ double scaled_to_double(long long t, int e) {
   return __longlong_as_double((long long)(sgn | (((unsigned long long)(E + 1022) << 52) + m)));
 }
 
+// fold_group for group sums up to 2^24 (exact FP32 integers beyond the
+// magic-number range): a rounding conversion instead of the add trick.
+template <int S>
+__device__ __forceinline__ void fold_group_rn(long long &hi, long long &lo, int g, float acc) {
+  const long long v = (long long)__float2int_rn(acc);
+  if (g <= 4) hi += v << (7 * (4 - g));
+  else lo += v << (7 * (S + 1 - g));
+}
+
 // hi 2^{-28} + lo 2^{-7(S+1)}, times 2^E.
 template <int S>
 __device__ __forceinline__ double unfold(long long hi, long long lo, int E) {

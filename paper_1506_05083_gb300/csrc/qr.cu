@@ -837,8 +837,12 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
-  trsm_kernel<<<dim3(h.D, (ncol + kTS - 1) / kTS), kThreads, 0, st>>>(d_o, X, ncol);
-  e = cudaGetLastError();
+  if (h.slices > 0) {
+    e = launch_trsm_split(d_o, h, X, ncol, st);
+  } else {
+    trsm_kernel<<<dim3(h.D, (ncol + kTS - 1) / kTS), kThreads, 0, st>>>(d_o, X, ncol);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   scatter_coef_kernel<<<dim3(h.P, W), 128, 0, st>>>(d_o, W, X, coef);
   e = cudaGetLastError();
