@@ -384,8 +384,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-            "precision": (f"split-bf16 {args.slices} digits (QR trailing updates, Q^H); "
-                          "fill, panels, T, TRSM, transforms FP64") if args.prec == "split"
+            "precision": (f"split-bf16 {args.slices} digits (QR trailing updates, Q^H, TRSM off-diagonal "
+                          "blocks; fill transform 8 digits); "
+                          "fill samples, panels, T, TRSM diagonal blocks, transforms FP64") if args.prec == "split"
                          else "native fp64",
             "build_ms": float(np.mean(build_ms)),
             "build_tflops": qr_fl / (np.mean(build_ms) * 1e-3) / 1e12,
