@@ -109,6 +109,48 @@ __device__ __forceinline__ PanelDigits panel_digits(const unsigned short *dig, c
   return pd;
 }
 
+// W' = T^H W for T upper triangular: output (a, j) is a sum of a + 1 terms,
+// so outputs a and 15 - a are taken together (17 terms) to give every thread
+// the same FP64 chain. th_pair returns (a, 15 - a) of column j, lo = a.
+__device__ __forceinline__ void th_pair(const double2 (*T)[kNB + 1], const double2 *W, int ldw,
+                                        int j, int lo, double2 &out_lo, double2 &out_hi) {
+  const int hi = kNB - 1 - lo;
+  double2 al = make_double2(0.0, 0.0), ah = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int it = 0; it <= kNB; ++it) {               // kNB + 1 = 17 terms per pair
+    const bool low = it <= lo;
+    const int b = low ? it : it - lo - 1, a = low ? lo : hi;
+    const double2 tv = T[b][a], w = W[b * ldw + j];
+    const double re = tv.x * w.x + tv.y * w.y;      // conj(t) * w
+    const double im = tv.x * w.y - tv.y * w.x;
+    if (low) { al.x += re; al.y += im; } else { ah.x += re; ah.y += im; }
+  }
+  out_lo = al;
+  out_hi = ah;
+}
+
+// A pair (a, 15 - a) split over two threads (half 0: 9 terms, half 1: 8):
+// half 0 sums all of output lo and terms b = 0 .. 7 - lo of output hi, half 1
+// terms b = 8 - lo .. hi of output hi.
+__device__ __forceinline__ void th_pair_half(const double2 (*T)[kNB + 1], const double2 *W,
+                                             int ldw, int j, int lo, int half, double2 &al,
+                                             double2 &ah) {
+  const int hi = kNB - 1 - lo;
+  al = make_double2(0.0, 0.0);
+  ah = make_double2(0.0, 0.0);
+#pragma unroll 3
+  for (int it = 0; it <= kNB / 2; ++it) {
+    const bool low = half == 0 && it <= lo;
+    const int b = half == 0 ? (low ? it : it - lo - 1) : kNB / 2 - lo + it;
+    const int a = low ? lo : hi;
+    if (half == 1 && it == kNB / 2) break;
+    const double2 tv = T[b][a], w = W[b * ldw + j];
+    const double re = tv.x * w.x + tv.y * w.y;      // conj(t) * w
+    const double im = tv.x * w.y - tv.y * w.x;
+    if (low) { al.x += re; al.y += im; } else { ah.x += re; ah.y += im; }
+  }
+}
+
 // Column-max keys of X: `kin` (global, per column) when the previous update
 // left them, else `carry` (the previous panel's pass 3 of this CTA left them
 // in sm.kNext), else a scan of rows k0..rows-1. Pass 3 always leaves the keys
@@ -124,7 +166,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
                                           double2 *__restrict__ X, int ldx, int ncols,
                                           const unsigned long long *__restrict__ kin, bool carry,
                                           unsigned long long *__restrict__ kout, OzSmem<S> &sm,
-                                          ClExtra *cx = nullptr, int rlo = 0, int rhi = -1) {
+                                          ClExtra *cx = nullptr, int rlo = 0, int rhi = -1,
+                                          int xoff = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane >> 2, tig = lane & 3;
   if (rhi < 0) rhi = rows;
@@ -142,7 +185,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       unsigned long long m = 0;
       if (j < ncols)
         for (int i = r1st + lane; i < rhi; i += 32) {
-          const unsigned long long k = key2(X[(size_t)j * ldx + i]);
+          const unsigned long long k = key2(X[(size_t)j * ldx + i - xoff]);
           m = k > m ? k : m;
         }
       m = warp_max_u64(m);
@@ -173,8 +216,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       const int e = tid + u * kThreads, j = e / (kKC / 2), rp = e % (kKC / 2), i = r0 + 2 * rp;
       xst[u][0] = xst[u][1] = make_double2(0.0, 0.0);
       if (j < ncols) {
-        if (i < rhi) xst[u][0] = X[(size_t)j * ldx + i];
-        if (i + 1 < rhi) xst[u][1] = X[(size_t)j * ldx + i + 1];
+        if (i < rhi) xst[u][0] = X[(size_t)j * ldx + i - xoff];
+        if (i + 1 < rhi) xst[u][1] = X[(size_t)j * ldx + i + 1 - xoff];
       }
     }
   };
@@ -273,15 +316,27 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       cx->Wsum[a][jl] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < kNB * CW; e += kThreads) {
-      const int a = e / CW, jl = e % CW;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int b = 0; b <= a; ++b) {
-        const double2 t = sm.T[b][a], w = cx->Wsum[b][jl];
-        acc.x += t.x * w.x + t.y * w.y;                     // conj(t) * w
-        acc.y += t.x * w.y - t.y * w.x;
+    // kNB / 2 pairs (a, 15 - a) per column of the slice: one per thread, or
+    // one per two threads when there are enough threads (C >= 4)
+    static_assert((kNB / 2) * CW <= kThreads, "one pair per thread");
+    if constexpr ((kNB / 2) * CW * 2 <= kThreads) {
+      const int half = tid & 1, pi = tid >> 1;
+      const bool act = pi < (kNB / 2) * CW;
+      const int jl = pi % CW, lo = act ? pi / CW : 0;
+      double2 al, ah;
+      th_pair_half(sm.T, &cx->Wsum[0][0], kTN / 2 + 1, jl, lo, half, al, ah);
+      ah.x += __shfl_xor_sync(0xffffffffu, ah.x, 1);
+      ah.y += __shfl_xor_sync(0xffffffffu, ah.y, 1);
+      if (act && half == 0) {
+        cx->Wq[lo][rank * CW + jl] = al;
+        cx->Wq[kNB - 1 - lo][rank * CW + jl] = ah;
       }
-      cx->Wq[a][rank * CW + jl] = acc;
+    } else if (tid < (kNB / 2) * CW) {
+      const int jl = tid % CW, lo = tid / CW;
+      double2 olo, ohi;
+      th_pair(sm.T, &cx->Wsum[0][0], kTN / 2 + 1, jl, lo, olo, ohi);
+      cx->Wq[lo][rank * CW + jl] = olo;
+      cx->Wq[kNB - 1 - lo][rank * CW + jl] = ohi;
     }
     cl.sync();                                              // W' slices ready
     for (int e = tid; e < kNB * kTN; e += kThreads) {
@@ -291,23 +346,19 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     }
     __syncthreads();
   } else {
-  double2 wp[kNB * kTN / kThreads];
+  constexpr int kPairs = (kNB / 2) * kTN / kThreads;          // pairs (a, 15 - a) per thread
+  double2 wp[kPairs][2];
 #pragma unroll
-  for (int u = 0; u < kNB * kTN / kThreads; ++u) {
-    const int e = tid + u * kThreads, a = e / kTN, j = e % kTN;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = 0; b <= a; ++b) {
-      const double2 t = sm.T[b][a], w = sm.W[b][j];
-      acc.x += t.x * w.x + t.y * w.y;          // conj(t) * w
-      acc.y += t.x * w.y - t.y * w.x;
-    }
-    wp[u] = acc;
+  for (int u = 0; u < kPairs; ++u) {
+    const int e = tid + u * kThreads, j = e % kTN, lo = e / kTN;
+    th_pair(sm.T, &sm.W[0][0], kTN + 1, j, lo, wp[u][0], wp[u][1]);
   }
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < kNB * kTN / kThreads; ++u) {
-    const int e = tid + u * kThreads, a = e / kTN, j = e % kTN;
-    sm.W[a][j] = wp[u];
+  for (int u = 0; u < kPairs; ++u) {
+    const int e = tid + u * kThreads, j = e % kTN, lo = e / kTN;
+    sm.W[lo][j] = wp[u][0];
+    sm.W[kNB - 1 - lo][j] = wp[u][1];
   }
   __syncthreads();
   }
@@ -345,15 +396,23 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     }
     __syncthreads();
     if (r0 + 16 * warp >= rhi) continue;
-#pragma unroll 1
-    for (int nt = 0; nt < kTN / 8; ++nt) {
-      double2 xv[4];
+    // X values of tile nt + 1 are loaded while tile nt's products run
+    auto load_x = [&](int nt, double2 (&xv)[4]) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = r0 + 16 * warp + grp + (q >= 2 ? 8 : 0);
         const int j = 8 * nt + 2 * tig + (q & 1);
-        xv[q] = (i < rhi && j < ncols) ? X[(size_t)j * ldx + i] : make_double2(0.0, 0.0);
+        xv[q] = (i < rhi && j < ncols) ? X[(size_t)j * ldx + i - xoff] : make_double2(0.0, 0.0);
       }
+    };
+    double2 xnext[4];
+    load_x(0, xnext);
+#pragma unroll 1
+    for (int nt = 0; nt < kTN / 8; ++nt) {
+      double2 xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = xnext[q];
+      if (nt + 1 < kTN / 8) load_x(nt + 1, xnext);
       float acc[S][2][4];
 #pragma unroll
       for (int g = 0; g < S; ++g)
@@ -390,7 +449,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           double2 v = xv[q];
           v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][q], ylo[0][q]), e);
           v.y -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[1][q], ylo[1][q]), e);
-          X[(size_t)j * ldx + i] = v;
+          X[(size_t)j * ldx + i - xoff] = v;
           if (i >= knext) {
             const unsigned long long k = key2(v);
             cm[q & 1] = k > cm[q & 1] ? k : cm[q & 1];
@@ -463,7 +522,7 @@ apply_qh_cluster_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, 
   for (int p = 0; p < o.npanels; ++p) {
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
     oz_block_reflector_update<S, C>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows,
-                                    p * kNB, Tg, Xd, o.rows, ncols, nullptr, false, nullptr, sm, cx,
+                                    p * kNB, Tg, Xd, o.rows, ncols, nullptr, p > 0, nullptr, sm, cx,
                                     rlo, rhi);
   }
   cg::this_cluster().sync();                            // no CTA leaves while W' is being read
