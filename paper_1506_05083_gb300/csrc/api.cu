@@ -70,6 +70,23 @@ void fill_cos_digits(ObsHost &h, int S) {
       }
     }
   }
+  if (!d.fill_tc) return;
+  // tcgen05 layout: per (parity, 16-row chunk of the contraction, digit) one
+  // K-major no-swizzle tile of MR rows x 16 k (core matrices of 8 rows x 8 k,
+  // 128 bytes apart along k, 256 bytes apart along rows), so that one bulk
+  // copy brings a chunk's tiles of all digits
+  const int MR = d.fill_MR, nch = Lp / 16;
+  std::vector<unsigned short> tcl(h.fill_cdig.size(), 0);
+  for (int part = 0; part < 2; ++part)
+    for (int ch = 0; ch < nch; ++ch)
+      for (int s = 0; s < S; ++s)
+        for (int r = 0; r < MR; ++r)
+          for (int kk = 0; kk < 16; ++kk) {
+            const size_t tile = ((size_t)(part * nch + ch) * S + s) * MR * 16;
+            const size_t in = (size_t)(r / 8) * 128 + (kk / 8) * 64 + (r % 8) * 8 + (kk % 8);
+            tcl[tile + in] = h.fill_cdig[((size_t)s * rows + part * MR + r) * Lp + ch * 16 + kk];
+          }
+  h.fill_cdig.swap(tcl);
 }
 
 }  // namespace
@@ -295,11 +312,14 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       d.fill_L = (hh % 2 == 0) ? hh / 2 + 1 : (hh + 1) / 2;
       d.fill_Lp = (d.fill_L + 31) / 32 * 32;
       d.fill_MR = ((d.D + 1) / 2 + 15) / 16 * 16;
+      d.fill_tc = axi::fill_uses_tc(d.fill_Lp, d.fill_MR) ? 1 : 0;
       const int kinds = o.bc == AXI_BC_TRANSMISSION ? 4 : 1;
       const size_t per_pair = (size_t)2 * 2 * kinds * axi::kFillDigits * d.fill_Lp * sizeof(unsigned short);
       const size_t cap = (size_t)512 << 20;
       d.fill_chunk_pairs = (int)std::max<size_t>(8, std::min<size_t>((size_t)o.M * o.N, cap / per_pair));
-      fill_gdig_bytes = std::max(fill_gdig_bytes, per_pair * d.fill_chunk_pairs);
+      // the tcgen05 layout pads the columns to whole 128-column tiles
+      const size_t pad = d.fill_tc ? (size_t)2 * 128 * axi::kFillDigits * d.fill_Lp * sizeof(unsigned short) : 0;
+      fill_gdig_bytes = std::max(fill_gdig_bytes, per_pair * d.fill_chunk_pairs + pad);
       fill_gex_bytes = std::max(fill_gex_bytes, sizeof(int) * 2 * 2 * kinds * (size_t)d.fill_chunk_pairs);
       fill_cos_digits(h, axi::kFillDigits);
       h.off_fcdig = off; off = align_up(off + sizeof(unsigned short) * h.fill_cdig.size());

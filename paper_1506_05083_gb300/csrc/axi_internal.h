@@ -63,6 +63,7 @@ struct ObsDev {
   // cos-table digits [kFillDigits][2 MR][Lp] and row exponents [2 MR];
   // sample-digit scratch for fill_chunk_pairs ring pairs at a time.
   int fill_L, fill_Lp, fill_MR, fill_chunk_pairs;
+  int fill_tc;            // 1: tcgen05 transform (fill_uses_tc), digit tiles in its layout
   const unsigned short *fill_cdig;
   const int *fill_cex;
   uint32_t *fill_gdig;
@@ -76,6 +77,12 @@ struct ObsDev {
   const int *fft_perm_q;  // [q]
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
+
+// The split fill's transform runs on tcgen05 when its group sums stay exact
+// in FP32 over the whole contraction (folded length Lp <= 448) and the
+// accumulators of one parity fit tensor memory (MR <= 64 modes).
+constexpr int kFillTcMaxLp = 448;
+inline bool fill_uses_tc(int Lp, int MR) { return Lp <= kFillTcMaxLp && MR <= 64; }
 
 // Rows of R above 32-column block b, rounded up to 64, and their running
 // total over blocks 0..b-1 (sum of 64 ceil(j/2) for j < b = 64 floor(b^2/4)).

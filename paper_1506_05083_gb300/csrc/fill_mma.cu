@@ -14,7 +14,19 @@
 //   fill_samples_kernel  one warp per (pair, kind): FP64 samples, the fold,
 //                        per-column exponents and S = 8 balanced digits of
 //                        e and o (split2_fast), written to a scratch buffer;
-//   fill_gemm_kernel     CTA tile = all modes x NT real columns; the cos
+//   fill_gemm_tc_kernel  (Lp <= 448, MR <= 64) the same GEMM on the fifth-
+//                        generation tensor cores: CTA = 128 real columns x
+//                        the MR modes of one parity, tcgen05.mma (M = 128,
+//                        N = MR, K = 16) from shared-memory tiles in the
+//                        no-swizzle K-major layout (tcgen05.cuh), one FP32
+//                        accumulator per digit group g = s + t in tensor
+//                        memory, cp.async pipeline (2 stages and two CTAs
+//                        per SM for MR <= 32, else 4 stages) released by
+//                        tcgen05.commit; group sums stay exact over the whole
+//                        contraction (at most 36,928 per row of K, times
+//                        Lp <= 448 < 2^24), so the int64 fold happens once,
+//                        in the epilogue (tcgen05.ld);
+//   fill_gemm_kernel     (other sizes) CTA tile = all modes x NT real columns; the cos
 //                        table's digits (computed once per plan on the host)
 //                        and the sample digits are staged per 32-row chunk of
 //                        the contraction; every digit pair s + t <= 9 on BF16
@@ -26,6 +38,7 @@
 // FP64 work) moves to the tensor pipe.
 #include "axi_internal.h"
 #include "ozaki.cuh"
+#include "tcgen05.cuh"
 #include "trig.cuh"
 
 namespace axi {
@@ -51,7 +64,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // 32-bit words (two k per word); gex: [2 parts][cols2] exponents (one bit of
 // headroom, as split2_fast wants). Column c2 = 2 (pair_local * kinds + kind)
 // + (0 re, 1 im).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
 fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
                     uint32_t *__restrict__ gdig, int *__restrict__ gex) {
   const ObsDev &o = obs_arr[oi];
@@ -129,17 +142,40 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
     gex[cols2 + c2 + 1] = xo_i;
   }
   const int wpr = Lp / 2;                                  // words per digit row
-  uint32_t *de_r = gdig + (c2 * kFS) * wpr;
-  uint32_t *de_i = gdig + ((c2 + 1) * kFS) * wpr;
-  uint32_t *do_r = gdig + ((cols2 + c2) * kFS) * wpr;
-  uint32_t *do_i = gdig + ((cols2 + c2 + 1) * kFS) * wpr;
-  for (int w = lane; w < wpr; w += 32) {
-    const double2 e0 = eval(2 * w), e1 = eval(2 * w + 1);
-    const double2 o0 = oval(2 * w), o1 = oval(2 * w + 1);
-    oz::split2_fast<kFS>(e0.x, e1.x, xe_r, de_r + w, wpr);
-    oz::split2_fast<kFS>(e0.y, e1.y, xe_i, de_i + w, wpr);
-    oz::split2_fast<kFS>(o0.x, o1.x, xo_r, do_r + w, wpr);
-    oz::split2_fast<kFS>(o0.y, o1.y, xo_i, do_i + w, wpr);
+  if (!o.fill_tc) {
+    // [part][cols2][kFS][Lp]
+    uint32_t *de_r = gdig + (c2 * kFS) * wpr;
+    uint32_t *de_i = gdig + ((c2 + 1) * kFS) * wpr;
+    uint32_t *do_r = gdig + ((cols2 + c2) * kFS) * wpr;
+    uint32_t *do_i = gdig + ((cols2 + c2 + 1) * kFS) * wpr;
+    for (int w = lane; w < wpr; w += 32) {
+      const double2 e0 = eval(2 * w), e1 = eval(2 * w + 1);
+      const double2 o0 = oval(2 * w), o1 = oval(2 * w + 1);
+      oz::split2_fast<kFS>(e0.x, e1.x, xe_r, de_r + w, wpr);
+      oz::split2_fast<kFS>(e0.y, e1.y, xe_i, de_i + w, wpr);
+      oz::split2_fast<kFS>(o0.x, o1.x, xo_r, do_r + w, wpr);
+      oz::split2_fast<kFS>(o0.y, o1.y, xo_i, do_i + w, wpr);
+    }
+  } else {
+    // tcgen05 tiles: [part][128-column block][16-k chunk][digit] K-major
+    // no-swizzle tiles of 128 rows x 16 k (4096 bytes, 1024 words); column c
+    // is row c mod 128, word w holds k = 2w, 2w + 1
+    const int nch = Lp / 16, nblk = ((int)cols2 + 127) / 128;
+    auto tile = [&](int pt, size_t c) {
+      const int cb = (int)(c >> 7), r = (int)(c & 127);
+      return gdig + ((size_t)(pt * nblk + cb) * nch) * kFS * 1024 + (r >> 3) * 64 + (r & 7) * 4;
+    };
+    uint32_t *de_r = tile(0, c2), *de_i = tile(0, c2 + 1);
+    uint32_t *do_r = tile(1, c2), *do_i = tile(1, c2 + 1);
+    for (int w = lane; w < wpr; w += 32) {
+      const double2 e0 = eval(2 * w), e1 = eval(2 * w + 1);
+      const double2 o0 = oval(2 * w), o1 = oval(2 * w + 1);
+      const size_t off = (size_t)(w >> 3) * kFS * 1024 + ((w & 7) >> 2) * 32 + (w & 3);
+      oz::split2_fast<kFS>(e0.x, e1.x, xe_r, de_r + off, 1024);
+      oz::split2_fast<kFS>(e0.y, e1.y, xe_i, de_i + off, 1024);
+      oz::split2_fast<kFS>(o0.x, o1.x, xo_r, do_r + off, 1024);
+      oz::split2_fast<kFS>(o0.y, o1.y, xo_i, do_i + off, 1024);
+    }
   }
 }
 
@@ -283,6 +319,170 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
   if (bad) atomicOr(o.status, kStatNonFinite);
 }
 
+
+// ---------------------------------------------------------------------------
+// tcgen05 form. Grid (ceil(cols2 / 128), 2 parities), 256 threads. The sample
+// digits arrive in tiles (fill_samples_kernel's tcgen05 layout): per
+// (parity, 128-column block, 16-k chunk) the eight digits' K-major
+// no-swizzle tiles of 128 rows x 16 k, 32 KB contiguous; the cos-table
+// digits likewise per (parity, chunk), MR rows each. Stage b of the
+// pipeline receives one chunk of both through two bulk copies (TMA) that
+// complete on full[b]; thread 0 issues the MMAs of a chunk once full[b]
+// flips and releases the buffer through tcgen05.commit on empty[b].
+constexpr int kTcCols = 128;              // real columns per CTA (MMA M)
+constexpr int kTcThreads = 256;
+constexpr int kTcTileA = kTcCols * 16 * 2;        // bytes of one digit's A tile per chunk
+
+__host__ __device__ inline int tc_stage_bytes(int MR) { return kFS * kTcTileA + kFS * MR * 32; }
+__host__ __device__ inline uint32_t tc_tmem_cols(int MR) {
+  uint32_t n = 32;
+  while (n < (uint32_t)(kFS * MR)) n <<= 1;
+  return n;
+}
+
+template <int kTcStages>
+__global__ void __launch_bounds__(kTcThreads, 2)
+fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
+                    const uint32_t *__restrict__ gdig, const int *__restrict__ gex,
+                    double2 *__restrict__ out, int ld_rows, int ld_cols) {
+  const ObsDev &o = obs_arr[oi];
+  const int Lp = o.fill_Lp, MR = o.fill_MR, D = o.D;
+  const int part = blockIdx.y;
+  const int cols2 = npairs * kinds * 2;
+  const int c0 = blockIdx.x * kTcCols;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nch = Lp / 16, nblk = (cols2 + kTcCols - 1) / kTcCols;
+  const uint32_t a_bytes = kFS * kTcTileA, b_bytes = kFS * MR * 32;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const uint32_t ncols_tmem = tc_tmem_cols(MR);
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, ncols_tmem);
+  if (tid == 0) {
+    for (int b = 0; b < kTcStages; ++b) {
+      tc::mbar_init(&full[b], 1);
+      tc::mbar_init(&empty[b], 1);
+    }
+    fail = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const unsigned char *gA =
+        reinterpret_cast<const unsigned char *>(gdig) + (size_t)(part * nblk + blockIdx.x) * nch * a_bytes;
+    const unsigned char *gB =
+        reinterpret_cast<const unsigned char *>(o.fill_cdig) + (size_t)part * nch * b_bytes;
+    auto issue = [&](int c) {
+      const int b = c % kTcStages;
+      unsigned char *buf = tsm + (size_t)b * stage_bytes;
+      tc::mbar_arrive_expect_tx(&full[b], a_bytes + b_bytes);
+      tc::bulk_g2s(buf, gA + (size_t)c * a_bytes, a_bytes, &full[b]);
+      tc::bulk_g2s(buf + a_bytes, gB + (size_t)c * b_bytes, b_bytes, &full[b]);
+    };
+    const uint32_t idesc = tc::idesc_bf16_f32(kTcCols, MR);
+    constexpr long long kWaitCycles = 2000000000ll;   // about a second
+    int issued = 0, consumed = 0;
+    for (; issued < kTcStages && issued < nch; ++issued) issue(issued);
+    bool ok = true;
+    for (int ch = 0; ch < nch && ok; ++ch) {
+      const int b = ch % kTcStages;
+      if (!tc::mbar_wait(&full[b], (ch / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
+      consumed = ch + 1;
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(tsm + (size_t)b * stage_bytes), b0 = a0 + a_bytes;
+#pragma unroll
+      for (int s = 1; s <= kFS; ++s)
+#pragma unroll
+        for (int t = 1; t <= kFS + 1 - s; ++t) {
+          const uint64_t da = tc::smem_desc(a0 + (s - 1) * kTcTileA, 128, 256);
+          const uint64_t db = tc::smem_desc(b0 + (t - 1) * MR * 32, 128, 256);
+          tc::mma_bf16(tmem + (uint32_t)((s + t - 2) * MR), da, db, idesc, ch > 0 || s > 1);
+        }
+      tc::commit(&empty[b]);
+      // refill the buffer of chunk ch - 1 once its MMAs are done
+      if (ch >= 1 && issued < nch) {
+        const int pb = (ch - 1) % kTcStages;
+        if (!tc::mbar_wait(&empty[pb], ((ch - 1) / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
+        issue(issued++);
+      }
+    }
+    if (ok) ok = tc::mbar_wait(&empty[(nch - 1) % kTcStages], ((nch - 1) / kTcStages) & 1, kWaitCycles);
+    if (!ok) {
+      // let the copies still in flight land before the CTA's shared memory is released
+      for (int c = consumed; c < issued; ++c)
+        (void)tc::mbar_wait(&full[c % kTcStages], (c / kTcStages) & 1, kWaitCycles);
+      fail = 1;
+      atomicOr(o.status, kStatTimeout);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const bool ok = fail == 0;
+
+  if (ok) {
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. (the CTA's columns) and
+    // mode slices w / 4, w / 4 + 2, ... of 16 modes
+    const int lb = 32 * (warp & 3);
+    const int col = c0 + lb + lane;
+    const int ex_col = col < cols2 ? gex[(size_t)part * cols2 + col] : 0;
+    const int cp = col / 2, kind = cp % kinds, pl = cp / kinds;
+    const int p = pair0 + pl, m = p / o.N, j = p % o.N;
+    int orow = m, ocol = j;
+    double sign = 1.0;
+    if (o.bc == AXI_BC_TRANSMISSION) {
+      const bool ext = kind >= 2;
+      orow += (kind & 1) ? o.M : 0;
+      ocol += ext ? o.N : 0;
+      sign = ext ? -1.0 : 1.0;
+    }
+    const bool writer = (lane & 1) == 0 && col < cols2;
+    const size_t mode_stride = (size_t)ld_cols * ld_rows;
+    bool bad = false;
+    for (int sl = warp >> 2; sl < MR / 16; sl += kTcThreads / 128) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+#pragma unroll
+      for (int g = 2; g <= kFS + 1; ++g) {
+        uint32_t r[16];
+        tc::ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((g - 2) * MR + 16 * sl), r);
+        tc::ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const long long v = (long long)__float2int_rn(__uint_as_float(r[i]));
+          if (g <= 4) hi[i] += v << (7 * (4 - g));
+          else lo[i] += v << (7 * (kFS + 1 - g));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int mr = 16 * sl + i, n = 2 * mr + part;
+        const int E = o.fill_cex[part * MR + mr] + ex_col;
+        const double val =
+            oz::scaled_to_double(hi[i], E - 28) + oz::scaled_to_double(lo[i], E - 7 * (kFS + 1));
+        const double vim = __shfl_down_sync(0xffffffffu, val, 1);
+        if (writer && n < D) {
+          const double2 v = make_double2(sign * val, sign * vim);
+          bad |= !isfinite(v.x) || !isfinite(v.y);
+          out[(size_t)n * mode_stride + (size_t)ocol * ld_rows + orow] = v;
+        }
+      }
+    }
+    if (bad) atomicOr(o.status, kStatNonFinite);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols_tmem);
+}
+
 }  // namespace
 
 int fill_gemm_cols(int MR) {
@@ -300,11 +500,17 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
   const int npairs_total = h.M * h.N;
   const int NT = fill_gemm_cols(h.fill_MR);
   const size_t smemA = sizeof(double2) * (size_t)kFWarpsA * (h.q / 2 + 1);
-  const size_t smemB = fill_gemm_smem(h.fill_MR);
-  static size_t grantedA = 0, grantedB = 0;
+  const bool tc = h.fill_tc != 0;
+  // two CTAs per SM (TMEM and shared memory both allow it) for MR <= 32,
+  // else one CTA with a deeper pipeline
+  const bool two = h.fill_MR <= 32;
+  const size_t smemB = tc ? (size_t)(two ? 2 : 4) * tc_stage_bytes(h.fill_MR) : fill_gemm_smem(h.fill_MR);
+  static size_t grantedA = 0, grantedB = 0, grantedT2 = 0, grantedT4 = 0;
   cudaError_t e = ensure_dynamic_smem(fill_samples_kernel, smemA, grantedA);
   if (e != cudaSuccess) return e;
-  e = ensure_dynamic_smem(fill_gemm_kernel, smemB, grantedB);
+  e = !tc ? ensure_dynamic_smem(fill_gemm_kernel, smemB, grantedB)
+          : two ? ensure_dynamic_smem(fill_gemm_tc_kernel<2>, smemB, grantedT2)
+                : ensure_dynamic_smem(fill_gemm_tc_kernel<4>, smemB, grantedT4);
   if (e != cudaSuccess) return e;
   for (int pair0 = 0; pair0 < npairs_total; pair0 += h.fill_chunk_pairs) {
     const int np = min(h.fill_chunk_pairs, npairs_total - pair0);
@@ -313,8 +519,16 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int cols2 = np * kinds * 2;
-    fill_gemm_kernel<<<(cols2 + NT - 1) / NT, kFThreadsB, smemB, st>>>(
-        d_obs, oi, pair0, np, kinds, NT, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
+    const dim3 tgrid((cols2 + kTcCols - 1) / kTcCols, 2);
+    if (tc && two)
+      fill_gemm_tc_kernel<2><<<tgrid, kTcThreads, smemB, st>>>(
+          d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
+    else if (tc)
+      fill_gemm_tc_kernel<4><<<tgrid, kTcThreads, smemB, st>>>(
+          d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
+    else
+      fill_gemm_kernel<<<(cols2 + NT - 1) / NT, kFThreadsB, smemB, st>>>(
+          d_obs, oi, pair0, np, kinds, NT, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -2,6 +2,7 @@
 against the FP64 oracle. Parity bar as for the native path: e_bd, e_ff <= 1e-10
 at the default 7 digits; fewer digits must degrade gracefully and monotonically.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -29,6 +30,28 @@ def test_split_fill_parity(name):
     """Split plans fill with the tensor-core transform (8 digits, fill_mma.cu):
     same bar as the FP64 fill, e_A <= 1e-13 against the oracle's direct sums."""
     axi, op, (wl, ob, geo, A, fac) = _op(name, 7)
+    Ag = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    err = np.abs(Ag - A).max() / np.abs(A).max()
+    assert err < 1e-13, err
+
+
+@pytest.mark.parametrize("P,q", [(180, 0), (240, 0), (8, 1800)])
+def test_split_fill_parity_shapes(P, q):
+    """Mode counts that fill the tensor-core accumulators (P = 180: 48 modes per
+    parity, N = 48; P = 240: 64, every TMEM column), and a contraction too long
+    for exact FP32 group sums over one pass (q = 1800: 451 folded nodes), which
+    takes the mma.sync transform with periodic int64 folds."""
+    from paper_1506_05083_gb300 import axi
+    wl = synth.small_case(seed=29, k=3.0, M=24, N=20, P=P, q=q)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    if not ob.q:
+        ob = dataclasses.replace(ob, q=O.choose_q(ob, coll, src, srcx))
+    A = O.system_matrix(ob, coll, src, srcx)
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])],
+                      prec=axi.PREC_SPLIT_BF16 | (7 << 8))
     Ag = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
     torch.cuda.synchronize()
     assert op.status() == 0
