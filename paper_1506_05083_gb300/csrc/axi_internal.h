@@ -78,6 +78,9 @@ struct ObsDev {
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
 
+// Streaming multiprocessors of the current device (cached).
+int sm_count();
+
 // The split fill's transform runs on tcgen05 when its group sums stay exact
 // in FP32 over the whole contraction (folded length Lp <= 448) and the
 // accumulators of one parity fit tensor memory (MR <= 64 modes).

@@ -321,15 +321,25 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
 
 
 // ---------------------------------------------------------------------------
-// tcgen05 form. Grid (ceil(cols2 / 128), 2 parities), 256 threads. The sample
-// digits arrive in tiles (fill_samples_kernel's tcgen05 layout): per
-// (parity, 128-column block, 16-k chunk) the eight digits' K-major
-// no-swizzle tiles of 128 rows x 16 k, 32 KB contiguous; the cos-table
-// digits likewise per (parity, chunk), MR rows each. Stage b of the
-// pipeline receives one chunk of both through two bulk copies (TMA) that
-// complete on full[b]; thread 0 issues the MMAs of a chunk once full[b]
-// flips and releases the buffer through tcgen05.commit on empty[b].
-constexpr int kTcCols = 128;              // real columns per CTA (MMA M)
+// tcgen05 form, persistent. A tile is (parity, 128-column block); the sample
+// digits arrive in fill_samples_kernel's tcgen05 layout: per (parity,
+// column block, 16-k chunk) the eight digits' K-major no-swizzle tiles of 128
+// rows x 16 k, 32 KB contiguous; the cos-table digits likewise per (parity,
+// chunk), MR rows each. Each CTA walks the tiles blockIdx.x, + gridDim.x, ...
+// with its warps specialised:
+//   thread 0     streams chunks through kTcStages shared-memory buffers with
+//                two bulk copies (TMA) each, completing on full[b]; issues the
+//                MMAs of a chunk once full[b] flips (one per sample digit s,
+//                N = (9 - s) MR: every cos digit t <= 9 - s at once, column
+//                block t accumulating into group s + t) and frees the buffer with
+//                tcgen05.commit on empty[b]; after a tile's last chunk it
+//                commits acc_full, and before a tile's first MMA it waits
+//                for tmem_free (the epilogue has read the accumulators);
+//   warps 4..7   the epilogue: accumulators (TMEM lanes = the tile's 128
+//                columns) to int64, doubles, the modal matrices; then one
+//                arrival each on tmem_free.
+// The next tile's copies stream in while the epilogue of the current runs.
+constexpr int kTcCols = 128;              // real columns per tile (MMA M)
 constexpr int kTcThreads = 256;
 constexpr int kTcTileA = kTcCols * 16 * 2;        // bytes of one digit's A tile per chunk
 
@@ -340,6 +350,10 @@ __host__ __device__ inline uint32_t tc_tmem_cols(int MR) {
   return n;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+
 template <int kTcStages>
 __global__ void __launch_bounds__(kTcThreads, 2)
 fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
@@ -347,16 +361,17 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
                     double2 *__restrict__ out, int ld_rows, int ld_cols) {
   const ObsDev &o = obs_arr[oi];
   const int Lp = o.fill_Lp, MR = o.fill_MR, D = o.D;
-  const int part = blockIdx.y;
   const int cols2 = npairs * kinds * 2;
-  const int c0 = blockIdx.x * kTcCols;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nch = Lp / 16, nblk = (cols2 + kTcCols - 1) / kTcCols;
+  const int ntiles = 2 * nblk;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const uint32_t a_bytes = kFS * kTcTileA, b_bytes = kFS * MR * 32;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const uint32_t ncols_tmem = tc_tmem_cols(MR);
+  constexpr long long kWaitCycles = 2000000000ll;     // about a second per wait
   extern __shared__ __align__(1024) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
+  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full, tmem_free;
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
 
@@ -366,112 +381,138 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
       tc::mbar_init(&full[b], 1);
       tc::mbar_init(&empty[b], 1);
     }
+    tc::mbar_init(&acc_full, 1);
+    tc::mbar_init(&tmem_free, 4);                       // one arrival per epilogue warp
     fail = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
+  auto tile_of = [&](int i, int &part, int &cb) {
+    const int tt = blockIdx.x + i * gridDim.x;
+    part = tt / nblk;
+    cb = tt % nblk;
+  };
 
   if (tid == 0) {
-    const unsigned char *gA =
-        reinterpret_cast<const unsigned char *>(gdig) + (size_t)(part * nblk + blockIdx.x) * nch * a_bytes;
-    const unsigned char *gB =
-        reinterpret_cast<const unsigned char *>(o.fill_cdig) + (size_t)part * nch * b_bytes;
-    auto issue = [&](int c) {
-      const int b = c % kTcStages;
+    const int total = my_tiles * nch;
+    auto issue = [&](int gc) {
+      int part, cb;
+      tile_of(gc / nch, part, cb);
+      const int ch = gc % nch, b = gc % kTcStages;
       unsigned char *buf = tsm + (size_t)b * stage_bytes;
+      const unsigned char *ga = reinterpret_cast<const unsigned char *>(gdig) +
+                                ((size_t)(part * nblk + cb) * nch + ch) * a_bytes;
+      const unsigned char *gb = reinterpret_cast<const unsigned char *>(o.fill_cdig) +
+                                ((size_t)part * nch + ch) * b_bytes;
       tc::mbar_arrive_expect_tx(&full[b], a_bytes + b_bytes);
-      tc::bulk_g2s(buf, gA + (size_t)c * a_bytes, a_bytes, &full[b]);
-      tc::bulk_g2s(buf + a_bytes, gB + (size_t)c * b_bytes, b_bytes, &full[b]);
+      tc::bulk_g2s(buf, ga, a_bytes, &full[b]);
+      tc::bulk_g2s(buf + a_bytes, gb, b_bytes, &full[b]);
     };
-    const uint32_t idesc = tc::idesc_bf16_f32(kTcCols, MR);
-    constexpr long long kWaitCycles = 2000000000ll;   // about a second
-    int issued = 0, consumed = 0;
-    for (; issued < kTcStages && issued < nch; ++issued) issue(issued);
+    int issued = 0, consumed = 0, committed = -1;
+    for (; issued < kTcStages && issued < total; ++issued) issue(issued);
     bool ok = true;
-    for (int ch = 0; ch < nch && ok; ++ch) {
-      const int b = ch % kTcStages;
-      if (!tc::mbar_wait(&full[b], (ch / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
-      consumed = ch + 1;
+    for (int i = 0; i < my_tiles && ok; ++i) {
+      if (i > 0 && !tc::mbar_wait(&tmem_free, (i - 1) & 1, kWaitCycles)) { ok = false; break; }
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(tsm + (size_t)b * stage_bytes), b0 = a0 + a_bytes;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int gc = i * nch + ch, b = gc % kTcStages;
+        if (!tc::mbar_wait(&full[b], (gc / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
+        consumed = gc + 1;
+        const uint32_t a0 = tc::smem_u32(tsm + (size_t)b * stage_bytes), b0 = a0 + a_bytes;
+        // Digit s of the samples against the cos-table digits t = 1 .. 9 - s at
+        // once: the stacked B tiles (row (t - 1) MR + mode) form one K-major
+        // tile, and D's column block t lands on group s + t's accumulator at
+        // TMEM column (s + t - 2) MR. N is cut into pieces of at most 256.
 #pragma unroll
-      for (int s = 1; s <= kFS; ++s)
-#pragma unroll
-        for (int t = 1; t <= kFS + 1 - s; ++t) {
+        for (int s = 1; s <= kFS; ++s) {
           const uint64_t da = tc::smem_desc(a0 + (s - 1) * kTcTileA, 128, 256);
-          const uint64_t db = tc::smem_desc(b0 + (t - 1) * MR * 32, 128, 256);
-          tc::mma_bf16(tmem + (uint32_t)((s + t - 2) * MR), da, db, idesc, ch > 0 || s > 1);
+          const int ntot = (kFS + 1 - s) * MR;
+          for (int off = 0; off < ntot; off += 256) {
+            const int n = min(256, ntot - off);
+            const uint64_t db = tc::smem_desc(b0 + off * 32, 128, 256);
+            tc::mma_bf16(tmem + (uint32_t)((s - 1) * MR + off), da, db, tc::idesc_bf16_f32(kTcCols, n),
+                         ch > 0 || s > 1);
+          }
         }
-      tc::commit(&empty[b]);
-      // refill the buffer of chunk ch - 1 once its MMAs are done
-      if (ch >= 1 && issued < nch) {
-        const int pb = (ch - 1) % kTcStages;
-        if (!tc::mbar_wait(&empty[pb], ((ch - 1) / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
-        issue(issued++);
+        tc::commit(&empty[b]);
+        committed = gc;
+        if (ch == nch - 1) tc::commit(&acc_full);       // the tile's accumulators are final
+        // refill the buffer of chunk gc - 1 once its MMAs are done
+        if (gc >= 1 && issued < total) {
+          const int pg = gc - 1;
+          if (!tc::mbar_wait(&empty[pg % kTcStages], (pg / kTcStages) & 1, kWaitCycles)) { ok = false; break; }
+          issue(issued++);
+        }
       }
     }
-    if (ok) ok = tc::mbar_wait(&empty[(nch - 1) % kTcStages], ((nch - 1) / kTcStages) & 1, kWaitCycles);
     if (!ok) {
-      // let the copies still in flight land before the CTA's shared memory is released
+      // let the copies and MMAs in flight finish before shared memory and TMEM go
       for (int c = consumed; c < issued; ++c)
         (void)tc::mbar_wait(&full[c % kTcStages], (c / kTcStages) & 1, kWaitCycles);
-      fail = 1;
+      if (committed >= 0)
+        (void)tc::mbar_wait(&empty[committed % kTcStages], (committed / kTcStages) & 1, kWaitCycles);
+      atomicOr(&fail, 1);
       atomicOr(o.status, kStatTimeout);
     }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const bool ok = fail == 0;
-
-  if (ok) {
-    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. (the CTA's columns) and
-    // mode slices w / 4, w / 4 + 2, ... of 16 modes
+  } else if (warp >= 4) {
+    // epilogue warps: TMEM lanes 32 (w - 4) .. + 31, all mode slices
     const int lb = 32 * (warp & 3);
-    const int col = c0 + lb + lane;
-    const int ex_col = col < cols2 ? gex[(size_t)part * cols2 + col] : 0;
-    const int cp = col / 2, kind = cp % kinds, pl = cp / kinds;
-    const int p = pair0 + pl, m = p / o.N, j = p % o.N;
-    int orow = m, ocol = j;
-    double sign = 1.0;
-    if (o.bc == AXI_BC_TRANSMISSION) {
-      const bool ext = kind >= 2;
-      orow += (kind & 1) ? o.M : 0;
-      ocol += ext ? o.N : 0;
-      sign = ext ? -1.0 : 1.0;
-    }
-    const bool writer = (lane & 1) == 0 && col < cols2;
     const size_t mode_stride = (size_t)ld_cols * ld_rows;
     bool bad = false;
-    for (int sl = warp >> 2; sl < MR / 16; sl += kTcThreads / 128) {
-      long long hi[16], lo[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
-#pragma unroll
-      for (int g = 2; g <= kFS + 1; ++g) {
-        uint32_t r[16];
-        tc::ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((g - 2) * MR + 16 * sl), r);
-        tc::ld_wait();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const long long v = (long long)__float2int_rn(__uint_as_float(r[i]));
-          if (g <= 4) hi[i] += v << (7 * (4 - g));
-          else lo[i] += v << (7 * (kFS + 1 - g));
-        }
+    for (int i = 0; i < my_tiles; ++i) {
+      const bool w = tc::mbar_wait(&acc_full, i & 1, kWaitCycles);
+      if (!__all_sync(0xffffffffu, w) || *(volatile int *)&fail) break;
+      tc::fence_after_sync();
+      int part, cb;
+      tile_of(i, part, cb);
+      const int col = cb * kTcCols + lb + lane;
+      const int ex_col = col < cols2 ? gex[(size_t)part * cols2 + col] : 0;
+      const int cp = col / 2, kind = cp % kinds, pl = cp / kinds;
+      const int p = pair0 + pl, m = p / o.N, j = p % o.N;
+      int orow = m, ocol = j;
+      double sign = 1.0;
+      if (o.bc == AXI_BC_TRANSMISSION) {
+        const bool ext = kind >= 2;
+        orow += (kind & 1) ? o.M : 0;
+        ocol += ext ? o.N : 0;
+        sign = ext ? -1.0 : 1.0;
       }
+      const bool writer = (lane & 1) == 0 && col < cols2;
+      for (int sl = 0; sl < MR / 16; ++sl) {
+        long long hi[16], lo[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int mr = 16 * sl + i, n = 2 * mr + part;
-        const int E = o.fill_cex[part * MR + mr] + ex_col;
-        const double val =
-            oz::scaled_to_double(hi[i], E - 28) + oz::scaled_to_double(lo[i], E - 7 * (kFS + 1));
-        const double vim = __shfl_down_sync(0xffffffffu, val, 1);
-        if (writer && n < D) {
-          const double2 v = make_double2(sign * val, sign * vim);
-          bad |= !isfinite(v.x) || !isfinite(v.y);
-          out[(size_t)n * mode_stride + (size_t)ocol * ld_rows + orow] = v;
+        for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
+#pragma unroll
+        for (int g = 2; g <= kFS + 1; ++g) {
+          uint32_t r[16];
+          tc::ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((g - 2) * MR + 16 * sl), r);
+          tc::ld_wait();
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[q]));
+            if (g <= 4) hi[q] += v << (7 * (4 - g));
+            else lo[q] += v << (7 * (kFS + 1 - g));
+          }
+        }
+        if (sl == MR / 16 - 1) {                        // every accumulator of the tile read
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tmem_free);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int mr = 16 * sl + q, n = 2 * mr + part;
+          const int E = o.fill_cex[part * MR + mr] + ex_col;
+          const double val =
+              oz::scaled_to_double(hi[q], E - 28) + oz::scaled_to_double(lo[q], E - 7 * (kFS + 1));
+          const double vim = __shfl_down_sync(0xffffffffu, val, 1);
+          if (writer && n < D) {
+            const double2 v = make_double2(sign * val, sign * vim);
+            bad |= !isfinite(v.x) || !isfinite(v.y);
+            out[(size_t)n * mode_stride + (size_t)ocol * ld_rows + orow] = v;
+          }
         }
       }
     }
@@ -480,7 +521,10 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, ncols_tmem);
+  if (warp == 0) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem, ncols_tmem);
+  }
 }
 
 }  // namespace
@@ -519,7 +563,9 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int cols2 = np * kinds * 2;
-    const dim3 tgrid((cols2 + kTcCols - 1) / kTcCols, 2);
+    // persistent: as many CTAs as fit at once (two per SM for MR <= 32)
+    const int ntiles = 2 * ((cols2 + kTcCols - 1) / kTcCols);
+    const dim3 tgrid(min(ntiles, (two ? 2 : 1) * sm_count()));
     if (tc && two)
       fill_gemm_tc_kernel<2><<<tgrid, kTcThreads, smemB, st>>>(
           d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);

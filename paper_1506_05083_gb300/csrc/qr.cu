@@ -751,6 +751,8 @@ cudaError_t launch_panel_cluster(const ObsDev *d_obs, const int *d_task_obs, con
   return cudaLaunchKernelEx(&cfg, qr_panel_smem_kernel<C>, d_obs, d_task_obs, d_task_mode, p);
 }
 
+}  // namespace
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -761,8 +763,6 @@ int sm_count() {
   }
   return n;
 }
-
-}  // namespace
 
 // The panel is bound by the FP64 pipe of the SMs that factor it: when the
 // step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
