@@ -333,14 +333,19 @@ fill_gemm_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npai
 //                N = (9 - s) MR: every cos digit t <= 9 - s at once, column
 //                block t accumulating into group s + t) and frees the buffer with
 //                tcgen05.commit on empty[b]; after a tile's last chunk it
-//                commits acc_full, and before a tile's first MMA it waits
-//                for tmem_free (the epilogue has read the accumulators);
-//   warps 4..7   the epilogue: accumulators (TMEM lanes = the tile's 128
-//                columns) to int64, doubles, the modal matrices; then one
-//                arrival each on tmem_free.
+//                commits acc_full[a], and before a tile's first MMA it waits
+//                for tmem_free[a] (the epilogue has read accumulator set a;
+//                kTcAcc = 2 sets when 16 MR columns fit tensor memory, so the
+//                next tile's MMAs run while the epilogue reads the last);
+//   warps 4..11  the epilogue, two warps per SM sub-partition to hide the
+//                TMEM-load and integer latencies: warp w reads TMEM lanes
+//                32 (w mod 4) .. + 31 (the tile's columns) for the 16-mode
+//                slices (w - 4) / 4, + 2, ..., turns them into int64,
+//                doubles, the modal matrices; one arrival each on tmem_free.
 // The next tile's copies stream in while the epilogue of the current runs.
 constexpr int kTcCols = 128;              // real columns per tile (MMA M)
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 384;
+constexpr int kTcEpiWarps = 8;
 constexpr int kTcTileA = kTcCols * 16 * 2;        // bytes of one digit's A tile per chunk
 
 __host__ __device__ inline int tc_stage_bytes(int MR) { return kFS * kTcTileA + kFS * MR * 32; }
@@ -354,8 +359,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
 }
 
-template <int kTcStages>
-__global__ void __launch_bounds__(kTcThreads, 2)
+template <int kTcStages, int kTcAcc>
+__global__ void __launch_bounds__(kTcThreads, 1)
 fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int npairs, int kinds,
                     const uint32_t *__restrict__ gdig, const int *__restrict__ gex,
                     double2 *__restrict__ out, int ld_rows, int ld_cols) {
@@ -368,10 +373,11 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const uint32_t a_bytes = kFS * kTcTileA, b_bytes = kFS * MR * 32;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  const uint32_t ncols_tmem = tc_tmem_cols(MR);
+  const uint32_t ncols_tmem = tc_tmem_cols(kTcAcc * MR);
   constexpr long long kWaitCycles = 2000000000ll;     // about a second per wait
   extern __shared__ __align__(1024) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full, tmem_free;
+  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full[kTcAcc],
+      tmem_free[kTcAcc];
   __shared__ uint32_t tmem_base;
   __shared__ int fail;
 
@@ -381,8 +387,10 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
       tc::mbar_init(&full[b], 1);
       tc::mbar_init(&empty[b], 1);
     }
-    tc::mbar_init(&acc_full, 1);
-    tc::mbar_init(&tmem_free, 4);                       // one arrival per epilogue warp
+    for (int a = 0; a < kTcAcc; ++a) {
+      tc::mbar_init(&acc_full[a], 1);
+      tc::mbar_init(&tmem_free[a], kTcEpiWarps);        // one arrival per epilogue warp
+    }
     fail = 0;
   }
   tc::fence_before_sync();
@@ -414,7 +422,12 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
     for (; issued < kTcStages && issued < total; ++issued) issue(issued);
     bool ok = true;
     for (int i = 0; i < my_tiles && ok; ++i) {
-      if (i > 0 && !tc::mbar_wait(&tmem_free, (i - 1) & 1, kWaitCycles)) { ok = false; break; }
+      const int ab = i % kTcAcc;
+      const uint32_t acc = tmem + (uint32_t)(ab * kFS * MR);
+      if (i >= kTcAcc && !tc::mbar_wait(&tmem_free[ab], (i / kTcAcc - 1) & 1, kWaitCycles)) {
+        ok = false;
+        break;
+      }
       tc::fence_after_sync();
       for (int ch = 0; ch < nch; ++ch) {
         const int gc = i * nch + ch, b = gc % kTcStages;
@@ -432,13 +445,13 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
           for (int off = 0; off < ntot; off += 256) {
             const int n = min(256, ntot - off);
             const uint64_t db = tc::smem_desc(b0 + off * 32, 128, 256);
-            tc::mma_bf16(tmem + (uint32_t)((s - 1) * MR + off), da, db, tc::idesc_bf16_f32(kTcCols, n),
+            tc::mma_bf16(acc + (uint32_t)((s - 1) * MR + off), da, db, tc::idesc_bf16_f32(kTcCols, n),
                          ch > 0 || s > 1);
           }
         }
         tc::commit(&empty[b]);
         committed = gc;
-        if (ch == nch - 1) tc::commit(&acc_full);       // the tile's accumulators are final
+        if (ch == nch - 1) tc::commit(&acc_full[ab]);   // the tile's accumulators are final
         // refill the buffer of chunk gc - 1 once its MMAs are done
         if (gc >= 1 && issued < total) {
           const int pg = gc - 1;
@@ -457,12 +470,14 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
       atomicOr(o.status, kStatTimeout);
     }
   } else if (warp >= 4) {
-    // epilogue warps: TMEM lanes 32 (w - 4) .. + 31, all mode slices
+    // epilogue warps
     const int lb = 32 * (warp & 3);
     const size_t mode_stride = (size_t)ld_cols * ld_rows;
     bool bad = false;
     for (int i = 0; i < my_tiles; ++i) {
-      const bool w = tc::mbar_wait(&acc_full, i & 1, kWaitCycles);
+      const int ab = i % kTcAcc;
+      const uint32_t acc = tmem + (uint32_t)(ab * kFS * MR);
+      const bool w = tc::mbar_wait(&acc_full[ab], (i / kTcAcc) & 1, kWaitCycles);
       if (!__all_sync(0xffffffffu, w) || *(volatile int *)&fail) break;
       tc::fence_after_sync();
       int part, cb;
@@ -480,14 +495,20 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
         sign = ext ? -1.0 : 1.0;
       }
       const bool writer = (lane & 1) == 0 && col < cols2;
-      for (int sl = 0; sl < MR / 16; ++sl) {
+      const int sl0 = (warp - 4) >> 2;
+      if (sl0 >= MR / 16) {                             // no slice here (MR = 16)
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tmem_free[ab]);
+      }
+      for (int sl = sl0; sl < MR / 16; sl += kTcEpiWarps / 4) {
         long long hi[16], lo[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
 #pragma unroll
         for (int g = 2; g <= kFS + 1; ++g) {
           uint32_t r[16];
-          tc::ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((g - 2) * MR + 16 * sl), r);
+          tc::ld16(acc + ((uint32_t)lb << 16) + (uint32_t)((g - 2) * MR + 16 * sl), r);
           tc::ld_wait();
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -496,10 +517,10 @@ fill_gemm_tc_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
             else lo[q] += v << (7 * (kFS + 1 - g));
           }
         }
-        if (sl == MR / 16 - 1) {                        // every accumulator of the tile read
+        if (sl + kTcEpiWarps / 4 >= MR / 16) {          // this warp's last slice: its TMEM reads are done
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tmem_free);
+          if (lane == 0) mbar_arrive(&tmem_free[ab]);
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -545,16 +566,15 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
   const int NT = fill_gemm_cols(h.fill_MR);
   const size_t smemA = sizeof(double2) * (size_t)kFWarpsA * (h.q / 2 + 1);
   const bool tc = h.fill_tc != 0;
-  // two CTAs per SM (TMEM and shared memory both allow it) for MR <= 32,
-  // else one CTA with a deeper pipeline
+  // one CTA per SM, 4 stages; two accumulator sets when 16 MR TMEM columns fit
   const bool two = h.fill_MR <= 32;
-  const size_t smemB = tc ? (size_t)(two ? 2 : 4) * tc_stage_bytes(h.fill_MR) : fill_gemm_smem(h.fill_MR);
-  static size_t grantedA = 0, grantedB = 0, grantedT2 = 0, grantedT4 = 0;
+  const size_t smemB = tc ? (size_t)4 * tc_stage_bytes(h.fill_MR) : fill_gemm_smem(h.fill_MR);
+  static size_t grantedA = 0, grantedB = 0, grantedT2 = 0, grantedT1 = 0;
   cudaError_t e = ensure_dynamic_smem(fill_samples_kernel, smemA, grantedA);
   if (e != cudaSuccess) return e;
   e = !tc ? ensure_dynamic_smem(fill_gemm_kernel, smemB, grantedB)
-          : two ? ensure_dynamic_smem(fill_gemm_tc_kernel<2>, smemB, grantedT2)
-                : ensure_dynamic_smem(fill_gemm_tc_kernel<4>, smemB, grantedT4);
+          : two ? ensure_dynamic_smem(fill_gemm_tc_kernel<4, 2>, smemB, grantedT2)
+                : ensure_dynamic_smem(fill_gemm_tc_kernel<4, 1>, smemB, grantedT1);
   if (e != cudaSuccess) return e;
   for (int pair0 = 0; pair0 < npairs_total; pair0 += h.fill_chunk_pairs) {
     const int np = min(h.fill_chunk_pairs, npairs_total - pair0);
@@ -563,14 +583,14 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int cols2 = np * kinds * 2;
-    // persistent: as many CTAs as fit at once (two per SM for MR <= 32)
+    // persistent: one CTA per SM
     const int ntiles = 2 * ((cols2 + kTcCols - 1) / kTcCols);
-    const dim3 tgrid(min(ntiles, (two ? 2 : 1) * sm_count()));
+    const dim3 tgrid(min(ntiles, sm_count()));
     if (tc && two)
-      fill_gemm_tc_kernel<2><<<tgrid, kTcThreads, smemB, st>>>(
+      fill_gemm_tc_kernel<4, 2><<<tgrid, kTcThreads, smemB, st>>>(
           d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
     else if (tc)
-      fill_gemm_tc_kernel<4><<<tgrid, kTcThreads, smemB, st>>>(
+      fill_gemm_tc_kernel<4, 1><<<tgrid, kTcThreads, smemB, st>>>(
           d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex, out, ld_rows, ld_cols);
     else
       fill_gemm_kernel<<<(cols2 + NT - 1) / NT, kFThreadsB, smemB, st>>>(
