@@ -323,6 +323,14 @@ const char *axi_status_string(int32_t s);
  * missing pointers; n = 0 does nothing. */
 axi_status axi_diag_sincos(const double *d_x, int32_t n, double *d_sin, double *d_cos, void *stream);
 
+/* axi_diag_sincos_table -- diagnostics, as axi_diag_sincos, for the table form
+ * the fill's samples use: (cos, sin) of a multiple j of 2 pi / 1024 from a
+ * 1024-entry table in shared memory, short Taylor series for the remainder,
+ * angle addition (valid for |x| < 2^20). The first call on a device uploads
+ * the table to a static device array (16 KB). Same arguments and errors. */
+axi_status axi_diag_sincos_table(const double *d_x, int32_t n, double *d_sin, double *d_cos,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

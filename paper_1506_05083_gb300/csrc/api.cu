@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "axi_internal.h"
+#include "trig.cuh"
 
 using axi::ObsDev;
 
@@ -24,6 +25,8 @@ struct ObsHost {
   std::vector<int> fft_perm, fft_perm_q;
   std::vector<double2> tw_q;
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
+  size_t off_ring = 0;
+  std::vector<double2> tab_ring;
   size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_rdig = 0, off_rex = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
   std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
   std::vector<int> fill_cex;               // and row exponents [2 MR]
@@ -291,6 +294,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.off_cos = off; off = align_up(off + sizeof(double) * h.tab_cos.size());
     h.off_s2 = off; off = align_up(off + sizeof(double) * h.tab_s2.size());
     h.off_tw = off; off = align_up(off + sizeof(double2) * h.tw_P.size());
+    h.tab_ring.resize(axi::trig::kRingTab);
+    axi::trig::ring_table_host(h.tab_ring.data());
+    h.off_ring = off; off = align_up(off + sizeof(double2) * h.tab_ring.size());
     h.off_A = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.rows);
     h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
     h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
@@ -461,6 +467,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.tab_cos = reinterpret_cast<const double *>(ws + h.off_cos);
     d.tab_s2 = reinterpret_cast<const double *>(ws + h.off_s2);
     d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
+    d.tab_ring = reinterpret_cast<const double2 *>(ws + h.off_ring);
     d.fft_perm = reinterpret_cast<const int *>(ws + h.off_perm);
     d.fft_perm_q = reinterpret_cast<const int *>(ws + h.off_perm_q);
     d.tw_q = reinterpret_cast<const double2 *>(ws + h.off_tw_q);
@@ -487,6 +494,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_cos, h.tab_cos.data(), sizeof(double) * h.tab_cos.size()},
         {h.off_s2, h.tab_s2.data(), sizeof(double) * h.tab_s2.size()},
         {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
+        {h.off_ring, h.tab_ring.data(), sizeof(double2) * h.tab_ring.size()},
         {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
         {h.off_perm_q, h.fft_perm_q.data(), sizeof(int) * h.fft_perm_q.size()},
         {h.off_tw_q, h.tw_q.data(), sizeof(double2) * h.tw_q.size()},

@@ -32,6 +32,7 @@ struct ObsDev {
   const double *tab_cos;  // [q]   cos(2 pi r / q)
   const double *tab_s2;   // [q/2+1] sin^2(pi l / q)
   const double2 *tw_P;    // [P]   e^{-2 pi i r / P}
+  const double2 *tab_ring;  // [1024] (cos, sin)(2 pi i / 1024), the fill samples' sin/cos table
   double2 *A;             // [D][cols][rows] packed QR factors (column-major)
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)

@@ -71,7 +71,10 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   const int q = o.q, h = q / 2, L = o.fill_L, Lp = o.fill_Lp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ double2 fseq[];
-  double2 *seq = fseq + (size_t)warp * (h + 1);
+  double2 *ring = fseq;                           // [1024] sin/cos table
+  for (int i = threadIdx.x; i < trig::kRingTab; i += blockDim.x) ring[i] = o.tab_ring[i];
+  __syncthreads();
+  double2 *seq = fseq + trig::kRingTab + (size_t)warp * (h + 1);
   const int pl = blockIdx.x * kFWarpsA + warp;
   if (pl >= npairs) return;                       // whole warp; no block barriers below
   const int kind = blockIdx.y;
@@ -94,7 +97,7 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
     const double inv = rsqrt(R2);
     const double R = R2 * inv, kR = k * R;
     double sn, cs;
-    trig::sincos_ring(kR, &sn, &cs);
+    trig::sincos_ring_tab(kR, ring, &sn, &cs);
     double2 s;
     if (!deriv) {
       const double iw = inv * wq;
@@ -564,7 +567,7 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
   const int kinds = h.bc == AXI_BC_TRANSMISSION ? 4 : 1;
   const int npairs_total = h.M * h.N;
   const int NT = fill_gemm_cols(h.fill_MR);
-  const size_t smemA = sizeof(double2) * (size_t)kFWarpsA * (h.q / 2 + 1);
+  const size_t smemA = sizeof(double2) * ((size_t)trig::kRingTab + (size_t)kFWarpsA * (h.q / 2 + 1));
   const bool tc = h.fill_tc != 0;
   // one CTA per SM, 4 stages; two accumulator sets when 16 MR TMEM columns fit
   const bool two = h.fill_MR <= 32;

@@ -12,6 +12,7 @@
 // 23 FP64 operations. Valid for |x| < 2^20 (the samples use x = k R, far
 // below that); tests/test_gpu_trig.py checks it against CUDA's sincos.
 #pragma once
+#include <cmath>
 #include <cuda_runtime.h>
 
 namespace axi {
@@ -53,6 +54,45 @@ __device__ __forceinline__ void sincos_ring(double x, double *sp, double *cp) {
   const long long sgn = 1ll << 63;
   *sp = __longlong_as_double((q & 2u) ? sw ^ sgn : sw);
   *cp = __longlong_as_double(((q + 1u) & 2u) ? cw ^ sgn : cw);
+}
+
+// Table form for kernels that can hold a 16 KB table in shared memory:
+//   x = j delta + r,  delta = 2 pi / 1024,  j = rint(x / delta),  |r| <= delta / 2,
+// (cos, sin)(j delta) from the table (entry j mod 1024), sin r and cos r from
+// three- and two-term Taylor series (|r| <= 0.00307: truncation below 2e-19
+// relative), then the angle-addition formulas. delta's two Cody-Waite parts
+// are the pi/2 parts above divided by 256 (exact); the third part would
+// change r by less than 1e-26 for |x| < 2^20 and is dropped. 14 FP64
+// operations; entries of the table are accurate to half a unit in the last
+// place, so the result is within a few units of 2^-53 of the true value.
+constexpr int kRingTab = 1024;
+
+// (cos, sin)(2 pi i / 1024), i = 0 .. 1023, on the host.
+inline void ring_table_host(double2 *tab) {
+  const double twopi = 6.283185307179586476925286766559;
+  for (int i = 0; i < kRingTab; ++i) {
+    const double a = twopi * i / kRingTab;
+    tab[i] = make_double2(std::cos(a), std::sin(a));
+  }
+}
+
+__device__ __forceinline__ void sincos_ring_tab(double x, const double2 *__restrict__ tab, double *sp,
+                                                double *cp) {
+  constexpr double kRound = 6755399441055744.0;            // 1.5 * 2^52
+  constexpr double kInvDelta = 162.97466172610083;         // 512 / pi
+  constexpr double kDelta1 = 1.5707963267948966 / 256.0;   // exact scalings of the pi/2 parts
+  constexpr double kDelta2 = 6.123233995736766e-17 / 256.0;
+  const double t = fma(x, kInvDelta, kRound);
+  const double j = t - kRound;
+  const unsigned idx = (unsigned)__double2loint(t) & (kRingTab - 1);   // j mod 1024
+  double r = fma(-j, kDelta1, x);
+  r = fma(-j, kDelta2, r);
+  const double z = r * r;
+  const double s = fma(r * z, fma(z, 1.0 / 120.0, -1.0 / 6.0), r);  // sin r
+  const double c = fma(z, fma(z, 1.0 / 24.0, -0.5), 1.0);            // cos r
+  const double2 e = tab[idx];                                        // (cos, sin)(j delta)
+  *sp = fma(s, e.x, c * e.y);
+  *cp = fma(c, e.x, -(s * e.y));
 }
 
 }  // namespace trig

@@ -1,6 +1,8 @@
-"""The ring-kernel sin/cos routine (Cody-Waite reduction + Taylor series,
-csrc/trig.cuh) against CUDA's sincos (torch.sin / torch.cos on the device)
-and numpy's, through the diagnostics entry point axi_diag_sincos.
+"""The ring-kernel sin/cos routines (csrc/trig.cuh) against CUDA's sincos
+(torch.sin / torch.cos on the device) and numpy's, through the diagnostics
+entry points: axi_diag_sincos (Cody-Waite reduction + Taylor series) and
+axi_diag_sincos_table (1024-entry table + short series + angle addition, the
+form the fill's samples use).
 
 Bound: absolute error <= 1e-15 (about 4.5 units of 2^-52 at 1.0) for
 |x| <= 2000, which covers k R for every workload here (k <= 45, R <= 10).
@@ -15,7 +17,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_sincos_ring_against_cuda_and_numpy():
+@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table"])
+def test_sincos_ring_against_cuda_and_numpy(entry):
     from paper_1506_05083_gb300 import axi
     rng = np.random.default_rng(3)
     x = np.concatenate([
@@ -23,12 +26,14 @@ def test_sincos_ring_against_cuda_and_numpy():
         rng.uniform(-50.0, 50.0, 50_000),
         np.arange(-40, 41) * (math.pi / 4),                  # octant boundaries
         np.arange(-40, 41) * (math.pi / 2) + 1e-9,
+        np.arange(-3000, 3001) * (2 * math.pi / 1024),        # table points
+        np.arange(-3000, 3001) * (2 * math.pi / 1024) + math.pi / 1024,   # half-way
         [0.0, -0.0, 1e-300, 5e-324, 1e-8, math.pi, 1000.0 * math.pi],
     ])
     xd = torch.tensor(x, device="cuda")
     s = torch.empty_like(xd)
     c = torch.empty_like(xd)
-    code = axi.lib().axi_diag_sincos(C.c_void_p(xd.data_ptr()), len(x), C.c_void_p(s.data_ptr()),
+    code = getattr(axi.lib(), entry)(C.c_void_p(xd.data_ptr()), len(x), C.c_void_p(s.data_ptr()),
                                      C.c_void_p(c.data_ptr()), None)
     assert code == axi.OK
     torch.cuda.synchronize()
@@ -42,9 +47,10 @@ def test_sincos_ring_against_cuda_and_numpy():
     assert np.abs(s.cpu().numpy() ** 2 + c.cpu().numpy() ** 2 - 1.0).max() <= 1e-15
 
 
-def test_diag_sincos_arguments():
+@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table"])
+def test_diag_sincos_arguments(entry):
     from paper_1506_05083_gb300 import axi
-    L = axi.lib()
-    assert L.axi_diag_sincos(None, -1, None, None, None) == axi.ERR_ARG
-    assert L.axi_diag_sincos(None, 0, None, None, None) == axi.OK
-    assert L.axi_diag_sincos(None, 5, None, None, None) == axi.ERR_ARG
+    f = getattr(axi.lib(), entry)
+    assert f(None, -1, None, None, None) == axi.ERR_ARG
+    assert f(None, 0, None, None, None) == axi.OK
+    assert f(None, 5, None, None, None) == axi.ERR_ARG
