@@ -87,12 +87,11 @@ def algorithmic_flops(M, N, P, W):
 
 # FP64 issue slots (one slot = one DFMA) of the fill kernel's arithmetic, from
 # its source: per ring sample rsqrt (8.2 slots, measured) + the ring sin/cos
-# of trig.cuh (native FP64 plans: reduction + Taylor series, 23 operations;
-# split plans: the 1024-entry table form, 14) + the products around them (11
+# of trig.cuh (the 1024-entry table form, 14 operations) + the products around them (11
 # for the normal derivative, 6 for the value kernel); per FFT butterfly the
 # adds, multiplies and twiddle products of fft.cuh (radix 2: 8, 3: 22, 4: 28,
 # 5: 52); the pruned last stage costs 2 (r - 1) per needed mode.
-SINCOS_SLOTS = {False: 23.0, True: 14.0}
+SINCOS_SLOTS = 14.0
 SLOTS_PRODUCTS = {"deriv": 8.2 + 11.0, "value": 8.2 + 6.0}
 SLOTS_BUTTERFLY = {2: 8, 3: 22, 4: 28, 5: 52}
 
@@ -128,7 +127,7 @@ def fill_slots(M, N, P, q, bc_kinds, split):
         rad, last = fill_fft_plan(q, D)
         per_kind = sum(SLOTS_BUTTERFLY[r] * (q // r) for r in rad)
         per_kind += 2 * (last - 1) * D if last else 0
-    per_pair = sum((h + 1) * (SLOTS_PRODUCTS[k] + SINCOS_SLOTS[split]) + per_kind for k in bc_kinds)
+    per_pair = sum((h + 1) * (SLOTS_PRODUCTS[k] + SINCOS_SLOTS) + per_kind for k in bc_kinds)
     return M * N * per_pair
 
 

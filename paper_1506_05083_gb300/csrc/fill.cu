@@ -174,7 +174,7 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
     const double inv = rsqrt(R2);
     const double R = R2 * inv, kR = k * R;
     double sn, cs;
-    trig::sincos_ring(kR, &sn, &cs);
+    trig::sincos_ring_tab(kR, o.tab_ring, &sn, &cs);   // table in global memory (L1-resident)
     double2 s;
     if (!deriv) {
       const double iw = inv * wq;
