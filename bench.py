@@ -39,10 +39,10 @@ import synth  # noqa: E402
 METRIC = "operator build time (FP64-equiv TFLOP/s), per-wave apply us at 1e-10 rel err"
 FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_probe_gb300.md)
 # DRAM bytes (read + write) of one split-plan fill on the smooth-body workload
-# (fill_samples_kernel 0.46 MB + 256.5 MB, fill_gemm_kernel 319.4 MB + 27.1 MB),
+# (fill_samples_kernel 3.0 MB + 261.4 MB, fill_gemm_tc_kernel 319.9 MB + 21.1 MB),
 # from the ncu capture in profiles/fill_split_smooth_k10_N180_M216_P120.md. The
 # FP64 plans' fill_fft_kernel has no capture of its current form (None).
-FILL_TRAFFIC_BYTES = {"split": 463360 + 256481536 + 319419136 + 27128832, "fp64": None}
+FILL_TRAFFIC_BYTES = {"split": 3003392 + 261359616 + 319930880 + 21131008, "fp64": None}
 
 
 def workload():
@@ -394,8 +394,8 @@ def main():
             "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
             "e2e": {"value": ws * (qr_fl + ap_fl) / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"kernel": ("fill_samples_kernel + fill_gemm_kernel (FP64 samples, "
-                                    "tensor-core transform)") if args.prec == "split"
+            "roofline": {"kernel": ("fill_samples_kernel + fill_gemm_tc_kernel (FP64 samples, "
+                                    "tcgen05 transform)") if args.prec == "split"
                                    else "fill_fft_kernel",
                          "bound": "alu", "achieved": ach,
                          "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
