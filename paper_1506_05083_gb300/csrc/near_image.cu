@@ -111,7 +111,7 @@ near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, 
     const double inv = rsqrt(R2);
     const double R = R2 * inv;
     double sn, cs;
-    trig::sincos_ring(g.k * R, &sn, &cs);
+    trig::sincos_ring_tab(g.k * R, o.tab_ring, &sn, &cs);   // table through L1
     const double f = (nx * dx + ny * dy + nz * dz) * inv * inv * inv * kInv4Pi, kR = g.k * R;
     kv = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));   // (ikR - 1) e^{ikR}
   }

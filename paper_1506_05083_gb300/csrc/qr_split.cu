@@ -499,6 +499,32 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
                                Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin, false, kout, sm);
 }
 
+// L2 prefetch of what panel step p reads in the apply: this CTA's rows of the
+// V^H and V digit blocks and T. The kept digit blocks of a whole operator
+// exceed L2, so without it every panel step starts with DRAM-latency loads.
+template <int S>
+__device__ __forceinline__ void prefetch_panel_l2(const PanelDigits &pd, int k0, int rlo, int rhi,
+                                                  const double2 *Tg) {
+  auto pf = [](const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); };
+  const int tid = threadIdx.x;
+  const int r1 = max(k0, rlo) - k0, r2 = rhi - k0;        // local rows of the panel's block
+  if (r2 <= r1) return;
+  // V^H digits: S * 2 * kNB rows of kp, this CTA's columns r1 .. r2 (128-byte lines)
+  const int l1 = (r1 * 2) >> 7, l2 = ((r2 * 2 - 1) >> 7) + 1;        // lines per row
+  const int nl = l2 - l1;
+  for (int e = tid; e < S * 2 * kNB * nl; e += kThreads) {
+    const int row = e / nl, l = l1 + e % nl;
+    pf(reinterpret_cast<const char *>(pd.vh + (size_t)row * pd.kp) + 128 * l);
+  }
+  // V row digits: per (digit, part) the rows r1 .. r2 of kNB entries, contiguous
+  const int bytes = (r2 - r1) * kNB * 2, nb = (bytes + 127) / 128;
+  for (int e = tid; e < S * 2 * nb; e += kThreads) {
+    const int sp = e / nb, l = e % nb;
+    pf(reinterpret_cast<const char *>(pd.v + ((size_t)sp * pd.kp + r1) * kNB) + 128 * l);
+  }
+  if (tid < kNB * kNB * 16 / 128) pf(reinterpret_cast<const char *>(Tg) + 128 * tid);
+}
+
 // Q^H on RHS blocks with the rows of each (mode, 32-column tile) split over a
 // cluster of C CTAs (grid.x = D * C): the panels stay sequential, but each
 // CTA multiplies only its share of the rows, so a handful of waves' columns
@@ -519,8 +545,13 @@ apply_qh_cluster_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, 
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   ClExtra *cx = reinterpret_cast<ClExtra *>(smraw + (sizeof(OzSmem<S>) + 15) / 16 * 16);
   double2 *Xd = X + ((size_t)d * ncols_total + c0) * o.rows;
+  prefetch_panel_l2<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, 0), 0, rlo, rhi,
+                       o.T + (size_t)d * o.npanels * kNB * kNB);
   for (int p = 0; p < o.npanels; ++p) {
     const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+    if (p + 1 < o.npanels)                              // the next step's digits into L2
+      prefetch_panel_l2<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p + 1), (p + 1) * kNB, rlo,
+                           rhi, Tg + kNB * kNB);
     oz_block_reflector_update<S, C>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows,
                                     p * kNB, Tg, Xd, o.rows, ncols, nullptr, p > 0, nullptr, sm, cx,
                                     rlo, rhi);
