@@ -17,26 +17,32 @@
 // with the image phases. Without the symmetry every image is its own
 // representative with one rotation.
 //
-// Arithmetic: kernel values are generated in FP64 (rsqrt, sincos) and both
-// operands are split into S balanced base-128 digits (ozaki.cuh); the GEMM
-// runs on BF16 mma.sync with all digit groups' FP32 sums live, folded into
-// int64 every 256 products of the contraction. Both operands are split with
-// one bit of headroom so every digit satisfies |d| <= 64; a group sum of one
-// complex component then stays below 256 * 2 * 7 * 2^12 < 2^24, an exact FP32
-// integer converted with __float2int_rn.
+// Arithmetic: kernel values are generated in FP64 (rsqrt, table sin/cos) and
+// both operands are split into S balanced base-128 digits (ozaki.cuh), written
+// straight into K-major no-swizzle tiles (core matrices of 8 rows x 8 k) of
+// 128 targets x 16 sources (A) and 32 columns x 16 sources (B). The GEMM runs
+// on tcgen05 (near_gemm_tc_kernel): per 16-source chunk, for every kernel
+// digit s and part, one MMA against the stacked strength digits t <= S + 1 - s,
+// whose column blocks land on the FP32 group accumulators s + t in tensor
+// memory (real and imaginary parts separately; -Ai Bi through the
+// instruction's negate-A bit). Both operands are split with one bit of
+// headroom so every digit satisfies |d| <= 64; a group sum then stays below
+// 256 * 2 * 7 * 2^12 < 2^24 over 256 sources, after which the epilogue warps
+// fold the accumulators into exact int64 sums and the MMAs start over.
 #include "axi_internal.h"
 #include "trig.cuh"
 #include "ozaki.cuh"
+#include "tcgen05.cuh"
 
 namespace axi {
 namespace {
 
 constexpr double kInv4Pi = 0.07957747154594766788;
-constexpr int kGM = 64;        // targets per GEMM CTA
-constexpr int kGN = 32;        // (rotation, wave) columns per GEMM CTA
-constexpr int kGK = 32;        // contraction chunk
-constexpr int kLDK = kGK + 8;  // padded k stride in shared memory
-constexpr int kFlushChunks = 8;  // fold FP32 group sums every 8 chunks (256 products)
+constexpr int kGK = 32;        // sources padded to a multiple of this
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
 
 struct NearGeom {
   int M, N, P, nrot, nrep, W, S, Sp;   // S = N*P sources, Sp padded to kGK
@@ -91,8 +97,10 @@ near_rowexp_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, i
   }
 }
 
-// Kernel-value digits of the representative image for targets [t0, t0 + nt):
-// A[s][part][ti][Sp] (k = source index contiguous), zero beyond S.
+// Kernel-value digits of the representative image for targets [t0, t0 + nt),
+// in tiles: per (128-target block, 16-source chunk) the 2 SD planes (part-major:
+// re digits 1..SD, then im) of 128 x 16, 4096 bytes each, element (r, kk) at
+// (r / 8) 256 + (kk / 8) 128 + (r % 8) 16 + (kk % 8) 2; zero beyond S.
 template <int SD>
 __global__ void __launch_bounds__(256)
 near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, int nt,
@@ -115,11 +123,12 @@ near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, 
     const double f = (nx * dx + ny * dy + nz * dz) * inv * inv * inv * kInv4Pi, kR = g.k * R;
     kv = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));   // (ikR - 1) e^{ikR}
   }
-  const size_t plane = (size_t)nt * g.Sp;
   const int e = erow[ti];
-  unsigned short *dst = A + (size_t)ti * g.Sp + s;
-  oz::split_store_n(kv.x, e, SD, dst, 2 * plane);
-  oz::split_store_n(kv.y, e, SD, dst + plane, 2 * plane);
+  const int r = ti & 127, kk = s & 15;
+  unsigned short *dst = A + ((size_t)(ti >> 7) * (g.Sp / 16) + (s >> 4)) * 2 * SD * 2048 +
+                        (r >> 3) * 128 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
+  oz::split_store_n(kv.x, e, SD, dst, 2048);                   // planes 4096 bytes apart
+  oz::split_store_n(kv.y, e, SD, dst + SD * 2048, 2048);
 }
 
 // Exponent of each wave's strengths (max over all sources).
@@ -143,7 +152,9 @@ near_sigexp_kernel(NearGeom g, const double2 *__restrict__ sigma, int *__restric
   if (threadIdx.x == 0) ecol[w] = oz::key_exponent(red[0]) + 1;   // headroom: |d| <= 64
 }
 
-// Strength digits: column c = r W + w holds sigma_w(R^r s), s = j P + l -> (j, l + r P/4).
+// Strength digits: column c = r W + w holds sigma_w(R^r s), s = j P + l -> (j, l + r P/4);
+// tiles per (32-column block, 16-source chunk): 2 SD planes (re digits, then
+// im) of 32 x 16, 1024 bytes each, the A tile layout with 32 rows.
 template <int SD>
 __global__ void __launch_bounds__(256)
 near_bdigits_kernel(NearGeom g, const double2 *__restrict__ sigma, const int *__restrict__ ecol,
@@ -158,121 +169,176 @@ near_bdigits_kernel(NearGeom g, const double2 *__restrict__ sigma, const int *__
     const int lr = (l + r * (g.P / 4)) % g.P;
     v = sigma[(size_t)w * g.sld + j * g.P + lr];
   }
-  const int NC = g.nrot * g.W;
-  const size_t plane = (size_t)NC * g.Sp;
-  unsigned short *dst = B + (size_t)c * g.Sp + s;
-  oz::split_store_n(v.x, ecol[w], SD, dst, 2 * plane);
-  oz::split_store_n(v.y, ecol[w], SD, dst + plane, 2 * plane);
+  const int rr = c & 31, kk = s & 15;
+  unsigned short *dst = B + ((size_t)(c >> 5) * (g.Sp / 16) + (s >> 4)) * 2 * SD * 512 +
+                        (rr >> 3) * 128 + (kk >> 3) * 64 + (rr & 7) * 8 + (kk & 7);
+  oz::split_store_n(v.x, ecol[w], SD, dst, 512);               // planes 1024 bytes apart
+  oz::split_store_n(v.y, ecol[w], SD, dst + SD * 512, 512);
 }
 
-// C[ti][c] = sum_s K[ti][s] B[s][c] for one block of targets; 8 warps, each a
-// 16 x 16 output tile (one m16 fragment x two n8 fragments); int64 folds of
-// every digit group, FP64 at the end.
-template <int SD>
-__global__ void __launch_bounds__(256)
-near_gemm_kernel(NearGeom g, int nt, const unsigned short *__restrict__ A,
-                 const unsigned short *__restrict__ B, const int *__restrict__ erow,
-                 const int *__restrict__ ecol, double2 *__restrict__ C) {
-  constexpr int NG = SD;                         // groups g = 2 .. SD + 1
-  extern __shared__ __align__(16) unsigned char near_smem[];
-  typedef __nv_bfloat16 ATile[2][kGM][kLDK];
-  typedef __nv_bfloat16 BTile[2][kGN][kLDK];
-  ATile *As = reinterpret_cast<ATile *>(near_smem);                       // [SD]
-  BTile *Bs = reinterpret_cast<BTile *>(near_smem + sizeof(ATile) * SD);  // [SD]
-  const int NC = g.nrot * g.W;
-  const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;       // 4 x 2 warps: rows 16 wm, columns 16 wn
-  const int grp = lane >> 2, tig = lane & 3;
-  const size_t aplane = (size_t)nt * g.Sp, bplane = (size_t)NC * g.Sp;
+// C[ti][c] = sum_s K[ti][s] B[s][c] for one block of targets on tcgen05. CTA
+// tile: 128 targets (MMA M) x 32 columns; 384 threads. Thread 0 streams the
+// 16-source chunks (two bulk copies each: 2 SD A planes, 2 SD B planes) through
+// 3 shared-memory stages and issues per chunk 4 SD MMAs:
+//   re += Ar_s [Br_1 .. Br_{SD+1-s}] - Ai_s [Bi_1 ..]  (negate-A bit),
+//   im += Ar_s [Bi_1 .. ] + Ai_s [Br_1 .. ],
+// N = (SD + 1 - s) 32, column block t landing on group s + t (TMEM columns
+// (g - 2) 32 for re, SD 32 + (g - 2) 32 for im). Every kNearFold chunks (256
+// sources) the epilogue warps 4..11 (TMEM lanes 32 (w mod 4) .., 16 columns
+// each) convert the group sums to int64 and add them to exact hi/lo sums, then
+// release the accumulators; at the end they write C in FP64.
+constexpr int kNearCols = 32;
+constexpr int kNearThreads = 384;
+constexpr int kNearStages = 3;
+constexpr int kNearFold = 16;                 // chunks of 16 sources per fold
 
-  float acc[NG][2][2][4];                        // [group][re/im][n-fragment][element]
-  long long hi[2][2][4], lo[2][2][4];
+template <int SD>
+__host__ __device__ constexpr int near_stage_bytes() { return 2 * SD * 4096 + 2 * SD * 1024; }
+
+template <int SD>
+__global__ void __launch_bounds__(kNearThreads, 1)
+near_gemm_tc_kernel(NearGeom g, int nt, const unsigned short *__restrict__ A,
+                    const unsigned short *__restrict__ B, const int *__restrict__ erow,
+                    const int *__restrict__ ecol, double2 *__restrict__ C, int *__restrict__ status) {
+  const int NC = g.nrot * g.W;
+  const int mb = blockIdx.x, nb = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nch = g.Sp / 16;
+  const int nfold = (nch + kNearFold - 1) / kNearFold;
+  constexpr uint32_t a_bytes = 2 * SD * 4096, b_bytes = 2 * SD * 1024;
+  constexpr uint32_t stage_bytes = a_bytes + b_bytes;
+  constexpr uint32_t ncols_tmem = 512;               // 2 SD x 32 <= 448 columns used
+  constexpr long long kWaitCycles = 2000000000ll;
+  extern __shared__ __align__(1024) unsigned char nsm[];
+  __shared__ __align__(8) uint64_t full[kNearStages], empty[kNearStages], acc_full, tmem_free;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, ncols_tmem);
+  if (tid == 0) {
+    for (int b = 0; b < kNearStages; ++b) {
+      tc::mbar_init(&full[b], 1);
+      tc::mbar_init(&empty[b], 1);
+    }
+    tc::mbar_init(&acc_full, 1);
+    tc::mbar_init(&tmem_free, 8);                     // one arrival per epilogue warp
+    fail = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const unsigned char *gA = reinterpret_cast<const unsigned char *>(A) + (size_t)mb * nch * a_bytes;
+    const unsigned char *gB = reinterpret_cast<const unsigned char *>(B) + (size_t)nb * nch * b_bytes;
+    auto issue = [&](int c) {
+      const int b = c % kNearStages;
+      unsigned char *buf = nsm + (size_t)b * stage_bytes;
+      tc::mbar_arrive_expect_tx(&full[b], a_bytes + b_bytes);
+      tc::bulk_g2s(buf, gA + (size_t)c * a_bytes, a_bytes, &full[b]);
+      tc::bulk_g2s(buf + a_bytes, gB + (size_t)c * b_bytes, b_bytes, &full[b]);
+    };
+    int issued = 0, consumed = 0, committed = -1;
+    for (; issued < kNearStages && issued < nch; ++issued) issue(issued);
+    bool ok = true;
+    for (int ch = 0; ch < nch && ok; ++ch) {
+      const int f = ch / kNearFold, first = ch % kNearFold == 0;
+      if (first && f > 0) {
+        if (!tc::mbar_wait(&tmem_free, (f - 1) & 1, kWaitCycles)) { ok = false; break; }
+        tc::fence_after_sync();
+      }
+      const int b = ch % kNearStages;
+      if (!tc::mbar_wait(&full[b], (ch / kNearStages) & 1, kWaitCycles)) { ok = false; break; }
+      consumed = ch + 1;
+      const uint32_t a0 = tc::smem_u32(nsm + (size_t)b * stage_bytes), b0 = a0 + a_bytes;
+      const uint32_t bre = b0, bim = b0 + SD * 1024;
 #pragma unroll
-  for (int q = 0; q < NG; ++q)
+      for (int s = 1; s <= SD; ++s) {
+        const int nn = (SD + 1 - s) * kNearCols;
+        const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+        const uint32_t idesc_neg = tc::idesc_bf16_f32(128, nn, true);
+        const uint64_t dar = tc::smem_desc(a0 + (s - 1) * 4096, 128, 256);
+        const uint64_t dai = tc::smem_desc(a0 + (SD + s - 1) * 4096, 128, 256);
+        const uint64_t dbr = tc::smem_desc(bre, 128, 256), dbi = tc::smem_desc(bim, 128, 256);
+        const uint32_t dre = tmem + (uint32_t)((s - 1) * kNearCols);
+        const uint32_t dim = tmem + (uint32_t)((SD + s - 1) * kNearCols);
+        const bool acc = !(first && s == 1);
+        tc::mma_bf16(dre, dar, dbr, idesc, acc);
+        tc::mma_bf16(dre, dai, dbi, idesc_neg, true);
+        tc::mma_bf16(dim, dar, dbi, idesc, acc);
+        tc::mma_bf16(dim, dai, dbr, idesc, true);
+      }
+      tc::commit(&empty[b]);
+      committed = ch;
+      if (ch % kNearFold == kNearFold - 1 || ch == nch - 1) tc::commit(&acc_full);
+      if (ch >= 1 && issued < nch) {
+        const int pg = ch - 1;
+        if (!tc::mbar_wait(&empty[pg % kNearStages], (pg / kNearStages) & 1, kWaitCycles)) { ok = false; break; }
+        issue(issued++);
+      }
+    }
+    if (!ok) {
+      for (int c = consumed; c < issued; ++c)
+        (void)tc::mbar_wait(&full[c % kNearStages], (c / kNearStages) & 1, kWaitCycles);
+      if (committed >= 0)
+        (void)tc::mbar_wait(&empty[committed % kNearStages], (committed / kNearStages) & 1, kWaitCycles);
+      atomicOr(&fail, 1);
+      atomicOr(status, kStatTimeout);
+    }
+  } else if (warp >= 4) {
+    const int lb = 32 * (warp & 3), hf = (warp - 4) >> 2;     // TMEM lanes, 16-column half
+    long long hi[2][16], lo[2][16];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int f = 0; f < 2; ++f)
+      for (int q = 0; q < 16; ++q) hi[c][q] = lo[c][q] = 0;
+    bool ok = true;
+    for (int f = 0; f < nfold; ++f) {
+      const bool w = tc::mbar_wait(&acc_full, f & 1, kWaitCycles);
+      if (!__all_sync(0xffffffffu, w) || *(volatile int *)&fail) { ok = false; break; }
+      tc::fence_after_sync();
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[q][c][f][e] = 0.f;
+      for (int c = 0; c < 2; ++c)
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+        for (int gg = 2; gg <= SD + 1; ++gg) {
+          uint32_t r[16];
+          tc::ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((c * SD + gg - 2) * kNearCols + 16 * hf), r);
+          tc::ld_wait();
 #pragma unroll
-    for (int f = 0; f < 2; ++f)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) hi[c][f][e] = lo[c][f][e] = 0;
-
-  const int nchunk = g.Sp / kGK;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int k0 = ch * kGK;
-    __syncthreads();
-    // A: SD*2*kGM rows of kGK digits (64 bytes = 4 x 16 B); B likewise with kGN rows
-    for (int e = tid; e < SD * 2 * kGM * 4; e += 256) {
-      const int q = e & 3, row = e >> 2;                  // row = (s*2 + part)*kGM + r
-      const int sp = row / kGM, r = row % kGM;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (m0 + r < nt)
-        v = reinterpret_cast<const uint4 *>(A + (size_t)sp * aplane + (size_t)(m0 + r) * g.Sp + k0)[q];
-      reinterpret_cast<uint4 *>(&As[0][0][0][0] + row * kLDK)[q] = v;
+          for (int q = 0; q < 16; ++q) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[q]));
+            if (gg <= 4) hi[c][q] += v << (7 * (4 - gg));
+            else lo[c][q] += v << (7 * (SD + 1 - gg));
+          }
+        }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cta(&tmem_free);
     }
-    for (int e = tid; e < SD * 2 * kGN * 4; e += 256) {
-      const int q = e & 3, row = e >> 2;
-      const int sp = row / kGN, r = row % kGN;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (n0 + r < NC)
-        v = reinterpret_cast<const uint4 *>(B + (size_t)sp * bplane + (size_t)(n0 + r) * g.Sp + k0)[q];
-      reinterpret_cast<uint4 *>(&Bs[0][0][0][0] + row * kLDK)[q] = v;
-    }
-    __syncthreads();
+    if (ok) {
+      const int r = mb * 128 + lb + lane;
+      if (r < nt) {
+        const int er = erow[r];
 #pragma unroll
-    for (int kk = 0; kk < kGK; kk += 16) {
-#pragma unroll
-      for (int s = 1; s <= SD; ++s) {
-        uint32_t ar[4], ai[4];
-        oz::load_a(&As[s - 1][0][16 * wm][kk], kLDK, lane, ar);
-        oz::load_a(&As[s - 1][1][16 * wm][kk], kLDK, lane, ai);
-#pragma unroll
-        for (int t = 1; t <= SD + 1 - s; ++t) {
-#pragma unroll
-          for (int f = 0; f < 2; ++f) {
-            uint32_t br[2], bi[2];
-            oz::load_b(&Bs[t - 1][0][16 * wn + 8 * f][kk], kLDK, lane, br);
-            oz::load_b(&Bs[t - 1][1][16 * wn + 8 * f][kk], kLDK, lane, bi);
-            oz::cmma(acc[s + t - 2][0][f], acc[s + t - 2][1][f], ar, ai, br, bi);
+        for (int q = 0; q < 16; ++q) {
+          const int c = nb * kNearCols + 16 * hf + q;
+          if (c < NC) {
+            const int ex = er + ecol[c % g.W];
+            C[(size_t)r * NC + c] = make_double2(oz::unfold<SD>(hi[0][q], lo[0][q], ex),
+                                                 oz::unfold<SD>(hi[1][q], lo[1][q], ex));
           }
         }
       }
     }
-    if ((ch + 1) % kFlushChunks == 0 || ch + 1 == nchunk) {
-#pragma unroll
-      for (int q = 0; q < NG; ++q)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int f = 0; f < 2; ++f)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const long long v = (long long)__float2int_rn(acc[q][c][f][e]);
-              const int g2 = q + 2;
-              if (g2 <= 4) hi[c][f][e] += v << (7 * (4 - g2));
-              else lo[c][f][e] += v << (7 * (SD + 1 - g2));
-              acc[q][c][f][e] = 0.f;
-            }
-    }
   }
-#pragma unroll
-  for (int f = 0; f < 2; ++f)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = m0 + 16 * wm + grp + (e >= 2 ? 8 : 0);
-      const int c = n0 + 16 * wn + 8 * f + 2 * tig + (e & 1);
-      if (r < nt && c < NC) {
-        const int ex = erow[r] + ecol[c % g.W];
-        C[(size_t)r * NC + c] = make_double2(oz::unfold<SD>(hi[0][f][e], lo[0][f][e], ex),
-                                             oz::unfold<SD>(hi[1][f][e], lo[1][f][e], ex));
-      }
-    }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem, ncols_tmem);
+  }
 }
 
 // U[w][t0 + ti] += sum_r ph_w(R^r rep) C[(m, l - r P/4)][r W + w] for the block's targets.
@@ -363,8 +429,8 @@ size_t near_image_scratch_bytes(const ObsDev &h, int W, double ex, double ey, in
   const int NC = g.nrot * W;
   add(sizeof(int) * tb);                                 // row exponents
   add(sizeof(int) * W);                                  // column exponents
-  add(sizeof(unsigned short) * 2 * (size_t)slices * tb * g.Sp);   // A digits
-  add(sizeof(unsigned short) * 2 * (size_t)slices * NC * g.Sp);   // B digits
+  add(sizeof(unsigned short) * 2 * (size_t)slices * ((tb + 127) / 128 * 128) * g.Sp);   // A digit tiles
+  add(sizeof(unsigned short) * 2 * (size_t)slices * ((NC + 31) / 32 * 32) * g.Sp);     // B digit tiles
   add(sizeof(double2) * (size_t)tb * NC);                          // C block
   return b;
 }
@@ -379,12 +445,14 @@ static cudaError_t near_split(const ObsDev *d_o, const ObsDev &h, const NearGeom
   auto take = [&](size_t n) { char *p = sc; sc += (n + 255) & ~(size_t)255; return p; };
   int *erow = reinterpret_cast<int *>(take(sizeof(int) * tb));
   int *ecol = reinterpret_cast<int *>(take(sizeof(int) * g.W));
-  unsigned short *A = reinterpret_cast<unsigned short *>(take(sizeof(unsigned short) * 2 * (size_t)SD * tb * g.Sp));
-  unsigned short *B = reinterpret_cast<unsigned short *>(take(sizeof(unsigned short) * 2 * (size_t)SD * NC * g.Sp));
+  unsigned short *A = reinterpret_cast<unsigned short *>(
+      take(sizeof(unsigned short) * 2 * (size_t)SD * ((tb + 127) / 128 * 128) * g.Sp));
+  unsigned short *B = reinterpret_cast<unsigned short *>(
+      take(sizeof(unsigned short) * 2 * (size_t)SD * ((NC + 31) / 32 * 32) * g.Sp));
   double2 *C = reinterpret_cast<double2 *>(take(sizeof(double2) * (size_t)tb * NC));
-  const size_t gemm_smem = sizeof(__nv_bfloat16) * SD * 2 * (kGM + kGN) * kLDK;
+  const size_t gemm_smem = (size_t)kNearStages * near_stage_bytes<SD>();
   static size_t granted = 0;
-  cudaError_t e = ensure_dynamic_smem(near_gemm_kernel<SD>, gemm_smem, granted);
+  cudaError_t e = ensure_dynamic_smem(near_gemm_tc_kernel<SD>, gemm_smem, granted);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(U, 0, sizeof(double2) * (size_t)g.W * T, st);
   if (e != cudaSuccess) return e;
@@ -396,8 +464,8 @@ static cudaError_t near_split(const ObsDev *d_o, const ObsDev &h, const NearGeom
     for (int rep = 0; rep < g.nrep; ++rep) {
       near_rowexp_kernel<<<(nt + 7) / 8, 256, 0, st>>>(d_o, g, rep, t0, nt, erow);
       near_adigits_kernel<SD><<<dim3((g.Sp + 255) / 256, nt), 256, 0, st>>>(d_o, g, rep, t0, nt, erow, A);
-      near_gemm_kernel<SD><<<dim3((nt + kGM - 1) / kGM, (NC + kGN - 1) / kGN), 256, gemm_smem, st>>>(
-          g, nt, A, B, erow, ecol, C);
+      near_gemm_tc_kernel<SD><<<dim3((nt + 127) / 128, (NC + kNearCols - 1) / kNearCols), kNearThreads,
+                                gemm_smem, st>>>(g, nt, A, B, erow, ecol, C, h.status);
       near_combine_kernel<<<152 * 8, 256, 0, st>>>(g, rep, t0, nt, dirs, C, U, T);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
