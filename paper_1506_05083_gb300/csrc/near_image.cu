@@ -71,7 +71,9 @@ __device__ __forceinline__ void source_point(const ObsDev &o, int s, double &x, 
 // Per target row: exponent of an upper bound of |dG/dn| over all sources of
 // the representative image: |dG/dn| <= sqrt(1 + k^2 R^2) / (4 pi R^2), decreasing
 // in R, at the smallest distance. One extra bit of headroom keeps the leading
-// digit within 64.
+// digit within 64. The smallest squared distance is searched in FP32 (any
+// lower bound of it keeps the bound valid) and shrunk by 1% to cover FP32
+// rounding of the coordinates.
 __global__ void __launch_bounds__(256)
 near_rowexp_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, int nt,
                    int *__restrict__ erow) {
@@ -81,17 +83,20 @@ near_rowexp_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, i
   if (ti >= nt) return;
   double tx, ty, tz, nx, ny, nz;
   target_point(o, t0 + ti, tx, ty, tz, nx, ny, nz);
-  const double sx = g.rep_a[rep] * g.ex, sy = g.rep_b[rep] * g.ey;
-  double r2min = 1e300;
+  const float px = (float)(tx - g.rep_a[rep] * g.ex), py = (float)(ty - g.rep_b[rep] * g.ey);
+  const float pz = (float)tz;
+  float r2f = 3.0e38f;
   for (int s = lane; s < g.S; s += 32) {
-    double x, y, z;
-    source_point(o, s, x, y, z);
-    const double dx = tx - x - sx, dy = ty - y - sy, dz = tz - z;
-    r2min = fmin(r2min, fma(dx, dx, fma(dy, dy, dz * dz)));
+    const int j = s / o.P, l = s % o.P;
+    const double2 tw = o.tw_P[l];
+    const float rs = (float)o.src[2 * j];
+    const float dx = px - rs * (float)tw.x, dy = py + rs * (float)tw.y, dz = pz - (float)o.src[2 * j + 1];
+    r2f = fminf(r2f, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) r2min = fmin(r2min, __shfl_xor_sync(0xffffffffu, r2min, off));
+  for (int off = 16; off > 0; off >>= 1) r2f = fminf(r2f, __shfl_xor_sync(0xffffffffu, r2f, off));
   if (lane == 0) {
+    const double r2min = 0.99 * (double)r2f;
     const double bound = sqrt(1.0 + g.k * g.k * r2min) / r2min * kInv4Pi;
     erow[ti] = oz::key_exponent(oz::abs_key(bound)) + 1;
   }
