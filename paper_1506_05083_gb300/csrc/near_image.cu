@@ -74,15 +74,22 @@ __device__ __forceinline__ void source_point(const ObsDev &o, int s, double &x, 
 // digit within 64. The smallest squared distance is searched in FP32 (any
 // lower bound of it keeps the bound valid) and shrunk by 1% to cover FP32
 // rounding of the coordinates.
+// It also leaves, per target, the target shifted by minus the image offset and
+// the normal times 1/(4 pi) (ttab[ti][0..5]) for the kernel-value kernel.
 __global__ void __launch_bounds__(256)
 near_rowexp_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, int nt,
-                   int *__restrict__ erow) {
+                   int *__restrict__ erow, double *__restrict__ ttab) {
   const ObsDev &o = *od;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ti = blockIdx.x * 8 + warp;
   if (ti >= nt) return;
   double tx, ty, tz, nx, ny, nz;
   target_point(o, t0 + ti, tx, ty, tz, nx, ny, nz);
+  if (lane < 6) {
+    const double v[6] = {tx - g.rep_a[rep] * g.ex, ty - g.rep_b[rep] * g.ey, tz,
+                         nx * kInv4Pi, ny * kInv4Pi, nz * kInv4Pi};
+    ttab[(size_t)ti * 8 + lane] = v[lane];
+  }
   const float px = (float)(tx - g.rep_a[rep] * g.ex), py = (float)(ty - g.rep_b[rep] * g.ey);
   const float pz = (float)tz;
   float r2f = 3.0e38f;
@@ -106,26 +113,28 @@ near_rowexp_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, i
 // in tiles: per (128-target block, 16-source chunk) the 2 SD planes (part-major:
 // re digits 1..SD, then im) of 128 x 16, 4096 bytes each, element (r, kk) at
 // (r / 8) 256 + (kk / 8) 128 + (r % 8) 16 + (kk % 8) 2; zero beyond S.
+// Target data come from near_rowexp_kernel's table (shift and 1/(4 pi) folded
+// in), source coordinates from near_sources_kernel's, so a kernel value costs
+// only the distance, rsqrt, the table sin/cos and the products.
 template <int SD>
 __global__ void __launch_bounds__(256)
-near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, int nt,
-                    const int *__restrict__ erow, unsigned short *__restrict__ A) {
+near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int nt, const int *__restrict__ erow,
+                    const double *__restrict__ ttab, const double *__restrict__ sxyz,
+                    unsigned short *__restrict__ A) {
   const ObsDev &o = *od;
   const int ti = blockIdx.y;
   const int s = blockIdx.x * 256 + threadIdx.x;
   if (ti >= nt || s >= g.Sp) return;
   double2 kv = make_double2(0.0, 0.0);
   if (s < g.S) {
-    double tx, ty, tz, nx, ny, nz, x, y, z;
-    target_point(o, t0 + ti, tx, ty, tz, nx, ny, nz);
-    source_point(o, s, x, y, z);
-    const double dx = tx - x - g.rep_a[rep] * g.ex, dy = ty - y - g.rep_b[rep] * g.ey, dz = tz - z;
+    const double *tt = ttab + (size_t)ti * 8;
+    const double dx = tt[0] - sxyz[s], dy = tt[1] - sxyz[g.Sp + s], dz = tt[2] - sxyz[2 * g.Sp + s];
     const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
     const double inv = rsqrt(R2);
-    const double R = R2 * inv;
+    const double R = R2 * inv, kR = g.k * R;
     double sn, cs;
-    trig::sincos_ring_tab(g.k * R, o.tab_ring, &sn, &cs);   // table through L1
-    const double f = (nx * dx + ny * dy + nz * dz) * inv * inv * inv * kInv4Pi, kR = g.k * R;
+    trig::sincos_ring_tab(kR, o.tab_ring, &sn, &cs);   // table through L1
+    const double f = fma(tt[3], dx, fma(tt[4], dy, tt[5] * dz)) * (inv * inv) * inv;
     kv = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));   // (ikR - 1) e^{ikR}
   }
   const int e = erow[ti];
@@ -134,6 +143,19 @@ near_adigits_kernel(const ObsDev *__restrict__ od, NearGeom g, int rep, int t0, 
                         (r >> 3) * 128 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
   oz::split_store_n(kv.x, e, SD, dst, 2048);                   // planes 4096 bytes apart
   oz::split_store_n(kv.y, e, SD, dst + SD * 2048, 2048);
+}
+
+// Source coordinates, sxyz = [x | y | z] with Sp entries each.
+__global__ void __launch_bounds__(256)
+near_sources_kernel(const ObsDev *__restrict__ od, NearGeom g, double *__restrict__ sxyz) {
+  const ObsDev &o = *od;
+  for (int s = blockIdx.x * 256 + threadIdx.x; s < g.S; s += gridDim.x * 256) {
+    double x, y, z;
+    source_point(o, s, x, y, z);
+    sxyz[s] = x;
+    sxyz[g.Sp + s] = y;
+    sxyz[2 * g.Sp + s] = z;
+  }
 }
 
 // Exponent of each wave's strengths (max over all sources).
@@ -433,6 +455,8 @@ size_t near_image_scratch_bytes(const ObsDev &h, int W, double ex, double ey, in
   const int tb = block_targets(h, W, g.nrot);
   const int NC = g.nrot * W;
   add(sizeof(int) * tb);                                 // row exponents
+  add(sizeof(double) * 8 * tb);                          // target table
+  add(sizeof(double) * 3 * g.Sp);                        // source coordinates
   add(sizeof(int) * W);                                  // column exponents
   add(sizeof(unsigned short) * 2 * (size_t)slices * ((tb + 127) / 128 * 128) * g.Sp);   // A digit tiles
   add(sizeof(unsigned short) * 2 * (size_t)slices * ((NC + 31) / 32 * 32) * g.Sp);     // B digit tiles
@@ -449,6 +473,8 @@ static cudaError_t near_split(const ObsDev *d_o, const ObsDev &h, const NearGeom
   const int NC = g.nrot * g.W;
   auto take = [&](size_t n) { char *p = sc; sc += (n + 255) & ~(size_t)255; return p; };
   int *erow = reinterpret_cast<int *>(take(sizeof(int) * tb));
+  double *ttab = reinterpret_cast<double *>(take(sizeof(double) * 8 * tb));
+  double *sxyz = reinterpret_cast<double *>(take(sizeof(double) * 3 * g.Sp));
   int *ecol = reinterpret_cast<int *>(take(sizeof(int) * g.W));
   unsigned short *A = reinterpret_cast<unsigned short *>(
       take(sizeof(unsigned short) * 2 * (size_t)SD * ((tb + 127) / 128 * 128) * g.Sp));
@@ -462,13 +488,15 @@ static cudaError_t near_split(const ObsDev *d_o, const ObsDev &h, const NearGeom
   e = cudaMemsetAsync(U, 0, sizeof(double2) * (size_t)g.W * T, st);
   if (e != cudaSuccess) return e;
   near_sigexp_kernel<<<g.W, 256, 0, st>>>(g, sigma, ecol);
+  near_sources_kernel<<<(g.S + 255) / 256, 256, 0, st>>>(d_o, g, sxyz);
   near_bdigits_kernel<SD><<<dim3((g.Sp + 255) / 256, NC), 256, 0, st>>>(g, sigma, ecol, B);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int t0 = 0; t0 < T; t0 += tb) {
     const int nt = T - t0 < tb ? T - t0 : tb;
     for (int rep = 0; rep < g.nrep; ++rep) {
-      near_rowexp_kernel<<<(nt + 7) / 8, 256, 0, st>>>(d_o, g, rep, t0, nt, erow);
-      near_adigits_kernel<SD><<<dim3((g.Sp + 255) / 256, nt), 256, 0, st>>>(d_o, g, rep, t0, nt, erow, A);
+      near_rowexp_kernel<<<(nt + 7) / 8, 256, 0, st>>>(d_o, g, rep, t0, nt, erow, ttab);
+      near_adigits_kernel<SD><<<dim3((g.Sp + 255) / 256, nt), 256, 0, st>>>(d_o, g, nt, erow, ttab,
+                                                                              sxyz, A);
       near_gemm_tc_kernel<SD><<<dim3((nt + 127) / 128, (NC + kNearCols - 1) / kNearCols), kNearThreads,
                                 gemm_smem, st>>>(g, nt, A, B, erow, ecol, C, h.status);
       near_combine_kernel<<<152 * 8, 256, 0, st>>>(g, rep, t0, nt, dirs, C, U, T);
