@@ -4,9 +4,9 @@
 //
 // R (cols x cols, upper triangular, real diagonal) is taken in 32-column
 // blocks from the bottom. For block b (rows/columns r0 = 32 b .. r0 + nb):
-//   1. the 32 x 32 diagonal block is solved in FP64, one warp per RHS column
-//      (as in trsm_kernel: a division-free elimination with the block's
-//      reciprocal diagonal);
+//   1. the 32 x 32 diagonal block is solved in FP64, one warp per RHS column,
+//      after scaling the block's rows and the RHS by the reciprocal diagonal
+//      (a unit-diagonal elimination: four FMAs per step);
 //   2. the rows above are updated, Y(0:r0, :) -= R(0:r0, block) X_b, as a
 //      digit GEMM: R's rows are split once, at the end of the build
 //      (r_digits_kernel, one exponent per row and block, balanced digits,
@@ -120,19 +120,26 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
     }
     if (tid < kTB) sm.rinv[tid] = tid < nb ? 1.0 / R[(size_t)(r0 + tid) * ld + r0 + tid].x : 0.0;
     __syncthreads();
+    // rows of the block scaled by the reciprocal (real) diagonal: the solve
+    // then runs on a unit-diagonal triangle and each step is four FMAs
+    for (int e = tid; e < kTB * kTB; e += kTT) {
+      const int r = e % kTB, c = e / kTB;
+      if (r < c) {
+        const double inv = sm.rinv[r];
+        sm.Rb[r][c] = make_double2(sm.Rb[r][c].x * inv, sm.Rb[r][c].y * inv);
+      }
+    }
+    __syncthreads();
     // 1. diagonal block in FP64, warp c solves column c
     if (warp < ncols) {
       const int c = warp;
+      const double inv = sm.rinv[lane];
       double2 y = sm.Yb[lane][c];
+      y = make_double2(y.x * inv, y.y * inv);
       for (int rr = nb - 1; rr >= 0; --rr) {
-        double2 x = make_double2(0.0, 0.0);
-        if (lane == rr) {
-          const double inv = sm.rinv[rr];
-          y = make_double2(y.x * inv, y.y * inv);
-          x = y;
-        }
-        x.x = __shfl_sync(0xffffffffu, x.x, rr);
-        x.y = __shfl_sync(0xffffffffu, x.y, rr);
+        double2 x;
+        x.x = __shfl_sync(0xffffffffu, y.x, rr);              // final once the rows below are done
+        x.y = __shfl_sync(0xffffffffu, y.y, rr);
         if (lane < rr) {
           const double2 rv = sm.Rb[lane][rr];
           y = make_double2(fma(-rv.x, x.x, fma(rv.y, x.y, y.x)), fma(-rv.x, x.y, fma(-rv.y, x.x, y.y)));
