@@ -37,12 +37,14 @@ def test_split_fill_parity(name):
     assert err < 1e-13, err
 
 
-@pytest.mark.parametrize("P,q", [(180, 0), (240, 0), (8, 1800)])
+@pytest.mark.parametrize("P,q", [(180, 0), (240, 0), (8, 1728), (8, 1800)])
 def test_split_fill_parity_shapes(P, q):
     """Mode counts that fill the tensor-core accumulators (P = 180: 48 modes per
-    parity, N = 48; P = 240: 64, every TMEM column), and a contraction too long
-    for exact FP32 group sums over one pass (q = 1800: 451 folded nodes), which
-    takes the mma.sync transform with periodic int64 folds."""
+    parity, N = 48; P = 240: 64, every TMEM column), the longest contraction the
+    tcgen05 transform takes in one pass (q = 1728: 433 folded nodes, padded to
+    448), and one too long for exact FP32 group sums over one pass (q = 1800:
+    451 folded nodes), which takes the mma.sync transform with periodic int64
+    folds."""
     from paper_1506_05083_gb300 import axi
     wl = synth.small_case(seed=29, k=3.0, M=24, N=20, P=P, q=q)
     ob = wl.obstacles[0]
