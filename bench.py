@@ -27,6 +27,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -135,7 +136,9 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the samples go to $AXI_BENCH_OUT (default: the system temp directory)
+        out = os.environ.get("AXI_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
