@@ -207,6 +207,23 @@ def cpu_baseline_line(ob, dirs, steps=1):
                       f"{dirs.shape[0]} waves (numpy FP64, BLAS threads = host cores)"}
 
 
+def slowest_rank_ms(ms, device):
+    """Max over ranks of a per-rank step time: the slowest rank bounds the job.
+    Identity without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, flops_per_rank, ms):
+    """Whole-job TFLOP/s: every rank's work over the slowest rank's time."""
+    return ws * flops_per_rank / (ms * 1e-3) / 1e12
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -351,12 +368,8 @@ def main():
     build_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
     apply_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
     fill_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
-    ms = float(np.mean(step_ms))
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * (qr_fl + ap_fl) / (ms * 1e-3) / 1e12
+    ms = slowest_rank_ms(float(np.mean(step_ms)), dev)
+    value = job_value(ws, qr_fl + ap_fl, ms)
 
     # end to end through the public API with host buffers: H2D of the wave
     # directions from pinned memory, build + apply, D2H of the coefficients
@@ -373,7 +386,7 @@ def main():
         b.record(stream)
         b.synchronize()
         e2e.append(a.elapsed_time(b))
-    e2e_ms = float(np.mean(e2e[1:]))
+    e2e_ms = slowest_rank_ms(float(np.mean(e2e[1:])), dev)
     h2d = dirs_host.numel() * 8
     d2h = coef_host.numel() * 16
 
@@ -395,7 +408,7 @@ def main():
             "build_ms": float(np.mean(build_ms)),
             "build_tflops": qr_fl / (np.mean(build_ms) * 1e-3) / 1e12,
             "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
-            "e2e": {"value": ws * (qr_fl + ap_fl) / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "e2e": {"value": job_value(ws, qr_fl + ap_fl, e2e_ms), "unit": "TFLOP/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": {"kernel": ("fill_samples_kernel + fill_gemm_tc_kernel (FP64 samples, "
                                     "tcgen05 transform)") if args.prec == "split"
