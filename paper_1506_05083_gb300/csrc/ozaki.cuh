@@ -223,25 +223,7 @@ __host__ __device__ constexpr int unfold1_shift() {
   return -7 * (S + 1) + ((7 * (S + 1) - 28) - ((7 * (S + 1) - 28) < 28 ? (7 * (S + 1) - 28) : 28));
 }
 
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {
-  return *reinterpret_cast<const uint32_t *>(p);
-}
 __device__ __forceinline__ uint32_t neg2(uint32_t v) { return v ^ 0x80008000u; }
-
-// A fragment (16 x 16, row-major, k contiguous) at tile origin `base` with row stride ld.
-__device__ __forceinline__ void load_a(const __nv_bfloat16 *base, int ld, int lane, uint32_t (&a)[4]) {
-  const int g = lane >> 2, t = lane & 3;
-  a[0] = ld32(base + g * ld + 2 * t);
-  a[1] = ld32(base + (g + 8) * ld + 2 * t);
-  a[2] = ld32(base + g * ld + 8 + 2 * t);
-  a[3] = ld32(base + (g + 8) * ld + 8 + 2 * t);
-}
-// B fragment (16 x 8, stored [n][k] with k contiguous) at origin `base` with n stride ld.
-__device__ __forceinline__ void load_b(const __nv_bfloat16 *base, int ld, int lane, uint32_t (&b)[2]) {
-  const int g = lane >> 2, t = lane & 3;
-  b[0] = ld32(base + g * ld + 2 * t);
-  b[1] = ld32(base + g * ld + 8 + 2 * t);
-}
 
 // ldmatrix: four 8x8 b16 matrices from shared memory; lane l gives the row
 // address of row (l mod 8) of matrix (l / 8), and receives in r[m] the pair
