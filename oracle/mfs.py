@@ -29,7 +29,10 @@ which implements them independently):
 
 Pins (tests/test_oracle_pins.py) for each function:
   curve/geometry      closed-form sphere points, finite-difference normals,
-                      proxies inside the body, Taylor check of complexification
+                      proxies inside the body, Taylor check of complexification;
+                      cup: both ends on the axis with z' = 0, arc radii 1 +- a,
+                      rim within a of the opening angle b, normals away from
+                      the shell (Fig. 2(c) caption, Sec. 3)
   ring_samples        finite-difference normal derivative of G
   fill                adaptive quadrature (scipy.integrate.quad) of the ring
                       integral; Laplace k=0, n=0 elliptic-K closed form;
@@ -41,7 +44,9 @@ Pins (tests/test_oracle_pins.py) for each function:
                       brute-force 3D point-source MFS with q = P;
                       rotation covariance; reciprocity
   transmission        k_minus = k null case (u = 0 outside)
-  near_image_sum      direct 3D summation over explicit image points
+  near_image_sum      direct 3D summation over explicit image points; the
+                      Bloch phases by the coherent zeroth Bragg order of the
+                      eight images at a distant target (eq. per)
 """
 from __future__ import annotations
 
@@ -292,7 +297,7 @@ def factor_operator(ob, coll, src, src_ext):
 
 
 # ----------------------------------------------------------------------------
-# A4-A6: apply (Sec. 3 eq. fhatquad; Sec. 4.4 application of A_n^+; Sec. 4.2)
+# A4-A6: apply (Sec. 3 eq. fhatquad; Sec. 4.2 application of A_n^+; Sec. 4.1)
 # ----------------------------------------------------------------------------
 
 def incident_samples(ob, coll, dirs):
@@ -329,7 +334,7 @@ def rhs_modes(f):
 
 
 def solve_modes(ob, factors, fhat):
-    """c_n = R^{-1} (Q^H fhat_n)_{1:cols} for every mode n (Sec. 4.4: apply the
+    """c_n = R^{-1} (Q^H fhat_n)_{1:cols} for every mode n (Sec. 4.2: apply the
     factors, never an explicit inverse); modes +-n use the factors of |n|.
     fhat [W][P][rows] -> coef [W][P][cols].
     """
@@ -345,7 +350,7 @@ def solve_modes(ob, factors, fhat):
 
 
 def point_strengths(coef, qe):
-    """Ring -> point sources (Sec. 4.2): sigma_{j,l} = (1/qe) sum_n c_nj
+    """Ring -> point sources (Sec. 4.1): sigma_{j,l} = (1/qe) sum_n c_nj
     e^{i n phi_l}, phi_l = 2 pi l / qe.  coef [W][P][N] -> [W][N][qe].
     """
     W, P, N = coef.shape
@@ -395,7 +400,7 @@ def potential(ob, src, coef, targets, qe=None, k=None, normals=None):
 
 
 def near_image_sum(ob, coll, src, coef, dirs, lattice, target_idx=None):
-    """A7 (Sec. 4.2, action of A_else): normal derivative at the ring nodes
+    """A7 (Sec. 4.1, action of A_else): normal derivative at the ring nodes
     x_{m,l} (rho_m, phi_l = 2 pi l / P, z_m) of the eight phased images of the
     point sources (q = P), omitting the central copy:
       U_w(x_t) = sum_{(a,b) != (0,0)} alpha_w^a beta_w^b

@@ -143,7 +143,7 @@ def test_q_rule_converged():
     assert np.abs(A1 - A2).max() < 1e-14 * np.abs(A1).max()
 
 
-# --- least squares (Sec. 3 eq. linsys; Sec. 4.4) -----------------------------
+# --- least squares (Sec. 3 eq. linsys; Sec. 4.2) -----------------------------
 
 def test_householder_against_lapack():
     rng = np.random.default_rng(0)
@@ -310,3 +310,74 @@ def test_near_image_sum_translation():
             ph = np.exp(1j * ob.k * (d[:, 0] * a * lat[0] + d[:, 1] * b * lat[1]))
             ref += ph[:, None] * O.potential(ob, src, c, X - shift, normals=Nn)
     assert np.abs(U - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+# --- cup generating curve (Fig. 2(c) caption; Sec. 3 smoothness on the axis) --
+
+def test_cup_curve_facts():
+    """Facts the cup's description fixes, independent of how the curve is coded:
+    both ends lie on the axis (rho = 0) with z' = 0 there to rounding (Sec. 3
+    says the cup meets this to double precision because erf saturates); away
+    from the rim the outer arc has radius 1 + a = 1.2 and the inner arc
+    1 - a = 0.8 (half-thickness a); the rim, the extreme polar angle of the
+    curve, sits within a of the opening half-angle b; outward normals point
+    away from the shell material (radially out on the outer arc, towards the
+    centre on the inner arc)."""
+    for b in (math.pi / 2, math.pi / 6):
+        ob = synth.cup(b=b)
+        a = ob.params[0]
+        zeta, dz = O.curve(ob, np.array([0.0, math.pi]))
+        assert np.abs(zeta.imag).max() < 1e-15                      # rho = 0 at both ends
+        assert np.abs(dz.real).max() < 1e-15                        # z'(0) = z'(pi) = 0
+        assert np.abs(np.abs(zeta) - np.array([1 + a, 1 - a])).max() < 1e-15
+        assert np.all(zeta.real < 0)                                # closed end at -z (opening at +z)
+        t = np.linspace(0.0, math.pi, 20001)
+        zt, _ = O.curve(ob, t)
+        far = np.abs(t - math.pi / 2) >= 5 * a
+        outer, inner = far & (t < math.pi / 2), far & (t > math.pi / 2)
+        assert np.abs(np.abs(zt[outer]) - (1 + a)).max() < 1e-12
+        assert np.abs(np.abs(zt[inner]) - (1 - a)).max() < 1e-12
+        assert zt.imag[1:-1].min() > 0                              # rho > 0 between the ends
+        theta = np.arctan2(np.abs(zt.imag), zt.real)                # polar angle from +z
+        assert abs(theta.min() - b) < a
+        # collocation normals: radial on the outer arc, anti-radial on the inner
+        ob_c = synth.cup(b=b, M=200, N=160)
+        coll, _, _ = O.geometry(ob_c)
+        tm = math.pi * (np.arange(ob_c.M) + 0.5) / ob_c.M
+        rad = coll[:, :2] / np.hypot(coll[:, 0], coll[:, 1])[:, None]
+        fo = (tm < math.pi / 2 - 6 * a)
+        fi = (tm > math.pi / 2 + 6 * a)
+        assert np.abs(coll[fo, 2:] - rad[fo]).max() < 1e-12
+        assert np.abs(coll[fi, 2:] + rad[fi]).max() < 1e-12
+
+
+# --- Bloch phases of the near images (eqs. per, bloch; A_else in Sec. 4.1) ----
+
+@pytest.mark.parametrize("specular", [False, True])
+def test_near_image_phases_zeroth_bragg_order(specular):
+    """Quasi-periodicity (eq. per) makes the copy of the obstacle at lattice
+    offset (a e_x, b e_y) radiate with the Bloch factor alpha^a beta^b of the
+    incident wave, and such an array radiates coherently in its zeroth Bragg
+    orders: the directions whose components along the lattice plane equal the
+    incident direction's (straight through, and the specular reflection). So at
+    a very distant target in such a direction, the eight-image sum of the
+    target-normal derivative equals 8 times the central copy's own
+    contribution, (i k e^{ikR}/R) F_0(xhat) with F_0 the far field. A wrong
+    sign of either phase exponent, or alpha and beta exchanged, breaks it."""
+    ob, coll, src, srcx = _small(k=2.0, M=20, N=16, P=12)
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    # incident direction with azimuth on a ring node (phi_1 = 2 pi / P, 30
+    # degrees: d_x != d_y, so exchanging alpha and beta shows) so the far
+    # target can sit at node l = 1 of a one-row "collocation" array
+    th, phi = 0.7, 2 * math.pi / ob.P
+    d = np.array([[math.sin(th) * math.cos(phi), math.sin(th) * math.sin(phi), math.cos(th)]])
+    c = O.solve_modes(ob, fac, O.rhs_modes(O.incident_samples(ob, coll, d)))
+    xz = -math.cos(th) if specular else math.cos(th)
+    xhat = np.array([math.sin(th) * math.cos(phi), math.sin(th) * math.sin(phi), xz])
+    R = 1e8
+    far = np.array([[R * math.sin(th), R * xz, math.sin(th), xz]])  # rho, z, n_rho, n_z
+    lat = (3.1, 2.7)
+    U = O.near_image_sum(ob, far, src, c, d, lat, target_idx=np.array([1]))[0, 0]
+    F0 = O.far_field(ob, src, c, xhat[None])[0, 0]
+    ratio = U / (1j * ob.k * np.exp(1j * ob.k * R) / R * F0)
+    assert abs(ratio - 8.0) < 1e-4, ratio
