@@ -12,12 +12,12 @@
  *                    Householder QR (Sec. 3, eq. linsys: a backward-stable
  *                    dense least-squares solve per mode);
  *   apply_operator : FFT of boundary data to modes (eq. fhatquad), Q^H and
- *                    triangular solve per mode (Sec. 4.4, never an explicit
+ *                    triangular solve per mode (Sec. 4.2, never an explicit
  *                    inverse), optional inverse FFT to point strengths
- *                    (Sec. 4.2);
+ *                    (Sec. 4.1);
  *   eval_field     : scattered potential, normal derivative or far field of
  *                    the coefficients, optionally summed over the eight
- *                    phased nearest lattice images (Sec. 4.2, A_else).
+ *                    phased nearest lattice images (Sec. 4.1, A_else).
  *
  * Conventions (all entry points):
  *   - Every call returns an axi_status; nothing aborts, throws or prints.
@@ -210,12 +210,12 @@ axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_
 
 /*
  * axi_apply_operator -- apply A_0^+ of obstacle `obs` to W data sets
- * (eq. fhatquad with q = P; Sec. 4.4 application of the factors):
+ * (eq. fhatquad with q = P; Sec. 4.2 application of the factors):
  *   fhat_n = (1/P) sum_l f_l e^{-2 pi i n l/P};  c_n = R^{-1} (Q^H fhat_n)_{1:cols}.
  *   d_f      : device [W][rows][P] samples on the ring nodes.
  *   d_coef   : out, device [W][P][cols], mode n at index n mod P.
  *   d_sigma  : out or NULL, device [W][cols][P] point strengths
- *              sigma_jl = (1/P) sum_n c_nj e^{2 pi i n l/P} (Sec. 4.2).
+ *              sigma_jl = (1/P) sum_n c_nj e^{2 pi i n l/P} (Sec. 4.1).
  *   d_scratch, scratch_bytes : >= axi_apply_workspace_bytes(op, obs, W).
  * Errors: AXI_ERR_ARG, AXI_ERR_WORKSPACE, AXI_ERR_CUDA.
  */
@@ -261,14 +261,14 @@ typedef enum {
 /*
  * axi_eval_field -- evaluate the exterior scattered field of coefficients
  * d_coef [W][P][cols] of obstacle `obs` from its point strengths
- * (sigma over qe = P azimuthal nodes, Sec. 4.2):
+ * (sigma over qe = P azimuthal nodes, Sec. 4.1):
  *   POTENTIAL     u(x)  = sum_{j,l} G_k(x, y_jl) sigma_jl
  *   NORMAL_DERIV  du/dn = sum_{j,l} dG_k/dn_x(x, y_jl) sigma_jl
  *   FAR_FIELD     F(xh) = (1/4pi) sum_{j,l} e^{-i k xh.y_jl} sigma_jl.
  * With lattice != NULL the sum runs over the eight phased nearest images
  * y_jl + a e_x + b e_y, (a, b) in {-1,0,1}^2 \ {(0,0)}, weighted by
  * alpha^a beta^b, alpha = e^{i k d_x e_x}, beta = e^{i k d_y e_y} (eq. bloch,
- * Sec. 4.2 A_else) with d read per wave from d_dirs [W][3].
+ * Sec. 4.1 A_else) with d read per wave from d_dirs [W][3].
  *   d_targets [T][3], d_normals [T][3] (NORMAL_DERIV), d_out [W][T].
  *   d_scratch : >= W * cols * P * 16 bytes (point strengths).
  */
@@ -282,7 +282,7 @@ axi_status axi_eval_field(const axi_operator *op, int32_t obs, int32_t W,
                           void *stream);
 
 /*
- * axi_near_image_sum -- A_else of Sec. 4.2 for one obstacle: the normal
+ * axi_near_image_sum -- A_else of Sec. 4.1 for one obstacle: the normal
  * derivative, at every ring node x_t = (rho_m, 2 pi l / P, z_m) with its
  * normal, of the eight phased nearest lattice images of the point sources
  * (P per proxy ring, strengths from d_coef as in axi_eval_field):

@@ -1,6 +1,6 @@
 // Mixed-radix (4, 2, 3, 5) in-place FFT of one length-P sequence by one warp,
 // FP64, for the transforms of the apply: boundary data to modes
-// (eq. fhatquad with q = P) and coefficients to point strengths (Sec. 4.2).
+// (eq. fhatquad with q = P) and coefficients to point strengths (Sec. 4.1).
 //
 // Decimation in frequency: with P = r_1 r_2 ... r_m, stage s splits every
 // block of length L into r = r_s interleaved sub-sequences, applies the

@@ -4,10 +4,10 @@
 // M x P ring nodes (rho_m, phi_l = 2 pi l / P, z_m) that the RHS transform
 // (eq. fhatquad with q = P) consumes.
 //
-// Field evaluation (Sec. 4.2): each ring source of mode n is replaced by P
+// Field evaluation (Sec. 4.1): each ring source of mode n is replaced by P
 // point sources with strengths sigma_jl (the inverse transform of c_nj over
 // n), so u(x) = sum_{j,l} G_k(x, y_jl) sigma_jl. With a lattice the sum runs
-// over the eight phased nearest images, the action A_else of Sec. 4.2 done by
+// over the eight phased nearest images, the action A_else of Sec. 4.1 done by
 // direct summation instead of an FMM.
 #include "axi_internal.h"
 #include "trig.cuh"

@@ -1,4 +1,4 @@
-// Step A7: the eight phased nearest-image sums at all ring nodes (Sec. 4.2,
+// Step A7: the eight phased nearest-image sums at all ring nodes (Sec. 4.1,
 // the action of A_else), as a split-precision GEMM on tensor cores.
 //
 //   U_w(x_t) = sum_{img != 0} ph_w(img) sum_s dG/dn_t(x_t, y_s + d_img) sigma_w(s),

@@ -2,7 +2,7 @@
 // matrix, and application of the factors to right-hand sides.
 //
 // Sec. 3 (eq. linsys) solves each mode's rectangular system by a dense
-// backward-stable least-squares method; Sec. 4.4 applies the factors, never
+// backward-stable least-squares method; Sec. 4.2 applies the factors, never
 // an explicit inverse. We use unpivoted Householder QR with the LAPACK
 // reflector convention: H = I - tau v v^H, v[0] = 1, and H^H maps the column
 // (alpha; x) to (beta; 0) with real beta = -sign(Re alpha) ||(alpha; x)||,
@@ -690,7 +690,7 @@ __global__ void scatter_coef_kernel(const ObsDev *__restrict__ od, int W,
   for (int j = threadIdx.x; j < cols; j += blockDim.x) dst[j] = src[j];
 }
 
-// sigma[w][j][l] = (1/P) sum_n c[w][n][j] e^{+2 pi i n l / P}  (Sec. 4.2)
+// sigma[w][j][l] = (1/P) sum_n c[w][n][j] e^{+2 pi i n l / P}  (Sec. 4.1)
 __global__ void __launch_bounds__(kThreads)
 point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__restrict__ coef,
                       double2 *__restrict__ sigma) {

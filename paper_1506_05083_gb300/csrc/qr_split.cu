@@ -3,7 +3,7 @@
 // The trailing update of the blocked Householder QR and the Q^H of the apply
 // both compute, for one panel's reflectors V (K x nb, unit lower trapezoidal)
 // and compact-WY factor T,
-//     X <- X - V (T^H (V^H X))         (Sec. 3 eq. linsys; Sec. 4.4),
+//     X <- X - V (T^H (V^H X))         (Sec. 3 eq. linsys; Sec. 4.2),
 // on a tile of kTN target columns. Here the two GEMMs run as Ozaki slice
 // products on BF16 mma.sync (ozaki.cuh) and T^H in FP64:
 //   digits  the panel's reflectors are split once per factorisation

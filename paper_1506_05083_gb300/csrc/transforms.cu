@@ -1,7 +1,7 @@
 // FFT-based transforms of the apply (FP64), replacing the direct O(P^2) sums
 // when P = 2^a 3^b 5^c:
 //   boundary data to modes   fhat_n = (1/P) sum_l f_l e^{-2 pi i n l / P}  (eq. fhatquad, q = P)
-//   modes to point strengths sigma_l = (1/P) sum_n c_n e^{+2 pi i n l / P}  (Sec. 4.2)
+//   modes to point strengths sigma_l = (1/P) sum_n c_n e^{+2 pi i n l / P}  (Sec. 4.1)
 // One warp per sequence (fft.cuh); 8 sequences per CTA.
 #include "axi_internal.h"
 #include "fft.cuh"

@@ -1,4 +1,4 @@
-// Split-precision back substitution R X = Y of the apply (Sec. 4.4): the
+// Split-precision back substitution R X = Y of the apply (Sec. 4.2): the
 // blocked substitution of trsm_kernel with its off-diagonal updates on BF16
 // tensor cores.
 //

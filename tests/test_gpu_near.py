@@ -1,4 +1,4 @@
-"""Near-image sum (the action of A_else, Sec. 4.2) at every ring node: the
+"""Near-image sum (the action of A_else, Sec. 4.1) at every ring node: the
 split-precision GEMM path against the direct FP64 path (all targets) and both
 against the oracle's direct 3D sum (target subsample). Lattices with and
 without the 90-degree symmetry, and P not divisible by 4."""
