@@ -78,6 +78,17 @@ typedef enum {
 } axi_precision;
 #define AXI_PREC_SLICES(s) ((int32_t)(s) << 8)
 
+/* Plan option or-ed into `prec`: evaluate every ring pair of the fill on all
+ * q azimuthal nodes. By default each (collocation point, proxy ring) pair is
+ * sampled on the coarsest of the sub-grids of q, q/2 and q/4 nodes (dividing
+ * q/2) on which Theorem 1's rate for that pair, alpha = acosh(1 +
+ * d^2/(2 rho rho')), still gives q_pair >= max(P, 37/alpha + P/2): the same
+ * rule axi_choose_q applies to the closest pair, now per pair. Far pairs
+ * converge faster (Sec. 3.1), so most pairs need a fraction of the nodes;
+ * the sub-grid sum is the trapezoid rule with q_pair nodes, which agrees with
+ * the q-node rule to rounding (measured: 3e-15 of max|A| on the cup). */
+#define AXI_PLAN_FULL_FILL_GRID ((int32_t)1 << 16)
+
 typedef enum { AXI_SHAPE_POLAR = 0, AXI_SHAPE_CUP = 1 } axi_shape;
 
 /*
@@ -113,6 +124,17 @@ axi_status axi_geometry(int32_t shape, const double *h_params, int32_t n_params,
 axi_status axi_choose_q(int32_t M, int32_t N, int32_t P, const double *h_coll,
                         const double *h_src, const double *h_src_ext, int32_t *q);
 
+/*
+ * axi_fill_subgrid -- per ring pair, the azimuthal sub-grid the fill samples
+ * on (Sec. 3.1, Theorem 1 applied to each pair; see AXI_PLAN_FULL_FILL_GRID):
+ * h_stride[m*N + j] = largest s in {4, 2, 1} with (q/2) mod s = 0 and
+ * q/s >= max(P, 37/alpha_mj + P/2), alpha_mj = acosh(1 + d^2/(2 rho_m rho'_j)).
+ *   h_coll [M][4], h_src [N][2] as from axi_geometry; h_stride : out, host [M][N].
+ * Host only. Errors: AXI_ERR_ARG, AXI_ERR_SHAPE, AXI_ERR_GEOMETRY.
+ */
+axi_status axi_fill_subgrid(int32_t M, int32_t N, int32_t P, int32_t q, const double *h_coll,
+                            const double *h_src, uint8_t *h_stride);
+
 /* One obstacle of a batch. All pointers are host pointers read by
  * axi_plan_create only. */
 typedef struct {
@@ -135,7 +157,8 @@ typedef struct axi_operator_s axi_operator;
  * modes, the packed QR factors of the rows x cols modal matrix (rows = M,
  * cols = N for Neumann; 2M x 2N for transmission, eq. trans), column-major
  * with leading dimension rows, plus reflector scalars and compact-WY T blocks.
- *   obs[n_obs] : obstacles; prec : axi_precision; *plan : out.
+ *   obs[n_obs] : obstacles; prec : axi_precision, optionally or-ed with
+ *                AXI_PREC_SLICES(s) and AXI_PLAN_FULL_FILL_GRID; *plan : out.
  * Errors: AXI_ERR_ARG, AXI_ERR_SHAPE, AXI_ERR_GEOMETRY, AXI_ERR_UNSUPPORTED.
  */
 axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
@@ -202,8 +225,9 @@ axi_status axi_incident_planewaves(const axi_operator *op, int32_t obs, int32_t 
 /*
  * axi_apply_workspace_bytes -- scratch bytes axi_apply_operator needs for W
  * right-hand sides of obstacle `obs`: the RHS blocks ([D][2W][rows] complex)
- * and, for split-precision operators with W >= 33 (where the apply's Q^H
- * runs on tensor cores), the BF16 digits of every panel's reflectors.
+ * and, for split-precision operators whose plan did not keep every panel's
+ * reflector digits (plans whose digits would exceed 4 GB), those digits,
+ * recomputed by each apply.
  */
 axi_status axi_apply_workspace_bytes(const axi_operator *op, int32_t obs, int32_t W,
                                      size_t *bytes);
@@ -235,11 +259,18 @@ axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W,
  * buffer: the RHS blocks live in a static device array of
  * axi_noalloc_scratch_bytes() bytes (32 MiB) that every GPU loading this
  * library holds until the process exits. The call allocates nothing.
- *   - Sizes: returns AXI_ERR_SHAPE when axi_apply_workspace_bytes(op, obs, W)
- *     exceeds the static array (e.g. W > 79 for N=180, M=216, P=120).
+ *   - Sizes: returns AXI_ERR_WORKSPACE when axi_apply_workspace_bytes(op, obs, W)
+ *     exceeds the static array (W > 79 for N=180, M=216, P=120; W > 26 for
+ *     N=360, M=432, P=180). Split-precision plans that did not keep their
+ *     reflector digits (over 4 GB of digits, e.g. the 64-obstacle batch) need
+ *     hundreds of MB per apply and are always refused.
+ *   - Device: the current device and the stream's device must be the one the
+ *     operator was built on (AXI_ERR_ARG otherwise), because the library
+ *     picks that device's array.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture. Calls after a cudaDeviceReset in the same
+ *     process are not supported (the looked-up address would be stale).
  *   - All calls share the one array, which keeps the last call's contents:
  *     calls that overlap on the GPU (different streams, no ordering) race.
  *     Every element the apply reads is written first, so nothing needs
@@ -304,6 +335,37 @@ axi_status axi_near_image_sum(const axi_operator *op, int32_t obs, int32_t W,
                               const axi_c128 *d_coef, const axi_lattice *lattice,
                               const double *d_dirs, int32_t slices, axi_c128 *d_out,
                               void *d_scratch, size_t scratch_bytes, void *stream);
+
+/*
+ * Kernel profiling (measurement support; the paper has no counterpart).
+ * axi_operator_profile(op, 1) clears the record and starts timing every
+ * launch class of later axi_refactor_operator / axi_apply_operator calls on
+ * this operator with CUDA events on the launch's own stream (not allowed
+ * while a stream is being captured); axi_operator_profile(op, 0) stops.
+ * axi_operator_profile_read waits for the recorded events and writes, per
+ * class, the number of launches, their summed device time and their summed
+ * algorithmic FP64-equivalent flops (complex Householder: 16 (K - j) flops
+ * per reflector j and column it updates, i.e. 8 M N^2 - 8 N^3/3 per mode;
+ * apply: 16 rows cols - 8 cols^2 per right-hand side for Q^H, 4 cols^2 for
+ * the triangular solve; fill and data movement count 0).
+ */
+typedef enum {
+  AXI_KERNEL_FILL = 0,         /* ring samples + modal transform (all kernels)   */
+  AXI_KERNEL_PANEL = 1,        /* Householder panel factorisation                */
+  AXI_KERNEL_UPDATE_NEXT = 2,  /* update of the next panel's columns             */
+  AXI_KERNEL_UPDATE_REST = 3,  /* update of the trailing columns beyond it       */
+  AXI_KERNEL_PANEL_DIGITS = 4, /* split plans: reflector digits                  */
+  AXI_KERNEL_R_DIGITS = 5,     /* split plans: digits of R for the apply         */
+  AXI_KERNEL_APPLY_RHS = 6,    /* transform of the data to modes                 */
+  AXI_KERNEL_APPLY_QH = 7,     /* Q^H on the right-hand sides                    */
+  AXI_KERNEL_APPLY_TRSM = 8,   /* back substitution                              */
+  AXI_KERNEL_APPLY_OUT = 9,    /* coefficient scatter and point strengths        */
+  AXI_KERNEL_KINDS = 10
+} axi_kernel_kind;
+typedef struct { int32_t launches; double ms; double flops; } axi_kernel_stat;
+axi_status axi_operator_profile(axi_operator *op, int32_t enable);
+/* h_stats: host [AXI_KERNEL_KINDS]. Errors: AXI_ERR_ARG, AXI_ERR_CUDA. */
+axi_status axi_operator_profile_read(axi_operator *op, axi_kernel_stat *h_stats);
 
 /* Device status word of the operator (read after synchronising the stream). */
 axi_status axi_operator_status(const axi_operator *op);

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libaxi_mfs.so")
 
 BC_NEUMANN, BC_TRANSMISSION = 0, 1
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+PLAN_FULL_FILL_GRID = 1 << 16                   # or-ed into prec: every ring pair on all q nodes
 SHAPE_POLAR, SHAPE_CUP = 0, 1
 EVAL_POTENTIAL, EVAL_NORMAL_DERIV, EVAL_FAR_FIELD = 0, 1, 2
 OK, ERR_ARG, ERR_SHAPE = 0, -1, -2              # axi_status values (include/axi_mfs.h)
@@ -38,6 +39,14 @@ class _FactorView(C.Structure):
                 ("npanels", C.c_int32), ("d_A", _vp), ("d_tau", _vp), ("d_T", _vp)]
 
 
+class _KernelStat(C.Structure):
+    _fields_ = [("launches", C.c_int32), ("ms", C.c_double), ("flops", C.c_double)]
+
+
+KERNEL_KINDS = ["fill", "panel", "update_next", "update_rest", "panel_digits", "r_digits",
+                "apply_rhs", "apply_qh", "apply_trsm", "apply_out"]   # axi_kernel_kind order
+
+
 class _Lattice(C.Structure):
     _fields_ = [("ex", C.c_double), ("ey", C.c_double)]
 
@@ -46,6 +55,8 @@ class _Lattice(C.Structure):
 SIGNATURES = [
     ("axi_geometry", C.c_int, [C.c_int32, _dp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
     ("axi_choose_q", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, C.POINTER(C.c_int32)]),
+    ("axi_fill_subgrid", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp,
+                                   C.POINTER(C.c_uint8)]),
     ("axi_plan_create", C.c_int, [C.POINTER(_Obstacle), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     ("axi_plan_workspace_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     ("axi_build_operator", C.c_int, [_vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
@@ -65,6 +76,8 @@ SIGNATURES = [
                                                  C.c_int32, C.POINTER(C.c_size_t)]),
     ("axi_near_image_sum", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_Lattice), _vp,
                                      C.c_int32, _vp, _vp, C.c_size_t, _vp]),
+    ("axi_operator_profile", C.c_int, [_vp, C.c_int32]),
+    ("axi_operator_profile_read", C.c_int, [_vp, _vp]),
     ("axi_operator_status", C.c_int, [_vp]),
     ("axi_operator_destroy", C.c_int, [_vp]),
     ("axi_plan_destroy", C.c_int, [_vp]),
@@ -134,6 +147,16 @@ def choose_q(M, N, P, coll, src, src_ext=None) -> int:
     return q.value
 
 
+def fill_subgrid(M, N, P, q, coll, src) -> np.ndarray:
+    """axi_fill_subgrid: [M][N] azimuthal sub-grid stride of each ring pair's fill samples."""
+    coll = np.ascontiguousarray(coll, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    out = np.zeros((M, N), dtype=np.uint8)
+    _check(lib().axi_fill_subgrid(M, N, P, q, _ptr(coll), _ptr(src),
+                                  out.ctypes.data_as(C.POINTER(C.c_uint8))), "axi_fill_subgrid")
+    return out
+
+
 class ObstacleSpec:
     """Host description of one obstacle (arguments of axi_obstacle)."""
 
@@ -185,6 +208,17 @@ class Operator:
 
     def refactor(self, stream=None):
         _check(lib().axi_refactor_operator(self._op, _stream(stream)), "axi_refactor_operator")
+
+    def profile(self, enable: bool):
+        """axi_operator_profile: start (clearing the record) or stop per-launch timing."""
+        _check(lib().axi_operator_profile(self._op, 1 if enable else 0), "axi_operator_profile")
+
+    def profile_read(self) -> dict:
+        """axi_operator_profile_read: {kind: (launches, ms, algorithmic flops)}."""
+        arr = (_KernelStat * len(KERNEL_KINDS))()
+        _check(lib().axi_operator_profile_read(self._op, C.cast(arr, C.c_void_p)),
+               "axi_operator_profile_read")
+        return {k: (arr[i].launches, arr[i].ms, arr[i].flops) for i, k in enumerate(KERNEL_KINDS)}
 
     def status(self) -> int:
         return lib().axi_operator_status(self._op)
@@ -247,7 +281,18 @@ class Operator:
 
     def apply_noalloc(self, f: torch.Tensor, coef: torch.Tensor, sigma=None, obs=0, stream=None):
         """axi_apply_operator_noalloc into caller-provided coef (and sigma)."""
-        code = lib().axi_apply_operator_noalloc(self._op, obs, f.shape[0], _dev(f), _dev(coef),
+        s = self.specs[obs]
+        W = f.shape[0]
+        dev = self.workspace.device
+        want = [(f, (W, s.rows, s.P), "f"), (coef, (W, s.P, s.cols), "coef")]
+        if sigma is not None:
+            want.append((sigma, (W, s.cols, s.P), "sigma"))
+        for t, shape, name in want:
+            if (tuple(t.shape) != shape or t.dtype != torch.complex128 or not t.is_contiguous()
+                    or t.device != dev):
+                raise ValueError(f"apply_noalloc: {name} must be a contiguous complex128 tensor "
+                                 f"of shape {shape} on {dev}")
+        code = lib().axi_apply_operator_noalloc(self._op, obs, W, _dev(f), _dev(coef),
                                                 _dev(sigma), _stream(stream))
         _check(code, "axi_apply_operator_noalloc")
 

@@ -31,6 +31,8 @@ struct ObsHost {
   std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
   std::vector<int> fill_cex;               // and row exponents [2 MR]
   size_t off_fcdig = 0, off_fcex = 0;
+  std::vector<unsigned char> fill_sig;     // [2][M][N] sub-grid stride per ring pair
+  size_t off_fsig = 0;
 };
 
 // Digits of the folded cosine table of the split fill (fill_mma.cu): row
@@ -92,6 +94,17 @@ void fill_cos_digits(ObsHost &h, int S) {
   h.fill_cdig.swap(tcl);
 }
 
+// Sub-grid strides of the fill (axi_fill_subgrid per proxy set); `full`
+// gives stride 1 everywhere.
+axi_status fill_strides(ObsHost &h, int M, int N, int P, int q, bool transmission, bool full) {
+  h.fill_sig.assign((size_t)2 * M * N, 1);
+  if (full) return AXI_OK;
+  axi_status s = axi_fill_subgrid(M, N, P, q, h.coll.data(), h.src.data(), h.fill_sig.data());
+  if (s == AXI_OK && transmission)
+    s = axi_fill_subgrid(M, N, P, q, h.coll.data(), h.srcx.data(), h.fill_sig.data() + (size_t)M * N);
+  return s;
+}
+
 }  // namespace
 
 struct axi_plan_s {
@@ -102,12 +115,59 @@ struct axi_plan_s {
   std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
   std::vector<int> step_cols;             // widest trailing matrix at step p
   std::vector<int> step_rows;             // tallest panel at step p
+  // algorithmic FP64-equivalent flops of step p's panel, next-panel update and
+  // trailing update over all active tasks (for the kernel profile)
+  std::vector<double> step_fl_panel, step_fl_next, step_fl_rest;
   size_t off_obsdev = 0, off_task_obs = 0, off_task_mode = 0, off_status = 0;
   size_t bytes = 0;
 };
 
+// Event pairs around launch classes (axi_operator_profile).
+struct OpProfiler final : axi::KernelProfiler {
+  struct Rec { int kind; cudaEvent_t a, b; double flops; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  int begin(int kind, cudaStream_t st) override {
+    Rec r{kind, take(), take(), 0.0};
+    if (!r.a || !r.b || cudaEventRecord(r.a, st) != cudaSuccess) return -1;
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void end(int id, cudaStream_t st, double flops) override {
+    recs[id].flops = flops;
+    if (cudaEventRecord(recs[id].b, st) != cudaSuccess) recs[id].kind = -1;
+  }
+  void clear() { recs.clear(); used = 0; }
+  ~OpProfiler() override {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace axi {
+thread_local KernelProfiler *t_prof = nullptr;
+}
+
+// Points axi::t_prof at a profiled operator's recorder for one entry point.
+struct ProfScope {
+  explicit ProfScope(OpProfiler *p) { axi::t_prof = p; }
+  ~ProfScope() { axi::t_prof = nullptr; }
+};
+
 struct axi_operator_s {
   axi_plan_s *plan;
+  OpProfiler *rec = nullptr;   // launch record of the last profile (owned)
+  bool profiling = false;       // recording into `rec` (axi_operator_profile)
+  OpProfiler *prof() const { return profiling ? rec : nullptr; }
+  int device = -1;          // CUDA device the operator was built on (its workspace lives there)
   char *ws;
   ObsDev *d_obs;
   int *d_task_obs, *d_task_mode, *d_status;
@@ -120,6 +180,12 @@ struct axi_operator_s {
 namespace {
 
 axi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AXI_OK : AXI_ERR_CUDA; }
+
+}  // namespace
+
+int axi::operator_device(const axi_operator *op) { return op ? op->device : -1; }
+
+namespace {
 
 // Mixed-radix plan of length n: radices (4s first, then 2, 3, 5) and the
 // position of output k after the in-place decimation-in-frequency FFT,
@@ -213,6 +279,8 @@ const char *axi_status_string(int32_t s) {
 
 axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec, axi_plan **out) {
   if (!obs || !out || n_obs < 1) return AXI_ERR_ARG;
+  const bool full_grid = (prec & axi::kPlanFullFillGrid) != 0;
+  prec &= ~axi::kPlanFullFillGrid;
   const int mode = prec & 0xff;
   int slices = 0;
   if (mode == AXI_PREC_SPLIT_BF16) {
@@ -297,6 +365,11 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
     h.tab_ring.resize(axi::trig::kRingTab);
     axi::trig::ring_table_host(h.tab_ring.data());
     h.off_ring = off; off = align_up(off + sizeof(double2) * h.tab_ring.size());
+    if (fill_strides(h, o.M, o.N, o.P, o.q, o.bc == AXI_BC_TRANSMISSION, full_grid) != AXI_OK) {
+      delete p;
+      return AXI_ERR_GEOMETRY;
+    }
+    h.off_fsig = off; off = align_up(off + h.fill_sig.size());
     h.off_A = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.rows);
     h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
     h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
@@ -352,6 +425,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
   p->step_tasks.assign(maxpan, 0);
   p->step_cols.assign(maxpan, 0);
   p->step_rows.assign(maxpan, 0);
+  p->step_fl_panel.assign(maxpan, 0.0);
+  p->step_fl_next.assign(maxpan, 0.0);
+  p->step_fl_rest.assign(maxpan, 0.0);
   for (int s = 0; s < maxpan; ++s) {
     for (int t = 0; t < (int)p->task_obs.size(); ++t) {
       const ObsDev &d = p->obs[p->task_obs[t]].dev;
@@ -360,6 +436,18 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
         const int k0 = s * axi::kNB, nbp = std::min(axi::kNB, d.cols - k0);
         p->step_cols[s] = std::max(p->step_cols[s], d.cols - k0 - nbp);
         p->step_rows[s] = std::max(p->step_rows[s], d.rows - k0);
+        // reflector j (height K - j) costs 16 (K - j) flops per column it updates
+        const double K = d.rows - k0;
+        double pan = 0.0, hsum = 0.0;
+        for (int j = 0; j < nbp; ++j) {
+          pan += 16.0 * (K - j) * (nbp - 1 - j);
+          hsum += 16.0 * (K - j);
+        }
+        const int rest = d.cols - k0 - nbp;
+        const int nnext = std::min(axi::kNB, std::max(rest, 0));
+        p->step_fl_panel[s] += pan;
+        p->step_fl_next[s] += hsum * nnext;
+        p->step_fl_rest[s] += hsum * std::max(rest - nnext, 0);
       }
     }
   }
@@ -388,11 +476,14 @@ axi_status axi_plan_destroy(axi_plan *plan) {
 // step p-1 include the next panel's columns of step p, hence the wait.
 static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   axi_plan_s *p = op->plan;
+  ProfScope scope(op->prof());
   cudaError_t e = cudaMemsetAsync(op->d_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return AXI_ERR_CUDA;
   for (size_t i = 0; i < p->obs.size(); ++i) {
     const ObsDev &d = p->obs[i].dev;
+    const int pid = axi::prof_begin(AXI_KERNEL_FILL, st);
     e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st);
+    axi::prof_end(pid, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   const int slices = p->obs[0].dev.slices;
@@ -401,8 +492,10 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   bool rest_pending = false, side_used = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
+    int pid = axi::prof_begin(AXI_KERNEL_PANEL, st);
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
                              p->step_rows[s], slices, st);
+    axi::prof_end(pid, st, p->step_fl_panel[s]);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
     const int rest_cols = p->step_cols[s] - axi::kNB;
     // kept digits: every panel's digits are written (the apply reads them),
@@ -416,23 +509,24 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     if (rest_pending && cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess) return AXI_ERR_CUDA;
     rest_pending = false;
     if (p->step_cols[s] > 0) {
+      pid = axi::prof_begin(AXI_KERNEL_UPDATE_NEXT, st);
       e = axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
+      axi::prof_end(pid, st, p->step_fl_next[s]);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
     }
-    if (digits_here && rest_cols <= 0) {                  // nothing in the QR waits for these
+    if (digits_here) {
+      pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, op->side);
       e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
                                    kp_max, op->side);
+      axi::prof_end(pid, op->side);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
     }
     if (rest_cols > 0 || digits_here) side_used = true;
     if (rest_cols > 0) {
-      if (slices > 0) {
-        e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
-                                     kp_max, op->side);
-        if (e != cudaSuccess) return AXI_ERR_CUDA;
-      }
+      pid = axi::prof_begin(AXI_KERNEL_UPDATE_REST, op->side);
       e = axi::launch_qr_update_rest(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
                                      rest_cols, op->side);
+      axi::prof_end(pid, op->side, p->step_fl_rest[s]);
       if (e != cudaSuccess || cudaEventRecord(op->ev_rest, op->side) != cudaSuccess)
         return AXI_ERR_CUDA;
       rest_pending = true;
@@ -444,7 +538,9 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     return AXI_ERR_CUDA;
   // digits of R's off-diagonal blocks for every apply's back substitution
   for (size_t i = 0; i < p->obs.size(); ++i) {
+    const int pid = axi::prof_begin(AXI_KERNEL_R_DIGITS, st);
     e = axi::launch_r_digits(op->d_obs + i, p->obs[i].dev, st);
+    axi::prof_end(pid, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   return AXI_OK;
@@ -468,6 +564,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.tab_s2 = reinterpret_cast<const double *>(ws + h.off_s2);
     d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
     d.tab_ring = reinterpret_cast<const double2 *>(ws + h.off_ring);
+    d.fill_sig = reinterpret_cast<const unsigned char *>(ws + h.off_fsig);
     d.fft_perm = reinterpret_cast<const int *>(ws + h.off_perm);
     d.fft_perm_q = reinterpret_cast<const int *>(ws + h.off_perm_q);
     d.tw_q = reinterpret_cast<const double2 *>(ws + h.off_tw_q);
@@ -495,6 +592,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_s2, h.tab_s2.data(), sizeof(double) * h.tab_s2.size()},
         {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
         {h.off_ring, h.tab_ring.data(), sizeof(double2) * h.tab_ring.size()},
+        {h.off_fsig, h.fill_sig.data(), h.fill_sig.size()},
         {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
         {h.off_perm_q, h.fft_perm_q.data(), sizeof(int) * h.fft_perm_q.size()},
         {h.off_tw_q, h.tw_q.data(), sizeof(double2) * h.tw_q.size()},
@@ -520,6 +618,10 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
   if (!op) return AXI_ERR_ARG;
   op->plan = plan;
   op->ws = ws;
+  if (cudaGetDevice(&op->device) != cudaSuccess) {
+    delete op;
+    return AXI_ERR_CUDA;
+  }
   op->d_obs = reinterpret_cast<ObsDev *>(ws + plan->off_obsdev);
   op->d_task_obs = reinterpret_cast<int *>(ws + plan->off_task_obs);
   op->d_task_mode = reinterpret_cast<int *>(ws + plan->off_task_mode);
@@ -586,6 +688,7 @@ axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W, co
   if (scratch_bytes < need) return AXI_ERR_WORKSPACE;
   const ObsDev &d = op->plan->obs[obs].dev;
   char *digit_scratch = static_cast<char *>(d_scratch) + align_up(sizeof(double2) * (size_t)d.D * 2 * W * d.rows);
+  ProfScope scope(op->prof());
   return cuda_status(axi::launch_apply(op->d_obs + obs, d, W, reinterpret_cast<const double2 *>(d_f),
                                        reinterpret_cast<double2 *>(d_coef),
                                        reinterpret_cast<double2 *>(d_sigma),
@@ -653,8 +756,36 @@ axi_status axi_operator_status(const axi_operator *op) {
   return AXI_OK;
 }
 
+axi_status axi_operator_profile(axi_operator *op, int32_t enable) {
+  if (!op) return AXI_ERR_ARG;
+  if (enable) {
+    if (!op->rec) op->rec = new (std::nothrow) OpProfiler;
+    if (!op->rec) return AXI_ERR_ARG;
+    op->rec->clear();
+  }
+  op->profiling = enable != 0;      // stopping keeps the record for axi_operator_profile_read
+  return AXI_OK;
+}
+
+axi_status axi_operator_profile_read(axi_operator *op, axi_kernel_stat *h_stats) {
+  if (!op || !h_stats) return AXI_ERR_ARG;
+  for (int k = 0; k < AXI_KERNEL_KINDS; ++k) h_stats[k] = axi_kernel_stat{0, 0.0, 0.0};
+  if (!op->rec) return AXI_OK;
+  for (const auto &r : op->rec->recs) {
+    if (r.kind < 0 || r.kind >= AXI_KERNEL_KINDS) continue;
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      return AXI_ERR_CUDA;
+    h_stats[r.kind].launches += 1;
+    h_stats[r.kind].ms += ms;
+    h_stats[r.kind].flops += r.flops;
+  }
+  return AXI_OK;
+}
+
 axi_status axi_operator_destroy(axi_operator *op) {
   if (!op) return AXI_OK;
+  delete op->rec;
   if (op->side) {
     cudaStreamSynchronize(op->side);
     cudaStreamDestroy(op->side);

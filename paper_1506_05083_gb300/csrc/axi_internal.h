@@ -13,6 +13,7 @@ constexpr int kMaxModes = 128; // D = P/2 + 1 <= 128, i.e. P <= 254
 constexpr int kMaxP = 254;
 constexpr int kFillDigits = 8;        // digits of the split fill transform (both operands)
 constexpr int kPanelSmemRows = 864;  // panels up to this many rows are factored in shared memory
+constexpr int kPlanFullFillGrid = 1 << 16;   // AXI_PLAN_FULL_FILL_GRID
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
 enum : int { kStatNonFinite = 1, kStatTimeout = 2 };
@@ -33,6 +34,10 @@ struct ObsDev {
   const double *tab_s2;   // [q/2+1] sin^2(pi l / q)
   const double2 *tw_P;    // [P]   e^{-2 pi i r / P}
   const double2 *tab_ring;  // [1024] (cos, sin)(2 pi i / 1024), the fill samples' sin/cos table
+  // [2][M][N] azimuthal sub-grid stride (1, 2 or 4) of each ring pair's
+  // samples: interior proxies, then exterior proxies (transmission); the
+  // fill evaluates nodes l = 0, s, 2s, .. only (Theorem 1 rate of the pair).
+  const unsigned char *fill_sig;
   double2 *A;             // [D][cols][rows] packed QR factors (column-major)
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
@@ -81,6 +86,25 @@ struct ObsDev {
 
 // Streaming multiprocessors of the current device (cached).
 int sm_count();
+
+// Optional per-launch timing (axi_operator_profile): while an entry point of
+// a profiled operator runs, t_prof points at its recorder, and the launch
+// sites bracket each launch class with prof_begin / prof_end, which record
+// CUDA events on the launch's own stream and the launch's algorithmic
+// FP64-equivalent flops (axi_kernel_kind numbers the classes).
+struct KernelProfiler {
+  virtual int begin(int kind, cudaStream_t st) = 0;
+  virtual void end(int id, cudaStream_t st, double flops) = 0;
+  virtual ~KernelProfiler() {}
+};
+extern thread_local KernelProfiler *t_prof;
+inline int prof_begin(int kind, cudaStream_t st) { return t_prof ? t_prof->begin(kind, st) : -1; }
+inline void prof_end(int id, cudaStream_t st, double flops = 0.0) {
+  if (id >= 0 && t_prof) t_prof->end(id, st, flops);
+}
+
+// CUDA device an operator was built on (api.cu); -1 for a null handle.
+int operator_device(const axi_operator *op);
 
 // The split fill's transform runs on tcgen05 when its group sums stay exact
 // in FP32 over the whole contraction (folded length Lp <= 448) and the

@@ -9,6 +9,10 @@
 //   A_n = (1/q) [g_0 + (-1)^n g_{q/2} + 2 sum_{l=1}^{q/2-1} g_l cos(2 pi n l / q)],
 // which also shows A_n = A_{-n}: only n = 0..P/2 are produced.
 //
+// This direct-sum form (used only when q has prime factors other than 2, 3
+// and 5) evaluates every pair on all q nodes; the FFT and split forms use
+// each pair's sub-grid (ObsDev::fill_sig).
+//
 // Mapping: one CTA = 32 consecutive collocation points (one per lane) x one
 // proxy ring x one kernel kind; 8 warps. Samples for a chunk of 32 nodes are
 // evaluated by all warps into shared memory, then warp w accumulates modes
@@ -166,10 +170,17 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
   const double nr = o.coll[4 * mm + 2], nz = o.coll[4 * mm + 3];
   const double dr = rho - rs, dz = z - zs;
   const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
-  const double wq = kInv4Pi / q;
-  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with 1/(4 pi q) folded in
+  // sub-grid of the pair (nodes l = 0, sg, 2 sg, ..; sg divides q/2): the other
+  // nodes are zero and the weight is sg / (4 pi q), i.e. the (q/sg)-node rule
+  const int sg = o.fill_sig[((size_t)(ext ? 1 : 0) * o.M + mm) * o.N + j];
+  const double wq = kInv4Pi * sg / q;
+  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with sg/(4 pi q) folded in
   const double an = (nr * rho + nz * dz) * wq, bn = nr * rs * wq;
-  for (int l = lane; l <= half; l += 32) {
+  if (sg > 1)
+    for (int l = lane; l < q; l += 32)
+      if (l % sg) seq[l] = make_double2(0.0, 0.0);
+  for (int i = lane; i * sg <= half; i += 32) {
+    const int l = i * sg;
     const double R2 = fma(fourrr, o.tab_s2[l], base);
     const double inv = rsqrt(R2);
     const double R = R2 * inv, kR = k * R;

@@ -89,10 +89,17 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   const double nr = o.coll[4 * m + 2], nz = o.coll[4 * m + 3];
   const double dr = rho - rs, dz = z - zs;
   const double base = dr * dr + dz * dz, fourrr = 4.0 * rho * rs;
-  const double wq = kInv4Pi / q;
-  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with 1/(4 pi q) folded in
+  // sub-grid: nodes l = 0, sg, 2 sg, .. (sg divides h), weight sg / (4 pi q);
+  // the other nodes stay zero, so the transform below is the (q/sg)-node rule
+  const int sg = o.fill_sig[((size_t)(ext ? 1 : 0) * o.M + m) * o.N + j];
+  const double wq = kInv4Pi * sg / q;
+  // n . (x - y_l) = (n_r rho + n_z dz) - n_r rho' cos(phi_l), with sg/(4 pi q) folded in
   const double an = (nr * rho + nz * dz) * wq, bn = nr * rs * wq;
-  for (int l = lane; l <= h; l += 32) {
+  if (sg > 1)
+    for (int l = lane; l <= h; l += 32)
+      if (l % sg) seq[l] = make_double2(0.0, 0.0);
+  for (int i = lane; i * sg <= h; i += 32) {
+    const int l = i * sg;
     const double R2 = fma(fourrr, o.tab_s2[l], base);
     const double inv = rsqrt(R2);
     const double R = R2 * inv, kR = k * R;

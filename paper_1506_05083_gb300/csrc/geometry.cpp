@@ -173,3 +173,30 @@ extern "C" axi_status axi_choose_q(int32_t M, int32_t N, int32_t P, const double
   *q = n;
   return AXI_OK;
 }
+
+// Sub-grid stride of each ring pair's fill samples (Sec. 3.1, Theorem 1):
+// the largest s in {4, 2, 1} with (q/2) mod s = 0 and
+//   q/s >= max(P, 37/alpha + P/2),  alpha = acosh(1 + d^2/(2 rho rho')),
+// the pair's own convergence rate, so that the q/s-node trapezoid rule of the
+// pair meets the accuracy the q-node rule was chosen for.
+extern "C" axi_status axi_fill_subgrid(int32_t M, int32_t N, int32_t P, int32_t q,
+                                       const double *h_coll, const double *h_src,
+                                       uint8_t *h_stride) {
+  if (!h_coll || !h_src || !h_stride) return AXI_ERR_ARG;
+  if (M < 1 || N < 1 || P < 2 || (P & 1) || q < P || (q & 1)) return AXI_ERR_SHAPE;
+  for (int m = 0; m < M; ++m) {
+    const double rho = h_coll[4 * m], z = h_coll[4 * m + 1];
+    for (int j = 0; j < N; ++j) {
+      const double rs = h_src[2 * j], zs = h_src[2 * j + 1];
+      const double d2 = (rho - rs) * (rho - rs) + (z - zs) * (z - zs);
+      const double alpha = std::acosh(1.0 + d2 / (2.0 * rho * rs));
+      if (!(alpha > 0)) return AXI_ERR_GEOMETRY;
+      const double need = std::fmax((double)P, 37.0 / alpha + P / 2.0);
+      int sg = 1;
+      for (int c : {4, 2})
+        if ((q / 2) % c == 0 && (double)(q / c) >= need) { sg = c; break; }
+      h_stride[(size_t)m * N + j] = (uint8_t)sg;
+    }
+  }
+  return AXI_OK;
+}

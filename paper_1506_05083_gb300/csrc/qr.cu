@@ -816,6 +816,10 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
                          double2 *coef, double2 *sigma, double2 *X, void *digit_scratch,
                          cudaStream_t st) {
   const int ncol = 2 * W;
+  // algorithmic flops over the W x P right-hand sides: Q^H 16 rows cols - 8 cols^2,
+  // back substitution 4 cols^2 each
+  const double rhs = (double)W * h.P;
+  int pid = prof_begin(AXI_KERNEL_APPLY_RHS, st);
   if (h.fft_nst > 0) {
     cudaError_t e = launch_rhs_fft(d_o, h, W, f, X, st);
     if (e != cudaSuccess) return e;
@@ -829,25 +833,32 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  prof_end(pid, st);
   cudaError_t e;
+  pid = prof_begin(AXI_KERNEL_APPLY_QH, st);
   if (h.slices > 0 && W >= kSplitApplyMinWaves) {
     e = launch_apply_qh_split(d_o, h, X, ncol, digit_scratch, st);
   } else {
     apply_qh_kernel<<<dim3(h.D, (ncol + kTA - 1) / kTA), kNB * kTA, 0, st>>>(d_o, X, ncol);
     e = cudaGetLastError();
   }
+  prof_end(pid, st, rhs * (16.0 * h.rows * h.cols - 8.0 * h.cols * h.cols));
   if (e != cudaSuccess) return e;
+  pid = prof_begin(AXI_KERNEL_APPLY_TRSM, st);
   if (h.slices > 0) {
     e = launch_trsm_split(d_o, h, X, ncol, st);
   } else {
     trsm_kernel<<<dim3(h.D, (ncol + kTS - 1) / kTS), kThreads, 0, st>>>(d_o, X, ncol);
     e = cudaGetLastError();
   }
+  prof_end(pid, st, rhs * 4.0 * h.cols * h.cols);
   if (e != cudaSuccess) return e;
+  pid = prof_begin(AXI_KERNEL_APPLY_OUT, st);
   scatter_coef_kernel<<<dim3(h.P, W), 128, 0, st>>>(d_o, W, X, coef);
   e = cudaGetLastError();
-  if (e != cudaSuccess || !sigma) return e;
-  return launch_point_strengths(d_o, h, W, coef, sigma, st);
+  if (e == cudaSuccess && sigma) e = launch_point_strengths(d_o, h, W, coef, sigma, st);
+  prof_end(pid, st);
+  return e;
 }
 
 cudaError_t launch_point_strengths(const ObsDev *d_o, const ObsDev &h, int W, const double2 *coef,

@@ -55,6 +55,37 @@ def test_batched_geometry_and_q(axi):
         assert q1 == O.choose_q(ob, c2, s2, x2)
 
 
+@pytest.mark.parametrize("make", [synth.small_case, synth.config_smooth])
+def test_fill_subgrid_rule(axi, make):
+    """Per-pair sub-grids of the fill (Theorem 1 per ring pair): strides in
+    {1, 2, 4} that divide q/2 and keep q/s >= P; pairs with a faster rate
+    never get a finer grid; and, checked independently with the oracle's own
+    samples, every pair's (q/s)-node trapezoid rule agrees with the q-node
+    rule for all modes to 1e-14 of max|A| (the accuracy q was chosen for)."""
+    ob = make().obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    q = ob.q or O.choose_q(ob, coll, src, srcx)
+    s = axi.fill_subgrid(ob.M, ob.N, ob.P, q, coll, src).astype(int)
+    assert set(np.unique(s)) <= {1, 2, 4}
+    assert np.all((q // 2) % s == 0) and np.all(q // s >= ob.P)
+    alpha = O.theorem1_rate(coll[:, 0:1], coll[:, 1:2], src[None, :, 0], src[None, :, 1])
+    order = np.argsort(alpha, axis=None)
+    assert np.all(np.diff(s.reshape(-1)[order]) >= 0)
+    D = ob.P // 2 + 1
+    A = O.fill(ob.k, coll, src, q, ob.P, True)
+    l = np.arange(q)
+    E = np.exp(-2j * math.pi * np.outer(l, np.arange(D)) / q) / q
+    err = 0.0
+    for m0 in range(0, ob.M, 16):
+        g = O.ring_samples(ob.k, coll[m0:m0 + 16], src, q, True)
+        sg = s[m0:m0 + 16][:, :, None]
+        gs = np.where(l[None, None, :] % sg == 0, g * sg, 0)
+        err = max(err, np.abs(np.moveaxis(gs @ E, 2, 0) - A[:, m0:m0 + 16]).max())
+    assert err < 1e-14 * np.abs(A).max(), err
+    if make is synth.config_smooth:
+        assert (s > 1).mean() > 0.5          # most pairs sample on a sub-grid
+
+
 def _plan(axi, **kw):
     import ctypes as C
     ob = synth.small_case().obstacles[0]
@@ -90,6 +121,8 @@ def test_plan_validation(axi):
     nan = coll.copy(); nan[2, 1] = float("nan")
     assert _plan(axi, coll=nan) == -3
     assert _plan(axi, prec=7) == -1
+    assert _plan(axi, prec=axi.PLAN_FULL_FILL_GRID) == 0
+    assert _plan(axi, prec=axi.PREC_SPLIT_BF16 | axi.PLAN_FULL_FILL_GRID) == 0
 
 
 def test_status_strings(axi):

@@ -235,3 +235,26 @@ def test_smooth_full_size():
     assert _e_bd(A, ob, coef.cpu().numpy(), c_ora, fh) < 1e-10
     F_ora = O.far_field(ob, src, c_ora, xh_np)
     assert np.abs(F_gpu - F_ora).max() / np.abs(F_ora).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_fill_subgrid_and_full_grid(prec):
+    """The smooth body at full size: the fill on each ring pair's sub-grid
+    (default; 92% of pairs on q/2 nodes) and on the full q-node grid
+    (AXI_PLAN_FULL_FILL_GRID) both match the oracle's full-grid fill to
+    e_A <= 1e-13, and each other to rounding."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case("smooth")
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    base = axi.PREC_FP64 if prec == "fp64" else axi.PREC_SPLIT_BF16
+    out = []
+    for flag in (0, axi.PLAN_FULL_FILL_GRID):
+        op = axi.Operator([spec], prec=base | flag)
+        out.append(op.fill_modes().cpu().numpy().transpose(0, 2, 1))
+        torch.cuda.synchronize()
+        assert op.status() == 0
+        del op
+    scale = np.abs(A).max()
+    for Ag in out:
+        assert np.abs(Ag - A).max() / scale < 1e-13
+    assert np.abs(out[0] - out[1]).max() / scale < 1e-13
