@@ -22,12 +22,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_apply_scratch on the current device. In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device with that device current and cached.
-axi_status scratch_address(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AXI_ERR_CUDA;
+// Device address of g_apply_scratch on device `dev` (the current device). In
+// host code the symbol is only a host-side stand-in, so the address is
+// looked up once per device with that device current and cached; a device
+// reset (cudaDeviceReset) would make the cached address stale, so calls
+// after a reset in the same process are not supported.
+axi_status scratch_address(int dev, void **out) {
+  if (dev < 0 || dev >= kMaxDevices) return AXI_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[dev]) {
     void *p = nullptr;
@@ -46,12 +47,23 @@ extern "C" axi_status axi_apply_operator_noalloc(const axi_operator *op, int32_t
                                                  const axi_c128 *d_f, axi_c128 *d_coef,
                                                  axi_c128 *d_sigma, void *stream) {
   if (!op || !d_f || !d_coef || W < 1) return AXI_ERR_ARG;
+  // The library, not the caller, picks the scratch: it must be the array of
+  // the device that holds the operator, and the stream must belong to it.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return AXI_ERR_CUDA;
+  if (dev != axi::operator_device(op)) return AXI_ERR_ARG;
+  if (stream) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev) != cudaSuccess)
+      return AXI_ERR_ARG;
+    if (sdev != dev) return AXI_ERR_ARG;
+  }
   size_t need = 0;
   axi_status s = axi_apply_workspace_bytes(op, obs, W, &need);
   if (s != AXI_OK) return s;
-  if (need > kNoAllocScratchBytes) return AXI_ERR_SHAPE;  // W too large for the static scratch
+  if (need > kNoAllocScratchBytes) return AXI_ERR_WORKSPACE;  // too large for the static scratch
   void *scratch = nullptr;
-  s = scratch_address(&scratch);
+  s = scratch_address(dev, &scratch);
   if (s != AXI_OK) return s;
   // Every element of the scratch that the apply reads is written by it first
   // (the transform to modes fills all D x 2W RHS columns), so no clearing is
