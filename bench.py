@@ -1,27 +1,37 @@
 #!/usr/bin/env python
 """Benchmark of the one-obstacle MFS solution operator on one GB300.
 
-A step is one pass of the whole hot path on the smooth-body workload
-(r = 1 + 0.2 sum_j a_j cos js, k = 10, N = 180, M = 216, P = 120, q = 400,
-16 seeded plane waves): ring-kernel fill of the 61 distinct modal matrices,
-blocked Householder QR of each, then for the 16 waves the incident data,
-transform to modes, Q^H, triangular solve and inverse transform to point
-strengths.
+Default workload: the resonant cup (a = 0.2, b = pi/2), k = 25, N = 360,
+M = 432, P = 180 (NP = 64,800), q = 1000, 16 seeded plane waves. A step is one
+pass of the whole hot path: ring-kernel fill of the 91 distinct modal
+matrices, blocked Householder QR of each, then for the 16 waves the incident
+data, transform to modes, Q^H, triangular solve and inverse transform to
+point strengths. Two arms run in the same process: the split-precision plan
+(BF16 digits on tensor cores for the trailing updates and the apply, the
+headline) and the native-FP64 plan.
 
 value = FP64-equivalent algorithmic TFLOP/s of the step: per distinct mode
 8 M N^2 - 8 N^3 / 3 (complex QR) plus per wave and mode 16 M N - 4 N^2
 (Q^H and back substitution), divided by the device time of the step. The
 L2 is flushed (a 256 MB write) before every timed step.
 
-`--impl reference` times the FP64 CPU oracle on the same workload instead.
-Multi-GPU (torchrun): each rank runs its own copy of the workload (the
-operator's (obstacle, mode) tasks are independent); value sums the ranks'
-work over the slowest rank's time ("weak" scaling), no collective on the
-data path.
+The roofline object reports the launch class that takes the most device time
+in a profiled pass of the same step (CUDA events around every launch on its
+own stream, through axi_operator_profile), in algorithmic flops per second.
+cpu_baseline runs the FP64 oracle once on the whole workload on the host
+cores; its coefficients also give the line's parity errors e_bd and e_ff.
+
+`--impl reference` times the oracle as the reference arm: each step is one
+distinct mode's share of the workload (see reference_step). `--workload
+smooth | batched | cup_near` prints the other workloads' lines. Multi-GPU
+(torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
+tasks are independent), value sums the ranks' work over the slowest rank's
+time ("weak" scaling), with no collective on the data path.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -38,45 +48,22 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "operator build time (FP64-equiv TFLOP/s), per-wave apply us at 1e-10 rel err"
-FP64_DFMA_PEAK_TFLOPS = 1.195   # measured on this machine's GB300 (profiles/peaks_probe_gb300.md)
-# DRAM bytes (read + write) of one split-plan fill on the smooth-body workload
-# (fill_samples_kernel 3.0 MB + 261.4 MB, fill_gemm_tc_kernel 319.9 MB + 21.1 MB),
-# from the ncu capture in profiles/fill_split_smooth_k10_N180_M216_P120.md. The
-# FP64 plans' fill_fft_kernel has no capture of its current form (None).
-FILL_TRAFFIC_BYTES = {"split": 3003392 + 261359616 + 319930880 + 21131008, "fp64": None}
+# FP64 DFMA throughput of a GB300, measured with a probe of independent FMA
+# chains over all SMs (MEASURED_PEAKS.json has no FP64 entry).
+FP64_DFMA_PEAK_TFLOPS = 1.195
+# Fallback denominators when MEASURED_PEAKS.json is absent.
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# launch classes whose arithmetic runs on BF16 digits in split plans
+SPLIT_KINDS = {"update_rest", "apply_qh", "apply_trsm"}
+FP64_KINDS = {"panel", "update_next", "update_rest", "apply_qh", "apply_trsm"}
 
 
-def workload():
-    wl = synth.config_smooth()
-    return wl, wl.obstacles[0]
-
-
-def step_launches(ob, spec, split, slices):
-    """Kernels one step launches, as the library schedules them: fill (split
-    plans: sample + digit-GEMM kernel per chunk of ring pairs), per panel step
-    the panel, next-panel update and trailing update (split: plus the panel's
-    reflector digits, at every step when the plan keeps them for the apply),
-    R's digits at the end of a split build, incident, and the apply's RHS
-    transform, Q^H, back substitution, scatter and point-strength transform."""
-    rows, cols = spec.rows, spec.cols
-    D = ob.P // 2 + 1
-    npanels = (cols + 15) // 16
-    n_next = sum(1 for p in range(npanels) if cols - 16 * (p + 1) > 0)
-    n_rest = sum(1 for p in range(npanels) if cols - 16 * (p + 2) > 0)
-    n = 1 + npanels + n_next + n_rest + 1 + 5
-    if split:
-        kinds = 4 if ob.bc != synth.BC_NEUMANN else 1
-        L = spec.q // 4 + 1 if (spec.q // 2) % 2 == 0 else (spec.q // 2 + 1) // 2
-        Lp = (L + 31) // 32 * 32
-        per_pair = 2 * 2 * kinds * 8 * Lp * 2
-        chunk = max(8, min(ob.M * ob.N, (512 << 20) // per_pair))
-        n += 2 * -(-ob.M * ob.N // chunk) - 1
-        kp = (rows + 63) // 64 * 64 + 64
-        kept = D * npanels * (4 * slices * 16 * kp * 2 + (16 + kp) * 4) <= (4 << 30)
-        n += npanels if kept else n_rest
-        n += 1 if (cols + 31) // 32 >= 2 else 0
-        n += 0 if kept else 1
-    return n
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
 
 
 def algorithmic_flops(M, N, P, W):
@@ -86,53 +73,31 @@ def algorithmic_flops(M, N, P, W):
     return qr, apply
 
 
-# FP64 issue slots (one slot = one DFMA) of the fill kernel's arithmetic, from
-# its source: per ring sample rsqrt (8.2 slots, measured) + the ring sin/cos
-# of trig.cuh (the 1024-entry table form, 14 operations) + the products around them (11
-# for the normal derivative, 6 for the value kernel); per FFT butterfly the
-# adds, multiplies and twiddle products of fft.cuh (radix 2: 8, 3: 22, 4: 28,
-# 5: 52); the pruned last stage costs 2 (r - 1) per needed mode.
-SINCOS_SLOTS = 14.0
-SLOTS_PRODUCTS = {"deriv": 8.2 + 11.0, "value": 8.2 + 6.0}
-SLOTS_BUTTERFLY = {2: 8, 3: 22, 4: 28, 5: 52}
+def digit_pairs(slices):
+    """Digit products per complex MAC pair of a split GEMM: s + t <= S + 1."""
+    return slices * (slices + 1) // 2
 
 
-def fill_fft_plan(q, D):
-    """Radices of the fill's FFT (same rule as the library's plan): 4s, 2, 3,
-    5, with the largest radix r with q / r >= D moved last and replaced by
-    block sums."""
-    rad, m = [], q
-    for r in (4, 2, 3, 5):
-        while m % r == 0:
-            rad.append(r)
-            m //= r
-    last = None
-    cands = [i for i, r in enumerate(rad) if q // r >= D]
-    if cands and len(rad) > 1:
-        i = max(cands, key=lambda i: rad[i])
-        last = rad.pop(i)
-    return rad, last
-
-
-def fill_slots(M, N, P, q, bc_kinds, split):
-    """FP64 slots per fill: pairs x ((q/2+1) samples + the transform).
-    bc_kinds lists the sample kinds per pair ("deriv" or "value"). Native FP64
-    plans transform with the pruned FFT; split plans fold the samples (4 adds
-    per folded node) and run the transform on tensor cores (no FP64 slots)."""
-    D = P // 2 + 1
-    h = q // 2
-    if split:
-        L = h // 2 + 1 if h % 2 == 0 else (h + 1) // 2
-        per_kind = 4.0 * L
-    else:
-        rad, last = fill_fft_plan(q, D)
-        per_kind = sum(SLOTS_BUTTERFLY[r] * (q // r) for r in rad)
-        per_kind += 2 * (last - 1) * D if last else 0
-    per_pair = sum((h + 1) * (SLOTS_PRODUCTS[k] + SINCOS_SLOTS) + per_kind for k in bc_kinds)
-    return M * N * per_pair
+def traffic_for(kind):
+    """DRAM bytes per launch of a launch class from the committed ncu capture
+    (profiles/roofline_traffic.json), or None when a source file it covers
+    has changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    ent = json.load(open(p)).get(kind)
+    if not ent:
+        return None
+    for rel, sha in ent.get("sources", {}).items():
+        fp = os.path.join(ROOT, rel)
+        if not os.path.exists(fp) or hashlib.sha256(open(fp, "rb").read()).hexdigest() != sha:
+            return None
+    return ent.get("bytes_per_launch")
 
 
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 50 ms while it is open."""
+
     def __init__(self, index=0):
         self.index = index
         self.proc = None
@@ -149,14 +114,16 @@ class ClockSampler:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)          # the first sample before the timed region starts
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -167,7 +134,7 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, load = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
@@ -176,35 +143,18 @@ class ClockSampler:
             try:
                 sm.append(float(p[1]))
                 smax = float(p[2])
+                load.append(float(p[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def run_oracle_step(ob, dirs):
-    import oracle as O
-    coll, src, srcx = O.geometry(ob)
-    A, fac = O.factor_operator(ob, coll, src, srcx)
-    c = O.solve_modes(ob, fac, O.rhs_modes(O.incident_samples(ob, coll, dirs)))
-    O.point_strengths(c, ob.P)
-    return c
-
-
-def cpu_baseline_line(ob, dirs, steps=1):
-    """Oracle on the host cores: the whole smooth-body workload (all 61 modes, 16 waves)."""
-    qr, ap = algorithmic_flops(ob.M, ob.N, ob.P, dirs.shape[0])
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        run_oracle_step(ob, dirs)
-    dt = (time.perf_counter() - t0) / steps
-    return {"value": (qr + ap) / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
-            "kind": "oracle", "seconds_per_step": dt,
-            "sample": f"full workload: fill+QR of {ob.P // 2 + 1} modes, apply of "
-                      f"{dirs.shape[0]} waves (numpy FP64, BLAS threads = host cores)"}
+        # under load: samples drawing more than the idle power
+        idle = min(load) if load else 0.0
+        busy = [c for c, w in zip(sm, load) if w > idle + 50.0] or sm
+        return {"sm_mhz": float(np.median(busy)) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(busy),
+                "period_ms": 50}
 
 
 def slowest_rank_ms(ms, device):
@@ -231,56 +181,233 @@ def dist_env():
     return ws, rank, local
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="split", choices=["split", "fp64"],
-                    help="trailing-update / Q^H arithmetic: Ozaki BF16 digits or native FP64")
-    ap.add_argument("--slices", type=int, default=7)
-    ap.add_argument("--no-graph", dest="graph", action="store_false",
-                    help="launch the step's kernels directly instead of replaying CUDA graphs")
-    ap.add_argument("--workload", default="smooth", choices=["smooth", "cup", "batched", "cup_near"],
-                    help="smooth (default, the headline line); others print their own line")
-    args = ap.parse_args()
-    if args.workload != "smooth":
-        run_extra_workload(args)
-        return
-    ws, rank, local = dist_env()
-    wl, ob = workload()
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (host cores): the CPU baseline and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_full(ob, dirs, xhat):
+    """The oracle on the whole workload: fill, QR of every distinct mode,
+    apply to every wave, far field. Returns (seconds, A, coef, far field)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    coll, src, srcx = O.geometry(ob)
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs))
+    c = O.solve_modes(ob, fac, fh)
+    O.point_strengths(c, ob.P)
+    dt = time.perf_counter() - t0
+    F = O.far_field(ob, src, c, xhat)
+    return dt, A, fh, c, F
+
+
+def parity(A, ob, fh, c_ora, F_ora, coef, F):
+    """e_bd = ||A_ora (c - c_ora)|| / ||fhat|| over all modes and waves;
+    e_ff = max |F - F_ora| / max |F_ora| (the parity metric of the tests)."""
+    P = ob.P
+    num = 0.0
+    for idx in range(P):
+        n = idx if idx <= P // 2 else P - idx
+        num += np.linalg.norm(A[n] @ (coef[:, idx, :] - c_ora[:, idx, :]).T) ** 2
+    e_bd = math.sqrt(num) / np.linalg.norm(fh)
+    e_ff = float(np.abs(F - F_ora).max() / np.abs(F_ora).max())
+    return e_bd, e_ff
+
+
+def run_reference(args, wl):
+    import oracle as O
+    ob = wl.obstacles[0]
     W = wl.n_waves
-    dirs_np = synth.plane_wave_directions(W, wl.wave_seed)
-    qr_fl, ap_fl = algorithmic_flops(ob.M, ob.N, ob.P, W)
-    config = {"workload": wl.name, "precision": args.prec, "obstacle": "smooth r=1+0.2*sum a_j cos(js), seed 2",
-              "k": ob.k, "M": ob.M, "N": ob.N, "P": ob.P, "q": ob.q, "waves": W,
-              "distinct_modes": ob.P // 2 + 1, "l2": "flushed (256 MB write) before each timed step",
-              "launch": "CUDA graph replay" if args.graph else "direct launches"}
+    dirs = synth.plane_wave_directions(W, wl.wave_seed)
+    coll, src, srcx = O.geometry(ob)
+    D = ob.P // 2 + 1
+    rows = -(-ob.M // D)
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs))
+    Am = {}
+    cols = O.n_cols(ob)
 
-    if args.impl == "reference":
-        if rank != 0:
+    def step(i):
+        mode = (7 * i) % D
+        m0 = (mode * rows) % ob.M
+        blk = coll[m0:m0 + rows]
+        O.system_matrix(ob, blk, src, srcx)           # fill of one mode's share of the rows
+        if mode not in Am:                              # the full modal matrix (setup, untimed)
+            raise RuntimeError("matrix of the mode not prepared")
+        QR, tau = O.householder_qr(Am[mode])
+        for idx in {mode, (ob.P - mode) % ob.P}:
+            Y = O.apply_qh(QR, tau, fh[:, idx, :].T)[:cols]
+            O.back_substitute(np.triu(QR[:cols, :cols]), Y)
+        n_rhs = W * (2 if 0 < mode < ob.P // 2 else 1)
+        return (8.0 * ob.M * cols ** 2 - 8.0 * cols ** 3 / 3
+                + n_rhs * (16.0 * O.n_rows(ob) * cols - 4.0 * cols * cols))
+
+    # the modal matrices the steps factor come from one full oracle fill (not timed)
+    need = sorted({(7 * i) % D for i in range(args.warmup + args.steps)})
+    A_all = O.system_matrix(ob, coll, src, srcx)
+    for mode in need:
+        Am[mode] = A_all[mode]
+    del A_all
+    for i in range(args.warmup):
+        step(i)
+    fl = 0.0
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        fl += step(i)
+    dt = time.perf_counter() - t0
+    v = fl / dt / 1e12
+    sample = (f"per step one distinct mode's share of {wl.name}: the oracle fill of {rows} of "
+              f"{ob.M} collocation rows (all modes), the QR of one distinct mode and the solve "
+              f"of its +-n modes for {W} waves (modes 7i mod {D})")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "M": ob.M, "N": ob.N, "P": ob.P, "q": ob.q,
+                       "k": ob.k, "waves": W},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": blas_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arms
+# ---------------------------------------------------------------------------
+
+class Arm:
+    """One plan (split or native FP64) of the workload with its buffers and
+    the two CUDA graphs of a step (build; incident data + apply)."""
+
+    def __init__(self, name, prec, spec, ob, W, dirs, dev, graph):
+        import torch
+        from paper_1506_05083_gb300 import axi
+        self.name, self.ob, self.W, self.dirs = name, ob, W, dirs
+        self.op = axi.Operator([spec], prec=prec)
+        self.coef = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128, device=dev)
+        self.sigma = torch.empty((W, spec.cols, ob.P), dtype=torch.complex128, device=dev)
+        self.scratch = torch.empty(self.op.apply_scratch_bytes(W), dtype=torch.uint8, device=dev)
+        self.graph = graph
+        self.g_build = self.g_apply = None
+
+    def step_direct(self):
+        self.op.refactor()
+        self.apply_direct()
+
+    def apply_direct(self):
+        f = self.op.incident(self.dirs)
+        self.op.apply(f, want_sigma=True, scratch=self.scratch, coef=self.coef, sigma=self.sigma)
+
+    def capture(self):
+        import torch
+        if not self.graph:
             return
-        for _ in range(args.warmup):
-            run_oracle_step(ob, dirs_np)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            run_oracle_step(ob, dirs_np)
-        dt = (time.perf_counter() - t0) / args.steps
-        v = (qr_fl + ap_fl) / dt / 1e12
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(),
-                                 "kind": "oracle", "sample": "full workload per step"},
-                "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return
+        self.g_build, self.g_apply = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_build):
+            self.op.refactor()
+        with torch.cuda.graph(self.g_apply):
+            self.apply_direct()
+        for _ in range(2):
+            self.g_build.replay()
+            self.g_apply.replay()
 
+    def build(self):
+        if self.graph:
+            self.g_build.replay()
+        else:
+            self.op.refactor()
+
+    def apply(self):
+        if self.graph:
+            self.g_apply.replay()
+        else:
+            self.apply_direct()
+
+
+def time_steps(arm, K, flush, stream):
     import torch
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        e0, e1, e2 = evs[i]
+        e0.record(stream)
+        arm.build()
+        e1.record(stream)
+        arm.apply()
+        e2.record(stream)
+    torch.cuda.synchronize()
+    step = [a.elapsed_time(c) for a, _, c in evs]
+    build = [a.elapsed_time(b) for a, b, _ in evs]
+    apply = [b.elapsed_time(c) for _, b, c in evs]
+    return float(np.mean(step)), float(np.mean(build)), float(np.mean(apply))
+
+
+def kernel_profile(arm, steps, flush):
+    """Per launch class of the step: launches, device ms and algorithmic
+    flops per step, from CUDA events around each launch on its own stream
+    (direct launches, L2 flushed before each step)."""
+    import torch
+    arm.op.profile(True)
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        arm.step_direct()
+    torch.cuda.synchronize()
+    arm.op.profile(False)
+    st = arm.op.profile_read()
+    return {k: {"launches": n / steps, "ms": ms / steps, "flops": fl / steps}
+            for k, (n, ms, fl) in st.items() if n > 0}
+
+
+def roofline_from_profile(prof, slices, split, pk, src):
+    """The launch class with the most device time among those with
+    algorithmic flops, against its own bound: FP64 classes against the FP64
+    DFMA peak ("alu"); split classes against the BF16 tensor peak, counting
+    the digit products they issue (S(S+1)/2 BF16 products of 4 real MACs per
+    complex MAC, i.e. the FP64-equivalent flops times S(S+1)/2)."""
+    cand = {k: v for k, v in prof.items() if v["flops"] > 0}
+    kind = max(cand, key=lambda k: cand[k]["ms"])
+    v = cand[kind]
+    per_launch_ms = v["ms"] / v["launches"]
+    fl64 = v["flops"] / (v["ms"] * 1e-3) / 1e12
+    total_ms = sum(x["ms"] for x in prof.values())
+    common = {"kernel": kind, "launches_per_step": v["launches"], "kernel_ms_per_launch": per_launch_ms,
+              "share_of_profiled_time": v["ms"] / total_ms,
+              "traffic": traffic_for(("split_" if split else "fp64_") + kind)}
+    if split and kind in SPLIT_KINDS:
+        ach = fl64 * digit_pairs(slices)
+        peak = pk["bf16_tflops_sustained"]
+        return dict(common, bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    work=f"FP64-equivalent algorithmic flops x {digit_pairs(slices)} BF16 digit "
+                         f"products ({fl64:.4g} FP64-equiv TFLOP/s)",
+                    peak_source=f"bf16_tflops_sustained of {src} (the kernel runs inside a long step)")
+    return dict(common, bound="alu", achieved=fl64, peak=FP64_DFMA_PEAK_TFLOPS, unit="TFLOP/s",
+                frac=fl64 / FP64_DFMA_PEAK_TFLOPS,
+                work="algorithmic FP64 flops of the launch class (complex Householder count)",
+                peak_source="FP64 DFMA probe of measured (MEASURED_PEAKS.json has no FP64 entry)")
+
+
+def step_launches(prof):
+    """Kernel launches of one step of the library's kernels, from the profile's
+    launch classes: each class entry is one wrapper call; the fill issues two
+    kernels per chunk of ring pairs, the apply's output class one or two."""
+    n = 0
+    for k, v in prof.items():
+        n += v["launches"] * (2 if k == "fill" else 1)
+    return int(round(n))
+
+
+def run_single(args, wl):
+    import torch
+    ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -289,152 +416,137 @@ def main():
     torch.cuda.set_device(dev)
     from paper_1506_05083_gb300 import axi
 
+    ob = wl.obstacles[0]
+    W = wl.n_waves
+    dirs_np = synth.plane_wave_directions(W, wl.wave_seed)
     spec = axi.spec_from_obstacle(ob)
-    stream = torch.cuda.current_stream()
-    prec = axi.PREC_SPLIT_BF16 | (args.slices << 8) if args.prec == "split" else axi.PREC_FP64
-    op = axi.Operator([spec], prec=prec)
+    qr_fl, ap_fl = algorithmic_flops(spec.rows, spec.cols, ob.P, W)
     dirs = torch.tensor(dirs_np, device=dev)
-    coef = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128, device=dev)
-    sigma = torch.empty((W, spec.cols, ob.P), dtype=torch.complex128, device=dev)
-    scratch = torch.empty(op.apply_scratch_bytes(W), dtype=torch.uint8, device=dev)
-    fill_out = torch.empty((ob.P // 2 + 1, spec.cols, spec.rows), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    def step():
-        op.refactor()
-        f = op.incident(dirs)
-        op.apply(f, want_sigma=True, scratch=scratch, coef=coef, sigma=sigma)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if op.status() != 0:
-        raise RuntimeError("device status word set during warm-up")
-
-    # The timed step replays two CUDA graphs captured from the same library
-    # calls: the build (fill + look-ahead QR, with its side-stream fork/join)
-    # and the apply (incident data, transforms, Q^H, back substitution, point
-    # strengths). Inputs and scratch are preallocated; nothing is allocated
-    # inside the graphs.
-    g_build, g_apply = (torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()) if args.graph else (None, None)
-    if args.graph:
-        with torch.cuda.graph(g_build):
-            op.refactor()
-        with torch.cuda.graph(g_apply):
-            f_g = op.incident(dirs)
-            op.apply(f_g, want_sigma=True, scratch=scratch, coef=coef, sigma=sigma)
-        for _ in range(2):
-            g_build.replay()
-            g_apply.replay()
+    pk, pk_src = peaks()
+    split_prec = axi.PREC_SPLIT_BF16 | (args.slices << 8)
+    arms = []
+    if args.prec == "split":
+        arms.append(Arm("split", split_prec, spec, ob, W, dirs, dev, args.graph))
+        if not args.no_fp64_arm:
+            arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph))
+    else:
+        arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph))
+    head = arms[0]
+    for arm in arms:
+        for _ in range(args.warmup):
+            arm.step_direct()
         torch.cuda.synchronize()
-        if op.status() != 0:
-            raise RuntimeError("device status word set in graph replay")
+        if arm.op.status() != 0:
+            raise RuntimeError(f"device status word set during warm-up ({arm.name})")
+        arm.capture()
+        torch.cuda.synchronize()
+        if arm.op.status() != 0:
+            raise RuntimeError(f"device status word set in graph replay ({arm.name})")
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    res = {}
     with ClockSampler(dev.index) as clk:
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            e0, e1, e2 = evs[i]
-            e0.record(stream)
-            if args.graph:
-                g_build.replay()
-            else:
-                op.refactor()
-            e1.record(stream)
-            if args.graph:
-                g_apply.replay()
-            else:
-                f = op.incident(dirs)
-                op.apply(f, want_sigma=True, scratch=scratch, coef=coef, sigma=sigma)
-            e2.record(stream)
-        torch.cuda.synchronize()
+        for arm in arms:
+            res[arm.name] = time_steps(arm, args.steps, flush, stream)
         if ws > 1:
             torch.distributed.barrier()
-        # dominant-kernel timing: the fill kernel alone, same stream, L2 flushed
-        fev = []
-        for i in range(5):
-            flush.fill_(i)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            op.fill_modes(out=fill_out)
-            b.record(stream)
-            fev.append((a, b))
-        torch.cuda.synchronize()
-    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
-    build_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
-    apply_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
-    fill_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
-    ms = slowest_rank_ms(float(np.mean(step_ms)), dev)
+    ms = slowest_rank_ms(res[head.name][0], dev)
     value = job_value(ws, qr_fl + ap_fl, ms)
+    coef_dev = {arm.name: arm.coef.cpu().numpy() for arm in arms}
+
+    # kernel profile of the headline arm (separate, untimed pass)
+    prof = kernel_profile(head, 3, flush)
+    split = head.name == "split"
+    roof = roofline_from_profile(prof, args.slices, split, pk, pk_src)
+    total_prof = sum(v["ms"] for v in prof.values())
 
     # end to end through the public API with host buffers: H2D of the wave
     # directions from pinned memory, build + apply, D2H of the coefficients
     dirs_host = torch.tensor(dirs_np).pin_memory()
-    coef_host = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128).pin_memory()
+    coef_host = torch.empty(tuple(head.coef.shape), dtype=torch.complex128).pin_memory()
     e2e = []
     for i in range(max(3, min(args.steps, 10))):
         flush.fill_(i & 0xFF)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         dirs.copy_(dirs_host, non_blocking=True)
-        step()
-        coef_host.copy_(coef, non_blocking=True)
+        head.step_direct()
+        coef_host.copy_(head.coef, non_blocking=True)
         b.record(stream)
         b.synchronize()
         e2e.append(a.elapsed_time(b))
     e2e_ms = slowest_rank_ms(float(np.mean(e2e[1:])), dev)
-    h2d = dirs_host.numel() * 8
-    d2h = coef_host.numel() * 16
-
-    kinds = ["deriv"] if ob.bc == synth.BC_NEUMANN else ["value", "deriv", "value", "deriv"]
-    slots = fill_slots(ob.M, ob.N, ob.P, spec.q, kinds, args.prec == "split")
-    ach = 2.0 * slots / (fill_ms * 1e-3) / 1e12          # one slot = one FMA = 2 flops
-    launches_per_step = step_launches(ob, spec, args.prec == "split", args.slices)
     torch.cuda.synchronize()
-    status = op.status()
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-            "precision": (f"split-bf16 {args.slices} digits (QR trailing updates, Q^H, TRSM off-diagonal "
-                          "blocks; fill transform 8 digits); "
-                          "fill samples, panels, T, TRSM diagonal blocks, transforms FP64") if args.prec == "split"
-                         else "native fp64",
-            "build_ms": float(np.mean(build_ms)),
-            "build_tflops": qr_fl / (np.mean(build_ms) * 1e-3) / 1e12,
-            "apply_us_per_wave": float(np.mean(apply_ms)) * 1e3 / W,
-            "e2e": {"value": job_value(ws, qr_fl + ap_fl, e2e_ms), "unit": "TFLOP/s",
-                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"kernel": ("fill_samples_kernel + fill_gemm_tc_kernel (FP64 samples, "
-                                    "tcgen05 transform)") if args.prec == "split"
-                                   else "fill_fft_kernel",
-                         "bound": "alu", "achieved": ach,
-                         "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_DFMA_PEAK_TFLOPS, "traffic": FILL_TRAFFIC_BYTES[args.prec],
-                         "work": "FP64 issue slots of the kernel's arithmetic x 2 flops "
-                                 f"({slots:.4g} slots per launch)",
-                         "peak_source": "FP64 DFMA probe of measured (MEASURED_PEAKS.json has "
-                                        "no FP64 entry)",
-                         "kernel_ms": fill_ms},
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(),
-            "device_status": status,
-        }
-        if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline_line(ob, dirs_np)
-        print(json.dumps(line))
+    status = {arm.name: arm.op.status() for arm in arms}
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    s_ms, s_build, s_apply = res[head.name]
+    prec_txt = (f"split-bf16 {args.slices} digits: QR trailing updates beyond the next panel, Q^H "
+                "and the off-diagonal blocks of the back substitution as BF16 digit products on "
+                "tensor cores; the fill's modal transform as an 8-digit product; ring samples, "
+                "Householder panels, the next panel's update, T, W' and the diagonal blocks of "
+                "the back substitution in FP64") if split else "native fp64"
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "precision": head.name, "M": ob.M, "N": ob.N, "P": ob.P,
+                   "q": spec.q, "k": ob.k, "waves": W, "distinct_modes": ob.P // 2 + 1,
+                   "l2": "flushed (256 MB write) before each timed step",
+                   "launch": "CUDA graph replay" if args.graph else "direct launches"},
+        "precision": prec_txt,
+        "build_ms": s_build, "build_tflops": qr_fl / (s_build * 1e-3) / 1e12,
+        "apply_us_per_wave": s_apply * 1e3 / W,
+        "e2e": {"value": job_value(ws, qr_fl + ap_fl, e2e_ms), "unit": "TFLOP/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": dirs_host.numel() * 8,
+                "d2h_bytes_per_step": coef_host.numel() * 16},
+        "roofline": roof,
+        "kernel_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                               "share": round(v["ms"] / total_prof, 4),
+                               "tflops_fp64_equiv": (v["flops"] / (v["ms"] * 1e-3) / 1e12
+                                                     if v["flops"] > 0 else None)}
+                           for k, v in prof.items()},
+        "gpu_launches": step_launches(prof) * args.steps * len(arms),
+        "clocks": clk.summary(),
+        "device_status": status,
+    }
+    for arm in arms[1:]:
+        a_ms, a_build, a_apply = res[arm.name]
+        line[f"{arm.name}_arm"] = {
+            "value": job_value(ws, qr_fl + ap_fl, slowest_rank_ms(a_ms, dev)), "ms_per_step": a_ms,
+            "build_ms": a_build, "apply_us_per_wave": a_apply * 1e3 / W,
+            "headline_speedup": a_ms / s_ms}
+    if not args.no_cpu_baseline and ws == 1:
+        xh = synth.plane_wave_directions(64, 99)
+        dt, A, fh, c_ora, F_ora = oracle_full(ob, dirs_np, xh)
+        line["cpu_baseline"] = {
+            "value": (qr_fl + ap_fl) / dt / 1e12, "unit": "TFLOP/s", "cores": blas_threads(),
+            "kind": "oracle", "seconds_per_step": dt,
+            "sample": f"the whole workload once: fill, QR of all {ob.P // 2 + 1} distinct modes, "
+                      f"solve of {W} waves (numpy FP64; BLAS calls threaded over the cores, "
+                      "elementwise kernels single-threaded)"}
+        par = {}
+        xh_t = torch.tensor(xh, device=dev)
+        for arm in arms:
+            F = arm.op.eval_field(torch.tensor(coef_dev[arm.name], device=dev), xh_t,
+                                  axi.EVAL_FAR_FIELD).cpu().numpy()
+            e_bd, e_ff = parity(A, ob, fh, c_ora, F_ora, coef_dev[arm.name], F)
+            par[arm.name] = {"e_bd": e_bd, "e_ff": e_ff}
+        line["parity_vs_oracle"] = par
+    print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
 def run_extra_workload(args):
     """Device-timed lines for the other workloads (one GPU, CUDA events, L2 flushed):
-    cup      cup k=25, N=360, M=432, P=180: build + 16-wave apply per step
     batched  64 seeded obstacles in one plan: build of all + 4 waves applied to each
     cup_near cup factors built once; per step a 256-wave apply + the 3x3 near-image sum
     """
@@ -448,11 +560,10 @@ def run_extra_workload(args):
     if args.workload == "batched":
         wl = synth.config_batched()
         specs = [axi.spec_from_obstacle(o) for o in wl.obstacles]
-        W = wl.n_waves
     else:
-        wl = synth.config_cup() if args.workload == "cup" else synth.config_cup_apply()
+        wl = synth.config_cup_apply()
         specs = [axi.spec_from_obstacle(wl.obstacles[0])]
-        W = wl.n_waves
+    W = wl.n_waves
     op = axi.Operator(specs, prec=prec)
     qr_fl = sum((s.P // 2 + 1) * (8.0 * s.rows * s.cols ** 2 - 8.0 * s.cols ** 3 / 3) for s in specs)
     ap_fl = sum(W * s.P * (16.0 * s.rows * s.cols - 4.0 * s.cols ** 2) for s in specs)
@@ -521,6 +632,37 @@ def run_extra_workload(args):
     if near:
         line["near_image_pairs_per_s"] = 8.0 * s0.M * s0.P * s0.N * s0.P * W / (apply_ms * 1e-3)
     print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="time only the split-precision plan")
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"],
+                    help="headline plan: Ozaki BF16 digits or native FP64")
+    ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the step's kernels directly instead of replaying CUDA graphs")
+    ap.add_argument("--workload", default="cup", choices=["cup", "smooth", "batched", "cup_near"],
+                    help="cup (default, the headline), smooth; batched and cup_near print their "
+                         "own device-timed lines")
+    args = ap.parse_args()
+    if args.workload in ("batched", "cup_near"):
+        run_extra_workload(args)
+        return
+    wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
+    if args.impl == "reference":
+        ws, rank, _ = dist_env()
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, wl)))
+        return
+    run_single(args, wl)
 
 
 if __name__ == "__main__":

@@ -164,6 +164,30 @@ typedef struct axi_operator_s axi_operator;
 axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
                            axi_plan **plan);
 
+/*
+ * Schedule tuning (the paper has no counterpart): the choices the build
+ * makes that do not change what it computes, as a flat JSON object of
+ * integers:
+ *   "next_update"   0 auto, 1 native FP64, 2 BF16 digits (split plans) for
+ *                   the next panel's columns of each step;
+ *   "panel_cluster" 0 auto (by the number of (obstacle, mode) tasks), or 1,
+ *                   2, 4 CTAs per mode for the Householder panels;
+ *   "rest_grid"     0 one CTA per (task, column tile), 1 persistent (one CTA
+ *                   per SM) for the trailing updates of split plans.
+ * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
+ * keys kept; AXI_ERR_ARG on malformed input or values out of range);
+ * axi_plan_get_tuning writes the current one into buf[n] (AXI_ERR_ARG if it
+ * does not fit). axi_operator_autotune times every candidate schedule with
+ * CUDA events on `stream` (one warm-up and `reps` builds each, reps in
+ * 1..100; it synchronises the stream, so not under stream capture), keeps the
+ * fastest in the plan, rebuilds the operator with it and, when json_out is
+ * not NULL, writes the choice with its build time ("build_ms") and the number
+ * of candidates. Caching the result is the caller's: pass it back with
+ * axi_plan_set_tuning before axi_build_operator.
+ */
+axi_status axi_plan_set_tuning(axi_plan *plan, const char *json);
+axi_status axi_plan_get_tuning(const axi_plan *plan, char *buf, size_t n);
+
 /* Bytes of device workspace the plan needs (256-byte aligned base required). */
 axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes);
 
@@ -189,6 +213,23 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes,
  * in a CUDA graph. Errors: AXI_ERR_ARG, AXI_ERR_CUDA.
  */
 axi_status axi_refactor_operator(axi_operator *op, void *stream);
+
+/* See axi_plan_set_tuning. Errors: AXI_ERR_ARG, AXI_ERR_CUDA. */
+axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, char *json_out,
+                                 size_t n);
+
+/*
+ * axi_refactor_operator_modes -- factor given modal matrices instead of the
+ * fill's (Sec. 3, eq. linsys): for each obstacle i with h_modes[i] != NULL,
+ * the D matrices at device address h_modes[i] ([D][cols][rows], the layout
+ * axi_fill_modes writes) are copied into the operator and factored; obstacles
+ * with h_modes[i] == NULL are filled as usual. h_modes is a host array of
+ * n_obs device pointers, read during the call. A non-finite entry shows as
+ * AXI_ERR_NUMERIC from axi_operator_status after the stream is synchronised.
+ * Asynchronous; no allocation. Errors: AXI_ERR_ARG, AXI_ERR_CUDA.
+ */
+axi_status axi_refactor_operator_modes(axi_operator *op, const axi_c128 *const *h_modes,
+                                       void *stream);
 
 /*
  * axi_fill_modes -- the fill step alone (Sec. 3.1, eq. ptr): write the D
@@ -392,6 +433,15 @@ axi_status axi_diag_sincos(const double *d_x, int32_t n, double *d_sin, double *
  * the table to a static device array (16 KB). Same arguments and errors. */
 axi_status axi_diag_sincos_table(const double *d_x, int32_t n, double *d_sin, double *d_cos,
                                  void *stream);
+
+/* axi_diag_wait_timeout -- diagnostics of the failure path of the library's
+ * bounded device waits (the paper has no counterpart): one CTA allocates
+ * tensor memory, waits on an mbarrier that nothing completes with the same
+ * bounded wait the tcgen05 kernels use, limited to max_cycles SM clocks,
+ * then latches AXI_ERR_TIMEOUT in the operator's status word, frees the
+ * tensor memory and returns; the context stays usable and the next build
+ * clears the word. max_cycles in [1, 2^34]. Errors: AXI_ERR_ARG, AXI_ERR_CUDA. */
+axi_status axi_diag_wait_timeout(const axi_operator *op, int64_t max_cycles, void *stream);
 
 #ifdef __cplusplus
 }

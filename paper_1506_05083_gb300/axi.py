@@ -59,8 +59,13 @@ SIGNATURES = [
                                    C.POINTER(C.c_uint8)]),
     ("axi_plan_create", C.c_int, [C.POINTER(_Obstacle), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     ("axi_plan_workspace_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    ("axi_plan_set_tuning", C.c_int, [_vp, C.c_char_p]),
+    ("axi_plan_get_tuning", C.c_int, [_vp, C.c_char_p, C.c_size_t]),
+    ("axi_operator_autotune", C.c_int, [_vp, C.c_int32, _vp, C.c_char_p, C.c_size_t]),
     ("axi_build_operator", C.c_int, [_vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
     ("axi_refactor_operator", C.c_int, [_vp, _vp]),
+    ("axi_refactor_operator_modes", C.c_int, [_vp, C.POINTER(_vp), _vp]),
+    ("axi_diag_wait_timeout", C.c_int, [_vp, C.c_int64, _vp]),
     ("axi_fill_modes", C.c_int, [_vp, C.c_int32, _vp, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
@@ -180,7 +185,7 @@ class Operator:
     """Plan + workspace + built operator (axi_plan_create / axi_build_operator)."""
 
     def __init__(self, specs: List[ObstacleSpec], prec: int = PREC_FP64, device="cuda",
-                 stream=None):
+                 stream=None, tuning: Optional[str] = None):
         self.specs = specs
         arr = (_Obstacle * len(specs))()
         for i, s in enumerate(specs):
@@ -189,6 +194,8 @@ class Operator:
         plan = C.c_void_p()
         _check(lib().axi_plan_create(arr, len(specs), prec, C.byref(plan)), "axi_plan_create")
         self._plan = plan
+        if tuning is not None:
+            _check(lib().axi_plan_set_tuning(plan, tuning.encode()), "axi_plan_set_tuning")
         nb = C.c_size_t(0)
         _check(lib().axi_plan_workspace_bytes(plan, C.byref(nb)), "axi_plan_workspace_bytes")
         self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
@@ -206,6 +213,23 @@ class Operator:
         except Exception:
             pass
 
+    def tuning(self) -> str:
+        """axi_plan_get_tuning: the plan's schedule choices as JSON."""
+        buf = C.create_string_buffer(256)
+        _check(lib().axi_plan_get_tuning(self._plan, buf, 256), "axi_plan_get_tuning")
+        return buf.value.decode()
+
+    def set_tuning(self, json_text: str):
+        """axi_plan_set_tuning (takes effect at the next build)."""
+        _check(lib().axi_plan_set_tuning(self._plan, json_text.encode()), "axi_plan_set_tuning")
+
+    def autotune(self, reps=3, stream=None) -> str:
+        """axi_operator_autotune: time every candidate schedule, keep the fastest."""
+        buf = C.create_string_buffer(512)
+        _check(lib().axi_operator_autotune(self._op, reps, _stream(stream), buf, 512),
+               "axi_operator_autotune")
+        return buf.value.decode()
+
     def refactor(self, stream=None):
         _check(lib().axi_refactor_operator(self._op, _stream(stream)), "axi_refactor_operator")
 
@@ -219,6 +243,26 @@ class Operator:
         _check(lib().axi_operator_profile_read(self._op, C.cast(arr, C.c_void_p)),
                "axi_operator_profile_read")
         return {k: (arr[i].launches, arr[i].ms, arr[i].flops) for i, k in enumerate(KERNEL_KINDS)}
+
+    def refactor_from_modes(self, modes, stream=None):
+        """axi_refactor_operator_modes: factor the given [D][cols][rows] complex128
+        device tensors (None = fill that obstacle as usual)."""
+        arr = (_vp * len(self.specs))()
+        for i, m in enumerate(modes):
+            if m is not None:
+                s = self.specs[i]
+                if (tuple(m.shape) != (s.P // 2 + 1, s.cols, s.rows) or m.dtype != torch.complex128
+                        or not m.is_contiguous() or m.device != self.workspace.device):
+                    raise ValueError(f"modes[{i}] must be a contiguous complex128 tensor of shape "
+                                     f"{(s.P // 2 + 1, s.cols, s.rows)} on {self.workspace.device}")
+                arr[i] = m.data_ptr()
+        _check(lib().axi_refactor_operator_modes(self._op, arr, _stream(stream)),
+               "axi_refactor_operator_modes")
+
+    def diag_wait_timeout(self, max_cycles: int, stream=None):
+        """axi_diag_wait_timeout: a bounded device wait that runs out (status AXI_ERR_TIMEOUT)."""
+        _check(lib().axi_diag_wait_timeout(self._op, int(max_cycles), _stream(stream)),
+               "axi_diag_wait_timeout")
 
     def status(self) -> int:
         return lib().axi_operator_status(self._op)

@@ -3,7 +3,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "axi_internal.h"
@@ -110,6 +113,7 @@ axi_status fill_strides(ObsHost &h, int M, int N, int P, int q, bool transmissio
 struct axi_plan_s {
   std::vector<ObsHost> obs;
   int prec = 0;
+  axi::Tuning tune;                       // schedule choices (axi_plan_set_tuning / autotune)
   size_t off_fgdig = 0, off_fgex = 0;     // split fill: sample-digit scratch (shared)
   std::vector<int> task_obs, task_mode;   // sorted by obstacle panel count, descending
   std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
@@ -184,6 +188,7 @@ axi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? AXI_OK : AXI_E
 }  // namespace
 
 int axi::operator_device(const axi_operator *op) { return op ? op->device : -1; }
+int *axi::operator_status_word(const axi_operator *op) { return op ? op->d_status : nullptr; }
 
 namespace {
 
@@ -255,6 +260,58 @@ axi_status validate(const axi_obstacle &o) {
       }
     }
   }
+  return AXI_OK;
+}
+
+// Tuning as a flat JSON object of integers, e.g.
+// {"next_update": 2, "panel_cluster": 1, "rest_grid": 0}; unknown keys are
+// ignored, missing keys keep their value.
+bool parse_tuning(const char *js, axi::Tuning &t) {
+  if (!js) return false;
+  const char *c = js;
+  while (*c && *c != '{') ++c;
+  if (*c != '{') return false;
+  ++c;
+  while (true) {
+    while (*c == ' ' || *c == '\n' || *c == '\t' || *c == '\r' || *c == ',') ++c;
+    if (*c == '}') return true;
+    if (*c != '"') return false;
+    const char *k0 = ++c;
+    while (*c && *c != '"') ++c;
+    if (*c != '"') return false;
+    const std::string key(k0, c - k0);
+    ++c;
+    while (*c == ' ') ++c;
+    if (*c != ':') return false;
+    ++c;
+    char *end = nullptr;
+    const double v = std::strtod(c, &end);
+    if (end == c) return false;
+    c = end;
+    const int iv = (int)v;
+    if (key == "next_update") {
+      if (iv < 0 || iv > 2) return false;
+      t.next_update = iv;
+    } else if (key == "panel_cluster") {
+      if (iv != 0 && iv != 1 && iv != 2 && iv != 4) return false;
+      t.panel_cluster = iv;
+    } else if (key == "rest_grid") {
+      if (iv < 0 || iv > 1) return false;
+      t.rest_grid = iv;
+    }
+  }
+}
+
+std::string tuning_json(const axi::Tuning &t) {
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d}",
+                t.next_update, t.panel_cluster, t.rest_grid);
+  return buf;
+}
+
+axi_status copy_out(const std::string &js, char *buf, size_t n) {
+  if (!buf || n < js.size() + 1) return AXI_ERR_ARG;
+  std::memcpy(buf, js.c_str(), js.size() + 1);
   return AXI_OK;
 }
 
@@ -461,6 +518,19 @@ axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes) {
   return AXI_OK;
 }
 
+axi_status axi_plan_set_tuning(axi_plan *plan, const char *json) {
+  if (!plan) return AXI_ERR_ARG;
+  axi::Tuning t = plan->tune;
+  if (!parse_tuning(json, t)) return AXI_ERR_ARG;
+  plan->tune = t;
+  return AXI_OK;
+}
+
+axi_status axi_plan_get_tuning(const axi_plan *plan, char *buf, size_t n) {
+  if (!plan) return AXI_ERR_ARG;
+  return copy_out(tuning_json(plan->tune), buf, n);
+}
+
 axi_status axi_plan_destroy(axi_plan *plan) {
   delete plan;
   return AXI_OK;
@@ -474,13 +544,20 @@ axi_status axi_plan_destroy(axi_plan *plan) {
 // so panel(p+1) and the small next-panel update form the critical path while
 // the bulk of each trailing update runs beside them. The columns beyond of
 // step p-1 include the next panel's columns of step p, hence the wait.
-static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
+static axi_status run_build(axi_operator_s *op, cudaStream_t st,
+                            const axi_c128 *const *modes = nullptr) {
   axi_plan_s *p = op->plan;
   ProfScope scope(op->prof());
   cudaError_t e = cudaMemsetAsync(op->d_status, 0, sizeof(int), st);
   if (e != cudaSuccess) return AXI_ERR_CUDA;
   for (size_t i = 0; i < p->obs.size(); ++i) {
     const ObsDev &d = p->obs[i].dev;
+    if (modes && modes[i]) {              // the caller's modal matrices instead of the fill
+      e = cudaMemcpyAsync(d.A, modes[i], sizeof(double2) * (size_t)d.D * d.cols * d.rows,
+                          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return AXI_ERR_CUDA;
+      continue;
+    }
     const int pid = axi::prof_begin(AXI_KERNEL_FILL, st);
     e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st);
     axi::prof_end(pid, st);
@@ -493,10 +570,17 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
     int pid = axi::prof_begin(AXI_KERNEL_PANEL, st);
+    bool panel_digits = false;
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
-                             p->step_rows[s], slices, st);
+                             p->step_rows[s], slices, p->tune.panel_cluster, st, &panel_digits);
     axi::prof_end(pid, st, p->step_fl_panel[s]);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
+    if (panel_digits) {                 // the digits right behind the panel, over the whole GPU
+      pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, st);
+      e = axi::launch_vdigits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max, st);
+      axi::prof_end(pid, st);
+      if (e != cudaSuccess) return AXI_ERR_CUDA;
+    }
     const int rest_cols = p->step_cols[s] - axi::kNB;
     // kept digits: every panel's digits are written (the apply reads them),
     // also at the last steps that have no trailing update
@@ -510,11 +594,16 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     rest_pending = false;
     if (p->step_cols[s] > 0) {
       pid = axi::prof_begin(AXI_KERNEL_UPDATE_NEXT, st);
-      e = axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
+      // split plans whose panel wrote its digits update the next panel's
+      // columns in split precision too; otherwise in native FP64
+      e = panel_digits && p->tune.next_update != 1
+              ? axi::launch_qr_update_next_split(op->d_obs, op->d_task_obs, op->d_task_mode, nt,
+                                                 (int)s, slices, p->step_rows[s], st)
+              : axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
       axi::prof_end(pid, st, p->step_fl_next[s]);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
     }
-    if (digits_here) {
+    if (digits_here && !panel_digits) {
       pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, op->side);
       e = axi::launch_panel_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
                                    kp_max, op->side);
@@ -525,7 +614,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st) {
     if (rest_cols > 0) {
       pid = axi::prof_begin(AXI_KERNEL_UPDATE_REST, op->side);
       e = axi::launch_qr_update_rest(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
-                                     rest_cols, op->side);
+                                     rest_cols, p->tune.rest_grid == 1, op->side);
       axi::prof_end(pid, op->side, p->step_fl_rest[s]);
       if (e != cudaSuccess || cudaEventRecord(op->ev_rest, op->side) != cudaSuccess)
         return AXI_ERR_CUDA;
@@ -643,6 +732,11 @@ axi_status axi_refactor_operator(axi_operator *op, void *stream) {
   return run_build(op, static_cast<cudaStream_t>(stream));
 }
 
+axi_status axi_refactor_operator_modes(axi_operator *op, const axi_c128 *const *h_modes, void *stream) {
+  if (!op || !h_modes) return AXI_ERR_ARG;
+  return run_build(op, static_cast<cudaStream_t>(stream), h_modes);
+}
+
 axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, void *stream) {
   if (!op || !d_out || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;
@@ -753,6 +847,68 @@ axi_status axi_operator_status(const axi_operator *op) {
     return AXI_ERR_CUDA;
   if (s & axi::kStatTimeout) return AXI_ERR_TIMEOUT;
   if (s & axi::kStatNonFinite) return AXI_ERR_NUMERIC;
+  return AXI_OK;
+}
+
+axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, char *json_out,
+                                 size_t n) {
+  if (!op || reps < 1 || reps > 100) return AXI_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  axi_plan_s *p = op->plan;
+  const axi::Tuning keep = p->tune;
+  const bool split = p->obs[0].dev.slices > 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return AXI_ERR_CUDA;
+  }
+  axi::Tuning best = keep;
+  double best_ms = 1e300;
+  int tried = 0;
+  axi_status s = AXI_OK;
+  for (int nu : {1, 2}) {
+    if (nu == 2 && !split) continue;
+    for (int pc : {1, 2, 4})
+      for (int rg : {0, 1}) {
+        p->tune.next_update = nu;
+        p->tune.panel_cluster = pc;
+        p->tune.rest_grid = rg;
+        s = run_build(op, st);                           // warm-up of this schedule
+        if (s != AXI_OK) break;
+        if (cudaEventRecord(a, st) != cudaSuccess) { s = AXI_ERR_CUDA; break; }
+        for (int r = 0; r < reps && s == AXI_OK; ++r) s = run_build(op, st);
+        if (s != AXI_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+          s = AXI_ERR_CUDA;
+          break;
+        }
+        ++tried;
+        if (ms / reps < best_ms) {
+          best_ms = ms / reps;
+          best = p->tune;
+        }
+      }
+    if (s != AXI_OK) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (s != AXI_OK) {
+    p->tune = keep;
+    return s;
+  }
+  p->tune = best;
+  s = run_build(op, st);                                 // leave the operator built with it
+  if (s != AXI_OK) return s;
+  if (json_out) {
+    std::string js = tuning_json(best);
+    char tail[96];
+    std::snprintf(tail, sizeof(tail), ", \"build_ms\": %.4f, \"candidates\": %d}", best_ms, tried);
+    js.pop_back();
+    js += tail;
+    return copy_out(js, json_out, n);
+  }
   return AXI_OK;
 }
 

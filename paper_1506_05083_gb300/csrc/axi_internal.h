@@ -15,6 +15,13 @@ constexpr int kFillDigits = 8;        // digits of the split fill transform (bot
 constexpr int kPanelSmemRows = 864;  // panels up to this many rows are factored in shared memory
 constexpr int kPlanFullFillGrid = 1 << 16;   // AXI_PLAN_FULL_FILL_GRID
 
+// Schedule choices of a plan (axi_plan_set_tuning, axi_operator_autotune).
+struct Tuning {
+  int next_update = 0;    // 0 auto, 1 native FP64, 2 split digits (split plans)
+  int panel_cluster = 0;  // 0 auto (by the number of tasks), else 1, 2 or 4 CTAs per mode
+  int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM)
+};
+
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
 enum : int { kStatNonFinite = 1, kStatTimeout = 2 };
 
@@ -105,6 +112,8 @@ inline void prof_end(int id, cudaStream_t st, double flops = 0.0) {
 
 // CUDA device an operator was built on (api.cu); -1 for a null handle.
 int operator_device(const axi_operator *op);
+// The operator's device status word (api.cu).
+int *operator_status_word(const axi_operator *op);
 
 // The split fill's transform runs on tcgen05 when its group sums stay exact
 // in FP32 over the whole contraction (folded length Lp <= 448) and the
@@ -147,19 +156,34 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
 size_t fill_gemm_smem(int MR);
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
                         double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
+// Sets *digits_written when the panel kernel also wrote the exponents of the
+// panel's reflector columns, so that launch_vdigits can write the digits
+// (split plans, panels in shared memory).
+// cluster: CTAs per mode for shared-memory panels (0 = by the number of tasks).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int panel, int max_panel_rows, int slices, cudaStream_t st);
+                            int ntasks, int panel, int max_panel_rows, int slices, int cluster,
+                            cudaStream_t st, bool *digits_written);
 // Trailing update of panel step `panel`: the next panel's kNB columns (native
 // FP64, critical path), and the columns beyond (split or FP64; col_off = kNB).
 cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int panel, cudaStream_t st);
+// Split plans: digits of panel p's reflectors over the whole GPU, after a
+// panel kernel that wrote the reflector columns' exponents.
+cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                           int ntasks, int p, int kp_max, cudaStream_t st);
+// Split plans: the next panel's columns in split precision, rows of each mode
+// spread over a cluster (needs the panel's digits; max_rows = tallest panel).
+cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
+                                        const int *d_task_mode, int ntasks, int panel, int slices,
+                                        int max_rows, cudaStream_t st);
 cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int panel, int slices,
-                                  int max_rest_cols, cudaStream_t st);
+                                  int max_rest_cols, bool persistent, cudaStream_t st);
 int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel, int slices,
-                                   int col_off, int ntiles, int max_cols, cudaStream_t st);
+                                   int col_off, int ntiles, int max_cols, bool persistent,
+                                   cudaStream_t st);
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);

@@ -1,6 +1,7 @@
 // Diagnostics entry points (not part of the method): expose device helpers
 // so the tests can compare them with CUDA's own routines.
 #include "axi_internal.h"
+#include "tcgen05.cuh"
 #include "trig.cuh"
 
 #include <mutex>
@@ -26,6 +27,30 @@ __global__ void diag_sincos_tab_kernel(const double *__restrict__ x, int n, cons
 
 // the table variant's table, uploaded once per device on first use
 __device__ double2 g_diag_ring_tab[trig::kRingTab];
+
+// The failure path of the tcgen05 kernels, without their work: one CTA takes
+// tensor memory, waits with the kernels' bounded wait (tc::mbar_wait) on an
+// mbarrier that nothing completes, and when the limit runs out latches the
+// timeout bit of the status word, releases its tensor memory and returns.
+__global__ void __launch_bounds__(128)
+diag_wait_timeout_kernel(long long max_cycles, int *__restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
+  if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, max_cycles)) atomicOr(status, kStatTimeout);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem_base, 32);
+  }
+}
 
 }  // namespace
 }  // namespace axi
@@ -66,5 +91,12 @@ extern "C" axi_status axi_diag_sincos_table(const double *d_x, int32_t n, double
   if (blocks > 152 * 8) blocks = 152 * 8;
   axi::diag_sincos_tab_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_x, n, gtab, d_sin,
                                                                                      d_cos);
+  return cudaGetLastError() == cudaSuccess ? AXI_OK : AXI_ERR_CUDA;
+}
+
+extern "C" axi_status axi_diag_wait_timeout(const axi_operator *op, int64_t max_cycles, void *stream) {
+  if (!op || max_cycles < 1 || max_cycles > ((int64_t)1 << 34)) return AXI_ERR_ARG;
+  axi::diag_wait_timeout_kernel<<<1, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      (long long)max_cycles, axi::operator_status_word(op));
   return cudaGetLastError() == cudaSuccess ? AXI_OK : AXI_ERR_CUDA;
 }

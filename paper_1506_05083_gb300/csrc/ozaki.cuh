@@ -43,6 +43,12 @@ __device__ __forceinline__ unsigned long long abs_key(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
+// Largest key of the real and imaginary parts of a complex value.
+__device__ __forceinline__ unsigned long long abs_key2(double2 v) {
+  const unsigned long long a = abs_key(v.x), b = abs_key(v.y);
+  return a > b ? a : b;
+}
+
 // Exponent e with |x| < 2^e for the largest key (0 for an all-zero set).
 __device__ __forceinline__ int key_exponent(unsigned long long key) {
   if (key == 0) return 0;

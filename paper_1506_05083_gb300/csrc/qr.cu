@@ -466,6 +466,58 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
     double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
     for (int e = tid; e < kNB * kNB; e += NT) Tg[e] = Tsh[e % kNB][e / kNB];
   }
+  if (o.slices == 0) return;
+
+  // Split plans: the exponent of each reflector column (the largest |V(i, a)|
+  // over all rows, unit diagonal included) for the digits of V^H, which
+  // vdigits_kernel (qr_split.cu) writes next over the whole GPU.
+  const int kp = o.kp;
+  const int dslot = o.dig_kept ? p : (p & 1);
+  int *vex = o.vexp + ((size_t)d * o.dig_nslot + dslot) * (kNB + kp);
+  __shared__ unsigned long long colkey[kNB], wkey[kW][kNB];
+  {
+    unsigned long long m[kNB];
+#pragma unroll
+    for (int a = 0; a < kNB; ++a) m[a] = 0ull;
+    for (int sl = tid; sl < Kl; sl += NT) {
+      const int i = row_of(sl);
+      if (i >= K) break;
+#pragma unroll
+      for (int a = 0; a < kNB; ++a) {
+        const double2 v = (a >= nbp || i < a) ? make_double2(0.0, 0.0)
+                          : (i == a ? make_double2(1.0, 0.0) : Ps[a * Kl + sl]);
+        const unsigned long long k = oz::abs_key2(v);
+        m[a] = k > m[a] ? k : m[a];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < kNB; ++a) {
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, m[a], o2);
+        m[a] = w > m[a] ? w : m[a];
+      }
+      if (lane == 0) wkey[warp][a] = m[a];
+    }
+  }
+  __syncthreads();
+  if (tid < kNB) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < kW; ++w) m = wkey[w][tid] > m ? wkey[w][tid] : m;
+    colkey[tid] = m;
+  }
+  csync();                                       // every CTA's column maxima
+  if (rank == 0 && tid < kNB) {
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const unsigned long long *ck = colkey;
+      if constexpr (C > 1) ck = cg::this_cluster().map_shared_rank(colkey, r);
+      m = ck[tid] > m ? ck[tid] : m;
+    }
+    vex[tid] = oz::key_exponent(m);
+  }
+  csync();                                       // remote reads done before any CTA leaves
 }
 
 // ---------------------------------------------------------------------------
@@ -767,14 +819,17 @@ int sm_count() {
 // The panel is bound by the FP64 pipe of the SMs that factor it: when the
 // step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int max_panel_rows, int slices, cudaStream_t st) {
-  (void)slices;
+                            int ntasks, int p, int max_panel_rows, int slices, int cluster,
+                            cudaStream_t st, bool *digits_written) {
+  // the shared-memory panel also writes the reflector columns' exponents,
+  // after which vdigits_kernel writes split plans' digits (launch_vdigits)
+  *digits_written = slices > 0 && max_panel_rows <= kPanelSmemRows;
   if (ntasks <= 0) return cudaSuccess;
   if (max_panel_rows <= kPanelSmemRows) {
     const int sms = sm_count();
-    if (4 * ntasks <= sms)
+    if (cluster == 4 || (cluster == 0 && 4 * ntasks <= sms))
       return launch_panel_cluster<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
-    if (2 * ntasks <= sms)
+    if (cluster == 2 || (cluster == 0 && 2 * ntasks <= sms))
       return launch_panel_cluster<2>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
     return launch_panel_cluster<1>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
   }
@@ -798,13 +853,13 @@ cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
 // Columns from kNB past the panel onward, native FP64 or split digits.
 cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int p, int slices,
-                                  int max_rest_cols, cudaStream_t st) {
+                                  int max_rest_cols, bool persistent, cudaStream_t st) {
   if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
   if (slices > 0)
     return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, kNB,
                                   (max_rest_cols + split_update_tile_cols() - 1) /
                                       split_update_tile_cols(),
-                                  split_update_tile_cols(), st);
+                                  split_update_tile_cols(), persistent, st);
   static const bool carve = (prefer_max_shared(qr_update_kernel<kTN>), true);
   (void)carve;
   qr_update_kernel<kTN><<<dim3(ntasks, (max_rest_cols + kTN - 1) / kTN), kThreads, 0, st>>>(

@@ -473,30 +473,72 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   if (kout != nullptr && tid < ncols) kout[tid] = sm.kNext[tid];
 }
 
-// Three CTAs' worth of registers per SM (at most 170 each): two trailing-
-// update CTAs then leave room for a panel CTA on the same SM.
+// Work items (task, column tile) taken blockIdx.x, blockIdx.x + gridDim.x,
+// ...: a grid of one CTA per item, or a persistent grid of one CTA per SM
+// (the tuning's choice). Three CTAs' worth of registers per SM (at most 170
+// each), so two update CTAs leave room for a panel CTA on the same SM.
 template <int S>
 __global__ void __launch_bounds__(kThreads, 3)
 qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
-                       const int *__restrict__ task_mode, int p, int col_off, int max_cols) {
-  const ObsDev &o = obs[task_obs[blockIdx.x]];
-  const int d = task_mode[blockIdx.x];
-  const int k0 = p * kNB;
-  const int nbp = min(kNB, o.cols - k0);
-  const int c0 = k0 + nbp + col_off + blockIdx.y * kTN;
-  if (c0 >= o.cols) return;
-  const int ncols = min(min(kTN, max_cols), o.cols - c0);
+                       const int *__restrict__ task_mode, int p, int col_off, int max_cols,
+                       int ntasks, int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
+  for (int item = blockIdx.x; item < ntasks * ntiles; item += gridDim.x) {
+    const int task = item % ntasks, tile = item / ntasks;
+    const ObsDev &o = obs[task_obs[task]];
+    const int d = task_mode[task];
+    const int k0 = p * kNB;
+    const int nbp = min(kNB, o.cols - k0);
+    const int c0 = k0 + nbp + col_off + tile * kTN;
+    if (c0 >= o.cols) continue;                           // uniform over the CTA
+    const int ncols = min(min(kTN, max_cols), o.cols - c0);
+    double2 *A = o.A + (size_t)d * o.cols * o.rows;
+    const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+    // carried column keys: slot p mod 2 written by step p-1, slot (p+1) mod 2 for step p+1
+    const unsigned long long *kin =
+        p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
+    unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
+    const int dslot = o.dig_kept ? p : (p & 1);
+    __syncthreads();                                      // shared memory of the previous item
+    oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot),
+                                 o.rows, k0, Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin,
+                                 false, kout, sm);
+  }
+}
+
+// The next panel's columns (the kNB after panel p) in split precision, with
+// each mode's rows [k0, rows) split over a cluster of C CTAs (grid.x =
+// ntasks * C): on the critical path of the factorisation, so the rows of
+// one mode are spread over C SMs. Column exponents come from the keys the
+// previous step's trailing update carried (scanned at the first step).
+template <int S, int C>
+__global__ void __launch_bounds__(kThreads)
+qr_update_next_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                            const int *__restrict__ task_mode, int p) {
+  const int rank = (int)cg::this_cluster().block_rank();
+  const int task = blockIdx.x / C;
+  const ObsDev &o = obs[task_obs[task]];
+  const int d = task_mode[task];
+  const int k0 = p * kNB;
+  const int nbp = min(kNB, o.cols - k0);
+  const int c0 = k0 + nbp;
+  if (c0 >= o.cols) return;                             // uniform over the cluster
+  const int ncols = min(kNB, o.cols - c0);
+  const int RB = ((o.rows - k0 + C - 1) / C + 31) / 32 * 32;
+  const int rlo = k0 + rank * RB, rhi = min(o.rows, rlo + RB);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
+  ClExtra *cx = reinterpret_cast<ClExtra *>(smraw + (sizeof(OzSmem<S>) + 15) / 16 * 16);
   double2 *A = o.A + (size_t)d * o.cols * o.rows;
   const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
-  // carried column keys: slot p mod 2 written by step p-1, slot (p+1) mod 2 for step p+1
   const unsigned long long *kin =
       p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
-  unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
   const int dslot = o.dig_kept ? p : (p & 1);
-  oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot), o.rows, k0,
-                               Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin, false, kout, sm);
+  oz_block_reflector_update<S, C>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot),
+                                  o.rows, k0, Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin,
+                                  false, nullptr, sm, cx, rlo, rhi);
+  cg::this_cluster().sync();                            // no CTA leaves while W' is being read
 }
 
 // L2 prefetch of what panel step p reads in the apply: this CTA's rows of the
@@ -624,6 +666,65 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   }
 }
 
+// Digits of panel p's reflectors over the whole GPU (split plans whose panel
+// kernel wrote the reflector columns' exponents): one CTA per (task, 64 rows
+// of the digit block), the same layout as panel_digits_kernel. The block's
+// V rows are staged in shared memory by coalesced column reads; row
+// exponents are formed here; the V^H digits are stored with consecutive
+// threads on consecutive rows, the V row digits with consecutive threads on
+// consecutive reflectors, so every store instruction writes contiguous bytes.
+constexpr int kVdRows = 64;
+__global__ void __launch_bounds__(256)
+vdigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+               const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int r0 = blockIdx.y * kVdRows;
+  const int kp = o.kp;
+  if (r0 >= kp) return;
+  const int S = o.slices;
+  const int slot = o.dig_kept ? p : (p & 1);
+  const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows;
+  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  const size_t blk = (size_t)4 * S * kNB * kp;
+  unsigned short *vh = o.vdig + ((size_t)d * o.dig_nslot + slot) * blk;
+  unsigned short *vr = vh + blk / 2;
+  int *ex = o.vexp + ((size_t)d * o.dig_nslot + slot) * (kNB + kp);
+  __shared__ double2 Vs[kNB][kVdRows + 1];
+  __shared__ int ecol[kNB], erow[kVdRows];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNB * kVdRows; e += 256) {
+    const int a = e / kVdRows, rr = e % kVdRows;
+    Vs[a][rr] = vget(A, rows, rows, k0, nbp, k0 + r0 + rr, a);
+  }
+  if (tid < kNB) ecol[tid] = ex[tid];                    // written by the panel kernel
+  __syncthreads();
+  if (tid < kVdRows) {
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int a = 0; a < kNB; ++a) {
+      const unsigned long long k = key2(Vs[a][tid]);
+      m = k > m ? k : m;
+    }
+    erow[tid] = oz::key_exponent(m);
+    ex[kNB + r0 + tid] = erow[tid];
+  }
+  __syncthreads();
+  const size_t sh = (size_t)2 * kNB * kp, sv = (size_t)2 * kp * kNB;
+  for (int e = tid; e < kNB * kVdRows; e += 256) {        // V^H: [s][part][a][r]
+    const int a = e / kVdRows, rr = e % kVdRows;
+    const double2 x = Vs[a][rr];
+    oz::split_store_n(x.x, ecol[a], S, vh + (size_t)a * kp + r0 + rr, sh);
+    oz::split_store_n(-x.y, ecol[a], S, vh + (size_t)(kNB + a) * kp + r0 + rr, sh);
+  }
+  for (int e = tid; e < kNB * kVdRows; e += 256) {        // V rows: [s][part][r][a]
+    const int rr = e / kNB, a = e % kNB;
+    const double2 x = Vs[a][rr];
+    oz::split_store_n(x.x, erow[rr], S, vr + (size_t)(r0 + rr) * kNB + a, sv);
+    oz::split_store_n(x.y, erow[rr], S, vr + (size_t)(kp + r0 + rr) * kNB + a, sv);
+  }
+}
+
 template <int S>
 cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st) {
@@ -641,16 +742,52 @@ cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const in
 template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int col_off, int ntiles, int max_cols,
-                            cudaStream_t st) {
+                            bool persistent, cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
   static const bool carve = (prefer_max_shared(qr_update_split_kernel<S>), true);
   (void)carve;
-  qr_update_split_kernel<S><<<dim3(ntasks, ntiles), kThreads, smem, st>>>(
-      d_obs, d_task_obs, d_task_mode, p, col_off, max_cols);
+  const int items = ntasks * ntiles;
+  const int grid = persistent ? min(items, sm_count()) : items;
+  qr_update_split_kernel<S><<<grid, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p,
+                                                          col_off, max_cols, ntasks, ntiles);
   return cudaGetLastError();
+}
+
+template <int S, int C>
+cudaError_t launch_next_split_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int p, cudaStream_t st) {
+  const size_t smem = (sizeof(OzSmem<S>) + 15) / 16 * 16 + sizeof(ClExtra);
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(qr_update_next_split_kernel<S, C>, smem, granted);
+  if (e != cudaSuccess) return e;
+  static const bool carve = (prefer_max_shared(qr_update_next_split_kernel<S, C>), true);
+  (void)carve;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntasks * C);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qr_update_next_split_kernel<S, C>, d_obs, d_task_obs, d_task_mode, p);
+}
+
+template <int S>
+cudaError_t launch_next_split_c(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int p, int max_rows, cudaStream_t st) {
+  // rows per CTA: a 64-row chunk or more in each member of the cluster; at
+  // most about one CTA per SM (the trailing update holds one CTA on each)
+  if (max_rows >= 256 && 4 * ntasks <= sm_count())
+    return launch_next_split_s<S, 4>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
+  return launch_next_split_s<S, 2>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
 }
 
 template <int S, int C>
@@ -702,18 +839,40 @@ int split_update_tile_cols() { return kTN; }
 
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int p, int slices,
-                                   int col_off, int ntiles, int max_cols, cudaStream_t st) {
+                                   int col_off, int ntiles, int max_cols, bool persistent,
+                                   cudaStream_t st) {
   switch (slices) {
     case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, st);
+                                          max_cols, persistent, st);
     case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, st);
+                                          max_cols, persistent, st);
     case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, st);
+                                          max_cols, persistent, st);
     case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, st);
+                                          max_cols, persistent, st);
     case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, st);
+                                          max_cols, persistent, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                           int ntasks, int p, int kp_max, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  vdigits_kernel<<<dim3(ntasks, kp_max / kVdRows), 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
+                                        const int *d_task_mode, int ntasks, int p, int slices,
+                                        int max_rows, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  switch (slices) {
+    case 4: return launch_next_split_c<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
+    case 5: return launch_next_split_c<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
+    case 6: return launch_next_split_c<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
+    case 7: return launch_next_split_c<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
+    case 8: return launch_next_split_c<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
     default: return cudaErrorInvalidValue;
   }
 }

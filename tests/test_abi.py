@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI (no GPU): the library loads, exports every
 declared entry point, and its host logic (geometry, quadrature rule,
 validation) agrees with the oracle and rejects bad input."""
+import json
 import math
 import os
 import re
@@ -128,3 +129,29 @@ def test_plan_validation(axi):
 def test_status_strings(axi):
     for c in range(-8, 1):
         assert axi.lib().axi_status_string(c)
+
+
+def test_plan_tuning_json(axi):
+    """Schedule tuning round-trips as JSON; malformed input and values out of
+    range are refused without changing the plan."""
+    import ctypes as C
+    ob = synth.small_case().obstacles[0]
+    coll, src, _ = axi.geometry(ob.shape, ob.params, ob.M, ob.N, ob.tau)
+    arr = (axi._Obstacle * 1)()
+    arr[0] = axi._Obstacle(0, ob.M, ob.N, ob.P, 64, ob.k, 0.0, axi._ptr(coll), axi._ptr(src), None)
+    plan = C.c_void_p()
+    L = axi.lib()
+    assert L.axi_plan_create(arr, 1, axi.PREC_SPLIT_BF16, C.byref(plan)) == 0
+    buf = C.create_string_buffer(256)
+    try:
+        assert L.axi_plan_get_tuning(plan, buf, 256) == 0
+        assert json.loads(buf.value.decode()) == {"next_update": 0, "panel_cluster": 0, "rest_grid": 0}
+        assert L.axi_plan_set_tuning(plan, b'{"panel_cluster": 2, "rest_grid": 1, "other": 7}') == 0
+        assert L.axi_plan_get_tuning(plan, buf, 256) == 0
+        assert json.loads(buf.value.decode()) == {"next_update": 0, "panel_cluster": 2, "rest_grid": 1}
+        for bad in (b'{"panel_cluster": 3}', b'{"next_update": 5}', b'panel_cluster: 1', b'{"rest_grid" 1}'):
+            assert L.axi_plan_set_tuning(plan, bad) == -1
+        assert json.loads(buf.value.decode())["panel_cluster"] == 2
+        assert L.axi_plan_get_tuning(plan, buf, 8) == -1          # buffer too small
+    finally:
+        L.axi_plan_destroy(plan)
