@@ -298,6 +298,9 @@ class Arm:
         self.scratch = torch.empty(self.op.apply_scratch_bytes(W), dtype=torch.uint8, device=dev)
         self.graph = graph
         self.g_build = self.g_apply = None
+        # schedule choices (panel cluster size, next-panel update arithmetic,
+        # trailing-update grid) timed on the device by the library's autotuner
+        self.tuning = json.loads(self.op.autotune(reps=2))
 
     def step_direct(self):
         self.op.refactor()
@@ -500,7 +503,8 @@ def run_single(args, wl):
         "config": {"workload": wl.name, "precision": head.name, "M": ob.M, "N": ob.N, "P": ob.P,
                    "q": spec.q, "k": ob.k, "waves": W, "distinct_modes": ob.P // 2 + 1,
                    "l2": "flushed (256 MB write) before each timed step",
-                   "launch": "CUDA graph replay" if args.graph else "direct launches"},
+                   "launch": "CUDA graph replay" if args.graph else "direct launches",
+                   "tuning": {arm.name: arm.tuning for arm in arms}},
         "precision": prec_txt,
         "build_ms": s_build, "build_tflops": qr_fl / (s_build * 1e-3) / 1e12,
         "apply_us_per_wave": s_apply * 1e3 / W,

@@ -173,7 +173,8 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *   "panel_cluster" 0 auto (by the number of (obstacle, mode) tasks), or 1,
  *                   2, 4 CTAs per mode for the Householder panels;
  *   "rest_grid"     0 one CTA per (task, column tile), 1 persistent (one CTA
- *                   per SM) for the trailing updates of split plans.
+ *                   per SM) for the trailing updates of split plans;
+ *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA.
  * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
  * keys kept; AXI_ERR_ARG on malformed input or values out of range);
  * axi_plan_get_tuning writes the current one into buf[n] (AXI_ERR_ARG if it

@@ -298,14 +298,18 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
     } else if (key == "rest_grid") {
       if (iv < 0 || iv > 1) return false;
       t.rest_grid = iv;
+    } else if (key == "panel_threads") {
+      if (iv != 0 && iv != 128 && iv != 256) return false;
+      t.panel_threads = iv;
     }
   }
 }
 
 std::string tuning_json(const axi::Tuning &t) {
-  char buf[160];
-  std::snprintf(buf, sizeof(buf), "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d}",
-                t.next_update, t.panel_cluster, t.rest_grid);
+  char buf[200];
+  std::snprintf(buf, sizeof(buf),
+                "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d}",
+                t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads);
   return buf;
 }
 
@@ -572,7 +576,8 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
     int pid = axi::prof_begin(AXI_KERNEL_PANEL, st);
     bool panel_digits = false;
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
-                             p->step_rows[s], slices, p->tune.panel_cluster, st, &panel_digits);
+                             p->step_rows[s], slices, p->tune.panel_cluster,
+                             p->tune.panel_threads, st, &panel_digits);
     axi::prof_end(pid, st, p->step_fl_panel[s]);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
     if (panel_digits) {                 // the digits right behind the panel, over the whole GPU
@@ -869,10 +874,12 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
-      for (int rg : {0, 1}) {
+      for (int rg : {0, 1})
+        for (int pt : {128, 256}) {
         p->tune.next_update = nu;
         p->tune.panel_cluster = pc;
         p->tune.rest_grid = rg;
+        p->tune.panel_threads = pt;
         s = run_build(op, st);                           // warm-up of this schedule
         if (s != AXI_OK) break;
         if (cudaEventRecord(a, st) != cudaSuccess) { s = AXI_ERR_CUDA; break; }

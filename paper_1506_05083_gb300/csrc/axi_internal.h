@@ -20,6 +20,7 @@ struct Tuning {
   int next_update = 0;    // 0 auto, 1 native FP64, 2 split digits (split plans)
   int panel_cluster = 0;  // 0 auto (by the number of tasks), else 1, 2 or 4 CTAs per mode
   int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM)
+  int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
 };
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
@@ -162,7 +163,7 @@ cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
 // cluster: CTAs per mode for shared-memory panels (0 = by the number of tasks).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int panel, int max_panel_rows, int slices, int cluster,
-                            cudaStream_t st, bool *digits_written);
+                            int threads, cudaStream_t st, bool *digits_written);
 // Trailing update of panel step `panel`: the next panel's kNB columns (native
 // FP64, critical path), and the columns beyond (split or FP64; col_off = kNB).
 cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,

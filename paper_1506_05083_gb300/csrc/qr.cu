@@ -25,8 +25,10 @@ namespace axi {
 namespace {
 
 constexpr int kThreads = 256;
-// The shared-memory panel is bound by the FP64 pipe of one SM: fewer threads
-// (about two rows each) halve the per-warp reductions and scalar work.
+// The shared-memory panel is bound by the FP64 pipe of one SM: 128 threads
+// (about two rows each) keep the per-warp reductions and scalar work small;
+// 256 threads give each SM sub-partition a second warp to cover the FP64
+// latency (the tuning chooses).
 constexpr int kPanelThreads = 128;
 constexpr int kTN = 16;   // columns of the target per CTA in block-reflector kernels
 constexpr int kRC = 32;   // rows per shared-memory chunk
@@ -231,7 +233,7 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 // ---------------------------------------------------------------------------
 // Panel held in shared memory, factored by a cluster of C CTAs (C = 1: one
 // CTA, K = rows - k0 <= kPanelSmemRows). Thread t of CTA r owns the rows
-// i = r NT + t + u C NT (NT = kPanelThreads) for the whole panel, so only
+// i = r NT + t + u C NT (NT threads per CTA) for the whole panel, so only
 // reductions cross threads. Column jj needs, from the rows i > jj of its
 // unscaled column x,
 //   xn2 = sum |x_i|^2,  P_c = sum conj(x_i) a_c[i] (c > jj),  Q_a = sum conj(v_a[i]) x_i (a < jj);
@@ -246,11 +248,10 @@ qr_panel_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs
 // Gram entries:
 //   T(jj, jj) = tau_jj,  T(0:jj, jj) = -tau_jj T(0:jj, 0:jj) (V(:, 0:jj)^H v_jj).
 // ---------------------------------------------------------------------------
-template <int C>
-__global__ void __launch_bounds__(kPanelThreads)
+template <int C, int NT>
+__global__ void __launch_bounds__(NT)
 qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                      const int *__restrict__ task_mode, int p) {
-  constexpr int NT = kPanelThreads;
   constexpr int kStride = C * NT;
   constexpr int kBuf = C > 1 ? 2 : 1;
   const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -774,23 +775,23 @@ point_strength_kernel(const ObsDev *__restrict__ od, int W, const double2 *__res
 
 namespace {
 
-template <int C>
+template <int C, int NT>
 cudaError_t launch_panel_cluster(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                                  int ntasks, int p, int max_panel_rows, cudaStream_t st) {
   auto local_rows = [](int K) {
-    return C > 1 ? kPanelThreads * ((K + C * kPanelThreads - 1) / (C * kPanelThreads)) : K;
+    return C > 1 ? NT * ((K + C * NT - 1) / (C * NT)) : K;
   };
   const size_t smem = sizeof(double2) * (size_t)kNB * local_rows(max_panel_rows);
   static size_t granted = 0;
-  cudaError_t e = ensure_dynamic_smem(qr_panel_smem_kernel<C>,
+  cudaError_t e = ensure_dynamic_smem(qr_panel_smem_kernel<C, NT>,
                                       sizeof(double2) * (size_t)kNB * local_rows(kPanelSmemRows),
                                       granted);
   if (e != cudaSuccess) return e;
-  static const bool carve = (prefer_max_shared(qr_panel_smem_kernel<C>), true);
+  static const bool carve = (prefer_max_shared(qr_panel_smem_kernel<C, NT>), true);
   (void)carve;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ntasks * C);
-  cfg.blockDim = dim3(kPanelThreads);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -800,7 +801,7 @@ cudaError_t launch_panel_cluster(const ObsDev *d_obs, const int *d_task_obs, con
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = C > 1 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, qr_panel_smem_kernel<C>, d_obs, d_task_obs, d_task_mode, p);
+  return cudaLaunchKernelEx(&cfg, qr_panel_smem_kernel<C, NT>, d_obs, d_task_obs, d_task_mode, p);
 }
 
 }  // namespace
@@ -818,20 +819,32 @@ int sm_count() {
 
 // The panel is bound by the FP64 pipe of the SMs that factor it: when the
 // step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
+template <int NT>
+cudaError_t launch_panel_nt(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int max_panel_rows, int cluster, cudaStream_t st) {
+  const int sms = sm_count();
+  if (cluster == 4 || (cluster == 0 && 4 * ntasks <= sms))
+    return launch_panel_cluster<4, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+  if (cluster == 2 || (cluster == 0 && 2 * ntasks <= sms))
+    return launch_panel_cluster<2, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+  return launch_panel_cluster<1, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+}
+
+// The panel is bound by the FP64 pipe of the SMs that factor it: when the
+// step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int max_panel_rows, int slices, int cluster,
-                            cudaStream_t st, bool *digits_written) {
+                            int threads, cudaStream_t st, bool *digits_written) {
   // the shared-memory panel also writes the reflector columns' exponents,
   // after which vdigits_kernel writes split plans' digits (launch_vdigits)
   *digits_written = slices > 0 && max_panel_rows <= kPanelSmemRows;
   if (ntasks <= 0) return cudaSuccess;
   if (max_panel_rows <= kPanelSmemRows) {
-    const int sms = sm_count();
-    if (cluster == 4 || (cluster == 0 && 4 * ntasks <= sms))
-      return launch_panel_cluster<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
-    if (cluster == 2 || (cluster == 0 && 2 * ntasks <= sms))
-      return launch_panel_cluster<2>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
-    return launch_panel_cluster<1>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+    if (threads == 256)
+      return launch_panel_nt<256>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows,
+                                  cluster, st);
+    return launch_panel_nt<kPanelThreads>(d_obs, d_task_obs, d_task_mode, ntasks, p,
+                                          max_panel_rows, cluster, st);
   }
   qr_panel_kernel<<<ntasks, kThreads, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   return cudaGetLastError();
