@@ -44,6 +44,9 @@ Pins (tests/test_oracle_pins.py) for each function:
                       brute-force 3D point-source MFS with q = P;
                       rotation covariance; reciprocity
   transmission        k_minus = k null case (u = 0 outside)
+  tsvd_solve          matrices of known singular values (cutoff applied to the
+                      constructed factors); equals the QR solution when the
+                      matrix is well conditioned
   near_image_sum      direct 3D summation over explicit image points; the
                       Bloch phases by the coherent zeroth Bragg order of the
                       eight images at a distant target (eq. per)
@@ -62,7 +65,7 @@ __all__ = [
     "back_substitute", "factor_operator", "incident_samples", "rhs_modes",
     "solve_modes", "point_strengths", "far_field", "potential",
     "near_image_sum", "sphere_series_far_field", "sphere_series_potential",
-    "n_rows", "n_cols",
+    "n_rows", "n_cols", "tsvd_solve", "solve_modes_tsvd", "TSVD_CUTOFF",
 ]
 
 FOUR_PI = 4.0 * math.pi
@@ -346,6 +349,32 @@ def solve_modes(ob, factors, fhat):
         QR, tau = factors[abs(n)]
         Y = apply_qh(QR, tau, fhat[:, idx, :].T)[:cols]
         coef[:, idx, :] = back_substitute(np.triu(QR[:cols, :cols]), Y).T
+    return coef
+
+
+TSVD_CUTOFF = 1e-10
+
+
+def tsvd_solve(A, F, cutoff=TSVD_CUTOFF):
+    """Truncated-SVD least squares (Sec. 4.2, application of A_n^+): with
+    A = U diag(s) V^H, x = V diag(1/s_k) U^H F over the singular values
+    s_k >= cutoff * s_max, applied as two products and a scaling, never as an
+    explicit pseudo-inverse. F [M][r] -> x [N][r]."""
+    U, sv, Vh = np.linalg.svd(A, full_matrices=False)
+    keep = sv >= cutoff * sv[0]
+    y = (U[:, keep].conj().T @ F) / sv[keep][:, None]
+    return Vh[keep].conj().T @ y
+
+
+def solve_modes_tsvd(ob, A, fhat, cutoff=TSVD_CUTOFF):
+    """Truncated-SVD variant of solve_modes: c_n = A_n^+ fhat_n with the
+    1e-10 relative cutoff of Sec. 4.2; modes +-n use the matrix of |n|.
+    A [P/2+1][rows][cols], fhat [W][P][rows] -> coef [W][P][cols]."""
+    W, P, rows = fhat.shape
+    coef = np.zeros((W, P, A.shape[2]), dtype=np.complex128)
+    for idx in range(P):
+        n = idx if idx <= P // 2 else P - idx
+        coef[:, idx, :] = tsvd_solve(A[n], fhat[:, idx, :].T, cutoff).T
     return coef
 
 

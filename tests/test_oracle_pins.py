@@ -381,3 +381,43 @@ def test_near_image_phases_zeroth_bragg_order(specular):
     F0 = O.far_field(ob, src, c, xhat[None])[0, 0]
     ratio = U / (1j * ob.k * np.exp(1j * ob.k * R) / R * F0)
     assert abs(ratio - 8.0) < 1e-4, ratio
+
+
+# --- truncated-SVD pseudo-inverse (Sec. 4.2) ---------------------------------
+
+def _unitary(rng, n):
+    Z = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(Z)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))
+
+
+def test_tsvd_solve_on_known_factors():
+    """A = U diag(s) V^H built from known unitary factors, with singular values
+    far on either side of the 1e-10 relative cutoff: the solution must be
+    V_k diag(1/s_k) U_k^H F over exactly the kept ones (computed from the
+    constructed factors, not from an SVD)."""
+    rng = np.random.default_rng(5)
+    M, N = 40, 24
+    U = _unitary(rng, M)[:, :N]
+    V = _unitary(rng, N)
+    s = np.logspace(0, -16, N)
+    s[(s > 1e-12) & (s < 1e-8)] = 1e-7             # nothing near the cutoff
+    s = 1e3 * np.sort(s)[::-1]                      # relative cutoff: 1e-7 here, not 1e-10
+    A = (U * s) @ V.conj().T
+    F = rng.standard_normal((M, 3)) + 1j * rng.standard_normal((M, 3))
+    k = s >= 1e-10 * s[0]
+    assert 0 < k.sum() < N
+    x_ref = V[:, k] @ ((U[:, k].conj().T @ F) / s[k][:, None])
+    x = O.tsvd_solve(A, F)
+    assert np.abs(x - x_ref).max() < 1e-6 * np.abs(x_ref).max()
+    # the kept part of the residual vanishes: U_k^H (A x - F) = 0
+    assert np.abs(U[:, k].conj().T @ (A @ x - F)).max() < 1e-13 * np.abs(x).max()
+
+
+def test_tsvd_equals_qr_when_well_conditioned():
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((50, 30)) + 1j * rng.standard_normal((50, 30))
+    F = rng.standard_normal((50, 2)) + 1j * rng.standard_normal((50, 2))
+    QR, tau = O.householder_qr(A)
+    x_qr = O.back_substitute(np.triu(QR[:30]), O.apply_qh(QR, tau, F)[:30])
+    assert np.abs(O.tsvd_solve(A, F) - x_qr).max() < 1e-12 * np.abs(x_qr).max()
