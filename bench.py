@@ -429,6 +429,13 @@ def run_single(args, wl):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     pk, pk_src = peaks()
     split_prec = axi.PREC_SPLIT_BF16 | (args.slices << 8)
+    # plan-time host work, not in build_ms: geometry copy, fill tables, the
+    # per-pair sub-grids and the cosine-table digits (axi_plan_create)
+    plan_ms = {}
+    for name, pr in (("split", split_prec), ("fp64", axi.PREC_FP64)):
+        t0 = time.perf_counter()
+        axi.Plan([spec], prec=pr)
+        plan_ms[name] = (time.perf_counter() - t0) * 1e3
     arms = []
     if args.prec == "split":
         arms.append(Arm("split", split_prec, spec, ob, W, dirs, dev, args.graph))
@@ -507,6 +514,7 @@ def run_single(args, wl):
                    "tuning": {arm.name: arm.tuning for arm in arms}},
         "precision": prec_txt,
         "build_ms": s_build, "build_tflops": qr_fl / (s_build * 1e-3) / 1e12,
+        "plan_host_ms": plan_ms,
         "apply_us_per_wave": s_apply * 1e3 / W,
         "e2e": {"value": job_value(ws, qr_fl + ap_fl, e2e_ms), "unit": "TFLOP/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": dirs_host.numel() * 8,

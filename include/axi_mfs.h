@@ -89,6 +89,17 @@ typedef enum {
  * the q-node rule to rounding (measured: 3e-15 of max|A| on the cup). */
 #define AXI_PLAN_FULL_FILL_GRID ((int32_t)1 << 16)
 
+/* Plan option or-ed into `prec`: the truncated-SVD form of the operator
+ * (Sec. 4.2, the paper's factorisation of each block for its preconditioner):
+ * after the Householder QR A_n = Q R, every mode's N x N factor R is
+ * decomposed as R = U_R Sigma V^H by one-sided Jacobi in FP64, and the apply
+ * computes c = V Sigma^+ U_R^H (Q^H fhat_n)_{1:N}, Sigma^+ keeping the
+ * singular values >= 1e-10 sigma_max (the paper's truncation), as two
+ * products and a scaling: the pseudo-inverse is never formed. The workspace
+ * holds U_R, V and Sigma per mode (2 N^2 + N numbers). A mode whose Jacobi
+ * sweeps do not converge in 40 latches AXI_ERR_TIMEOUT. */
+#define AXI_PLAN_TSVD ((int32_t)1 << 17)
+
 typedef enum { AXI_SHAPE_POLAR = 0, AXI_SHAPE_CUP = 1 } axi_shape;
 
 /*
@@ -189,6 +200,23 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
 axi_status axi_plan_set_tuning(axi_plan *plan, const char *json);
 axi_status axi_plan_get_tuning(const axi_plan *plan, char *buf, size_t n);
 
+/*
+ * axi_plan_shard -- restrict a plan to process `rank` of `world` (call before
+ * axi_build_operator). The (obstacle, distinct mode) tasks are independent
+ * (Sec. 3: the modal systems decouple), so they are split over the
+ * processes by estimated cost, longest first (QR flops 8 rows cols^2 -
+ * 8 cols^3/3 per task), each to the least loaded process; every process
+ * computes the same assignment. The build fills every mode (the ring samples
+ * are shared by all modes) but factors only the owned ones; the apply
+ * leaves the coefficients of the other modes zero, so a sum over the
+ * processes (one all-reduce of d_coef) assembles the full coefficients, and
+ * point strengths or fields are then computed from those (axi_eval_field).
+ * axi_plan_owned_modes writes the owned-mode mask of obstacle `obs` into
+ * h_mask[D] (1 owned, 0 not). Errors: AXI_ERR_ARG.
+ */
+axi_status axi_plan_shard(axi_plan *plan, int32_t rank, int32_t world);
+axi_status axi_plan_owned_modes(const axi_plan *plan, int32_t obs, uint8_t *h_mask);
+
 /* Bytes of device workspace the plan needs (256-byte aligned base required). */
 axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes);
 
@@ -252,6 +280,19 @@ typedef struct {
 } axi_factor_view;
 
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *view);
+
+/* Device view of a truncated-SVD operator's R = U_R Sigma V^H (AXI_PLAN_TSVD):
+ * for mode d, U_R and V are n x n column-major at d_U + d n^2 and d_V + d n^2,
+ * sigma at d_sigma + d n (unsorted), and d_sweeps[d] the Jacobi sweeps taken.
+ * AXI_ERR_UNSUPPORTED for other plans. */
+typedef struct {
+  int32_t n, D;
+  const axi_c128 *d_U, *d_V;
+  const double *d_sigma;
+  const int32_t *d_sweeps;
+} axi_svd_view;
+
+axi_status axi_operator_svd(const axi_operator *op, int32_t obs, axi_svd_view *view);
 
 /*
  * axi_incident_planewaves -- boundary data of W incident plane waves

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libaxi_mfs.so")
 BC_NEUMANN, BC_TRANSMISSION = 0, 1
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
 PLAN_FULL_FILL_GRID = 1 << 16                   # or-ed into prec: every ring pair on all q nodes
+PLAN_TSVD = 1 << 17                             # or-ed into prec: truncated-SVD form of A_n^+
 SHAPE_POLAR, SHAPE_CUP = 0, 1
 EVAL_POTENTIAL, EVAL_NORMAL_DERIV, EVAL_FAR_FIELD = 0, 1, 2
 OK, ERR_ARG, ERR_SHAPE = 0, -1, -2              # axi_status values (include/axi_mfs.h)
@@ -47,6 +48,11 @@ KERNEL_KINDS = ["fill", "panel", "update_next", "update_rest", "panel_digits", "
                 "apply_rhs", "apply_qh", "apply_trsm", "apply_out"]   # axi_kernel_kind order
 
 
+class _SvdView(C.Structure):
+    _fields_ = [("n", C.c_int32), ("D", C.c_int32), ("d_U", _vp), ("d_V", _vp),
+                ("d_sigma", _vp), ("d_sweeps", _vp)]
+
+
 class _Lattice(C.Structure):
     _fields_ = [("ex", C.c_double), ("ey", C.c_double)]
 
@@ -59,6 +65,8 @@ SIGNATURES = [
                                    C.POINTER(C.c_uint8)]),
     ("axi_plan_create", C.c_int, [C.POINTER(_Obstacle), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     ("axi_plan_workspace_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    ("axi_plan_shard", C.c_int, [_vp, C.c_int32, C.c_int32]),
+    ("axi_plan_owned_modes", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_uint8)]),
     ("axi_plan_set_tuning", C.c_int, [_vp, C.c_char_p]),
     ("axi_plan_get_tuning", C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     ("axi_operator_autotune", C.c_int, [_vp, C.c_int32, _vp, C.c_char_p, C.c_size_t]),
@@ -68,6 +76,7 @@ SIGNATURES = [
     ("axi_diag_wait_timeout", C.c_int, [_vp, C.c_int64, _vp]),
     ("axi_fill_modes", C.c_int, [_vp, C.c_int32, _vp, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
+    ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     ("axi_apply_workspace_bytes", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     ("axi_apply_operator", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
@@ -152,6 +161,46 @@ def choose_q(M, N, P, coll, src, src_ext=None) -> int:
     return q.value
 
 
+class Plan:
+    """A host-only plan (axi_plan_create) without device memory: for the
+    mode partition of axi_plan_shard and other host queries."""
+
+    def __init__(self, specs: List[ObstacleSpec], prec: int = PREC_FP64):
+        self.specs = specs
+        arr = (_Obstacle * len(specs))()
+        for i, s in enumerate(specs):
+            arr[i] = _Obstacle(s.bc, s.M, s.N, s.P, s.q, s.k, s.k_minus, _ptr(s.coll), _ptr(s.src),
+                               _ptr(s.src_ext) if s.src_ext is not None else None)
+        plan = C.c_void_p()
+        _check(lib().axi_plan_create(arr, len(specs), prec, C.byref(plan)), "axi_plan_create")
+        self._plan = plan
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                lib().axi_plan_destroy(self._plan)
+        except Exception:
+            pass
+
+    def shard(self, rank: int, world: int):
+        _check(lib().axi_plan_shard(self._plan, rank, world), "axi_plan_shard")
+
+    def owned_modes(self, obs=0) -> np.ndarray:
+        mask = np.zeros(self.specs[obs].P // 2 + 1, dtype=np.uint8)
+        _check(lib().axi_plan_owned_modes(self._plan, obs,
+                                          mask.ctypes.data_as(C.POINTER(C.c_uint8))),
+               "axi_plan_owned_modes")
+        return mask.astype(bool)
+
+
+def gather_coefficients(coef: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum of the processes' coefficient arrays (each holds its owned modes,
+    zeros elsewhere) in place: one all-reduce of the real view."""
+    import torch.distributed as dist
+    dist.all_reduce(torch.view_as_real(coef), op=dist.ReduceOp.SUM, group=group)
+    return coef
+
+
 def fill_subgrid(M, N, P, q, coll, src) -> np.ndarray:
     """axi_fill_subgrid: [M][N] azimuthal sub-grid stride of each ring pair's fill samples."""
     coll = np.ascontiguousarray(coll, dtype=np.float64)
@@ -185,7 +234,7 @@ class Operator:
     """Plan + workspace + built operator (axi_plan_create / axi_build_operator)."""
 
     def __init__(self, specs: List[ObstacleSpec], prec: int = PREC_FP64, device="cuda",
-                 stream=None, tuning: Optional[str] = None):
+                 stream=None, tuning: Optional[str] = None, shard=None):
         self.specs = specs
         arr = (_Obstacle * len(specs))()
         for i, s in enumerate(specs):
@@ -196,6 +245,8 @@ class Operator:
         self._plan = plan
         if tuning is not None:
             _check(lib().axi_plan_set_tuning(plan, tuning.encode()), "axi_plan_set_tuning")
+        if shard is not None:                       # (rank, world)
+            _check(lib().axi_plan_shard(plan, int(shard[0]), int(shard[1])), "axi_plan_shard")
         nb = C.c_size_t(0)
         _check(lib().axi_plan_workspace_bytes(plan, C.byref(nb)), "axi_plan_workspace_bytes")
         self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
@@ -290,6 +341,22 @@ class Operator:
         tau = view(v.d_tau, (v.D, v.cols))
         T = view(v.d_T, (v.D, v.npanels, v.nb, v.nb))
         return A, tau, T, v.nb
+
+    def svd(self, obs=0):
+        """(U [D][n][n] col-major, V, sigma [D][n], sweeps [D]) views of a truncated-SVD operator."""
+        v = _SvdView()
+        _check(lib().axi_operator_svd(self._op, obs, C.byref(v)), "axi_operator_svd")
+        base = self.workspace.data_ptr()
+
+        def view(ptr, nbytes, dtype, shape):
+            off = ptr - base
+            return self.workspace[off:off + nbytes].view(dtype).view(*shape)
+
+        n, D = v.n, v.D
+        return (view(v.d_U, 16 * D * n * n, torch.complex128, (D, n, n)),
+                view(v.d_V, 16 * D * n * n, torch.complex128, (D, n, n)),
+                view(v.d_sigma, 8 * D * n, torch.float64, (D, n)),
+                view(v.d_sweeps, 4 * D, torch.int32, (D,)))
 
     def incident(self, dirs: torch.Tensor, obs=0, stream=None) -> torch.Tensor:
         s = self.specs[obs]

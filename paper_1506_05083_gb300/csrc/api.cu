@@ -30,12 +30,15 @@ struct ObsHost {
   size_t off_coll, off_src, off_srcx, off_cos, off_s2, off_tw, off_A, off_tau, off_T;
   size_t off_ring = 0;
   std::vector<double2> tab_ring;
+  size_t off_svdU = 0, off_svdV = 0, off_svdS = 0, off_svdSw = 0;
   size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_rdig = 0, off_rex = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
   std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
   std::vector<int> fill_cex;               // and row exponents [2 MR]
   size_t off_fcdig = 0, off_fcex = 0;
   std::vector<unsigned char> fill_sig;     // [2][M][N] sub-grid stride per ring pair
   size_t off_fsig = 0;
+  std::vector<unsigned char> owned;        // [D] modes this process factors (axi_plan_shard)
+  size_t off_owned = 0;
 };
 
 // Digits of the folded cosine table of the split fill (fill_mma.cu): row
@@ -116,6 +119,7 @@ struct axi_plan_s {
   axi::Tuning tune;                       // schedule choices (axi_plan_set_tuning / autotune)
   size_t off_fgdig = 0, off_fgex = 0;     // split fill: sample-digit scratch (shared)
   std::vector<int> task_obs, task_mode;   // sorted by obstacle panel count, descending
+  std::vector<int> all_task_obs, all_task_mode;   // every task, before axi_plan_shard
   std::vector<int> step_tasks;            // tasks active at panel step p (a prefix)
   std::vector<int> step_cols;             // widest trailing matrix at step p
   std::vector<int> step_rows;             // tallest panel at step p
@@ -319,6 +323,45 @@ axi_status copy_out(const std::string &js, char *buf, size_t n) {
   return AXI_OK;
 }
 
+// Per panel step of the current task list (sorted by panel count, so the
+// tasks active at step s form a prefix): active tasks, widest trailing
+// matrix, tallest panel, and the algorithmic flops of the step's panels and
+// updates (for the kernel profile).
+void step_tables(axi_plan_s *p) {
+  int maxpan = 0;
+  for (size_t t = 0; t < p->task_obs.size(); ++t)
+    maxpan = std::max(maxpan, p->obs[p->task_obs[t]].dev.npanels);
+  p->step_tasks.assign(maxpan, 0);
+  p->step_cols.assign(maxpan, 0);
+  p->step_rows.assign(maxpan, 0);
+  p->step_fl_panel.assign(maxpan, 0.0);
+  p->step_fl_next.assign(maxpan, 0.0);
+  p->step_fl_rest.assign(maxpan, 0.0);
+  for (int s = 0; s < maxpan; ++s) {
+    for (int t = 0; t < (int)p->task_obs.size(); ++t) {
+      const ObsDev &d = p->obs[p->task_obs[t]].dev;
+      if (d.npanels > s) {
+        p->step_tasks[s] = t + 1;
+        const int k0 = s * axi::kNB, nbp = std::min(axi::kNB, d.cols - k0);
+        p->step_cols[s] = std::max(p->step_cols[s], d.cols - k0 - nbp);
+        p->step_rows[s] = std::max(p->step_rows[s], d.rows - k0);
+        // reflector j (height K - j) costs 16 (K - j) flops per column it updates
+        const double K = d.rows - k0;
+        double pan = 0.0, hsum = 0.0;
+        for (int j = 0; j < nbp; ++j) {
+          pan += 16.0 * (K - j) * (nbp - 1 - j);
+          hsum += 16.0 * (K - j);
+        }
+        const int rest = d.cols - k0 - nbp;
+        const int nnext = std::min(axi::kNB, std::max(rest, 0));
+        p->step_fl_panel[s] += pan;
+        p->step_fl_next[s] += hsum * nnext;
+        p->step_fl_rest[s] += hsum * std::max(rest - nnext, 0);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -341,7 +384,8 @@ const char *axi_status_string(int32_t s) {
 axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec, axi_plan **out) {
   if (!obs || !out || n_obs < 1) return AXI_ERR_ARG;
   const bool full_grid = (prec & axi::kPlanFullFillGrid) != 0;
-  prec &= ~axi::kPlanFullFillGrid;
+  const bool tsvd = (prec & axi::kPlanTsvd) != 0;
+  prec &= ~(axi::kPlanFullFillGrid | axi::kPlanTsvd);
   const int mode = prec & 0xff;
   int slices = 0;
   if (mode == AXI_PREC_SPLIT_BF16) {
@@ -431,9 +475,18 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       return AXI_ERR_GEOMETRY;
     }
     h.off_fsig = off; off = align_up(off + h.fill_sig.size());
+    h.owned.assign(d.D, 1);
+    h.off_owned = off; off = align_up(off + h.owned.size());
     h.off_A = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.rows);
     h.off_tau = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols);
     h.off_T = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.npanels * axi::kNB * axi::kNB);
+    d.tsvd = tsvd ? 1 : 0;
+    if (tsvd) {
+      h.off_svdU = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.cols);
+      h.off_svdV = off; off = align_up(off + sizeof(double2) * (size_t)d.D * d.cols * d.cols);
+      h.off_svdS = off; off = align_up(off + sizeof(double) * (size_t)d.D * d.cols);
+      h.off_svdSw = off; off = align_up(off + sizeof(int) * (size_t)d.D);
+    }
     if (slices > 0) {
       // digit rows: rounded up to 64, plus 64 zero rows so that a 64-row chunk
       // starting at any row of X stays inside the block
@@ -478,40 +531,11 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return p->obs[a].dev.npanels > p->obs[b].dev.npanels;
   });
-  int maxpan = 0;
-  for (int i : order) {
+  for (int i : order)
     for (int m = 0; m < p->obs[i].dev.D; ++m) { p->task_obs.push_back(i); p->task_mode.push_back(m); }
-    maxpan = std::max(maxpan, p->obs[i].dev.npanels);
-  }
-  p->step_tasks.assign(maxpan, 0);
-  p->step_cols.assign(maxpan, 0);
-  p->step_rows.assign(maxpan, 0);
-  p->step_fl_panel.assign(maxpan, 0.0);
-  p->step_fl_next.assign(maxpan, 0.0);
-  p->step_fl_rest.assign(maxpan, 0.0);
-  for (int s = 0; s < maxpan; ++s) {
-    for (int t = 0; t < (int)p->task_obs.size(); ++t) {
-      const ObsDev &d = p->obs[p->task_obs[t]].dev;
-      if (d.npanels > s) {
-        p->step_tasks[s] = t + 1;
-        const int k0 = s * axi::kNB, nbp = std::min(axi::kNB, d.cols - k0);
-        p->step_cols[s] = std::max(p->step_cols[s], d.cols - k0 - nbp);
-        p->step_rows[s] = std::max(p->step_rows[s], d.rows - k0);
-        // reflector j (height K - j) costs 16 (K - j) flops per column it updates
-        const double K = d.rows - k0;
-        double pan = 0.0, hsum = 0.0;
-        for (int j = 0; j < nbp; ++j) {
-          pan += 16.0 * (K - j) * (nbp - 1 - j);
-          hsum += 16.0 * (K - j);
-        }
-        const int rest = d.cols - k0 - nbp;
-        const int nnext = std::min(axi::kNB, std::max(rest, 0));
-        p->step_fl_panel[s] += pan;
-        p->step_fl_next[s] += hsum * nnext;
-        p->step_fl_rest[s] += hsum * std::max(rest - nnext, 0);
-      }
-    }
-  }
+  p->all_task_obs = p->task_obs;
+  p->all_task_mode = p->task_mode;
+  step_tables(p);
   *out = p;
   return AXI_OK;
 }
@@ -519,6 +543,49 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
 axi_status axi_plan_workspace_bytes(const axi_plan *plan, size_t *bytes) {
   if (!plan || !bytes) return AXI_ERR_ARG;
   *bytes = plan->bytes;
+  return AXI_OK;
+}
+
+axi_status axi_plan_shard(axi_plan *plan, int32_t rank, int32_t world) {
+  if (!plan || world < 1 || rank < 0 || rank >= world) return AXI_ERR_ARG;
+  // longest processing time first: tasks by decreasing QR flops (ties in
+  // task-list order) each to the least loaded rank (ties to the lowest), the
+  // same assignment on every process
+  const size_t nt = plan->all_task_obs.size();
+  std::vector<double> fl(nt);
+  for (size_t t = 0; t < nt; ++t) {
+    const ObsDev &d = plan->obs[plan->all_task_obs[t]].dev;
+    fl[t] = 8.0 * d.rows * (double)d.cols * d.cols - 8.0 / 3.0 * (double)d.cols * d.cols * d.cols;
+  }
+  std::vector<size_t> order(nt);
+  for (size_t t = 0; t < nt; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return fl[a] > fl[b]; });
+  std::vector<double> load(world, 0.0);
+  std::vector<int> owner(nt, 0);
+  for (size_t t : order) {
+    int best = 0;
+    for (int r = 1; r < world; ++r)
+      if (load[r] < load[best]) best = r;
+    owner[t] = best;
+    load[best] += fl[t];
+  }
+  plan->task_obs.clear();
+  plan->task_mode.clear();
+  for (auto &h : plan->obs) std::fill(h.owned.begin(), h.owned.end(), 0);
+  for (size_t t = 0; t < nt; ++t) {
+    if (owner[t] != rank) continue;
+    plan->task_obs.push_back(plan->all_task_obs[t]);
+    plan->task_mode.push_back(plan->all_task_mode[t]);
+    plan->obs[plan->all_task_obs[t]].owned[plan->all_task_mode[t]] = 1;
+  }
+  step_tables(plan);
+  return AXI_OK;
+}
+
+axi_status axi_plan_owned_modes(const axi_plan *plan, int32_t obs, uint8_t *h_mask) {
+  if (!plan || !h_mask || obs < 0 || obs >= (int)plan->obs.size()) return AXI_ERR_ARG;
+  const auto &o = plan->obs[obs].owned;
+  std::memcpy(h_mask, o.data(), o.size());
   return AXI_OK;
 }
 
@@ -630,11 +697,17 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
   if (side_used && (cudaEventRecord(op->ev_rest, op->side) != cudaSuccess ||
                     cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess))
     return AXI_ERR_CUDA;
-  // digits of R's off-diagonal blocks for every apply's back substitution
   for (size_t i = 0; i < p->obs.size(); ++i) {
-    const int pid = axi::prof_begin(AXI_KERNEL_R_DIGITS, st);
-    e = axi::launch_r_digits(op->d_obs + i, p->obs[i].dev, st);
-    axi::prof_end(pid, st);
+    const ObsDev &d = p->obs[i].dev;
+    if (d.tsvd) {                         // SVD of R: the apply uses V Sigma^+ U_R^H
+      const int pid = axi::prof_begin(AXI_KERNEL_R_DIGITS, st);
+      e = axi::launch_tsvd(op->d_obs + i, d, st);
+      axi::prof_end(pid, st);
+    } else {                              // digits of R's off-diagonal blocks for the back substitution
+      const int pid = axi::prof_begin(AXI_KERNEL_R_DIGITS, st);
+      e = axi::launch_r_digits(op->d_obs + i, d, st);
+      axi::prof_end(pid, st);
+    }
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
   return AXI_OK;
@@ -659,12 +732,17 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.tw_P = reinterpret_cast<const double2 *>(ws + h.off_tw);
     d.tab_ring = reinterpret_cast<const double2 *>(ws + h.off_ring);
     d.fill_sig = reinterpret_cast<const unsigned char *>(ws + h.off_fsig);
+    d.mode_owned = reinterpret_cast<const unsigned char *>(ws + h.off_owned);
     d.fft_perm = reinterpret_cast<const int *>(ws + h.off_perm);
     d.fft_perm_q = reinterpret_cast<const int *>(ws + h.off_perm_q);
     d.tw_q = reinterpret_cast<const double2 *>(ws + h.off_tw_q);
     d.A = reinterpret_cast<double2 *>(ws + h.off_A);
     d.tau = reinterpret_cast<double2 *>(ws + h.off_tau);
     d.T = reinterpret_cast<double2 *>(ws + h.off_T);
+    d.svdU = d.tsvd ? reinterpret_cast<double2 *>(ws + h.off_svdU) : nullptr;
+    d.svdV = d.tsvd ? reinterpret_cast<double2 *>(ws + h.off_svdV) : nullptr;
+    d.svdS = d.tsvd ? reinterpret_cast<double *>(ws + h.off_svdS) : nullptr;
+    d.svdSweeps = d.tsvd ? reinterpret_cast<int *>(ws + h.off_svdSw) : nullptr;
     d.vdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_vdig) : nullptr;
     d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
     d.ckey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ckey) : nullptr;
@@ -687,6 +765,7 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
         {h.off_tw, h.tw_P.data(), sizeof(double2) * h.tw_P.size()},
         {h.off_ring, h.tab_ring.data(), sizeof(double2) * h.tab_ring.size()},
         {h.off_fsig, h.fill_sig.data(), h.fill_sig.size()},
+        {h.off_owned, h.owned.data(), h.owned.size()},
         {h.off_perm, h.fft_perm.data(), sizeof(int) * h.fft_perm.size()},
         {h.off_perm_q, h.fft_perm_q.data(), sizeof(int) * h.fft_perm_q.size()},
         {h.off_tw_q, h.tw_q.data(), sizeof(double2) * h.tw_q.size()},
@@ -756,6 +835,19 @@ axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_
   v->d_A = reinterpret_cast<const axi_c128 *>(d.A);
   v->d_tau = reinterpret_cast<const axi_c128 *>(d.tau);
   v->d_T = reinterpret_cast<const axi_c128 *>(d.T);
+  return AXI_OK;
+}
+
+axi_status axi_operator_svd(const axi_operator *op, int32_t obs, axi_svd_view *v) {
+  if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (!d.tsvd) return AXI_ERR_UNSUPPORTED;
+  v->n = d.cols;
+  v->D = d.D;
+  v->d_U = reinterpret_cast<const axi_c128 *>(d.svdU);
+  v->d_V = reinterpret_cast<const axi_c128 *>(d.svdV);
+  v->d_sigma = d.svdS;
+  v->d_sweeps = d.svdSweeps;
   return AXI_OK;
 }
 

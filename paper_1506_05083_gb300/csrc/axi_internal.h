@@ -14,6 +14,7 @@ constexpr int kMaxP = 254;
 constexpr int kFillDigits = 8;        // digits of the split fill transform (both operands)
 constexpr int kPanelSmemRows = 864;  // panels up to this many rows are factored in shared memory
 constexpr int kPlanFullFillGrid = 1 << 16;   // AXI_PLAN_FULL_FILL_GRID
+constexpr int kPlanTsvd = 1 << 17;           // AXI_PLAN_TSVD
 
 // Schedule choices of a plan (axi_plan_set_tuning, axi_operator_autotune).
 struct Tuning {
@@ -46,6 +47,9 @@ struct ObsDev {
   // samples: interior proxies, then exterior proxies (transmission); the
   // fill evaluates nodes l = 0, s, 2s, .. only (Theorem 1 rate of the pair).
   const unsigned char *fill_sig;
+  // [D] 1 for the modes this process factors and applies (axi_plan_shard);
+  // the apply leaves the other modes' coefficients zero
+  const unsigned char *mode_owned;
   double2 *A;             // [D][cols][rows] packed QR factors (column-major)
   double2 *tau;           // [D][cols] reflector scalars
   double2 *T;             // [D][npanels][kNB][kNB] compact-WY T blocks (col-major)
@@ -82,6 +86,11 @@ struct ObsDev {
   const int *fill_cex;
   uint32_t *fill_gdig;
   int *fill_gex;
+  // truncated-SVD plans (AXI_PLAN_TSVD): R = U_R Sigma V^H per mode
+  int tsvd;
+  double2 *svdU, *svdV;   // [D][cols][cols] column-major
+  double *svdS;           // [D][cols]
+  int *svdSweeps;         // [D] Jacobi sweeps taken
   int fft_nst;            // radices of P for the apply's FFTs (0: P has other prime factors)
   int fft_rad[8];
   const int *fft_perm;    // [P] position of output n after the in-place FFT
@@ -91,6 +100,10 @@ struct ObsDev {
   const int *fft_perm_q;  // [q]
   const double2 *tw_q;    // [q] e^{-2 pi i r / q}
 };
+
+__host__ __device__ inline bool owns_mode(const ObsDev &o, int d) {
+  return o.mode_owned == nullptr || o.mode_owned[d] != 0;
+}
 
 // Streaming multiprocessors of the current device (cached).
 int sm_count();
@@ -202,6 +215,10 @@ bool split_slices_supported(int slices);
 // kp_max: the largest digit row stride (kp) over the tasks of the launch
 cudaError_t launch_panel_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                                 int ntasks, int panel, int slices, int kp_max, cudaStream_t st);
+// tsvd.cu: SVD of every mode's R (after the QR) and its truncated apply
+cudaError_t launch_tsvd(const ObsDev *d_o, const ObsDev &h, cudaStream_t st);
+cudaError_t launch_tsvd_apply(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
+                              cudaStream_t st);
 cudaError_t launch_incident(const ObsDev *d_o, const ObsDev &h_o, int W, const double *dirs,
                             double2 *f, cudaStream_t st);
 cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h_o, int W, const double2 *f,

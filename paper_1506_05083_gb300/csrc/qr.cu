@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(kNB * kTA)
 apply_qh_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
   const ObsDev &o = *od;
   const int d = blockIdx.x;
+  if (!owns_mode(o, d)) return;
   const int c0 = blockIdx.y * kTA;
   if (c0 >= ncols_total) return;
   const int ncols = min(kTA, ncols_total - c0);
@@ -629,6 +630,7 @@ __global__ void __launch_bounds__(kThreads)
 trsm_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int ncols_total) {
   const ObsDev &o = *od;
   const int d = blockIdx.x;
+  if (!owns_mode(o, d)) return;
   const int c0 = blockIdx.y * kTS;
   if (c0 >= ncols_total) return;
   const int ncols = min(kTS, ncols_total - c0);
@@ -740,7 +742,8 @@ __global__ void scatter_coef_kernel(const ObsDev *__restrict__ od, int W,
   const int s = ni <= P / 2 ? 0 : 1;
   const double2 *src = X + ((size_t)dmode * 2 * W + 2 * w + s) * rows;
   double2 *dst = coef + ((size_t)w * P + ni) * cols;
-  for (int j = threadIdx.x; j < cols; j += blockDim.x) dst[j] = src[j];
+  const bool own = owns_mode(o, dmode);              // other processes own the rest
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) dst[j] = own ? src[j] : make_double2(0.0, 0.0);
 }
 
 // sigma[w][j][l] = (1/P) sum_n c[w][n][j] e^{+2 pi i n l / P}  (Sec. 4.1)
@@ -913,7 +916,9 @@ cudaError_t launch_apply(const ObsDev *d_o, const ObsDev &h, int W, const double
   prof_end(pid, st, rhs * (16.0 * h.rows * h.cols - 8.0 * h.cols * h.cols));
   if (e != cudaSuccess) return e;
   pid = prof_begin(AXI_KERNEL_APPLY_TRSM, st);
-  if (h.slices > 0) {
+  if (h.tsvd) {
+    e = launch_tsvd_apply(d_o, h, X, ncol, st);     // V Sigma^+ U_R^H instead of R^{-1}
+  } else if (h.slices > 0) {
     e = launch_trsm_split(d_o, h, X, ncol, st);
   } else {
     trsm_kernel<<<dim3(h.D, (ncol + kTS - 1) / kTS), kThreads, 0, st>>>(d_o, X, ncol);

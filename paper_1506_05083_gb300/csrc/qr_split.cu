@@ -579,7 +579,7 @@ apply_qh_cluster_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, 
   const int rank = (int)cg::this_cluster().block_rank();
   const int d = blockIdx.x / C;
   const int c0 = blockIdx.y * kTN;
-  if (c0 >= ncols_total) return;                        // uniform over the cluster
+  if (c0 >= ncols_total || !owns_mode(o, d)) return;  // uniform over the cluster
   const int ncols = min(kTN, ncols_total - c0);
   const int RB = ((o.rows + C - 1) / C + 31) / 32 * 32;
   const int rlo = rank * RB, rhi = min(o.rows, rlo + RB);
@@ -613,6 +613,7 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   const bool qr = task_obs != nullptr;
   const ObsDev &o = qr ? obs[task_obs[blockIdx.x]] : obs[0];
   const int d = qr ? task_mode[blockIdx.x] : blockIdx.x;
+  if (!owns_mode(o, d)) return;
   const int p = qr ? p_qr : blockIdx.y;
   // QR: two slots per mode alternating with the step, because the look-ahead
   // lets step p's trailing update still read its digits while step p+1's are

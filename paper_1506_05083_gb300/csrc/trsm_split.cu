@@ -46,7 +46,7 @@ r_digits_kernel(const ObsDev *__restrict__ od) {
   const int S = o.slices;
   const int d = blockIdx.x, b = blockIdx.y, m0 = 64 * blockIdx.z;
   const int rb = r_digit_block_rows(b);
-  if (m0 >= rb) return;
+  if (m0 >= rb || !owns_mode(o, d)) return;
   const int n = o.cols, ld = o.rows;
   const int r0 = b * kTB, nb = min(kTB, n - r0);
   const double2 *R = o.A + (size_t)d * o.cols * o.rows;
@@ -95,7 +95,7 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
   const ObsDev &o = *od;
   const int d = blockIdx.x;
   const int c0 = blockIdx.y * kTC;
-  if (c0 >= ncols_total) return;
+  if (c0 >= ncols_total || !owns_mode(o, d)) return;
   const int ncols = min(kTC, ncols_total - c0);
   const int n = o.cols, ld = o.rows, nblk = (n + kTB - 1) / kTB;
   const size_t mrows = r_digit_rows_before(nblk);
