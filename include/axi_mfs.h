@@ -184,7 +184,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *   "panel_cluster" 0 auto (by the number of (obstacle, mode) tasks), or 1,
  *                   2, 4 CTAs per mode for the Householder panels;
  *   "rest_grid"     0 one CTA per (task, column tile), 1 persistent (one CTA
- *                   per SM) for the trailing updates of split plans;
+ *                   per SM) for the trailing updates of split plans, 2 the
+ *                   tcgen05 trailing update (tensor-memory accumulators, 64
+ *                   columns per CTA; split plans whose next-panel update
+ *                   is in digits, else as 0);
  *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA.
  * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
  * keys kept; AXI_ERR_ARG on malformed input or values out of range);

@@ -31,6 +31,7 @@ struct ObsHost {
   size_t off_ring = 0;
   std::vector<double2> tab_ring;
   size_t off_svdU = 0, off_svdV = 0, off_svdS = 0, off_svdSw = 0;
+  size_t off_ybuf = 0, off_ykey = 0, off_ydig = 0, off_yexp = 0;
   size_t off_vdig = 0, off_vexp = 0, off_ckey = 0, off_rdig = 0, off_rex = 0, off_perm = 0, off_perm_q = 0, off_tw_q = 0;
   std::vector<unsigned short> fill_cdig;   // split fill: cos-table digits [S][2 MR][Lp]
   std::vector<int> fill_cex;               // and row exponents [2 MR]
@@ -300,7 +301,7 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
       if (iv != 0 && iv != 1 && iv != 2 && iv != 4) return false;
       t.panel_cluster = iv;
     } else if (key == "rest_grid") {
-      if (iv < 0 || iv > 1) return false;
+      if (iv < 0 || iv > 2) return false;
       t.rest_grid = iv;
     } else if (key == "panel_threads") {
       if (iv != 0 && iv != 128 && iv != 256) return false;
@@ -498,6 +499,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
       h.off_vdig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * d.dig_nslot * 4 * slices * axi::kNB * d.kp);
       h.off_vexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * d.dig_nslot * (axi::kNB + d.kp));
       h.off_ckey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * d.cols);
+      h.off_ybuf = off; off = align_up(off + sizeof(double2) * (size_t)d.D * 2 * axi::kNB * d.kp);
+      h.off_ykey = off; off = align_up(off + sizeof(unsigned long long) * (size_t)d.D * 2 * axi::kNB);
+      h.off_ydig = off; off = align_up(off + sizeof(unsigned short) * (size_t)d.D * 2 * 2 * slices * axi::kNB * d.kp);
+      h.off_yexp = off; off = align_up(off + sizeof(int) * (size_t)d.D * 2 * axi::kNB);
       h.off_rdig = off; off = align_up(off + axi::r_digit_bytes(d));
       h.off_rex = off; off = align_up(off + axi::r_exponent_bytes(d));
       // split fill: folded length, padding, cos-table digits, pair chunk
@@ -684,9 +689,19 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
     }
     if (rest_cols > 0 || digits_here) side_used = true;
     if (rest_cols > 0) {
+      // split plans whose panel wrote its column exponents: Y = V T beside
+      // the critical path, so the trailing update forms W' in one product
+      const bool use_y = slices > 0 && panel_digits;
+      if (use_y) {
+        pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, op->side);
+        e = axi::launch_y_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max,
+                                 op->side);
+        axi::prof_end(pid, op->side);
+        if (e != cudaSuccess) return AXI_ERR_CUDA;
+      }
       pid = axi::prof_begin(AXI_KERNEL_UPDATE_REST, op->side);
       e = axi::launch_qr_update_rest(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, slices,
-                                     rest_cols, p->tune.rest_grid == 1, op->side);
+                                     rest_cols, p->tune.rest_grid, use_y, op->side);
       axi::prof_end(pid, op->side, p->step_fl_rest[s]);
       if (e != cudaSuccess || cudaEventRecord(op->ev_rest, op->side) != cudaSuccess)
         return AXI_ERR_CUDA;
@@ -747,6 +762,10 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
     d.vexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_vexp) : nullptr;
     d.ckey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ckey) : nullptr;
     d.rdig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_rdig) : nullptr;
+    d.ybuf = d.slices > 0 ? reinterpret_cast<double2 *>(ws + h.off_ybuf) : nullptr;
+    d.ykey = d.slices > 0 ? reinterpret_cast<unsigned long long *>(ws + h.off_ykey) : nullptr;
+    d.ydig = d.slices > 0 ? reinterpret_cast<unsigned short *>(ws + h.off_ydig) : nullptr;
+    d.yexp = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_yexp) : nullptr;
     d.rex = d.slices > 0 ? reinterpret_cast<int *>(ws + h.off_rex) : nullptr;
     if (d.slices > 0) {
       d.fill_cdig = reinterpret_cast<const unsigned short *>(ws + h.off_fcdig);
@@ -966,8 +985,10 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
-      for (int rg : {0, 1})
+      for (int rg : {0, 1, 2})
         for (int pt : {128, 256}) {
+        if (rg == 2 && nu != 2) continue;             // the tcgen05 update reads Y^H digits
+
         p->tune.next_update = nu;
         p->tune.panel_cluster = pc;
         p->tune.rest_grid = rg;

@@ -20,7 +20,8 @@ constexpr int kPlanTsvd = 1 << 17;           // AXI_PLAN_TSVD
 struct Tuning {
   int next_update = 0;    // 0 auto, 1 native FP64, 2 split digits (split plans)
   int panel_cluster = 0;  // 0 auto (by the number of tasks), else 1, 2 or 4 CTAs per mode
-  int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM)
+  int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM),
+                          // 2 tcgen05 kernel (split plans whose update reads Y^H digits; else as 0)
   int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
 };
 
@@ -76,6 +77,14 @@ struct ObsDev {
   // 32 b + k), exponents [rb] (one per row of the block).
   unsigned short *rdig;
   int *rex;
+  // split precision only: Y = V T of the current panel for the trailing
+  // update (slots p mod 2): Y [D][2][kNB][kp] FP64, column maxima ykey
+  // [D][2][kNB], digits of Y^H [D][2][slices][re/im][kNB][kp], exponents
+  // yexp [D][2][kNB]
+  double2 *ybuf;
+  unsigned long long *ykey;
+  unsigned short *ydig;
+  int *yexp;
   // split precision only: the fill's transform as a digit GEMM (fill_mma.cu).
   // Folded length L, padded Lp (multiple of 32), MR rows per parity part;
   // cos-table digits [kFillDigits][2 MR][Lp] and row exponents [2 MR];
@@ -190,14 +199,23 @@ cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int
 cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
                                         const int *d_task_mode, int ntasks, int panel, int slices,
                                         int max_rows, cudaStream_t st);
+// use_y: the trailing update reads Y^H digits (launch_y_digits) and skips T^H W.
+// rest_grid: Tuning::rest_grid.
 cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int panel, int slices,
-                                  int max_rest_cols, bool persistent, cudaStream_t st);
+                                  int max_rest_cols, int rest_grid, bool use_y, cudaStream_t st);
+// The trailing update of split plans on tcgen05 (W' = Y^H X, X -= V W'),
+// 64 columns per CTA; needs the Y^H digits.
+cudaError_t launch_qr_update_tc(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int p, int slices, int max_rest_cols, cudaStream_t st);
+// Y = V T of panel p and the digits of Y^H (split plans, after launch_vdigits).
+cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int kp_max, cudaStream_t st);
 int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel, int slices,
                                    int col_off, int ntiles, int max_cols, bool persistent,
-                                   cudaStream_t st);
+                                   bool use_y, cudaStream_t st);
 cudaError_t launch_apply_qh_split(const ObsDev *d_o, const ObsDev &h, double2 *X, int ncol,
                                   void *digit_scratch, cudaStream_t st);
 size_t apply_digit_bytes(const ObsDev &h);

@@ -509,6 +509,8 @@ qr_panel_smem_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ tas
   }
   csync();                                       // every CTA's column maxima
   if (rank == 0 && tid < kNB) {
+    // the column maxima of Y = V T (y_rows_kernel) start from zero
+    o.ykey[((size_t)d * 2 + (p & 1)) * kNB + tid] = 0ull;
     unsigned long long m = 0ull;
 #pragma unroll
     for (int r = 0; r < C; ++r) {
@@ -869,13 +871,15 @@ cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
 // Columns from kNB past the panel onward, native FP64 or split digits.
 cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int p, int slices,
-                                  int max_rest_cols, bool persistent, cudaStream_t st) {
+                                  int max_rest_cols, int rest_grid, bool use_y, cudaStream_t st) {
   if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
+  if (slices > 0 && use_y && rest_grid == 2)
+    return launch_qr_update_tc(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, max_rest_cols, st);
   if (slices > 0)
     return launch_qr_update_split(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, kNB,
                                   (max_rest_cols + split_update_tile_cols() - 1) /
                                       split_update_tile_cols(),
-                                  split_update_tile_cols(), persistent, st);
+                                  split_update_tile_cols(), rest_grid == 1, use_y, st);
   static const bool carve = (prefer_max_shared(qr_update_kernel<kTN>), true);
   (void)carve;
   qr_update_kernel<kTN><<<dim3(ntasks, (max_rest_cols + kTN - 1) / kTN), kThreads, 0, st>>>(

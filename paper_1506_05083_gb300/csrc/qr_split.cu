@@ -88,10 +88,12 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // scratch one slot per panel. Block of 4*S*kNB*kp entries: V^H digits
 // [S][2][kNB][kp], then V row digits [S][2][kp][kNB]; exponents [kNB + kp].
 struct PanelDigits {
-  const unsigned short *vh;
-  const unsigned short *v;
-  const int *ex;
+  const unsigned short *vh;   // digits of the left factor of the first product (V^H, or Y^H)
+  const unsigned short *v;    // V row digits
+  const int *ex;              // [kNB + kp]: exponents of vh's rows, then of V's rows
+  const int *exh;             // exponents of vh's rows (ex unless given apart)
   int kp;
+  bool pre_t;                 // vh holds Y^H = (V T)^H: the first product is already W'
 };
 
 template <int S>
@@ -105,7 +107,9 @@ __device__ __forceinline__ PanelDigits panel_digits(const unsigned short *dig, c
   pd.vh = dig + ((size_t)d * nslot + slot) * blk;
   pd.v = pd.vh + blk / 2;
   pd.ex = ex + ((size_t)d * nslot + slot) * (kNB + kp);
+  pd.exh = pd.ex;
   pd.kp = kp;
+  pd.pre_t = false;
   return pd;
 }
 
@@ -174,7 +178,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   const int r1st = max(k0, rlo);
 
   // ---- pass 0: exponents of X's columns over rows k0..rows-1 (V's are stored)
-  if (tid < kNB) sm.eVH[tid] = pd.ex[tid];
+  if (tid < kNB) sm.eVH[tid] = pd.exh[tid];
   if (kin != nullptr || carry) {
     if (tid < kTN) {
       const unsigned long long m = tid < ncols ? (carry ? sm.kNext[tid] : kin[tid]) : 0ull;
@@ -345,7 +349,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       sm.W[a][j] = q[a * (kTN + 1) + j];
     }
     __syncthreads();
-  } else {
+  } else if (!pd.pre_t) {
   constexpr int kPairs = (kNB / 2) * kTN / kThreads;          // pairs (a, 15 - a) per thread
   double2 wp[kPairs][2];
 #pragma unroll
@@ -481,7 +485,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreads, 3)
 qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                        const int *__restrict__ task_mode, int p, int col_off, int max_cols,
-                       int ntasks, int ntiles) {
+                       int ntasks, int ntiles, bool use_y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   OzSmem<S> &sm = *reinterpret_cast<OzSmem<S> *>(smraw);
   for (int item = blockIdx.x; item < ntasks * ntiles; item += gridDim.x) {
@@ -500,9 +504,14 @@ qr_update_split_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ t
         p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
     unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
     const int dslot = o.dig_kept ? p : (p & 1);
+    PanelDigits pd = panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot);
+    if (use_y) {                                          // W' = Y^H X in one product
+      pd.vh = o.ydig + ((size_t)d * 2 + (p & 1)) * (size_t)2 * S * kNB * o.kp;
+      pd.exh = o.yexp + ((size_t)d * 2 + (p & 1)) * kNB;
+      pd.pre_t = true;
+    }
     __syncthreads();                                      // shared memory of the previous item
-    oz_block_reflector_update<S>(panel_digits<S>(o.vdig, o.vexp, o.kp, d, o.dig_nslot, dslot),
-                                 o.rows, k0, Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin,
+    oz_block_reflector_update<S>(pd, o.rows, k0, Tg, A + (size_t)c0 * o.rows, o.rows, ncols, kin,
                                  false, kout, sm);
   }
 }
@@ -726,6 +735,92 @@ vdigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
   }
 }
 
+// Y = V T for panel p (the trailing update then forms W' = Y^H X in one
+// product, with no FP64 T^H W per column tile): one CTA per (task, 64 rows),
+// rows of V staged with their unit diagonal, Y written column by column
+// ([16][kp] per mode and slot p mod 2), the largest |Y| of each column into
+// ykey by atomic maximum (cleared by the panel kernel of step p).
+__global__ void __launch_bounds__(256)
+y_rows_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+              const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int r0 = blockIdx.y * kVdRows, kp = o.kp;
+  if (r0 >= kp) return;
+  const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows;
+  const double2 *A = o.A + (size_t)d * o.cols * o.rows;
+  const double2 *Tg = o.T + ((size_t)d * o.npanels + p) * kNB * kNB;
+  double2 *Y = o.ybuf + ((size_t)d * 2 + (p & 1)) * kNB * kp;
+  unsigned long long *yk = o.ykey + ((size_t)d * 2 + (p & 1)) * kNB;
+  __shared__ double2 Vs[kVdRows][kNB + 1], Ts[kNB][kNB + 1];
+  __shared__ unsigned long long wk[8][kNB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < kNB * kVdRows; e += 256) {
+    const int a = e / kVdRows, rr = e % kVdRows;
+    Vs[rr][a] = vget(A, rows, rows, k0, nbp, k0 + r0 + rr, a);
+  }
+  for (int e = tid; e < kNB * kNB; e += 256) Ts[e % kNB][e / kNB] = Tg[e];
+  __syncthreads();
+  // thread = (column b = tid / 16, 4 rows)
+  const int b = tid >> 4, rq = (tid & 15) * 4;
+  unsigned long long mk = 0ull;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = rq + u;
+    double2 y = make_double2(0.0, 0.0);
+    for (int a = 0; a <= b; ++a) {
+      const double2 v = Vs[rr][a], t = Ts[a][b];
+      y.x = fma(v.x, t.x, fma(-v.y, t.y, y.x));
+      y.y = fma(v.x, t.y, fma(v.y, t.x, y.y));
+    }
+    Y[(size_t)b * kp + r0 + rr] = y;
+    const unsigned long long k = key2(y);
+    mk = k > mk ? k : mk;
+  }
+  // column maxima: the 16 threads of a column are consecutive lanes
+#pragma unroll
+  for (int off = 8; off > 0; off >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, mk, off);
+    mk = w > mk ? w : mk;
+  }
+  if ((lane & 15) == 0) wk[warp][lane >> 4] = mk;       // warp w holds columns 2w, 2w + 1
+  __syncthreads();
+  if (tid < kNB) {
+    const unsigned long long m = wk[tid >> 1][tid & 1];
+    if (m) atomicMax(yk + tid, m);
+  }
+}
+
+// Digits of Y^H (conjugated, one exponent per column of Y, the layout of the
+// V^H digits) from y_rows_kernel's Y and column maxima.
+__global__ void __launch_bounds__(256)
+ydigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+               const int *__restrict__ task_mode, int p) {
+  const ObsDev &o = obs[task_obs[blockIdx.x]];
+  const int d = task_mode[blockIdx.x];
+  const int r0 = blockIdx.y * kVdRows, kp = o.kp;
+  if (r0 >= kp) return;
+  const int S = o.slices, slot = p & 1;
+  const double2 *Y = o.ybuf + ((size_t)d * 2 + slot) * kNB * kp;
+  const unsigned long long *yk = o.ykey + ((size_t)d * 2 + slot) * kNB;
+  unsigned short *yh = o.ydig + ((size_t)d * 2 + slot) * (size_t)2 * S * kNB * kp;
+  int *ye = o.yexp + ((size_t)d * 2 + slot) * kNB;
+  __shared__ int ecol[kNB];
+  const int tid = threadIdx.x;
+  if (tid < kNB) {
+    ecol[tid] = oz::key_exponent(yk[tid]);
+    if (blockIdx.y == 0) ye[tid] = ecol[tid];
+  }
+  __syncthreads();
+  const size_t sh = (size_t)2 * kNB * kp;
+  for (int e = tid; e < kNB * kVdRows; e += 256) {        // [s][part][b][r]
+    const int b = e / kVdRows, rr = e % kVdRows;
+    const double2 y = Y[(size_t)b * kp + r0 + rr];
+    oz::split_store_n(y.x, ecol[b], S, yh + (size_t)b * kp + r0 + rr, sh);
+    oz::split_store_n(-y.y, ecol[b], S, yh + (size_t)(kNB + b) * kp + r0 + rr, sh);
+  }
+}
+
 template <int S>
 cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st) {
@@ -743,7 +838,7 @@ cudaError_t launch_digits_s(const ObsDev *d_obs, const int *d_task_obs, const in
 template <int S>
 cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int col_off, int ntiles, int max_cols,
-                            bool persistent, cudaStream_t st) {
+                            bool persistent, bool use_y, cudaStream_t st) {
   const size_t smem = sizeof(OzSmem<S>);
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_split_kernel<S>, smem, granted);
@@ -753,7 +848,7 @@ cudaError_t launch_update_s(const ObsDev *d_obs, const int *d_task_obs, const in
   const int items = ntasks * ntiles;
   const int grid = persistent ? min(items, sm_count()) : items;
   qr_update_split_kernel<S><<<grid, kThreads, smem, st>>>(d_obs, d_task_obs, d_task_mode, p,
-                                                          col_off, max_cols, ntasks, ntiles);
+                                                          col_off, max_cols, ntasks, ntiles, use_y);
   return cudaGetLastError();
 }
 
@@ -841,18 +936,18 @@ int split_update_tile_cols() { return kTN; }
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int p, int slices,
                                    int col_off, int ntiles, int max_cols, bool persistent,
-                                   cudaStream_t st) {
+                                   bool use_y, cudaStream_t st) {
   switch (slices) {
     case 4: return launch_update_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, persistent, st);
+                                          max_cols, persistent, use_y, st);
     case 5: return launch_update_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, persistent, st);
+                                          max_cols, persistent, use_y, st);
     case 6: return launch_update_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, persistent, st);
+                                          max_cols, persistent, use_y, st);
     case 7: return launch_update_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, persistent, st);
+                                          max_cols, persistent, use_y, st);
     case 8: return launch_update_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, col_off, ntiles,
-                                          max_cols, persistent, st);
+                                          max_cols, persistent, use_y, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -861,6 +956,17 @@ cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int
                            int ntasks, int p, int kp_max, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   vdigits_kernel<<<dim3(ntasks, kp_max / kVdRows), 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                            int ntasks, int p, int kp_max, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  const dim3 grid(ntasks, kp_max / kVdRows);
+  y_rows_kernel<<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ydigits_kernel<<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   return cudaGetLastError();
 }
 

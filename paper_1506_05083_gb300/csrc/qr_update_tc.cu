@@ -1,0 +1,389 @@
+// Trailing update of the split-precision QR on fifth-generation tensor cores.
+//
+// For panel p, a tile of 64 trailing columns X (rows k0 .. rows-1) of one mode
+// is updated as
+//     X <- X - V W',   W' = Y^H X,   Y = V T          (compact WY, Sec. 3)
+// with both products as BF16 digit products on tcgen05.mma (kind::f16, FP32
+// accumulators in tensor memory), the digits as in ozaki.cuh: X split on the
+// fly with one bit of headroom (digits in [-64, 65]), Y^H (ydigits_kernel), V's
+// rows (vdigits_kernel) and W' balanced (|d| <= 128).
+//
+// First product, W'^T = X^T conj(Y) contracted over the rows in 16-row chunks:
+// the 128 MMA rows are [Re X ; Im X] of the 64 columns, the N columns the
+// 16 columns of Re Y^H then Im Y^H, per digit; one MMA per digit s of X against
+// the stacked digits t = 1 .. S+1-s of Y^H lands digit group g = s + t at
+// tensor-memory columns 32 (g - 2). A group sums at most 16 rows x 7 pairs x
+// 65 x 128 < 2^20 per chunk, so the accumulators are read every 8 chunks (sums
+// below 2^23, exact in FP32), combined exactly in int64 and added to FP64 sums
+// (one rounding per 128 rows, far below the digits' own truncation). Then W'_re = P(Re X, Re Y^H) - P(Im X, Im Y^H),
+// W'_im = P(Im X, Re Y^H) + P(Re X, Im Y^H), exchanged through shared memory.
+//
+// Second product, for 128 rows and 16 columns at a time:
+//   D_re = [Vr | Vi] [W'r ; -W'i],   D_im = [Vr | Vi] [W'i ; W'r]     (K = 32),
+// one pair of K = 16 MMAs per digit s of V against the stacked digits of W'
+// (group g at columns 16 (g - 2), imaginary parts 16 S further); a group sums at
+// most 32 x 7 x 128 x 128 < 2^22, exact in one pass. The epilogue folds the
+// groups, rebuilds doubles with integer instructions, subtracts from X and
+// keeps each column's largest |entry| over the next step's rows.
+//
+// Operand tiles are written by the CTA's threads into shared memory in the
+// no-swizzle K-major layout (tcgen05.cuh) and made visible to the tensor core
+// with a proxy fence; thread 0 issues the MMAs; completion comes back through
+// mbarriers with bounded waits (on expiry the timeout bit of the status word
+// is set, in-flight MMAs are waited for with a bound, tensor memory is freed
+// and the CTA returns; the decision to stop is block-uniform, taken by
+// __syncthreads_or).
+#include "axi_internal.h"
+#include "ozaki.cuh"
+#include "tcgen05.cuh"
+
+namespace axi {
+namespace {
+
+constexpr int kUC = 64;                 // X columns per CTA
+constexpr int kUT = 256;                // threads
+constexpr int kFold = 8;                // 16-row chunks per fold of the first product
+constexpr uint32_t kTmemCols = 256;
+constexpr long long kWaitCycles = 2000000000ll;
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// K-major no-swizzle core-matrix offset (bytes) of element (r, k) of a tile
+// whose rows are `kw` elements wide (kw = 16: SBO 256; kw = 32: SBO 512).
+__device__ __forceinline__ uint32_t core_off(int r, int k, int kw) {
+  return (uint32_t)((r >> 3) * (kw * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+template <int S>
+struct TcLayout {
+  // first product, per stage: A1 [S][128 x 16] (4 KB each), B1 [S][32 x 16] (1 KB each)
+  static constexpr uint32_t kA1 = S * 4096, kB1 = S * 1024, kStage = kA1 + kB1;
+  // second product: A2 [S][128 x 32] (8 KB each), B2 [2 variants][S][16 x 32] (1 KB each)
+  static constexpr uint32_t kA2 = S * 8192, kB2 = 2 * S * 1024;
+  static constexpr uint32_t kOps = (2 * kStage > kA2 + kB2 ? 2 * kStage : kA2 + kB2);
+  // FP64 exchange of the first product (aliases the operand area after it)
+  static constexpr uint32_t kP = 128 * 32 * 8;
+  static_assert(kP <= kOps, "exchange fits the operand area");
+  static constexpr uint32_t kW = 16 * kUC * 16;      // W' [16][64] complex
+  static constexpr uint32_t kTotal = kOps + kW + 1024;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kUT, 2)
+qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
+                    const int *__restrict__ task_mode, int p, int ntasks) {
+  using L = TcLayout<S>;
+  const int task = blockIdx.x % ntasks, tile = blockIdx.x / ntasks;
+  const ObsDev &o = obs[task_obs[task]];
+  const int d = task_mode[task];
+  const int k0 = p * kNB, nbp = min(kNB, o.cols - k0);
+  const int c0 = k0 + nbp + kNB + tile * kUC;          // beyond the next panel's columns
+  if (c0 >= o.cols) return;                             // uniform over the CTA
+  const int ncols = min(kUC, o.cols - c0);
+  const int rows = o.rows, K = rows - k0, nch = (K + 15) / 16, kp = o.kp;
+  double2 *X = o.A + (size_t)d * o.cols * rows + (size_t)c0 * rows;
+  const unsigned short *yh = o.ydig + ((size_t)d * 2 + (p & 1)) * (size_t)2 * S * kNB * kp;
+  const int *yex = o.yexp + ((size_t)d * 2 + (p & 1)) * kNB;
+  const int dslot = o.dig_kept ? p : (p & 1);
+  const size_t vblk = (size_t)4 * S * kNB * kp;
+  const unsigned short *vr = o.vdig + ((size_t)d * o.dig_nslot + dslot) * vblk + vblk / 2;
+  const int *vex = o.vexp + ((size_t)d * o.dig_nslot + dslot) * (kNB + kp) + kNB;
+  const unsigned long long *kin = p > 0 ? o.ckey + ((size_t)d * 2 + (p & 1)) * o.cols + c0 : nullptr;
+  unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
+
+  extern __shared__ __align__(1024) unsigned char usm[];
+  unsigned char *ops = usm;
+  double2 *Wp = reinterpret_cast<double2 *>(usm + L::kOps);           // W' [b][j]
+  __shared__ __align__(8) uint64_t mma_done[2], acc_full, d_full, drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int eX[kUC], eW[kUC], eY[kNB];
+  __shared__ unsigned long long knext[kUC];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quad = warp & 3, half = warp >> 2;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_init(&mma_done[0], 1);
+    tc::mbar_init(&mma_done[1], 1);
+    tc::mbar_init(&acc_full, 1);
+    tc::mbar_init(&d_full, 1);
+    tc::mbar_init(&drain, 1);
+  }
+  if (tid < kNB) eY[tid] = yex[tid];
+  if (tid < kUC) knext[tid] = 0ull;
+  // column exponents of X over rows k0.. (carried keys, else a scan), one bit of headroom
+  if (kin != nullptr) {
+    if (tid < kUC) eX[tid] = tid < ncols ? oz::key_exponent(kin[tid]) + 1 : 0;
+  } else {
+    for (int j = warp; j < kUC; j += kUT / 32) {
+      unsigned long long m = 0;
+      if (j < ncols)
+        for (int i = k0 + lane; i < rows; i += 32) {
+          const unsigned long long k = oz::abs_key2(X[(size_t)j * rows + i]);
+          m = k > m ? k : m;
+        }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, off);
+        m = w > m ? w : m;
+      }
+      if (lane == 0) eX[j] = oz::key_exponent(m) + 1;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
+
+  // ---- first product: W'^T = X^T conj(Y) over the rows, two operand stages
+  // each fold (8 chunks, 128 rows) is exact in int64 and added to FP64 sums
+  double pacc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) pacc[q] = 0.0;
+  const int prow = 32 * quad + lane, pj = prow & 63;
+  int nfold = 0;
+  bool ok = true;
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    unsigned char *A1 = ops + b * L::kStage, *B1 = A1 + L::kA1;
+    bool w = true;                                      // stage b free: chunk c - 2's MMAs done
+    if (c >= 2) w = tc::mbar_wait(&mma_done[b], ((c - 2) >> 1) & 1, kWaitCycles);
+    if (__syncthreads_or(!w)) { ok = false; break; }
+    const int i0 = k0 + 16 * c;
+    // A1: rows r < 64 Re X(:, r), r >= 64 Im X(:, r - 64); k = row i0 + k.
+    // Thread: column j = tid / 4, rows 4 (tid % 4) .. +3 (two pairs).
+    {
+      const int j = tid >> 2, kq = (tid & 3) * 4;
+      double2 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + kq + u;
+        x[u] = (j < ncols && i < rows) ? X[(size_t)j * rows + i] : make_double2(0.0, 0.0);
+      }
+      const int e = eX[j];
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        const int k = kq + 2 * pr;
+        uint32_t *dre = reinterpret_cast<uint32_t *>(A1 + core_off(j, k, 16));
+        uint32_t *dim = reinterpret_cast<uint32_t *>(A1 + core_off(64 + j, k, 16));
+        oz::split2_fast<S>(x[2 * pr].x, x[2 * pr + 1].x, e, dre, 1024);
+        oz::split2_fast<S>(x[2 * pr].y, x[2 * pr + 1].y, e, dim, 1024);
+      }
+    }
+    // B1: row n = 16 part + b' of digit t holds Y^H digit (part, b') at rows
+    // i0 .. i0 + 15, two 16-byte pieces per (t, n) from the [t][part][b'][kp] layout
+    for (int e = tid; e < S * 32 * 2; e += kUT) {
+      const int t = e / 64, n = (e / 2) & 31, kg = e & 1;
+      const uint4 v = *reinterpret_cast<const uint4 *>(
+          yh + ((size_t)(t * 2 + (n >> 4)) * kNB + (n & 15)) * kp + (i0 - k0) + 8 * kg);
+      *reinterpret_cast<uint4 *>(B1 + t * 1024 + core_off(n, 8 * kg, 16)) = v;
+    }
+    fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const bool first = (c % kFold) == 0, fold = c % kFold == kFold - 1 || c == nch - 1;
+    if (tid == 0) {
+      const uint32_t a0 = tc::smem_u32(A1), b0 = tc::smem_u32(B1);
+#pragma unroll
+      for (int s = 1; s <= S; ++s) {
+        const uint64_t da = tc::smem_desc(a0 + (s - 1) * 4096, 128, 256);
+        const uint64_t db = tc::smem_desc(b0, 128, 256);
+        tc::mma_bf16(tmem + (uint32_t)(32 * (s - 1)), da, db, tc::idesc_bf16_f32(128, 32 * (S + 1 - s)),
+                     !(first && s == 1));
+      }
+      tc::commit(&mma_done[b]);
+      if (fold) tc::commit(&acc_full);
+    }
+    if (fold) {                                         // fold the groups into int64 sums
+      const bool wf = tc::mbar_wait(&acc_full, nfold & 1, kWaitCycles);
+      ++nfold;
+      if (__syncthreads_or(!wf)) { ok = false; break; }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int qh = 0; qh < 2; ++qh) {
+        long long hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
+#pragma unroll
+        for (int g = 2; g <= S + 1; ++g) {
+          uint32_t r[8];
+          tc::ld8(tmem + lane_addr + (uint32_t)(32 * (g - 2) + 16 * half + 8 * qh), r);
+          tc::ld_wait();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) oz::fold_group_rn<S>(hi[q], lo[q], g, __uint_as_float(r[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          pacc[8 * qh + q] += oz::unfold<S>(hi[q], lo[q], eX[pj] + eY[8 * qh + q]);
+      }
+      tc::fence_before_sync();
+      __syncthreads();                                  // TMEM read before the next MMAs
+    }
+  }
+  if (ok) {
+    // P(r, n) in FP64: r = part_x * 64 + j, n = part_y * 16 + b'
+    double *P = reinterpret_cast<double *>(ops);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) P[prow * 32 + 16 * half + q] = pacc[q];
+    __syncthreads();
+    // W'(b', j) = Y^H X: re = P(Re, Re) - P(Im, Im), im = P(Im, Re) + P(Re, Im)
+    for (int e = tid; e < kNB * kUC; e += kUT) {
+      const int bb = e / kUC, jj = e % kUC;
+      Wp[bb * kUC + jj] = make_double2(P[jj * 32 + bb] - P[(64 + jj) * 32 + 16 + bb],
+                                       P[(64 + jj) * 32 + bb] + P[jj * 32 + 16 + bb]);
+    }
+    __syncthreads();
+    if (tid < kUC) {
+      unsigned long long m = 0;
+      for (int bb = 0; bb < kNB; ++bb) {
+        const unsigned long long k = oz::abs_key2(Wp[bb * kUC + tid]);
+        m = k > m ? k : m;
+      }
+      eW[tid] = oz::key_exponent(m);
+    }
+    __syncthreads();
+  }
+
+  // ---- second product: X -= V W', 128 rows x 16 columns per unit
+  unsigned char *A2 = ops, *B2 = ops + L::kA2;
+  constexpr uint32_t kDim = 16 * S;                     // TMEM column of the imaginary parts
+  const int knext_row = k0 + kNB;
+  int nunit = 0;
+  for (int rb = 0; ok && 128 * rb < K; ++rb) {
+    const int r0 = 128 * rb;                            // rows k0 + r0 .. of the block
+    // A2: row rr, k < 16 Vr(rr, k), k >= 16 Vi(rr, k - 16) from the [s][part][r][16] layout
+    for (int e = tid; e < S * 128 * 4; e += kUT) {
+      const int s = e / 512, rr = (e >> 2) & 127, piece = e & 3;    // piece = part * 2 + kg
+      const uint4 v = *reinterpret_cast<const uint4 *>(
+          vr + ((size_t)(s * 2 + (piece >> 1)) * kp + r0 + rr) * kNB + 8 * (piece & 1));
+      *reinterpret_cast<uint4 *>(A2 + s * 8192 + core_off(rr, 8 * piece, 32)) = v;
+    }
+    const int er = vex[r0 + 32 * quad + lane];
+    const int i = k0 + r0 + 32 * quad + lane;
+    for (int u = 0; u < kUC / 16 && 16 * u < ncols; ++u) {
+      // B2: variant 0 rows jj: k < 16 W'r(k, jj), k >= 16 -W'i; variant 1: W'i, W'r
+      for (int e = tid; e < 2 * 16 * 32; e += kUT) {
+        const int var = e >> 9, jj = (e >> 5) & 15, k = e & 31;
+        const double2 w = Wp[(k & 15) * kUC + 16 * u + jj];
+        const double x = var == 0 ? (k < 16 ? w.x : -w.y) : (k < 16 ? w.y : w.x);
+        oz::split_store_n(x, eW[16 * u + jj], S,
+                          reinterpret_cast<unsigned short *>(B2 + var * S * 1024 + core_off(jj, k, 32)),
+                          512);
+      }
+      fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t a0 = tc::smem_u32(A2), b0 = tc::smem_u32(B2);
+#pragma unroll
+        for (int s = 1; s <= S; ++s) {
+          const uint32_t idesc = tc::idesc_bf16_f32(128, 16 * (S + 1 - s));
+#pragma unroll
+          for (int var = 0; var < 2; ++var)
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+              const uint64_t da = tc::smem_desc(a0 + (s - 1) * 8192 + kh * 256, 128, 512);
+              const uint64_t db = tc::smem_desc(b0 + var * S * 1024 + kh * 256, 128, 512);
+              tc::mma_bf16(tmem + (uint32_t)(kDim * var + 16 * (s - 1)), da, db, idesc,
+                           !(s == 1 && kh == 0));
+            }
+        }
+        tc::commit(&d_full);
+      }
+      const bool w = tc::mbar_wait(&d_full, nunit & 1, kWaitCycles);
+      ++nunit;
+      if (__syncthreads_or(!w)) { ok = false; break; }
+      tc::fence_after_sync();
+      // epilogue: warp (quad, half) takes TMEM lanes 32 quad .. (rows) and the
+      // real (half 0) or imaginary (half 1) part of the unit's 16 columns
+      double *Xd = reinterpret_cast<double *>(X);
+#pragma unroll
+      for (int qh = 0; qh < 2; ++qh) {
+        long long yh2[8], yl2[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) yh2[q] = yl2[q] = 0;
+#pragma unroll
+        for (int g = 2; g <= S + 1; ++g) {
+          uint32_t rv[8];
+          tc::ld8(tmem + lane_addr + (uint32_t)(kDim * half + 16 * (g - 2) + 8 * qh), rv);
+          tc::ld_wait();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) oz::fold_group<S>(yh2[q], yl2[q], g, __uint_as_float(rv[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int jj = 16 * u + 8 * qh + q;
+          unsigned long long key = 0ull;
+          if (i < rows && jj < ncols) {
+            const int e = er + eW[jj] + oz::unfold1_shift<S>();
+            double *xp = Xd + 2 * ((size_t)jj * rows + i) + half;
+            const double v = *xp - oz::scaled_to_double(oz::unfold1_int<S>(yh2[q], yl2[q]), e);
+            *xp = v;
+            if (i >= knext_row) key = oz::abs_key(v);
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, key, off);
+            key = o2 > key ? o2 : key;
+          }
+          if (lane == 0 && key != 0ull) atomicMax(&knext[jj], key);
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();                                  // TMEM and B2 free for the next unit
+    }
+    __syncthreads();                                    // A2 free for the next row block
+  }
+  if (!ok) {
+    // a wait ran out: let any MMA still in flight finish (bounded) before the
+    // tensor memory is released, and report the timeout
+    if (tid == 0) {
+      tc::commit(&drain);
+      (void)tc::mbar_wait(&drain, 0, kWaitCycles);
+      atomicOr(o.status, kStatTimeout);
+    }
+  } else if (tid < ncols) {
+    kout[tid] = knext[tid];
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int S>
+cudaError_t launch_tc_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                        int ntasks, int p, int ntiles, cudaStream_t st) {
+  const size_t smem = TcLayout<S>::kTotal;
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(qr_update_tc_kernel<S>, smem, granted);
+  if (e != cudaSuccess) return e;
+  static const bool carve = (prefer_max_shared(qr_update_tc_kernel<S>), true);
+  (void)carve;
+  qr_update_tc_kernel<S><<<ntasks * ntiles, kUT, smem, st>>>(d_obs, d_task_obs, d_task_mode, p,
+                                                            ntasks);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_qr_update_tc(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                                int ntasks, int p, int slices, int max_rest_cols, cudaStream_t st) {
+  if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
+  const int ntiles = (max_rest_cols + kUC - 1) / kUC;
+  switch (slices) {
+    case 4: return launch_tc_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    case 5: return launch_tc_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    case 6: return launch_tc_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    case 7: return launch_tc_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    case 8: return launch_tc_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace axi

@@ -106,3 +106,37 @@ def test_split_digits_sweep():
     assert errs[-1] < 1e-11
     assert errs[0] > errs[-1]
     assert all(e < 1e-3 for e in errs)
+
+
+@pytest.mark.parametrize("name", ["medium", "smooth", "small_trans"])
+def test_split_tc_update_parity(name):
+    """The trailing update on tcgen05 (tuning rest_grid 2: W' = Y^H X and
+    X -= V W' as BF16 digit products with tensor-memory accumulators): Q R
+    reproduces the filled modes, the apply meets the oracle bar, and the
+    coefficients agree with the mma.sync update's to the digits' precision."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case(name)
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    prec = axi.PREC_SPLIT_BF16 | (7 << 8)
+    dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+    coefs = {}
+    for rg in (0, 2):
+        op = axi.Operator([spec], prec=prec, tuning='{"next_update": 2, "rest_grid": %d}' % rg)
+        assert '"rest_grid": %d' % rg in op.tuning()
+        coefs[rg] = op.apply(op.incident(torch.tensor(dirs_np, device="cuda"))).cpu().numpy()
+        if rg == 2:
+            Af = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
+            Ap, tau, T, nb = op.factors()
+            Ap = Ap.cpu().numpy().transpose(0, 2, 1)
+            tau = tau.cpu().numpy()
+        torch.cuda.synchronize()
+        assert op.status() == 0
+    rows, cols = Ap.shape[1], Ap.shape[2]
+    for d in (0, 1, ob.P // 2):
+        Q = _householder_q(Ap[d], tau[d], rows, cols)
+        R = np.triu(Ap[d][:cols])
+        assert np.linalg.norm(Q[:, :cols] @ R - Af[d]) < 1e-12 * np.linalg.norm(Af[d])
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+    c_ora = O.solve_modes(ob, fac, fh)
+    assert _e_bd(A, ob, coefs[2], c_ora, fh) < 1e-10
+    assert _e_bd(A, ob, coefs[2], coefs[0], fh) < 1e-10

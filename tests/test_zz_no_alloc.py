@@ -51,6 +51,18 @@ def test_noalloc_apply_matches_apply(prec):
         assert np.abs(coef - coef_ref).max() <= 1e-12 * np.abs(coef_ref).max()
         assert np.abs(sig - sig_ref).max() <= 1e-12 * np.abs(sig_ref).max()
     assert np.abs(results[0][0] - results[2][0]).max() > 0   # the calls really differ
+    # nothing allocated: the caching allocator's and the driver's counters stay
+    # put over further calls (the kernels are loaded by the calls above)
+    dirs = torch.tensor(synth.plane_wave_directions(7, 34), device="cuda")
+    f = op.incident(dirs)
+    coef = torch.empty((7, spec.P, spec.cols), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    torch_before, free_before = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        op.apply_noalloc(f, coef)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == torch_before
+    assert torch.cuda.mem_get_info()[0] == free_before
 
 
 def test_noalloc_rejects_batch_beyond_static_scratch():
