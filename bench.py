@@ -288,19 +288,23 @@ class Arm:
     """One plan (split or native FP64) of the workload with its buffers and
     the two CUDA graphs of a step (build; incident data + apply)."""
 
-    def __init__(self, name, prec, spec, ob, W, dirs, dev, graph):
+    def __init__(self, name, prec, spec, ob, W, dirs, dev, graph, tuning=None):
         import torch
         from paper_1506_05083_gb300 import axi
         self.name, self.ob, self.W, self.dirs = name, ob, W, dirs
-        self.op = axi.Operator([spec], prec=prec)
+        self.op = axi.Operator([spec], prec=prec, tuning=tuning)
         self.coef = torch.empty((W, ob.P, spec.cols), dtype=torch.complex128, device=dev)
         self.sigma = torch.empty((W, spec.cols, ob.P), dtype=torch.complex128, device=dev)
         self.scratch = torch.empty(self.op.apply_scratch_bytes(W), dtype=torch.uint8, device=dev)
         self.graph = graph
         self.g_build = self.g_apply = None
         # schedule choices (panel cluster size, next-panel update arithmetic,
-        # trailing-update grid) timed on the device by the library's autotuner
-        self.tuning = json.loads(self.op.autotune(reps=2))
+        # trailing-update kernel) timed on the device by the library's
+        # autotuner, unless given
+        if tuning is None:
+            self.tuning = json.loads(self.op.autotune(reps=2))
+        else:
+            self.tuning = dict(json.loads(self.op.tuning()), given=True)
 
     def step_direct(self):
         self.op.refactor()
@@ -438,11 +442,11 @@ def run_single(args, wl):
         plan_ms[name] = (time.perf_counter() - t0) * 1e3
     arms = []
     if args.prec == "split":
-        arms.append(Arm("split", split_prec, spec, ob, W, dirs, dev, args.graph))
+        arms.append(Arm("split", split_prec, spec, ob, W, dirs, dev, args.graph, args.tuning))
         if not args.no_fp64_arm:
             arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph))
     else:
-        arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph))
+        arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph, args.tuning))
     head = arms[0]
     for arm in arms:
         for _ in range(args.warmup):
@@ -658,6 +662,9 @@ def main():
     ap.add_argument("--prec", default="split", choices=["split", "fp64"],
                     help="headline plan: Ozaki BF16 digits or native FP64")
     ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--tuning", default=None,
+                    help="schedule of the headline plan as the library's tuning JSON "
+                         "(default: autotuned on the device)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup", choices=["cup", "smooth", "batched", "cup_near"],

@@ -188,7 +188,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   tcgen05 trailing update (tensor-memory accumulators, 64
  *                   columns per CTA; split plans whose next-panel update
  *                   is in digits, else as 0);
- *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA.
+ *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA;
+ *   "crit_stream"   0 the panels and next-panel updates on `stream`, 1 on
+ *                   a stream of the operator with the device's highest
+ *                   priority (forked from and joined back into `stream`).
  * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
  * keys kept; AXI_ERR_ARG on malformed input or values out of range);
  * axi_plan_get_tuning writes the current one into buf[n] (AXI_ERR_ARG if it

@@ -181,9 +181,11 @@ struct axi_operator_s {
   ObsDev *d_obs;
   int *d_task_obs, *d_task_mode, *d_status;
   // look-ahead: the bulk of each trailing update runs on `side` while the
-  // next panel runs on the caller's stream (fork/join through the events)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
+  // next panel runs on `crit` (highest stream priority, so its CTAs are
+  // dispatched ahead of queued trailing-update CTAs) or on the caller's
+  // stream; fork/join through the events
+  cudaStream_t side = nullptr, crit = nullptr;
+  cudaEvent_t ev_panel = nullptr, ev_rest = nullptr, ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -303,6 +305,9 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
     } else if (key == "rest_grid") {
       if (iv < 0 || iv > 2) return false;
       t.rest_grid = iv;
+    } else if (key == "crit_stream") {
+      if (iv < 0 || iv > 1) return false;
+      t.crit_stream = iv;
     } else if (key == "panel_threads") {
       if (iv != 0 && iv != 128 && iv != 256) return false;
       t.panel_threads = iv;
@@ -313,8 +318,9 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
 std::string tuning_json(const axi::Tuning &t) {
   char buf[200];
   std::snprintf(buf, sizeof(buf),
-                "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d}",
-                t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads);
+                "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d, "
+                "\"crit_stream\": %d}",
+                t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream);
   return buf;
 }
 
@@ -642,6 +648,14 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
   const int slices = p->obs[0].dev.slices;
   int kp_max = 0;
   for (const auto &ob : p->obs) kp_max = ob.dev.kp > kp_max ? ob.dev.kp : kp_max;
+  // the panel chain on the high-priority stream, joined back below
+  const cudaStream_t caller = st;
+  if (p->tune.crit_stream == 1 && !p->step_tasks.empty()) {
+    if (cudaEventRecord(op->ev_fork, caller) != cudaSuccess ||
+        cudaStreamWaitEvent(op->crit, op->ev_fork, 0) != cudaSuccess)
+      return AXI_ERR_CUDA;
+    st = op->crit;
+  }
   bool rest_pending = false, side_used = false;
   for (size_t s = 0; s < p->step_tasks.size(); ++s) {
     const int nt = p->step_tasks[s];
@@ -712,6 +726,12 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
   if (side_used && (cudaEventRecord(op->ev_rest, op->side) != cudaSuccess ||
                     cudaStreamWaitEvent(st, op->ev_rest, 0) != cudaSuccess))
     return AXI_ERR_CUDA;
+  if (st != caller) {
+    if (cudaEventRecord(op->ev_join, st) != cudaSuccess ||
+        cudaStreamWaitEvent(caller, op->ev_join, 0) != cudaSuccess)
+      return AXI_ERR_CUDA;
+    st = caller;
+  }
   for (size_t i = 0; i < p->obs.size(); ++i) {
     const ObsDev &d = p->obs[i].dev;
     if (d.tsvd) {                         // SVD of R: the apply uses V Sigma^+ U_R^H
@@ -818,9 +838,14 @@ axi_status axi_build_operator(axi_plan *plan, void *d_workspace, size_t bytes, v
   op->d_task_obs = reinterpret_cast<int *>(ws + plan->off_task_obs);
   op->d_task_mode = reinterpret_cast<int *>(ws + plan->off_task_mode);
   op->d_status = reinterpret_cast<int *>(ws + plan->off_status);
-  if (cudaStreamCreateWithFlags(&op->side, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&op->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&op->crit, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&op->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&op->ev_rest, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&op->ev_rest, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     axi_operator_destroy(op);
     return AXI_ERR_CUDA;
   }
@@ -986,8 +1011,10 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
       for (int rg : {0, 1, 2})
-        for (int pt : {128, 256}) {
+        for (int pt : {128, 256})
+        for (int cs : {0, 1}) {
         if (rg == 2 && nu != 2) continue;             // the tcgen05 update reads Y^H digits
+        p->tune.crit_stream = cs;
 
         p->tune.next_update = nu;
         p->tune.panel_cluster = pc;
@@ -1066,8 +1093,14 @@ axi_status axi_operator_destroy(axi_operator *op) {
     cudaStreamSynchronize(op->side);
     cudaStreamDestroy(op->side);
   }
+  if (op->crit) {
+    cudaStreamSynchronize(op->crit);
+    cudaStreamDestroy(op->crit);
+  }
   if (op->ev_panel) cudaEventDestroy(op->ev_panel);
   if (op->ev_rest) cudaEventDestroy(op->ev_rest);
+  if (op->ev_fork) cudaEventDestroy(op->ev_fork);
+  if (op->ev_join) cudaEventDestroy(op->ev_join);
   delete op;
   return AXI_OK;
 }

@@ -23,6 +23,8 @@ struct Tuning {
   int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM),
                           // 2 tcgen05 kernel (split plans whose update reads Y^H digits; else as 0)
   int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
+  int crit_stream = 0;    // 0 the panel chain on the caller's stream, 1 on a stream of the
+                          // operator with the device's highest priority
 };
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).

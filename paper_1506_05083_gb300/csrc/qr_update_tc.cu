@@ -15,8 +15,9 @@
 // tensor-memory columns 32 (g - 2). A group sums at most 16 rows x 7 pairs x
 // 65 x 128 < 2^20 per chunk, so the accumulators are read every 8 chunks (sums
 // below 2^23, exact in FP32), combined exactly in int64 and added to FP64 sums
-// (one rounding per 128 rows, far below the digits' own truncation). Then W'_re = P(Re X, Re Y^H) - P(Im X, Im Y^H),
-// W'_im = P(Im X, Re Y^H) + P(Re X, Im Y^H), exchanged through shared memory.
+// (one rounding per 128 rows, far below the digits' own truncation). Then
+//   W'_re = P(Re X, Re Y^H) - P(Im X, Im Y^H),  W'_im = P(Im X, Re Y^H) + P(Re X, Im Y^H),
+// exchanged through shared memory.
 //
 // Second product, for 128 rows and 16 columns at a time:
 //   D_re = [Vr | Vi] [W'r ; -W'i],   D_im = [Vr | Vi] [W'i ; W'r]     (K = 32),
@@ -24,12 +25,16 @@
 // (group g at columns 16 (g - 2), imaginary parts 16 S further); a group sums at
 // most 32 x 7 x 128 x 128 < 2^22, exact in one pass. The epilogue folds the
 // groups, rebuilds doubles with integer instructions, subtracts from X and
-// keeps each column's largest |entry| over the next step's rows.
+// keeps, per column, the high word of the largest |entry|'s IEEE key over the
+// next step's rows (the exponent is all the next step's split needs).
 //
-// Operand tiles are written by the CTA's threads into shared memory in the
-// no-swizzle K-major layout (tcgen05.cuh) and made visible to the tensor core
-// with a proxy fence; thread 0 issues the MMAs; completion comes back through
-// mbarriers with bounded waits (on expiry the timeout bit of the status word
+// Loads are asynchronous and one step ahead: the raw X values and Y^H digits of
+// chunk c + 1 are copied (cp.async, 16 bytes per copy) while chunk c is split,
+// the V-row digits of a 128-row block likewise, and the X values the epilogue
+// subtracts from are loaded before it waits for its MMAs. Digit tiles sit in
+// shared memory in the no-swizzle K-major layout (tcgen05.cuh), made visible
+// to the tensor core with a proxy fence; thread 0 issues the MMAs; completion
+// comes back through mbarriers with bounded waits (on expiry the timeout bit of the status word
 // is set, in-flight MMAs are waited for with a bound, tensor memory is freed
 // and the CTA returns; the decision to stop is block-uniform, taken by
 // __syncthreads_or).
@@ -45,6 +50,8 @@ constexpr int kUT = 256;                // threads
 constexpr int kFold = 8;                // 16-row chunks per fold of the first product
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitCycles = 2000000000ll;
+constexpr int kRawLd = 17;             // raw X column stride (complex): conflict-free 16-byte reads
+constexpr uint32_t kRawBytes = kRawLd * kUC * 16;   // one chunk of raw X: [64 columns][16 rows] complex
 
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -58,16 +65,20 @@ __device__ __forceinline__ uint32_t core_off(int r, int k, int kw) {
 
 template <int S>
 struct TcLayout {
-  // first product, per stage: A1 [S][128 x 16] (4 KB each), B1 [S][32 x 16] (1 KB each)
-  static constexpr uint32_t kA1 = S * 4096, kB1 = S * 1024, kStage = kA1 + kB1;
-  // second product: A2 [S][128 x 32] (8 KB each), B2 [2 variants][S][16 x 32] (1 KB each)
+  // first product: A1 [S][128 x 16] (4 KB per digit), two stages of raw X
+  // chunks and two of B1 [S][32 x 16] (1 KB per digit)
+  static constexpr uint32_t kA1 = S * 4096;
+  static constexpr uint32_t kRaw = kA1;
+  static constexpr uint32_t kB1 = kRaw + 2 * kRawBytes;
+  static constexpr uint32_t kOps = kB1 + 2 * S * 1024;
+  // second product (aliases the first's area): A2 [S][128 x 32] (8 KB per
+  // digit), B2 [2 variants][S][16 x 32] (1 KB per digit)
   static constexpr uint32_t kA2 = S * 8192, kB2 = 2 * S * 1024;
-  static constexpr uint32_t kOps = (2 * kStage > kA2 + kB2 ? 2 * kStage : kA2 + kB2);
+  static_assert(kA2 + kB2 <= kOps, "second product fits the operand area");
   // FP64 exchange of the first product (aliases the operand area after it)
-  static constexpr uint32_t kP = 128 * 32 * 8;
-  static_assert(kP <= kOps, "exchange fits the operand area");
+  static_assert(128 * 33 * 8 <= kOps, "exchange fits the operand area");
   static constexpr uint32_t kW = 16 * kUC * 16;      // W' [16][64] complex
-  static constexpr uint32_t kTotal = kOps + kW + 1024;
+  static constexpr uint32_t kTotal = kOps + kW;
 };
 
 template <int S>
@@ -94,36 +105,60 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   unsigned long long *kout = o.ckey + ((size_t)d * 2 + ((p + 1) & 1)) * o.cols + c0;
 
   extern __shared__ __align__(1024) unsigned char usm[];
-  unsigned char *ops = usm;
+  unsigned char *A1 = usm;
   double2 *Wp = reinterpret_cast<double2 *>(usm + L::kOps);           // W' [b][j]
-  __shared__ __align__(8) uint64_t mma_done[2], acc_full, d_full, drain;
+  __shared__ __align__(8) uint64_t mma_done, acc_full, d_full, drain;
   __shared__ uint32_t tmem_base;
   __shared__ int eX[kUC], eW[kUC], eY[kNB];
-  __shared__ unsigned long long knext[kUC];
+  __shared__ unsigned knext[kUC];        // high words of the column keys (exponent bits)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quad = warp & 3, half = warp >> 2;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) {
-    tc::mbar_init(&mma_done[0], 1);
-    tc::mbar_init(&mma_done[1], 1);
+    tc::mbar_init(&mma_done, 1);
     tc::mbar_init(&acc_full, 1);
     tc::mbar_init(&d_full, 1);
     tc::mbar_init(&drain, 1);
   }
+  // Chunk c's raw X (thread: column tid / 4, rows 4 (tid % 4) .. +3, the
+  // values it splits itself) and Y^H digits (row n = 16 part + b' of digit t:
+  // Y^H digit (part, b') at rows i0 .. i0 + 15, two 16-byte pieces from the
+  // [t][part][b'][kp] layout) into stage c mod 2, one commit group per chunk.
+  const int xj = tid >> 2, xk = (tid & 3) * 4;
+  auto issue = [&](int c) {
+    const int stg = c & 1, i0 = k0 + 16 * c;
+    double2 *raw = reinterpret_cast<double2 *>(usm + L::kRaw + stg * kRawBytes);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + xk + u;
+      const bool valid = xj < ncols && i < rows;
+      oz::cp_async16(raw + xj * kRawLd + xk + u, valid ? X + (size_t)xj * rows + i : X, valid);
+    }
+    unsigned char *B1 = usm + L::kB1 + stg * S * 1024;
+    for (int e = tid; e < S * 32 * 2; e += kUT) {
+      const int t = e / 64, n = (e / 2) & 31, kg = e & 1;
+      oz::cp_async16(B1 + t * 1024 + core_off(n, 8 * kg, 16),
+                     yh + ((size_t)(t * 2 + (n >> 4)) * kNB + (n & 15)) * kp + (i0 - k0) + 8 * kg, true);
+    }
+    oz::cp_async_commit();
+  };
+  issue(0);                                             // overlaps the set-up below
   if (tid < kNB) eY[tid] = yex[tid];
-  if (tid < kUC) knext[tid] = 0ull;
+  if (tid < kUC) knext[tid] = 0u;
   // column exponents of X over rows k0.. (carried keys, else a scan), one bit of headroom
   if (kin != nullptr) {
     if (tid < kUC) eX[tid] = tid < ncols ? oz::key_exponent(kin[tid]) + 1 : 0;
   } else {
     for (int j = warp; j < kUC; j += kUT / 32) {
       unsigned long long m = 0;
-      if (j < ncols)
+      if (j < ncols) {
+#pragma unroll 4
         for (int i = k0 + lane; i < rows; i += 32) {
           const unsigned long long k = oz::abs_key2(X[(size_t)j * rows + i]);
           m = k > m ? k : m;
         }
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, off);
@@ -138,7 +173,7 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   const uint32_t tmem = tmem_base;
   const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
 
-  // ---- first product: W'^T = X^T conj(Y) over the rows, two operand stages
+  // ---- first product: W'^T = X^T conj(Y) over the rows
   // each fold (8 chunks, 128 rows) is exact in int64 and added to FP64 sums
   double pacc[16];
 #pragma unroll
@@ -147,47 +182,33 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   int nfold = 0;
   bool ok = true;
   for (int c = 0; c < nch; ++c) {
-    const int b = c & 1;
-    unsigned char *A1 = ops + b * L::kStage, *B1 = A1 + L::kA1;
-    bool w = true;                                      // stage b free: chunk c - 2's MMAs done
-    if (c >= 2) w = tc::mbar_wait(&mma_done[b], ((c - 2) >> 1) & 1, kWaitCycles);
+    // MMA(c - 1) done: A1 and stage (c + 1) mod 2 are free
+    bool w = true;
+    if (c >= 1) w = tc::mbar_wait(&mma_done, (c - 1) & 1, kWaitCycles);
     if (__syncthreads_or(!w)) { ok = false; break; }
-    const int i0 = k0 + 16 * c;
-    // A1: rows r < 64 Re X(:, r), r >= 64 Im X(:, r - 64); k = row i0 + k.
-    // Thread: column j = tid / 4, rows 4 (tid % 4) .. +3 (two pairs).
+    if (c + 1 < nch) issue(c + 1);
+    else oz::cp_async_commit();                         // empty group: chunk c's is the older one
+    oz::cp_async_wait<1>();
+    // A1: rows r < 64 Re X(:, r), r >= 64 Im X(:, r - 64); k = row i0 + k
     {
-      const int j = tid >> 2, kq = (tid & 3) * 4;
-      double2 x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + kq + u;
-        x[u] = (j < ncols && i < rows) ? X[(size_t)j * rows + i] : make_double2(0.0, 0.0);
-      }
-      const int e = eX[j];
+      const double2 *raw = reinterpret_cast<const double2 *>(usm + L::kRaw + (c & 1) * kRawBytes);
+      const int e = eX[xj];
 #pragma unroll
       for (int pr = 0; pr < 2; ++pr) {
-        const int k = kq + 2 * pr;
-        uint32_t *dre = reinterpret_cast<uint32_t *>(A1 + core_off(j, k, 16));
-        uint32_t *dim = reinterpret_cast<uint32_t *>(A1 + core_off(64 + j, k, 16));
-        oz::split2_fast<S>(x[2 * pr].x, x[2 * pr + 1].x, e, dre, 1024);
-        oz::split2_fast<S>(x[2 * pr].y, x[2 * pr + 1].y, e, dim, 1024);
+        const double2 x0 = raw[xj * kRawLd + xk + 2 * pr], x1 = raw[xj * kRawLd + xk + 2 * pr + 1];
+        uint32_t *dre = reinterpret_cast<uint32_t *>(A1 + core_off(xj, xk + 2 * pr, 16));
+        uint32_t *dim = reinterpret_cast<uint32_t *>(A1 + core_off(64 + xj, xk + 2 * pr, 16));
+        oz::split2_fast<S>(x0.x, x1.x, e, dre, 1024);
+        oz::split2_fast<S>(x0.y, x1.y, e, dim, 1024);
       }
     }
-    // B1: row n = 16 part + b' of digit t holds Y^H digit (part, b') at rows
-    // i0 .. i0 + 15, two 16-byte pieces per (t, n) from the [t][part][b'][kp] layout
-    for (int e = tid; e < S * 32 * 2; e += kUT) {
-      const int t = e / 64, n = (e / 2) & 31, kg = e & 1;
-      const uint4 v = *reinterpret_cast<const uint4 *>(
-          yh + ((size_t)(t * 2 + (n >> 4)) * kNB + (n & 15)) * kp + (i0 - k0) + 8 * kg);
-      *reinterpret_cast<uint4 *>(B1 + t * 1024 + core_off(n, 8 * kg, 16)) = v;
-    }
-    fence_proxy_async();
+    fence_proxy_async();                                // A1 writes and B1 copies -> tensor core
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const bool first = (c % kFold) == 0, fold = c % kFold == kFold - 1 || c == nch - 1;
     if (tid == 0) {
-      const uint32_t a0 = tc::smem_u32(A1), b0 = tc::smem_u32(B1);
+      const uint32_t a0 = tc::smem_u32(A1), b0 = tc::smem_u32(usm + L::kB1 + (c & 1) * S * 1024);
 #pragma unroll
       for (int s = 1; s <= S; ++s) {
         const uint64_t da = tc::smem_desc(a0 + (s - 1) * 4096, 128, 256);
@@ -195,10 +216,10 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
         tc::mma_bf16(tmem + (uint32_t)(32 * (s - 1)), da, db, tc::idesc_bf16_f32(128, 32 * (S + 1 - s)),
                      !(first && s == 1));
       }
-      tc::commit(&mma_done[b]);
+      tc::commit(&mma_done);
       if (fold) tc::commit(&acc_full);
     }
-    if (fold) {                                         // fold the groups into int64 sums
+    if (fold) {                                         // fold the groups
       const bool wf = tc::mbar_wait(&acc_full, nfold & 1, kWaitCycles);
       ++nfold;
       if (__syncthreads_or(!wf)) { ok = false; break; }
@@ -209,12 +230,16 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
 #pragma unroll
         for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
 #pragma unroll
-        for (int g = 2; g <= S + 1; ++g) {
-          uint32_t r[8];
+        for (int g = 2; g <= S + 1; g += 2) {
+          uint32_t r[8], r2[8];
           tc::ld8(tmem + lane_addr + (uint32_t)(32 * (g - 2) + 16 * half + 8 * qh), r);
+          if (g + 1 <= S + 1) tc::ld8(tmem + lane_addr + (uint32_t)(32 * (g - 1) + 16 * half + 8 * qh), r2);
           tc::ld_wait();
 #pragma unroll
-          for (int q = 0; q < 8; ++q) oz::fold_group_rn<S>(hi[q], lo[q], g, __uint_as_float(r[q]));
+          for (int q = 0; q < 8; ++q) {
+            oz::fold_group_rn<S>(hi[q], lo[q], g, __uint_as_float(r[q]));
+            if (g + 1 <= S + 1) oz::fold_group_rn<S>(hi[q], lo[q], g + 1, __uint_as_float(r2[q]));
+          }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -224,17 +249,19 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
       __syncthreads();                                  // TMEM read before the next MMAs
     }
   }
+  oz::cp_async_wait<0>();                               // no copy outlives the loop
   if (ok) {
     // P(r, n) in FP64: r = part_x * 64 + j, n = part_y * 16 + b'
-    double *P = reinterpret_cast<double *>(ops);
+    __syncthreads();
+    double *P = reinterpret_cast<double *>(usm);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) P[prow * 32 + 16 * half + q] = pacc[q];
+    for (int q = 0; q < 16; ++q) P[prow * 33 + 16 * half + q] = pacc[q];
     __syncthreads();
     // W'(b', j) = Y^H X: re = P(Re, Re) - P(Im, Im), im = P(Im, Re) + P(Re, Im)
     for (int e = tid; e < kNB * kUC; e += kUT) {
       const int bb = e / kUC, jj = e % kUC;
-      Wp[bb * kUC + jj] = make_double2(P[jj * 32 + bb] - P[(64 + jj) * 32 + 16 + bb],
-                                       P[(64 + jj) * 32 + bb] + P[jj * 32 + 16 + bb]);
+      Wp[bb * kUC + jj] = make_double2(P[jj * 33 + bb] - P[(64 + jj) * 33 + 16 + bb],
+                                       P[(64 + jj) * 33 + bb] + P[jj * 33 + 16 + bb]);
     }
     __syncthreads();
     if (tid < kUC) {
@@ -249,32 +276,35 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   }
 
   // ---- second product: X -= V W', 128 rows x 16 columns per unit
-  unsigned char *A2 = ops, *B2 = ops + L::kA2;
+  unsigned char *A2 = usm, *B2 = usm + L::kA2;
   constexpr uint32_t kDim = 16 * S;                     // TMEM column of the imaginary parts
   const int knext_row = k0 + kNB;
+  double *Xd = reinterpret_cast<double *>(X);
   int nunit = 0;
   for (int rb = 0; ok && 128 * rb < K; ++rb) {
     const int r0 = 128 * rb;                            // rows k0 + r0 .. of the block
     // A2: row rr, k < 16 Vr(rr, k), k >= 16 Vi(rr, k - 16) from the [s][part][r][16] layout
     for (int e = tid; e < S * 128 * 4; e += kUT) {
       const int s = e / 512, rr = (e >> 2) & 127, piece = e & 3;    // piece = part * 2 + kg
-      const uint4 v = *reinterpret_cast<const uint4 *>(
-          vr + ((size_t)(s * 2 + (piece >> 1)) * kp + r0 + rr) * kNB + 8 * (piece & 1));
-      *reinterpret_cast<uint4 *>(A2 + s * 8192 + core_off(rr, 8 * piece, 32)) = v;
+      oz::cp_async16(A2 + s * 8192 + core_off(rr, 8 * piece, 32),
+                     vr + ((size_t)(s * 2 + (piece >> 1)) * kp + r0 + rr) * kNB + 8 * (piece & 1), true);
     }
+    oz::cp_async_commit();
     const int er = vex[r0 + 32 * quad + lane];
     const int i = k0 + r0 + 32 * quad + lane;
+    const bool row_ok = i < rows;
+    oz::cp_async_wait<0>();
     for (int u = 0; u < kUC / 16 && 16 * u < ncols; ++u) {
       // B2: variant 0 rows jj: k < 16 W'r(k, jj), k >= 16 -W'i; variant 1: W'i, W'r
       for (int e = tid; e < 2 * 16 * 32; e += kUT) {
         const int var = e >> 9, jj = (e >> 5) & 15, k = e & 31;
-        const double2 w = Wp[(k & 15) * kUC + 16 * u + jj];
-        const double x = var == 0 ? (k < 16 ? w.x : -w.y) : (k < 16 ? w.y : w.x);
+        const double2 wv = Wp[(k & 15) * kUC + 16 * u + jj];
+        const double x = var == 0 ? (k < 16 ? wv.x : -wv.y) : (k < 16 ? wv.y : wv.x);
         oz::split_store_n(x, eW[16 * u + jj], S,
                           reinterpret_cast<unsigned short *>(B2 + var * S * 1024 + core_off(jj, k, 32)),
                           512);
       }
-      fence_proxy_async();
+      fence_proxy_async();                              // B2 writes (and the A2 copies) -> tensor core
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
@@ -295,43 +325,51 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
         }
         tc::commit(&d_full);
       }
-      const bool w = tc::mbar_wait(&d_full, nunit & 1, kWaitCycles);
+      // the X values this thread updates, loaded while the MMAs run: row i,
+      // the unit's 16 columns, real (half 0) or imaginary (half 1) part
+      double xv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int jj = 16 * u + q;
+        xv[q] = (row_ok && jj < ncols) ? Xd[2 * ((size_t)jj * rows + i) + half] : 0.0;
+      }
+      const bool wd = tc::mbar_wait(&d_full, nunit & 1, kWaitCycles);
       ++nunit;
-      if (__syncthreads_or(!w)) { ok = false; break; }
+      if (__syncthreads_or(!wd)) { ok = false; break; }
       tc::fence_after_sync();
       // epilogue: warp (quad, half) takes TMEM lanes 32 quad .. (rows) and the
-      // real (half 0) or imaginary (half 1) part of the unit's 16 columns
-      double *Xd = reinterpret_cast<double *>(X);
+      // real (half 0) or imaginary (half 1) accumulators of the 16 columns
 #pragma unroll
       for (int qh = 0; qh < 2; ++qh) {
         long long yh2[8], yl2[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) yh2[q] = yl2[q] = 0;
+        // groups two at a time: two loads in flight per wait
 #pragma unroll
-        for (int g = 2; g <= S + 1; ++g) {
-          uint32_t rv[8];
+        for (int g = 2; g <= S + 1; g += 2) {
+          uint32_t rv[8], rw[8];
           tc::ld8(tmem + lane_addr + (uint32_t)(kDim * half + 16 * (g - 2) + 8 * qh), rv);
+          if (g + 1 <= S + 1)
+            tc::ld8(tmem + lane_addr + (uint32_t)(kDim * half + 16 * (g - 1) + 8 * qh), rw);
           tc::ld_wait();
 #pragma unroll
-          for (int q = 0; q < 8; ++q) oz::fold_group<S>(yh2[q], yl2[q], g, __uint_as_float(rv[q]));
+          for (int q = 0; q < 8; ++q) {
+            oz::fold_group<S>(yh2[q], yl2[q], g, __uint_as_float(rv[q]));
+            if (g + 1 <= S + 1) oz::fold_group<S>(yh2[q], yl2[q], g + 1, __uint_as_float(rw[q]));
+          }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int jj = 16 * u + 8 * qh + q;
-          unsigned long long key = 0ull;
-          if (i < rows && jj < ncols) {
+          unsigned hk = 0u;       // the key's high word: all that the exponent needs
+          if (row_ok && jj < ncols) {
             const int e = er + eW[jj] + oz::unfold1_shift<S>();
-            double *xp = Xd + 2 * ((size_t)jj * rows + i) + half;
-            const double v = *xp - oz::scaled_to_double(oz::unfold1_int<S>(yh2[q], yl2[q]), e);
-            *xp = v;
-            if (i >= knext_row) key = oz::abs_key(v);
+            const double v = xv[8 * qh + q] - oz::scaled_to_double(oz::unfold1_int<S>(yh2[q], yl2[q]), e);
+            Xd[2 * ((size_t)jj * rows + i) + half] = v;
+            if (i >= knext_row) hk = (unsigned)(oz::abs_key(v) >> 32);
           }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, key, off);
-            key = o2 > key ? o2 : key;
-          }
-          if (lane == 0 && key != 0ull) atomicMax(&knext[jj], key);
+          hk = __reduce_max_sync(0xffffffffu, hk);
+          if (lane == 0 && hk != 0u) atomicMax(&knext[jj], hk);
         }
       }
       tc::fence_before_sync();
@@ -348,7 +386,7 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
       atomicOr(o.status, kStatTimeout);
     }
   } else if (tid < ncols) {
-    kout[tid] = knext[tid];
+    kout[tid] = (unsigned long long)knext[tid] << 32;
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -83,22 +83,23 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Waits (non-blocking tests, at most about `max_cycles` SM clocks) for the
-// phase with the given parity to complete. Returns false on timeout.
+// Waits (at most about `max_cycles` SM clocks) for the phase with the given
+// parity to complete: mbarrier.try_wait suspends the thread in hardware for a
+// bounded, implementation-defined time and returns as soon as the phase
+// completes, so no software sleep adds latency. Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long max_cycles) {
   const uint32_t a = smem_u32(mbar);
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > max_cycles) return false;
-    __nanosleep(32);
   }
 }
 

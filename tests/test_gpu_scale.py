@@ -1,4 +1,4 @@
-"""Full-scale workloads against the oracle: the 64-obstacle batch (sampled
+"""Full-scale workloads against the oracle: the 64-obstacle batch (17 sampled
 obstacles), the cup precision table (native FP64 vs 5..8 BF16 digits), and
 the split-precision apply for a large batch of waves."""
 import dataclasses
@@ -25,59 +25,54 @@ def _oracle(ob):
     return ob, coll, src, A, fac
 
 
-def _sensitivity(ob, A, fh, c_ora, rng):
-    """e_bd between the oracle solution and the oracle re-solved with every
-    modal matrix perturbed by u * max|A_n| complex Gaussian noise: how far
-    boundary data moves per unit-roundoff normwise change of the matrix."""
-    u = np.finfo(float).eps / 2
-    num = 0.0
-    for idx in range(ob.P):
-        n = idx if idx <= ob.P // 2 else ob.P - idx
-        noise = rng.standard_normal(A[n].shape) + 1j * rng.standard_normal(A[n].shape)
-        Ap = A[n] + u * np.abs(A[n]).max() * noise / math.sqrt(2)
-        QR, tau = O.householder_qr(Ap)
-        y = O.apply_qh(QR, tau, fh[:, idx, :].T)[:A.shape[2]]
-        cp = O.back_substitute(np.triu(QR[:A.shape[2], :A.shape[2]]), y)
-        num += np.linalg.norm(A[n] @ (c_ora[:, idx].T - cp)) ** 2
-    return math.sqrt(num) / np.linalg.norm(fh)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batched_residuals.json")
+# 17 of the 64 obstacles: P = 240 (17, 51, 61, 14, 35, 5), the two largest N
+# the oracle factors in seconds (5: N = 359, 59: N = 350), transmission
+# (7, 58, 50, 14, 44, 34, 35), k from 3 to 27, resolved and unresolved bodies
+BATCH_CHECKED = (15, 24, 9, 45, 17, 28, 51, 7, 58, 61, 50, 14, 44, 34, 35, 59, 5)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])
 def test_batched_64_obstacles_sampled(prec):
-    """All 64 obstacles in one plan; five of them checked against the oracle.
+    """All 64 obstacles in one plan; 17 of them checked against the oracle.
 
     The batched workload draws N, P and k independently, so some obstacles are
-    unresolved (oracle residual 1e-5..1e-4, coefficient norms up to ~1e11) and
-    their least-squares solutions are sensitive to rounding-level changes of the
-    matrix. Bar: e_bd <= max(1e-10, 1e3 * s), s = the oracle's own sensitivity
-    to a u*max|A| normwise perturbation (the fill parity bar, 1e-13*max|A|, is
-    ~1e3 u). Resolved obstacles (9, 35; residual < 1e-6) have s ~ 1e-15, so
-    the bar there is the plain 1e-10.
+    unresolved (oracle residual above 1e-6) and their least-squares solutions
+    are sensitive to rounding-level changes of the matrix. The oracle's
+    residual r and its sensitivity s (e_bd after a u*max|A| normwise
+    perturbation of every modal matrix) come from tests/golden/
+    batched_residuals.json, written by the committed oracle-only script
+    beside it. Bar: e_bd < 1e-10 where r < 1e-6; elsewhere e_bd <=
+    max(1e-10, 1e3 s) (the fill's parity bar, 1e-13 max|A|, is ~1e3 u).
     """
     from paper_1506_05083_gb300 import axi
+    golden = json.load(open(GOLDEN))
     wl = synth.config_batched()
     specs = [axi.spec_from_obstacle(ob) for ob in wl.obstacles]
     p = axi.PREC_FP64 if prec == "fp64" else axi.PREC_SPLIT_BF16
     op = axi.Operator(specs, prec=p)
     torch.cuda.synchronize()
     assert op.status() == 0
-    rng = np.random.default_rng(123)
-    for i in (9, 35, 24, 7, 15):
-        ob_in = wl.obstacles[i]
-        ob, coll, src, A, fac = _oracle(ob_in)
-        assert specs[i].q == ob.q
+    unresolved = sum(1 for g in golden.values() if g["residual"] >= 1e-6)
+    print(f"batched workload: {unresolved} of {len(golden)} obstacles unresolved (residual >= 1e-6)")
+    report = []
+    for i in BATCH_CHECKED:
+        g = golden[str(i)]
+        ob, coll, src, A, fac = _oracle(wl.obstacles[i])
+        assert specs[i].q == ob.q == g["q"]
         dirs = synth.plane_wave_directions(4, 500 + i)
         coef = op.apply(op.incident(torch.tensor(dirs, device="cuda"), obs=i), obs=i).cpu().numpy()
         fh = O.rhs_modes(O.incident_samples(ob, coll, dirs))
         c_ora = O.solve_modes(ob, fac, fh)
-        res = math.sqrt(sum(
-            np.linalg.norm(A[idx if idx <= ob.P // 2 else ob.P - idx] @ c_ora[:, idx].T
-                           - fh[:, idx].T) ** 2 for idx in range(ob.P))) / np.linalg.norm(fh)
-        s = _sensitivity(ob, A, fh, c_ora, rng)
         e = _e_bd(A, ob, coef, c_ora, fh)
-        assert e <= max(1e-10, 1e3 * s), (i, e, s)
-        if res < 1e-6:
-            assert e < 1e-10, (i, e)
+        bar = 1e-10 if g["residual"] < 1e-6 else max(1e-10, 1e3 * g["sensitivity"])
+        report.append((i, g["N"], g["P"], g["bc"], g["residual"], g["sensitivity"], e, bar))
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    for row in report:
+        print("obstacle %d N=%d P=%d bc=%d residual %.1e sensitivity %.1e e_bd %.2e bar %.1e" % row)
+    for i, N, P, bc, r, s_, e, bar in report:
+        assert e <= bar, (i, e, bar)
 
 
 def test_split_apply_many_waves():
