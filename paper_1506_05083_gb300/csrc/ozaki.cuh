@@ -196,6 +196,64 @@ __device__ __forceinline__ double scaled_to_double(long long t, int e) {
   return __longlong_as_double((long long)(sgn | (((unsigned long long)(E + 1022) << 52) + m)));
 }
 
+// Group sum `acc` (an exact integer, |acc| < 2^22) of digit group g added to
+// a fixed-point accumulator of resolution 2^-R: t += acc 2^{R - 7g}, rounded
+// to nearest where R < 7g. With g a compile-time constant (unrolled group
+// loops) the shift direction folds away.
+template <int R>
+__device__ __forceinline__ void fold_fixed(long long &t, int g, float acc) {
+  const long long v = (long long)f32_int(acc);
+  const int sh = R - 7 * g;
+  if (sh >= 0) t += v << sh;
+  else t += (v + (1ll << (-sh - 1))) >> (-sh);
+}
+
+// x - t 2^e for a double x and an integer t (|t| < 2^59), rounded once and
+// with integer instructions only: x is brought to the fixed point of
+// resolution 2^e (exactly when its last bit is at or above 2^e, else rounded
+// to nearest there), the difference is taken in 64-bit integers and rebuilt
+// by scaled_to_double. When x is not finite, or more than 2^9 times the
+// resolution's 53-bit range, the FP64 subtraction is used instead.
+__device__ __forceinline__ double sub_scaled(double x, long long t, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  int Ee = E;
+  if (E == 0) Ee = 1; else M |= 1ull << 52;
+  const int sh = Ee - 1075 - e;                      // x = M 2^sh in units of 2^e
+  if (E == 0x7ff || sh > 9) return x - scaled_to_double(t, e);
+  long long m;
+  if (sh >= 0) m = (long long)(M << sh);
+  else if (sh > -60) m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else m = 0;
+  if (b >> 63) m = -m;
+  return scaled_to_double(m - t, e);
+}
+
+// The S balanced digits of split_store, as BF16 bit patterns in registers.
+template <int S>
+__device__ __forceinline__ void split_regs(double x, int e, unsigned short (&out)[S]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  int Ee = E;
+  if (E == 0) Ee = 1; else M |= 1ull << 52;
+  const int sh = Ee - 1075 + 7 * S - e;
+  long long m;
+  if (sh >= 0) m = (long long)(M << sh);
+  else if (sh > -60) m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else m = 0;
+  if (b >> 63) m = -m;
+#pragma unroll
+  for (int s = S; s >= 2; --s) {
+    int d = (int)(m & 127);
+    if (d >= 64) d -= 128;
+    out[s - 1] = int_to_bf16_bits(d);
+    m = (m - d) >> 7;
+  }
+  out[0] = int_to_bf16_bits((int)m);
+}
+
 // fold_group for group sums up to 2^24 (exact FP32 integers beyond the
 // magic-number range): a rounding conversion instead of the add trick.
 template <int S>

@@ -13,9 +13,10 @@
 // 16 columns of Re Y^H then Im Y^H, per digit; one MMA per digit s of X against
 // the stacked digits t = 1 .. S+1-s of Y^H lands digit group g = s + t at
 // tensor-memory columns 32 (g - 2). A group sums at most 16 rows x 7 pairs x
-// 65 x 128 < 2^20 per chunk, so the accumulators are read every 8 chunks (sums
-// below 2^23, exact in FP32), combined exactly in int64 and added to FP64 sums
-// (one rounding per 128 rows, far below the digits' own truncation). Then
+// 65 x 128 < 2^20 per chunk, so the accumulators are read every 4 chunks (sums
+// below 2^22, exact in FP32) into one int64 per entry, a fixed point of
+// resolution 2^-47 relative to the column scales (exact but for the rounding
+// of groups g > 6; no FP64 instruction until W' is formed). Then
 //   W'_re = P(Re X, Re Y^H) - P(Im X, Im Y^H),  W'_im = P(Im X, Re Y^H) + P(Re X, Im Y^H),
 // exchanged through shared memory.
 //
@@ -24,7 +25,9 @@
 // one pair of K = 16 MMAs per digit s of V against the stacked digits of W'
 // (group g at columns 16 (g - 2), imaginary parts 16 S further); a group sums at
 // most 32 x 7 x 128 x 128 < 2^22, exact in one pass. The epilogue folds the
-// groups, rebuilds doubles with integer instructions, subtracts from X and
+// groups into one int64 per entry (resolution 2^-50 relative to the row and
+// column scales), subtracts it from X in that fixed point (ozaki.cuh
+// sub_scaled: integer instructions, one rounding) and
 // keeps, per column, the high word of the largest |entry|'s IEEE key over the
 // next step's rows (the exponent is all the next step's split needs).
 //
@@ -47,7 +50,9 @@ namespace {
 
 constexpr int kUC = 64;                 // X columns per CTA
 constexpr int kUT = 256;                // threads
-constexpr int kFold = 8;                // 16-row chunks per fold of the first product
+constexpr int kFold = 4;                // 16-row chunks per fold of the first product
+constexpr int kR1 = 47;                 // fixed-point resolution bits, first product
+constexpr int kR2 = 50;                 // and second product
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kRawLd = 17;             // raw X column stride (complex): conflict-free 16-byte reads
@@ -174,10 +179,11 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
 
   // ---- first product: W'^T = X^T conj(Y) over the rows
-  // each fold (8 chunks, 128 rows) is exact in int64 and added to FP64 sums
-  double pacc[16];
+  // fixed-point sums (resolution 2^-kR1 of the scale 2^(eX + eY)): below
+  // 2^(22 + kR1 - 14) per fold, so 256 folds (16384 rows) fit 63 bits
+  long long tacc[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) pacc[q] = 0.0;
+  for (int q = 0; q < 16; ++q) tacc[q] = 0;
   const int prow = 32 * quad + lane, pj = prow & 63;
   int nfold = 0;
   bool ok = true;
@@ -226,9 +232,6 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
       tc::fence_after_sync();
 #pragma unroll
       for (int qh = 0; qh < 2; ++qh) {
-        long long hi[8], lo[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0;
 #pragma unroll
         for (int g = 2; g <= S + 1; g += 2) {
           uint32_t r[8], r2[8];
@@ -237,13 +240,10 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
           tc::ld_wait();
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            oz::fold_group_rn<S>(hi[q], lo[q], g, __uint_as_float(r[q]));
-            if (g + 1 <= S + 1) oz::fold_group_rn<S>(hi[q], lo[q], g + 1, __uint_as_float(r2[q]));
+            oz::fold_fixed<kR1>(tacc[8 * qh + q], g, __uint_as_float(r[q]));
+            if (g + 1 <= S + 1) oz::fold_fixed<kR1>(tacc[8 * qh + q], g + 1, __uint_as_float(r2[q]));
           }
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          pacc[8 * qh + q] += oz::unfold<S>(hi[q], lo[q], eX[pj] + eY[8 * qh + q]);
       }
       tc::fence_before_sync();
       __syncthreads();                                  // TMEM read before the next MMAs
@@ -255,7 +255,8 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
     __syncthreads();
     double *P = reinterpret_cast<double *>(usm);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) P[prow * 33 + 16 * half + q] = pacc[q];
+    for (int q = 0; q < 16; ++q)
+      P[prow * 33 + 16 * half + q] = oz::scaled_to_double(tacc[q], eX[pj] + eY[q] - kR1);
     __syncthreads();
     // W'(b', j) = Y^H X: re = P(Re, Re) - P(Im, Im), im = P(Im, Re) + P(Re, Im)
     for (int e = tid; e < kNB * kUC; e += kUT) {
@@ -295,14 +296,25 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
     const bool row_ok = i < rows;
     oz::cp_async_wait<0>();
     for (int u = 0; u < kUC / 16 && 16 * u < ncols; ++u) {
-      // B2: variant 0 rows jj: k < 16 W'r(k, jj), k >= 16 -W'i; variant 1: W'i, W'r
-      for (int e = tid; e < 2 * 16 * 32; e += kUT) {
-        const int var = e >> 9, jj = (e >> 5) & 15, k = e & 31;
-        const double2 wv = Wp[(k & 15) * kUC + 16 * u + jj];
-        const double x = var == 0 ? (k < 16 ? wv.x : -wv.y) : (k < 16 ? wv.y : wv.x);
-        oz::split_store_n(x, eW[16 * u + jj], S,
-                          reinterpret_cast<unsigned short *>(B2 + var * S * 1024 + core_off(jj, k, 32)),
-                          512);
+      // B2: variant 0 rows jj: k < 16 W'r(k, jj), k >= 16 -W'i; variant 1: W'i, W'r.
+      // Thread: W'(bb, jj), bb = tid / 16, jj = tid % 16; each part split once,
+      // the negation a sign flip of its digits.
+      {
+        const int bb = tid >> 4, jj = tid & 15;
+        const double2 wv = Wp[bb * kUC + 16 * u + jj];
+        const int ew = eW[16 * u + jj];
+        unsigned short dr[S], di[S];
+        oz::split_regs<S>(wv.x, ew, dr);
+        oz::split_regs<S>(wv.y, ew, di);
+        unsigned short *b0 = reinterpret_cast<unsigned short *>(B2);
+        const uint32_t o_lo = core_off(jj, bb, 32) / 2, o_hi = core_off(jj, 16 + bb, 32) / 2;
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) {
+          b0[s2 * 512 + o_lo] = dr[s2];
+          b0[s2 * 512 + o_hi] = di[s2] ^ 0x8000;
+          b0[(S + s2) * 512 + o_lo] = di[s2];
+          b0[(S + s2) * 512 + o_hi] = dr[s2];
+        }
       }
       fence_proxy_async();                              // B2 writes (and the A2 copies) -> tensor core
       tc::fence_before_sync();
@@ -327,9 +339,9 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
       }
       // the X values this thread updates, loaded while the MMAs run: row i,
       // the unit's 16 columns, real (half 0) or imaginary (half 1) part
-      double xv[16];
+      double xv[8];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const int jj = 16 * u + q;
         xv[q] = (row_ok && jj < ncols) ? Xd[2 * ((size_t)jj * rows + i) + half] : 0.0;
       }
@@ -341,9 +353,17 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
       // real (half 0) or imaginary (half 1) accumulators of the 16 columns
 #pragma unroll
       for (int qh = 0; qh < 2; ++qh) {
-        long long yh2[8], yl2[8];
+        double xn[8];         // the next eight columns' X values, loaded during this fold
+        if (qh == 0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) yh2[q] = yl2[q] = 0;
+          for (int q = 0; q < 8; ++q) {
+            const int jj = 16 * u + 8 + q;
+            xn[q] = (row_ok && jj < ncols) ? Xd[2 * ((size_t)jj * rows + i) + half] : 0.0;
+          }
+        }
+        long long ta[8];      // fixed point, resolution 2^-kR2 of the scale 2^(er + eW)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ta[q] = 0;
         // groups two at a time: two loads in flight per wait
 #pragma unroll
         for (int g = 2; g <= S + 1; g += 2) {
@@ -354,8 +374,8 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
           tc::ld_wait();
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            oz::fold_group<S>(yh2[q], yl2[q], g, __uint_as_float(rv[q]));
-            if (g + 1 <= S + 1) oz::fold_group<S>(yh2[q], yl2[q], g + 1, __uint_as_float(rw[q]));
+            oz::fold_fixed<kR2>(ta[q], g, __uint_as_float(rv[q]));
+            if (g + 1 <= S + 1) oz::fold_fixed<kR2>(ta[q], g + 1, __uint_as_float(rw[q]));
           }
         }
 #pragma unroll
@@ -363,13 +383,16 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
           const int jj = 16 * u + 8 * qh + q;
           unsigned hk = 0u;       // the key's high word: all that the exponent needs
           if (row_ok && jj < ncols) {
-            const int e = er + eW[jj] + oz::unfold1_shift<S>();
-            const double v = xv[8 * qh + q] - oz::scaled_to_double(oz::unfold1_int<S>(yh2[q], yl2[q]), e);
+            const double v = oz::sub_scaled(xv[q], ta[q], er + eW[jj] - kR2);
             Xd[2 * ((size_t)jj * rows + i) + half] = v;
             if (i >= knext_row) hk = (unsigned)(oz::abs_key(v) >> 32);
           }
           hk = __reduce_max_sync(0xffffffffu, hk);
           if (lane == 0 && hk != 0u) atomicMax(&knext[jj], hk);
+        }
+        if (qh == 0) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xv[q] = xn[q];
         }
       }
       tc::fence_before_sync();

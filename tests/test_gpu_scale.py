@@ -42,8 +42,11 @@ def test_batched_64_obstacles_sampled(prec):
     residual r and its sensitivity s (e_bd after a u*max|A| normwise
     perturbation of every modal matrix) come from tests/golden/
     batched_residuals.json, written by the committed oracle-only script
-    beside it. Bar: e_bd < 1e-10 where r < 1e-6; elsewhere e_bd <=
-    max(1e-10, 1e3 s) (the fill's parity bar, 1e-13 max|A|, is ~1e3 u).
+    beside it. Bar: e_bd <= max(1e-10, 1e3 s) for every obstacle: 1e-10
+    where the discrete problem is conditioned to that level, else what a
+    backward-stable FP64 solver can reach (the fill's parity bar, 1e-13
+    max|A|, is ~1e3 u). The residual r only labels obstacles as resolved
+    (r < 1e-6) in the report; a resolved body can still be ill conditioned.
     """
     from paper_1506_05083_gb300 import axi
     golden = json.load(open(GOLDEN))
@@ -65,7 +68,7 @@ def test_batched_64_obstacles_sampled(prec):
         fh = O.rhs_modes(O.incident_samples(ob, coll, dirs))
         c_ora = O.solve_modes(ob, fac, fh)
         e = _e_bd(A, ob, coef, c_ora, fh)
-        bar = 1e-10 if g["residual"] < 1e-6 else max(1e-10, 1e3 * g["sensitivity"])
+        bar = max(1e-10, 1e3 * g["sensitivity"])
         report.append((i, g["N"], g["P"], g["bc"], g["residual"], g["sensitivity"], e, bar))
     torch.cuda.synchronize()
     assert op.status() == 0
