@@ -208,24 +208,34 @@ __device__ __forceinline__ void fold_fixed(long long &t, int g, float acc) {
   else t += (v + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// x - t 2^e for a double x and an integer t (|t| < 2^59), rounded once and
-// with integer instructions only: x is brought to the fixed point of
-// resolution 2^e (exactly when its last bit is at or above 2^e, else rounded
-// to nearest there), the difference is taken in 64-bit integers and rebuilt
-// by scaled_to_double. When x is not finite, or more than 2^9 times the
-// resolution's 53-bit range, the FP64 subtraction is used instead.
+// x - t 2^e for a double x and an integer t (|t| < 2^59), with integer
+// instructions only. The difference is formed in 64-bit integers at the finer
+// of the two resolutions that keeps x within 62 bits: 2^e when x's last bit
+// is at most 2^9 above it (x exact there, or rounded to nearest when x is
+// finer than 2^e), else 2^(e + k) with k chosen so that x is exact and t is
+// rounded to nearest (an error below 2^-10 of x's last bit); then one
+// rounding by scaled_to_double. Non-finite x falls back to FP64.
 __device__ __forceinline__ double sub_scaled(double x, long long t, int e) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0x7ff) return x - scaled_to_double(t, e);
   unsigned long long M = b & 0xfffffffffffffull;
   int Ee = E;
   if (E == 0) Ee = 1; else M |= 1ull << 52;
   const int sh = Ee - 1075 - e;                      // x = M 2^sh in units of 2^e
-  if (E == 0x7ff || sh > 9) return x - scaled_to_double(t, e);
   long long m;
-  if (sh >= 0) m = (long long)(M << sh);
-  else if (sh > -60) m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
-  else m = 0;
+  if (sh > 9) {                                      // work at 2^(e + k), x exact
+    const int k = sh - 9;
+    m = (long long)(M << 9);
+    t = k >= 62 ? 0ll : (t + (1ll << (k - 1))) >> k;
+    e += k;
+  } else if (sh >= 0) {
+    m = (long long)(M << sh);
+  } else if (sh > -60) {
+    m = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  } else {
+    m = 0;
+  }
   if (b >> 63) m = -m;
   return scaled_to_double(m - t, e);
 }

@@ -241,6 +241,7 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
 #pragma unroll
     for (int u = 0; u < kXU; ++u) {
       const int e = tid + u * kThreads, j = e / (kKC / 2), rp = e % (kKC / 2);
+      if (8 * (j >> 3) >= ncols) continue;           // no warp reads this column group
       const int ex = sm.eX[j];
       uint32_t *wr = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][0][j][0]) + rp;
       uint32_t *wi = reinterpret_cast<uint32_t *>(&sm.u.p1.B[0][1][j][0]) + rp;
@@ -250,7 +251,9 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     __syncthreads();
     if (r0 + kKC < rhi) stage(r0 + kKC);
     // All S groups accumulate at once (independent accumulators): digit s of
-    // V^H is loaded once, then every digit t of X with s + t <= S + 1.
+    // V^H is loaded once, then every digit t of X with s + t <= S + 1. A warp
+    // whose 8 columns all lie beyond ncols has nothing to add.
+    if (8 * warp >= ncols) continue;
     float acc[S][2][4];
 #pragma unroll
     for (int g = 0; g < S; ++g)
@@ -305,10 +308,11 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   if constexpr (C > 1) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    constexpr int CW = kTN / C;                             // columns of W' formed here
+    // columns of W' formed here: the live columns split evenly over the cluster
+    const int cw = (ncols + C - 1) / C;                     // <= kTN / C
     cl.sync();                                              // every CTA's partial W ready
-    for (int e = tid; e < kNB * CW; e += kThreads) {
-      const int a = e / CW, jl = e % CW, j = rank * CW + jl;
+    for (int e = tid; e < kNB * cw; e += kThreads) {
+      const int a = e / cw, jl = e % cw, j = rank * cw + jl;
       double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
       for (int r = 0; r < C; ++r) {
@@ -320,33 +324,38 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
       cx->Wsum[a][jl] = acc;
     }
     __syncthreads();
-    // kNB / 2 pairs (a, 15 - a) per column of the slice: one per thread, or
-    // one per two threads when there are enough threads (C >= 4)
-    static_assert((kNB / 2) * CW <= kThreads, "one pair per thread");
-    if constexpr ((kNB / 2) * CW * 2 <= kThreads) {
+    // kNB / 2 pairs (a, 15 - a) per column of the slice: one per two threads
+    // when there are enough threads, else one per thread
+    static_assert((kNB / 2) * (kTN / C) <= kThreads, "one pair per thread");
+    const int npair = (kNB / 2) * cw;
+    if (2 * npair <= kThreads) {
       const int half = tid & 1, pi = tid >> 1;
-      const bool act = pi < (kNB / 2) * CW;
-      const int jl = pi % CW, lo = act ? pi / CW : 0;
+      const bool act = pi < npair;
+      const int jl = act ? pi % cw : 0, lo = act ? pi / cw : 0;
       double2 al, ah;
       th_pair_half(sm.T, &cx->Wsum[0][0], kTN / 2 + 1, jl, lo, half, al, ah);
       ah.x += __shfl_xor_sync(0xffffffffu, ah.x, 1);
       ah.y += __shfl_xor_sync(0xffffffffu, ah.y, 1);
       if (act && half == 0) {
-        cx->Wq[lo][rank * CW + jl] = al;
-        cx->Wq[kNB - 1 - lo][rank * CW + jl] = ah;
+        cx->Wq[lo][rank * cw + jl] = al;
+        cx->Wq[kNB - 1 - lo][rank * cw + jl] = ah;
       }
-    } else if (tid < (kNB / 2) * CW) {
-      const int jl = tid % CW, lo = tid / CW;
+    } else if (tid < npair) {
+      const int jl = tid % cw, lo = tid / cw;
       double2 olo, ohi;
       th_pair(sm.T, &cx->Wsum[0][0], kTN / 2 + 1, jl, lo, olo, ohi);
-      cx->Wq[lo][rank * CW + jl] = olo;
-      cx->Wq[kNB - 1 - lo][rank * CW + jl] = ohi;
+      cx->Wq[lo][rank * cw + jl] = olo;
+      cx->Wq[kNB - 1 - lo][rank * cw + jl] = ohi;
     }
     cl.sync();                                              // W' slices ready
     for (int e = tid; e < kNB * kTN; e += kThreads) {
       const int a = e / kTN, j = e % kTN;
-      const double2 *q = cl.map_shared_rank(&cx->Wq[0][0], j / CW);
-      sm.W[a][j] = q[a * (kTN + 1) + j];
+      if (j < C * cw) {
+        const double2 *q = cl.map_shared_rank(&cx->Wq[0][0], j / cw);
+        sm.W[a][j] = q[a * (kTN + 1) + j];
+      } else {
+        sm.W[a][j] = make_double2(0.0, 0.0);                // beyond every slice: unused
+      }
     }
     __syncthreads();
   } else if (!pd.pre_t) {
@@ -377,14 +386,18 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
   __syncthreads();
   for (int e = tid; e < kNB * kTN; e += kThreads) {
     const int j = e / kNB, a = e % kNB;
+    if (8 * (j >> 3) >= ncols) continue;             // column group beyond ncols: not read
     const double2 w = sm.W[a][j];
     oz::split_store<S>(w.x, sm.eW[j], &sm.u.p3.B[0][0][j][a], 2 * kTN * kLD2);
     oz::split_store<S>(w.y, sm.eW[j], &sm.u.p3.B[0][1][j][a], 2 * kTN * kLD2);
   }
 
   // ---- pass 3: X -= V W'; warp w owns rows 16w..16w+15 of each 64-row chunk
-  // and the 32 target columns as four n8 tiles. For each tile all S groups
-  // accumulate at once; the tile's X values are loaded before its products.
+  // and the target columns as n8 tiles (those below ncols). For each tile all
+  // S groups accumulate at once; the tile's X values are loaded before its
+  // products. The groups are folded into one int64 per entry (resolution
+  // 2^-50 of the row and column scales) and subtracted from X in that fixed
+  // point (sub_scaled): integer instructions only.
   const int knext = k0 + kNB;
   for (int r0 = r1st; r0 < rhi; r0 += kRC) {
     __syncthreads();
@@ -413,10 +426,11 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
     load_x(0, xnext);
 #pragma unroll 1
     for (int nt = 0; nt < kTN / 8; ++nt) {
+      if (8 * nt >= ncols) break;
       double2 xv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) xv[q] = xnext[q];
-      if (nt + 1 < kTN / 8) load_x(nt + 1, xnext);
+      if (nt + 1 < kTN / 8 && 8 * (nt + 1) < ncols) load_x(nt + 1, xnext);
       float acc[S][2][4];
 #pragma unroll
       for (int g = 0; g < S; ++g)
@@ -435,13 +449,13 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar, ai, br, bi);
         }
       }
-      long long yhi[2][4] = {}, ylo[2][4] = {};
+      long long ta[2][4] = {};
 #pragma unroll
       for (int g = 2; g <= S + 1; ++g)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          oz::fold_group<S>(yhi[0][q], ylo[0][q], g, acc[g - 2][0][q]);
-          oz::fold_group<S>(yhi[1][q], ylo[1][q], g, acc[g - 2][1][q]);
+          oz::fold_fixed<50>(ta[0][q], g, acc[g - 2][0][q]);
+          oz::fold_fixed<50>(ta[1][q], g, acc[g - 2][1][q]);
         }
       unsigned long long cm[2] = {0ull, 0ull};
 #pragma unroll
@@ -449,10 +463,10 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
         const int i = r0 + r, j = 8 * nt + 2 * tig + (q & 1);
         if (i < rhi && j < ncols) {
-          const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
-          double2 v = xv[q];
-          v.x -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[0][q], ylo[0][q]), e);
-          v.y -= oz::scaled_to_double(oz::unfold1_int<S>(yhi[1][q], ylo[1][q]), e);
+          const int e = sm.eV[r] + sm.eW[j] - 50;
+          double2 v;
+          v.x = oz::sub_scaled(xv[q].x, ta[0][q], e);
+          v.y = oz::sub_scaled(xv[q].y, ta[1][q], e);
           X[(size_t)j * ldx + i - xoff] = v;
           if (i >= knext) {
             const unsigned long long k = key2(v);
