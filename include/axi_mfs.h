@@ -187,7 +187,8 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   per SM) for the trailing updates of split plans, 2 the
  *                   tcgen05 trailing update (tensor-memory accumulators, 64
  *                   columns per CTA; split plans whose next-panel update
- *                   is in digits, else as 0);
+ *                   is in digits, else as 0), 3 the same with one CTA per
+ *                   SM (room beside it for a panel or next-panel CTA);
  *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA;
  *   "crit_stream"   0 the panels and next-panel updates on `stream`, 1 on
  *                   a stream of the operator with the device's highest

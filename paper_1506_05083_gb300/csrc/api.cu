@@ -303,7 +303,7 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
       if (iv != 0 && iv != 1 && iv != 2 && iv != 4) return false;
       t.panel_cluster = iv;
     } else if (key == "rest_grid") {
-      if (iv < 0 || iv > 2) return false;
+      if (iv < 0 || iv > 3) return false;
       t.rest_grid = iv;
     } else if (key == "crit_stream") {
       if (iv < 0 || iv > 1) return false;
@@ -1010,10 +1010,10 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
-      for (int rg : {0, 1, 2})
+      for (int rg : {0, 1, 2, 3})
         for (int pt : {128, 256})
         for (int cs : {0, 1}) {
-        if (rg == 2 && nu != 2) continue;             // the tcgen05 update reads Y^H digits
+        if (rg >= 2 && nu != 2) continue;             // the tcgen05 update reads Y^H digits
         p->tune.crit_stream = cs;
 
         p->tune.next_update = nu;

@@ -21,7 +21,8 @@ struct Tuning {
   int next_update = 0;    // 0 auto, 1 native FP64, 2 split digits (split plans)
   int panel_cluster = 0;  // 0 auto (by the number of tasks), else 1, 2 or 4 CTAs per mode
   int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM),
-                          // 2 tcgen05 kernel (split plans whose update reads Y^H digits; else as 0)
+                          // 2 tcgen05 kernel (split plans whose update reads Y^H digits; else as 0),
+                          // 3 the same with one CTA per SM (room for a critical-path CTA beside it)
   int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
   int crit_stream = 0;    // 0 the panel chain on the caller's stream, 1 on a stream of the
                           // operator with the device's highest priority
@@ -209,7 +210,8 @@ cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
 // The trailing update of split plans on tcgen05 (W' = Y^H X, X -= V W'),
 // 64 columns per CTA; needs the Y^H digits.
 cudaError_t launch_qr_update_tc(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                                int ntasks, int p, int slices, int max_rest_cols, cudaStream_t st);
+                                int ntasks, int p, int slices, int max_rest_cols, bool one_per_sm,
+                                cudaStream_t st);
 // Y = V T of panel p and the digits of Y^H (split plans, after launch_vdigits).
 cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int kp_max, cudaStream_t st);

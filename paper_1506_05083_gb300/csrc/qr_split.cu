@@ -164,7 +164,11 @@ __device__ __forceinline__ void th_pair_half(const double2 (*T)[kNB + 1], const 
 // CTA is one of a cluster of C that splits the rows: their partial V^H X are
 // summed through distributed shared memory, CTA r forms W' = T^H W for
 // columns [r kTN/C, (r+1) kTN/C), and every CTA gathers the whole W'.
-template <int S, int C = 1>
+// FE: the pass-3 epilogue folds into one fixed-point int64 and subtracts in
+// integers (sub_scaled); otherwise two int64 folds, one integer-built double
+// and an FP64 subtraction (measured faster in the apply's Q^H, where the
+// cluster's warps interleave with the FP64 T^H W of other CTAs).
+template <int S, int C = 1, bool FE = true>
 __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0,
                                           const double2 *__restrict__ Tg,
                                           double2 *__restrict__ X, int ldx, int ncols,
@@ -449,13 +453,18 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
           oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar, ai, br, bi);
         }
       }
-      long long ta[2][4] = {};
+      long long ta[2][4] = {}, tb[2][4] = {};
 #pragma unroll
       for (int g = 2; g <= S + 1; ++g)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          oz::fold_fixed<50>(ta[0][q], g, acc[g - 2][0][q]);
-          oz::fold_fixed<50>(ta[1][q], g, acc[g - 2][1][q]);
+          if constexpr (FE) {
+            oz::fold_fixed<50>(ta[0][q], g, acc[g - 2][0][q]);
+            oz::fold_fixed<50>(ta[1][q], g, acc[g - 2][1][q]);
+          } else {
+            oz::fold_group<S>(ta[0][q], tb[0][q], g, acc[g - 2][0][q]);
+            oz::fold_group<S>(ta[1][q], tb[1][q], g, acc[g - 2][1][q]);
+          }
         }
       unsigned long long cm[2] = {0ull, 0ull};
 #pragma unroll
@@ -463,10 +472,16 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         const int r = 16 * warp + grp + (q >= 2 ? 8 : 0);
         const int i = r0 + r, j = 8 * nt + 2 * tig + (q & 1);
         if (i < rhi && j < ncols) {
-          const int e = sm.eV[r] + sm.eW[j] - 50;
           double2 v;
-          v.x = oz::sub_scaled(xv[q].x, ta[0][q], e);
-          v.y = oz::sub_scaled(xv[q].y, ta[1][q], e);
+          if constexpr (FE) {
+            const int e = sm.eV[r] + sm.eW[j] - 50;
+            v.x = oz::sub_scaled(xv[q].x, ta[0][q], e);
+            v.y = oz::sub_scaled(xv[q].y, ta[1][q], e);
+          } else {
+            const int e = sm.eV[r] + sm.eW[j] + oz::unfold1_shift<S>();
+            v.x = xv[q].x - oz::scaled_to_double(oz::unfold1_int<S>(ta[0][q], tb[0][q]), e);
+            v.y = xv[q].y - oz::scaled_to_double(oz::unfold1_int<S>(ta[1][q], tb[1][q]), e);
+          }
           X[(size_t)j * ldx + i - xoff] = v;
           if (i >= knext) {
             const unsigned long long k = key2(v);
@@ -617,9 +632,9 @@ apply_qh_cluster_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, 
     if (p + 1 < o.npanels)                              // the next step's digits into L2
       prefetch_panel_l2<S>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p + 1), (p + 1) * kNB, rlo,
                            rhi, Tg + kNB * kNB);
-    oz_block_reflector_update<S, C>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p), o.rows,
-                                    p * kNB, Tg, Xd, o.rows, ncols, nullptr, p > 0, nullptr, sm, cx,
-                                    rlo, rhi);
+    oz_block_reflector_update<S, C, false>(panel_digits<S>(dig, dex, o.kp, d, o.npanels, p),
+                                           o.rows, p * kNB, Tg, Xd, o.rows, ncols, nullptr, p > 0,
+                                           nullptr, sm, cx, rlo, rhi);
   }
   cg::this_cluster().sync();                            // no CTA leaves while W' is being read
 }

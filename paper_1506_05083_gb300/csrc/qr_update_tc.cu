@@ -417,10 +417,16 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// one_per_sm: pad the dynamic shared memory so that a second update CTA does
+// not fit on an SM, leaving registers and shared memory for a panel or a
+// next-panel update CTA of the critical path beside it.
+constexpr size_t kOnePerSmSmem = 120 * 1024;
+
 template <int S>
 cudaError_t launch_tc_s(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                        int ntasks, int p, int ntiles, cudaStream_t st) {
-  const size_t smem = TcLayout<S>::kTotal;
+                        int ntasks, int p, int ntiles, bool one_per_sm, cudaStream_t st) {
+  const size_t smem = one_per_sm && TcLayout<S>::kTotal < kOnePerSmSmem ? kOnePerSmSmem
+                                                                        : TcLayout<S>::kTotal;
   static size_t granted = 0;
   cudaError_t e = ensure_dynamic_smem(qr_update_tc_kernel<S>, smem, granted);
   if (e != cudaSuccess) return e;
@@ -434,15 +440,16 @@ cudaError_t launch_tc_s(const ObsDev *d_obs, const int *d_task_obs, const int *d
 }  // namespace
 
 cudaError_t launch_qr_update_tc(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                                int ntasks, int p, int slices, int max_rest_cols, cudaStream_t st) {
+                                int ntasks, int p, int slices, int max_rest_cols, bool one_per_sm,
+                                cudaStream_t st) {
   if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
   const int ntiles = (max_rest_cols + kUC - 1) / kUC;
   switch (slices) {
-    case 4: return launch_tc_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
-    case 5: return launch_tc_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
-    case 6: return launch_tc_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
-    case 7: return launch_tc_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
-    case 8: return launch_tc_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, st);
+    case 4: return launch_tc_s<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, one_per_sm, st);
+    case 5: return launch_tc_s<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, one_per_sm, st);
+    case 6: return launch_tc_s<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, one_per_sm, st);
+    case 7: return launch_tc_s<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, one_per_sm, st);
+    case 8: return launch_tc_s<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, ntiles, one_per_sm, st);
     default: return cudaErrorInvalidValue;
   }
 }
