@@ -192,14 +192,21 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA;
  *   "crit_stream"   0 the panels and next-panel updates on `stream`, 1 on
  *                   a stream of the operator with the device's highest
- *                   priority (forked from and joined back into `stream`).
+ *                   priority (forked from and joined back into `stream`);
+ *   "fill_chunk_mb" split plans: 0 the plan's fill chunk (up to 512 MB of
+ *                   sample digits per chunk of ring pairs), else at most
+ *                   this many MB per chunk (0..4096), so that a chunk's
+ *                   digits stay in L2 between the sample and transform
+ *                   kernels.
  * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
  * keys kept; AXI_ERR_ARG on malformed input or values out of range);
  * axi_plan_get_tuning writes the current one into buf[n] (AXI_ERR_ARG if it
  * does not fit). axi_operator_autotune times every candidate schedule with
  * CUDA events on `stream` (one warm-up and `reps` builds each, reps in
- * 1..100; it synchronises the stream, so not under stream capture), keeps the
- * fastest in the plan, rebuilds the operator with it and, when json_out is
+ * 1..100; it synchronises the stream, so not under stream capture): first
+ * the panel chain's choices together, then, for split plans, the fill chunk
+ * with the best of those. It keeps the fastest in the plan, rebuilds the
+ * operator with it and, when json_out is
  * not NULL, writes the choice with its build time ("build_ms") and the number
  * of candidates. Caching the result is the caller's: pass it back with
  * axi_plan_set_tuning before axi_build_operator.

@@ -305,6 +305,9 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
     } else if (key == "rest_grid") {
       if (iv < 0 || iv > 3) return false;
       t.rest_grid = iv;
+    } else if (key == "fill_chunk_mb") {
+      if (iv < 0 || iv > 4096) return false;
+      t.fill_chunk_mb = iv;
     } else if (key == "crit_stream") {
       if (iv < 0 || iv > 1) return false;
       t.crit_stream = iv;
@@ -319,8 +322,9 @@ std::string tuning_json(const axi::Tuning &t) {
   char buf[200];
   std::snprintf(buf, sizeof(buf),
                 "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d, "
-                "\"crit_stream\": %d}",
-                t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream);
+                "\"crit_stream\": %d, \"fill_chunk_mb\": %d}",
+                t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream,
+                t.fill_chunk_mb);
   return buf;
 }
 
@@ -641,7 +645,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
       continue;
     }
     const int pid = axi::prof_begin(AXI_KERNEL_FILL, st);
-    e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st);
+    e = axi::launch_fill(op->d_obs, d, (int)i, d.A, d.rows, d.cols, st, p->tune.fill_chunk_mb);
     axi::prof_end(pid, st);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
   }
@@ -869,7 +873,8 @@ axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, 
   if (!op || !d_out || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;
   return cuda_status(axi::launch_fill(op->d_obs, d, obs, reinterpret_cast<double2 *>(d_out), d.rows,
-                                      d.cols, static_cast<cudaStream_t>(stream)));
+                                      d.cols, static_cast<cudaStream_t>(stream),
+                                      op->plan->tune.fill_chunk_mb));
 }
 
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
@@ -1006,38 +1011,62 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   axi::Tuning best = keep;
   double best_ms = 1e300;
   int tried = 0;
+  // one warm-up build of the plan's current tuning, then `reps` timed builds
+  auto time_it = [&](double &ms_out) -> axi_status {
+    axi_status s = run_build(op, st);
+    if (s != AXI_OK) return s;
+    if (cudaEventRecord(a, st) != cudaSuccess) return AXI_ERR_CUDA;
+    for (int r = 0; r < reps && s == AXI_OK; ++r) s = run_build(op, st);
+    if (s != AXI_OK) return s;
+    float ms = 0.0f;
+    if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+      return AXI_ERR_CUDA;
+    ms_out = ms / reps;
+    ++tried;
+    return AXI_OK;
+  };
   axi_status s = AXI_OK;
+  // the panel chain's schedule first
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
       for (int rg : {0, 1, 2, 3})
         for (int pt : {128, 256})
-        for (int cs : {0, 1}) {
-        if (rg >= 2 && nu != 2) continue;             // the tcgen05 update reads Y^H digits
-        p->tune.crit_stream = cs;
-
-        p->tune.next_update = nu;
-        p->tune.panel_cluster = pc;
-        p->tune.rest_grid = rg;
-        p->tune.panel_threads = pt;
-        s = run_build(op, st);                           // warm-up of this schedule
-        if (s != AXI_OK) break;
-        if (cudaEventRecord(a, st) != cudaSuccess) { s = AXI_ERR_CUDA; break; }
-        for (int r = 0; r < reps && s == AXI_OK; ++r) s = run_build(op, st);
-        if (s != AXI_OK) break;
-        float ms = 0.0f;
-        if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-          s = AXI_ERR_CUDA;
-          break;
-        }
-        ++tried;
-        if (ms / reps < best_ms) {
-          best_ms = ms / reps;
-          best = p->tune;
-        }
-      }
+          for (int cs : {0, 1}) {
+            if (rg >= 2 && nu != 2) continue;         // the tcgen05 update reads Y^H digits
+            p->tune = keep;
+            p->tune.next_update = nu;
+            p->tune.panel_cluster = pc;
+            p->tune.rest_grid = rg;
+            p->tune.panel_threads = pt;
+            p->tune.crit_stream = cs;
+            double ms = 0.0;
+            s = time_it(ms);
+            if (s != AXI_OK) break;
+            if (ms < best_ms) {
+              best_ms = ms;
+              best = p->tune;
+            }
+          }
     if (s != AXI_OK) break;
+  }
+  // then the split fill's chunk size with that schedule (smaller chunks keep
+  // the sample digits in L2 between the two fill kernels)
+  if (s == AXI_OK && split && p->obs[0].dev.fill_cdig != nullptr) {
+    const axi::Tuning base = best;
+    for (int fc : {0, 256, 128, 96, 64}) {
+      if (fc == base.fill_chunk_mb) continue;
+      p->tune = base;
+      p->tune.fill_chunk_mb = fc;
+      double ms = 0.0;
+      s = time_it(ms);
+      if (s != AXI_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = p->tune;
+      }
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

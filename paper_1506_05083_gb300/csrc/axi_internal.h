@@ -26,6 +26,8 @@ struct Tuning {
   int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
   int crit_stream = 0;    // 0 the panel chain on the caller's stream, 1 on a stream of the
                           // operator with the device's highest priority
+  int fill_chunk_mb = 0;  // split fill: 0 the plan's chunk (up to 512 MB of sample digits),
+                          // else at most this many MB per chunk (small chunks stay in L2)
 };
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
@@ -177,11 +179,13 @@ inline cudaError_t ensure_dynamic_smem(Kernel *kernel, size_t bytes, size_t &gra
 
 // Launch wrappers (each returns the cudaError_t of its launch).
 // fill_mma.cu: the split-precision transform of the fill
+// chunk_mb > 0 caps the ring pairs per chunk at that many MB of sample digits
+// (Tuning::fill_chunk_mb; the plan's chunk otherwise).
 cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out,
-                            int ld_rows, int ld_cols, cudaStream_t st);
+                            int ld_rows, int ld_cols, int chunk_mb, cudaStream_t st);
 size_t fill_gemm_smem(int MR);
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
-                        double2 *out, int ld_rows, int ld_cols, cudaStream_t st);
+                        double2 *out, int ld_rows, int ld_cols, cudaStream_t st, int chunk_mb = 0);
 // Sets *digits_written when the panel kernel also wrote the exponents of the
 // panel's reflector columns, so that launch_vdigits can write the digits
 // (split plans, panels in shared memory).

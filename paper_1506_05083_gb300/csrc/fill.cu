@@ -227,10 +227,10 @@ fill_fft_kernel(const ObsDev *__restrict__ obs_arr, int oi, double2 *__restrict_
 }  // namespace
 
 cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out, int ld_rows,
-                        int ld_cols, cudaStream_t st) {
+                        int ld_cols, cudaStream_t st, int chunk_mb) {
   // split-precision plans: samples in FP64, the transform on tensor cores
   if (h.slices > 0 && h.fill_cdig != nullptr)
-    return launch_fill_mma(d_obs, h, oi, out, ld_rows, ld_cols, st);
+    return launch_fill_mma(d_obs, h, oi, out, ld_rows, ld_cols, chunk_mb, st);
   if (h.fft_nst_q > 0) {
     const int nw = h.q <= 512 ? 8 : 4;                      // pairs (warps) per CTA
     const size_t smem = sizeof(double2) * (h.q + (h.q + 1) / 2 + (size_t)nw * h.q);

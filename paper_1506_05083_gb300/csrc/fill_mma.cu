@@ -570,9 +570,17 @@ size_t fill_gemm_smem(int MR) {
 }
 
 cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double2 *out,
-                            int ld_rows, int ld_cols, cudaStream_t st) {
+                            int ld_rows, int ld_cols, int chunk_mb, cudaStream_t st) {
   const int kinds = h.bc == AXI_BC_TRANSMISSION ? 4 : 1;
   const int npairs_total = h.M * h.N;
+  // ring pairs per chunk: the plan's (its scratch holds that many), or fewer
+  // so that one chunk's sample digits stay in L2 between the two kernels
+  int chunk = h.fill_chunk_pairs;
+  if (chunk_mb > 0) {
+    const size_t per_pair = (size_t)2 * 2 * kinds * kFillDigits * h.fill_Lp * sizeof(unsigned short);
+    const size_t want = ((size_t)chunk_mb << 20) / per_pair;
+    chunk = (int)std::max<size_t>(8, std::min<size_t>((size_t)chunk, want));
+  }
   const int NT = fill_gemm_cols(h.fill_MR);
   const size_t smemA = sizeof(double2) * ((size_t)trig::kRingTab + (size_t)kFWarpsA * (h.q / 2 + 1));
   const bool tc = h.fill_tc != 0;
@@ -586,8 +594,8 @@ cudaError_t launch_fill_mma(const ObsDev *d_obs, const ObsDev &h, int oi, double
           : two ? ensure_dynamic_smem(fill_gemm_tc_kernel<4, 2>, smemB, grantedT2)
                 : ensure_dynamic_smem(fill_gemm_tc_kernel<4, 1>, smemB, grantedT1);
   if (e != cudaSuccess) return e;
-  for (int pair0 = 0; pair0 < npairs_total; pair0 += h.fill_chunk_pairs) {
-    const int np = min(h.fill_chunk_pairs, npairs_total - pair0);
+  for (int pair0 = 0; pair0 < npairs_total; pair0 += chunk) {
+    const int np = min(chunk, npairs_total - pair0);
     fill_samples_kernel<<<dim3((np + kFWarpsA - 1) / kFWarpsA, kinds), 32 * kFWarpsA, smemA, st>>>(
         d_obs, oi, pair0, np, kinds, h.fill_gdig, h.fill_gex);
     e = cudaGetLastError();

@@ -143,3 +143,26 @@ def test_split_tc_update_parity(name):
         assert _e_bd(A, ob, coefs[rg], c_ora, fh) < 1e-10
         assert _e_bd(A, ob, coefs[rg], coefs[0], fh) < 1e-10
     assert np.array_equal(coefs[2], coefs[3])
+
+
+def test_split_fill_chunking_is_exact():
+    """The fill's chunk of ring pairs (tuning fill_chunk_mb) only changes how
+    many pairs each pair of fill launches covers: the modal matrices, and so
+    the factors and coefficients, are bit-identical for every chunk size,
+    including chunks far smaller than one launch's natural size."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case("smooth")
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    prec = axi.PREC_SPLIT_BF16 | (7 << 8)
+    dirs = torch.tensor(synth.plane_wave_directions(wl.n_waves, wl.wave_seed), device="cuda")
+    out = {}
+    for mb in (0, 8, 1):
+        op = axi.Operator([spec], prec=prec, tuning='{"fill_chunk_mb": %d}' % mb)
+        out[mb] = (op.fill_modes().cpu().numpy(), op.apply(op.incident(dirs)).cpu().numpy())
+        torch.cuda.synchronize()
+        assert op.status() == 0
+    for mb in (8, 1):
+        assert np.array_equal(out[mb][0], out[0][0])
+        assert np.array_equal(out[mb][1], out[0][1])
+    err = np.abs(out[1][0].transpose(0, 2, 1) - A).max() / np.abs(A).max()
+    assert err < 1e-13, err
