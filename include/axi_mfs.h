@@ -183,12 +183,14 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   the next panel's columns of each step;
  *   "panel_cluster" 0 auto (by the number of (obstacle, mode) tasks), or 1,
  *                   2, 4 CTAs per mode for the Householder panels;
- *   "rest_grid"     0 one CTA per (task, column tile), 1 persistent (one CTA
- *                   per SM) for the trailing updates of split plans, 2 the
- *                   tcgen05 trailing update (tensor-memory accumulators, 64
- *                   columns per CTA; split plans whose next-panel update
- *                   is in digits, else as 0), 3 the same with one CTA per
- *                   SM (room beside it for a panel or next-panel CTA);
+ *   "rest_grid"     trailing updates of split plans: 0 auto (2 where the
+ *                   update can read Y^H digits, i.e. the panel wrote its
+ *                   reflector exponents, else 4), 1 mma.sync persistent (one
+ *                   CTA per SM), 2 the tcgen05 trailing update
+ *                   (tensor-memory accumulators, 64 columns per CTA), 3 the
+ *                   same with one CTA per SM (room beside it for a panel or
+ *                   next-panel CTA), 4 mma.sync with one CTA per (task,
+ *                   column tile);
  *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA;
  *   "crit_stream"   0 the panels and next-panel updates on `stream`, 1 on
  *                   a stream of the operator with the device's highest
@@ -197,7 +199,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   sample digits per chunk of ring pairs), else at most
  *                   this many MB per chunk (0..4096), so that a chunk's
  *                   digits stay in L2 between the sample and transform
- *                   kernels.
+ *                   kernels;
+ *   "apply_cluster" split plans' Q^H in axi_apply_operator: 0 auto (4 CTAs
+ *                   per (mode, 32-column tile) when all of them fit in one
+ *                   wave of two CTAs per SM, else 2), or 2, 4.
  * axi_plan_set_tuning parses such an object (unknown keys ignored, missing
  * keys kept; AXI_ERR_ARG on malformed input or values out of range);
  * axi_plan_get_tuning writes the current one into buf[n] (AXI_ERR_ARG if it

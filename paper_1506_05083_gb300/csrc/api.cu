@@ -303,11 +303,14 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
       if (iv != 0 && iv != 1 && iv != 2 && iv != 4) return false;
       t.panel_cluster = iv;
     } else if (key == "rest_grid") {
-      if (iv < 0 || iv > 3) return false;
+      if (iv < 0 || iv > 4) return false;
       t.rest_grid = iv;
     } else if (key == "fill_chunk_mb") {
       if (iv < 0 || iv > 4096) return false;
       t.fill_chunk_mb = iv;
+    } else if (key == "apply_cluster") {
+      if (iv != 0 && iv != 2 && iv != 4) return false;
+      t.apply_cluster = iv;
     } else if (key == "crit_stream") {
       if (iv < 0 || iv > 1) return false;
       t.crit_stream = iv;
@@ -322,9 +325,9 @@ std::string tuning_json(const axi::Tuning &t) {
   char buf[200];
   std::snprintf(buf, sizeof(buf),
                 "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d, "
-                "\"crit_stream\": %d, \"fill_chunk_mb\": %d}",
+                "\"crit_stream\": %d, \"fill_chunk_mb\": %d, \"apply_cluster\": %d}",
                 t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream,
-                t.fill_chunk_mb);
+                t.fill_chunk_mb, t.apply_cluster);
   return buf;
 }
 
@@ -672,7 +675,8 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
     if (e != cudaSuccess) return AXI_ERR_CUDA;
     if (panel_digits) {                 // the digits right behind the panel, over the whole GPU
       pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, st);
-      e = axi::launch_vdigits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max, st);
+      e = axi::launch_vdigits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max, slices,
+                                st);
       axi::prof_end(pid, st);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
     }
@@ -712,7 +716,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
       const bool use_y = slices > 0 && panel_digits;
       if (use_y) {
         pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, op->side);
-        e = axi::launch_y_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max,
+        e = axi::launch_y_digits(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, kp_max, slices,
                                  op->side);
         axi::prof_end(pid, op->side);
         if (e != cudaSuccess) return AXI_ERR_CUDA;
@@ -926,7 +930,8 @@ axi_status axi_apply_operator(const axi_operator *op, int32_t obs, int32_t W, co
   size_t need = 0;
   axi_apply_workspace_bytes(op, obs, W, &need);
   if (scratch_bytes < need) return AXI_ERR_WORKSPACE;
-  const ObsDev &d = op->plan->obs[obs].dev;
+  ObsDev d = op->plan->obs[obs].dev;                      // host copy with the plan's tuning
+  d.apply_cluster = op->plan->tune.apply_cluster;
   char *digit_scratch = static_cast<char *>(d_scratch) + align_up(sizeof(double2) * (size_t)d.D * 2 * W * d.rows);
   ProfScope scope(op->prof());
   return cuda_status(axi::launch_apply(op->d_obs + obs, d, W, reinterpret_cast<const double2 *>(d_f),
@@ -1031,7 +1036,7 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
     for (int pc : {1, 2, 4})
-      for (int rg : {0, 1, 2, 3})
+      for (int rg : {4, 1, 2, 3})
         for (int pt : {128, 256})
           for (int cs : {0, 1}) {
             if (rg >= 2 && nu != 2) continue;         // the tcgen05 update reads Y^H digits

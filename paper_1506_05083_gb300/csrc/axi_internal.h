@@ -20,14 +20,17 @@ constexpr int kPlanTsvd = 1 << 17;           // AXI_PLAN_TSVD
 struct Tuning {
   int next_update = 0;    // 0 auto, 1 native FP64, 2 split digits (split plans)
   int panel_cluster = 0;  // 0 auto (by the number of tasks), else 1, 2 or 4 CTAs per mode
-  int rest_grid = 0;      // 0 one CTA per (task, column tile), 1 persistent (one CTA per SM),
-                          // 2 tcgen05 kernel (split plans whose update reads Y^H digits; else as 0),
-                          // 3 the same with one CTA per SM (room for a critical-path CTA beside it)
+  int rest_grid = 0;      // split trailing update: 0 auto (2 where the update reads Y^H digits,
+                          // else 4), 1 mma.sync persistent (one CTA per SM), 2 tcgen05 kernel,
+                          // 3 the same with one CTA per SM (room for a critical-path CTA beside it),
+                          // 4 mma.sync, one CTA per (task, column tile)
   int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
   int crit_stream = 0;    // 0 the panel chain on the caller's stream, 1 on a stream of the
                           // operator with the device's highest priority
   int fill_chunk_mb = 0;  // split fill: 0 the plan's chunk (up to 512 MB of sample digits),
                           // else at most this many MB per chunk (small chunks stay in L2)
+  int apply_cluster = 0;  // split Q^H of the apply: CTAs per (mode, column tile) cluster,
+                          // 0 auto (4 when every cluster fits in one wave of CTAs, else 2)
 };
 
 // Device status bits latched by kernels (OR-ed into ObsDev::status).
@@ -96,6 +99,7 @@ struct ObsDev {
   // sample-digit scratch for fill_chunk_pairs ring pairs at a time.
   int fill_L, fill_Lp, fill_MR, fill_chunk_pairs;
   int fill_tc;            // 1: tcgen05 transform (fill_uses_tc), digit tiles in its layout
+  int apply_cluster;      // host side only: Tuning::apply_cluster for the split Q^H launch
   const unsigned short *fill_cdig;
   const int *fill_cex;
   uint32_t *fill_gdig;
@@ -200,7 +204,7 @@ cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,
 // Split plans: digits of panel p's reflectors over the whole GPU, after a
 // panel kernel that wrote the reflector columns' exponents.
 cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int p, int kp_max, cudaStream_t st);
+                           int ntasks, int p, int kp_max, int slices, cudaStream_t st);
 // Split plans: the next panel's columns in split precision, rows of each mode
 // spread over a cluster (needs the panel's digits; max_rows = tallest panel).
 cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
@@ -218,7 +222,7 @@ cudaError_t launch_qr_update_tc(const ObsDev *d_obs, const int *d_task_obs, cons
                                 cudaStream_t st);
 // Y = V T of panel p and the digits of Y^H (split plans, after launch_vdigits).
 cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int kp_max, cudaStream_t st);
+                            int ntasks, int p, int kp_max, int slices, cudaStream_t st);
 int split_update_tile_cols();
 cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
                                    const int *d_task_mode, int ntasks, int panel, int slices,

@@ -56,13 +56,13 @@ __device__ __forceinline__ int key_exponent(unsigned long long key) {
   return E == 0 ? -1022 : E - 1022;
 }
 
-// BF16 bit pattern of a small integer (|d| <= 255), built with integer ops.
+// BF16 bit pattern of a small integer (|d| <= 255): d + 256 is placed in the
+// mantissa of 2^23 (an OR, the sum staying below 2^23), 2^23 + 256 is taken
+// off exactly in FP32, and the FP32 result, having at most 8 significant
+// bits, truncates to BF16 without rounding (0 gives +0).
 __device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
-  if (d == 0) return 0;
-  const unsigned short sign = d < 0 ? 0x8000 : 0;
-  const unsigned a = d < 0 ? -d : d;
-  const int p = 31 - __clz(a);                      // a = 2^p * 1.f, p <= 7
-  return sign | (unsigned short)((127 + p) << 7) | (unsigned short)((a << (7 - p)) & 0x7f);
+  const float f = __uint_as_float(0x4B000000u | (unsigned)(d + 256)) - 8388864.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
 }
 
 // Balanced digits of x * 2^{-e} (|x| < 2^e): m = round(x * 2^{7S - e}) is

@@ -873,7 +873,7 @@ cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,
                                   const int *d_task_mode, int ntasks, int p, int slices,
                                   int max_rest_cols, int rest_grid, bool use_y, cudaStream_t st) {
   if (ntasks <= 0 || max_rest_cols <= 0) return cudaSuccess;
-  if (slices > 0 && use_y && (rest_grid == 2 || rest_grid == 3))
+  if (slices > 0 && use_y && (rest_grid == 0 || rest_grid == 2 || rest_grid == 3))
     return launch_qr_update_tc(d_obs, d_task_obs, d_task_mode, ntasks, p, slices, max_rest_cols,
                                rest_grid == 3, st);
   if (slices > 0)

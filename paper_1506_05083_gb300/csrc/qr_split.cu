@@ -713,6 +713,7 @@ panel_digits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
 // threads on consecutive rows, the V row digits with consecutive threads on
 // consecutive reflectors, so every store instruction writes contiguous bytes.
 constexpr int kVdRows = 64;
+template <int S>
 __global__ void __launch_bounds__(256)
 vdigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                const int *__restrict__ task_mode, int p) {
@@ -721,7 +722,6 @@ vdigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
   const int r0 = blockIdx.y * kVdRows;
   const int kp = o.kp;
   if (r0 >= kp) return;
-  const int S = o.slices;
   const int slot = o.dig_kept ? p : (p & 1);
   const int k0 = p * kNB, nbp = min(kNB, o.cols - k0), rows = o.rows;
   const double2 *A = o.A + (size_t)d * o.cols * o.rows;
@@ -753,14 +753,16 @@ vdigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
   for (int e = tid; e < kNB * kVdRows; e += 256) {        // V^H: [s][part][a][r]
     const int a = e / kVdRows, rr = e % kVdRows;
     const double2 x = Vs[a][rr];
-    oz::split_store_n(x.x, ecol[a], S, vh + (size_t)a * kp + r0 + rr, sh);
-    oz::split_store_n(-x.y, ecol[a], S, vh + (size_t)(kNB + a) * kp + r0 + rr, sh);
+    oz::split_store<S>(x.x, ecol[a], reinterpret_cast<__nv_bfloat16 *>(vh + (size_t)a * kp + r0 + rr), (int)sh);
+    oz::split_store<S>(-x.y, ecol[a], reinterpret_cast<__nv_bfloat16 *>(vh + (size_t)(kNB + a) * kp + r0 + rr),
+                       (int)sh);
   }
   for (int e = tid; e < kNB * kVdRows; e += 256) {        // V rows: [s][part][r][a]
     const int rr = e / kNB, a = e % kNB;
     const double2 x = Vs[a][rr];
-    oz::split_store_n(x.x, erow[rr], S, vr + (size_t)(r0 + rr) * kNB + a, sv);
-    oz::split_store_n(x.y, erow[rr], S, vr + (size_t)(kp + r0 + rr) * kNB + a, sv);
+    oz::split_store<S>(x.x, erow[rr], reinterpret_cast<__nv_bfloat16 *>(vr + (size_t)(r0 + rr) * kNB + a), (int)sv);
+    oz::split_store<S>(x.y, erow[rr], reinterpret_cast<__nv_bfloat16 *>(vr + (size_t)(kp + r0 + rr) * kNB + a),
+                       (int)sv);
   }
 }
 
@@ -822,6 +824,7 @@ y_rows_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
 
 // Digits of Y^H (conjugated, one exponent per column of Y, the layout of the
 // V^H digits) from y_rows_kernel's Y and column maxima.
+template <int S>
 __global__ void __launch_bounds__(256)
 ydigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
                const int *__restrict__ task_mode, int p) {
@@ -829,7 +832,7 @@ ydigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
   const int d = task_mode[blockIdx.x];
   const int r0 = blockIdx.y * kVdRows, kp = o.kp;
   if (r0 >= kp) return;
-  const int S = o.slices, slot = p & 1;
+  const int slot = p & 1;
   const double2 *Y = o.ybuf + ((size_t)d * 2 + slot) * kNB * kp;
   const unsigned long long *yk = o.ykey + ((size_t)d * 2 + slot) * kNB;
   unsigned short *yh = o.ydig + ((size_t)d * 2 + slot) * (size_t)2 * S * kNB * kp;
@@ -845,8 +848,9 @@ ydigits_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task_obs,
   for (int e = tid; e < kNB * kVdRows; e += 256) {        // [s][part][b][r]
     const int b = e / kVdRows, rr = e % kVdRows;
     const double2 y = Y[(size_t)b * kp + r0 + rr];
-    oz::split_store_n(y.x, ecol[b], S, yh + (size_t)b * kp + r0 + rr, sh);
-    oz::split_store_n(-y.y, ecol[b], S, yh + (size_t)(kNB + b) * kp + r0 + rr, sh);
+    oz::split_store<S>(y.x, ecol[b], reinterpret_cast<__nv_bfloat16 *>(yh + (size_t)b * kp + r0 + rr), (int)sh);
+    oz::split_store<S>(-y.y, ecol[b], reinterpret_cast<__nv_bfloat16 *>(yh + (size_t)(kNB + b) * kp + r0 + rr),
+                       (int)sh);
   }
 }
 
@@ -950,8 +954,16 @@ cudaError_t launch_apply_qh_s(const ObsDev *d_o, const ObsDev &h, double2 *X, in
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // rows split over a cluster of 4 CTAs (2 for short panels)
-  if (h.rows >= 192) return launch_apply_cluster_s<S, 4>(d_o, h, X, ncol, dig, dex, st);
+  // rows split over a cluster of 4 CTAs (2 for short panels); every cluster
+  // loops over all panels, so clusters that do not find room beside the
+  // first wave of CTAs (two per SM) would run a whole second pass: auto takes
+  // 4 only when D x 4 CTAs fit in one wave
+  int C = h.apply_cluster;
+  if (C == 0) {
+    const int tiles = (ncol + kTN - 1) / kTN;
+    C = (h.rows >= 192 && (long long)h.D * tiles * 4 <= 2ll * sm_count()) ? 4 : 2;
+  }
+  if (C == 4) return launch_apply_cluster_s<S, 4>(d_o, h, X, ncol, dig, dex, st);
   return launch_apply_cluster_s<S, 2>(d_o, h, X, ncol, dig, dex, st);
 }
 
@@ -982,20 +994,35 @@ cudaError_t launch_qr_update_split(const ObsDev *d_obs, const int *d_task_obs,
 }
 
 cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                           int ntasks, int p, int kp_max, cudaStream_t st) {
+                           int ntasks, int p, int kp_max, int slices, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
-  vdigits_kernel<<<dim3(ntasks, kp_max / kVdRows), 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  const dim3 grid(ntasks, kp_max / kVdRows);
+  switch (slices) {
+    case 4: vdigits_kernel<4><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 5: vdigits_kernel<5><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 6: vdigits_kernel<6><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 7: vdigits_kernel<7><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 8: vdigits_kernel<8><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                            int ntasks, int p, int kp_max, cudaStream_t st) {
+                            int ntasks, int p, int kp_max, int slices, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   const dim3 grid(ntasks, kp_max / kVdRows);
   y_rows_kernel<<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ydigits_kernel<<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p);
+  switch (slices) {
+    case 4: ydigits_kernel<4><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 5: ydigits_kernel<5><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 6: ydigits_kernel<6><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 7: ydigits_kernel<7><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    case 8: ydigits_kernel<8><<<grid, 256, 0, st>>>(d_obs, d_task_obs, d_task_mode, p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -15,8 +15,10 @@
 //      s + t <= S + 1 on BF16 mma.sync (group sums over the 32-term complex
 //      contraction stay below 2^23: exact in FP32), recombined with integer instructions
 //      into the FP64 read-modify-write of Y.
-// One CTA per (mode, 8 RHS columns), as trsm_kernel, so the sequential
-// diagonal solves still spread over all SM sub-partitions.
+// One CTA per (mode, 16 RHS columns): warp w solves columns w and w + 8 of
+// each diagonal block as two interleaved (independent) chains, and the
+// update's two n8 tiles go to warps 0-3 and 4-7. With two CTAs per SM the
+// 32 columns of 16 waves on the cup's 91 modes fit in one wave of CTAs.
 #include "axi_internal.h"
 #include "ozaki.cuh"
 
@@ -24,7 +26,7 @@ namespace axi {
 namespace {
 
 constexpr int kTB = 32;          // block size of the substitution
-constexpr int kTC = 8;           // RHS columns per CTA (one warp each in the diagonal solve)
+constexpr int kTC = 16;          // RHS columns per CTA (warp w solves columns w and w + 8)
 constexpr int kTT = 256;         // threads
 constexpr int kRM = 64;          // rows of R per staged chunk of the update
 constexpr int kLDR = kTB + 8;    // padded k stride (bf16) of the staged digits
@@ -80,13 +82,15 @@ r_digits_kernel(const ObsDev *__restrict__ od) {
 
 template <int S>
 struct TrsmSmem {
-  double2 Rb[kTB][kTB + 1];
+  union {                                // the diagonal block, then the R chunks of the update
+    double2 Rb[kTB][kTB + 1];
+    __nv_bfloat16 A[S][2][kRM][kLDR];    // digits of an R chunk ([row][column of the block])
+  };
   double2 Yb[kTB][kTC + 1];
   double rinv[kTB];
   int eX[kTC];
   int eR[kRM];
   __nv_bfloat16 B[S][2][kTC][kLDR];      // digits of X_b ([column][row of the block])
-  __nv_bfloat16 A[S][2][kRM][kLDR];      // digits of an R chunk ([row][column of the block])
 };
 
 template <int S>
@@ -130,22 +134,27 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
       }
     }
     __syncthreads();
-    // 1. diagonal block in FP64, warp c solves column c
+    // 1. diagonal block in FP64, warp w solves columns w and w + 8
     if (warp < ncols) {
-      const int c = warp;
+      const int c0w = warp, c1w = warp + kTC / 2;
       const double inv = sm.rinv[lane];
-      double2 y = sm.Yb[lane][c];
+      double2 y = sm.Yb[lane][c0w], z = sm.Yb[lane][c1w];   // column c1w is zero when unused
       y = make_double2(y.x * inv, y.y * inv);
+      z = make_double2(z.x * inv, z.y * inv);
       for (int rr = nb - 1; rr >= 0; --rr) {
-        double2 x;
+        double2 x, w;
         x.x = __shfl_sync(0xffffffffu, y.x, rr);              // final once the rows below are done
         x.y = __shfl_sync(0xffffffffu, y.y, rr);
+        w.x = __shfl_sync(0xffffffffu, z.x, rr);
+        w.y = __shfl_sync(0xffffffffu, z.y, rr);
         if (lane < rr) {
           const double2 rv = sm.Rb[lane][rr];
           y = make_double2(fma(-rv.x, x.x, fma(rv.y, x.y, y.x)), fma(-rv.x, x.y, fma(-rv.y, x.x, y.y)));
+          z = make_double2(fma(-rv.x, w.x, fma(rv.y, w.y, z.x)), fma(-rv.x, w.y, fma(-rv.y, w.x, z.y)));
         }
       }
-      sm.Yb[lane][c] = y;
+      sm.Yb[lane][c0w] = y;
+      if (c1w < ncols) sm.Yb[lane][c1w] = z;
     }
     __syncthreads();
     for (int e = tid; e < kTB * kTC; e += kTT) {
@@ -154,15 +163,17 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
     }
     if (r0 == 0) break;
     // 2. digits of X_b: one exponent (with headroom) per column
-    if (warp < kTC) {
-      const unsigned long long m = (lane < nb && warp < ncols) ? key2(sm.Yb[lane][warp]) : 0ull;
+#pragma unroll
+    for (int h = 0; h < kTC / 8; ++h) {
+      const int c = warp + 8 * h;
+      const unsigned long long m = (lane < nb && c < ncols) ? key2(sm.Yb[lane][c]) : 0ull;
       unsigned long long mm = m;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xffffffffu, mm, off);
         mm = w > mm ? w : mm;
       }
-      if (lane == 0) sm.eX[warp] = oz::key_exponent(mm) + 1;
+      if (lane == 0) sm.eX[c] = oz::key_exponent(mm) + 1;
     }
     __syncthreads();
     if (tid < kTC * (kTB / 2)) {
@@ -173,7 +184,8 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
       oz::split2_fast<S>(y0.x, y1.x, sm.eX[c], wr, 2 * kTC * kLDR / 2);
       oz::split2_fast<S>(y0.y, y1.y, sm.eX[c], wi, 2 * kTC * kLDR / 2);
     }
-    // 3. rows above: Y(0:r0) -= R(0:r0, block) X_b, 64 rows per chunk, warps 0..3
+    // 3. rows above: Y(0:r0) -= R(0:r0, block) X_b, 64 rows per chunk; warps
+    // 0..3 take columns 0..7, warps 4..7 columns 8..15, 16 rows each
     const size_t before = r_digit_rows_before(ib);
     const int rb = r_digit_block_rows(ib);
     const unsigned short *dg = o.rdig + ((size_t)d * mrows * S + before * S) * 2 * kTB;
@@ -189,7 +201,8 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
       }
       if (tid < kRM) sm.eR[tid] = ex[m0 + tid];
       __syncthreads();
-      if (warp < 4 && m0 + 16 * warp < r0) {
+      const int wr = warp & 3, nt = warp >> 2;                  // row group, n8 tile
+      if (m0 + 16 * wr < r0 && 8 * nt < ncols) {
         float acc[S][2][4];
 #pragma unroll
         for (int g = 0; g < S; ++g)
@@ -200,12 +213,12 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
 #pragma unroll
           for (int s = 1; s <= S; ++s) {
             uint32_t ar[4], ai[4];
-            oz::ldsm_x4(ar, &sm.A[s - 1][0][16 * warp + a_row][kk + a_k]);
-            oz::ldsm_x4(ai, &sm.A[s - 1][1][16 * warp + a_row][kk + a_k]);
+            oz::ldsm_x4(ar, &sm.A[s - 1][0][16 * wr + a_row][kk + a_k]);
+            oz::ldsm_x4(ai, &sm.A[s - 1][1][16 * wr + a_row][kk + a_k]);
 #pragma unroll
             for (int t = 1; t <= S + 1 - s; ++t) {
               uint32_t b4[4];                               // re k0-7, re k8-15, im k0-7, im k8-15
-              oz::ldsm_x4(b4, &sm.B[t - 1][lmat >> 1][lrow][kk + 8 * (lmat & 1)]);
+              oz::ldsm_x4(b4, &sm.B[t - 1][lmat >> 1][8 * nt + lrow][kk + 8 * (lmat & 1)]);
               const uint32_t br[2] = {b4[0], b4[1]}, bi[2] = {b4[2], b4[3]};
               oz::cmma(acc[s + t - 2][0], acc[s + t - 2][1], ar, ai, br, bi);
             }
@@ -221,8 +234,8 @@ trsm_split_kernel(const ObsDev *__restrict__ od, double2 *__restrict__ X, int nc
           }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int r = 16 * warp + grp + (e >= 2 ? 8 : 0);
-          const int i = m0 + r, c = 2 * tig + (e & 1);
+          const int r = 16 * wr + grp + (e >= 2 ? 8 : 0);
+          const int i = m0 + r, c = 8 * nt + 2 * tig + (e & 1);
           if (i < r0 && c < ncols) {
             const int E = sm.eR[r] + sm.eX[c] + oz::unfold1_shift<S>();
             double2 *y = &Xd[(size_t)c * ld + i];

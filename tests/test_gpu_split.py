@@ -110,8 +110,8 @@ def test_split_digits_sweep():
 
 @pytest.mark.parametrize("name", ["medium", "smooth", "small_trans"])
 def test_split_tc_update_parity(name):
-    """The trailing update on tcgen05 (tuning rest_grid 2, and 3 with one CTA
-    per SM: W' = Y^H X and X -= V W' as BF16 digit products with
+    """The trailing update on tcgen05 (tuning rest_grid 2, 3 with one CTA
+    per SM, and 0 = auto; 4 is the mma.sync form: W' = Y^H X and X -= V W' as BF16 digit products with
     tensor-memory accumulators): Q R reproduces the filled modes, the apply
     meets the oracle bar, the coefficients agree with the mma.sync update's
     to the digits' precision, and the occupancy choice changes no bit."""
@@ -121,7 +121,7 @@ def test_split_tc_update_parity(name):
     prec = axi.PREC_SPLIT_BF16 | (7 << 8)
     dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
     coefs = {}
-    for rg in (0, 2, 3):
+    for rg in (4, 0, 2, 3):
         op = axi.Operator([spec], prec=prec, tuning='{"next_update": 2, "rest_grid": %d}' % rg)
         assert '"rest_grid": %d' % rg in op.tuning()
         coefs[rg] = op.apply(op.incident(torch.tensor(dirs_np, device="cuda"))).cpu().numpy()
@@ -141,8 +141,9 @@ def test_split_tc_update_parity(name):
     c_ora = O.solve_modes(ob, fac, fh)
     for rg in (2, 3):       # tcgen05 update, two or one CTA per SM
         assert _e_bd(A, ob, coefs[rg], c_ora, fh) < 1e-10
-        assert _e_bd(A, ob, coefs[rg], coefs[0], fh) < 1e-10
+        assert _e_bd(A, ob, coefs[rg], coefs[4], fh) < 1e-10
     assert np.array_equal(coefs[2], coefs[3])
+    assert np.array_equal(coefs[0], coefs[2])      # auto picks the tcgen05 update here
 
 
 def test_split_fill_chunking_is_exact():
