@@ -433,10 +433,14 @@ def run_single(args, wl):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     pk, pk_src = peaks()
     split_prec = axi.PREC_SPLIT_BF16 | (args.slices << 8)
+    # --factor tsvd: the truncated-SVD form of the operator (QR, then an SVD of
+    # R with the 1e-10 relative cutoff) in both arms
+    plan_bits = axi.PLAN_TSVD if args.factor == "tsvd" else 0
+    split_prec |= plan_bits
     # plan-time host work, not in build_ms: geometry copy, fill tables, the
     # per-pair sub-grids and the cosine-table digits (axi_plan_create)
     plan_ms = {}
-    for name, pr in (("split", split_prec), ("fp64", axi.PREC_FP64)):
+    for name, pr in (("split", split_prec), ("fp64", axi.PREC_FP64 | plan_bits)):
         t0 = time.perf_counter()
         axi.Plan([spec], prec=pr)
         plan_ms[name] = (time.perf_counter() - t0) * 1e3
@@ -444,9 +448,10 @@ def run_single(args, wl):
     if args.prec == "split":
         arms.append(Arm("split", split_prec, spec, ob, W, dirs, dev, args.graph, args.tuning))
         if not args.no_fp64_arm:
-            arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph))
+            arms.append(Arm("fp64", axi.PREC_FP64 | plan_bits, spec, ob, W, dirs, dev, args.graph))
     else:
-        arms.append(Arm("fp64", axi.PREC_FP64, spec, ob, W, dirs, dev, args.graph, args.tuning))
+        arms.append(Arm("fp64", axi.PREC_FP64 | plan_bits, spec, ob, W, dirs, dev, args.graph,
+                        args.tuning))
     head = arms[0]
     for arm in arms:
         for _ in range(args.warmup):
@@ -513,6 +518,8 @@ def run_single(args, wl):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "precision": head.name, "M": ob.M, "N": ob.N, "P": ob.P,
                    "q": spec.q, "k": ob.k, "waves": W, "distinct_modes": ob.P // 2 + 1,
+                   "factor": "QR + truncated SVD of R (1e-10 cutoff)" if args.factor == "tsvd"
+                             else "QR",
                    "l2": "flushed (256 MB write) before each timed step",
                    "launch": "CUDA graph replay" if args.graph else "direct launches",
                    "tuning": {arm.name: arm.tuning for arm in arms}},
@@ -662,6 +669,8 @@ def main():
     ap.add_argument("--prec", default="split", choices=["split", "fp64"],
                     help="headline plan: Ozaki BF16 digits or native FP64")
     ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--factor", default="qr", choices=["qr", "tsvd"],
+                    help="qr (default): A_n^+ applied as R^-1 Q^H; tsvd: the truncated-SVD form")
     ap.add_argument("--tuning", default=None,
                     help="schedule of the headline plan as the library's tuning JSON "
                          "(default: autotuned on the device)")
