@@ -495,6 +495,14 @@ axi_status axi_diag_sincos(const double *d_x, int32_t n, double *d_sin, double *
 axi_status axi_diag_sincos_table(const double *d_x, int32_t n, double *d_sin, double *d_cos,
                                  void *stream);
 
+/* axi_diag_sincos_fixed -- diagnostics, as axi_diag_sincos, for the
+ * fixed-point form the split fill's samples use: the same reduction to a
+ * multiple of 2 pi / 1024 in FP64, then the series and the angle addition in
+ * 64-bit integers against a table with 62 fractional bits, one rounding to
+ * double (valid for |x| < 2^20). Same arguments and errors. */
+axi_status axi_diag_sincos_fixed(const double *d_x, int32_t n, double *d_sin, double *d_cos,
+                                 void *stream);
+
 /* axi_diag_wait_timeout -- diagnostics of the failure path of the library's
  * bounded device waits (the paper has no counterpart): one CTA allocates
  * tensor memory, waits on an mbarrier that nothing completes with the same

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("axi_noalloc_scratch_bytes", C.c_size_t, []),
     ("axi_diag_sincos", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     ("axi_diag_sincos_table", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    ("axi_diag_sincos_fixed", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     ("axi_eval_field", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_int32,
                                  C.POINTER(_Lattice), _vp, _vp, _vp, C.c_size_t, _vp]),
     ("axi_near_image_workspace_bytes", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(_Lattice),

@@ -34,7 +34,7 @@ def _sources():
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh", ".inc"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "axi_mfs.h"))
     if not force and os.path.exists(OUT):
         t = os.path.getmtime(OUT)

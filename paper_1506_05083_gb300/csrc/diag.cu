@@ -28,6 +28,21 @@ __global__ void diag_sincos_tab_kernel(const double *__restrict__ x, int n, cons
 // the table variant's table, uploaded once per device on first use
 __device__ double2 g_diag_ring_tab[trig::kRingTab];
 
+// the fixed-point variant's table (ring_table_q62.inc)
+__device__ const long long g_diag_ring_q62[trig::kRingTab][2] = {
+#include "ring_table_q62.inc"
+};
+
+__global__ void diag_sincos_q_kernel(const double *__restrict__ x, int n, double *__restrict__ s,
+                                     double *__restrict__ c) {
+  __shared__ longlong2 tab[trig::kRingTab];
+  for (int i = threadIdx.x; i < trig::kRingTab; i += blockDim.x)
+    tab[i] = make_longlong2(g_diag_ring_q62[i][0], g_diag_ring_q62[i][1]);
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    trig::sincos_ring_q(x[i], tab, &s[i], &c[i]);
+}
+
 // The failure path of the tcgen05 kernels, without their work: one CTA takes
 // tensor memory, waits with the kernels' bounded wait (tc::mbar_wait) on an
 // mbarrier that nothing completes, and when the limit runs out latches the
@@ -91,6 +106,16 @@ extern "C" axi_status axi_diag_sincos_table(const double *d_x, int32_t n, double
   if (blocks > 152 * 8) blocks = 152 * 8;
   axi::diag_sincos_tab_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_x, n, gtab, d_sin,
                                                                                      d_cos);
+  return cudaGetLastError() == cudaSuccess ? AXI_OK : AXI_ERR_CUDA;
+}
+
+extern "C" axi_status axi_diag_sincos_fixed(const double *d_x, int32_t n, double *d_sin, double *d_cos,
+                                            void *stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_sin || !d_cos))) return AXI_ERR_ARG;
+  if (n == 0) return AXI_OK;
+  int blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  axi::diag_sincos_q_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_x, n, d_sin, d_cos);
   return cudaGetLastError() == cudaSuccess ? AXI_OK : AXI_ERR_CUDA;
 }
 

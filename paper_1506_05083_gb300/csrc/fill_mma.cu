@@ -11,7 +11,8 @@
 // That is two real GEMMs per plan: [cos table of the even modes] x [e of every
 // pair, real and imaginary part as separate columns], likewise odd/o.
 //
-//   fill_samples_kernel  one warp per (pair, kind): FP64 samples, the fold,
+//   fill_samples_kernel  one warp per (pair, kind): FP64 samples (sin/cos of
+//                        k R in 64-bit fixed point, trig::sincos_ring_q), the fold,
 //                        per-column exponents and S = 8 balanced digits of
 //                        e and o (split2_fast), written to a scratch buffer;
 //   fill_gemm_tc_kernel  (Lp <= 448, MR <= 64) the same GEMM on the fifth-
@@ -43,6 +44,12 @@
 
 namespace axi {
 namespace {
+// (cos, sin)(2 pi i / 1024) with 62 fractional bits for trig::sincos_ring_q
+__device__ const long long g_ring_q62[1024][2] = {
+#include "ring_table_q62.inc"
+};
+}  // namespace
+namespace {
 
 constexpr double kInv4Pi = 0.07957747154594766788;
 constexpr int kFS = kFillDigits;          // digits of both operands (8)
@@ -71,8 +78,9 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
   const int q = o.q, h = q / 2, L = o.fill_L, Lp = o.fill_Lp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ double2 fseq[];
-  double2 *ring = fseq;                           // [1024] sin/cos table
-  for (int i = threadIdx.x; i < trig::kRingTab; i += blockDim.x) ring[i] = o.tab_ring[i];
+  longlong2 *ring = reinterpret_cast<longlong2 *>(fseq);   // [1024] (cos, sin) 2^62
+  for (int i = threadIdx.x; i < trig::kRingTab; i += blockDim.x)
+    ring[i] = make_longlong2(g_ring_q62[i][0], g_ring_q62[i][1]);
   __syncthreads();
   double2 *seq = fseq + trig::kRingTab + (size_t)warp * (h + 1);
   const int pl = blockIdx.x * kFWarpsA + warp;
@@ -104,7 +112,7 @@ fill_samples_kernel(const ObsDev *__restrict__ obs_arr, int oi, int pair0, int n
     const double inv = rsqrt(R2);
     const double R = R2 * inv, kR = k * R;
     double sn, cs;
-    trig::sincos_ring_tab(kR, ring, &sn, &cs);
+    trig::sincos_ring_q(kR, ring, &sn, &cs);
     double2 s;
     if (!deriv) {
       const double iw = inv * wq;

@@ -208,6 +208,19 @@ __device__ __forceinline__ void fold_fixed(long long &t, int g, float acc) {
   else t += (v + (1ll << (-sh - 1))) >> (-sh);
 }
 
+// fold_fixed for the adjacent groups g and g + 1 at once: their exact sums
+// (|acc| < 2^22) combine as acc_g 2^7 + acc_g1 in 32 bits (below 2^30), so
+// the pair costs one 64-bit shift and add. For R >= 7 g (group g lands at or
+// above the resolution) it is bit-identical to two fold_fixed calls: a right
+// shift of the pair drops at most 7 bits, all of them from acc_g1.
+template <int R>
+__device__ __forceinline__ void fold_fixed_pair(long long &t, int g, float acc_g, float acc_g1) {
+  const int v = f32_int(acc_g) * 128 + f32_int(acc_g1);
+  const int sh = R - 7 * (g + 1);
+  if (sh >= 0) t += (long long)v << sh;
+  else t += ((long long)v + (1ll << (-sh - 1))) >> (-sh);
+}
+
 // x - t 2^e for a double x and an integer t (|t| < 2^59), with integer
 // instructions only. The difference is formed in 64-bit integers at the finer
 // of the two resolutions that keeps x within 62 bits: 2^e when x's last bit

@@ -454,18 +454,29 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
         }
       }
       long long ta[2][4] = {}, tb[2][4] = {};
+      if constexpr (FE) {
 #pragma unroll
-      for (int g = 2; g <= S + 1; ++g)
+        for (int g = 2; g <= S + 1; g += 2)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if constexpr (FE) {
-            oz::fold_fixed<50>(ta[0][q], g, acc[g - 2][0][q]);
-            oz::fold_fixed<50>(ta[1][q], g, acc[g - 2][1][q]);
-          } else {
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              if (g + 1 <= S + 1 && 50 >= 7 * g) {
+                oz::fold_fixed_pair<50>(ta[c][q], g, acc[g - 2][c][q], acc[g - 1][c][q]);
+              } else {
+                oz::fold_fixed<50>(ta[c][q], g, acc[g - 2][c][q]);
+                if (g + 1 <= S + 1) oz::fold_fixed<50>(ta[c][q], g + 1, acc[g - 1][c][q]);
+              }
+            }
+      } else {
+#pragma unroll
+        for (int g = 2; g <= S + 1; ++g)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
             oz::fold_group<S>(ta[0][q], tb[0][q], g, acc[g - 2][0][q]);
             oz::fold_group<S>(ta[1][q], tb[1][q], g, acc[g - 2][1][q]);
           }
-        }
+      }
       unsigned long long cm[2] = {0ull, 0ull};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

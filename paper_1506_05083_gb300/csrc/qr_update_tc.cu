@@ -240,8 +240,12 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
           tc::ld_wait();
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            oz::fold_fixed<kR1>(tacc[8 * qh + q], g, __uint_as_float(r[q]));
-            if (g + 1 <= S + 1) oz::fold_fixed<kR1>(tacc[8 * qh + q], g + 1, __uint_as_float(r2[q]));
+            if (g + 1 <= S + 1 && kR1 >= 7 * g)
+              oz::fold_fixed_pair<kR1>(tacc[8 * qh + q], g, __uint_as_float(r[q]), __uint_as_float(r2[q]));
+            else {
+              oz::fold_fixed<kR1>(tacc[8 * qh + q], g, __uint_as_float(r[q]));
+              if (g + 1 <= S + 1) oz::fold_fixed<kR1>(tacc[8 * qh + q], g + 1, __uint_as_float(r2[q]));
+            }
           }
         }
       }
@@ -374,8 +378,12 @@ qr_update_tc_kernel(const ObsDev *__restrict__ obs, const int *__restrict__ task
           tc::ld_wait();
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            oz::fold_fixed<kR2>(ta[q], g, __uint_as_float(rv[q]));
-            if (g + 1 <= S + 1) oz::fold_fixed<kR2>(ta[q], g + 1, __uint_as_float(rw[q]));
+            if (g + 1 <= S + 1 && kR2 >= 7 * g)
+              oz::fold_fixed_pair<kR2>(ta[q], g, __uint_as_float(rv[q]), __uint_as_float(rw[q]));
+            else {
+              oz::fold_fixed<kR2>(ta[q], g, __uint_as_float(rv[q]));
+              if (g + 1 <= S + 1) oz::fold_fixed<kR2>(ta[q], g + 1, __uint_as_float(rw[q]));
+            }
           }
         }
 #pragma unroll

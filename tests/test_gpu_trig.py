@@ -1,8 +1,9 @@
 """The ring-kernel sin/cos routines (csrc/trig.cuh) against CUDA's sincos
 (torch.sin / torch.cos on the device) and numpy's, through the diagnostics
-entry points: axi_diag_sincos (Cody-Waite reduction + Taylor series) and
-axi_diag_sincos_table (1024-entry table + short series + angle addition, the
-form the fill's samples use).
+entry points: axi_diag_sincos (Cody-Waite reduction + Taylor series),
+axi_diag_sincos_table (1024-entry table + short series + angle addition) and
+axi_diag_sincos_fixed (the same reduction, then series and angle addition in
+64-bit fixed point: the form the split fill's samples use).
 
 Bound: absolute error <= 1e-15 (about 4.5 units of 2^-52 at 1.0) for
 |x| <= 2000, which covers k R for every workload here (k <= 45, R <= 10).
@@ -17,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table"])
+@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table", "axi_diag_sincos_fixed"])
 def test_sincos_ring_against_cuda_and_numpy(entry):
     from paper_1506_05083_gb300 import axi
     rng = np.random.default_rng(3)
@@ -47,7 +48,7 @@ def test_sincos_ring_against_cuda_and_numpy(entry):
     assert np.abs(s.cpu().numpy() ** 2 + c.cpu().numpy() ** 2 - 1.0).max() <= 1e-15
 
 
-@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table"])
+@pytest.mark.parametrize("entry", ["axi_diag_sincos", "axi_diag_sincos_table", "axi_diag_sincos_fixed"])
 def test_diag_sincos_arguments(entry):
     from paper_1506_05083_gb300 import axi
     f = getattr(axi.lib(), entry)
