@@ -191,7 +191,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   same with one CTA per SM (room beside it for a panel or
  *                   next-panel CTA), 4 mma.sync with one CTA per (task,
  *                   column tile);
- *   "panel_threads" 0 auto (128), 128 or 256 threads per panel CTA;
+ *   "panel_threads" 0 auto (256 threads when a panel of more than 128 rows
+ *                   runs on one CTA, else 128), 128 or 256 threads per
+ *                   panel CTA;
  *   "crit_stream"   0 the panels and next-panel updates on `stream`, 1 on
  *                   a stream of the operator with the device's highest
  *                   priority (forked from and joined back into `stream`);
@@ -212,8 +214,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  * the panel chain's choices together, then, for split plans, the fill chunk
  * with the best of those. It keeps the fastest in the plan, rebuilds the
  * operator with it and, when json_out is
- * not NULL, writes the choice with its build time ("build_ms") and the number
- * of candidates. Caching the result is the caller's: pass it back with
+ * not NULL, writes the choice with its build time ("build_ms"), the number
+ * of candidates timed and the number skipped because they cannot run on this
+ * device or plan ("skipped"). Caching the result is the caller's: pass it back with
  * axi_plan_set_tuning before axi_build_operator.
  */
 axi_status axi_plan_set_tuning(axi_plan *plan, const char *json);

@@ -1015,7 +1015,7 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   }
   axi::Tuning best = keep;
   double best_ms = 1e300;
-  int tried = 0;
+  int tried = 0, skipped = 0;
   // one warm-up build of the plan's current tuning, then `reps` timed builds
   auto time_it = [&](double &ms_out) -> axi_status {
     axi_status s = run_build(op, st);
@@ -1035,9 +1035,9 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   // the panel chain's schedule first
   for (int nu : {1, 2}) {
     if (nu == 2 && !split) continue;
-    for (int pc : {1, 2, 4})
+    for (int pc : {0, 1, 2, 4})
       for (int rg : {4, 1, 2, 3})
-        for (int pt : {128, 256})
+        for (int pt : {0, 128, 256})
           for (int cs : {0, 1}) {
             if (rg >= 2 && nu != 2) continue;         // the tcgen05 update reads Y^H digits
             p->tune = keep;
@@ -1048,13 +1048,17 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
             p->tune.crit_stream = cs;
             double ms = 0.0;
             s = time_it(ms);
-            if (s != AXI_OK) break;
+            if (s != AXI_OK) {                        // a candidate that cannot run here
+              (void)cudaGetLastError();
+              ++skipped;
+              s = AXI_OK;
+              continue;
+            }
             if (ms < best_ms) {
               best_ms = ms;
               best = p->tune;
             }
           }
-    if (s != AXI_OK) break;
   }
   // then the split fill's chunk size with that schedule (smaller chunks keep
   // the sample digits in L2 between the two fill kernels)
@@ -1066,7 +1070,12 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
       p->tune.fill_chunk_mb = fc;
       double ms = 0.0;
       s = time_it(ms);
-      if (s != AXI_OK) break;
+      if (s != AXI_OK) {
+        (void)cudaGetLastError();
+        ++skipped;
+        s = AXI_OK;
+        continue;
+      }
       if (ms < best_ms) {
         best_ms = ms;
         best = p->tune;
@@ -1075,6 +1084,7 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (s == AXI_OK && best_ms >= 1e300) s = AXI_ERR_CUDA;  // no candidate ran
   if (s != AXI_OK) {
     p->tune = keep;
     return s;
@@ -1085,7 +1095,8 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
   if (json_out) {
     std::string js = tuning_json(best);
     char tail[96];
-    std::snprintf(tail, sizeof(tail), ", \"build_ms\": %.4f, \"candidates\": %d}", best_ms, tried);
+    std::snprintf(tail, sizeof(tail), ", \"build_ms\": %.4f, \"candidates\": %d, \"skipped\": %d}",
+                  best_ms, tried, skipped);
     js.pop_back();
     js += tail;
     return copy_out(js, json_out, n);

@@ -24,7 +24,7 @@ struct Tuning {
                           // else 4), 1 mma.sync persistent (one CTA per SM), 2 tcgen05 kernel,
                           // 3 the same with one CTA per SM (room for a critical-path CTA beside it),
                           // 4 mma.sync, one CTA per (task, column tile)
-  int panel_threads = 0;  // 0 auto (128), 128 or 256 threads per panel CTA
+  int panel_threads = 0;  // 0 auto (256 on one CTA with more than 128 rows, else 128), 128, 256
   int crit_stream = 0;    // 0 the panel chain on the caller's stream, 1 on a stream of the
                           // operator with the device's highest priority
   int fill_chunk_mb = 0;  // split fill: 0 the plan's chunk (up to 512 MB of sample digits),

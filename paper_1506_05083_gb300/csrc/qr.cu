@@ -786,11 +786,11 @@ cudaError_t launch_panel_cluster(const ObsDev *d_obs, const int *d_task_obs, con
   auto local_rows = [](int K) {
     return C > 1 ? NT * ((K + C * NT - 1) / (C * NT)) : K;
   };
+  // the step's own panel height (the first step is the tallest, so the grant
+  // made there covers the rest of the build)
   const size_t smem = sizeof(double2) * (size_t)kNB * local_rows(max_panel_rows);
   static size_t granted = 0;
-  cudaError_t e = ensure_dynamic_smem(qr_panel_smem_kernel<C, NT>,
-                                      sizeof(double2) * (size_t)kNB * local_rows(kPanelSmemRows),
-                                      granted);
+  cudaError_t e = ensure_dynamic_smem(qr_panel_smem_kernel<C, NT>, smem, granted);
   if (e != cudaSuccess) return e;
   static const bool carve = (prefer_max_shared(qr_panel_smem_kernel<C, NT>), true);
   (void)carve;
@@ -822,6 +822,25 @@ int sm_count() {
   return n;
 }
 
+// Whether one CTA of NT threads can hold a panel of `rows` rows (dynamic)
+// beside the kernel's static shared arrays.
+template <int NT>
+bool panel_fits_one_cta(int rows) {
+  static int limit = -1;
+  static size_t static_bytes = 0;
+  if (limit < 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, qr_panel_smem_kernel<1, NT>) != cudaSuccess)
+      return false;
+    limit = optin;
+    static_bytes = fa.sharedSizeBytes;
+  }
+  return static_bytes + sizeof(double2) * (size_t)kNB * rows <= (size_t)limit;
+}
+
 // The panel is bound by the FP64 pipe of the SMs that factor it: when the
 // step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
 template <int NT>
@@ -831,6 +850,8 @@ cudaError_t launch_panel_nt(const ObsDev *d_obs, const int *d_task_obs, const in
   if (cluster == 4 || (cluster == 0 && 4 * ntasks <= sms))
     return launch_panel_cluster<4, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
   if (cluster == 2 || (cluster == 0 && 2 * ntasks <= sms))
+    return launch_panel_cluster<2, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
+  if (!panel_fits_one_cta<NT>(max_panel_rows))   // the panel and the static arrays exceed one CTA
     return launch_panel_cluster<2, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
   return launch_panel_cluster<1, NT>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, st);
 }
@@ -845,7 +866,14 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
   *digits_written = slices > 0 && max_panel_rows <= kPanelSmemRows;
   if (ntasks <= 0) return cudaSuccess;
   if (max_panel_rows <= kPanelSmemRows) {
-    if (threads == 256)
+    // threads 0 (auto): 256 when the panel runs on one CTA and has more than
+    // 128 rows (two warps per SM sub-partition hide the FP64 latency of the
+    // per-row sweep; in clusters the wider CTAs' exchanges cost more), else 128
+    const int sms = sm_count();
+    const int c_auto = (cluster == 0 && 4 * ntasks <= sms) ? 4 : (cluster == 0 && 2 * ntasks <= sms) ? 2 : 1;
+    const int c_eff = cluster != 0 ? cluster : c_auto;
+    const bool wide = threads == 256 || (threads == 0 && c_eff == 1 && max_panel_rows > 128);
+    if (wide)
       return launch_panel_nt<256>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows,
                                   cluster, st);
     return launch_panel_nt<kPanelThreads>(d_obs, d_task_obs, d_task_mode, ntasks, p,
