@@ -202,6 +202,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *                   this many MB per chunk (0..4096), so that a chunk's
  *                   digits stay in L2 between the sample and transform
  *                   kernels;
+ *   "next_cluster"  split plans' next-panel update: CTAs per mode, 0 auto
+ *                   (4 when four per mode fit one per SM and the panel has
+ *                   256 rows or more, else 2), or 1, 2, 4;
  *   "apply_cluster" split plans' Q^H in axi_apply_operator: 0 auto (4 CTAs
  *                   per (mode, 32-column tile) when all of them fit in one
  *                   wave of two CTAs per SM, else 2), or 2, 4.
@@ -211,8 +214,8 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  * does not fit). axi_operator_autotune times every candidate schedule with
  * CUDA events on `stream` (one warm-up and `reps` builds each, reps in
  * 1..100; it synchronises the stream, so not under stream capture): first
- * the panel chain's choices together, then, for split plans, the fill chunk
- * with the best of those. It keeps the fastest in the plan, rebuilds the
+ * the panel chain's choices together, then, for split plans, the next-panel
+ * update's cluster and the fill chunk, each with the best so far. It keeps the fastest in the plan, rebuilds the
  * operator with it and, when json_out is
  * not NULL, writes the choice with its build time ("build_ms"), the number
  * of candidates timed and the number skipped because they cannot run on this

@@ -308,6 +308,9 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
     } else if (key == "fill_chunk_mb") {
       if (iv < 0 || iv > 4096) return false;
       t.fill_chunk_mb = iv;
+    } else if (key == "next_cluster") {
+      if (iv != 0 && iv != 1 && iv != 2 && iv != 4) return false;
+      t.next_cluster = iv;
     } else if (key == "apply_cluster") {
       if (iv != 0 && iv != 2 && iv != 4) return false;
       t.apply_cluster = iv;
@@ -325,9 +328,10 @@ std::string tuning_json(const axi::Tuning &t) {
   char buf[200];
   std::snprintf(buf, sizeof(buf),
                 "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d, "
-                "\"crit_stream\": %d, \"fill_chunk_mb\": %d, \"apply_cluster\": %d}",
+                "\"crit_stream\": %d, \"fill_chunk_mb\": %d, \"next_cluster\": %d, "
+                "\"apply_cluster\": %d}",
                 t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream,
-                t.fill_chunk_mb, t.apply_cluster);
+                t.fill_chunk_mb, t.next_cluster, t.apply_cluster);
   return buf;
 }
 
@@ -697,7 +701,8 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
       // columns in split precision too; otherwise in native FP64
       e = panel_digits && p->tune.next_update != 1
               ? axi::launch_qr_update_next_split(op->d_obs, op->d_task_obs, op->d_task_mode, nt,
-                                                 (int)s, slices, p->step_rows[s], st)
+                                                 (int)s, slices, p->step_rows[s],
+                                                 p->tune.next_cluster, st)
               : axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
       axi::prof_end(pid, st, p->step_fl_next[s]);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
@@ -1060,8 +1065,28 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
             }
           }
   }
-  // then the split fill's chunk size with that schedule (smaller chunks keep
-  // the sample digits in L2 between the two fill kernels)
+  // then, one choice at a time with the best so far: the next-panel update's
+  // cluster (split plans whose panels write digits) and the split fill's
+  // chunk size (smaller chunks keep the sample digits in L2)
+  if (s == AXI_OK && split) {
+    for (int nc : {1, 2, 4}) {
+      if (best.next_update == 1 || nc == best.next_cluster) continue;
+      p->tune = best;
+      p->tune.next_cluster = nc;
+      double ms = 0.0;
+      s = time_it(ms);
+      if (s != AXI_OK) {
+        (void)cudaGetLastError();
+        ++skipped;
+        s = AXI_OK;
+        continue;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = p->tune;
+      }
+    }
+  }
   if (s == AXI_OK && split && p->obs[0].dev.fill_cdig != nullptr) {
     const axi::Tuning base = best;
     for (int fc : {0, 256, 128, 96, 64}) {

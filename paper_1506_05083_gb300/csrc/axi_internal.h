@@ -29,6 +29,8 @@ struct Tuning {
                           // operator with the device's highest priority
   int fill_chunk_mb = 0;  // split fill: 0 the plan's chunk (up to 512 MB of sample digits),
                           // else at most this many MB per chunk (small chunks stay in L2)
+  int next_cluster = 0;   // split next-panel update: CTAs per mode, 0 auto (4 when every
+                          // mode's four fit one per SM and the panel has 256 rows, else 2), 1, 2, 4
   int apply_cluster = 0;  // split Q^H of the apply: CTAs per (mode, column tile) cluster,
                           // 0 auto (4 when every cluster fits in one wave of CTAs, else 2)
 };
@@ -209,7 +211,7 @@ cudaError_t launch_vdigits(const ObsDev *d_obs, const int *d_task_obs, const int
 // spread over a cluster (needs the panel's digits; max_rows = tallest panel).
 cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
                                         const int *d_task_mode, int ntasks, int panel, int slices,
-                                        int max_rows, cudaStream_t st);
+                                        int max_rows, int cluster, cudaStream_t st);
 // use_y: the trailing update reads Y^H digits (launch_y_digits) and skips T^H W.
 // rest_grid: Tuning::rest_grid.
 cudaError_t launch_qr_update_rest(const ObsDev *d_obs, const int *d_task_obs,

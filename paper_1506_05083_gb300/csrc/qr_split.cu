@@ -368,7 +368,8 @@ __device__ void oz_block_reflector_update(const PanelDigits pd, int rows, int k0
 #pragma unroll
   for (int u = 0; u < kPairs; ++u) {
     const int e = tid + u * kThreads, j = e % kTN, lo = e / kTN;
-    th_pair(sm.T, &sm.W[0][0], kTN + 1, j, lo, wp[u][0], wp[u][1]);
+    wp[u][0] = wp[u][1] = make_double2(0.0, 0.0);
+    if (j < ncols) th_pair(sm.T, &sm.W[0][0], kTN + 1, j, lo, wp[u][0], wp[u][1]);
   }
   __syncthreads();
 #pragma unroll
@@ -922,11 +923,14 @@ cudaError_t launch_next_split_s(const ObsDev *d_obs, const int *d_task_obs, cons
 
 template <int S>
 cudaError_t launch_next_split_c(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
-                                int ntasks, int p, int max_rows, cudaStream_t st) {
-  // rows per CTA: a 64-row chunk or more in each member of the cluster; at
-  // most about one CTA per SM (the trailing update holds one CTA on each)
-  if (max_rows >= 256 && 4 * ntasks <= sm_count())
-    return launch_next_split_s<S, 4>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
+                                int ntasks, int p, int max_rows, int cluster, cudaStream_t st) {
+  // cluster 0 (auto): rows per CTA a 64-row chunk or more in each member of
+  // the cluster, at most about one CTA per SM (the trailing update holds one
+  // CTA on each); else the tuning's 1, 2 or 4
+  int C = cluster;
+  if (C == 0) C = (max_rows >= 256 && 4 * ntasks <= sm_count()) ? 4 : 2;
+  if (C == 4) return launch_next_split_s<S, 4>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
+  if (C == 1) return launch_next_split_s<S, 1>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
   return launch_next_split_s<S, 2>(d_obs, d_task_obs, d_task_mode, ntasks, p, st);
 }
 
@@ -1039,14 +1043,14 @@ cudaError_t launch_y_digits(const ObsDev *d_obs, const int *d_task_obs, const in
 
 cudaError_t launch_qr_update_next_split(const ObsDev *d_obs, const int *d_task_obs,
                                         const int *d_task_mode, int ntasks, int p, int slices,
-                                        int max_rows, cudaStream_t st) {
+                                        int max_rows, int cluster, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   switch (slices) {
-    case 4: return launch_next_split_c<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
-    case 5: return launch_next_split_c<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
-    case 6: return launch_next_split_c<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
-    case 7: return launch_next_split_c<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
-    case 8: return launch_next_split_c<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, st);
+    case 4: return launch_next_split_c<4>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, cluster, st);
+    case 5: return launch_next_split_c<5>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, cluster, st);
+    case 6: return launch_next_split_c<6>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, cluster, st);
+    case 7: return launch_next_split_c<7>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, cluster, st);
+    case 8: return launch_next_split_c<8>(d_obs, d_task_obs, d_task_mode, ntasks, p, max_rows, cluster, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -167,3 +167,27 @@ def test_split_fill_chunking_is_exact():
         assert np.array_equal(out[mb][1], out[0][1])
     err = np.abs(out[1][0].transpose(0, 2, 1) - A).max() / np.abs(A).max()
     assert err < 1e-13, err
+
+
+@pytest.mark.parametrize("name", ["medium", "smooth"])
+def test_split_next_cluster_parity(name):
+    """The next panel's columns updated by clusters of 1, 2 or 4 CTAs per mode
+    (tuning next_cluster): each meets the oracle bar, and they agree with each
+    other to the digits' precision (the row split changes only the order in
+    which the cluster's partial V^H X are added)."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case(name)
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+    c_ora = O.solve_modes(ob, fac, fh)
+    coefs = {}
+    for nc in (1, 2, 4):
+        op = axi.Operator([spec], prec=axi.PREC_SPLIT_BF16 | (7 << 8),
+                          tuning='{"next_update": 2, "next_cluster": %d}' % nc)
+        coefs[nc] = op.apply(op.incident(torch.tensor(dirs_np, device="cuda"))).cpu().numpy()
+        torch.cuda.synchronize()
+        assert op.status() == 0
+        assert _e_bd(A, ob, coefs[nc], c_ora, fh) < 1e-10
+    assert _e_bd(A, ob, coefs[1], coefs[2], fh) < 1e-10
+    assert _e_bd(A, ob, coefs[4], coefs[2], fh) < 1e-10
