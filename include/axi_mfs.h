@@ -205,6 +205,15 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  *   "next_cluster"  split plans' next-panel update: CTAs per mode, 0 auto
  *                   (4 when four per mode fit one per SM and the panel has
  *                   256 rows or more, else 2), or 1, 2, 4;
+ *   "panel_fixed"   split plans' Householder panels: 0 auto (FP64), 1 FP64,
+ *                   2 in 58-bit fixed point (exact integer sums, integer
+ *                   updates, FP64 scalars; one CTA per mode, so with
+ *                   panel_cluster 0 or 1; the build fails with AXI_ERR_CUDA
+ *                   where a panel does not fit one CTA);
+ *   "rest_start"    0 each step's trailing update starts as soon as the
+ *                   panel (and its digits) is done, beside the next-panel
+ *                   update; 1 it starts after the next-panel update, so that
+ *                   it runs beside the next panel only;
  *   "apply_cluster" split plans' Q^H in axi_apply_operator: 0 auto (4 CTAs
  *                   per (mode, 32-column tile) when all of them fit in one
  *                   wave of two CTAs per SM, else 2), or 2, 4.
@@ -215,7 +224,9 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  * CUDA events on `stream` (one warm-up and `reps` builds each, reps in
  * 1..100; it synchronises the stream, so not under stream capture): first
  * the panel chain's choices together, then, for split plans, the next-panel
- * update's cluster and the fill chunk, each with the best so far. It keeps the fastest in the plan, rebuilds the
+ * update's cluster and the fixed-point panel (128 and 256 threads), then
+ * the other trailing-update start (on either stream priority), then, for
+ * split plans, the fill chunk, each with the best so far. It keeps the fastest in the plan, rebuilds the
  * operator with it and, when json_out is
  * not NULL, writes the choice with its build time ("build_ms"), the number
  * of candidates timed and the number skipped because they cannot run on this

@@ -267,8 +267,8 @@ class Operator:
 
     def tuning(self) -> str:
         """axi_plan_get_tuning: the plan's schedule choices as JSON."""
-        buf = C.create_string_buffer(256)
-        _check(lib().axi_plan_get_tuning(self._plan, buf, 256), "axi_plan_get_tuning")
+        buf = C.create_string_buffer(512)
+        _check(lib().axi_plan_get_tuning(self._plan, buf, 512), "axi_plan_get_tuning")
         return buf.value.decode()
 
     def set_tuning(self, json_text: str):

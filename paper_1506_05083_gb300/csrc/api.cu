@@ -317,6 +317,12 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
     } else if (key == "crit_stream") {
       if (iv < 0 || iv > 1) return false;
       t.crit_stream = iv;
+    } else if (key == "panel_fixed") {
+      if (iv < 0 || iv > 2) return false;
+      t.panel_fixed = iv;
+    } else if (key == "rest_start") {
+      if (iv < 0 || iv > 1) return false;
+      t.rest_start = iv;
     } else if (key == "panel_threads") {
       if (iv != 0 && iv != 128 && iv != 256) return false;
       t.panel_threads = iv;
@@ -325,13 +331,13 @@ bool parse_tuning(const char *js, axi::Tuning &t) {
 }
 
 std::string tuning_json(const axi::Tuning &t) {
-  char buf[200];
+  char buf[320];
   std::snprintf(buf, sizeof(buf),
                 "{\"next_update\": %d, \"panel_cluster\": %d, \"rest_grid\": %d, \"panel_threads\": %d, "
                 "\"crit_stream\": %d, \"fill_chunk_mb\": %d, \"next_cluster\": %d, "
-                "\"apply_cluster\": %d}",
+                "\"panel_fixed\": %d, \"rest_start\": %d, \"apply_cluster\": %d}",
                 t.next_update, t.panel_cluster, t.rest_grid, t.panel_threads, t.crit_stream,
-                t.fill_chunk_mb, t.next_cluster, t.apply_cluster);
+                t.fill_chunk_mb, t.next_cluster, t.panel_fixed, t.rest_start, t.apply_cluster);
   return buf;
 }
 
@@ -674,7 +680,7 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
     bool panel_digits = false;
     e = axi::launch_qr_panel(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s,
                              p->step_rows[s], slices, p->tune.panel_cluster,
-                             p->tune.panel_threads, st, &panel_digits);
+                             p->tune.panel_threads, p->tune.panel_fixed, st, &panel_digits);
     axi::prof_end(pid, st, p->step_fl_panel[s]);
     if (e != cudaSuccess) return AXI_ERR_CUDA;
     if (panel_digits) {                 // the digits right behind the panel, over the whole GPU
@@ -688,7 +694,10 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
     // kept digits: every panel's digits are written (the apply reads them),
     // also at the last steps that have no trailing update
     const bool digits_here = slices > 0 && (rest_cols > 0 || p->obs[0].dev.dig_kept);
-    if (rest_cols > 0 || digits_here) {
+    // the side stream's work of this step starts behind the panel (and its
+    // digits), or, with rest_start 1, behind the next-panel update as well
+    const bool fork_late = p->tune.rest_start == 1 && p->step_cols[s] > 0;
+    if ((rest_cols > 0 || digits_here) && !fork_late) {
       if (cudaEventRecord(op->ev_panel, st) != cudaSuccess ||
           cudaStreamWaitEvent(op->side, op->ev_panel, 0) != cudaSuccess)
         return AXI_ERR_CUDA;
@@ -706,6 +715,11 @@ static axi_status run_build(axi_operator_s *op, cudaStream_t st,
               : axi::launch_qr_update_next(op->d_obs, op->d_task_obs, op->d_task_mode, nt, (int)s, st);
       axi::prof_end(pid, st, p->step_fl_next[s]);
       if (e != cudaSuccess) return AXI_ERR_CUDA;
+    }
+    if ((rest_cols > 0 || digits_here) && fork_late) {
+      if (cudaEventRecord(op->ev_panel, st) != cudaSuccess ||
+          cudaStreamWaitEvent(op->side, op->ev_panel, 0) != cudaSuccess)
+        return AXI_ERR_CUDA;
     }
     if (digits_here && !panel_digits) {
       pid = axi::prof_begin(AXI_KERNEL_PANEL_DIGITS, op->side);
@@ -1073,6 +1087,49 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
       if (best.next_update == 1 || nc == best.next_cluster) continue;
       p->tune = best;
       p->tune.next_cluster = nc;
+      double ms = 0.0;
+      s = time_it(ms);
+      if (s != AXI_OK) {
+        (void)cudaGetLastError();
+        ++skipped;
+        s = AXI_OK;
+        continue;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = p->tune;
+      }
+    }
+  }
+  // split plans: the fixed-point panel (one CTA of 128 or 256 threads per mode)
+  if (s == AXI_OK && split) {
+    const axi::Tuning base = best;
+    for (int pt : {128, 256}) {
+      p->tune = base;
+      p->tune.panel_fixed = 2;
+      p->tune.panel_cluster = 1;
+      p->tune.panel_threads = pt;
+      double ms = 0.0;
+      s = time_it(ms);
+      if (s != AXI_OK) {
+        (void)cudaGetLastError();
+        ++skipped;
+        s = AXI_OK;
+        continue;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = p->tune;
+      }
+    }
+  }
+  // the trailing updates' start, on either stream priority
+  if (s == AXI_OK) {
+    const axi::Tuning base = best;
+    for (int cs : {0, 1}) {
+      p->tune = base;
+      p->tune.rest_start = 1 - base.rest_start;
+      p->tune.crit_stream = cs;
       double ms = 0.0;
       s = time_it(ms);
       if (s != AXI_OK) {

@@ -31,6 +31,11 @@ struct Tuning {
                           // else at most this many MB per chunk (small chunks stay in L2)
   int next_cluster = 0;   // split next-panel update: CTAs per mode, 0 auto (4 when every
                           // mode's four fit one per SM and the panel has 256 rows, else 2), 1, 2, 4
+  int panel_fixed = 0;    // split plans' panel: 0 auto (FP64), 1 FP64, 2 fixed point (one CTA per
+                          // mode)
+  int rest_start = 0;     // trailing update of a step: 0 starts after the panel's digits (beside
+                          // the next-panel update), 1 after the next-panel update (beside the
+                          // next panel only)
   int apply_cluster = 0;  // split Q^H of the apply: CTAs per (mode, column tile) cluster,
                           // 0 auto (4 when every cluster fits in one wave of CTAs, else 2)
 };
@@ -196,9 +201,17 @@ cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
 // panel's reflector columns, so that launch_vdigits can write the digits
 // (split plans, panels in shared memory).
 // cluster: CTAs per mode for shared-memory panels (0 = by the number of tasks).
+// fixed: split plans' panel arithmetic, 0 and 1 FP64, 2 fixed point
+// (qr_panel_fx.cu; one CTA per mode, so only with cluster 0 or 1).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int panel, int max_panel_rows, int slices, int cluster,
-                            int threads, cudaStream_t st, bool *digits_written);
+                            int threads, int fixed, cudaStream_t st, bool *digits_written);
+// The fixed-point panel (qr_panel_fx.cu): whether a panel of `rows` rows fits
+// one CTA of `threads` (128 or 256), and its launch.
+bool panel_fx_fits(int rows, int threads);
+cudaError_t launch_qr_panel_fx(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
+                               int ntasks, int panel, int max_panel_rows, int threads,
+                               cudaStream_t st);
 // Trailing update of panel step `panel`: the next panel's kNB columns (native
 // FP64, critical path), and the columns beyond (split or FP64; col_off = kNB).
 cudaError_t launch_qr_update_next(const ObsDev *d_obs, const int *d_task_obs,

@@ -860,11 +860,19 @@ cudaError_t launch_panel_nt(const ObsDev *d_obs, const int *d_task_obs, const in
 // step has few tasks, each is spread over a cluster of 2 or 4 CTAs (SMs).
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int p, int max_panel_rows, int slices, int cluster,
-                            int threads, cudaStream_t st, bool *digits_written) {
+                            int threads, int fixed, cudaStream_t st, bool *digits_written) {
   // the shared-memory panel also writes the reflector columns' exponents,
   // after which vdigits_kernel writes split plans' digits (launch_vdigits)
   *digits_written = slices > 0 && max_panel_rows <= kPanelSmemRows;
   if (ntasks <= 0) return cudaSuccess;
+  if (slices > 0 && max_panel_rows <= kPanelSmemRows && fixed == 2 && cluster <= 1) {
+    // split plans, on request: the panel in fixed point on one CTA per mode
+    // (threads 0: 256 above 128 rows, else 128), where the panel fits one CTA
+    const int nt = threads != 0 ? threads : (max_panel_rows > 128 ? 256 : 128);
+    if (panel_fx_fits(max_panel_rows, nt))
+      return launch_qr_panel_fx(d_obs, d_task_obs, d_task_mode, ntasks, p, max_panel_rows, nt, st);
+    return cudaErrorInvalidConfiguration;                     // asked for, but it does not fit
+  }
   if (max_panel_rows <= kPanelSmemRows) {
     // threads 0 (auto): 256 when the panel runs on one CTA and has more than
     // 128 rows (two warps per SM sub-partition hide the FP64 latency of the

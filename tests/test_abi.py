@@ -147,13 +147,13 @@ def test_plan_tuning_json(axi):
         assert L.axi_plan_get_tuning(plan, buf, 256) == 0
         assert json.loads(buf.value.decode()) == {"next_update": 0, "panel_cluster": 0, "rest_grid": 0,
                                                   "panel_threads": 0, "crit_stream": 0, "fill_chunk_mb": 0,
-                                                  "next_cluster": 0, "apply_cluster": 0}
+                                                  "next_cluster": 0, "panel_fixed": 0, "rest_start": 0, "apply_cluster": 0}
         assert L.axi_plan_set_tuning(plan, b'{"panel_cluster": 2, "rest_grid": 1, "other": 7}') == 0
         assert L.axi_plan_get_tuning(plan, buf, 256) == 0
         assert json.loads(buf.value.decode()) == {"next_update": 0, "panel_cluster": 2, "rest_grid": 1,
                                                   "panel_threads": 0, "crit_stream": 0, "fill_chunk_mb": 0,
-                                                  "next_cluster": 0, "apply_cluster": 0}
-        for bad in (b'{"panel_cluster": 3}', b'{"rest_grid": 5}', b'{"crit_stream": 2}', b'{"fill_chunk_mb": -1}', b'{"apply_cluster": 3}', b'{"next_cluster": 3}', b'{"panel_threads": 64}', b'{"next_update": 5}', b'panel_cluster: 1', b'{"rest_grid" 1}'):
+                                                  "next_cluster": 0, "panel_fixed": 0, "rest_start": 0, "apply_cluster": 0}
+        for bad in (b'{"panel_cluster": 3}', b'{"rest_grid": 5}', b'{"crit_stream": 2}', b'{"fill_chunk_mb": -1}', b'{"apply_cluster": 3}', b'{"next_cluster": 3}', b'{"rest_start": 2}', b'{"panel_fixed": 3}', b'{"panel_threads": 64}', b'{"next_update": 5}', b'panel_cluster: 1', b'{"rest_grid" 1}'):
             assert L.axi_plan_set_tuning(plan, bad) == -1
         assert json.loads(buf.value.decode())["panel_cluster"] == 2
         assert L.axi_plan_get_tuning(plan, buf, 8) == -1          # buffer too small

@@ -191,3 +191,81 @@ def test_split_next_cluster_parity(name):
         assert _e_bd(A, ob, coefs[nc], c_ora, fh) < 1e-10
     assert _e_bd(A, ob, coefs[1], coefs[2], fh) < 1e-10
     assert _e_bd(A, ob, coefs[4], coefs[2], fh) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["medium", "smooth"])
+def test_split_rest_start_is_exact(name):
+    """Starting each trailing update after the next-panel update (tuning
+    rest_start 1), on either stream priority, changes only when kernels run,
+    not what they compute: the coefficients equal those of rest_start 0 bit
+    for bit, and meet the oracle bar."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case(name)
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+    c_ora = O.solve_modes(ob, fac, fh)
+    coefs = []
+    for rs, cs in ((0, 0), (1, 0), (1, 1)):
+        op = axi.Operator([spec], prec=axi.PREC_SPLIT_BF16 | (7 << 8),
+                          tuning='{"next_update": 2, "rest_start": %d, "crit_stream": %d}' % (rs, cs))
+        coefs.append(op.apply(op.incident(torch.tensor(dirs_np, device="cuda"))).cpu().numpy())
+        torch.cuda.synchronize()
+        assert op.status() == 0
+    assert _e_bd(A, ob, coefs[0], c_ora, fh) < 1e-10
+    assert np.array_equal(coefs[1], coefs[0])
+    assert np.array_equal(coefs[2], coefs[0])
+
+
+@pytest.mark.parametrize("name", ["small", "medium", "smooth"])
+def test_split_panel_fixed_parity(name):
+    """The Householder panel in 58-bit fixed point (tuning panel_fixed 2:
+    exact integer sums, integer updates, FP64 scalars): Q R reproduces the
+    filled modes, Q is unitary, every panel's I - V T V^H equals the product
+    of its reflectors, the apply meets the oracle bar and agrees with the
+    FP64 panel's, and 128 and 256 threads give the same bits (integer sums
+    do not depend on their order)."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, (coll, src, srcx), A, fac = _case(name)
+    spec = axi.spec_from_obstacle(wl.obstacles[0])
+    prec = axi.PREC_SPLIT_BF16 | (7 << 8)
+    dirs_np = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)
+    coefs, facs = {}, {}
+    for key, t in (("fp64", '{"next_update": 2, "panel_fixed": 1}'),
+                   ("fx128", '{"next_update": 2, "panel_fixed": 2, "panel_threads": 128}'),
+                   ("fx256", '{"next_update": 2, "panel_fixed": 2, "panel_threads": 256}')):
+        op = axi.Operator([spec], prec=prec, tuning=t)
+        coefs[key] = op.apply(op.incident(torch.tensor(dirs_np, device="cuda"))).cpu().numpy()
+        Ap, tau, T, nb = op.factors()
+        facs[key] = (Ap.cpu().numpy().transpose(0, 2, 1), tau.cpu().numpy(), T.cpu().numpy())
+        if key == "fx128":
+            Af = op.fill_modes().cpu().numpy().transpose(0, 2, 1)
+        torch.cuda.synchronize()
+        assert op.status() == 0
+    Ap, tau, T = facs["fx128"]
+    rows, cols = Ap.shape[1], Ap.shape[2]
+    for d in (0, 1, ob.P // 2):
+        Q = _householder_q(Ap[d], tau[d], rows, cols)
+        R = np.triu(Ap[d][:cols])
+        assert np.all(np.diag(R).imag == 0)
+        assert np.linalg.norm(Q[:, :cols] @ R - Af[d]) < 1e-12 * np.linalg.norm(Af[d])
+        assert np.abs(Q.conj().T @ Q - np.eye(rows)).max() < 1e-13
+        for p in range(T.shape[1]):
+            k0 = p * nb
+            nbp = min(nb, cols - k0)
+            V = np.zeros((rows, nbp), dtype=np.complex128)
+            Hprod = np.eye(rows, dtype=np.complex128)
+            for a in range(nbp):
+                c = k0 + a
+                V[c, a] = 1.0
+                V[c + 1:, a] = Ap[d][c + 1:, c]
+                Hprod = Hprod @ (np.eye(rows) - tau[d][c] * np.outer(V[:, a], V[:, a].conj()))
+            Tp = T[d, p].T[:nbp, :nbp]
+            assert np.abs(np.eye(rows) - V @ Tp @ V.conj().T - Hprod).max() < 1e-13
+    for k in range(3):
+        assert np.array_equal(facs["fx256"][k], facs["fx128"][k])
+    assert np.array_equal(coefs["fx256"], coefs["fx128"])
+    fh = O.rhs_modes(O.incident_samples(ob, coll, dirs_np))
+    c_ora = O.solve_modes(ob, fac, fh)
+    assert _e_bd(A, ob, coefs["fx128"], c_ora, fh) < 1e-10
+    assert _e_bd(A, ob, coefs["fx128"], coefs["fp64"], fh) < 1e-10
