@@ -374,7 +374,7 @@ def kernel_profile(arm, steps, flush):
             for k, (n, ms, fl) in st.items() if n > 0}
 
 
-def roofline_from_profile(prof, slices, split, pk, src):
+def roofline_from_profile(prof, slices, split, pk, src, tuning=None):
     """The launch class with the most device time among those with
     algorithmic flops, against its own bound: FP64 classes against the FP64
     DFMA peak ("alu"); split classes against the BF16 tensor peak, counting
@@ -386,9 +386,13 @@ def roofline_from_profile(prof, slices, split, pk, src):
     per_launch_ms = v["ms"] / v["launches"]
     fl64 = v["flops"] / (v["ms"] * 1e-3) / 1e12
     total_ms = sum(x["ms"] for x in prof.values())
-    common = {"kernel": kind, "launches_per_step": v["launches"], "kernel_ms_per_launch": per_launch_ms,
+    # the split plans' panel runs in FP64 or, when the tuning asks, in
+    # fixed point (qr_panel_fx.cu): each has its own traffic capture
+    fixed_panel = split and kind == "panel" and (tuning or {}).get("panel_fixed") == 2
+    common = {"kernel": kind + ("_fixed_point" if fixed_panel else ""),
+              "launches_per_step": v["launches"], "kernel_ms_per_launch": per_launch_ms,
               "share_of_profiled_time": v["ms"] / total_ms,
-              "traffic": traffic_for(("split_" if split else "fp64_") + kind)}
+              "traffic": traffic_for(("split_" if split else "fp64_") + kind + ("_fx" if fixed_panel else ""))}
     if split and kind in SPLIT_KINDS:
         ach = fl64 * digit_pairs(slices)
         peak = pk["bf16_tflops_sustained"]
@@ -398,7 +402,9 @@ def roofline_from_profile(prof, slices, split, pk, src):
                     peak_source=f"bf16_tflops_sustained of {src} (the kernel runs inside a long step)")
     return dict(common, bound="alu", achieved=fl64, peak=FP64_DFMA_PEAK_TFLOPS, unit="TFLOP/s",
                 frac=fl64 / FP64_DFMA_PEAK_TFLOPS,
-                work="algorithmic FP64 flops of the launch class (complex Householder count)",
+                work="algorithmic FP64 flops of the launch class (complex Householder count)"
+                     + ("; computed with integer arithmetic, reported against the FP64 rate it replaces"
+                        if fixed_panel else ""),
                 peak_source="FP64 DFMA probe of measured (MEASURED_PEAKS.json has no FP64 entry)")
 
 
@@ -480,7 +486,7 @@ def run_single(args, wl):
     # kernel profile of the headline arm (separate, untimed pass)
     prof = kernel_profile(head, 3, flush)
     split = head.name == "split"
-    roof = roofline_from_profile(prof, args.slices, split, pk, pk_src)
+    roof = roofline_from_profile(prof, args.slices, split, pk, pk_src, getattr(head, "tuning", None))
     total_prof = sum(v["ms"] for v in prof.values())
 
     # end to end through the public API with host buffers: H2D of the wave
