@@ -10,6 +10,8 @@ Every function follows the paper's statement of the method directly: direct
 summation in place of FFTs, unblocked Householder QR, plain back substitution,
 no blocking or reordering. Each function cites the section or equation it
 restates. Parity status of each function (what pins it) is listed in
-`oracle/mfs.py`'s module docstring.
+`oracle/mfs.py`'s module docstring; the periodizing scheme's spherical-wave
+block B~ (Sec. 4.1) is in `oracle/periodizing.py`, with its own pins.
 """
 from .mfs import *  # noqa: F401,F403
+from . import periodizing  # noqa: F401

@@ -1,0 +1,100 @@
+"""Pins of the oracle's spherical-wave block B~ (Sec. 4, eq. urep; Sec. 4.1)
+against facts fixed outside it (no GPU): closed forms of the special
+functions, the plane-wave (Rayleigh) expansion, and the oracle's own
+independent incident-data path."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import periodizing as OP
+
+
+def _small(bc=0, P=32, k=3.0):
+    wl = synth.small_case(seed=7, k=k, M=40, N=32, P=P, bc=bc)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    return ob, coll
+
+
+def test_spherical_bessel_closed_forms():
+    x = np.array([0.3, 1.0, 2.7, 9.5, 31.0])
+    s, c = np.sin(x), np.cos(x)
+    assert np.allclose(OP.sph_jn(0, x), s / x, rtol=1e-14, atol=0)
+    assert np.allclose(OP.sph_jn(1, x), s / x**2 - c / x, rtol=1e-13, atol=1e-16)
+    assert np.allclose(OP.sph_jn(2, x), (3 / x**3 - 1 / x) * s - 3 * c / x**2, rtol=1e-12, atol=1e-16)
+    assert np.allclose(OP.sph_jn(0, x, derivative=True), -OP.sph_jn(1, x), rtol=1e-14, atol=1e-17)
+
+
+def test_spherical_harmonics_closed_forms():
+    th, ph = 0.83, 2.1
+    st, ct, e = math.sin(th), math.cos(th), np.exp(1j * ph)
+    cases = {
+        (0, 0): 0.5 / math.sqrt(math.pi),
+        (1, 0): 0.5 * math.sqrt(3 / math.pi) * ct,
+        (1, 1): -0.5 * math.sqrt(1.5 / math.pi) * st * e,          # Condon-Shortley phase
+        (1, -1): 0.5 * math.sqrt(1.5 / math.pi) * st / e,
+        (2, 2): 0.25 * math.sqrt(7.5 / math.pi) * st**2 * e**2,
+        (2, 1): -0.5 * math.sqrt(7.5 / math.pi) * st * ct * e,
+    }
+    for (l, m), ref in cases.items():
+        assert abs(OP.sph_y(l, m, th, ph)[0] - ref) < 1e-15
+
+
+@pytest.mark.parametrize("d", [(0.0, 0.0, 1.0), (0.36, -0.48, 0.8), (1.0, 0.0, 0.0)])
+def test_plane_wave_expansion_value_and_normal_derivative(d):
+    """e^{ik d.x} = sum_lm d_lm j_l(kr) Y_lm(x^) and its gradient i k d e^{ik d.x}:
+    pins the value and the chain-rule gradient of the spherical waves."""
+    rng = np.random.default_rng(3)
+    k, p = 2.5, 34
+    x = rng.uniform(-1.2, 1.2, (40, 3))
+    nvec = rng.normal(size=(40, 3))
+    nvec /= np.linalg.norm(nvec, axis=1, keepdims=True)
+    d = np.asarray(d)
+    coef = OP.plane_wave_coefficients(p, d)
+    u = np.zeros(40, dtype=np.complex128)
+    dn = np.zeros(40, dtype=np.complex128)
+    for l in range(p + 1):
+        for m in range(-l, l + 1):
+            v, g = OP.sph_wave_value_grad(l, m, k, x)
+            u += coef[l * l + l + m] * v
+            dn += coef[l * l + l + m] * np.sum(g * nvec, axis=1)
+    ref = np.exp(1j * k * (x @ d))
+    assert np.abs(u - ref).max() < 1e-13
+    assert np.abs(dn - 1j * k * (nvec @ d) * ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_btilde_block_structure(bc):
+    """Only m = n survives the mean over phi (axis on the expansion's z axis),
+    and the surviving entries are real for real k."""
+    ob, coll = _small(bc=bc, P=16)
+    p = 6
+    B = OP.btilde(ob, coll, p, q=64, rows=range(0, 40, 5))
+    scale = np.abs(B).max()
+    for n in range(B.shape[0]):
+        keep = OP.btilde_columns(p, n)
+        mask = np.ones(B.shape[2], bool)
+        mask[keep] = False
+        assert np.abs(B[n][:, mask]).max() < 1e-14 * scale
+        if keep.size:
+            assert np.abs(B[n][:, keep].imag).max() < 1e-14 * scale
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_btilde_reproduces_incident_modes(bc):
+    """B~ applied to a plane wave's spherical-wave coefficients gives the
+    plane wave's modal boundary data, computed independently by
+    `incident_samples` (value, normal derivative at the ring nodes) and
+    `rhs_modes` (the DFT over phi), which hold minus that data."""
+    ob, coll = _small(bc=bc, P=32)
+    p = 30
+    d = np.array([math.sin(0.3), 0.0, math.cos(0.3)])
+    B = OP.btilde(ob, coll, p, q=96, modes=range(0, 6))
+    fh = O.rhs_modes(O.incident_samples(ob, coll, d[None, :]))[0]     # [P][rows]
+    coef = OP.plane_wave_coefficients(p, d)
+    for n in range(6):
+        got = B[n] @ coef
+        assert np.abs(got + fh[n]).max() < 1e-12 * np.abs(fh[0]).max()
