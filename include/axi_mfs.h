@@ -304,6 +304,33 @@ axi_status axi_refactor_operator_modes(axi_operator *op, const axi_c128 *const *
  */
 axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, void *stream);
 
+/*
+ * The periodizing scheme's spherical-wave block B~ (Sec. 4, eq. urep; Sec.
+ * 4.1, the B~ display): the modal boundary data of obstacle `obs` due to the
+ * regular waves u_lm = j_l(k r) Y_lm(theta, phi), l = 0 .. p, |m| <= l
+ * (Y_lm orthonormal with the Condon-Shortley phase, theta the polar angle of
+ * the collocation point (rho, z), k the exterior wavenumber). Rows are those
+ * of the operator's modal matrices: Neumann, M rows of the normal
+ * derivative; transmission, 2M rows, values then normal derivatives. The
+ * obstacle's axis is the expansion's z axis, so the mean over phi keeps
+ * only m = n and B~ is block diagonal and real: mode n holds the columns
+ * l = n .. p, mode -n is (-1)^n times mode n, every other entry is zero.
+ *
+ * axi_btilde_count writes the number of doubles of the packed blocks for
+ * degree p (0 <= p <= AXI_BTILDE_MAX_DEGREE). axi_fill_btilde writes them to
+ * d_out, a device buffer of at least that many doubles (8-byte aligned,
+ * owned by the caller): for n = 0 .. min(P/2, p) in turn, the block of mode
+ * n as a rows x (p + 1 - n) column-major array (column l - n holds degree
+ * l). Enqueued on `stream`; a non-finite entry sets the operator's status
+ * word (AXI_ERR_NUMERIC from axi_operator_status).
+ * Errors: AXI_ERR_ARG (null pointers, obs or p out of range, count too
+ * small), AXI_ERR_CUDA.
+ */
+#define AXI_BTILDE_MAX_DEGREE 255
+axi_status axi_btilde_count(const axi_operator *op, int32_t obs, int32_t p, size_t *count);
+axi_status axi_fill_btilde(const axi_operator *op, int32_t obs, int32_t p, double *d_out,
+                           size_t count, void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

@@ -73,6 +73,8 @@ def sph_wave_value_grad(l, m, k, x):
     """u_lm(x) = j_l(k r) Y_lm(theta, phi) at Cartesian points x [..., 3] and
     its Cartesian gradient [..., 3], by the chain rule through (r, theta, phi):
       grad u = d_r u e_r + (1/r) d_theta u e_theta + 1/(r sin theta) d_phi u e_phi.
+    m may be an array that broadcasts against x[..., 0] (all orders of one
+    degree in one call).
     """
     x = np.asarray(x, dtype=np.float64)
     X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
@@ -137,10 +139,10 @@ def btilde(ob, coll, p, q, modes=None, rows=None):
     F_val = np.zeros((nr, n_harmonics(p), q), dtype=np.complex128)
     F_dn = np.zeros_like(F_val)
     for l in range(p + 1):
-        for m in range(-l, l + 1):
-            u, g = sph_wave_value_grad(l, m, ob.k, X)
-            F_val[:, l * l + l + m, :] = u
-            F_dn[:, l * l + l + m, :] = np.sum(g * Nv, axis=-1)
+        ms = np.arange(-l, l + 1)[:, None, None]
+        u, g = sph_wave_value_grad(l, ms, ob.k, X[None])               # [2l+1][rows][q]
+        F_val[:, l * l:(l + 1) ** 2, :] = np.moveaxis(u, 0, 1)
+        F_dn[:, l * l:(l + 1) ** 2, :] = np.moveaxis(np.sum(g * Nv[None], axis=-1), 0, 1)
     s = np.arange(q)
     E = np.exp(-2j * math.pi * np.outer(s, np.asarray(modes)) / q) / q     # [q][modes]
     dn = np.einsum("ics,sn->nic", F_dn, E)

@@ -75,6 +75,8 @@ SIGNATURES = [
     ("axi_refactor_operator_modes", C.c_int, [_vp, C.POINTER(_vp), _vp]),
     ("axi_diag_wait_timeout", C.c_int, [_vp, C.c_int64, _vp]),
     ("axi_fill_modes", C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    ("axi_btilde_count", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_fill_btilde", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
@@ -326,6 +328,26 @@ class Operator:
                               device=self.workspace.device)
         _check(lib().axi_fill_modes(self._op, obs, _dev(out), _stream(stream)), "axi_fill_modes")
         return out
+
+    def btilde(self, p, obs=0, out=None, stream=None):
+        """axi_fill_btilde: the spherical-wave block B~ of degree p as a list of
+        per-mode [p + 1 - n][rows] views (mode n = 0 .. min(P/2, p)) into one
+        packed float64 buffer (returned second)."""
+        n = C.c_size_t()
+        _check(lib().axi_btilde_count(self._op, obs, p, C.byref(n)), "axi_btilde_count")
+        if out is None:
+            out = torch.empty(n.value, dtype=torch.float64, device=self.workspace.device)
+        if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < n.value:
+            raise ValueError("btilde: out must be a contiguous float64 tensor of the count's size")
+        _check(lib().axi_fill_btilde(self._op, obs, p, _dev(out), out.numel(), _stream(stream)),
+               "axi_fill_btilde")
+        s = self.specs[obs]
+        blocks, off = [], 0
+        for m in range(min(s.P // 2, p) + 1):
+            sz = (p + 1 - m) * s.rows
+            blocks.append(out[off:off + sz].view(p + 1 - m, s.rows))
+            off += sz
+        return blocks, out
 
     def factors(self, obs=0):
         """(A [D][cols][rows], tau [D][cols], T [D][npanels][nb][nb] col-major) views."""

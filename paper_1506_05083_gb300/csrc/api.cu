@@ -900,6 +900,24 @@ axi_status axi_fill_modes(const axi_operator *op, int32_t obs, axi_c128 *d_out, 
                                       op->plan->tune.fill_chunk_mb));
 }
 
+axi_status axi_btilde_count(const axi_operator *op, int32_t obs, int32_t p, size_t *count) {
+  if (!op || !count || obs < 0 || obs >= (int)op->plan->obs.size() || p < 0 ||
+      p > AXI_BTILDE_MAX_DEGREE)
+    return AXI_ERR_ARG;
+  *count = axi::btilde_count(op->plan->obs[obs].dev, p);
+  return AXI_OK;
+}
+
+axi_status axi_fill_btilde(const axi_operator *op, int32_t obs, int32_t p, double *d_out,
+                           size_t count, void *stream) {
+  if (!op || !d_out || obs < 0 || obs >= (int)op->plan->obs.size() || p < 0 ||
+      p > AXI_BTILDE_MAX_DEGREE || (reinterpret_cast<uintptr_t>(d_out) & 7))
+    return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (count < axi::btilde_count(d, p)) return AXI_ERR_ARG;
+  return cuda_status(axi::launch_btilde(op->d_obs, d, obs, p, d_out, static_cast<cudaStream_t>(stream)));
+}
+
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
   if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;

@@ -206,6 +206,11 @@ cudaError_t launch_fill(const ObsDev *d_obs, const ObsDev &h_obs, int obs_index,
 cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const int *d_task_mode,
                             int ntasks, int panel, int max_panel_rows, int slices, int cluster,
                             int threads, int fixed, cudaStream_t st, bool *digits_written);
+// The spherical-wave block B~ of the periodizing scheme (periodize.cu):
+// doubles of the packed mode blocks for degree p, and their fill.
+size_t btilde_count(const ObsDev &h, int p);
+cudaError_t launch_btilde(const ObsDev *d_obs, const ObsDev &h, int oi, int p, double *out,
+                          cudaStream_t st);
 // The fixed-point panel (qr_panel_fx.cu): whether a panel of `rows` rows fits
 // one CTA of `threads` (128 or 256), and its launch.
 bool panel_fx_fits(int rows, int threads);

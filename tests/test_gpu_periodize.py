@@ -1,0 +1,52 @@
+"""The periodizing scheme's spherical-wave block B~ (Sec. 4, eq. urep; Sec.
+4.1) on the GPU against the oracle's trapezoid-rule B~ (oracle/periodizing.py):
+each stored mode block equals the oracle's m = n columns, and the packing
+leaves the modes above min(P/2, p) out."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import periodizing as OP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _case(name):
+    if name == "small":
+        wl = synth.small_case(seed=7, k=3.0, M=40, N=32, P=16)
+    elif name == "small_trans":
+        wl = synth.small_case(seed=11, k=2.0, M=44, N=36, P=20, bc=synth.BC_TRANSMISSION)
+    elif name == "smooth":
+        wl = synth.config_smooth()
+    else:
+        wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    return wl, ob, coll
+
+
+@pytest.mark.parametrize("name,p,rows", [("small", 12, None), ("small_trans", 7, None),
+                                         ("smooth", 20, range(4, 216, 9)),
+                                         ("cup", 48, range(5, 432, 54))])
+def test_btilde_parity(name, p, rows):
+    from paper_1506_05083_gb300 import axi
+    wl, ob, coll = _case(name)
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])], prec=axi.PREC_FP64)
+    blocks, buf = op.btilde(p)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    nmax = min(ob.P // 2, p)
+    assert len(blocks) == nmax + 1
+    q = p + nmax + 2                                  # no aliasing: q > |m - n| for m, n <= p, nmax
+    ref = OP.btilde(ob, coll, p, q, modes=range(nmax + 1), rows=rows)
+    idx = np.arange(ob.M) if rows is None else np.asarray(rows)
+    if ob.bc == synth.BC_TRANSMISSION:
+        idx = np.concatenate([idx, ob.M + idx])
+    scale = np.abs(ref).max()
+    for n in range(nmax + 1):
+        got = blocks[n].cpu().numpy().T[idx]          # [rows][l - n]
+        want = ref[n][:, OP.btilde_columns(p, n)]
+        assert np.abs(want.imag).max() < 1e-13 * scale
+        assert np.abs(got - want.real).max() < 1e-12 * scale, n
