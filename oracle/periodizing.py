@@ -31,6 +31,17 @@ Readings (shared with the CUDA path, which implements them independently):
     B~ is block diagonal in the mode (only m = n), and real for real k; the
     trapezoid rule reproduces this exactly for q > |m| + |n| nodes.
 
+Q (the periodizing rows of eq. full for the unknowns [d; a; b]): the S
+blocks put the spherical waves and their x-, y-, z-derivatives at M1 x M1
+product Gauss nodes of the unit cell's faces, combined into the
+discrepancies of eqs. qp1-qp4 and the Cauchy data on T and D; the W blocks
+put the Rayleigh-Bloch waves on T and D (eqs. rb1-rb2, T-nD). Readings:
+the cell is [-ex/2, ex/2] x [-ey/2, ey/2] x [-z0, z0] around the obstacle;
+(kx, ky) = k (d_x, d_y) of the incident direction, alpha = e^{i kx ex},
+beta = e^{i ky ey}; the Rayleigh-Bloch set is |kappa| <= pi N0, ordered by
+m then n; k_z takes the principal square root (+i sqrt for evanescent
+waves).
+
 Pins (tests/test_oracle_periodizing.py):
   sph_jn             closed forms of j_0, j_1, j_2 and j_0' = -j_1
   sph_y              closed forms of Y_00, Y_1m, Y_22 (fixes the phase)
@@ -40,6 +51,11 @@ Pins (tests/test_oracle_periodizing.py):
   btilde             m != n entries vanish, m = n entries are real; B~ times
                      the plane wave's coefficients equals minus the modal
                      incident data of `incident_samples` + `rhs_modes`
+  q_matrix           a quasi-periodic plane wave (its spherical-wave
+                     coefficients, and its own Rayleigh-Bloch mode as a or b)
+                     leaves every discrepancy row zero, and the Cauchy rows
+                     of the wall it radiates through; the Gauss nodes against
+                     the closed form of the 2-node rule
 """
 from __future__ import annotations
 
@@ -49,7 +65,7 @@ import numpy as np
 import scipy.special as sps
 
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
-           "btilde", "btilde_columns", "n_harmonics"]
+           "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix"]
 
 
 def n_harmonics(p):
@@ -155,3 +171,91 @@ def btilde(ob, coll, p, q, modes=None, rows=None):
 def btilde_columns(p, n):
     """Column indices l^2 + l + n (l = |n| .. p) of mode n's non-zero block."""
     return np.array([l * l + l + n for l in range(abs(n), p + 1)], dtype=np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Q: the periodizing rows of the full system (Sec. 4.1, eq. full): the S
+# blocks (spherical waves on the walls) and the W blocks (Rayleigh-Bloch
+# waves on T and D, eqs. rb1-rb2 and T-nD)
+# ----------------------------------------------------------------------------
+
+def rb_modes(kx, ky, ex, ey, n0):
+    """The Rayleigh-Bloch wavevectors kappa = (kx + 2 pi m/ex, ky + 2 pi n/ey)
+    with |kappa| <= pi N0 (Sec. 4, after eq. Phinear), ordered by m, then n,
+    and k_z = +sqrt(k^2 - |kappa|^2) taken later (principal branch).
+    Returns an int array [n_rb][2] of (m, n)."""
+    R = math.pi * n0
+    out = []
+    mlo = math.floor((-R - kx) * ex / (2 * math.pi)) - 1
+    mhi = math.ceil((R - kx) * ex / (2 * math.pi)) + 1
+    nlo = math.floor((-R - ky) * ey / (2 * math.pi)) - 1
+    nhi = math.ceil((R - ky) * ey / (2 * math.pi)) + 1
+    for m in range(mlo, mhi + 1):
+        for n in range(nlo, nhi + 1):
+            kap_x = kx + 2 * math.pi * m / ex
+            kap_y = ky + 2 * math.pi * n / ey
+            if kap_x * kap_x + kap_y * kap_y <= R * R:
+                out.append((m, n))
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def wall_nodes(ex, ey, z0, m1):
+    """M1 x M1 product Gauss-Legendre nodes on the faces of the unit cell
+    U = [-ex/2, ex/2] x [-ey/2, ey/2] x [-z0, z0] (Sec. 4.1), per row block:
+    L/R share (y, z) (node a b -> y_a, z_b), B/F share (x, z), T/D share (x, y).
+    Returns dict of [M1*M1][3] points for L, R, B, F, T, D (row index a*M1 + b)."""
+    g, _ = np.polynomial.legendre.leggauss(m1)
+    A, Bn = np.meshgrid(g, g, indexing="ij")
+    a, b = A.ravel(), Bn.ravel()
+    one = np.ones_like(a)
+    return {
+        "L": np.stack([-ex / 2 * one, ey / 2 * a, z0 * b], -1),
+        "R": np.stack([ex / 2 * one, ey / 2 * a, z0 * b], -1),
+        "B": np.stack([ex / 2 * a, -ey / 2 * one, z0 * b], -1),
+        "F": np.stack([ex / 2 * a, ey / 2 * one, z0 * b], -1),
+        "T": np.stack([ex / 2 * a, ey / 2 * b, z0 * one], -1),
+        "D": np.stack([ex / 2 * a, ey / 2 * b, -z0 * one], -1),
+    }
+
+
+def q_matrix(k, p, kx, ky, ex, ey, z0, m1, n0):
+    """Q of eq. full for the spherical-wave and Rayleigh-Bloch unknowns
+    [d_lm; a; b]: 8 M1^2 rows in the printed order
+      u_R - alpha u_L, d_x u_R - alpha d_x u_L, u_F - beta u_B, d_y u_F - beta d_y u_B,
+      u_T, d_z u_T, u_D, d_z u_D
+    (eqs. qp1-qp4, T-nD with all normals along +x, +y, +z), alpha = e^{i kx ex},
+    beta = e^{i ky ey}; columns (p+1)^2 spherical waves (l^2 + l + m), then
+    a and b over `rb_modes` (the W blocks enter with a minus sign:
+    -e^{i(kap_x x + kap_y y)} and -i k_z e^{...} on T, -e^{...} and
+    +i k_z e^{...} on D). Returns (Q [rows][cols] complex, modes)."""
+    nodes = wall_nodes(ex, ey, z0, m1)
+    modes = rb_modes(kx, ky, ex, ey, n0)
+    nr = m1 * m1
+    nh = n_harmonics(p)
+    nrb = modes.shape[0]
+    alpha, beta = np.exp(1j * kx * ex), np.exp(1j * ky * ey)
+    Q = np.zeros((8 * nr, nh + 2 * nrb), dtype=np.complex128)
+    for l in range(p + 1):
+        ms = np.arange(-l, l + 1)[:, None]
+        cols = slice(l * l, (l + 1) ** 2)
+        U = {}
+        for f in "LRBFTD":
+            u, g = sph_wave_value_grad(l, ms, k, nodes[f][None])    # [2l+1][nr], [2l+1][nr][3]
+            U[f] = (u, g)
+        Q[0 * nr:1 * nr, cols] = (U["R"][0] - alpha * U["L"][0]).T
+        Q[1 * nr:2 * nr, cols] = (U["R"][1][..., 0] - alpha * U["L"][1][..., 0]).T
+        Q[2 * nr:3 * nr, cols] = (U["F"][0] - beta * U["B"][0]).T
+        Q[3 * nr:4 * nr, cols] = (U["F"][1][..., 1] - beta * U["B"][1][..., 1]).T
+        Q[4 * nr:5 * nr, cols] = U["T"][0].T
+        Q[5 * nr:6 * nr, cols] = U["T"][1][..., 2].T
+        Q[6 * nr:7 * nr, cols] = U["D"][0].T
+        Q[7 * nr:8 * nr, cols] = U["D"][1][..., 2].T
+    kap_x = kx + 2 * math.pi * modes[:, 0] / ex
+    kap_y = ky + 2 * math.pi * modes[:, 1] / ey
+    kz = np.sqrt((k * k - kap_x ** 2 - kap_y ** 2).astype(np.complex128))
+    for f, r0, c0, sgn in (("T", 4, nh, 1.0), ("D", 6, nh + nrb, -1.0)):
+        x = nodes[f]
+        E = np.exp(1j * (np.outer(x[:, 0], kap_x) + np.outer(x[:, 1], kap_y)))   # [nr][nrb]
+        Q[r0 * nr:(r0 + 1) * nr, c0:c0 + nrb] = -E
+        Q[(r0 + 1) * nr:(r0 + 2) * nr, c0:c0 + nrb] = -sgn * 1j * kz[None, :] * E
+    return Q, modes

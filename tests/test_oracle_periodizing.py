@@ -98,3 +98,44 @@ def test_btilde_reproduces_incident_modes(bc):
     for n in range(6):
         got = B[n] @ coef
         assert np.abs(got + fh[n]).max() < 1e-12 * np.abs(fh[0]).max()
+
+
+def test_gauss_nodes_two_point_rule():
+    nodes = OP.wall_nodes(2.0, 4.0, 3.0, 2)
+    g = 1.0 / math.sqrt(3.0)
+    assert np.allclose(np.sort(np.unique(nodes["T"][:, 0])), [-g, g], atol=1e-15)
+    assert np.allclose(np.sort(np.unique(nodes["L"][:, 2])), [-3 * g, 3 * g], atol=1e-15)
+    assert np.allclose(nodes["R"][:, 0], 1.0) and np.allclose(nodes["F"][:, 1], 2.0)
+
+
+@pytest.mark.parametrize("up", [True, False])
+def test_q_quasi_periodic_plane_wave(up):
+    """A plane wave e^{ik d.x} is quasi-periodic with alpha = e^{ik d_x e_x},
+    beta = e^{ik d_y e_y} (eq. per) and is the (0,0) Rayleigh-Bloch wave on
+    the wall it leaves through: with its spherical-wave coefficients and that
+    mode's amplitude, every discrepancy row (eqs. qp1-qp4) and the Cauchy rows
+    of that wall (eqs. T-nD) vanish, and the other wall's rows carry the wave."""
+    k, p, ex, ey, z0, m1, n0 = 3.0, 30, 2.0, 1.7, 1.5, 6, 3
+    d = np.array([0.36, -0.28, math.sqrt(1 - 0.36**2 - 0.28**2)])
+    if not up:
+        d[2] = -d[2]
+    kx, ky = k * d[0], k * d[1]
+    Q, modes = OP.q_matrix(k, p, kx, ky, ex, ey, z0, m1, n0)
+    nh, nrb, nr = OP.n_harmonics(p), modes.shape[0], m1 * m1
+    j0 = int(np.where((modes[:, 0] == 0) & (modes[:, 1] == 0))[0][0])
+    xi = np.zeros(nh + 2 * nrb, dtype=np.complex128)
+    xi[:nh] = OP.plane_wave_coefficients(p, d)
+    if up:
+        xi[nh + j0] = np.exp(1j * k * d[2] * z0)
+    else:
+        xi[nh + nrb + j0] = np.exp(-1j * k * d[2] * z0)
+    r = Q @ xi
+    nodes = OP.wall_nodes(ex, ey, z0, m1)
+    zero_blocks = [0, 1, 2, 3, 4, 5] if up else [0, 1, 2, 3, 6, 7]
+    for b in zero_blocks:
+        assert np.abs(r[b * nr:(b + 1) * nr]).max() < 1e-12, b
+    f = "D" if up else "T"
+    b0 = 6 if up else 4
+    u = np.exp(1j * k * (nodes[f] @ d))
+    assert np.abs(r[b0 * nr:(b0 + 1) * nr] - u).max() < 1e-12
+    assert np.abs(r[(b0 + 1) * nr:(b0 + 2) * nr] - 1j * k * d[2] * u).max() < 1e-12
