@@ -331,6 +331,48 @@ axi_status axi_btilde_count(const axi_operator *op, int32_t obs, int32_t p, size
 axi_status axi_fill_btilde(const axi_operator *op, int32_t obs, int32_t p, double *d_out,
                            size_t count, void *stream);
 
+/*
+ * The periodizing rows Q of the full system (Sec. 4.1, eq. full) for the
+ * spherical-wave and Rayleigh-Bloch unknowns [d; a; b] (Sec. 4, eqs. urep,
+ * rb1-rb2), the obstacle's exterior wavenumber k. The unit cell is
+ * [-ex/2, ex/2] x [-ey/2, ey/2] x [-z0, z0] around the obstacle; each face
+ * carries the m1 x m1 product Gauss-Legendre nodes (node (a, b) = row
+ * a m1 + b of each block: (y_a, z_b) on L and R, (x_a, z_b) on B and F,
+ * (x_a, y_b) on T and D). The 8 m1^2 rows, in blocks of m1^2:
+ *   u_R - alpha u_L, d_x u_R - alpha d_x u_L, u_F - beta u_B,
+ *   d_y u_F - beta d_y u_B, u_T, d_z u_T, u_D, d_z u_D
+ * (eqs. qp1-qp4, T-nD), alpha = e^{i kx ex}, beta = e^{i ky ey}. Columns:
+ * the (p + 1)^2 regular waves j_l(k r) Y_lm (column l^2 + l + m; Y_lm as in
+ * axi_fill_btilde), then the n_rb a's, then the n_rb b's over the Rayleigh-
+ * Bloch wavevectors kappa = (kx + 2 pi m / ex, ky + 2 pi n / ey) with
+ * |kappa| <= pi n0, ordered by m then n (axi_q_modes), k_z the principal
+ * root of k^2 - |kappa|^2; the a's carry -e^{i kappa.(x, y)} on u_T and
+ * -i k_z e^{...} on d_z u_T, the b's -e^{...} on u_D and +i k_z e^{...} on
+ * d_z u_D, zero elsewhere.
+ */
+typedef struct {
+  double kx, ky;   /* Bloch wavevector: k times the incident direction's x, y */
+  double ex, ey;   /* lattice periods (> 0) */
+  double z0;       /* half height of the cell (> 0), above the obstacle */
+  int32_t m1;      /* Gauss nodes per face direction: even, 2 .. 64 */
+  int32_t n0;      /* Rayleigh-Bloch cut |kappa| <= pi n0, n0 >= 0 */
+  int32_t p;       /* spherical-wave degree, 0 .. AXI_BTILDE_MAX_DEGREE */
+} axi_cell;
+
+/* Rows, columns and Rayleigh-Bloch count of Q for `cell`; AXI_ERR_ARG when a
+ * field is out of range (or the m range of the Rayleigh-Bloch set exceeds 128). */
+axi_status axi_q_shape(const axi_cell *cell, int64_t *rows, int64_t *cols, int64_t *n_rb);
+/* The Rayleigh-Bloch (m, n) pairs of the a and b columns, in order, into
+ * h_mn[2 * n_rb] (host); AXI_ERR_ARG if cap < n_rb. */
+axi_status axi_q_modes(const axi_cell *cell, int32_t *h_mn, int64_t cap);
+/* Q of obstacle `obs` into d_out, column-major with leading dimension
+ * ld >= rows (device memory owned by the caller, 16-byte aligned; every
+ * entry of the rows x cols block is written). Enqueued on `stream`; a
+ * non-finite entry sets the operator's status word.
+ * Errors: AXI_ERR_ARG, AXI_ERR_CUDA. */
+axi_status axi_fill_q(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
+                      int64_t ld, void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

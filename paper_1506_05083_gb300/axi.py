@@ -29,6 +29,27 @@ _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
 
 
+class Cell(C.Structure):
+    """axi_cell: the unit cell of the periodizing rows Q (include/axi_mfs.h)."""
+    _fields_ = [("kx", C.c_double), ("ky", C.c_double), ("ex", C.c_double), ("ey", C.c_double),
+                ("z0", C.c_double), ("m1", C.c_int32), ("n0", C.c_int32), ("p", C.c_int32)]
+
+
+def q_shape(cell: Cell):
+    """axi_q_shape: (rows, cols, n_rb) of Q for the cell."""
+    r, c, n = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().axi_q_shape(C.byref(cell), C.byref(r), C.byref(c), C.byref(n)), "axi_q_shape")
+    return r.value, c.value, n.value
+
+
+def q_modes(cell: Cell) -> np.ndarray:
+    """axi_q_modes: the Rayleigh-Bloch (m, n) of the a and b columns, [n_rb][2]."""
+    _, _, n = q_shape(cell)
+    out = np.zeros((max(n, 1), 2), dtype=np.int32)
+    _check(lib().axi_q_modes(C.byref(cell), C.c_void_p(out.ctypes.data), n), "axi_q_modes")
+    return out[:n]
+
+
 class _Obstacle(C.Structure):
     _fields_ = [("bc", C.c_int32), ("M", C.c_int32), ("N", C.c_int32), ("P", C.c_int32),
                 ("q", C.c_int32), ("k", C.c_double), ("k_minus", C.c_double),
@@ -76,6 +97,9 @@ SIGNATURES = [
     ("axi_diag_wait_timeout", C.c_int, [_vp, C.c_int64, _vp]),
     ("axi_fill_modes", C.c_int, [_vp, C.c_int32, _vp, _vp]),
     ("axi_btilde_count", C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_q_shape", C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    ("axi_q_modes", C.c_int, [_vp, _vp, C.c_int64]),
+    ("axi_fill_q", C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp]),
     ("axi_fill_btilde", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
@@ -348,6 +372,19 @@ class Operator:
             blocks.append(out[off:off + sz].view(p + 1 - m, s.rows))
             off += sz
         return blocks, out
+
+    def q_matrix(self, cell: Cell, obs=0, out=None, stream=None):
+        """axi_fill_q: the periodizing rows Q for the cell as a [cols][rows]
+        complex128 tensor (column-major Q)."""
+        rows, cols, _ = q_shape(cell)
+        if out is None:
+            out = torch.empty((cols, rows), dtype=torch.complex128, device=self.workspace.device)
+        if out.dtype != torch.complex128 or not out.is_contiguous() or out.shape[0] < cols \
+                or out.shape[1] < rows:
+            raise ValueError("q_matrix: out must be a contiguous complex128 [cols][ld >= rows] tensor")
+        _check(lib().axi_fill_q(self._op, obs, C.byref(cell), _dev(out), out.shape[1], _stream(stream)),
+               "axi_fill_q")
+        return out
 
     def factors(self, obs=0):
         """(A [D][cols][rows], tau [D][cols], T [D][npanels][nb][nb] col-major) views."""

@@ -918,6 +918,31 @@ axi_status axi_fill_btilde(const axi_operator *op, int32_t obs, int32_t p, doubl
   return cuda_status(axi::launch_btilde(op->d_obs, d, obs, p, d_out, static_cast<cudaStream_t>(stream)));
 }
 
+axi_status axi_q_shape(const axi_cell *cell, int64_t *rows, int64_t *cols, int64_t *n_rb) {
+  if (!cell || !rows || !cols || !n_rb) return AXI_ERR_ARG;
+  long long r = 0, c = 0, n = 0;
+  if (!axi::q_shape(*cell, r, c, n)) return AXI_ERR_ARG;
+  *rows = r; *cols = c; *n_rb = n;
+  return AXI_OK;
+}
+
+axi_status axi_q_modes(const axi_cell *cell, int32_t *h_mn, int64_t cap) {
+  if (!cell || !h_mn) return AXI_ERR_ARG;
+  return axi::q_modes(*cell, reinterpret_cast<int *>(h_mn), cap) ? AXI_OK : AXI_ERR_ARG;
+}
+
+axi_status axi_fill_q(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
+                      int64_t ld, void *stream) {
+  if (!op || !cell || !d_out || obs < 0 || obs >= (int)op->plan->obs.size() ||
+      (reinterpret_cast<uintptr_t>(d_out) & 15))
+    return AXI_ERR_ARG;
+  long long r = 0, c = 0, n = 0;
+  if (!axi::q_shape(*cell, r, c, n) || ld < r) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  return cuda_status(axi::launch_q(op->d_obs, d, obs, *cell, reinterpret_cast<double2 *>(d_out), ld,
+                                   static_cast<cudaStream_t>(stream)));
+}
+
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
   if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;

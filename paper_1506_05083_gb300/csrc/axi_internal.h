@@ -211,6 +211,12 @@ cudaError_t launch_qr_panel(const ObsDev *d_obs, const int *d_task_obs, const in
 size_t btilde_count(const ObsDev &h, int p);
 cudaError_t launch_btilde(const ObsDev *d_obs, const ObsDev &h, int oi, int p, double *out,
                           cudaStream_t st);
+// The periodizing rows Q (periodize.cu): shape and Rayleigh-Bloch modes of a
+// cell (false when a field is out of range), and the fill.
+bool q_shape(const axi_cell &c, long long &rows, long long &cols, long long &nrb);
+bool q_modes(const axi_cell &c, int *mn, long long cap);
+cudaError_t launch_q(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,
+                     long long ld, cudaStream_t st);
 // The fixed-point panel (qr_panel_fx.cu): whether a panel of `rows` rows fits
 // one CTA of `threads` (128 or 256), and its launch.
 bool panel_fx_fits(int rows, int threads);

@@ -159,3 +159,23 @@ def test_plan_tuning_json(axi):
         assert L.axi_plan_get_tuning(plan, buf, 8) == -1          # buffer too small
     finally:
         L.axi_plan_destroy(plan)
+
+
+def test_q_shape_and_modes_host():
+    """The periodizing rows' host logic (no GPU): the Rayleigh-Bloch set and
+    its order equal the oracle's enumeration, the shape follows, and
+    out-of-range cells are refused."""
+    from paper_1506_05083_gb300 import axi
+    from oracle import periodizing as OP
+    period = 13 * 2 * math.pi / 25.0
+    for (kx, ky, ex, ey, z0, m1, n0, p) in ((1.0, -0.8, 2.0, 1.7, 1.5, 6, 3, 12),
+                                            (25 * 0.36, -25 * 0.28, period, period, 2.0, 32, 11, 48),
+                                            (0.0, 0.0, 1.0, 3.0, 0.7, 2, 0, 0)):
+        cell = axi.Cell(kx, ky, ex, ey, z0, m1, n0, p)
+        modes = OP.rb_modes(kx, ky, ex, ey, n0)
+        assert np.array_equal(axi.q_modes(cell), modes)
+        assert axi.q_shape(cell) == (8 * m1 * m1, (p + 1) ** 2 + 2 * len(modes), len(modes))
+    for bad in (axi.Cell(0, 0, 1, 1, 1, 7, 3, 4), axi.Cell(0, 0, 1, 1, 1, 66, 3, 4),
+                axi.Cell(0, 0, -1, 1, 1, 6, 3, 4), axi.Cell(0, 0, 1, 1, 1, 6, 3, 256)):
+        with pytest.raises(axi.AxiError):
+            axi.q_shape(bad)

@@ -50,3 +50,33 @@ def test_btilde_parity(name, p, rows):
         want = ref[n][:, OP.btilde_columns(p, n)]
         assert np.abs(want.imag).max() < 1e-13 * scale
         assert np.abs(got - want.real).max() < 1e-12 * scale, n
+
+
+def _cell(axi, k, d, ex, ey, z0, m1, n0, p):
+    return axi.Cell(k * d[0], k * d[1], ex, ey, z0, m1, n0, p)
+
+
+@pytest.mark.parametrize("name", ["small", "cup"])
+def test_q_parity(name):
+    """The periodizing rows Q (S and W blocks) against the oracle's q_matrix:
+    the same Rayleigh-Bloch modes in the same order and every entry within
+    1e-12 of the matrix scale. The cup case has the bench's k, p and N0 with
+    fewer wall nodes."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, coll = _case(name)
+    if name == "small":
+        k, ex, ey, z0, m1, n0, p = ob.k, 2.0, 1.7, 1.5, 6, 3, 12
+    else:
+        period = 13 * 2 * np.pi / ob.k
+        k, ex, ey, z0, m1, n0, p = ob.k, period, period, 1.2 + period / 4, 8, 11, 48
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])], prec=axi.PREC_FP64)
+    cell = _cell(axi, k, d, ex, ey, z0, m1, n0, p)
+    Qg = op.q_matrix(cell)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    Qo, modes = OP.q_matrix(k, p, k * d[0], k * d[1], ex, ey, z0, m1, n0)
+    assert np.array_equal(axi.q_modes(cell), modes)
+    Q = Qg.cpu().numpy().T
+    assert Q.shape == Qo.shape
+    assert np.abs(Q - Qo).max() < 1e-12 * np.abs(Qo).max()
