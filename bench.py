@@ -23,8 +23,9 @@ cores; its coefficients also give the line's parity errors e_bd and e_ff.
 
 `--impl reference` times the oracle as the reference arm: each step is one
 distinct mode's share of the workload (see reference_step). `--workload
-smooth | batched | cup_near | cup_btilde` prints the other workloads' lines
-(cup_btilde: the periodizing scheme's spherical-wave block B~ of the cup). Multi-GPU
+smooth | batched | cup_near | cup_btilde | cup_q` prints the other workloads'
+lines (cup_btilde, cup_q: the periodizing scheme's spherical-wave block B~
+and rows Q for the cup). Multi-GPU
 (torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
 tasks are independent), value sums the ranks' work over the slowest rank's
 time ("weak" scaling), with no collective on the data path.
@@ -664,6 +665,91 @@ def run_extra_workload(args):
     print(json.dumps(line))
 
 
+def cup_cell(axi, wl):
+    """The cup's unit cell for the periodizing rows Q: lattice period 13
+    wavelengths at k = 25, z0 = the obstacle's height (1.2) plus a quarter
+    period, M1 = 4 k / pi rounded up to even (32), N0 = ceil(k / pi) + 3 (11),
+    p = 48, Bloch wavevector from the workload's first incident direction."""
+    k = 25.0
+    period = 13 * 2 * math.pi / k
+    d = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)[0]
+    m1 = int(math.ceil(4 * k / math.pi))
+    m1 += m1 & 1
+    return axi.Cell(k * d[0], k * d[1], period, period, 1.2 + period / 4, m1,
+                    int(math.ceil(k / math.pi)) + 3, 48)
+
+
+def run_q(args):
+    """The periodizing rows Q (S and W blocks, Sec. 4.1 eq. full) of the cup's
+    unit cell (cup_cell): device time of one fill through a CUDA graph replay
+    (L2 flushed), its DRAM roofline, and the oracle's q_matrix on 4 x 4
+    nodes per face on the host, scaled to the cell's nodes."""
+    import torch
+    from paper_1506_05083_gb300 import axi
+    from oracle import periodizing as OP
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=axi.PREC_FP64)
+    cell = cup_cell(axi, wl)
+    rows, cols, nrb = axi.q_shape(cell)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    buf = op.q_matrix(cell)
+    for _ in range(args.warmup):
+        op.q_matrix(cell, out=buf)
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            op.q_matrix(cell, out=buf)
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ts = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    pk, pk_src = peaks()
+    nbytes = 16.0 * rows * cols
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    line = {"metric": "periodizing rows Q fill time (Sec. 4.1, eq. full)", "value": ms * 1e3, "unit": "us",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cup_k25_cell13_M1_{cell.m1}_N0_{cell.n0}_p{cell.p}_Q",
+                       "rows": rows, "cols": cols, "n_rb": nrb, "m1": cell.m1, "n0": cell.n0,
+                       "p": cell.p, "ex": cell.ex, "z0": cell.z0, "launch": "CUDA graph replay",
+                       "l2": "flushed (256 MB write) before each timed step"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "traffic": None,
+                         "work": "Q written once (16 B per entry); the S blocks' FP64 recurrences, "
+                                 "not DRAM, bound the fill",
+                         "peak_source": f"hbm_gbs of {pk_src}"},
+            "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": op.status()}
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        OP.q_matrix(ob.k, cell.p, cell.kx, cell.ky, cell.ex, cell.ey, cell.z0, 4, cell.n0)
+        sec = time.perf_counter() - t0
+        full_us = sec * (cell.m1 * cell.m1) / 16.0 * 1e6
+        line["cpu_baseline"] = {"value": full_us, "unit": "us", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"q_matrix with 4 x 4 nodes per face (128 of {rows} rows), "
+                                          "scaled to the cell's nodes"}
+    print(json.dumps(line))
+
+
 def run_btilde(args):
     """The periodizing scheme's spherical-wave block B~ (Sec. 4.1) of the cup
     at degree p = 48: device time of one fill of all mode blocks (CUDA events,
@@ -759,16 +845,19 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup",
-                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde"],
-                    help="cup (default, the headline), smooth; batched, cup_near and cup_btilde "
-                         "(the periodizing scheme's spherical-wave block) print their own "
-                         "device-timed lines")
+                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q"],
+                    help="cup (default, the headline), smooth; batched, cup_near, cup_btilde and "
+                         "cup_q (the periodizing scheme's spherical-wave block B~ and rows Q) "
+                         "print their own device-timed lines")
     args = ap.parse_args()
     if args.workload in ("batched", "cup_near"):
         run_extra_workload(args)
         return
     if args.workload == "cup_btilde":
         run_btilde(args)
+        return
+    if args.workload == "cup_q":
+        run_q(args)
         return
     wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
     if args.impl == "reference":
