@@ -42,6 +42,14 @@ beta = e^{i ky ey}; the Rayleigh-Bloch set is |kappa| <= pi N0, ordered by
 m then n; k_z takes the principal square root (+i sqrt for evanescent
 waves).
 
+C (eq. full's C block, Neumann): the same rows applied to the ring part of
+eq. urep with the nine phased images of eq. Phinear, by definition on both
+walls of each pair. Readings: the ring integrals use the P-node trapezoid
+rule with absolute nodes 2 pi s / P (the point sources of Sec. 4.1, "q = P
+is sufficient" for distant interactions) and the repository's mode sign
+e^{+i n psi} (`point_strengths`); columns follow the operator's
+coefficients, mode n at n mod P.
+
 Pins (tests/test_oracle_periodizing.py):
   sph_jn             closed forms of j_0, j_1, j_2 and j_0' = -j_1
   sph_y              closed forms of Y_00, Y_1m, Y_22 (fixes the phase)
@@ -56,6 +64,9 @@ Pins (tests/test_oracle_periodizing.py):
                      leaves every discrepancy row zero, and the Cauchy rows
                      of the wall it radiates through; the Gauss nodes against
                      the closed form of the 2-node rule
+  c_matrix           C times a coefficient vector equals the phased image
+                     sums of `potential` (value and Cartesian derivatives) at
+                     the shifted wall nodes, combined into the same rows
 """
 from __future__ import annotations
 
@@ -65,7 +76,8 @@ import numpy as np
 import scipy.special as sps
 
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
-           "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix"]
+           "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix",
+           "c_matrix"]
 
 
 def n_harmonics(p):
@@ -259,3 +271,62 @@ def q_matrix(k, p, kx, ky, ex, ey, z0, m1, n0):
         Q[r0 * nr:(r0 + 1) * nr, c0:c0 + nrb] = -E
         Q[(r0 + 1) * nr:(r0 + 2) * nr, c0:c0 + nrb] = -sgn * 1j * kz[None, :] * E
     return Q, modes
+
+
+# ----------------------------------------------------------------------------
+# C: the periodizing rows' dependence on the ring coefficients eta (Sec. 4.1,
+# eq. full and the C-block paragraph), Neumann obstacles
+# ----------------------------------------------------------------------------
+
+def _ring_modes(k, src, P, X, axis=None):
+    """Phi_nj(X) (or its Cartesian derivative along `axis`) for every mode and
+    proxy ring, by the P-node trapezoid rule with absolute nodes
+    psi_s = 2 pi s / P (the point sources of Sec. 4.1):
+      Phi_nj(x) = (1/P) sum_s G_k(x, y_j(psi_s)) e^{+i n psi_s}
+    (the repository's mode convention, as in `point_strengths`).
+    X [T][3] -> [T][P (n mod P)][N]."""
+    N = src.shape[0]
+    psi = 2.0 * math.pi * np.arange(P) / P
+    Y = np.stack([src[:, 0][:, None] * np.cos(psi), src[:, 0][:, None] * np.sin(psi),
+                  np.broadcast_to(src[:, 1][:, None], (N, P))], -1)            # [N][P][3]
+    D = X[:, None, None, :] - Y[None]                                           # [T][N][P][3]
+    R = np.linalg.norm(D, axis=-1)
+    e = np.exp(1j * k * R)
+    if axis is None:
+        K = e / (4.0 * math.pi * R)
+    else:
+        K = D[..., axis] * (1j * k * R - 1.0) * e / (4.0 * math.pi * R ** 3)
+    n = np.arange(P)
+    n = np.where(n > P // 2, n - P, n)
+    E = np.exp(1j * np.outer(psi, n)) / P                                       # [P s][P n]
+    return np.einsum("tjs,sn->tnj", K, E)
+
+
+def c_matrix(ob, src, kx, ky, ex, ey, z0, m1, row_pairs=None):
+    """C of eq. full for a Neumann obstacle: the rows of `q_matrix` applied to
+    the ring part of u (eq. urep), u = sum_{n,j} c_nj Phi^near_nj with the
+    3 x 3 phased images of eq. Phinear,
+      Phi^near_nj(x) = sum_{|a|,|b| <= 1} alpha^a beta^b Phi_nj(x - a e_x - b e_y),
+    evaluated by its definition on both walls of each pair (18 terms, then
+    u_R - alpha u_L etc.; the cancellation of Sec. 4.1 is left to the
+    arithmetic). Columns: mode n at n mod P, then ring j (col = (n mod P) N + j),
+    the operator's coefficient order. row_pairs: indices a*M1 + b of the node
+    pairs to form (default all); returns [8 len][P N], blocks as q_matrix."""
+    P, k = ob.P, ob.k
+    nodes = wall_nodes(ex, ey, z0, m1)
+    idx = np.arange(m1 * m1) if row_pairs is None else np.asarray(row_pairs)
+    alpha, beta = np.exp(1j * kx * ex), np.exp(1j * ky * ey)
+
+    def near(X, axis=None):
+        out = 0.0
+        for a in (-1, 0, 1):
+            for b in (-1, 0, 1):
+                sh = np.array([a * ex, b * ey, 0.0])
+                out = out + alpha ** a * beta ** b * _ring_modes(k, src, P, X - sh, axis)
+        return out.reshape(X.shape[0], -1)                                      # [T][P N]
+
+    L, R, B, F, T, Dn = (nodes[f][idx] for f in "LRBFTD")
+    blocks = [near(R) - alpha * near(L), near(R, 0) - alpha * near(L, 0),
+              near(F) - beta * near(B), near(F, 1) - beta * near(B, 1),
+              near(T), near(T, 2), near(Dn), near(Dn, 2)]
+    return np.concatenate(blocks, axis=0)

@@ -139,3 +139,37 @@ def test_q_quasi_periodic_plane_wave(up):
     u = np.exp(1j * k * (nodes[f] @ d))
     assert np.abs(r[b0 * nr:(b0 + 1) * nr] - u).max() < 1e-12
     assert np.abs(r[(b0 + 1) * nr:(b0 + 2) * nr] - 1j * k * d[2] * u).max() < 1e-12
+
+
+def test_c_rows_match_potential_image_sums():
+    """C c equals the 3 x 3 phased image sums of the field `potential`
+    computes from the same coefficients (point strengths, point sources;
+    pinned against the sphere series), combined into the discrepancy and
+    Cauchy rows."""
+    wl = synth.small_case(seed=7, k=3.0, M=40, N=32, P=16)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    kx, ky, ex, ey, z0, m1 = 1.1, -0.7, 2.6, 2.3, 1.6, 4
+    C = OP.c_matrix(ob, src, kx, ky, ex, ey, z0, m1)
+    rng = np.random.default_rng(5)
+    coef = rng.normal(size=(1, ob.P, ob.N)) + 1j * rng.normal(size=(1, ob.P, ob.N))
+    got = C @ coef.reshape(-1)
+    nodes = OP.wall_nodes(ex, ey, z0, m1)
+    alpha, beta = np.exp(1j * kx * ex), np.exp(1j * ky * ey)
+
+    def u(X, axis=None):
+        out = 0.0
+        for a in (-1, 0, 1):
+            for b in (-1, 0, 1):
+                nrm = None
+                if axis is not None:
+                    nrm = np.zeros_like(X)
+                    nrm[:, axis] = 1.0
+                out = out + alpha ** a * beta ** b * O.potential(
+                    ob, src, coef, X - np.array([a * ex, b * ey, 0.0]), qe=ob.P, normals=nrm)[0]
+        return out
+
+    want = np.concatenate([u(nodes["R"]) - alpha * u(nodes["L"]), u(nodes["R"], 0) - alpha * u(nodes["L"], 0),
+                           u(nodes["F"]) - beta * u(nodes["B"]), u(nodes["F"], 1) - beta * u(nodes["B"], 1),
+                           u(nodes["T"]), u(nodes["T"], 2), u(nodes["D"]), u(nodes["D"], 2)])
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
