@@ -373,6 +373,27 @@ axi_status axi_q_modes(const axi_cell *cell, int32_t *h_mn, int64_t cap);
 axi_status axi_fill_q(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
                       int64_t ld, void *stream);
 
+/*
+ * The C block of the full system (Sec. 4.1, eq. full; Neumann obstacles): the
+ * rows of axi_fill_q applied to the ring part of eq. urep, u = sum_{n,j}
+ * c_nj Phi^near_nj, Phi^near the 3 x 3 phased images of eq. Phinear with
+ * alpha^a beta^b, Phi_nj(x) = (1/P) sum_s G_k(x, y_j(2 pi s / P))
+ * e^{+i n 2 pi s / P} (the P point sources per ring of Sec. 4.1; the mode
+ * sign of the operator's coefficients). Rows as axi_fill_q; columns in the
+ * operator's coefficient order, column (n mod P) N + j. Between the walls of
+ * a pair the near images cancel (Sec. 4.1): the discrepancy rows are formed
+ * from the six distant ones, T and D from all nine.
+ * axi_c_shape writes rows (8 m1^2) and columns (P N); axi_fill_c writes the
+ * block column-major into d_out with leading dimension ld >= rows (caller-
+ * owned device memory, 16-byte aligned). Enqueued on `stream`.
+ * Errors: AXI_ERR_ARG, AXI_ERR_UNSUPPORTED (transmission obstacles),
+ * AXI_ERR_CUDA.
+ */
+axi_status axi_c_shape(const axi_operator *op, int32_t obs, const axi_cell *cell, int64_t *rows,
+                       int64_t *cols);
+axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
+                      int64_t ld, void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

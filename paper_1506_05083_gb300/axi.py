@@ -100,6 +100,8 @@ SIGNATURES = [
     ("axi_q_shape", C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("axi_q_modes", C.c_int, [_vp, _vp, C.c_int64]),
     ("axi_fill_q", C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp]),
+    ("axi_c_shape", C.c_int, [_vp, C.c_int32, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    ("axi_fill_c", C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp]),
     ("axi_fill_btilde", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
@@ -384,6 +386,20 @@ class Operator:
             raise ValueError("q_matrix: out must be a contiguous complex128 [cols][ld >= rows] tensor")
         _check(lib().axi_fill_q(self._op, obs, C.byref(cell), _dev(out), out.shape[1], _stream(stream)),
                "axi_fill_q")
+        return out
+
+    def c_block(self, cell: Cell, obs=0, out=None, stream=None):
+        """axi_fill_c: the C block for the cell as a [cols][rows] complex128
+        tensor (column-major C; column (n mod P) N + j)."""
+        r, c = C.c_int64(), C.c_int64()
+        _check(lib().axi_c_shape(self._op, obs, C.byref(cell), C.byref(r), C.byref(c)), "axi_c_shape")
+        if out is None:
+            out = torch.empty((c.value, r.value), dtype=torch.complex128, device=self.workspace.device)
+        if out.dtype != torch.complex128 or not out.is_contiguous() or out.shape[0] < c.value \
+                or out.shape[1] < r.value:
+            raise ValueError("c_block: out must be a contiguous complex128 [cols][ld >= rows] tensor")
+        _check(lib().axi_fill_c(self._op, obs, C.byref(cell), _dev(out), out.shape[1], _stream(stream)),
+               "axi_fill_c")
         return out
 
     def factors(self, obs=0):

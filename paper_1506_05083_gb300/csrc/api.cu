@@ -943,6 +943,30 @@ axi_status axi_fill_q(const axi_operator *op, int32_t obs, const axi_cell *cell,
                                    static_cast<cudaStream_t>(stream)));
 }
 
+axi_status axi_c_shape(const axi_operator *op, int32_t obs, const axi_cell *cell, int64_t *rows,
+                       int64_t *cols) {
+  if (!op || !cell || !rows || !cols || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (d.bc != AXI_BC_NEUMANN) return AXI_ERR_UNSUPPORTED;
+  long long r = 0, c = 0;
+  if (!axi::c_shape(d, *cell, r, c)) return AXI_ERR_ARG;
+  *rows = r; *cols = c;
+  return AXI_OK;
+}
+
+axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
+                      int64_t ld, void *stream) {
+  if (!op || !cell || !d_out || obs < 0 || obs >= (int)op->plan->obs.size() ||
+      (reinterpret_cast<uintptr_t>(d_out) & 15))
+    return AXI_ERR_ARG;
+  const ObsDev &d = op->plan->obs[obs].dev;
+  if (d.bc != AXI_BC_NEUMANN) return AXI_ERR_UNSUPPORTED;
+  long long r = 0, c = 0;
+  if (!axi::c_shape(d, *cell, r, c) || ld < r) return AXI_ERR_ARG;
+  return cuda_status(axi::launch_c(op->d_obs, d, obs, *cell, reinterpret_cast<double2 *>(d_out), ld,
+                                   static_cast<cudaStream_t>(stream)));
+}
+
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
   if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;

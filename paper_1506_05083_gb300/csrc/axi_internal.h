@@ -217,6 +217,10 @@ bool q_shape(const axi_cell &c, long long &rows, long long &cols, long long &nrb
 bool q_modes(const axi_cell &c, int *mn, long long cap);
 cudaError_t launch_q(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,
                      long long ld, cudaStream_t st);
+// The C block (periodize.cu; Neumann obstacles): shape for a cell, and the fill.
+bool c_shape(const ObsDev &h, const axi_cell &c, long long &rows, long long &cols);
+cudaError_t launch_c(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,
+                     long long ld, cudaStream_t st);
 // The fixed-point panel (qr_panel_fx.cu): whether a panel of `rows` rows fits
 // one CTA of `threads` (128 or 256), and its launch.
 bool panel_fx_fits(int rows, int threads);

@@ -48,6 +48,7 @@
 #include <cmath>
 
 #include "axi_internal.h"
+#include "fft.cuh"
 
 namespace axi {
 namespace {
@@ -428,6 +429,141 @@ q_w_kernel(const ObsDev *__restrict__ obs_arr, int oi, QCell cell, double2 *__re
   }
 }
 
+// ---------------------------------------------------------------------------
+// C, the periodizing rows applied to the ring part of eq. urep (Neumann
+// obstacles): u = sum_{n,j} c_nj Phi^near_nj, Phi^near the 3 x 3 phased
+// images of eq. Phinear, Phi_nj(x) = (1/P) sum_s G(x, y_j(2 pi s/P))
+// e^{+i n 2 pi s/P} (the P point sources per ring of Sec. 4.1). With
+// u(x) = sum_{a,b} alpha^a beta^b Psi(x - a e_x - b e_y) the near terms cancel
+// between the walls of a pair (Sec. 4.1), leaving six distant ones:
+//   u_R - alpha u_L = sum_b beta^b (alpha^-1 Psi(x_L + 2 e_x - b e_y)
+//                                   - alpha^2 Psi(x_L - e_x - b e_y)),
+//   u_F - beta u_B  = sum_a alpha^a (beta^-1 Psi(x_B - a e_x + 2 e_y)
+//                                    - beta^2 Psi(x_B - a e_x - e_y)),
+// and the same for the derivative rows; T and D keep all nine images. One
+// warp per (row pair, ring j): per image point the lanes form the P samples
+// of G and of one Cartesian derivative of G, two warp FFTs give every mode,
+// and the image's coefficient times both is added in shared memory; the
+// row pair's two rows are written for all P modes (column (n mod P) N + j).
+// ---------------------------------------------------------------------------
+
+constexpr int kCWarps = 4;
+
+__global__ void __launch_bounds__(32 * kCWarps)
+c_kernel(const ObsDev *__restrict__ obs_arr, int oi, QCell cell, double2 *__restrict__ out, long long ld) {
+  const ObsDev &o = obs_arr[oi];
+  const int P = o.P, N = o.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ double2 c_sh[];
+  double2 *tw = c_sh;                                           // [P] e^{-2 pi i r / P}
+  int *perm = reinterpret_cast<int *>(c_sh + P);                // [P]
+  double2 *ws = c_sh + P + (P + 1) / 2 + (size_t)warp * 4 * P;  // value, derivative, their sums
+  double2 *sv = ws, *sd = ws + P, *av = ws + 2 * P, *ad = ws + 3 * P;
+  const bool fft = o.fft_nst > 0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    tw[i] = o.tw_P[i];
+    perm[i] = fft ? o.fft_perm[i] : i;
+  }
+  __syncthreads();
+  const int m1 = cell.m1, nr = m1 * m1;
+  const long long w = (long long)blockIdx.x * kCWarps + warp;   // row pair fastest, then ring
+  if (w >= 4LL * nr * N) return;                                // whole warp; no block barriers below
+  const int rp = (int)(w % (4LL * nr)), j = (int)(w / (4LL * nr));
+  const int grp = rp / nr, idx = rp - grp * nr, ia = idx / m1, ib = idx - ia * m1;
+  const double ga = cell.g[ia], gb = cell.g[ib];
+  const double ex = cell.ex, ey = cell.ey, hx = 0.5 * ex, hy = 0.5 * ey, z0 = cell.z0;
+  const double k = o.k, rs = o.src[2 * j], zs = o.src[2 * j + 1];
+  const double wgt = 1.0 / (4.0 * 3.14159265358979323846 * P);
+  double2 al, be;
+  sincos(cell.kx * ex, &al.y, &al.x);
+  sincos(cell.ky * ey, &be.y, &be.x);
+  const double2 al_inv = make_double2(al.x, -al.y), be_inv = make_double2(be.x, -be.y);
+  const double2 al2 = cmul2(al, al), be2 = cmul2(be, be);
+  for (int n = lane; n < P; n += 32) {
+    av[n] = make_double2(0.0, 0.0);
+    ad[n] = make_double2(0.0, 0.0);
+  }
+  const int axis = grp == 0 ? 0 : grp == 1 ? 1 : 2;
+  const int npts = grp < 2 ? 6 : 9;
+  bool finite = true;
+  for (int t = 0; t < npts; ++t) {
+    double x, y, z;
+    double2 cf;
+    if (grp == 0) {                                  // b = t % 3 - 1; far right / far left images
+      const int b = t % 3 - 1;
+      const double2 bb = b < 0 ? be_inv : b > 0 ? be : make_double2(1.0, 0.0);
+      const bool right = t < 3;
+      x = right ? -hx + 2.0 * ex : -hx - ex;
+      y = hy * ga - b * ey;
+      z = z0 * gb;
+      cf = right ? cmul2(al_inv, bb) : cmul2(make_double2(-al2.x, -al2.y), bb);
+    } else if (grp == 1) {
+      const int a = t % 3 - 1;
+      const double2 aa = a < 0 ? al_inv : a > 0 ? al : make_double2(1.0, 0.0);
+      const bool front = t < 3;
+      x = hx * ga - a * ex;
+      y = front ? -hy + 2.0 * ey : -hy - ey;
+      z = z0 * gb;
+      cf = front ? cmul2(aa, be_inv) : cmul2(aa, make_double2(-be2.x, -be2.y));
+    } else {
+      const int a = t / 3 - 1, b = t % 3 - 1;
+      const double2 aa = a < 0 ? al_inv : a > 0 ? al : make_double2(1.0, 0.0);
+      const double2 bb = b < 0 ? be_inv : b > 0 ? be : make_double2(1.0, 0.0);
+      x = hx * ga - a * ex;
+      y = hy * gb - b * ey;
+      z = grp == 2 ? z0 : -z0;
+      cf = cmul2(aa, bb);
+    }
+    for (int sidx = lane; sidx < P; sidx += 32) {
+      // y_j(psi_s) = (rs cos psi_s, rs sin psi_s, zs); cos, sin from the twiddle table
+      const double dx = x - rs * tw[sidx].x, dy = y + rs * tw[sidx].y, dz = z - zs;
+      const double R2 = dx * dx + dy * dy + dz * dz;
+      const double iR = rsqrt(R2), R = R2 * iR, kR = k * R;
+      double sn, cs;
+      sincos(kR, &sn, &cs);
+      const double g = wgt * iR;
+      sv[sidx] = make_double2(cs * g, sn * g);
+      const double dc = axis == 0 ? dx : axis == 1 ? dy : dz;
+      const double f = dc * g * iR * iR;               // (x - y)_c (ikR - 1) e^{ikR} / (4 pi P R^3)
+      sd[sidx] = make_double2(f * fma(-kR, sn, -cs), f * fma(kR, cs, -sn));
+    }
+    __syncwarp();
+    if (fft) {
+      fft::warp_fft(sv, P, tw, o.fft_rad, o.fft_nst, lane);
+      fft::warp_fft(sd, P, tw, o.fft_rad, o.fft_nst, lane);
+      // sum_s a_s e^{+2 pi i n s / P} is the forward transform at -n mod P
+      for (int n = lane; n < P; n += 32) {
+        const int pos = perm[(P - n) % P];
+        const double2 v = cmul2(cf, sv[pos]), d = cmul2(cf, sd[pos]);
+        av[n] = make_double2(av[n].x + v.x, av[n].y + v.y);
+        ad[n] = make_double2(ad[n].x + d.x, ad[n].y + d.y);
+      }
+    } else {                                          // direct sums for P with other prime factors
+      for (int n = lane; n < P; n += 32) {
+        double2 v = make_double2(0.0, 0.0), d = make_double2(0.0, 0.0);
+        for (int sidx = 0; sidx < P; ++sidx) {
+          const double2 e = make_double2(tw[((long long)n * sidx) % P].x, -tw[((long long)n * sidx) % P].y);
+          v = make_double2(v.x + sv[sidx].x * e.x - sv[sidx].y * e.y, v.y + sv[sidx].x * e.y + sv[sidx].y * e.x);
+          d = make_double2(d.x + sd[sidx].x * e.x - sd[sidx].y * e.y, d.y + sd[sidx].x * e.y + sd[sidx].y * e.x);
+        }
+        v = cmul2(cf, v);
+        d = cmul2(cf, d);
+        av[n] = make_double2(av[n].x + v.x, av[n].y + v.y);
+        ad[n] = make_double2(ad[n].x + d.x, ad[n].y + d.y);
+      }
+    }
+    __syncwarp();
+  }
+  const long long r0 = (long long)(2 * grp) * nr + idx, r1 = r0 + nr;
+  for (int n = lane; n < P; n += 32) {
+    const long long col = (long long)n * N + j;
+    out[col * ld + r0] = av[n];
+    out[col * ld + r1] = ad[n];
+    finite = finite && isfinite(av[n].x + av[n].y + ad[n].x + ad[n].y);
+  }
+  if (!__all_sync(0xffffffffu, finite) && lane == 0) atomicOr(o.status, kStatNonFinite);
+}
+
 }  // namespace
 
 size_t btilde_count(const ObsDev &h, int p) {
@@ -543,6 +679,28 @@ cudaError_t launch_q(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cel
   if (e != cudaSuccess || q.nrb == 0) return e;
   q_w_kernel<<<(2 * q.nrb + kWWarps - 1) / kWWarps, 32 * kWWarps, 0, st>>>(
       d_obs, oi, q, out, ld, (long long)(p + 1) * (p + 1));
+  return cudaGetLastError();
+}
+
+bool c_shape(const ObsDev &h, const axi_cell &c, long long &rows, long long &cols) {
+  static thread_local QCell q;
+  if (!make_qcell(c, q)) return false;
+  rows = 8LL * c.m1 * c.m1;
+  cols = (long long)h.P * h.N;
+  return true;
+}
+
+cudaError_t launch_c(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,
+                     long long ld, cudaStream_t st) {
+  static thread_local QCell q;
+  if (!make_qcell(c, q)) return cudaErrorInvalidValue;
+  const int P = h.P;
+  const size_t smem = sizeof(double2) * ((size_t)P + (P + 1) / 2 + (size_t)kCWarps * 4 * P);
+  static size_t granted = 0;
+  cudaError_t e = ensure_dynamic_smem(c_kernel, smem, granted);
+  if (e != cudaSuccess) return e;
+  const long long warps = 4LL * q.m1 * q.m1 * h.N;
+  c_kernel<<<(unsigned)((warps + kCWarps - 1) / kCWarps), 32 * kCWarps, smem, st>>>(d_obs, oi, q, out, ld);
   return cudaGetLastError();
 }
 

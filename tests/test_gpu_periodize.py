@@ -80,3 +80,31 @@ def test_q_parity(name):
     Q = Qg.cpu().numpy().T
     assert Q.shape == Qo.shape
     assert np.abs(Q - Qo).max() < 1e-12 * np.abs(Qo).max()
+
+
+@pytest.mark.parametrize("name,m1,pairs", [("small", 4, None), ("cup", 4, [0, 5, 10, 15])])
+def test_c_parity(name, m1, pairs):
+    """The C block (nine phased ring-source images, the six distant ones in
+    the wall pairs' discrepancies) against the oracle's c_matrix, which
+    forms all eighteen terms by definition: every entry of the sampled rows
+    within 1e-12 of the block scale."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, coll = _case(name)
+    _, src, _ = O.geometry(ob)
+    if name == "small":
+        ex, ey, z0 = 2.6, 2.3, 1.6
+    else:
+        period = 13 * 2 * np.pi / ob.k
+        ex, ey, z0 = period, period, 1.2 + period / 4
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])], prec=axi.PREC_FP64)
+    cell = axi.Cell(ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, 3, 4)
+    Cg = op.c_block(cell)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    Co = OP.c_matrix(ob, src, ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, row_pairs=pairs)
+    G = Cg.cpu().numpy().T                                        # [rows][cols]
+    nr = m1 * m1
+    idx = np.arange(nr) if pairs is None else np.asarray(pairs)
+    rows = np.concatenate([b * nr + idx for b in range(8)])
+    assert np.abs(G[rows] - Co).max() < 1e-12 * np.abs(Co).max()
