@@ -23,9 +23,9 @@ cores; its coefficients also give the line's parity errors e_bd and e_ff.
 
 `--impl reference` times the oracle as the reference arm: each step is one
 distinct mode's share of the workload (see reference_step). `--workload
-smooth | batched | cup_near | cup_btilde | cup_q` prints the other workloads'
-lines (cup_btilde, cup_q: the periodizing scheme's spherical-wave block B~
-and rows Q for the cup). Multi-GPU
+smooth | batched | cup_near | cup_btilde | cup_q | cup_c` prints the other
+workloads' lines (cup_btilde, cup_q, cup_c: the periodizing scheme's blocks
+B~, Q and C for the cup). Multi-GPU
 (torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
 tasks are independent), value sums the ranks' work over the slowest rank's
 time ("weak" scaling), with no collective on the data path.
@@ -750,6 +750,68 @@ def run_q(args):
     print(json.dumps(line))
 
 
+def run_c(args):
+    """The C block of the periodizing system (Sec. 4.1, eq. full) of the cup
+    for the cup's cell (cup_cell): device time of one fill (CUDA events, L2
+    flushed), its DRAM roofline, and the oracle's c_matrix on 4 row pairs of
+    4 x 4 nodes per face on the host, scaled to the cell's rows."""
+    import torch
+    from paper_1506_05083_gb300 import axi
+    from oracle import periodizing as OP
+    import oracle as O
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=axi.PREC_FP64)
+    cell = cup_cell(axi, wl)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    buf = op.c_block(cell)
+    rows, cols = buf.shape[1], buf.shape[0]
+    for _ in range(args.warmup):
+        op.c_block(cell, out=buf)
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    stream = torch.cuda.current_stream()
+    ts = []
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            op.c_block(cell, out=buf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    pk, pk_src = peaks()
+    nbytes = 16.0 * rows * cols
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    line = {"metric": "periodizing C block fill time (Sec. 4.1, eq. full)", "value": ms * 1e3, "unit": "us",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cup_k25_cell13_M1_{cell.m1}_C", "rows": int(rows), "cols": int(cols),
+                       "m1": cell.m1, "P": ob.P, "N": ob.N, "ex": cell.ex, "z0": cell.z0,
+                       "l2": "flushed (256 MB write) before each timed step"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "traffic": None,
+                         "work": "C written once (16 B per entry); the kernel-value samples (FP64 sqrt, "
+                                 "sin/cos) and FFTs bound the fill",
+                         "peak_source": f"hbm_gbs of {pk_src}"},
+            "gpu_launches": args.steps, "clocks": clk.summary(), "device_status": op.status()}
+    if not args.no_cpu_baseline:
+        _, src, _ = O.geometry(ob)
+        t0 = time.perf_counter()
+        OP.c_matrix(ob, src, cell.kx, cell.ky, cell.ex, cell.ey, cell.z0, 4, row_pairs=[0, 5, 10, 15])
+        sec = time.perf_counter() - t0
+        full_us = sec * rows / 32.0 * 1e6
+        line["cpu_baseline"] = {"value": full_us, "unit": "us", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"c_matrix on 4 row pairs (32 of {rows} rows), scaled to all rows"}
+    print(json.dumps(line))
+
+
 def run_btilde(args):
     """The periodizing scheme's spherical-wave block B~ (Sec. 4.1) of the cup
     at degree p = 48: device time of one fill of all mode blocks (CUDA events,
@@ -845,10 +907,10 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup",
-                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q"],
-                    help="cup (default, the headline), smooth; batched, cup_near, cup_btilde and "
-                         "cup_q (the periodizing scheme's spherical-wave block B~ and rows Q) "
-                         "print their own device-timed lines")
+                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q", "cup_c"],
+                    help="cup (default, the headline), smooth; batched, cup_near, cup_btilde, cup_q "
+                         "and cup_c (the periodizing scheme's blocks B~, Q and C) print their own "
+                         "device-timed lines")
     args = ap.parse_args()
     if args.workload in ("batched", "cup_near"):
         run_extra_workload(args)
@@ -858,6 +920,9 @@ def main():
         return
     if args.workload == "cup_q":
         run_q(args)
+        return
+    if args.workload == "cup_c":
+        run_c(args)
         return
     wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
     if args.impl == "reference":
