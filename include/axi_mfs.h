@@ -224,9 +224,10 @@ axi_status axi_plan_create(const axi_obstacle *obs, int32_t n_obs, int32_t prec,
  * CUDA events on `stream` (one warm-up and `reps` builds each, reps in
  * 1..100; it synchronises the stream, so not under stream capture): first
  * the panel chain's choices together, then, for split plans, the next-panel
- * update's cluster and the fixed-point panel (128 and 256 threads), then
- * the other trailing-update start (on either stream priority), then, for
- * split plans, the fill chunk, each with the best so far. It keeps the fastest in the plan, rebuilds the
+ * update's cluster, the fixed-point panel (128 and 256 threads) and the fill
+ * chunk, each with the best so far ("rest_start" is left as given: its two
+ * settings time alike with direct launches, but 1 is slower in a CUDA
+ * graph). It keeps the fastest in the plan, rebuilds the
  * operator with it and, when json_out is
  * not NULL, writes the choice with its build time ("build_ms"), the number
  * of candidates timed and the number skipped because they cannot run on this

@@ -1190,27 +1190,6 @@ axi_status axi_operator_autotune(axi_operator *op, int32_t reps, void *stream, c
       }
     }
   }
-  // the trailing updates' start, on either stream priority
-  if (s == AXI_OK) {
-    const axi::Tuning base = best;
-    for (int cs : {0, 1}) {
-      p->tune = base;
-      p->tune.rest_start = 1 - base.rest_start;
-      p->tune.crit_stream = cs;
-      double ms = 0.0;
-      s = time_it(ms);
-      if (s != AXI_OK) {
-        (void)cudaGetLastError();
-        ++skipped;
-        s = AXI_OK;
-        continue;
-      }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = p->tune;
-      }
-    }
-  }
   if (s == AXI_OK && split && p->obs[0].dev.fill_cdig != nullptr) {
     const axi::Tuning base = best;
     for (int fc : {0, 256, 128, 96, 64}) {
