@@ -108,3 +108,42 @@ def test_c_parity(name, m1, pairs):
     idx = np.arange(nr) if pairs is None else np.asarray(pairs)
     rows = np.concatenate([b * nr + idx for b in range(8)])
     assert np.abs(G[rows] - Co).max() < 1e-12 * np.abs(Co).max()
+
+
+def test_periodize_edges():
+    """Edges of the periodizing fills: C on the direct-sum path (P = 14 has
+    the prime 7, outside the FFT's radices), B~ and Q at degrees 0 and 1, a
+    2 x 2 node cell with an empty Rayleigh-Bloch set, and C refused for a
+    transmission obstacle."""
+    from paper_1506_05083_gb300 import axi
+    wl = synth.small_case(seed=7, k=3.0, M=40, N=32, P=14)
+    ob = wl.obstacles[0]
+    coll, src, _ = O.geometry(ob)
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])], prec=axi.PREC_FP64)
+    kx, ky, ex, ey, z0 = 1.1, -0.7, 2.6, 2.3, 1.6
+    cell = axi.Cell(kx, ky, ex, ey, z0, 4, 3, 4)
+    Cg = op.c_block(cell).cpu().numpy().T
+    Co = OP.c_matrix(ob, src, kx, ky, ex, ey, z0, 4)
+    assert np.abs(Cg - Co).max() < 1e-12 * np.abs(Co).max()
+    for p in (0, 1):
+        blocks, _ = op.btilde(p)
+        ref = OP.btilde(ob, coll, p, p + min(ob.P // 2, p) + 2, modes=range(len(blocks)))
+        for n, b in enumerate(blocks):
+            want = ref[n][:, OP.btilde_columns(p, n)].real
+            assert np.abs(b.cpu().numpy().T - want).max() < 1e-12 * np.abs(ref).max()
+        c2 = axi.Cell(0.0, 0.0, ex, ey, z0, 2, 0, p)
+        rows, cols, nrb = axi.q_shape(c2)
+        assert nrb == 1 and rows == 32                   # only kappa = 0 lies within pi * 0
+        Qo, _ = OP.q_matrix(ob.k, p, 0.0, 0.0, ex, ey, z0, 2, 0)
+        Qg = op.q_matrix(c2).cpu().numpy().T
+        assert np.abs(Qg - Qo).max() < 1e-12 * np.abs(Qo).max()
+        c3 = axi.Cell(0.5, 0.5, ex, ey, z0, 2, 0, p)      # |kappa| > 0 for every mode: none kept
+        assert axi.q_shape(c3)[2] == 0
+        Qo3, _ = OP.q_matrix(ob.k, p, 0.5, 0.5, ex, ey, z0, 2, 0)
+        assert np.abs(op.q_matrix(c3).cpu().numpy().T - Qo3).max() < 1e-12 * np.abs(Qo3).max()
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    wt = synth.small_case(seed=11, k=2.0, M=44, N=36, P=20, bc=synth.BC_TRANSMISSION)
+    opt = axi.Operator([axi.spec_from_obstacle(wt.obstacles[0])], prec=axi.PREC_FP64)
+    with pytest.raises(axi.AxiError):
+        opt.c_block(cell)
