@@ -67,6 +67,9 @@ Pins (tests/test_oracle_periodizing.py):
   c_matrix           C times a coefficient vector equals the phased image
                      sums of `potential` (value and Cartesian derivatives) at
                      the shifted wall nodes, combined into the same rows
+  q_pinv_solve       a matrix built with prescribed singular values (random
+                     unitary factors): the values come back, and the solve
+                     inverts the kept part exactly
 """
 from __future__ import annotations
 
@@ -77,7 +80,7 @@ import scipy.special as sps
 
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
            "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix",
-           "c_matrix"]
+           "c_matrix", "q_pinv_solve"]
 
 
 def n_harmonics(p):
@@ -330,3 +333,17 @@ def c_matrix(ob, src, kx, ky, ex, ey, z0, m1, row_pairs=None):
               near(F) - beta * near(B), near(F, 1) - beta * near(B, 1),
               near(T), near(T, 2), near(Dn), near(Dn, 2)]
     return np.concatenate(blocks, axis=0)
+
+
+# ----------------------------------------------------------------------------
+# Q^+ by the SVD (Sec. 4.2: "rapid to invert (via SVD)"; the O(k^6) stage)
+# ----------------------------------------------------------------------------
+
+def q_pinv_solve(Q, B, cutoff):
+    """x = Q^+ b through the SVD with singular values below cutoff * sigma_max
+    dropped (LAPACK's SVD through numpy, a library primitive); returns
+    (X, singular values in descending order)."""
+    U, s, Vh = np.linalg.svd(Q, full_matrices=False)
+    keep = s > cutoff * s[0]
+    W = (U[:, keep].conj().T @ B) / s[keep][:, None]
+    return Vh[keep].conj().T @ W, s

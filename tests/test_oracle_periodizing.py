@@ -173,3 +173,17 @@ def test_c_rows_match_potential_image_sums():
                            u(nodes["F"]) - beta * u(nodes["B"]), u(nodes["F"], 1) - beta * u(nodes["B"], 1),
                            u(nodes["T"]), u(nodes["T"], 2), u(nodes["D"]), u(nodes["D"], 2)])
     assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_q_pinv_solve_prescribed_singular_values():
+    rng = np.random.default_rng(9)
+    m, n = 40, 24
+    U, _ = np.linalg.qr(rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    s = np.concatenate([np.logspace(0, -3, 12), np.logspace(-13, -14, n - 12)])   # a clear gap
+    A = (U * s) @ V.conj().T
+    x_true = V[:, :12] @ (rng.normal(size=12) + 0j)          # in the span of the kept values
+    X, sv = OP.q_pinv_solve(A, (A @ x_true)[:, None], 1e-10)
+    assert np.allclose(sv[:12], s[:12], rtol=1e-12)
+    assert np.abs(sv[12:] - s[12:]).max() < 1e-15
+    assert np.abs(X[:, 0] - x_true).max() < 1e-11
