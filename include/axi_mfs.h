@@ -395,6 +395,38 @@ axi_status axi_c_shape(const axi_operator *op, int32_t obs, const axi_cell *cell
 axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell, axi_c128 *d_out,
                       int64_t ld, void *stream);
 
+/*
+ * Q^+ through the SVD (Sec. 4.2: the periodizing rows Q are inverted by
+ * their singular value decomposition), for any dense complex matrix.
+ *
+ * axi_svd_jacobi: one-sided (Hestenes) Jacobi SVD of the m x n matrix d_A
+ * (m >= n >= 1, column-major, leading dimension lda >= m), in place: on
+ * return d_A holds U Sigma (orthogonal columns), d_V (n x n, ldv >= n) the
+ * right singular vectors and d_sigma[n] the singular values (column norms
+ * of U Sigma, unsorted), so that A = (U Sigma) V^H. A sweep rotates every
+ * column pair once (n' - 1 rounds of n'/2 disjoint pairs, n' = n rounded up
+ * to even); the sweeps stop when every pair's |x^H y| / (||x|| ||y||) is at
+ * most tol (e.g. 1e-15), after at most max_sweeps. *sweeps receives the
+ * number run. The call synchronises `stream` after every sweep (not under
+ * stream capture); calls that overlap on one device share the convergence
+ * word. Device buffers are the caller's, 16-byte aligned (8 for d_sigma).
+ * Errors: AXI_ERR_ARG, AXI_ERR_NUMERIC (not converged in max_sweeps, or a
+ * non-finite value), AXI_ERR_CUDA.
+ *
+ * axi_svd_solve: X = V Sigma^+ U^H B with the singular values at or below
+ * cutoff * sigma_max dropped, from axi_svd_jacobi's output (d_US = d_A after
+ * the call): B is m x nrhs (ldb >= m), X is n x nrhs (ldx >= n), d_work
+ * holds n * nrhs complex values. Enqueued on `stream`.
+ * Errors: AXI_ERR_ARG, AXI_ERR_CUDA.
+ */
+axi_status axi_svd_jacobi(axi_c128 *d_A, int64_t m, int64_t n, int64_t lda, axi_c128 *d_V, int64_t ldv,
+                          double *d_sigma, double tol, int32_t max_sweeps, int32_t *sweeps,
+                          void *stream);
+axi_status axi_svd_solve(const axi_c128 *d_US, const axi_c128 *d_V, const double *d_sigma, int64_t m,
+                         int64_t n, int64_t lda, int64_t ldv, double cutoff, const axi_c128 *d_B,
+                         int64_t ldb, int64_t nrhs, axi_c128 *d_X, int64_t ldx, axi_c128 *d_work,
+                         void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

@@ -11,6 +11,8 @@ import ctypes as C
 import os
 from typing import List, Optional, Sequence
 
+import math
+
 import numpy as np
 import torch
 
@@ -27,6 +29,43 @@ OK, ERR_ARG, ERR_SHAPE = 0, -1, -2              # axi_status values (include/axi
 
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
+
+
+def svd_jacobi(A: torch.Tensor, tol=None, max_sweeps=30, stream=None):
+    """axi_svd_jacobi on a [n][m] complex128 CUDA tensor holding the m x n
+    matrix column-major (transposed view of the rows); A is overwritten with
+    U Sigma. tol defaults to sqrt(m) times the double rounding unit. Returns
+    (V as [n][n] column-major, sigma [n], sweeps)."""
+    if A.dtype != torch.complex128 or not A.is_cuda or not A.is_contiguous() or A.dim() != 2:
+        raise ValueError("svd_jacobi: A must be a contiguous complex128 CUDA tensor [n][m]")
+    n, m = A.shape
+    if tol is None:
+        tol = math.sqrt(m) * 2.0 ** -52
+    V = torch.empty((n, n), dtype=torch.complex128, device=A.device)
+    sigma = torch.empty(n, dtype=torch.float64, device=A.device)
+    sw = C.c_int32()
+    _check(lib().axi_svd_jacobi(_dev(A), m, n, m, _dev(V), n, _dev(sigma), tol, max_sweeps, C.byref(sw),
+                                _stream(stream)), "axi_svd_jacobi")
+    return V, sigma, sw.value
+
+
+def svd_solve(US: torch.Tensor, V: torch.Tensor, sigma: torch.Tensor, B: torch.Tensor, cutoff=1e-10,
+              stream=None) -> torch.Tensor:
+    """axi_svd_solve: X = V Sigma^+ U^H B (singular values at or below cutoff
+    sigma_max dropped); US [n][m], V [n][n], B [nrhs][m] column-major views.
+    Returns X as [nrhs][n]."""
+    n, m = US.shape
+    for t in (US, V, B):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("svd_solve: complex128 contiguous CUDA tensors expected")
+    if V.shape != (n, n) or B.dim() != 2 or B.shape[1] != m or sigma.numel() != n:
+        raise ValueError("svd_solve: shapes do not match")
+    nrhs = B.shape[0]
+    X = torch.empty((nrhs, n), dtype=torch.complex128, device=US.device)
+    W = torch.empty((nrhs, n), dtype=torch.complex128, device=US.device)
+    _check(lib().axi_svd_solve(_dev(US), _dev(V), _dev(sigma), m, n, m, n, cutoff, _dev(B), m, nrhs, _dev(X),
+                               n, _dev(W), _stream(stream)), "axi_svd_solve")
+    return X
 
 
 class Cell(C.Structure):
@@ -102,6 +141,10 @@ SIGNATURES = [
     ("axi_fill_q", C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp]),
     ("axi_c_shape", C.c_int, [_vp, C.c_int32, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("axi_fill_c", C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp]),
+    ("axi_svd_jacobi", C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int64, _vp, C.c_int64, _vp, C.c_double,
+                                 C.c_int32, C.POINTER(C.c_int32), _vp]),
+    ("axi_svd_solve", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_double, _vp,
+                                C.c_int64, C.c_int64, _vp, C.c_int64, _vp, _vp]),
     ("axi_fill_btilde", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),

@@ -967,6 +967,38 @@ axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell,
                                    static_cast<cudaStream_t>(stream)));
 }
 
+axi_status axi_svd_jacobi(axi_c128 *d_A, int64_t m, int64_t n, int64_t lda, axi_c128 *d_V, int64_t ldv,
+                          double *d_sigma, double tol, int32_t max_sweeps, int32_t *sweeps,
+                          void *stream) {
+  if (!d_A || !d_V || !d_sigma || !sweeps || n < 1 || m < n || lda < m || ldv < n || max_sweeps < 1 ||
+      n > (int64_t)1 << 20 || m > (int64_t)1 << 30 || !(tol >= 0.0) ||
+      (reinterpret_cast<uintptr_t>(d_A) & 15) || (reinterpret_cast<uintptr_t>(d_V) & 15) ||
+      (reinterpret_cast<uintptr_t>(d_sigma) & 7))
+    return AXI_ERR_ARG;
+  int sw = 0;
+  bool conv = false;
+  const cudaError_t e = axi::svd_jacobi(reinterpret_cast<double2 *>(d_A), m, n, lda,
+                                        reinterpret_cast<double2 *>(d_V), ldv, d_sigma, tol, max_sweeps,
+                                        &sw, &conv, static_cast<cudaStream_t>(stream));
+  *sweeps = sw;
+  if (e != cudaSuccess) return AXI_ERR_CUDA;
+  return conv ? AXI_OK : AXI_ERR_NUMERIC;
+}
+
+axi_status axi_svd_solve(const axi_c128 *d_US, const axi_c128 *d_V, const double *d_sigma, int64_t m,
+                         int64_t n, int64_t lda, int64_t ldv, double cutoff, const axi_c128 *d_B,
+                         int64_t ldb, int64_t nrhs, axi_c128 *d_X, int64_t ldx, axi_c128 *d_work,
+                         void *stream) {
+  if (!d_US || !d_V || !d_sigma || !d_B || !d_X || !d_work || n < 1 || m < n || lda < m || ldv < n ||
+      ldb < m || ldx < n || nrhs < 1 || nrhs > 65535 || n > (int64_t)1 << 20 || !(cutoff >= 0.0))
+    return AXI_ERR_ARG;
+  return cuda_status(axi::svd_solve(reinterpret_cast<const double2 *>(d_US),
+                                    reinterpret_cast<const double2 *>(d_V), d_sigma, m, n, lda, ldv, cutoff,
+                                    reinterpret_cast<const double2 *>(d_B), ldb, nrhs,
+                                    reinterpret_cast<double2 *>(d_X), ldx,
+                                    reinterpret_cast<double2 *>(d_work), static_cast<cudaStream_t>(stream)));
+}
+
 axi_status axi_operator_factors(const axi_operator *op, int32_t obs, axi_factor_view *v) {
   if (!op || !v || obs < 0 || obs >= (int)op->plan->obs.size()) return AXI_ERR_ARG;
   const ObsDev &d = op->plan->obs[obs].dev;

@@ -217,6 +217,14 @@ bool q_shape(const axi_cell &c, long long &rows, long long &cols, long long &nrb
 bool q_modes(const axi_cell &c, int *mn, long long cap);
 cudaError_t launch_q(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,
                      long long ld, cudaStream_t st);
+// Dense SVD for Q^+ (svd_dense.cu): one-sided Jacobi (A <- U Sigma, V, sigma;
+// *converged false when max_sweeps ran out) and the truncated solve.
+cudaError_t svd_jacobi(double2 *A, long long m, long long n, long long lda, double2 *V, long long ldv,
+                       double *sigma, double tol, int max_sweeps, int *sweeps, bool *converged,
+                       cudaStream_t st);
+cudaError_t svd_solve(const double2 *US, const double2 *V, const double *sigma, long long m, long long n,
+                      long long lda, long long ldv, double cutoff, const double2 *B, long long ldb,
+                      long long nrhs, double2 *X, long long ldx, double2 *W, cudaStream_t st);
 // The C block (periodize.cu; Neumann obstacles): shape for a cell, and the fill.
 bool c_shape(const ObsDev &h, const axi_cell &c, long long &rows, long long &cols);
 cudaError_t launch_c(const ObsDev *d_obs, const ObsDev &h, int oi, const axi_cell &c, double2 *out,

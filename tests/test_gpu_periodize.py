@@ -147,3 +147,59 @@ def test_periodize_edges():
     opt = axi.Operator([axi.spec_from_obstacle(wt.obstacles[0])], prec=axi.PREC_FP64)
     with pytest.raises(axi.AxiError):
         opt.c_block(cell)
+
+
+def _prescribed(rng, m, n, s):
+    U, _ = np.linalg.qr(rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    return (U * s) @ V.conj().T, V
+
+
+def test_svd_jacobi_prescribed():
+    """The one-sided Jacobi SVD of a matrix with prescribed singular values
+    (a gap at 1e-13): the values come back, (U Sigma) V^H rebuilds the
+    matrix, V is unitary, and the truncated solve equals the oracle's."""
+    from paper_1506_05083_gb300 import axi
+    rng = np.random.default_rng(4)
+    m, n = 70, 45
+    s = np.concatenate([np.logspace(0, -4, 30), np.logspace(-13, -14, n - 30)])
+    A, Vt = _prescribed(rng, m, n, s)
+    At = torch.tensor(np.ascontiguousarray(A.T), device="cuda")       # column-major view
+    V, sigma, sweeps = axi.svd_jacobi(At)
+    US = At.cpu().numpy().T
+    Vn = V.cpu().numpy().T
+    sg = sigma.cpu().numpy()
+    assert sweeps < 30
+    assert np.abs(np.sort(sg)[::-1] - s).max() < 1e-13
+    assert np.abs(US @ Vn.conj().T - A).max() < 1e-13
+    assert np.abs(Vn.conj().T @ Vn - np.eye(n)).max() < 1e-13
+    B = rng.normal(size=(m, 3)) + 1j * rng.normal(size=(m, 3))
+    X = axi.svd_solve(At, V, sigma, torch.tensor(np.ascontiguousarray(B.T), device="cuda"), cutoff=1e-10)
+    Xo, _ = OP.q_pinv_solve(A, B, 1e-10)
+    assert np.abs(X.cpu().numpy().T - Xo).max() < 1e-9 * np.abs(Xo).max()
+
+
+def test_svd_of_q_small_cell():
+    """Q^+ for the small cell's periodizing rows: the GPU Jacobi SVD of the
+    GPU-filled Q against numpy's SVD of the oracle's Q, and the truncated
+    solve at a cutoff inside the spectrum's widest gap."""
+    from paper_1506_05083_gb300 import axi
+    wl, ob, coll = _case("small")
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    op = axi.Operator([axi.spec_from_obstacle(wl.obstacles[0])], prec=axi.PREC_FP64)
+    cell = axi.Cell(ob.k * d[0], ob.k * d[1], 2.0, 1.7, 1.5, 6, 3, 12)
+    Qg = op.q_matrix(cell)                                            # [cols][rows]
+    Qo, _ = OP.q_matrix(ob.k, 12, ob.k * d[0], ob.k * d[1], 2.0, 1.7, 1.5, 6, 3)
+    so = np.linalg.svd(Qo, compute_uv=False)
+    V, sigma, sweeps = axi.svd_jacobi(Qg)
+    torch.cuda.synchronize()
+    sg = np.sort(sigma.cpu().numpy())[::-1]
+    assert np.abs(sg - so).max() < 1e-11 * so[0]
+    lo, hi = np.searchsorted(-so, -1e-6 * so[0]), np.searchsorted(-so, -1e-12 * so[0])
+    gap = lo + int(np.argmax(so[lo:hi - 1] / so[lo + 1:hi]))
+    cutoff = np.sqrt(so[gap] * so[gap + 1]) / so[0]
+    rng = np.random.default_rng(6)
+    B = rng.normal(size=(Qo.shape[0], 2)) + 1j * rng.normal(size=(Qo.shape[0], 2))
+    X = axi.svd_solve(Qg, V, sigma, torch.tensor(np.ascontiguousarray(B.T), device="cuda"), cutoff=cutoff)
+    Xo, _ = OP.q_pinv_solve(Qo, B, cutoff)
+    assert np.abs(X.cpu().numpy().T - Xo).max() < 1e-8 * np.abs(Xo).max()
