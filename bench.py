@@ -23,9 +23,9 @@ cores; its coefficients also give the line's parity errors e_bd and e_ff.
 
 `--impl reference` times the oracle as the reference arm: each step is one
 distinct mode's share of the workload (see reference_step). `--workload
-smooth | batched | cup_near | cup_btilde | cup_q | cup_c` prints the other
-workloads' lines (cup_btilde, cup_q, cup_c: the periodizing scheme's blocks
-B~, Q and C for the cup). Multi-GPU
+smooth | batched | cup_near | cup_btilde | cup_q | cup_c | cup_qsvd` prints
+the other workloads' lines (cup_btilde, cup_q, cup_c: the periodizing
+scheme's blocks B~, Q and C for the cup; cup_qsvd: the SVD of that Q). Multi-GPU
 (torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
 tasks are independent), value sums the ranks' work over the slowest rank's
 time ("weak" scaling), with no collective on the data path.
@@ -812,6 +812,56 @@ def run_c(args):
     print(json.dumps(line))
 
 
+def run_qsvd(args):
+    """The SVD of the cup cell's periodizing rows Q (Sec. 4.2: Q is inverted
+    through its SVD; the O(k^6) stage): each step fills Q (untimed) and times
+    the one-sided Jacobi SVD in place (CUDA events); the oracle's SVD of the
+    same Q (LAPACK through numpy) on the host as the CPU baseline."""
+    import torch
+    from paper_1506_05083_gb300 import axi
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=axi.PREC_FP64)
+    cell = cup_cell(axi, wl)
+    Q = op.q_matrix(cell)
+    cols, rows = Q.shape
+    stream = torch.cuda.current_stream()
+    ts, sweeps = [], []
+    with ClockSampler(0) as clk:
+        for i in range(args.warmup + args.steps):
+            op.q_matrix(cell, out=Q)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V, sigma, sw = axi.svd_jacobi(Q)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+                sweeps.append(sw)
+    ms = float(np.mean(ts))
+    sg = np.sort(sigma.cpu().numpy())[::-1]
+    line = {"metric": "SVD of the periodizing rows Q (Sec. 4.2)", "value": ms * 1e3, "unit": "us",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cup_k25_cell13_M1_{cell.m1}_N0_{cell.n0}_p{cell.p}_Q_svd",
+                       "rows": int(rows), "cols": int(cols), "sweeps": sweeps,
+                       "sigma_max": float(sg[0]), "sigma_min": float(sg[-1])},
+            "gpu_launches": None, "clocks": clk.summary(), "device_status": op.status()}
+    if not args.no_cpu_baseline:
+        Qh = op.q_matrix(cell).cpu().numpy().T
+        t0 = time.perf_counter()
+        so = np.linalg.svd(Qh, compute_uv=True, full_matrices=False)[1]
+        sec = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sec * 1e6, "unit": "us", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "numpy (LAPACK) SVD of the same Q, with the singular vectors"}
+        line["sigma_vs_oracle"] = float(np.abs(sg - so).max() / so[0])
+    print(json.dumps(line))
+
+
 def run_btilde(args):
     """The periodizing scheme's spherical-wave block B~ (Sec. 4.1) of the cup
     at degree p = 48: device time of one fill of all mode blocks (CUDA events,
@@ -907,7 +957,8 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup",
-                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q", "cup_c"],
+                    choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q", "cup_c",
+                             "cup_qsvd"],
                     help="cup (default, the headline), smooth; batched, cup_near, cup_btilde, cup_q "
                          "and cup_c (the periodizing scheme's blocks B~, Q and C) print their own "
                          "device-timed lines")
@@ -923,6 +974,9 @@ def main():
         return
     if args.workload == "cup_c":
         run_c(args)
+        return
+    if args.workload == "cup_qsvd":
+        run_qsvd(args)
         return
     wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
     if args.impl == "reference":
