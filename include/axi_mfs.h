@@ -403,9 +403,10 @@ axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell,
  * (m >= n >= 1, column-major, leading dimension lda >= m), in place: on
  * return d_A holds U Sigma (orthogonal columns), d_V (n x n, ldv >= n) the
  * right singular vectors and d_sigma[n] the singular values (column norms
- * of U Sigma, unsorted), so that A = (U Sigma) V^H. A sweep rotates every
- * column pair once (n' - 1 rounds of n'/2 disjoint pairs, n' = n rounded up
- * to even); the sweeps stop when every pair's |x^H y| / (||x|| ||y||) is at
+ * of U Sigma, unsorted), so that A = (U Sigma) V^H. A sweep orders the
+ * columns by decreasing norm (d_sigma holds that order during the call) and
+ * rotates every column pair once (n' - 1 rounds of n'/2 disjoint pairs,
+ * n' = n rounded up to even); the sweeps stop when every pair's |x^H y| / (||x|| ||y||) is at
  * most tol (e.g. 1e-15), after at most max_sweeps. *sweeps receives the
  * number run. The call synchronises `stream` after every sweep (not under
  * stream capture); calls that overlap on one device share the convergence
