@@ -179,3 +179,23 @@ def test_q_shape_and_modes_host():
                 axi.Cell(0, 0, -1, 1, 1, 6, 3, 4), axi.Cell(0, 0, 1, 1, 1, 6, 3, 256)):
         with pytest.raises(axi.AxiError):
             axi.q_shape(bad)
+
+
+def test_svd_arguments_refused_on_host():
+    """axi_svd_jacobi and axi_svd_solve check their arguments before any
+    device work: null pointers, m < n, short leading dimensions, a zero
+    sweep budget and misaligned buffers are AXI_ERR_ARG (-1) without a GPU."""
+    import ctypes as C
+    from paper_1506_05083_gb300 import axi
+    L = axi.lib()
+    p16 = C.c_void_p(1 << 20)                     # aligned stand-ins, never dereferenced
+    sw = C.c_int32()
+    assert L.axi_svd_jacobi(None, 8, 4, 8, p16, 4, p16, 1e-15, 10, C.byref(sw), None) == -1
+    assert L.axi_svd_jacobi(p16, 3, 4, 8, p16, 4, p16, 1e-15, 10, C.byref(sw), None) == -1   # m < n
+    assert L.axi_svd_jacobi(p16, 8, 4, 7, p16, 4, p16, 1e-15, 10, C.byref(sw), None) == -1   # lda < m
+    assert L.axi_svd_jacobi(p16, 8, 4, 8, p16, 3, p16, 1e-15, 10, C.byref(sw), None) == -1   # ldv < n
+    assert L.axi_svd_jacobi(p16, 8, 4, 8, p16, 4, p16, 1e-15, 0, C.byref(sw), None) == -1    # no sweeps
+    assert L.axi_svd_jacobi(C.c_void_p((1 << 20) + 8), 8, 4, 8, p16, 4, p16, 1e-15, 10,
+                            C.byref(sw), None) == -1                                        # misaligned
+    assert L.axi_svd_solve(p16, p16, p16, 8, 4, 8, 4, 1e-10, p16, 8, 0, p16, 4, p16, None) == -1
+    assert L.axi_svd_solve(p16, p16, p16, 8, 4, 8, 4, 1e-10, p16, 7, 1, p16, 4, p16, None) == -1
