@@ -70,6 +70,10 @@ Pins (tests/test_oracle_periodizing.py):
   q_pinv_solve       a matrix built with prescribed singular values (random
                      unitary factors): the values come back, and the solve
                      inverts the kept part exactly
+  btilde_samples     for p < P/2, the direct value of the truncated expansion's
+                     normal derivative, sum d_lm dn u_lm, at the P ring nodes
+                     (no trapezoid sum, no transform)
+  periodic_operator_apply   composed of the functions above, each pinned
 """
 from __future__ import annotations
 
@@ -78,9 +82,12 @@ import math
 import numpy as np
 import scipy.special as sps
 
+from .mfs import near_image_sum, rhs_modes, solve_modes
+
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
            "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix",
-           "c_matrix", "q_pinv_solve"]
+           "c_matrix", "q_pinv_solve", "btilde_samples",
+           "periodic_operator_apply"]
 
 
 def n_harmonics(p):
@@ -347,3 +354,46 @@ def q_pinv_solve(Q, B, cutoff):
     keep = s > cutoff * s[0]
     W = (U[:, keep].conj().T @ B) / s[keep][:, None]
     return Vh[keep].conj().T @ W, s
+
+
+# ----------------------------------------------------------------------------
+# One application of the preconditioned periodic operator (Sec. 4.2, eq. iter)
+# ----------------------------------------------------------------------------
+
+def btilde_samples(ob, coll, p, d):
+    """The B~ term of eq. iter carried back to the ring nodes: with the modal
+    data fhat_n = sum_lm B~_{n,lm} d_lm for the P modes the rows hold,
+    -P/2 < n <= P/2 (mode -P/2 is not among them, as in `rhs_modes`),
+      f_{m,l} = sum_n fhat_{n,m} e^{2 pi i n l / P}
+    (the inverse of eq. fhatquad's sum). Neumann rows; d [W][(p+1)^2] ->
+    [W][M][P]. B~ by `btilde` with q = 2 (p + P) + 2 nodes, more than
+    |m| + |n| for every pair, so its trapezoid sums are exact."""
+    P = ob.P
+    nm = np.arange(P)
+    nm = np.where(nm > P // 2, nm - P, nm)
+    Bt = btilde(ob, coll, p, 2 * (p + P) + 2, modes=list(nm))                 # [P][M][(p+1)^2]
+    fB = np.einsum("nrc,wc->wnr", Bt, np.atleast_2d(d))                        # [W][P][M]
+    E = np.exp(2j * math.pi * np.outer(nm, np.arange(P)) / P)                  # [n][l]
+    return np.einsum("wnr,nl->wrl", fB, E)
+
+
+def periodic_operator_apply(ob, coll, src, factors, g, dirs, lattice, C, Q, p, cutoff=1e-10):
+    """y = (I + A_else A_0^+ - B Q^+ C A_0^+) g, eq. iter, for a Neumann
+    obstacle. Reading: the paper states the operator on modal data; it acts
+    here on boundary samples g [W][M][P], i.e. conjugated by the transform of
+    eq. fhatquad, so that the device apply (samples in) and the near-image
+    sum (samples out) compose without extra transforms; a solve in either
+    space gives the same eta. Steps:
+      coef = A_0^+ g          `rhs_modes`, then `solve_modes` (the QR factors)
+      A_else coef             `near_image_sum` with the waves' Bloch phases
+      xi = Q^+ (C coef)       the rows of `c_matrix`, `q_pinv_solve` with
+                              the paper's 1e-10 relative cutoff
+      B xi                    `btilde_samples` of xi's spherical-wave part d
+    factors: the list of (packed QR, tau) of `factor_operator`. Returns y
+    [W][M][P]."""
+    W, M, P = g.shape
+    coef = solve_modes(ob, factors, rhs_modes(g))                              # [W][P][N]
+    ae = near_image_sum(ob, coll, src, coef, dirs, lattice).reshape(W, M, P)
+    yC = coef.reshape(W, -1) @ C.T                                             # [W][8 M1^2]
+    xi, _ = q_pinv_solve(Q, yC.T, cutoff)                                      # [nQ][W]
+    return g + ae - btilde_samples(ob, coll, p, xi[:n_harmonics(p)].T)

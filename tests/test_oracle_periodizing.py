@@ -187,3 +187,24 @@ def test_q_pinv_solve_prescribed_singular_values():
     assert np.allclose(sv[:12], s[:12], rtol=1e-12)
     assert np.abs(sv[12:] - s[12:]).max() < 1e-15
     assert np.abs(X[:, 0] - x_true).max() < 1e-11
+
+
+def test_btilde_samples_direct_expansion():
+    """B~ d carried back to the P ring nodes equals the normal derivative of
+    the truncated expansion sum d_lm u_lm evaluated at those nodes directly
+    (p < P/2, so every mode the waves hold is among the P modes): pins the
+    mode index of each column, the sign of the negative modes and the sign of
+    the transform back to samples."""
+    P, p = 16, 6
+    ob, coll = _small(P=P)
+    rng = np.random.default_rng(11)
+    d = rng.normal(size=(2, OP.n_harmonics(p))) + 1j * rng.normal(size=(2, OP.n_harmonics(p)))
+    X, Nv = OP._ring_nodes(coll, P)                                     # [M][P][3]
+    ref = np.zeros((2, coll.shape[0], P), dtype=np.complex128)
+    for l in range(p + 1):
+        for m in range(-l, l + 1):
+            _, g = OP.sph_wave_value_grad(l, m, ob.k, X)
+            dn = np.sum(g * Nv, axis=-1)
+            ref += d[:, l * l + l + m][:, None, None] * dn[None]
+    got = OP.btilde_samples(ob, coll, p, d)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
