@@ -23,9 +23,10 @@ cores; its coefficients also give the line's parity errors e_bd and e_ff.
 
 `--impl reference` times the oracle as the reference arm: each step is one
 distinct mode's share of the workload (see reference_step). `--workload
-smooth | batched | cup_near | cup_btilde | cup_q | cup_c | cup_qsvd` prints
+smooth | batched | cup_near | cup_btilde | cup_q | cup_c | cup_qsvd | cup_iter` prints
 the other workloads' lines (cup_btilde, cup_q, cup_c: the periodizing
-scheme's blocks B~, Q and C for the cup; cup_qsvd: the SVD of that Q). Multi-GPU
+scheme's blocks B~, Q and C for the cup; cup_qsvd: the SVD of that Q;
+cup_iter: one application of the preconditioned periodic operator). Multi-GPU
 (torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
 tasks are independent), value sums the ranks' work over the slowest rank's
 time ("weak" scaling), with no collective on the data path.
@@ -862,6 +863,142 @@ def run_qsvd(args):
     print(json.dumps(line))
 
 
+def run_iter(args):
+    """One application of the preconditioned periodic operator (Sec. 4.2, eq.
+    iter), y = (I + A_else A_0^+ - B Q^+ C A_0^+) g, for the cup in its cell
+    (cup_cell) on 16 right-hand sides sharing the cell's Bloch vector (the
+    vectors a Krylov solve would apply it to), the near-image sum split into 7
+    digits (MFS coefficients of rough data cancel in the image sum, and a
+    split's rounding is relative to sum |K| |sigma|: 7 digits keep the output
+    within about 3e-11 on the small cell's test): C, Q, Q's SVD (one-sided Jacobi)
+    and B~ are formed once, untimed; each timed step is one
+    `periodic_iter_apply` (CUDA events, L2 flushed before it), and a second
+    pass times each stage. CPU baseline: the oracle's steps on bounded
+    samples, each scaled to the whole application."""
+    import torch
+    from paper_1506_05083_gb300 import axi
+    from oracle import periodizing as OP
+    import oracle as O
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    prec = axi.PREC_SPLIT_BF16 | (args.slices << 8) if args.prec == "split" else axi.PREC_FP64
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=prec)
+    cell = cup_cell(axi, wl)
+    W = wl.n_waves
+    d0 = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)[0]
+    dirs = torch.tensor(np.stack([d0] * W), device=dev)
+    lat = (cell.ex, cell.ey)
+    Cb = op.c_block(cell)
+    US = op.q_matrix(cell)
+    V, sigma, sweeps = axi.svd_jacobi(US)
+    _, bt = op.btilde(cell.p)
+    rng = np.random.default_rng(2015)
+    g = torch.tensor(rng.normal(size=(W, ob.M, ob.P)) + 1j * rng.normal(size=(W, ob.M, ob.P)), device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        axi.periodic_iter_apply(op, g, lat, dirs, Cb, US, V, sigma, bt, cell.p, near_slices=7)
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ts, stages = [], {k: [] for k in ("apply", "near", "c_eta", "q_pinv", "combine")}
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            y = axi.periodic_iter_apply(op, g, lat, dirs, Cb, US, V, sigma, bt, cell.p, near_slices=7)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e = [ev() for _ in range(6)]
+            e[0].record(stream)
+            coef = op.apply(g)
+            e[1].record(stream)
+            a = axi.near_image_sum(op, coef, lat, dirs, slices=7)
+            e[2].record(stream)
+            c = axi.matvec_c128(Cb, coef.view(W, -1))
+            e[3].record(stream)
+            xi = axi.svd_solve(US, V, sigma, c)
+            e[4].record(stream)
+            axi.iter_combine(g, a.view(g.shape), bt, xi, cell.p)
+            e[5].record(stream)
+            torch.cuda.synchronize()
+            for k, (x0, x1) in zip(stages, zip(e[:-1], e[1:])):
+                stages[k].append(x0.elapsed_time(x1))
+    ms = float(np.mean(ts))
+    st_ms = {k: float(np.mean(v)) for k, v in stages.items()}
+    rows_c, cols_c = Cb.shape[1], Cb.shape[0]
+    fl = 8.0 * rows_c * cols_c * W                           # complex MACs of C eta, 8 flops each
+    tfl = fl / (st_ms["c_eta"] * 1e-3) / 1e12
+    gbs = 16.0 * rows_c * cols_c / (st_ms["c_eta"] * 1e-3) / 1e9
+    line = {"metric": "one application of the preconditioned periodic operator (Sec. 4.2, eq. iter)",
+            "value": ms * 1e3, "unit": "us", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cup_k25_cell13_M1_{cell.m1}_N0_{cell.n0}_p{cell.p}_iter_W{W}",
+                       "W": W, "M": ob.M, "N": ob.N, "P": ob.P, "prec": args.prec,
+                       "C": [int(rows_c), int(cols_c)], "Q": [int(US.shape[1]), int(US.shape[0])],
+                       "svd_sweeps": sweeps, "near_image_sum": "split, 7 digits",
+                       "l2": "flushed (256 MB write) before each timed step; C (8.5 GB) exceeds L2"},
+            "stages_ms": st_ms,
+            "near_pairs_per_s": ob.M * ob.P * ob.N * ob.P * 8 * W / (st_ms["near"] * 1e-3),
+            "roofline": {"bound": "alu", "achieved": tfl, "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tfl / FP64_DFMA_PEAK_TFLOPS, "traffic": None, "kernel": "matvec_kernel<16>",
+                         "work": f"C eta: 8 flops per complex MAC, {W} vectors; C read once at {gbs:.0f} GB/s",
+                         "peak_source": "FP64 DFMA probe of measured (MEASURED_PEAKS.json has no FP64 entry)"},
+            "gpu_launches": None, "clocks": clk.summary(), "device_status": op.status(),
+            "y_max": float(y.abs().max())}
+    if not args.no_cpu_baseline:
+        coll, src, srcx = O.geometry(ob)
+        M, N, P = ob.M, ob.N, ob.P
+        t = {}
+        # A_0^+: the oracle's QR solve on 4 of the P mode slots, scaled to P
+        A4 = rng.normal(size=(4, M, N)) + 1j * rng.normal(size=(4, M, N))
+        fac = [O.householder_qr(A4[j]) for j in range(4)]        # factoring is the build, untimed
+        fh = rng.normal(size=(W, 4, M)) + 1j * rng.normal(size=(W, 4, M))
+        t0 = time.perf_counter()
+        for j in range(4):
+            Y = O.apply_qh(fac[j][0], fac[j][1], fh[:, j, :].T)[:N]
+            O.back_substitute(np.triu(fac[j][0][:N, :N]), Y)
+        t["apply"] = (time.perf_counter() - t0) * P / 4
+        # A_else: the near-image sum at 64 of the M P targets
+        coef = rng.normal(size=(W, P, N)) + 1j * rng.normal(size=(W, P, N))
+        t0 = time.perf_counter()
+        O.near_image_sum(ob, coll, src, coef, np.stack([d0] * W), lat, target_idx=np.arange(64) * 97)
+        t["near"] = (time.perf_counter() - t0) * M * P / 64
+        # C eta on 512 rows of a Gaussian stand-in of C's shape
+        Cs = rng.normal(size=(512, cols_c)) + 1j * rng.normal(size=(512, cols_c))
+        t0 = time.perf_counter()
+        coef.reshape(W, -1) @ Cs.T
+        t["c_eta"] = (time.perf_counter() - t0) * rows_c / 512
+        del Cs
+        # Q^+: the oracle's SVD solve as it stands, on a Gaussian matrix of Q's shape
+        Qs = rng.normal(size=(US.shape[1], US.shape[0])) + 1j * rng.normal(size=(US.shape[1], US.shape[0]))
+        t0 = time.perf_counter()
+        OP.q_pinv_solve(Qs, rng.normal(size=(US.shape[1], W)) + 0j, 1e-10)
+        t["q_pinv"] = time.perf_counter() - t0
+        del Qs
+        # B xi: B~ of all P modes on 8 rows, scaled to M rows
+        t0 = time.perf_counter()
+        OP.btilde(ob, coll, cell.p, 2 * (cell.p + P) + 2, modes=list(range(-(P // 2) + 1, P // 2 + 1)),
+                  rows=np.arange(2) * 216)
+        t["combine"] = (time.perf_counter() - t0) * M / 2
+        total = sum(t.values())
+        line["cpu_baseline"] = {"value": total * 1e6, "unit": "us", "cores": os.cpu_count(), "kind": "oracle",
+                                "stages_s": t,
+                                "sample": "the oracle's steps on bounded samples scaled to the whole: QR solve "
+                                          "of 4 mode slots (x P/4), near-image sum at 64 targets, C eta on 512 "
+                                          "rows of a Gaussian stand-in, q_pinv_solve (its SVD included, as it "
+                                          "stands) on a Gaussian matrix of Q's shape, B~ on 2 rows"}
+    print(json.dumps(line))
+
+
 def run_btilde(args):
     """The periodizing scheme's spherical-wave block B~ (Sec. 4.1) of the cup
     at degree p = 48: device time of one fill of all mode blocks (CUDA events,
@@ -958,7 +1095,7 @@ def main():
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup",
                     choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q", "cup_c",
-                             "cup_qsvd"],
+                             "cup_qsvd", "cup_iter"],
                     help="cup (default, the headline), smooth; batched, cup_near, cup_btilde, cup_q "
                          "and cup_c (the periodizing scheme's blocks B~, Q and C) print their own "
                          "device-timed lines")
@@ -977,6 +1114,9 @@ def main():
         return
     if args.workload == "cup_qsvd":
         run_qsvd(args)
+        return
+    if args.workload == "cup_iter":
+        run_iter(args)
         return
     wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
     if args.impl == "reference":

@@ -428,6 +428,56 @@ axi_status axi_svd_solve(const axi_c128 *d_US, const axi_c128 *d_V, const double
                          int64_t ldb, int64_t nrhs, axi_c128 *d_X, int64_t ldx, axi_c128 *d_work,
                          void *stream);
 
+/*
+ * One application of the preconditioned periodic operator (Sec. 4.2, eq.
+ * iter), y = (I + A_else A_0^+ - B Q^+ C A_0^+) g, is composed of
+ *   coef = A_0^+ g                       axi_apply_operator
+ *   a    = A_else coef                   axi_near_image_sum
+ *   c    = C coef                        axi_matvec_c128 (C from axi_fill_c)
+ *   xi   = Q^+ c                         axi_svd_solve (Q from axi_fill_q,
+ *                                        its SVD from axi_svd_jacobi)
+ *   y    = g + a - B xi                  axi_iter_combine (B~ from
+ *                                        axi_fill_btilde)
+ * with g, a and y boundary samples [W][M][P] (the operator's right-hand-side
+ * layout), i.e. the paper's modal operator conjugated by the transform of
+ * eq. fhatquad; a Krylov solve in either space yields the same eta.
+ *
+ * axi_matvec_c128: Y[w * ldy + r] = sum_c A[c * lda + r] X[w * ldx + c] for
+ * a dense complex rows x cols matrix A (column-major, lda >= rows) and
+ * 1 <= nrhs <= 16 vectors, all device memory owned by the caller and
+ * 16-byte aligned. The
+ * columns are split into slices whose partial sums are added in a fixed
+ * order (results are reproducible run to run): d_work must hold
+ * axi_matvec_workspace_bytes bytes (none for small matrices: d_work may then
+ * be null). Enqueued on `stream`.
+ * Errors: AXI_ERR_ARG (null pointers, sizes or leading dimensions out of
+ * range, misaligned buffers), AXI_ERR_WORKSPACE (work too small),
+ * AXI_ERR_CUDA.
+ */
+axi_status axi_matvec_workspace_bytes(int64_t rows, int64_t cols, int32_t nrhs, size_t *bytes);
+axi_status axi_matvec_c128(const axi_c128 *d_A, int64_t lda, int64_t rows, int64_t cols,
+                           const axi_c128 *d_X, int64_t ldx, int32_t nrhs, axi_c128 *d_Y, int64_t ldy,
+                           void *d_work, size_t work_bytes, void *stream);
+
+/*
+ * axi_iter_combine: y = g + a - B xi for W waves of `rows` x P boundary
+ * samples (layout [W][rows][P], P <= 1536). B xi is the spherical-wave part
+ * d of xi (d_d + w * ldd, (p + 1)^2 entries in column order l^2 + l + m,
+ * ldd >= (p + 1)^2) through B~ (d_btilde, the packed blocks of
+ * axi_fill_btilde for the same rows, P and p; btilde_count its size in
+ * doubles): the modal data fhat_n = sum_l B~_n[., l] d_{l,n} of the P modes
+ * -P/2 < n <= P/2 (mode -n is (-1)^n times the block of n; modes |n| > p
+ * are zero), carried to the nodes by f_l = sum_n fhat_n e^{2 pi i n l / P}.
+ * d_g and d_a may be null (taken as zero); d_y may alias d_g or d_a. The
+ * complex buffers are 16-byte aligned, d_btilde 8-byte aligned.
+ * Enqueued on `stream`.
+ * Errors: AXI_ERR_ARG (null pointers, sizes out of range, misaligned
+ * buffers, btilde_count smaller than the packed blocks), AXI_ERR_CUDA.
+ */
+axi_status axi_iter_combine(int32_t W, int32_t rows, int32_t P, int32_t p, const axi_c128 *d_g,
+                            const axi_c128 *d_a, const double *d_btilde, size_t btilde_count,
+                            const axi_c128 *d_d, int64_t ldd, axi_c128 *d_y, void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

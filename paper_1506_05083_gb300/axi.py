@@ -68,6 +68,52 @@ def svd_solve(US: torch.Tensor, V: torch.Tensor, sigma: torch.Tensor, B: torch.T
     return X
 
 
+def matvec_c128(A: torch.Tensor, X: torch.Tensor, out=None, work=None, stream=None) -> torch.Tensor:
+    """axi_matvec_c128: Y = A X for a column-major A held as [cols][ld >= rows]
+    (the layout of `Operator.c_block`) and X [nrhs][cols]; rows = A's ld.
+    Returns Y [nrhs][rows]."""
+    cols, rows = A.shape
+    nrhs = X.shape[0]
+    for t in (A, X):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2:
+            raise ValueError("matvec_c128: contiguous complex128 CUDA matrices expected")
+    if X.shape[1] != cols:
+        raise ValueError("matvec_c128: X must be [nrhs][cols of A]")
+    if out is None:
+        out = torch.empty((nrhs, rows), dtype=torch.complex128, device=A.device)
+    nb = C.c_size_t()
+    _check(lib().axi_matvec_workspace_bytes(rows, cols, nrhs, C.byref(nb)), "axi_matvec_workspace_bytes")
+    if work is None and nb.value:
+        work = torch.empty(nb.value, dtype=torch.uint8, device=A.device)
+    _check(lib().axi_matvec_c128(_dev(A), rows, rows, cols, _dev(X), cols, nrhs, _dev(out), out.shape[1],
+                                 _dev(work), 0 if work is None else work.numel() * work.element_size(),
+                                 _stream(stream)), "axi_matvec_c128")
+    return out
+
+
+def iter_combine(g, a, bt: torch.Tensor, d: torch.Tensor, p: int, out=None, stream=None) -> torch.Tensor:
+    """axi_iter_combine: y = g + a - (B~ d carried to the ring nodes) for
+    samples [W][rows][P] (g or a may be None: zero); bt the packed buffer of
+    `Operator.btilde`, d [W][ldd >= (p+1)^2] the leading part of xi."""
+    ref = g if g is not None else a
+    if ref is None:
+        raise ValueError("iter_combine: the sample shape comes from g or a")
+    W, rows, P = ref.shape
+    for t in [x for x in (g, a, d) if x is not None]:
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("iter_combine: contiguous complex128 CUDA tensors expected")
+    for t in [x for x in (g, a) if x is not None]:
+        if tuple(t.shape) != (W, rows, P):
+            raise ValueError("iter_combine: g and a must have the same [W][rows][P] shape")
+    if d.dim() != 2 or d.shape[0] != W:
+        raise ValueError("iter_combine: d must be [W][ldd]")
+    if out is None:
+        out = torch.empty((W, rows, P), dtype=torch.complex128, device=ref.device)
+    _check(lib().axi_iter_combine(W, rows, P, p, _dev(g), _dev(a), _dev(bt), bt.numel(), _dev(d),
+                                  d.shape[1], _dev(out), _stream(stream)), "axi_iter_combine")
+    return out
+
+
 class Cell(C.Structure):
     """axi_cell: the unit cell of the periodizing rows Q (include/axi_mfs.h)."""
     _fields_ = [("kx", C.c_double), ("ky", C.c_double), ("ex", C.c_double), ("ey", C.c_double),
@@ -146,6 +192,11 @@ SIGNATURES = [
     ("axi_svd_solve", C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_double, _vp,
                                 C.c_int64, C.c_int64, _vp, C.c_int64, _vp, _vp]),
     ("axi_fill_btilde", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]),
+    ("axi_matvec_workspace_bytes", C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_matvec_c128", C.c_int, [_vp, C.c_int64, C.c_int64, C.c_int64, _vp, C.c_int64, C.c_int32, _vp,
+                                  C.c_int64, _vp, C.c_size_t, _vp]),
+    ("axi_iter_combine", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_size_t,
+                                   _vp, C.c_int64, _vp, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
@@ -575,3 +626,23 @@ def spec_from_obstacle(ob, q: Optional[int] = None) -> ObstacleSpec:
                                        srcx if ob.bc == BC_TRANSMISSION else None)
     return ObstacleSpec(ob.bc, ob.M, ob.N, ob.P, q, ob.k, ob.k_minus, coll, src,
                         srcx if ob.bc == BC_TRANSMISSION else None)
+
+
+def periodic_iter_apply(op, g: torch.Tensor, lattice, dirs: torch.Tensor, C_blk: torch.Tensor,
+                        US: torch.Tensor, V: torch.Tensor, sigma: torch.Tensor, bt: torch.Tensor, p: int,
+                        cutoff=1e-10, near_slices=0, obs=0, want_coef=False, stream=None):
+    """One application of eq. iter's operator, y = (I + A_else A_0^+ -
+    B Q^+ C A_0^+) g, on Neumann boundary samples g [W][M][P]: the operator's
+    apply, the near-image sum (FP64 direct for near_slices 0, else split into
+    that many digits on tensor cores), C eta, the SVD solve with Q's factors
+    (US, V, sigma of `svd_jacobi`) and the combine, each through its own C
+    entry point on `stream`. C_blk from `Operator.c_block`, bt from
+    `Operator.btilde` (degree p). Returns y [W][M][P] (and A_0^+ g, [W][P][N],
+    when want_coef)."""
+    W = g.shape[0]
+    coef = op.apply(g, obs=obs, stream=stream)                                 # [W][P][N]
+    a = near_image_sum(op, coef, lattice, dirs, slices=near_slices, obs=obs, stream=stream)
+    c = matvec_c128(C_blk, coef.view(W, -1), stream=stream)                   # [W][8 M1^2]
+    xi = svd_solve(US, V, sigma, c, cutoff=cutoff, stream=stream)              # [W][nQ]
+    y = iter_combine(g, a.view(g.shape), bt, xi, p, stream=stream)
+    return (y, coef) if want_coef else y

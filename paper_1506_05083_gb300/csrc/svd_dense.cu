@@ -117,43 +117,107 @@ column_norm_kernel(const double2 *__restrict__ A, long long lda, int m, double *
   if (threadIdx.x == 0) sigma[blockIdx.x] = sqrt(v[0]);
 }
 
-// W(i, r) = [sigma_i > cut sigma_max] (U Sigma)(:, i)^H B(:, r) / sigma_i^2,
-// one CTA per (i, r)
+// W(i, r) = [sigma_i > cut sigma_max] (U Sigma)(:, i)^H B(:, r) / sigma_i^2:
+// one CTA per column i and group of NR right-hand sides, so each column of
+// U Sigma is read once per group; sigma_max is reduced by the CTA (the
+// values are not sorted). Columns r past nrhs read the last one and are not
+// written.
+template <int NR>
 __global__ void __launch_bounds__(kJT)
 svd_project_kernel(const double2 *__restrict__ US, long long lda, int m, const double *__restrict__ sigma,
-                   int n, double cutoff, const double2 *__restrict__ B, long long ldb,
+                   int n, double cutoff, const double2 *__restrict__ B, long long ldb, int nrhs,
                    double2 *__restrict__ W) {
-  __shared__ double red[kJT / 32][4];
-  const int i = blockIdx.x, rhs = blockIdx.y;
+  __shared__ double red[kJT / 32][2 * NR];
+  __shared__ double smax_w[kJT / 32];
+  const int i = blockIdx.x, r0 = blockIdx.y * NR;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double smax = 0.0;
-  for (int q = 0; q < n; ++q) smax = fmax(smax, sigma[q]);
-  const double si = sigma[i];
-  const double2 *u = US + (long long)i * lda, *b = B + (long long)rhs * ldb;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < n; q += kJT) smax = fmax(smax, sigma[q]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if (lane == 0) smax_w[wp] = smax;
+  const double2 *u = US + (long long)i * lda;
+  const double2 *b[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) b[j] = B + (long long)min(r0 + j, nrhs - 1) * ldb;
+  double2 acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = make_double2(0.0, 0.0);
   for (int k = threadIdx.x; k < m; k += kJT) {
-    const double2 a = u[k], y = b[k];
-    v[0] = fma(a.x, y.x, fma(a.y, y.y, v[0]));
-    v[1] = fma(a.x, y.y, fma(-a.y, y.x, v[1]));
+    const double2 a = u[k];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double2 y = b[j][k];
+      acc[j].x = fma(a.x, y.x, fma(a.y, y.y, acc[j].x));
+      acc[j].y = fma(a.x, y.y, fma(-a.y, y.x, acc[j].y));
+    }
   }
-  block_sum4(v, red);
-  if (threadIdx.x == 0) {
-    const double w = si > cutoff * smax ? 1.0 / (si * si) : 0.0;
-    W[(long long)rhs * n + i] = make_double2(v[0] * w, v[1] * w);
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
+      acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, o);
+    }
+    if (lane == 0) {
+      red[wp][2 * j] = acc[j].x;
+      red[wp][2 * j + 1] = acc[j].y;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NR && r0 + (int)threadIdx.x < nrhs) {
+    double sm = 0.0, re = 0.0, im = 0.0;
+    for (int q = 0; q < kJT / 32; ++q) {               // fixed order: reproducible
+      sm = fmax(sm, smax_w[q]);
+      re += red[q][2 * threadIdx.x];
+      im += red[q][2 * threadIdx.x + 1];
+    }
+    const double si = sigma[i];
+    const double w = si > cutoff * sm ? 1.0 / (si * si) : 0.0;
+    W[(long long)(r0 + threadIdx.x) * n + i] = make_double2(re * w, im * w);
   }
 }
 
-// X(:, r) = V W(:, r), one thread per (row, r)
-__global__ void svd_expand_kernel(const double2 *__restrict__ V, long long ldv, int n,
-                                  const double2 *__restrict__ W, double2 *__restrict__ X, long long ldx) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
-  if (row >= n) return;
-  double2 acc = make_double2(0.0, 0.0);
-  const double2 *w = W + (long long)rhs * n;
-  for (int i = 0; i < n; ++i) {
-    const double2 a = V[(long long)i * ldv + row], b = w[i];
-    acc = make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+// X(:, r) = V W(:, r): one CTA per 32 rows and group of NR right-hand sides;
+// its 8 warps take the terms i = warp (mod 8), the lanes the rows, and the
+// warps' partial sums are added in a fixed order through shared memory.
+template <int NR>
+__global__ void __launch_bounds__(kJT)
+svd_expand_kernel(const double2 *__restrict__ V, long long ldv, int n, const double2 *__restrict__ W,
+                  int nrhs, double2 *__restrict__ X, long long ldx) {
+  __shared__ double2 red[kJT / 32][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + lane, r0 = blockIdx.y * NR;
+  const int rr = min(row, n - 1);
+  const double2 *w[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) w[j] = W + (long long)min(r0 + j, nrhs - 1) * n;
+  double2 acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int i = wp; i < n; i += kJT / 32) {
+    const double2 a = V[(long long)i * ldv + rr];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double2 y = w[j][i];
+      acc[j].x = fma(a.x, y.x, fma(-a.y, y.y, acc[j].x));
+      acc[j].y = fma(a.x, y.y, fma(a.y, y.x, acc[j].y));
+    }
   }
-  X[(long long)rhs * ldx + row] = acc;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    red[wp][lane] = acc[j];
+    __syncthreads();
+    if (wp == 0 && row < n && r0 + j < nrhs) {
+      double2 s = red[0][lane];
+      for (int q = 1; q < kJT / 32; ++q) {
+        s.x += red[q][lane].x;
+        s.y += red[q][lane].y;
+      }
+      X[(long long)(r0 + j) * ldx + row] = s;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -209,16 +273,28 @@ cudaError_t svd_jacobi(double2 *A, long long m, long long n, long long lda, doub
   return cudaGetLastError();
 }
 
+template <int NR>
+cudaError_t svd_solve_nr(const double2 *US, const double2 *V, const double *sigma, long long m, long long n,
+                         long long lda, long long ldv, double cutoff, const double2 *B, long long ldb,
+                         long long nrhs, double2 *X, long long ldx, double2 *W, cudaStream_t st) {
+  const unsigned groups = (unsigned)((nrhs + NR - 1) / NR);
+  svd_project_kernel<NR><<<dim3((unsigned)n, groups), kJT, 0, st>>>(US, lda, (int)m, sigma, (int)n, cutoff,
+                                                                     B, ldb, (int)nrhs, W);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  svd_expand_kernel<NR><<<dim3((unsigned)((n + 31) / 32), groups), kJT, 0, st>>>(V, ldv, (int)n, W,
+                                                                                  (int)nrhs, X, ldx);
+  return cudaGetLastError();
+}
+
 cudaError_t svd_solve(const double2 *US, const double2 *V, const double *sigma, long long m, long long n,
                       long long lda, long long ldv, double cutoff, const double2 *B, long long ldb,
                       long long nrhs, double2 *X, long long ldx, double2 *W, cudaStream_t st) {
-  svd_project_kernel<<<dim3((unsigned)n, (unsigned)nrhs), kJT, 0, st>>>(US, lda, (int)m, sigma, (int)n,
-                                                                        cutoff, B, ldb, W);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  svd_expand_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)nrhs), 128, 0, st>>>(V, ldv, (int)n, W, X,
-                                                                                       ldx);
-  return cudaGetLastError();
+  if (nrhs <= 1) return svd_solve_nr<1>(US, V, sigma, m, n, lda, ldv, cutoff, B, ldb, nrhs, X, ldx, W, st);
+  if (nrhs <= 2) return svd_solve_nr<2>(US, V, sigma, m, n, lda, ldv, cutoff, B, ldb, nrhs, X, ldx, W, st);
+  if (nrhs <= 4) return svd_solve_nr<4>(US, V, sigma, m, n, lda, ldv, cutoff, B, ldb, nrhs, X, ldx, W, st);
+  if (nrhs <= 8) return svd_solve_nr<8>(US, V, sigma, m, n, lda, ldv, cutoff, B, ldb, nrhs, X, ldx, W, st);
+  return svd_solve_nr<16>(US, V, sigma, m, n, lda, ldv, cutoff, B, ldb, nrhs, X, ldx, W, st);
 }
 
 }  // namespace axi

@@ -199,3 +199,37 @@ def test_svd_arguments_refused_on_host():
                             C.byref(sw), None) == -1                                        # misaligned
     assert L.axi_svd_solve(p16, p16, p16, 8, 4, 8, 4, 1e-10, p16, 8, 0, p16, 4, p16, None) == -1
     assert L.axi_svd_solve(p16, p16, p16, 8, 4, 8, 4, 1e-10, p16, 7, 1, p16, 4, p16, None) == -1
+
+
+def test_iter_entries_refused_on_host():
+    """The dense C eta product and the eq. iter combine check their arguments
+    before any device work (AXI_ERR_ARG = -1, AXI_ERR_WORKSPACE = -4), and the
+    product's workspace size is host arithmetic: the cup's C (8192 x 64800)
+    with 16 vectors takes 19 column slices of 8192 x 16 partial sums."""
+    import ctypes as C
+    from paper_1506_05083_gb300 import axi
+    L = axi.lib()
+    nb = C.c_size_t()
+    assert L.axi_matvec_workspace_bytes(8192, 64800, 16, C.byref(nb)) == 0
+    assert nb.value == 19 * 16 * 8192 * 16
+    assert L.axi_matvec_workspace_bytes(300, 50, 4, C.byref(nb)) == 0 and nb.value == 0
+    assert L.axi_matvec_workspace_bytes(300, 50, 17, C.byref(nb)) == -1
+    assert L.axi_matvec_workspace_bytes(0, 50, 1, C.byref(nb)) == -1
+    p16 = C.c_void_p(1 << 20)                     # aligned stand-ins, never dereferenced
+    bad = C.c_void_p((1 << 20) + 8)
+    mv = L.axi_matvec_c128
+    assert mv(None, 8, 8, 4, p16, 4, 1, p16, 8, None, 0, None) == -1
+    assert mv(p16, 7, 8, 4, p16, 4, 1, p16, 8, None, 0, None) == -1            # lda < rows
+    assert mv(p16, 8, 8, 4, p16, 3, 1, p16, 8, None, 0, None) == -1            # ldx < cols
+    assert mv(p16, 8, 8, 4, p16, 4, 0, p16, 8, None, 0, None) == -1            # no vectors
+    assert mv(p16, 8, 8, 4, p16, 4, 17, p16, 8, None, 0, None) == -1           # too many
+    assert mv(bad, 8, 8, 4, p16, 4, 1, p16, 8, None, 0, None) == -1            # misaligned
+    assert mv(p16, 300, 300, 1000, p16, 1000, 3, p16, 300, None, 0, None) == -4  # no workspace
+    cb = L.axi_iter_combine
+    # packed B~ of rows 40, P 16, p 8: modes 0..8 of widths 9..1 -> 45 columns
+    assert cb(2, 40, 16, 8, p16, p16, p16, 45 * 40 - 1, p16, 81, p16, None) == -1   # short B~
+    assert cb(2, 40, 16, 8, p16, p16, p16, 45 * 40, p16, 80, p16, None) == -1       # ldd < 81
+    assert cb(2, 40, 1537, 8, p16, p16, p16, 1 << 30, p16, 81, p16, None) == -1     # P too large
+    assert cb(2, 40, 16, 256, p16, p16, p16, 1 << 30, p16, 257 * 257, p16, None) == -1   # p > 255
+    assert cb(2, 40, 16, 8, bad, p16, p16, 45 * 40, p16, 81, p16, None) == -1       # misaligned g
+    assert cb(2, 40, 16, 8, p16, p16, None, 45 * 40, p16, 81, p16, None) == -1      # no B~

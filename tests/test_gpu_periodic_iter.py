@@ -1,0 +1,145 @@
+"""One application of the preconditioned periodic operator (Sec. 4.2, eq.
+iter) on the GPU against the oracle: the dense C eta product, the B~ term
+carried back to the ring nodes with the combine, and the whole composite
+y = (I + A_else A_0^+ - B Q^+ C A_0^+) g."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import mfs as OM
+from oracle import periodizing as OP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("rows,cols,nrhs", [(300, 1000, 1), (300, 1000, 3), (97, 5000, 16), (64, 50, 5),
+                                            (1, 1, 1)])
+def test_matvec_parity(rows, cols, nrhs):
+    """Y = A X against numpy's product: within 1e-13 of sum |A| |X| per row
+    (the summation order differs), and the same bits on a second run."""
+    from paper_1506_05083_gb300 import axi
+    rng = np.random.default_rng(rows + cols + nrhs)
+    A = rng.normal(size=(cols, rows)) + 1j * rng.normal(size=(cols, rows))      # column-major A
+    X = rng.normal(size=(nrhs, cols)) + 1j * rng.normal(size=(nrhs, cols))
+    At, Xt = torch.tensor(A, device="cuda"), torch.tensor(X, device="cuda")
+    Y1 = axi.matvec_c128(At, Xt)
+    Y2 = axi.matvec_c128(At, Xt)
+    torch.cuda.synchronize()
+    ref = X @ A                                                                  # [nrhs][rows]
+    bound = np.abs(X) @ np.abs(A)
+    assert np.all(np.abs(Y1.cpu().numpy() - ref) <= 1e-13 * bound + 1e-300)
+    assert torch.equal(Y1, Y2)
+
+
+def _small_op(P=16):
+    from paper_1506_05083_gb300 import axi
+    wl = synth.small_case(seed=7, k=3.0, M=40, N=32, P=P)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=axi.PREC_FP64)
+    return axi, wl, ob, coll, src, srcx, op
+
+
+@pytest.mark.parametrize("p", [6, 8, 12])
+def test_iter_combine_btilde_term(p):
+    """y = g + a - B d against g + a - `btilde_samples`: p below, at and above
+    P/2 (modes |n| > P/2 of the waves are not held by the rows), and with g
+    and a left out (B d alone, negated)."""
+    axi, wl, ob, coll, src, srcx, op = _small_op()
+    rng = np.random.default_rng(p)
+    W, nh = 2, OP.n_harmonics(p)
+    d = rng.normal(size=(W, nh + 3)) + 1j * rng.normal(size=(W, nh + 3))         # ldd > (p+1)^2
+    g = rng.normal(size=(W, ob.M, ob.P)) + 1j * rng.normal(size=(W, ob.M, ob.P))
+    a = rng.normal(size=g.shape) + 1j * rng.normal(size=g.shape)
+    _, bt = op.btilde(p)
+    dt, gt, at = (torch.tensor(x, device="cuda") for x in (d, g, a))
+    y = axi.iter_combine(gt, at, bt, dt, p).cpu().numpy()
+    y0 = axi.iter_combine(None, at * 0, bt, dt, p).cpu().numpy()
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    Bd = OP.btilde_samples(ob, coll, p, d[:, :nh])
+    scale = np.abs(Bd).max()
+    assert np.abs(y0 + Bd).max() < 1e-12 * scale
+    assert np.abs(y - (g + a - Bd)).max() < 1e-12 * max(scale, np.abs(g).max())
+
+
+def _abs_image_bound(ob, coll, src, coef, lattice):
+    """max over targets and waves of sum |dG/dn| |sigma| over the eight
+    images: the scale a digit split's rounding is relative to (large
+    coefficients whose images cancel leave the sum itself far smaller)."""
+    P, k = ob.P, ob.k
+    sig = np.abs(O.point_strengths(coef, P).reshape(coef.shape[0], -1))
+    X, Nv = OP._ring_nodes(coll, P)
+    X, Nv = X.reshape(-1, 3), Nv.reshape(-1, 3)
+    Y = OM._source_points(src, P).reshape(-1, 3)
+    B = 0.0
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            if a or b:
+                Dv = X[:, None, :] - (Y[None] + np.array([a * lattice[0], b * lattice[1], 0.0]))
+                R = np.linalg.norm(Dv, axis=-1)
+                K = np.abs(np.einsum("tc,tsc->ts", Nv, Dv)) * np.abs(1j * k * R - 1.0) / (4 * np.pi * R ** 3)
+                B = B + sig @ K.T
+    return np.max(B)
+
+
+@pytest.mark.parametrize("near_slices", [0, 6, 7])
+def test_periodic_iter_apply_parity(near_slices):
+    """The composite on the small obstacle in a cell of the same Bloch phases
+    as the near-image sum's waves: (1) every step after A_0^+ against the
+    oracle's steps on the device's own coefficients, 1e-11 of the output
+    scale; (2) the coefficients against the oracle's QR solve by the boundary
+    residual (they are not unique); (3) the whole output against the oracle's
+    composite, within the spread the coefficients' non-uniqueness allows.
+    With the near-image sum split into digits, (1) and (3) are bounded by the
+    split's rounding, relative to sum |dG/dn| |sigma| (2^-37 of it for 6
+    digits of 7 bits, 2^-44 for 7, with the FP32 group sums' margin)."""
+    axi, wl, ob, coll, src, srcx, op = _small_op()
+    ob.q = O.choose_q(ob, coll, src, srcx)
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    ex, ey, z0, m1, n0, p = 2.6, 2.3, 1.6, 6, 3, 8
+    cell = axi.Cell(ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, n0, p)
+    W = 2
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=(W, ob.M, ob.P)) + 1j * rng.normal(size=(W, ob.M, ob.P))
+    dirs = np.stack([d] * W)
+    Cg = op.c_block(cell)
+    Qg = op.q_matrix(cell)
+    US = Qg.clone()
+    V, sig, sweeps = axi.svd_jacobi(US)
+    _, bt = op.btilde(p)
+    y, coef = axi.periodic_iter_apply(op, torch.tensor(g, device="cuda"), (ex, ey),
+                                      torch.tensor(dirs, device="cuda"), Cg, US, V, sig, bt, p,
+                                      near_slices=near_slices, want_coef=True)
+    torch.cuda.synchronize()
+    assert op.status() == 0
+    y, c_gpu = y.cpu().numpy(), coef.cpu().numpy()
+    Co = OP.c_matrix(ob, src, cell.kx, cell.ky, ex, ey, z0, m1)
+    Qo, _ = OP.q_matrix(ob.k, p, cell.kx, cell.ky, ex, ey, z0, m1, n0)
+    # (1) the steps after A_0^+ on the device's coefficients
+    ae = O.near_image_sum(ob, coll, src, c_gpu, dirs, (ex, ey)).reshape(g.shape)
+    xi, _ = OP.q_pinv_solve(Qo, (c_gpu.reshape(W, -1) @ Co.T).T, 1e-10)
+    y_steps = g + ae - OP.btilde_samples(ob, coll, p, xi[:OP.n_harmonics(p)].T)
+    e1 = np.abs(y - y_steps).max() / np.abs(y_steps).max()
+    # (2) A_0^+ against the oracle's factors by the boundary residual
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    fh = O.rhs_modes(g)
+    c_ora = O.solve_modes(ob, fac, fh)
+    An = A[np.minimum(np.arange(ob.P), ob.P - np.arange(ob.P))]                # mode slot -> |n|
+    res = np.abs(np.einsum("prc,wpc->wpr", An, c_gpu - c_ora)).max() / np.abs(fh).max()
+    # (3) the whole composite
+    y_ora = OP.periodic_operator_apply(ob, coll, src, fac, g, dirs, (ex, ey), Co, Qo, p)
+    e3 = np.abs(y - y_ora).max() / np.abs(y_ora).max()
+    print(f"slices {near_slices}: steps {e1:.3e}  coef residual {res:.3e}  composite {e3:.3e}  "
+          f"sweeps {sweeps}")
+    if near_slices:
+        bound = _abs_image_bound(ob, coll, src, c_gpu, (ex, ey)) / np.abs(y_steps).max()
+        print(f"  sum|K||sigma| / max|y| = {bound:.3e}; error / bound: {e1 / bound:.3e}")
+        tol = 2.0 ** (-7 * near_slices + 5) * bound + 1e-11
+    else:
+        tol = 1e-11
+    assert e1 < tol
+    assert res < 1e-10
+    assert e3 < max(tol, 1e-11)

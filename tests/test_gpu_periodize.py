@@ -155,10 +155,12 @@ def _prescribed(rng, m, n, s):
     return (U * s) @ V.conj().T, V
 
 
-def test_svd_jacobi_prescribed():
+@pytest.mark.parametrize("nrhs", [1, 3, 16, 21])
+def test_svd_jacobi_prescribed(nrhs):
     """The one-sided Jacobi SVD of a matrix with prescribed singular values
     (a gap at 1e-13): the values come back, (U Sigma) V^H rebuilds the
-    matrix, V is unitary, and the truncated solve equals the oracle's."""
+    matrix, V is unitary, and the truncated solve equals the oracle's for
+    nrhs right-hand sides (groups of up to 16; 21 leaves a ragged group)."""
     from paper_1506_05083_gb300 import axi
     rng = np.random.default_rng(4)
     m, n = 70, 45
@@ -173,7 +175,7 @@ def test_svd_jacobi_prescribed():
     assert np.abs(np.sort(sg)[::-1] - s).max() < 1e-13
     assert np.abs(US @ Vn.conj().T - A).max() < 1e-13
     assert np.abs(Vn.conj().T @ Vn - np.eye(n)).max() < 1e-13
-    B = rng.normal(size=(m, 3)) + 1j * rng.normal(size=(m, 3))
+    B = rng.normal(size=(m, nrhs)) + 1j * rng.normal(size=(m, nrhs))
     X = axi.svd_solve(At, V, sigma, torch.tensor(np.ascontiguousarray(B.T), device="cuda"), cutoff=1e-10)
     Xo, _ = OP.q_pinv_solve(A, B, 1e-10)
     assert np.abs(X.cpu().numpy().T - Xo).max() < 1e-9 * np.abs(Xo).max()
