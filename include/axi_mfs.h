@@ -478,6 +478,51 @@ axi_status axi_iter_combine(int32_t W, int32_t rows, int32_t P, int32_t p, const
                             const axi_c128 *d_a, const double *d_btilde, size_t btilde_count,
                             const axi_c128 *d_d, int64_t ldd, axi_c128 *d_y, void *stream);
 
+/*
+ * Restarted GMRES (Sec. 4.2: eq. iter is solved by a Krylov method) for W
+ * independent systems A x_w = b_w of length n that share one operator, by
+ * reverse communication: the library keeps the Krylov state and asks the
+ * caller to apply A, so any composition of entry points can serve as A (for
+ * eq. iter: the five calls listed above axi_matvec_c128).
+ *
+ * axi_gmres_workspace_bytes: device bytes for n, W and the restart length
+ * (1..512): the (restart + 1) basis blocks of W x n complex values, one more
+ * block and a few scalars per wave. axi_gmres_create binds a caller-owned,
+ * 256-byte aligned device buffer of that size and the stopping rule:
+ * ||b_w - A x_w|| <= tol ||b_w||, at most max_iter Arnoldi steps per wave.
+ * The host state it allocates is released by axi_gmres_destroy (the device
+ * buffer stays the caller's).
+ *
+ * axi_gmres_iterate(g, d_b, d_x, &need, &d_in, &d_out, stream): d_b and d_x
+ * are [W][n] (16-byte aligned, not aliased). Starts from x = 0 on the first
+ * call. When it returns with need = 1, the caller writes A applied to the W
+ * vectors at d_in into d_out (both [W][n], inside the workspace or d_x; the
+ * operator must map zero to zero: a converged wave is fed zeros) on
+ * `stream`, then calls again with the same arguments; need = 0 means the
+ * solve has ended and d_x holds the iterate. Arnoldi uses classical
+ * Gram-Schmidt twice; a Hessenberg column is reduced by complex Givens
+ * rotations on the host; each restart forms b - A x by one application.
+ * The call synchronises `stream` (it reads the Arnoldi scalars).
+ * axi_gmres_result writes, per wave, the Arnoldi steps taken, the last
+ * relative residual (the true one at each restart, the Givens estimate in
+ * between) and whether tol was met (any argument may be null).
+ * Errors: AXI_ERR_ARG, AXI_ERR_WORKSPACE (buffer too small or misaligned),
+ * AXI_ERR_NUMERIC (a non-finite residual: the solve stops), AXI_ERR_CUDA.
+ *
+ * axi_vec_scale: x *= alpha for `count` complex values (e.g. xi = -Q^+ C eta
+ * from the SVD solve's output). Errors: AXI_ERR_ARG, AXI_ERR_CUDA.
+ */
+typedef struct axi_gmres axi_gmres;
+axi_status axi_gmres_workspace_bytes(int64_t n, int32_t W, int32_t restart, size_t *bytes);
+axi_status axi_gmres_create(int64_t n, int32_t W, int32_t restart, int32_t max_iter, double tol,
+                            void *d_work, size_t work_bytes, axi_gmres **out);
+axi_status axi_gmres_destroy(axi_gmres *g);
+axi_status axi_gmres_iterate(axi_gmres *g, const axi_c128 *d_b, axi_c128 *d_x, int32_t *need_apply,
+                             const axi_c128 **d_in, axi_c128 **d_out, void *stream);
+axi_status axi_gmres_result(const axi_gmres *g, int32_t *h_iters, double *h_relres,
+                            int32_t *h_converged);
+axi_status axi_vec_scale(int64_t count, double alpha, axi_c128 *d_x, void *stream);
+
 /* Device view of the packed factors of one obstacle (read-only). For mode d,
  * A + d*cols*rows is the rows x cols column-major array with R on and above
  * the diagonal (real diagonal) and the reflector vectors below it; tau + d*cols

@@ -74,6 +74,8 @@ Pins (tests/test_oracle_periodizing.py):
                      normal derivative, sum d_lm dn u_lm, at the P ring nodes
                      (no trapezoid sum, no transform)
   periodic_operator_apply   composed of the functions above, each pinned
+  periodic_solve_dense      the assembled matrix reproduces the operator on
+                     a random vector; the solve is LAPACK's
 """
 from __future__ import annotations
 
@@ -87,7 +89,7 @@ from .mfs import near_image_sum, rhs_modes, solve_modes
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
            "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix",
            "c_matrix", "q_pinv_solve", "btilde_samples",
-           "periodic_operator_apply"]
+           "periodic_operator_apply", "periodic_solve_dense"]
 
 
 def n_harmonics(p):
@@ -397,3 +399,21 @@ def periodic_operator_apply(ob, coll, src, factors, g, dirs, lattice, C, Q, p, c
     yC = coef.reshape(W, -1) @ C.T                                             # [W][8 M1^2]
     xi, _ = q_pinv_solve(Q, yC.T, cutoff)                                      # [nQ][W]
     return g + ae - btilde_samples(ob, coll, p, xi[:n_harmonics(p)].T)
+
+
+def periodic_solve_dense(ob, coll, src, factors, f, dirs, lattice, C, Q, p, cutoff=1e-10):
+    """Eq. iter solved directly, for small cases (Sec. 4.2): the operator's
+    matrix over the n = M P samples, column i the image of unit vector i
+    under `periodic_operator_apply`, solved by LAPACK for every wave of f
+    [W][M][P]; then eta = A_0^+ eta~ (`solve_modes`) and xi = -Q^+ C eta
+    (`q_pinv_solve`). dirs [3] is the Bloch direction. Returns (eta~ [W][M][P],
+    eta [W][P][N], xi [W][nQ], the operator matrix [n][n])."""
+    W, M, P = f.shape
+    n = M * P
+    E = np.eye(n, dtype=np.complex128).reshape(n, M, P)
+    Aop = periodic_operator_apply(ob, coll, src, factors, E, np.stack([np.asarray(dirs)] * n), lattice,
+                                  C, Q, p, cutoff).reshape(n, n).T
+    et = np.linalg.solve(Aop, f.reshape(W, n).T).T.reshape(W, M, P)
+    eta = solve_modes(ob, factors, rhs_modes(et))
+    xi, _ = q_pinv_solve(Q, (eta.reshape(W, -1) @ C.T).T, cutoff)
+    return et, eta, -xi.T, Aop

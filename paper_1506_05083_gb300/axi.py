@@ -197,6 +197,14 @@ SIGNATURES = [
                                   C.c_int64, _vp, C.c_size_t, _vp]),
     ("axi_iter_combine", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_size_t,
                                    _vp, C.c_int64, _vp, _vp]),
+    ("axi_gmres_workspace_bytes", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("axi_gmres_create", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, C.c_size_t,
+                                   C.POINTER(_vp)]),
+    ("axi_gmres_destroy", C.c_int, [_vp]),
+    ("axi_gmres_iterate", C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int32), C.POINTER(_vp), C.POINTER(_vp),
+                                    _vp]),
+    ("axi_gmres_result", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    ("axi_vec_scale", C.c_int, [C.c_int64, C.c_double, _vp, _vp]),
     ("axi_operator_factors", C.c_int, [_vp, C.c_int32, C.POINTER(_FactorView)]),
     ("axi_operator_svd", C.c_int, [_vp, C.c_int32, C.POINTER(_SvdView)]),
     ("axi_incident_planewaves", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
@@ -630,7 +638,7 @@ def spec_from_obstacle(ob, q: Optional[int] = None) -> ObstacleSpec:
 
 def periodic_iter_apply(op, g: torch.Tensor, lattice, dirs: torch.Tensor, C_blk: torch.Tensor,
                         US: torch.Tensor, V: torch.Tensor, sigma: torch.Tensor, bt: torch.Tensor, p: int,
-                        cutoff=1e-10, near_slices=0, obs=0, want_coef=False, stream=None):
+                        cutoff=1e-10, near_slices=0, obs=0, want_coef=False, out=None, stream=None):
     """One application of eq. iter's operator, y = (I + A_else A_0^+ -
     B Q^+ C A_0^+) g, on Neumann boundary samples g [W][M][P]: the operator's
     apply, the near-image sum (FP64 direct for near_slices 0, else split into
@@ -644,5 +652,67 @@ def periodic_iter_apply(op, g: torch.Tensor, lattice, dirs: torch.Tensor, C_blk:
     a = near_image_sum(op, coef, lattice, dirs, slices=near_slices, obs=obs, stream=stream)
     c = matvec_c128(C_blk, coef.view(W, -1), stream=stream)                   # [W][8 M1^2]
     xi = svd_solve(US, V, sigma, c, cutoff=cutoff, stream=stream)              # [W][nQ]
-    y = iter_combine(g, a.view(g.shape), bt, xi, p, stream=stream)
+    y = iter_combine(g, a.view(g.shape), bt, xi, p, out=out, stream=stream)
     return (y, coef) if want_coef else y
+
+
+def gmres(apply_fn, b: torch.Tensor, tol=1e-12, restart=40, max_iter=400, stream=None):
+    """axi_gmres_*: solve A x_w = b_w for every wave w of b [W][...] (complex128,
+    CUDA) by restarted GMRES from x = 0; apply_fn(v, out) writes A v into out
+    (both shaped like b). Returns (x, iterations, relative residuals,
+    converged flags)."""
+    if b.dtype != torch.complex128 or not b.is_cuda or not b.is_contiguous():
+        raise ValueError("gmres: b must be a contiguous complex128 CUDA tensor")
+    W = b.shape[0]
+    n = b[0].numel()
+    x = torch.empty_like(b)
+    nb = C.c_size_t()
+    _check(lib().axi_gmres_workspace_bytes(n, W, restart, C.byref(nb)), "axi_gmres_workspace_bytes")
+    work = torch.empty(nb.value, dtype=torch.uint8, device=b.device)
+    g = C.c_void_p()
+    _check(lib().axi_gmres_create(n, W, restart, max_iter, tol, _dev(work), nb.value, C.byref(g)),
+           "axi_gmres_create")
+    blk = 16 * W * n
+
+    def view(ptr):
+        if ptr == x.data_ptr():
+            return x
+        off = ptr - work.data_ptr()
+        if off < 0 or off + blk > nb.value:
+            raise RuntimeError("gmres: the driver asked for a block outside its buffers")
+        return work[off:off + blk].view(torch.complex128).view(b.shape)
+
+    try:
+        need, din, dout = C.c_int32(), C.c_void_p(), C.c_void_p()
+        while True:
+            _check(lib().axi_gmres_iterate(g, _dev(b), _dev(x), C.byref(need), C.byref(din), C.byref(dout),
+                                           _stream(stream)), "axi_gmres_iterate")
+            if not need.value:
+                break
+            apply_fn(view(din.value), view(dout.value))
+        its = (C.c_int32 * W)()
+        rel = (C.c_double * W)()
+        conv = (C.c_int32 * W)()
+        _check(lib().axi_gmres_result(g, its, rel, conv), "axi_gmres_result")
+    finally:
+        lib().axi_gmres_destroy(g)
+    return x, list(its), list(rel), [bool(c) for c in conv]
+
+
+def periodic_solve(op, f: torch.Tensor, lattice, dirs: torch.Tensor, C_blk: torch.Tensor, US: torch.Tensor,
+                   V: torch.Tensor, sigma: torch.Tensor, bt: torch.Tensor, p: int, cutoff=1e-10, near_slices=0,
+                   tol=1e-12, restart=40, max_iter=400, obs=0, stream=None):
+    """Eq. iter solved by GMRES for Neumann boundary samples f [W][M][P], then
+    eta = A_0^+ eta~ and xi = -Q^+ C eta (Sec. 4.2). Returns (eta~ [W][M][P],
+    eta [W][P][N], xi [W][nQ], iterations, relative residuals, converged)."""
+    def apply_fn(v, out):
+        periodic_iter_apply(op, v, lattice, dirs, C_blk, US, V, sigma, bt, p, cutoff=cutoff,
+                            near_slices=near_slices, obs=obs, out=out, stream=stream)
+
+    et, its, rel, conv = gmres(apply_fn, f, tol=tol, restart=restart, max_iter=max_iter, stream=stream)
+    eta = op.apply(et, obs=obs, stream=stream)
+    W = f.shape[0]
+    c = matvec_c128(C_blk, eta.view(W, -1), stream=stream)
+    xi = svd_solve(US, V, sigma, c, cutoff=cutoff, stream=stream)
+    _check(lib().axi_vec_scale(xi.numel(), -1.0, _dev(xi), _stream(stream)), "axi_vec_scale")
+    return et, eta, xi, its, rel, conv

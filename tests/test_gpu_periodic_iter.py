@@ -143,3 +143,65 @@ def test_periodic_iter_apply_parity(near_slices):
     assert e1 < tol
     assert res < 1e-10
     assert e3 < max(tol, 1e-11)
+
+
+def test_gmres_dense_operator():
+    """The GMRES driver alone on A = I + K (K Gaussian, spectral radius about
+    1/2; n = 300) applied by the matvec kernel, restart 10 so that the true
+    residual is re-formed several times; a zero right-hand side stays zero
+    with no steps. Against LAPACK's solve."""
+    from paper_1506_05083_gb300 import axi
+    rng = np.random.default_rng(8)
+    n, W = 300, 3
+    K = (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / (2 * np.sqrt(2 * n))
+    A = np.eye(n) + K
+    b = rng.normal(size=(W, n)) + 1j * rng.normal(size=(W, n))
+    b[2] = 0.0
+    At = torch.tensor(np.ascontiguousarray(A.T), device="cuda")                 # column-major A
+    x, its, rel, conv = axi.gmres(lambda v, out: axi.matvec_c128(At, v, out=out),
+                                  torch.tensor(b, device="cuda"), tol=1e-12, restart=10, max_iter=400)
+    torch.cuda.synchronize()
+    xr = np.linalg.solve(A, b[:2].T).T
+    assert conv == [True, True, True]
+    assert its[2] == 0 and np.all(x[2].cpu().numpy() == 0)
+    assert max(rel[:2]) <= 1e-12
+    assert np.abs(x[:2].cpu().numpy() - xr).max() < 1e-10 * np.abs(xr).max()
+    assert 10 < its[0] <= 400
+
+
+def test_periodic_solve_small():
+    """Eq. iter solved by GMRES on the GPU (tol 1e-12) for the small obstacle's
+    incident data in its cell: eta~ against the oracle's dense solve; the
+    residual of eq. iter and xi = -Q^+ C eta recomputed by the oracle's steps
+    from the device's eta~, eta and xi."""
+    axi, wl, ob, coll, src, srcx, op = _small_op()
+    ob.q = O.choose_q(ob, coll, src, srcx)
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    ex, ey, z0, m1, n0, p = 2.6, 2.3, 1.6, 6, 3, 8
+    cell = axi.Cell(ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, n0, p)
+    dirs = np.stack([d, d])
+    f = O.incident_samples(ob, coll, dirs)                                       # [W][M][P]
+    Cg, US = op.c_block(cell), op.q_matrix(cell)
+    V, sig, _ = axi.svd_jacobi(US)
+    _, bt = op.btilde(p)
+    et, eta, xi, its, rel, conv = axi.periodic_solve(op, torch.tensor(f, device="cuda"), (ex, ey),
+                                                     torch.tensor(dirs, device="cuda"), Cg, US, V, sig,
+                                                     bt, p, tol=1e-12, restart=40)
+    torch.cuda.synchronize()
+    assert op.status() == 0 and all(conv), (its, rel)
+    et, eta, xi = et.cpu().numpy(), eta.cpu().numpy(), xi.cpu().numpy()
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    Co = OP.c_matrix(ob, src, cell.kx, cell.ky, ex, ey, z0, m1)
+    Qo, _ = OP.q_matrix(ob.k, p, cell.kx, cell.ky, ex, ey, z0, m1, n0)
+    et_o, _, _, Aop = OP.periodic_solve_dense(ob, coll, src, fac, f, d, (ex, ey), Co, Qo, p)
+    e_et = np.abs(et - et_o).max() / np.abs(et_o).max()
+    ae = O.near_image_sum(ob, coll, src, eta, dirs, (ex, ey)).reshape(f.shape)
+    res = et + ae + OP.btilde_samples(ob, coll, p, xi[:, :OP.n_harmonics(p)]) - f
+    e_res = np.abs(res).max() / np.abs(f).max()
+    xo, _ = OP.q_pinv_solve(Qo, (eta.reshape(2, -1) @ Co.T).T, 1e-10)
+    e_xi = np.abs(xi + xo.T).max() / np.abs(xo).max()
+    print(f"iters {its} relres {rel}  eta~ {e_et:.2e}  residual {e_res:.2e}  xi {e_xi:.2e}  "
+          f"cond {np.linalg.cond(Aop):.1f}")
+    assert e_et < 1e-10
+    assert e_res < 1e-10
+    assert e_xi < 1e-10

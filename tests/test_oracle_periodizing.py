@@ -208,3 +208,27 @@ def test_btilde_samples_direct_expansion():
             ref += d[:, l * l + l + m][:, None, None] * dn[None]
     got = OP.btilde_samples(ob, coll, p, d)
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_periodic_solve_dense_assembly():
+    """The dense matrix of eq. iter's operator (columns = images of the unit
+    vectors) reproduces the operator on a random vector, and its solution
+    leaves a residual at rounding level: pins the assembly's orientation."""
+    wl = synth.small_case(seed=7, k=3.0, M=20, N=16, P=8)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    ob.q = O.choose_q(ob, coll, src, srcx)
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    ex, ey, z0, m1, n0, p = 2.6, 2.3, 1.6, 6, 2, 3
+    C = OP.c_matrix(ob, src, ob.k * d[0], ob.k * d[1], ex, ey, z0, m1)
+    Q, _ = OP.q_matrix(ob.k, p, ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, n0)
+    rng = np.random.default_rng(2)
+    f = rng.normal(size=(2, ob.M, ob.P)) + 1j * rng.normal(size=(2, ob.M, ob.P))
+    et, eta, xi, Aop = OP.periodic_solve_dense(ob, coll, src, fac, f, d, (ex, ey), C, Q, p)
+    v = rng.normal(size=(1, ob.M, ob.P)) + 1j * rng.normal(size=(1, ob.M, ob.P))
+    Av = OP.periodic_operator_apply(ob, coll, src, fac, v, d[None], (ex, ey), C, Q, p)
+    assert np.abs(Aop @ v.ravel() - Av.ravel()).max() < 1e-12 * np.abs(Av).max()
+    back = OP.periodic_operator_apply(ob, coll, src, fac, et, np.stack([d, d]), (ex, ey), C, Q, p)
+    assert np.abs(back - f).max() < 1e-10 * np.abs(f).max()
+    assert xi.shape == (2, Q.shape[1]) and eta.shape == (2, ob.P, ob.N)
