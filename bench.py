@@ -23,10 +23,12 @@ cores; its coefficients also give the line's parity errors e_bd and e_ff.
 
 `--impl reference` times the oracle as the reference arm: each step is one
 distinct mode's share of the workload (see reference_step). `--workload
-smooth | batched | cup_near | cup_btilde | cup_q | cup_c | cup_qsvd | cup_iter` prints
+smooth | batched | cup_near | cup_btilde | cup_q | cup_c | cup_qsvd | cup_iter |
+cup_solve` prints
 the other workloads' lines (cup_btilde, cup_q, cup_c: the periodizing
 scheme's blocks B~, Q and C for the cup; cup_qsvd: the SVD of that Q;
-cup_iter: one application of the preconditioned periodic operator). Multi-GPU
+cup_iter: one application of the preconditioned periodic operator; cup_solve:
+eq. iter solved by GMRES). Multi-GPU
 (torchrun): each rank runs its own copy of the workload (the (obstacle, mode)
 tasks are independent), value sums the ranks' work over the slowest rank's
 time ("weak" scaling), with no collective on the data path.
@@ -999,6 +1001,70 @@ def run_iter(args):
     print(json.dumps(line))
 
 
+def run_solve(args):
+    """Eq. iter solved by GMRES for the cup in its cell (cup_cell): one
+    incident direction (it fixes the Bloch vector, hence C and Q), the data
+    f = -du_inc/dn at the ring nodes, tol 1e-12 (the paper's), restart 60,
+    A_0^+ as the truncated SVD (the paper's form: the QR least-squares
+    solve of rough Krylov vectors gives coefficients large enough for the
+    split near-image sum's rounding, relative to sum |K| |sigma|, to swamp
+    the output), the near-image sum split into 7 digits; then eta = A_0^+ eta~ and
+    xi = -Q^+ C eta. C, Q, Q's SVD and B~ are formed once, untimed; warm-up
+    steps are single operator applications; each timed step is one whole
+    solve (CUDA events around it)."""
+    import torch
+    from paper_1506_05083_gb300 import axi
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.config_cup()
+    ob = wl.obstacles[0]
+    prec = axi.PREC_SPLIT_BF16 | (args.slices << 8) if args.prec == "split" else axi.PREC_FP64
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=prec | axi.PLAN_TSVD)
+    cell = cup_cell(axi, wl)
+    d0 = synth.plane_wave_directions(wl.n_waves, wl.wave_seed)[0]
+    dirs = torch.tensor(d0[None], device=dev)
+    lat = (cell.ex, cell.ey)
+    Cb = op.c_block(cell)
+    US = op.q_matrix(cell)
+    V, sigma, sweeps = axi.svd_jacobi(US)
+    _, bt = op.btilde(cell.p)
+    f = op.incident(dirs)                                                     # [1][M][P]
+    for _ in range(args.warmup):
+        axi.periodic_iter_apply(op, f, lat, dirs, Cb, US, V, sigma, bt, cell.p, near_slices=7)
+    torch.cuda.synchronize()
+    if op.status() != 0:
+        raise RuntimeError("device status word set during warm-up")
+    stream = torch.cuda.current_stream()
+    ts, its, rels = [], [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            et, eta, xi, it, rel, conv = axi.periodic_solve(op, f, lat, dirs, Cb, US, V, sigma, bt, cell.p,
+                                                            near_slices=7, tol=1e-12, restart=60,
+                                                            max_iter=args.max_iter)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            its.append(it[0])
+            rels.append(rel[0])
+    ms = float(np.mean(ts))
+    line = {"metric": "periodic solve of eq. iter by GMRES (Sec. 4.2), tol 1e-12", "value": ms * 1e3,
+            "unit": "us", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cup_k25_cell13_M1_{cell.m1}_N0_{cell.n0}_p{cell.p}_solve",
+                       "M": ob.M, "N": ob.N, "P": ob.P, "prec": args.prec, "A0_plus": "truncated SVD",
+                       "restart": 60, "max_iter": args.max_iter,
+                       "near_image_sum": "split, 7 digits", "svd_sweeps": sweeps,
+                       "warmup": "single operator applications"},
+            "gmres_iterations": its, "relres": rels, "converged": bool(conv[0]),
+            "ms_per_iteration": ms / max(1, its[-1]),
+            "xi_norm": float(xi.abs().max()), "gpu_launches": None, "clocks": clk.summary(),
+            "device_status": op.status()}
+    print(json.dumps(line))
+
+
 def run_btilde(args):
     """The periodizing scheme's spherical-wave block B~ (Sec. 4.1) of the cup
     at degree p = 48: device time of one fill of all mode blocks (CUDA events,
@@ -1086,6 +1152,8 @@ def main():
     ap.add_argument("--prec", default="split", choices=["split", "fp64"],
                     help="headline plan: Ozaki BF16 digits or native FP64")
     ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--max-iter", type=int, default=200,
+                    help="cup_solve: GMRES steps at most (Arnoldi steps, restarts excluded)")
     ap.add_argument("--factor", default="qr", choices=["qr", "tsvd"],
                     help="qr (default): A_n^+ applied as R^-1 Q^H; tsvd: the truncated-SVD form")
     ap.add_argument("--tuning", default=None,
@@ -1095,7 +1163,7 @@ def main():
                     help="launch the step's kernels directly instead of replaying CUDA graphs")
     ap.add_argument("--workload", default="cup",
                     choices=["cup", "smooth", "batched", "cup_near", "cup_btilde", "cup_q", "cup_c",
-                             "cup_qsvd", "cup_iter"],
+                             "cup_qsvd", "cup_iter", "cup_solve"],
                     help="cup (default, the headline), smooth; batched, cup_near, cup_btilde, cup_q "
                          "and cup_c (the periodizing scheme's blocks B~, Q and C) print their own "
                          "device-timed lines")
@@ -1117,6 +1185,9 @@ def main():
         return
     if args.workload == "cup_iter":
         run_iter(args)
+        return
+    if args.workload == "cup_solve":
+        run_solve(args)
         return
     wl = synth.config_cup() if args.workload == "cup" else synth.config_smooth()
     if args.impl == "reference":

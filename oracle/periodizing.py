@@ -84,7 +84,7 @@ import math
 import numpy as np
 import scipy.special as sps
 
-from .mfs import near_image_sum, rhs_modes, solve_modes
+from .mfs import near_image_sum, rhs_modes, solve_modes, solve_modes_tsvd
 
 __all__ = ["sph_jn", "sph_y", "sph_wave_value_grad", "plane_wave_coefficients",
            "btilde", "btilde_columns", "n_harmonics", "rb_modes", "wall_nodes", "q_matrix",
@@ -379,6 +379,15 @@ def btilde_samples(ob, coll, p, d):
     return np.einsum("wnr,nl->wrl", fB, E)
 
 
+def _a0_plus(ob, factors, fhat):
+    """A_0^+ fhat: `solve_modes` for the list of (packed QR, tau), or the
+    truncated SVD of Sec. 4.2 (`solve_modes_tsvd`, 1e-10 cutoff) when factors
+    is ("tsvd", A) with A the modal matrices [P/2+1][rows][cols]."""
+    if isinstance(factors, tuple) and factors[0] == "tsvd":
+        return solve_modes_tsvd(ob, factors[1], fhat)
+    return solve_modes(ob, factors, fhat)
+
+
 def periodic_operator_apply(ob, coll, src, factors, g, dirs, lattice, C, Q, p, cutoff=1e-10):
     """y = (I + A_else A_0^+ - B Q^+ C A_0^+) g, eq. iter, for a Neumann
     obstacle. Reading: the paper states the operator on modal data; it acts
@@ -391,10 +400,11 @@ def periodic_operator_apply(ob, coll, src, factors, g, dirs, lattice, C, Q, p, c
       xi = Q^+ (C coef)       the rows of `c_matrix`, `q_pinv_solve` with
                               the paper's 1e-10 relative cutoff
       B xi                    `btilde_samples` of xi's spherical-wave part d
-    factors: the list of (packed QR, tau) of `factor_operator`. Returns y
+    factors: the list of (packed QR, tau) of `factor_operator`, or ("tsvd",
+    A) for the paper's truncated-SVD A_0^+ (see `_a0_plus`). Returns y
     [W][M][P]."""
     W, M, P = g.shape
-    coef = solve_modes(ob, factors, rhs_modes(g))                              # [W][P][N]
+    coef = _a0_plus(ob, factors, rhs_modes(g))                                 # [W][P][N]
     ae = near_image_sum(ob, coll, src, coef, dirs, lattice).reshape(W, M, P)
     yC = coef.reshape(W, -1) @ C.T                                             # [W][8 M1^2]
     xi, _ = q_pinv_solve(Q, yC.T, cutoff)                                      # [nQ][W]
@@ -406,7 +416,8 @@ def periodic_solve_dense(ob, coll, src, factors, f, dirs, lattice, C, Q, p, cuto
     matrix over the n = M P samples, column i the image of unit vector i
     under `periodic_operator_apply`, solved by LAPACK for every wave of f
     [W][M][P]; then eta = A_0^+ eta~ (`solve_modes`) and xi = -Q^+ C eta
-    (`q_pinv_solve`). dirs [3] is the Bloch direction. Returns (eta~ [W][M][P],
+    (`q_pinv_solve`). dirs [3] is the Bloch direction; factors as in
+    `periodic_operator_apply`. Returns (eta~ [W][M][P],
     eta [W][P][N], xi [W][nQ], the operator matrix [n][n])."""
     W, M, P = f.shape
     n = M * P
@@ -414,6 +425,6 @@ def periodic_solve_dense(ob, coll, src, factors, f, dirs, lattice, C, Q, p, cuto
     Aop = periodic_operator_apply(ob, coll, src, factors, E, np.stack([np.asarray(dirs)] * n), lattice,
                                   C, Q, p, cutoff).reshape(n, n).T
     et = np.linalg.solve(Aop, f.reshape(W, n).T).T.reshape(W, M, P)
-    eta = solve_modes(ob, factors, rhs_modes(et))
+    eta = _a0_plus(ob, factors, rhs_modes(et))
     xi, _ = q_pinv_solve(Q, (eta.reshape(W, -1) @ C.T).T, cutoff)
     return et, eta, -xi.T, Aop

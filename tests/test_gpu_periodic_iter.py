@@ -205,3 +205,57 @@ def test_periodic_solve_small():
     assert e_et < 1e-10
     assert e_res < 1e-10
     assert e_xi < 1e-10
+
+
+def test_periodic_solve_ill_conditioned_tsvd():
+    """An obstacle with 140 proxies, whose worst modal block has sigma_min /
+    sigma_max near 3e-13, below the paper's 1e-10 truncation: with A_0^+ as the
+    truncated SVD (the operator's AXI_PLAN_TSVD form, Sec. 4.2) the Krylov
+    vectors' coefficients stay bounded, so the near-image sum split into 7
+    digits stays accurate and GMRES reaches 1e-10 (measured: 16 steps,
+    1.0e-11). eta~ against the oracle's dense solve with the same
+    truncated-SVD A_0^+, within kappa times the two solutions' residuals;
+    the residual of eq. iter
+    from the device's eta~, eta and xi by the oracle's steps, against the
+    same residual of the oracle's own solution (A_0^+ still amplifies
+    rounding by up to 1e10 / sigma_max, so neither is at rounding level)."""
+    from paper_1506_05083_gb300 import axi
+    wl = synth.small_case(seed=7, k=3.0, M=160, N=140, P=16)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    ob.q = O.choose_q(ob, coll, src, srcx)
+    op = axi.Operator([axi.spec_from_obstacle(ob)], prec=axi.PREC_FP64 | axi.PLAN_TSVD)
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    ex, ey, z0, m1, n0, p = 2.6, 2.3, 1.6, 6, 3, 8
+    cell = axi.Cell(ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, n0, p)
+    dirs = np.stack([d])
+    f = O.incident_samples(ob, coll, dirs)
+    Cg, US = op.c_block(cell), op.q_matrix(cell)
+    V, sig, _ = axi.svd_jacobi(US)
+    _, bt = op.btilde(p)
+    et, eta, xi, its, rel, conv = axi.periodic_solve(op, torch.tensor(f, device="cuda"), (ex, ey),
+                                                     torch.tensor(dirs, device="cuda"), Cg, US, V, sig,
+                                                     bt, p, near_slices=7, tol=1e-10, restart=40)
+    torch.cuda.synchronize()
+    assert op.status() == 0 and all(conv), (its, rel)
+    et, eta, xi = et.cpu().numpy(), eta.cpu().numpy(), xi.cpu().numpy()
+    A = O.system_matrix(ob, coll, src, srcx)
+    Co = OP.c_matrix(ob, src, cell.kx, cell.ky, ex, ey, z0, m1)
+    Qo, _ = OP.q_matrix(ob.k, p, cell.kx, cell.ky, ex, ey, z0, m1, n0)
+    et_o, eta_o, xi_o, Aop = OP.periodic_solve_dense(ob, coll, src, ("tsvd", A), f, d, (ex, ey), Co, Qo, p)
+    e_et = np.abs(et - et_o).max() / np.abs(et_o).max()
+
+    def residual(et_, eta_, xi_):
+        ae = O.near_image_sum(ob, coll, src, eta_, dirs, (ex, ey)).reshape(f.shape)
+        r = et_ + ae + OP.btilde_samples(ob, coll, p, xi_[:, :OP.n_harmonics(p)]) - f
+        return np.abs(r).max() / np.abs(f).max()
+
+    e_res, e_res_o = residual(et, eta, xi), residual(et_o, eta_o, xi_o)
+    print(f"iters {its} relres {rel}  eta~ {e_et:.2e}  residual {e_res:.2e} (oracle's own {e_res_o:.2e})  "
+          f"|eta| {np.abs(eta).max():.2e} (oracle {np.abs(eta_o).max():.2e})")
+    # two approximate solutions of a system of condition kappa differ by at
+    # most about kappa times the sum of their relative residuals (factor 2:
+    # max norms)
+    kappa = np.linalg.cond(Aop)
+    assert e_et < 2 * kappa * (e_res + e_res_o) + 1e-12, kappa
+    assert e_res < max(10 * e_res_o, 1e-10)
