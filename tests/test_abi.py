@@ -233,3 +233,19 @@ def test_iter_entries_refused_on_host():
     assert cb(2, 40, 16, 256, p16, p16, p16, 1 << 30, p16, 257 * 257, p16, None) == -1   # p > 255
     assert cb(2, 40, 16, 8, bad, p16, p16, 45 * 40, p16, 81, p16, None) == -1       # misaligned g
     assert cb(2, 40, 16, 8, p16, p16, None, 45 * 40, p16, 81, p16, None) == -1      # no B~
+
+
+def test_noalloc_arguments_refused_on_host():
+    """axi_apply_operator_noalloc refuses a null operator, null buffers and an
+    empty batch (AXI_ERR_ARG = -1) before it asks CUDA for the current
+    device; the device check itself (an operator built on another GPU than
+    the current one, or a stream of another device) needs two GPUs."""
+    import ctypes as C
+    from paper_1506_05083_gb300 import axi
+    L = axi.lib()
+    p16 = C.c_void_p(1 << 20)                     # stand-ins, never dereferenced
+    fn = L.axi_apply_operator_noalloc
+    assert fn(None, 0, 1, p16, p16, None, None) == -1
+    assert fn(p16, 0, 1, None, p16, None, None) == -1
+    assert fn(p16, 0, 1, p16, None, None, None) == -1
+    assert fn(p16, 0, 0, p16, p16, None, None) == -1
