@@ -16,6 +16,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "axi_internal.h"
@@ -297,37 +298,44 @@ extern "C" axi_status axi_gmres_create(int64_t n, int32_t W, int32_t restart, in
   axi_status s = axi_gmres_workspace_bytes(n, W, restart, &need);
   if (s != AXI_OK) return s;
   if (!d_work || work_bytes < need || (reinterpret_cast<uintptr_t>(d_work) & 255)) return AXI_ERR_WORKSPACE;
-  axi_gmres *g = new axi_gmres();
-  g->n = n;
-  g->W = W;
-  g->m = restart;
-  g->max_iter = max_iter;
-  g->tol = tol;
-  const size_t vec = sizeof(double2) * (size_t)n * W;
-  char *p = static_cast<char *>(d_work);
-  g->V = reinterpret_cast<double2 *>(p);
-  p += align256(vec * (restart + 1));
-  g->w = reinterpret_cast<double2 *>(p);
-  p += align256(vec);
-  g->c1 = reinterpret_cast<double2 *>(p);
-  p += align256(sizeof(double2) * (size_t)W * (restart + 1));
-  g->c2 = reinterpret_cast<double2 *>(p);
-  p += align256(sizeof(double2) * (size_t)W * (restart + 1));
-  g->a = reinterpret_cast<double *>(p);
-  g->state = 0;
-  g->nonfinite = false;
-  g->j = 0;
-  g->H.assign((size_t)W * (restart + 1) * restart, cplx(0.0));
-  g->cs.assign((size_t)W * restart, 0.0);
-  g->sn.assign((size_t)W * restart, cplx(0.0));
-  g->g.assign((size_t)W * (restart + 1), cplx(0.0));
-  g->bnorm.assign(W, 0.0);
-  g->relres.assign(W, 1.0);
-  g->iters.assign(W, 0);
-  g->kcyc.assign(W, 0);
-  g->conv.assign(W, 0);
-  g->live.assign(W, 0);
-  g->st = nullptr;
+  // host state: no exception may leave this C entry point
+  axi_gmres *g = new (std::nothrow) axi_gmres();
+  if (!g) return AXI_ERR_WORKSPACE;
+  try {
+    g->n = n;
+    g->W = W;
+    g->m = restart;
+    g->max_iter = max_iter;
+    g->tol = tol;
+    const size_t vec = sizeof(double2) * (size_t)n * W;
+    char *p = static_cast<char *>(d_work);
+    g->V = reinterpret_cast<double2 *>(p);
+    p += align256(vec * (restart + 1));
+    g->w = reinterpret_cast<double2 *>(p);
+    p += align256(vec);
+    g->c1 = reinterpret_cast<double2 *>(p);
+    p += align256(sizeof(double2) * (size_t)W * (restart + 1));
+    g->c2 = reinterpret_cast<double2 *>(p);
+    p += align256(sizeof(double2) * (size_t)W * (restart + 1));
+    g->a = reinterpret_cast<double *>(p);
+    g->state = 0;
+    g->nonfinite = false;
+    g->j = 0;
+    g->H.assign((size_t)W * (restart + 1) * restart, cplx(0.0));
+    g->cs.assign((size_t)W * restart, 0.0);
+    g->sn.assign((size_t)W * restart, cplx(0.0));
+    g->g.assign((size_t)W * (restart + 1), cplx(0.0));
+    g->bnorm.assign(W, 0.0);
+    g->relres.assign(W, 1.0);
+    g->iters.assign(W, 0);
+    g->kcyc.assign(W, 0);
+    g->conv.assign(W, 0);
+    g->live.assign(W, 0);
+    g->st = nullptr;
+  } catch (const std::bad_alloc &) {
+    delete g;
+    return AXI_ERR_WORKSPACE;
+  }
   *out = g;
   return AXI_OK;
 }
@@ -361,53 +369,59 @@ extern "C" axi_status axi_gmres_iterate(axi_gmres *g, const axi_c128 *d_b, axi_c
       if (!g->conv[w] && g->iters[w] < g->max_iter) return false;
     return true;
   };
-  switch (g->state) {
-    case 0: {  // x = 0, r = b
-      const std::vector<double> zero((size_t)g->W, 0.0), one((size_t)g->W, 1.0);
-      if ((e = axmy(g, zero, b, nullptr, x)) != cudaSuccess) break;
-      if ((e = axmy(g, one, b, nullptr, g->V)) != cudaSuccess) break;
-      std::vector<double2> h;
-      if ((e = dots(g, g->V, 1, g->V, g->c1, h)) != cudaSuccess) break;
-      for (int w = 0; w < g->W; ++w) g->bnorm[w] = std::sqrt(std::fmax(h[(size_t)w * (g->m + 1)].x, 0.0));
-      if ((e = start_cycle(g)) != cudaSuccess) break;
-      if (all_stopped()) {
-        g->state = 3;
+  try {
+    switch (g->state) {
+      case 0: {  // x = 0, r = b
+        const std::vector<double> zero((size_t)g->W, 0.0), one((size_t)g->W, 1.0);
+        if ((e = axmy(g, zero, b, nullptr, x)) != cudaSuccess) break;
+        if ((e = axmy(g, one, b, nullptr, g->V)) != cudaSuccess) break;
+        std::vector<double2> h;
+        if ((e = dots(g, g->V, 1, g->V, g->c1, h)) != cudaSuccess) break;
+        for (int w = 0; w < g->W; ++w) g->bnorm[w] = std::sqrt(std::fmax(h[(size_t)w * (g->m + 1)].x, 0.0));
+        if ((e = start_cycle(g)) != cudaSuccess) break;
+        if (all_stopped()) {
+          g->state = 3;
+          break;
+        }
+        g->state = 1;
+        request(g->V);
         break;
       }
-      g->state = 1;
-      request(g->V);
-      break;
+      case 1: {  // w = A V_j
+        if ((e = arnoldi_step(g)) != cudaSuccess) break;
+        g->j += 1;
+        if (!all_stopped() && g->j < g->m) {
+          request(g->V + (size_t)g->j * g->W * g->n);
+          break;
+        }
+        if ((e = end_cycle(g, x)) != cudaSuccess) break;
+        if (finished()) {
+          g->state = 3;
+          break;
+        }
+        g->state = 2;
+        request(x);
+        break;
+      }
+      case 2: {  // w = A x: V_0 = b - w, a new cycle
+        const std::vector<double> one((size_t)g->W, 1.0);
+        if ((e = axmy(g, one, b, g->w, g->V)) != cudaSuccess) break;
+        if ((e = start_cycle(g)) != cudaSuccess) break;
+        if (all_stopped()) {
+          g->state = 3;
+          break;
+        }
+        g->state = 1;
+        request(g->V);
+        break;
+      }
+      default:
+        break;
     }
-    case 1: {  // w = A V_j
-      if ((e = arnoldi_step(g)) != cudaSuccess) break;
-      g->j += 1;
-      if (!all_stopped() && g->j < g->m) {
-        request(g->V + (size_t)g->j * g->W * g->n);
-        break;
-      }
-      if ((e = end_cycle(g, x)) != cudaSuccess) break;
-      if (finished()) {
-        g->state = 3;
-        break;
-      }
-      g->state = 2;
-      request(x);
-      break;
-    }
-    case 2: {  // w = A x: V_0 = b - w, a new cycle
-      const std::vector<double> one((size_t)g->W, 1.0);
-      if ((e = axmy(g, one, b, g->w, g->V)) != cudaSuccess) break;
-      if ((e = start_cycle(g)) != cudaSuccess) break;
-      if (all_stopped()) {
-        g->state = 3;
-        break;
-      }
-      g->state = 1;
-      request(g->V);
-      break;
-    }
-    default:
-      break;
+  } catch (const std::bad_alloc &) {
+    g->state = 3;
+    *need_apply = 0;
+    return AXI_ERR_WORKSPACE;
   }
   if (e != cudaSuccess) return AXI_ERR_CUDA;
   if (g->nonfinite) {
