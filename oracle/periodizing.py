@@ -76,6 +76,8 @@ Pins (tests/test_oracle_periodizing.py):
   periodic_operator_apply   composed of the functions above, each pinned
   periodic_solve_dense      the assembled matrix reproduces the operator on
                      a random vector; the solve is LAPACK's
+  _a0_plus           the truncated-SVD and QR forms agree when no singular
+                     value falls below the cutoff
 """
 from __future__ import annotations
 

@@ -232,3 +232,24 @@ def test_periodic_solve_dense_assembly():
     back = OP.periodic_operator_apply(ob, coll, src, fac, et, np.stack([d, d]), (ex, ey), C, Q, p)
     assert np.abs(back - f).max() < 1e-10 * np.abs(f).max()
     assert xi.shape == (2, Q.shape[1]) and eta.shape == (2, ob.P, ob.N)
+
+
+def test_a0_plus_forms_agree_when_nothing_is_truncated():
+    """With every modal singular value above the 1e-10 cutoff, the truncated-
+    SVD A_0^+ (("tsvd", A)) and the QR solve give the same eq. iter operator:
+    pins the dispatch between the two forms."""
+    wl = synth.small_case(seed=7, k=3.0, M=20, N=16, P=8)
+    ob = wl.obstacles[0]
+    coll, src, srcx = O.geometry(ob)
+    ob.q = O.choose_q(ob, coll, src, srcx)
+    A, fac = O.factor_operator(ob, coll, src, srcx)
+    assert min(np.linalg.svd(A[d], compute_uv=False)[-1] / np.linalg.norm(A[d], 2)
+               for d in range(A.shape[0])) > 1e-8
+    d = np.array([0.36, -0.28, np.sqrt(1 - 0.36**2 - 0.28**2)])
+    ex, ey, z0, m1, n0, p = 2.6, 2.3, 1.6, 6, 2, 3
+    C = OP.c_matrix(ob, src, ob.k * d[0], ob.k * d[1], ex, ey, z0, m1)
+    Q, _ = OP.q_matrix(ob.k, p, ob.k * d[0], ob.k * d[1], ex, ey, z0, m1, n0)
+    g = np.random.default_rng(4).normal(size=(2, ob.M, ob.P)) + 0j
+    y_qr = OP.periodic_operator_apply(ob, coll, src, fac, g, np.stack([d, d]), (ex, ey), C, Q, p)
+    y_sv = OP.periodic_operator_apply(ob, coll, src, ("tsvd", A), g, np.stack([d, d]), (ex, ey), C, Q, p)
+    assert np.abs(y_qr - y_sv).max() < 1e-10 * np.abs(y_qr).max()
