@@ -950,6 +950,11 @@ def run_iter(args):
                        "l2": "flushed (256 MB write) before each timed step; C (8.5 GB) exceeds L2"},
             "stages_ms": st_ms,
             "near_pairs_per_s": ob.M * ob.P * ob.N * ob.P * 8 * W / (st_ms["near"] * 1e-3),
+            "dominant_stage": {"stage": max(st_ms, key=st_ms.get),
+                               "share": max(st_ms.values()) / sum(st_ms.values()),
+                               "note": "at 16 waves the near-image sum is bound by its FP64 kernel values "
+                                       "(one per target, source and image, the same for any W); its tcgen05 "
+                                       "GEMM's roofline is on the cup_near line; 'roofline' below is C eta's"},
             "roofline": {"bound": "alu", "achieved": tfl, "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": tfl / FP64_DFMA_PEAK_TFLOPS, "traffic": None, "kernel": "matvec_kernel<16>",
                          "work": f"C eta: 8 flops per complex MAC, {W} vectors; C read once at {gbs:.0f} GB/s",
