@@ -397,7 +397,10 @@ axi_status axi_fill_c(const axi_operator *op, int32_t obs, const axi_cell *cell,
 
 /*
  * Q^+ through the SVD (Sec. 4.2: the periodizing rows Q are inverted by
- * their singular value decomposition), for any dense complex matrix.
+ * their singular value decomposition), for any dense complex matrix with at
+ * least as many rows as columns. For Q (8 m1^2 rows, (p + 1)^2 + 2 n_rb
+ * columns; axi_q_shape) that asks for enough wall nodes: the paper's m1 of
+ * about 4 nodes per wavelength across a face keeps Q tall.
  *
  * axi_svd_jacobi: one-sided (Hestenes) Jacobi SVD of the m x n matrix d_A
  * (m >= n >= 1, column-major, leading dimension lda >= m), in place: on

@@ -33,9 +33,10 @@ _vp = C.c_void_p
 
 def svd_jacobi(A: torch.Tensor, tol=None, max_sweeps=30, stream=None):
     """axi_svd_jacobi on a [n][m] complex128 CUDA tensor holding the m x n
-    matrix column-major (transposed view of the rows); A is overwritten with
-    U Sigma. tol defaults to sqrt(m) times the double rounding unit. Returns
-    (V as [n][n] column-major, sigma [n], sweeps)."""
+    matrix column-major (transposed view of the rows; m >= n, so a Q from
+    `Operator.q_matrix` needs at least as many wall rows as columns); A is
+    overwritten with U Sigma. tol defaults to sqrt(m) times the double
+    rounding unit. Returns (V as [n][n] column-major, sigma [n], sweeps)."""
     if A.dtype != torch.complex128 or not A.is_cuda or not A.is_contiguous() or A.dim() != 2:
         raise ValueError("svd_jacobi: A must be a contiguous complex128 CUDA tensor [n][m]")
     n, m = A.shape
