@@ -249,3 +249,41 @@ def test_noalloc_arguments_refused_on_host():
     assert fn(p16, 0, 1, None, p16, None, None) == -1
     assert fn(p16, 0, 1, p16, None, None, None) == -1
     assert fn(p16, 0, 0, p16, p16, None, None) == -1
+
+
+def test_gmres_host_state_without_a_gpu():
+    """The GMRES driver's host side needs no device: the workspace size is
+    (restart + 1) basis blocks, one more block and small scalars per wave
+    (256-byte aligned pieces); create refuses a short or misaligned buffer
+    (AXI_ERR_WORKSPACE = -4) and bad arguments (-1); a fresh state reports
+    no steps, residual 1 and not converged; destroy releases it. The
+    vector scaling refuses null or misaligned buffers and does nothing for
+    an empty count."""
+    import ctypes as C
+    from paper_1506_05083_gb300 import axi
+    L = axi.lib()
+    nb = C.c_size_t()
+    n, W, m = 1000, 3, 8
+    assert L.axi_gmres_workspace_bytes(n, W, m, C.byref(nb)) == 0
+    a256 = lambda b: (b + 255) // 256 * 256                                  # noqa: E731
+    vec = 16 * n * W
+    assert nb.value == a256(vec * (m + 1)) + a256(vec) + 2 * a256(16 * W * (m + 1)) + a256(8 * W)
+    assert L.axi_gmres_workspace_bytes(n, W, 0, C.byref(nb)) == -1
+    assert L.axi_gmres_workspace_bytes(n, 0, m, C.byref(nb)) == -1
+    L.axi_gmres_workspace_bytes(n, W, m, C.byref(nb))
+    base = C.c_void_p(1 << 24)                    # aligned stand-in, never dereferenced here
+    g = C.c_void_p()
+    assert L.axi_gmres_create(n, W, m, 100, 1e-12, base, nb.value - 1, C.byref(g)) == -4
+    assert L.axi_gmres_create(n, W, m, 100, 1e-12, C.c_void_p((1 << 24) + 16), nb.value, C.byref(g)) == -4
+    assert L.axi_gmres_create(n, W, m, 0, 1e-12, base, nb.value, C.byref(g)) == -1
+    assert L.axi_gmres_create(n, W, m, 100, -1.0, base, nb.value, C.byref(g)) == -1
+    assert L.axi_gmres_create(n, W, m, 100, 1e-12, base, nb.value, C.byref(g)) == 0 and g.value
+    its, rel, conv = (C.c_int32 * W)(), (C.c_double * W)(), (C.c_int32 * W)()
+    assert L.axi_gmres_result(g, its, rel, conv) == 0
+    assert list(its) == [0] * W and list(rel) == [1.0] * W and list(conv) == [0] * W
+    need, din, dout = C.c_int32(), C.c_void_p(), C.c_void_p()
+    assert L.axi_gmres_iterate(g, None, base, C.byref(need), C.byref(din), C.byref(dout), None) == -1
+    assert L.axi_gmres_destroy(g) == 0
+    assert L.axi_vec_scale(4, 2.0, None, None) == -1
+    assert L.axi_vec_scale(4, 2.0, C.c_void_p((1 << 20) + 8), None) == -1
+    assert L.axi_vec_scale(0, 2.0, C.c_void_p(1 << 20), None) == 0
